@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Benchmark: MC spin-updates per second of PTCA sweeps at 100x100 with 8x8
+traveling clusters (n = 128 complex Hermitian), 30-degree cone proposals,
+t = 1, J_H = 8, mu = -6.5, T = 0.05.
+
+One step = one sweep (every site gets one proposal; 2 cluster eigensolves per
+proposal).  The headline is the mixed-precision path (FP32 reduction to
+tridiagonal form, FP64 eigenvalues and free energies); the plain FP64 GPU path
+is timed beside it on the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (under torchrun) every rank runs an independent replica
+chain (seed + rank); there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(Lx=100, Ly=100, L_c=8, periodic=1, t=1.0, J_H=8.0, mu=-6.5, T=0.05, cone_deg=30.0, seed=0)
+METRIC = "MC spin-updates/sec at 100x100, 8x8 cluster, vs plain FP64 GPU path"
+N_ORDER = 128
+# Algorithmic real flops of the Householder reduction of one n x n Hermitian
+# matrix in this implementation: each step reads and rewrites the trailing
+# triangle once with 16 real FMA per complex element (rank-2 update + both
+# halves of the Hermitian matrix-vector product): sum_m 32 m(m+1)/2 ~ (16/3) n^3.
+HH_FLOPS = sum(32 * m * (m + 1) // 2 for m in range(1, N_ORDER))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_alu_peak_tflops(sm_mhz: float) -> float:
+    # 152 SMs x 128 FP32 FMA lanes x 2 flops per FMA x SM clock.
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(cfg_kw, budget_s: float = 12.0, max_visits: int = 64):
+    """Oracle (plain FP64 C, one core) on a bounded sample of the workload:
+    the first visits of the first stage of the sweep, each = 2 cluster
+    diagonalisations + Metropolis.  Returns (updates/s, visits, seconds)."""
+    import math as _m
+
+    import oracle
+    m = oracle.Model(Lx=cfg_kw["Lx"], Ly=cfg_kw["Ly"], Lc=cfg_kw["L_c"], t=cfg_kw["t"], JH=cfg_kw["J_H"],
+                     mu=cfg_kw["mu"], T=cfg_kw["T"], schedule=cfg_kw["schedule"], stride=cfg_kw.get("stride", 0),
+                     proposal=1, cone_deg=cfg_kw["cone_deg"], seed=cfg_kw["seed"])
+    S = oracle.init_spins(m)
+    stage = oracle.schedule(m)[0]
+    t0 = time.perf_counter()
+    done = 0
+    for s in stage[:max_visits]:
+        s = int(s)
+        Fo = oracle.cluster_free_energy(m, S, s)
+        sn = oracle.propose(m, 0, s, S[s])
+        Fn = oracle.cluster_free_energy(m, S, s, sn)
+        u = oracle.uniform2(m.seed, 0, s, 2)[0]
+        _ = _m.log(u) < -(Fn - Fo) / m.T
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm, timed on the host cores."""
+    if rank != 0:
+        return
+    cfg_kw = dict(WORKLOAD, schedule=1, stride=0)
+    import oracle
+    oracle.build()
+    per_step = []
+    visits = 0
+    for i in range(args.warmup + args.steps):
+        rate, done, dt = cpu_oracle_rate(cfg_kw, budget_s=max(2.0, 30.0 / max(1, args.steps + args.warmup)),
+                                         max_visits=8)
+        if i >= args.warmup:
+            per_step.append(dt / done)
+            visits += done
+    sec_per_update = sum(per_step) / len(per_step)
+    value = 1.0 / sec_per_update
+    N = WORKLOAD["Lx"] * WORKLOAD["Ly"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_update * N,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "100x100 torus, 8x8 clusters (n=128), cone 30deg, T=0.05, block schedule",
+                   "sample": "first 8 visits of stage 0 per step"},
+        "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{visits} visits (2 Jacobi eigensolves of 128x128 each) over {args.steps} steps"},
+        "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def time_sweeps(ctx, steps, warmup, flush_buf, stream):
+    """Per-step device time (ms) of one sweep each, L2 flushed between steps."""
+    import torch
+    import paper_1502_07028_gb300 as P
+    for _ in range(warmup):
+        P.ptca_sweep(ctx.h, 1, stats=False, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush_buf.add_(1)  # write 256 MiB: evicts the 129 MB L2 between timed steps
+        ev[i][0].record(stream)
+        P.ptca_sweep(ctx.h, 1, stats=False, stream=stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--schedule", default="block", choices=["block", "tiled10", "tiled5"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_07028_gb300 as P
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    sched = {"block": (P.SCHEDULE_BLOCK, 0), "tiled10": (P.SCHEDULE_TILED, 10), "tiled5": (P.SCHEDULE_TILED, 5)}
+    schedule, stride = sched[args.schedule]
+    base = dict(WORKLOAD, seed=WORKLOAD["seed"] + rank, proposal=P.PROPOSAL_CONE, schedule=schedule, stride=stride)
+    N = base["Lx"] * base["Ly"]
+    n_stages = len(P.ptca_schedule(P.Config(**base, precision=P.MIXED)))
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    # --- mixed precision (headline)
+    ctx = P.Context(P.Config(**base, precision=P.MIXED))
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        step_ms = time_sweeps(ctx, args.steps, args.warmup, flush, stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier(world)
+    total_ms = max_over_ranks(world, sum(step_ms))
+    value = world * N * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    # --- end to end through the public API with host buffers
+    pin = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+    P.ptca_get_spins(ctx.h, pin, stream=stream)
+    out = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.ptca_set_spins(ctx.h, pin, stream=stream)       # H2D of the step's input configuration
+        P.ptca_sweep(ctx.h, 1, stats=False, stream=stream)
+        P.ptca_get_spins(ctx.h, out, stream=stream)       # D2H of the result (synchronises)
+        pin.copy_(out)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_value = world * N * e2e_steps / e2e_s
+    stats = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
+    acc_rate = stats.accepted / stats.attempts
+    ctx.close()
+
+    # --- plain FP64 GPU path on the same workload
+    ctx64 = P.Context(P.Config(**base, precision=P.FP64))
+    fp64_ms = time_sweeps(ctx64, args.fp64_steps, 1, flush, stream)
+    ctx64.close()
+    fp64_value = N * args.fp64_steps / (sum(fp64_ms) * 1e-3)
+
+    # --- roofline of the dominant kernel (the stage kernel, FP32 reduction)
+    launches_per_step = n_stages + 1
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    matrices_per_step = 2 * N
+    achieved_tflops = matrices_per_step * HH_FLOPS / (ms_per_step * 1e-3) / 1e12
+    peak = fp32_alu_peak_tflops(clocks["sm_max_mhz"] or 2070.0)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, done, dt = cpu_oracle_rate(dict(base), budget_s=15.0, max_visits=48)
+        cpu = {"value": rate, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} visits of the first stage (2 Jacobi eigensolves of 128x128 each), {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"100x100 torus, 8x8 clusters (n=128 complex Hermitian), cone 30deg, "
+                                   f"T=0.05, mu=-6.5, J_H=8, {args.schedule} schedule ({n_stages} stages), "
+                                   f"mixed precision", "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": "spin-updates/s", "h2d_bytes_per_step": N * 24,
+                    "d2h_bytes_per_step": N * 24},
+            "gpu_launches": launches_per_step * args.steps,
+            "fp64_path": {"value": fp64_value, "unit": "spin-updates/s", "ms_per_step": sum(fp64_ms) / len(fp64_ms)},
+            "speedup_vs_fp64_path": value / fp64_value / world,
+            "eigensolves_per_s": 2 * value,
+            "acceptance": acc_rate,
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak, "traffic": None,
+                         "note": "FP32 FMA pipe, Householder flops only; peak = 152 SM x 128 lanes x 2 x max clock"},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

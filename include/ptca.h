@@ -1,0 +1,228 @@
+/*
+ * ptca.h -- C ABI of the GB300 traveling-cluster Monte Carlo library (libptca.so).
+ *
+ * The library runs the hot path of the parallelised traveling cluster
+ * approximation (PTCA, Sec. III of Mukherjee, Patel, Bishop, Dagotto,
+ * arXiv:1502.07028) for the double-exchange spin-fermion model on a square
+ * lattice: classical unit spins S_i, electrons with nearest-neighbour hopping
+ * -t and a Hund coupling -J_H S_i . sigma.  For an update site i_s the
+ * traveling cluster is the L_c x L_c window of sites around it (Sec. II.b,
+ * Fig. 1); its Hamiltonian is a 2N_c x 2N_c complex Hermitian matrix (two spin
+ * species, Sec. IV).  Its eigenvalues eps_k give the cluster free energy
+ *     F = -T sum_k ln(1 + exp(-(eps_k - mu)/T))
+ * (the periodic cluster is a grand-canonical ensemble, Sec. II.b), and
+ * Metropolis on dF = F_new - F_old accepts or rejects a proposed spin
+ * (Sec. II.c steps a-f).  A sweep is a list of stages; the update sites of a
+ * stage are processed at once from the configuration at the start of the
+ * stage (Sec. III.a), which the schedule guarantees is the same as visiting
+ * them one after another.
+ *
+ * Conventions for every entry point:
+ *   - All compute runs in hand-written CUDA kernels on the device that was
+ *     current when ptca_init was called.  There is no CPU fallback: without a
+ *     usable GPU, ptca_init returns PTCA_ERR_CUDA.
+ *   - Buffers are owned by the caller unless stated.  "device pointer" means
+ *     memory the GPU can dereference (cudaMalloc / torch CUDA tensors).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered and asynchronous unless stated.
+ *   - No exception crosses the ABI.  On failure a call returns a status other
+ *     than PTCA_OK and ptca_last_error() describes it (per thread).  Invalid
+ *     arguments are rejected before any launch (PTCA_ERR_INVALID).
+ *   - Complex matrices are stored as the packed lower triangle, row-major:
+ *     element (r, c), c <= r, at index r(r+1)/2 + c, each element an
+ *     interleaved (re, im) pair of double (PTCA_FP64) or float (PTCA_MIXED).
+ *   - Spins are N x 3 row-major doubles (S_x, S_y, S_z), site i = y*Lx + x.
+ */
+#ifndef PTCA_H
+#define PTCA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTCA_VERSION_MAJOR 0
+#define PTCA_VERSION_MINOR 1
+
+typedef struct ptca_ctx ptca_ctx; /* opaque; created by ptca_init, freed by ptca_destroy */
+
+typedef enum {
+    PTCA_OK = 0,
+    PTCA_ERR_INVALID = 1,     /* bad argument or unsupported size, nothing launched  */
+    PTCA_ERR_CUDA = 2,        /* a CUDA call failed (no device, launch error, ...)    */
+    PTCA_ERR_OOM = 3,         /* device allocation failed                            */
+    PTCA_ERR_TIMEOUT = 4,     /* a bounded device-wide wait gave up                  */
+    PTCA_ERR_NUMERIC = 5,     /* NaN/Inf met in a free energy or eigenvalue          */
+    PTCA_ERR_UNSUPPORTED = 6  /* valid request that this build does not implement    */
+} ptca_status;
+
+enum { PTCA_SCHEDULE_TILED = 0, PTCA_SCHEDULE_BLOCK = 1 };
+enum { PTCA_FP64 = 0, PTCA_MIXED = 1 };
+enum { PTCA_PROPOSAL_SPHERE = 0, PTCA_PROPOSAL_CONE = 1 };
+
+/* Square lattice.  Ly == 1 is a one-dimensional chain (Sec. III.a, Fig. 3). */
+typedef struct {
+    int32_t Lx, Ly;
+    int32_t periodic; /* 1: torus; 0: open edges (windows are clipped at the edges) */
+} ptca_lattice;
+
+typedef struct {
+    double t;                 /* hopping                                              */
+    double J_H;               /* Hund coupling                                        */
+    double mu;                /* chemical potential                                   */
+    double T;                 /* temperature (> 0)                                    */
+    int32_t L_c;              /* linear cluster size, 2 <= L_c <= min(Lx, Ly)         */
+    int32_t cluster_periodic; /* -1: same as the lattice; 1: wrap inside the window   */
+                              /* (Sec. II.b); 0: open cluster                         */
+    int32_t update_offset;    /* position of the update site inside the window along  */
+                              /* each axis; -1: floor(L_c/2) for the tiled schedule,  */
+                              /* 0 (corner, Sec. III.a) for the block schedule        */
+    int32_t schedule;         /* PTCA_SCHEDULE_TILED or PTCA_SCHEDULE_BLOCK            */
+    int32_t stride;           /* tiled schedule: spacing of the update sites in a     */
+                              /* stage along each axis; 0: L_c                        */
+    int32_t precision;        /* PTCA_FP64 or PTCA_MIXED (FP32 reduction to tridiagonal */
+                              /* form; FP64 eigenvalues, free energies and dF)        */
+    int32_t proposal;         /* PTCA_PROPOSAL_SPHERE or PTCA_PROPOSAL_CONE            */
+    int32_t reserved0;
+    double cone_deg;          /* half-angle of the cone proposal, degrees             */
+    uint64_t seed;            /* key of the counter-based generator                   */
+} ptca_params;
+
+/* Per-call sweep statistics (host struct filled by ptca_sweep when non-NULL). */
+typedef struct {
+    int64_t attempts;   /* proposals made (N per sweep)                               */
+    int64_t accepted;   /* proposals accepted                                          */
+    int64_t eigensolves;/* cluster matrices diagonalised (2 per proposal)              */
+    int64_t resolved;   /* PTCA_MIXED: proposals re-solved in FP64 near the threshold  */
+    int64_t sweeps;     /* sweeps run so far on this context (RNG sweep counter)       */
+    double  seconds;    /* device time of the call, from CUDA events                   */
+} ptca_sweep_stats;
+
+/* Observables of the current configuration (ptca_observables). */
+typedef struct {
+    double S_00;        /* S(q) at q = (0,0), Eq. 2 for one configuration              */
+    double S_pipi;      /* S(q) at q = (pi,pi)                                          */
+    double F_site;      /* last sweep: mean over visits of F of the accepted state / N_c */
+    double acceptance;  /* last sweep: accepted / attempts                              */
+    double filling;     /* last sweep: mean over visits of sum_k f(eps_k) / N_c, f the  */
+                        /* Fermi function, for the accepted state                      */
+} ptca_obs;
+
+/* ----------------------------------------------------------------------- */
+/* Context lifetime                                                          */
+/* ----------------------------------------------------------------------- */
+
+/* Validate the problem, build the stage schedule (Sec. III.a), allocate the
+ * device state and draw the initial spins uniformly on the sphere from
+ * `seed` (counter-based Philox4x32-10).  Rejects with PTCA_ERR_INVALID:
+ * L_c out of range, a stride that lets a window of one stage contain another
+ * update site of the same stage that precedes it, a block schedule with
+ * L_c > floor(L/2)+1 on a torus, a tiled stride that does not divide L on a
+ * torus, T <= 0, a matrix size above the supported maximum (n = 2 N_c <= 224).
+ * Synchronous.  *out receives the context (owned by the library). */
+ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, ptca_ctx** out);
+
+/* Free every device buffer of the context.  Synchronous.  NULL is a no-op. */
+ptca_status ptca_destroy(ptca_ctx* ctx);
+
+/* Change the temperature (T > 0) or the chemical potential for later calls. */
+ptca_status ptca_set_T(ptca_ctx* ctx, double T);
+ptca_status ptca_set_mu(ptca_ctx* ctx, double mu);
+
+/* Copy the N x 3 spins out of / into the context.  on_device != 0: dst/src are
+ * device pointers and the copy is stream-ordered; on_device == 0: host
+ * pointers, and the call synchronises `stream` before returning.
+ * ptca_set_spins does not renormalise. */
+ptca_status ptca_get_spins(ptca_ctx* ctx, double* dst, int on_device, void* stream);
+ptca_status ptca_set_spins(ptca_ctx* ctx, const double* src, int on_device, void* stream);
+
+/* ----------------------------------------------------------------------- */
+/* Batched building blocks (each step of Sec. II.c, for many clusters)       */
+/* ----------------------------------------------------------------------- */
+
+/* Largest matrix order n (= 2 N_c) of this context and the element stride of
+ * the packed-triangle slots that ptca_build_clusters uses (nmax(nmax+1)/2). */
+ptca_status ptca_dims(const ptca_ctx* ctx, int32_t* nmax, int64_t* packed_stride);
+
+/* Step b (and d, with new_spins): build the cluster Hamiltonians H_clus of m
+ * update sites from the current spins.
+ *   sites      device int32[m], lattice sites (0 <= site < N)
+ *   new_spins  device double[m*3] replacing the spin of each update site, or NULL
+ *   H_out      device buffer of m * packed_stride complex elements in the
+ *              context precision; matrix i starts at offsets_out[i]
+ *   offsets_out device int64[m]  (= i * packed_stride)
+ *   n_out      device int32[m]   matrix order 2 * (window sites)
+ * Window, boundary and basis follow the module comment; basis index of window
+ * site (wx, wy) and spin s is 2*(wy*ex + wx) + s. */
+ptca_status ptca_build_clusters(ptca_ctx* ctx, const int32_t* sites, int32_t m,
+                                const double* new_spins, void* H_out, int64_t* offsets_out,
+                                int32_t* n_out, void* stream);
+
+/* Steps b/d: all eigenvalues, ascending, of m packed Hermitian matrices.
+ *   H        device, packed lower triangles in the context precision
+ *   offsets  device int64[m], element offset of matrix i in H
+ *   n        device int32[m], order of matrix i (1 <= n <= nmax)
+ *   eig_out  device double[], eigenvalues of matrix i at eig_out + eig_offsets[i]
+ *   eig_offsets device int64[m]
+ * PTCA_FP64: FP64 Householder reduction to tridiagonal form, FP64 bisection.
+ * PTCA_MIXED: FP32 reduction, FP32 bisection, one FP64 Newton correction per
+ * eigenvalue on the tridiagonal.  Sizes are checked on the device; a matrix
+ * with n outside [1, nmax] gets NaN eigenvalues. */
+ptca_status ptca_cluster_eigvals(ptca_ctx* ctx, const void* H, const int64_t* offsets,
+                                 const int32_t* n, int32_t m, double* eig_out,
+                                 const int64_t* eig_offsets, void* stream);
+
+/* Grand-canonical free energy of each eigenvalue list:
+ * F_i = -T sum_k ln(1 + exp(-(eig_k - mu)/T)), FP64, written to F_out[i]
+ * (device double[m]).  eig/eig_offsets/n as in ptca_cluster_eigvals. */
+ptca_status ptca_free_energy(ptca_ctx* ctx, const double* eig, const int64_t* eig_offsets,
+                             const int32_t* n, int32_t m, double mu, double T, double* F_out,
+                             void* stream);
+
+/* ----------------------------------------------------------------------- */
+/* The hot path: whole sweeps                                                */
+/* ----------------------------------------------------------------------- */
+
+/* Run n_sweeps PTCA sweeps (Sec. III.a-b): for every stage, every update site
+ * of the stage gathers its window, proposes a spin (Philox, counter =
+ * (site, purpose, sweep)), builds H_old and H_new, reduces both to tridiagonal
+ * form, computes their eigenvalues and free energies, and accepts iff
+ * ln u < -(F_new - F_old)/T; accepted spins become visible to the next stage.
+ * Asynchronous when stats_out == NULL; otherwise synchronises `stream` and
+ * fills *stats_out. */
+ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_out, void* stream);
+
+/* Per-visit record of the last sweep, in flattened stage order (length N):
+ * update site, F_old, F_new, ln u and the decision (1 accepted).  Device
+ * pointers; any of them may be NULL.  Stream-ordered. */
+ptca_status ptca_sweep_record(ptca_ctx* ctx, int32_t* site, double* F_old, double* F_new,
+                              double* lnu, uint8_t* accepted, void* stream);
+
+/* Observables of the current configuration and the last sweep (see
+ * ptca_obs).  S(q) follows Eq. 2 for one configuration.  Synchronises
+ * `stream` and writes the host struct *out. */
+ptca_status ptca_observables(ptca_ctx* ctx, ptca_obs* out, void* stream);
+
+/* ----------------------------------------------------------------------- */
+/* Host-only helpers (no GPU needed)                                         */
+/* ----------------------------------------------------------------------- */
+
+/* The stage schedule ptca_init would use (Sec. III.a), without a GPU.
+ * stage_start: host int32[N+1], sites: host int32[N]; *n_stages receives the
+ * number of stages; stage s holds sites[stage_start[s] .. stage_start[s+1]).
+ * Same validation as ptca_init. */
+ptca_status ptca_schedule(const ptca_lattice* lattice, const ptca_params* params,
+                          int32_t* stage_start, int32_t* sites, int32_t* n_stages);
+
+/* Description of the last failure on this thread (never NULL). */
+const char* ptca_last_error(void);
+
+/* Library version as major*100 + minor. */
+int32_t ptca_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTCA_H */

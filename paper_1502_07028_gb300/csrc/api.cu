@@ -1,0 +1,489 @@
+// api.cu -- C ABI of libptca.so (declared in include/ptca.h): argument
+// validation, the PTCA stage schedule (Sec. III.a), device state and the
+// launch sequence of a sweep.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ptca.h"
+#include "kernels.cuh"
+#include "launch.h"
+
+using ptca::Model;
+using ptca::StageArgs;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+ptca_status fail(ptca_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+ptca_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(e == cudaErrorMemoryAllocation ? PTCA_ERR_OOM : PTCA_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define PTCA_CUDA(call)                                              \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);          \
+    } while (0)
+
+// Resolved problem (defaults filled in).
+struct Problem {
+    int Lx, Ly, periodic, Lc, ox, oy, cluster_periodic, schedule, stride, precision, proposal;
+    double t, JH, mu, T, cone_deg;
+    uint64_t seed;
+    int N() const { return Lx * Ly; }
+    int nsite_max() const { return Lc * (Ly == 1 ? 1 : Lc); }
+    int nmax() const { return 2 * nsite_max(); }
+};
+
+// Window along one axis (same rule as the device code).
+void window_axis(int L, int periodic, int Lc, int o, int c, int& start, int& ext) {
+    if (L == 1) { start = 0; ext = 1; return; }
+    int a = c - o, b = c - o + Lc - 1;
+    if (periodic) { start = ((a % L) + L) % L; ext = Lc; return; }
+    if (a < 0) a = 0;
+    if (b > L - 1) b = L - 1;
+    start = a; ext = b - a + 1;
+}
+
+// Stage lists.  Tiled: stage (ax, ay) holds (ax + s p, ay + s q), row-major;
+// block: the lattice halved along each axis, 2^d blocks (Sec. III.a), each
+// block one stage, row-major inside.
+void make_schedule(const Problem& p, std::vector<int32_t>& start, std::vector<int32_t>& sites) {
+    start.assign(1, 0);
+    sites.clear();
+    sites.reserve(p.N());
+    if (p.schedule == PTCA_SCHEDULE_TILED) {
+        const int s = p.stride, sy = p.Ly == 1 ? 1 : s;
+        for (int ay = 0; ay < sy && ay < p.Ly; ++ay)
+            for (int ax = 0; ax < s && ax < p.Lx; ++ax) {
+                for (int y = ay; y < p.Ly; y += sy)
+                    for (int x = ax; x < p.Lx; x += s) sites.push_back(y * p.Lx + x);
+                start.push_back((int32_t)sites.size());
+            }
+    } else {
+        const int hx = (p.Lx + 1) / 2, hy = (p.Ly + 1) / 2, nby = p.Ly == 1 ? 1 : 2;
+        for (int by = 0; by < nby; ++by)
+            for (int bx = 0; bx < 2; ++bx) {
+                const int xa = bx ? hx : 0, xb = bx ? p.Lx : hx;
+                const int ya = p.Ly == 1 ? 0 : (by ? hy : 0), yb = p.Ly == 1 ? 1 : (by ? p.Ly : hy);
+                for (int y = ya; y < yb; ++y)
+                    for (int x = xa; x < xb; ++x) sites.push_back(y * p.Lx + x);
+                if ((int32_t)sites.size() > start.back()) start.push_back((int32_t)sites.size());
+            }
+    }
+}
+
+// Concurrent processing of a stage from its start configuration equals
+// visiting its sites one after another iff no site of the stage lies in the
+// window of a site listed after it.  Checked exactly over every window.
+bool schedule_exact(const Problem& p, const std::vector<int32_t>& start, const std::vector<int32_t>& sites,
+                    std::string& why) {
+    const int N = p.N();
+    std::vector<int32_t> stage_of(N, -1), pos(N, -1);
+    for (size_t s = 0; s + 1 < start.size(); ++s)
+        for (int k = start[s]; k < start[s + 1]; ++k) { stage_of[sites[k]] = (int)s; pos[sites[k]] = k; }
+    for (int k = 0; k < N; ++k) {
+        const int b = sites[k], cx = b % p.Lx, cy = b / p.Lx;
+        int x0, ex, y0, ey;
+        window_axis(p.Lx, p.periodic, p.Lc, p.ox, cx, x0, ex);
+        window_axis(p.Ly, p.periodic, p.Lc, p.oy, cy, y0, ey);
+        for (int wy = 0; wy < ey; ++wy)
+            for (int wx = 0; wx < ex; ++wx) {
+                int x = x0 + wx, y = y0 + wy;
+                if (p.periodic) { x %= p.Lx; y %= p.Ly; }
+                const int g = y * p.Lx + x;
+                if (g != b && stage_of[g] == stage_of[b] && pos[g] < pos[b]) {
+                    char buf[160];
+                    snprintf(buf, sizeof buf, "site %d lies in the window of site %d of the same stage", g, b);
+                    why = buf;
+                    return false;
+                }
+            }
+    }
+    return true;
+}
+
+ptca_status resolve(const ptca_lattice* lat, const ptca_params* par, Problem& p) {
+    if (!lat || !par) return fail(PTCA_ERR_INVALID, "null lattice or params");
+    p.Lx = lat->Lx; p.Ly = lat->Ly; p.periodic = lat->periodic ? 1 : 0;
+    if (p.Lx < 1 || p.Ly < 1 || (int64_t)p.Lx * p.Ly > (1 << 26))
+        return fail(PTCA_ERR_INVALID, "lattice extents out of range");
+    p.Lc = par->L_c;
+    if (p.Lc < 2 || p.Lc > p.Lx || (p.Ly > 1 && p.Lc > p.Ly))
+        return fail(PTCA_ERR_INVALID, "L_c must satisfy 2 <= L_c <= min(Lx, Ly)");
+    p.schedule = par->schedule;
+    if (p.schedule != PTCA_SCHEDULE_TILED && p.schedule != PTCA_SCHEDULE_BLOCK)
+        return fail(PTCA_ERR_INVALID, "unknown schedule");
+    int o = par->update_offset;
+    if (o < 0) o = p.schedule == PTCA_SCHEDULE_TILED ? p.Lc / 2 : 0;
+    if (o >= p.Lc) return fail(PTCA_ERR_INVALID, "update_offset must be < L_c");
+    p.ox = o;
+    p.oy = p.Ly == 1 ? 0 : o;
+    p.cluster_periodic = par->cluster_periodic < 0 ? p.periodic : (par->cluster_periodic ? 1 : 0);
+    p.stride = par->stride > 0 ? par->stride : p.Lc;
+    if (p.schedule == PTCA_SCHEDULE_TILED && p.periodic &&
+        (p.Lx % p.stride != 0 || (p.Ly > 1 && p.Ly % p.stride != 0)))
+        return fail(PTCA_ERR_INVALID, "tiled stride must divide the lattice extents on a torus");
+    p.precision = par->precision;
+    if (p.precision != PTCA_FP64 && p.precision != PTCA_MIXED) return fail(PTCA_ERR_INVALID, "unknown precision");
+    p.proposal = par->proposal;
+    if (p.proposal != PTCA_PROPOSAL_SPHERE && p.proposal != PTCA_PROPOSAL_CONE)
+        return fail(PTCA_ERR_INVALID, "unknown proposal");
+    p.t = par->t; p.JH = par->J_H; p.mu = par->mu; p.T = par->T; p.cone_deg = par->cone_deg; p.seed = par->seed;
+    if (!std::isfinite(p.t) || !std::isfinite(p.JH) || !std::isfinite(p.mu) || !std::isfinite(p.T) || !(p.T > 0))
+        return fail(PTCA_ERR_INVALID, "t, J_H, mu must be finite and T > 0");
+    if (p.proposal == PTCA_PROPOSAL_CONE && !(p.cone_deg > 0 && p.cone_deg <= 180))
+        return fail(PTCA_ERR_INVALID, "cone_deg must lie in (0, 180]");
+    if (p.nmax() > ptca::cluster_max_order(p.precision == PTCA_MIXED ? 1 : 0))
+        return fail(PTCA_ERR_INVALID, "cluster matrix order 2*N_c exceeds the supported maximum");
+    return PTCA_OK;
+}
+
+Model to_model(const Problem& p) {
+    Model m;
+    m.Lx = p.Lx; m.Ly = p.Ly; m.lattice_periodic = p.periodic;
+    m.Lc = p.Lc; m.ox = p.ox; m.oy = p.oy; m.cluster_periodic = p.cluster_periodic;
+    m.proposal = p.proposal;
+    m.t = p.t; m.JH = p.JH; m.mu = p.mu; m.T = p.T;
+    m.cone_cos = std::cos(p.cone_deg * ptca::kPi / 180.0);
+    m.seed = p.seed;
+    return m;
+}
+
+template <typename T> cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), (count ? count : 1) * sizeof(T));
+}
+
+}  // namespace
+
+struct ptca_ctx {
+    Problem p;
+    int device = 0;
+    int prec = 0;  // 0 FP64, 1 FP32 reduction
+    int N = 0, nstages = 0, max_stage = 0, nA = 0;
+    size_t smem = 0;
+    std::vector<int32_t> h_start, h_sites;
+    int32_t* d_sites = nullptr;
+    double* d_S[2] = {nullptr, nullptr};
+    double* d_F = nullptr;
+    double* d_fill = nullptr;
+    int32_t* d_ticket = nullptr;
+    int32_t* d_rec_site = nullptr;
+    double* d_rec_Fold = nullptr;
+    double* d_rec_Fnew = nullptr;
+    double* d_rec_lnu = nullptr;
+    uint8_t* d_rec_acc = nullptr;
+    double* d_rec_Facc = nullptr;
+    double* d_rec_fill = nullptr;
+    int32_t* d_rec_n = nullptr;
+    unsigned long long* d_counters = nullptr;
+    int32_t* d_err = nullptr;
+    double* d_obs = nullptr;
+    int64_t sweeps = 0;
+    int64_t total_accepted = 0;
+};
+
+static void free_ctx(ptca_ctx* c) {
+    void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
+                    c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
+                    c->d_rec_n, c->d_counters, c->d_err, c->d_obs};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete c;
+}
+
+extern "C" {
+
+int32_t ptca_version(void) { return PTCA_VERSION_MAJOR * 100 + PTCA_VERSION_MINOR; }
+
+const char* ptca_last_error(void) { return g_err.c_str(); }
+
+ptca_status ptca_schedule(const ptca_lattice* lattice, const ptca_params* params, int32_t* stage_start,
+                          int32_t* sites, int32_t* n_stages) {
+    Problem p;
+    ptca_status s = resolve(lattice, params, p);
+    if (s != PTCA_OK) return s;
+    if (!stage_start || !sites || !n_stages) return fail(PTCA_ERR_INVALID, "null output pointer");
+    std::vector<int32_t> st, si;
+    make_schedule(p, st, si);
+    std::string why;
+    if (!schedule_exact(p, st, si, why)) return fail(PTCA_ERR_INVALID, "schedule is not exact: " + why);
+    std::memcpy(stage_start, st.data(), st.size() * sizeof(int32_t));
+    std::memcpy(sites, si.data(), si.size() * sizeof(int32_t));
+    *n_stages = (int32_t)st.size() - 1;
+    return PTCA_OK;
+}
+
+ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, ptca_ctx** out) {
+    if (!out) return fail(PTCA_ERR_INVALID, "null out");
+    *out = nullptr;
+    Problem p;
+    ptca_status s = resolve(lattice, params, p);
+    if (s != PTCA_OK) return s;
+    std::vector<int32_t> st, si;
+    make_schedule(p, st, si);
+    std::string why;
+    if (!schedule_exact(p, st, si, why)) return fail(PTCA_ERR_INVALID, "schedule is not exact: " + why);
+
+    int dev = 0, ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) return fail(PTCA_ERR_CUDA, "no CUDA device available");
+    PTCA_CUDA(cudaGetDevice(&dev));
+    int optin = 0;
+    PTCA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+
+    ptca_ctx* c = new ptca_ctx();
+    c->p = p;
+    c->device = dev;
+    c->prec = p.precision == PTCA_MIXED ? 1 : 0;
+    c->N = p.N();
+    c->h_start = st;
+    c->h_sites = si;
+    c->nstages = (int)st.size() - 1;
+    for (int k = 0; k < c->nstages; ++k) c->max_stage = std::max(c->max_stage, st[k + 1] - st[k]);
+    c->nA = p.nmax();
+    c->smem = ptca::cluster_smem_bytes(c->prec, c->nA);
+    if (c->smem == 0 || c->smem + 256 > (size_t)optin) {
+        delete c;
+        return fail(PTCA_ERR_INVALID, "cluster matrix does not fit in shared memory for this precision "
+                                      "(FP64 supports 2*N_c up to about 144)");
+    }
+    cudaError_t ce = ptca::configure_cluster_kernels((size_t)optin);
+    if (ce != cudaSuccess) {
+        delete c;
+        return cuda_fail(ce, "ptca_init (configuring kernel shared memory)");
+    }
+    const int N = c->N;
+    if (ce == cudaSuccess) ce = dalloc(&c->d_sites, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_S[0], 3 * (size_t)N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_S[1], 3 * (size_t)N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_F, 2 * (size_t)c->max_stage);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_fill, 2 * (size_t)c->max_stage);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_ticket, c->max_stage);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_rec_site, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_rec_Fold, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_rec_Fnew, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_rec_lnu, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_rec_acc, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_rec_Facc, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_rec_fill, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_rec_n, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_counters, 4);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_err, 1);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_obs, 8);
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->d_sites, si.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_ticket, 0, c->max_stage * sizeof(int32_t));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_err, 0, sizeof(int32_t));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_acc, 0, N);
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_Facc, 0, N * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_fill, 0, N * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_n, 0, N * sizeof(int32_t));
+    const Model m = to_model(p);
+    if (ce == cudaSuccess) ce = ptca::launch_init_spins(m, c->d_S[0], N, 0);
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->d_S[1], c->d_S[0], 3 * (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice);
+    if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) {
+        free_ctx(c);
+        return cuda_fail(ce, "ptca_init");
+    }
+    *out = c;
+    return PTCA_OK;
+}
+
+ptca_status ptca_destroy(ptca_ctx* ctx) {
+    if (!ctx) return PTCA_OK;
+    cudaDeviceSynchronize();
+    free_ctx(ctx);
+    return PTCA_OK;
+}
+
+ptca_status ptca_set_T(ptca_ctx* ctx, double T) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (!(T > 0) || !std::isfinite(T)) return fail(PTCA_ERR_INVALID, "T must be finite and > 0");
+    ctx->p.T = T;
+    return PTCA_OK;
+}
+
+ptca_status ptca_set_mu(ptca_ctx* ctx, double mu) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (!std::isfinite(mu)) return fail(PTCA_ERR_INVALID, "mu must be finite");
+    ctx->p.mu = mu;
+    return PTCA_OK;
+}
+
+ptca_status ptca_get_spins(ptca_ctx* ctx, double* dst, int on_device, void* stream) {
+    if (!ctx || !dst) return fail(PTCA_ERR_INVALID, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
+    PTCA_CUDA(cudaMemcpyAsync(dst, ctx->d_S[0], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!on_device) PTCA_CUDA(cudaStreamSynchronize(st));
+    return PTCA_OK;
+}
+
+ptca_status ptca_set_spins(ptca_ctx* ctx, const double* src, int on_device, void* stream) {
+    if (!ctx || !src) return fail(PTCA_ERR_INVALID, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
+    PTCA_CUDA(cudaMemcpyAsync(ctx->d_S[0], src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    PTCA_CUDA(cudaMemcpyAsync(ctx->d_S[1], ctx->d_S[0], bytes, cudaMemcpyDeviceToDevice, st));
+    if (!on_device) PTCA_CUDA(cudaStreamSynchronize(st));
+    return PTCA_OK;
+}
+
+ptca_status ptca_dims(const ptca_ctx* ctx, int32_t* nmax, int64_t* packed_stride) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (nmax) *nmax = ctx->nA;
+    if (packed_stride) *packed_stride = (int64_t)ctx->nA * (ctx->nA + 1) / 2;
+    return PTCA_OK;
+}
+
+ptca_status ptca_build_clusters(ptca_ctx* ctx, const int32_t* sites, int32_t m, const double* new_spins,
+                                void* H_out, int64_t* offsets_out, int32_t* n_out, void* stream) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (m < 0) return fail(PTCA_ERR_INVALID, "m < 0");
+    if (m == 0) return PTCA_OK;
+    if (!sites || !H_out || !offsets_out || !n_out) return fail(PTCA_ERR_INVALID, "null buffer");
+    const int64_t stride = (int64_t)ctx->nA * (ctx->nA + 1) / 2;
+    PTCA_CUDA(ptca::launch_build(ctx->prec, to_model(ctx->p), ctx->d_S[0], sites, m, new_spins, H_out, stride,
+                                 offsets_out, n_out, static_cast<cudaStream_t>(stream)));
+    return PTCA_OK;
+}
+
+ptca_status ptca_cluster_eigvals(ptca_ctx* ctx, const void* H, const int64_t* offsets, const int32_t* n, int32_t m,
+                                 double* eig_out, const int64_t* eig_offsets, void* stream) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (m < 0) return fail(PTCA_ERR_INVALID, "m < 0");
+    if (m == 0) return PTCA_OK;
+    if (!H || !offsets || !n || !eig_out || !eig_offsets) return fail(PTCA_ERR_INVALID, "null buffer");
+    PTCA_CUDA(ptca::launch_eigvals(ctx->prec, ctx->nA, H, offsets, n, m, eig_out, eig_offsets,
+                                   static_cast<cudaStream_t>(stream)));
+    return PTCA_OK;
+}
+
+ptca_status ptca_free_energy(ptca_ctx* ctx, const double* eig, const int64_t* eig_offsets, const int32_t* n,
+                             int32_t m, double mu, double T, double* F_out, void* stream) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (m < 0) return fail(PTCA_ERR_INVALID, "m < 0");
+    if (!(T > 0) || !std::isfinite(T) || !std::isfinite(mu)) return fail(PTCA_ERR_INVALID, "bad mu or T");
+    if (m == 0) return PTCA_OK;
+    if (!eig || !eig_offsets || !n || !F_out) return fail(PTCA_ERR_INVALID, "null buffer");
+    PTCA_CUDA(ptca::launch_free_energy(eig, eig_offsets, n, m, mu, T, F_out, static_cast<cudaStream_t>(stream)));
+    return PTCA_OK;
+}
+
+ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_out, void* stream) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (n_sweeps < 0) return fail(PTCA_ERR_INVALID, "n_sweeps < 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (stats_out) {
+        PTCA_CUDA(cudaEventCreate(&ev0));
+        PTCA_CUDA(cudaEventCreate(&ev1));
+        PTCA_CUDA(cudaEventRecord(ev0, st));
+    }
+    PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
+    StageArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.m = to_model(ctx->p);
+    a.nA = ctx->nA;
+    a.Fbuf = ctx->d_F;
+    a.fillbuf = ctx->d_fill;
+    a.ticket = ctx->d_ticket;
+    a.rec_site = ctx->d_rec_site;
+    a.rec_Fold = ctx->d_rec_Fold;
+    a.rec_Fnew = ctx->d_rec_Fnew;
+    a.rec_lnu = ctx->d_rec_lnu;
+    a.rec_acc = ctx->d_rec_acc;
+    a.rec_Facc = ctx->d_rec_Facc;
+    a.rec_fill = ctx->d_rec_fill;
+    a.rec_n = ctx->d_rec_n;
+    a.counters = ctx->d_counters;
+    a.err = ctx->d_err;
+    int64_t g = 0;
+    int prev_s = -1;
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        a.sweep = (uint64_t)(ctx->sweeps + sw);
+        for (int s = 0; s < ctx->nstages; ++s, ++g) {
+            a.S_in = ctx->d_S[g & 1];
+            a.S_out = ctx->d_S[(g + 1) & 1];
+            a.sites = ctx->d_sites + ctx->h_start[s];
+            a.count = ctx->h_start[s + 1] - ctx->h_start[s];
+            a.rec_base = ctx->h_start[s];
+            if (prev_s >= 0) {
+                a.prev_sites = ctx->d_sites + ctx->h_start[prev_s];
+                a.prev_count = ctx->h_start[prev_s + 1] - ctx->h_start[prev_s];
+            } else {
+                a.prev_sites = nullptr;
+                a.prev_count = 0;
+            }
+            PTCA_CUDA(ptca::launch_stage(ctx->prec, a, st));
+            prev_s = s;
+        }
+    }
+    if (g > 0) {
+        // Bring the other buffer up to date so both hold the configuration.
+        const int last = prev_s;
+        PTCA_CUDA(ptca::launch_copy_sites(ctx->d_S[g & 1], ctx->d_S[(g + 1) & 1], ctx->d_sites + ctx->h_start[last],
+                                          ctx->h_start[last + 1] - ctx->h_start[last], st));
+    }
+    ctx->sweeps += n_sweeps;
+    if (stats_out) {
+        unsigned long long cnt[4];
+        int32_t err = 0;
+        PTCA_CUDA(cudaEventRecord(ev1, st));
+        PTCA_CUDA(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
+        PTCA_CUDA(cudaMemcpyAsync(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost, st));
+        PTCA_CUDA(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        stats_out->attempts = (int64_t)n_sweeps * ctx->N;
+        stats_out->accepted = (int64_t)cnt[0];
+        stats_out->eigensolves = (int64_t)cnt[1];
+        stats_out->resolved = 0;
+        stats_out->sweeps = ctx->sweeps;
+        stats_out->seconds = ms * 1e-3;
+        if (err) return fail(PTCA_ERR_NUMERIC, "non-finite free-energy difference in a sweep");
+    }
+    return PTCA_OK;
+}
+
+ptca_status ptca_sweep_record(ptca_ctx* ctx, int32_t* site, double* F_old, double* F_new, double* lnu,
+                              uint8_t* accepted, void* stream) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t N = ctx->N;
+    if (site) PTCA_CUDA(cudaMemcpyAsync(site, ctx->d_rec_site, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    if (F_old) PTCA_CUDA(cudaMemcpyAsync(F_old, ctx->d_rec_Fold, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (F_new) PTCA_CUDA(cudaMemcpyAsync(F_new, ctx->d_rec_Fnew, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (lnu) PTCA_CUDA(cudaMemcpyAsync(lnu, ctx->d_rec_lnu, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (accepted) PTCA_CUDA(cudaMemcpyAsync(accepted, ctx->d_rec_acc, N, cudaMemcpyDeviceToDevice, st));
+    return PTCA_OK;
+}
+
+ptca_status ptca_observables(ptca_ctx* ctx, ptca_obs* out, void* stream) {
+    if (!ctx || !out) return fail(PTCA_ERR_INVALID, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_CUDA(ptca::launch_observables(ctx->d_S[0], ctx->p.Lx, ctx->p.Ly, ctx->d_rec_Facc, ctx->d_rec_fill,
+                                       ctx->d_rec_acc, ctx->d_rec_n, ctx->N, ctx->d_obs, st));
+    double h[5];
+    PTCA_CUDA(cudaMemcpyAsync(h, ctx->d_obs, sizeof h, cudaMemcpyDeviceToHost, st));
+    PTCA_CUDA(cudaStreamSynchronize(st));
+    out->S_00 = h[0];
+    out->S_pipi = h[1];
+    out->F_site = h[2];
+    out->acceptance = h[3];
+    out->filling = h[4];
+    return PTCA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,289 @@
+// kernels.cuh -- CUDA kernels of the PTCA hot path (templated on the
+// reduction precision T and on NT = ceil(nmax/32)).
+#pragma once
+
+#include "cluster_solve.cuh"
+
+namespace ptca {
+
+constexpr int NW = 8;              // warps per CTA of the cluster kernels
+constexpr int CTA = 32 * NW;
+constexpr double kFermiCut = 40.0; // eigenvalues above mu + 40 T change F by < T e^-40 each
+
+// Shared-memory layout of one cluster CTA (byte offsets, 16-byte aligned).
+struct SmemLayout {
+    size_t A, Vb, Wv, pr, pc, d, e2, df, e2f, sp, red, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// nA: largest matrix order stored; nmaxc = 32 * NT; cs = sizeof(complex element)
+__host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs) {
+    SmemLayout L;
+    size_t o = 0;
+    L.A = o;   o = align16(o + (size_t)nA * (nA + 1) / 2 * cs);
+    L.Vb = o;  o = align16(o + 2 * (size_t)nmaxc * cs);
+    L.Wv = o;  o = align16(o + (size_t)nmaxc * cs);
+    L.pr = o;  o = align16(o + (size_t)nmaxc * cs);
+    L.pc = o;  o = align16(o + (size_t)NW * nmaxc * cs);
+    L.d = o;   o = align16(o + (size_t)nmaxc * sizeof(double));
+    L.e2 = o;  o = align16(o + (size_t)nmaxc * sizeof(double));
+    L.df = o;  o = align16(o + (size_t)nmaxc * sizeof(float));
+    L.e2f = o; o = align16(o + (size_t)nmaxc * sizeof(float));
+    L.sp = o;  o = align16(o + (size_t)(nmaxc / 2) * 3 * sizeof(double));
+    L.red = o; o = align16(o + 4 * (size_t)NW * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+template <typename T> struct Carve {
+    cplx_t<T>* A; HHScratch<T> hh; double* d; double* e2; float* df; float* e2f; double* sp; double* red;
+};
+
+template <typename T>
+__device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout& L) {
+    Carve<T> c;
+    c.A = reinterpret_cast<cplx_t<T>*>(base + L.A);
+    c.hh.Vb = reinterpret_cast<cplx_t<T>*>(base + L.Vb);
+    c.hh.Wv = reinterpret_cast<cplx_t<T>*>(base + L.Wv);
+    c.hh.pr = reinterpret_cast<cplx_t<T>*>(base + L.pr);
+    c.hh.pc = reinterpret_cast<cplx_t<T>*>(base + L.pc);
+    c.red = reinterpret_cast<double*>(base + L.red);
+    c.hh.redA = reinterpret_cast<T*>(base + L.red);
+    c.hh.redB = reinterpret_cast<T*>(base + L.red + 2 * NW * sizeof(double));
+    c.d = reinterpret_cast<double*>(base + L.d);
+    c.e2 = reinterpret_cast<double*>(base + L.e2);
+    c.df = reinterpret_cast<float*>(base + L.df);
+    c.e2f = reinterpret_cast<float*>(base + L.e2f);
+    c.sp = reinterpret_cast<double*>(base + L.sp);
+    return c;
+}
+
+// Eigenvalues of the tridiagonal (d, e2) in shared memory.  Computes the
+// eigenvalues with index < K (all when all_eigs, else those below
+// mu + 40 T), one thread per eigenvalue, and returns through eig (if not
+// null, global) and the block sums of softplus(-(eps-mu)/T) and of the Fermi
+// function.  T == float selects FP32 bisection + one FP64 Newton step; T ==
+// double selects FP64 bisection.
+template <typename T>
+__device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool all_eigs, double* eig,
+                              double& sum_sp, double& sum_fermi, int& n_solved) {
+    __shared__ double s_lo, s_hi, s_pivmin;
+    __shared__ float s_pivminf;
+    __shared__ int s_K;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // Gershgorin bounds, one row per thread, and FP32 copies of (d, e2).
+    double glo = 1e300, ghi = -1e300, ge = 0.0;
+    if (tid < n) {
+        const double el = tid > 0 ? sqrt(c.e2[tid - 1]) : 0.0;
+        const double er = tid < n - 1 ? sqrt(c.e2[tid]) : 0.0;
+        glo = c.d[tid] - el - er;
+        ghi = c.d[tid] + el + er;
+        ge = tid < n - 1 ? c.e2[tid] : 0.0;
+        c.df[tid] = (float)c.d[tid];
+        c.e2f[tid] = (float)ge;
+    }
+    glo = warp_min(glo); ghi = warp_max(ghi); ge = warp_max(ge);
+    if (lane == 0) { c.red[warp] = glo; c.red[NW + warp] = ghi; c.red[2 * NW + warp] = ge; }
+    __syncthreads();
+    if (tid == 0) {
+        double lo = c.red[0], hi = c.red[NW], emax2 = c.red[2 * NW];
+        for (int w = 1; w < NW; ++w) {
+            lo = fmin(lo, c.red[w]); hi = fmax(hi, c.red[NW + w]); emax2 = fmax(emax2, c.red[2 * NW + w]);
+        }
+        const double wdt = hi - lo, nrm = fmax(fabs(lo), fabs(hi));
+        lo -= 1e-12 * (wdt + nrm) + 1e-300;
+        hi += 1e-12 * (wdt + nrm) + 1e-300;
+        const double pivmin = DBL_MIN * fmax(1.0, emax2);
+        const float pivminf = FLT_MIN * fmaxf(1.0f, (float)emax2);
+        s_lo = lo; s_hi = hi; s_pivmin = pivmin; s_pivminf = pivminf;
+        int K = n;
+        if (!all_eigs) {
+            const double cut = mu + kFermiCut * temp;
+            if (cut < hi) {
+                if constexpr (sizeof(T) == 8) K = sturm_count_f64(n, c.d, c.e2, cut, pivmin);
+                else K = sturm_count_f32(n, c.df, c.e2f, (float)cut, pivminf);
+            }
+        }
+        s_K = K;
+    }
+    __syncthreads();
+    const int K = s_K;
+    const int k = lane * NW + warp;  // spread consecutive eigenvalues over the warps
+    double sp = 0.0, fe = 0.0;
+    if (k < K) {
+        const double lo = s_lo, hi = s_hi, pivmin = s_pivmin;
+        const double nrm = fmax(fabs(lo), fabs(hi));
+        double lam;
+        if constexpr (sizeof(T) == 8) {
+            lam = bisect_f64(n, c.d, c.e2, k, lo, hi, pivmin, 2.0 * DBL_EPSILON * nrm);
+        } else {
+            const float lof = (float)lo * (lo < 0 ? 1.0000002f : 0.9999998f) - 1e-30f;
+            const float hif = (float)hi * (hi > 0 ? 1.0000002f : 0.9999998f) + 1e-30f;
+            lam = bisect_f32_newton_f64(n, c.df, c.e2f, c.d, c.e2, k, lof, hif, s_pivminf,
+                                        2.0f * FLT_EPSILON * (float)nrm, pivmin);
+        }
+        const double x = -(lam - mu) / temp;
+        sp = softplus(x);
+        fe = 1.0 / (1.0 + exp(-x));
+        if (eig) eig[k] = lam;
+    }
+    __syncthreads();
+    sum_sp = block_sum<double>(sp, c.red);
+    sum_fermi = block_sum<double>(fe, c.red + NW);
+    n_solved = K;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_init_spins(Model m, double* __restrict__ S, int N);
+__global__ void k_copy_sites(const double* __restrict__ src, double* __restrict__ dst,
+                             const int32_t* __restrict__ sites, int count);
+__global__ void k_free_energy(const double* __restrict__ eig, const int64_t* __restrict__ eoff,
+                              const int32_t* __restrict__ n, int m, double mu, double temp,
+                              double* __restrict__ F);
+__global__ void k_observables(const double* __restrict__ S, int Lx, int Ly, const double* __restrict__ rec_Facc,
+                              const double* __restrict__ rec_fill, const uint8_t* __restrict__ rec_acc,
+                              const int32_t* __restrict__ rec_n, int N, double* __restrict__ out);
+
+// Build m cluster matrices straight into global memory.
+template <typename T>
+__global__ void __launch_bounds__(CTA) k_build(Model m, const double* __restrict__ S, const int32_t* __restrict__ sites,
+                                               int count, const double* __restrict__ new_spins, cplx_t<T>* H,
+                                               int64_t stride, int64_t* offsets, int32_t* nout) {
+    __shared__ double sp[3 * 128];
+    const int c = blockIdx.x;
+    if (c >= count) return;
+    const int site = sites[c];
+    const Window w = make_window(m, site);
+    cplx_t<T>* A = H + (int64_t)c * stride;
+    build_cluster<T>(m, w, S, new_spins ? new_spins + 3 * c : nullptr, sp, A);
+    if (threadIdx.x == 0) { offsets[c] = (int64_t)c * stride; nout[c] = 2 * w.ex * w.ey; }
+}
+
+// All eigenvalues of m packed matrices from global memory.
+template <typename T, int NT>
+__global__ void __launch_bounds__(CTA) k_eigvals(const cplx_t<T>* __restrict__ H, const int64_t* __restrict__ offsets,
+                                                 const int32_t* __restrict__ nin, int count, int nA,
+                                                 double* __restrict__ eig, const int64_t* __restrict__ eoff) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout L = smem_layout(nA, 32 * NT, sizeof(cplx_t<T>));
+    Carve<T> c = carve<T>(smem, L);
+    const int b = blockIdx.x;
+    if (b >= count) return;
+    const int n = nin[b];
+    double* out = eig + eoff[b];
+    if (n < 1 || n > nA || n > 32 * NT) {
+        for (int i = threadIdx.x; i < (n > 0 ? n : 0) && i < nA; i += blockDim.x) out[i] = nan("");
+        return;
+    }
+    const cplx_t<T>* src = H + offsets[b];
+    const int P = tri(n);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) c.A[i] = src[i];
+    __syncthreads();
+    householder_tridiag<T, NT, NW>(n, c.A, c.hh, c.d, c.e2);
+    double s1, s2;
+    int K;
+    tridiag_eig_F<T>(n, c, 0.0, 1.0, true, out, s1, s2, K);
+}
+
+// One PTCA stage (Sec. III.a): block 2c holds H_old of update site c, block
+// 2c+1 holds H_new with the proposed spin.  The second block to finish
+// applies Metropolis (Sec. II.c steps e-f) and writes the site's spin for the
+// next stage.  Reads come only from S_in (the configuration at the start of
+// the stage); S_out receives this stage's decisions plus the previous
+// stage's update sites copied forward, so S_out is the full configuration
+// after the stage.
+struct StageArgs {
+    Model m;
+    const double* S_in;
+    double* S_out;
+    const int32_t* sites;
+    int32_t count;
+    const int32_t* prev_sites;
+    int32_t prev_count;
+    int32_t rec_base;
+    int32_t nA;
+    uint64_t sweep;
+    double* Fbuf;
+    double* fillbuf;
+    int32_t* ticket;
+    int32_t* rec_site;
+    double* rec_Fold;
+    double* rec_Fnew;
+    double* rec_lnu;
+    uint8_t* rec_acc;
+    double* rec_Facc;
+    double* rec_fill;
+    int32_t* rec_n;
+    unsigned long long* counters;  // [0] accepted, [1] eigensolves
+    int32_t* err;
+};
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(CTA) k_stage(StageArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    __shared__ int s_last;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.prev_count; k += gridDim.x * blockDim.x) {
+        const int s = a.prev_sites[k];
+        a.S_out[3 * s] = a.S_in[3 * s];
+        a.S_out[3 * s + 1] = a.S_in[3 * s + 1];
+        a.S_out[3 * s + 2] = a.S_in[3 * s + 2];
+    }
+    const int c = blockIdx.x >> 1, var = blockIdx.x & 1;
+    if (c >= a.count) return;
+    const SmemLayout L = smem_layout(a.nA, 32 * NT, sizeof(cplx_t<T>));
+    Carve<T> cv = carve<T>(smem, L);
+    const int site = a.sites[c];
+    const Window w = make_window(a.m, site);
+    const int n = 2 * w.ex * w.ey;
+    if (threadIdx.x == 0 && var == 1)
+        propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, s_new);
+    __syncthreads();
+    build_cluster<T>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    __syncthreads();
+    householder_tridiag<T, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
+    double ssp, sfe;
+    int K;
+    tridiag_eig_F<T>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
+    if (threadIdx.x == 0) {
+        const double F = -a.m.T * ssp;
+        a.Fbuf[2 * c + var] = F;
+        a.fillbuf[2 * c + var] = sfe;
+        __threadfence();
+        const int old = atomicAdd(&a.ticket[c], 1);
+        s_last = (old == 1);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    a.ticket[c] = 0;
+    const double Fo = __ldcg(&a.Fbuf[2 * c]), Fn = __ldcg(&a.Fbuf[2 * c + 1]);
+    const double fo = __ldcg(&a.fillbuf[2 * c]), fn = __ldcg(&a.fillbuf[2 * c + 1]);
+    double sn[3];
+    const double* so = a.S_in + 3 * site;
+    if (var == 1) { sn[0] = s_new[0]; sn[1] = s_new[1]; sn[2] = s_new[2]; }
+    else propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, so, sn);
+    double u0, u1;
+    uniform2(a.m.seed, a.sweep, (uint32_t)site, RNG_ACCEPT, u0, u1);
+    const double lnu = log(u0);
+    const double dF = Fn - Fo;
+    if (!isfinite(dF)) atomicExch(a.err, 1);
+    const bool acc = lnu < -dF / a.m.T;
+    double* dst = a.S_out + 3 * site;
+    if (acc) { dst[0] = sn[0]; dst[1] = sn[1]; dst[2] = sn[2]; }
+    else { dst[0] = so[0]; dst[1] = so[1]; dst[2] = so[2]; }
+    const int r = a.rec_base + c;
+    a.rec_site[r] = site;
+    a.rec_Fold[r] = Fo;
+    a.rec_Fnew[r] = Fn;
+    a.rec_lnu[r] = lnu;
+    a.rec_acc[r] = acc ? 1 : 0;
+    a.rec_Facc[r] = acc ? Fn : Fo;
+    a.rec_fill[r] = acc ? fn : fo;
+    a.rec_n[r] = n;
+    if (acc) atomicAdd(&a.counters[0], 1ull);
+    atomicAdd(&a.counters[1], 2ull);
+}
+
+}  // namespace ptca

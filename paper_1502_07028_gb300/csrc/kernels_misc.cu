@@ -1,0 +1,142 @@
+// kernels_misc.cu -- small kernels (initial spins, copies, free energy of
+// eigenvalue lists, observables) and the precision dispatch of the launchers.
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace ptca {
+
+// Declarations of the per-precision launchers (kernels_f32.cu / kernels_f64.cu).
+size_t cluster_smem_bytes_f32(int nA);
+size_t cluster_smem_bytes_f64(int nA);
+int cluster_max_order_f32();
+int cluster_max_order_f64();
+cudaError_t configure_f32(size_t);
+cudaError_t configure_f64(size_t);
+cudaError_t launch_build_f32(const Model&, const double*, const int32_t*, int, const double*, void*, int64_t,
+                             int64_t*, int32_t*, cudaStream_t);
+cudaError_t launch_build_f64(const Model&, const double*, const int32_t*, int, const double*, void*, int64_t,
+                             int64_t*, int32_t*, cudaStream_t);
+cudaError_t launch_eigvals_f32(int, const void*, const int64_t*, const int32_t*, int, double*, const int64_t*,
+                               cudaStream_t);
+cudaError_t launch_eigvals_f64(int, const void*, const int64_t*, const int32_t*, int, double*, const int64_t*,
+                               cudaStream_t);
+cudaError_t launch_stage_f32(const StageArgs&, cudaStream_t);
+cudaError_t launch_stage_f64(const StageArgs&, cudaStream_t);
+
+size_t cluster_smem_bytes(int prec, int nA) { return prec ? cluster_smem_bytes_f32(nA) : cluster_smem_bytes_f64(nA); }
+int cluster_max_order(int prec) { return prec ? cluster_max_order_f32() : cluster_max_order_f64(); }
+cudaError_t configure_cluster_kernels(size_t smem_limit) {
+    cudaError_t e = configure_f32(smem_limit);
+    if (e != cudaSuccess) return e;
+    return configure_f64(smem_limit);
+}
+cudaError_t launch_build(int prec, const Model& m, const double* S, const int32_t* sites, int count,
+                         const double* new_spins, void* H, int64_t stride, int64_t* offsets, int32_t* nout,
+                         cudaStream_t st) {
+    return prec ? launch_build_f32(m, S, sites, count, new_spins, H, stride, offsets, nout, st)
+                : launch_build_f64(m, S, sites, count, new_spins, H, stride, offsets, nout, st);
+}
+cudaError_t launch_eigvals(int prec, int nA, const void* H, const int64_t* offsets, const int32_t* n, int count,
+                           double* eig, const int64_t* eoff, cudaStream_t st) {
+    return prec ? launch_eigvals_f32(nA, H, offsets, n, count, eig, eoff, st)
+                : launch_eigvals_f64(nA, H, offsets, n, count, eig, eoff, st);
+}
+cudaError_t launch_stage(int prec, const StageArgs& a, cudaStream_t st) {
+    return prec ? launch_stage_f32(a, st) : launch_stage_f64(a, st);
+}
+
+// Initial spins: uniform on the sphere from the counter generator.
+__global__ void k_init_spins(Model m, double* __restrict__ S, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double u0, u1, s[3];
+    uniform2(m.seed, 0, (uint32_t)i, RNG_INIT, u0, u1);
+    unit_from_uniforms(u0, u1, s);
+    S[3 * i] = s[0]; S[3 * i + 1] = s[1]; S[3 * i + 2] = s[2];
+}
+
+cudaError_t launch_init_spins(const Model& m, double* S, int N, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    k_init_spins<<<(N + 255) / 256, 256, 0, st>>>(m, S, N);
+    return cudaGetLastError();
+}
+
+__global__ void k_copy_sites(const double* __restrict__ src, double* __restrict__ dst,
+                             const int32_t* __restrict__ sites, int count) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int s = sites[k];
+    dst[3 * s] = src[3 * s]; dst[3 * s + 1] = src[3 * s + 1]; dst[3 * s + 2] = src[3 * s + 2];
+}
+
+cudaError_t launch_copy_sites(const double* src, double* dst, const int32_t* sites, int count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_copy_sites<<<(count + 255) / 256, 256, 0, st>>>(src, dst, sites, count);
+    return cudaGetLastError();
+}
+
+// F_i = -T sum_k softplus(-(eig_k - mu)/T), one warp per list.
+__global__ void k_free_energy(const double* __restrict__ eig, const int64_t* __restrict__ eoff,
+                              const int32_t* __restrict__ n, int m, double mu, double temp, double* __restrict__ F) {
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (wid >= m) return;
+    const double* e = eig + eoff[wid];
+    const int nn = n[wid];
+    double acc = 0.0;
+    for (int k = lane; k < nn; k += 32) acc += softplus(-(e[k] - mu) / temp);
+    acc = warp_sum(acc);
+    if (lane == 0) F[wid] = -temp * acc;
+}
+
+cudaError_t launch_free_energy(const double* eig, const int64_t* eoff, const int32_t* n, int count, double mu,
+                               double T, double* F, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const int threads = 256, blocks = (count * 32 + threads - 1) / threads;
+    k_free_energy<<<blocks, threads, 0, st>>>(eig, eoff, n, count, mu, T, F);
+    return cudaGetLastError();
+}
+
+// Observables (single CTA): S(q) = |sum_i S_i e^{i q.r_i}|^2 / N^2 at (0,0)
+// and (pi,pi) (Eq. 2 for one configuration), and the means over the last
+// sweep's visits of F_acc/N_c, the acceptance and the filling.
+// out: [S00, Spipi, F_site, acceptance, filling]
+__global__ void k_observables(const double* __restrict__ S, int Lx, int Ly, const double* __restrict__ rec_Facc,
+                              const double* __restrict__ rec_fill, const uint8_t* __restrict__ rec_acc,
+                              const int32_t* __restrict__ rec_n, int N, double* __restrict__ out) {
+    __shared__ double red[32];
+    double m0[3] = {0, 0, 0}, mp[3] = {0, 0, 0};
+    double fs = 0.0, ac = 0.0, fl = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int x = i % Lx, y = i / Lx;
+        const double sg = ((x + y) & 1) ? -1.0 : 1.0;
+        for (int a = 0; a < 3; ++a) { m0[a] += S[3 * i + a]; mp[a] += sg * S[3 * i + a]; }
+        if (rec_n[i] > 0) {
+            const double nc = 0.5 * (double)rec_n[i];
+            fs += rec_Facc[i] / nc;
+            ac += (double)rec_acc[i];
+            fl += rec_fill[i] / nc;
+        }
+    }
+    double vals[9] = {m0[0], m0[1], m0[2], mp[0], mp[1], mp[2], fs, ac, fl};
+    double tot[9];
+    for (int q = 0; q < 9; ++q) {
+        tot[q] = block_sum<double>(vals[q], red);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double N2 = (double)N * (double)N;
+        out[0] = (tot[0] * tot[0] + tot[1] * tot[1] + tot[2] * tot[2]) / N2;
+        out[1] = (tot[3] * tot[3] + tot[4] * tot[4] + tot[5] * tot[5]) / N2;
+        out[2] = tot[6] / N;
+        out[3] = tot[7] / N;
+        out[4] = tot[8] / N;
+    }
+}
+
+cudaError_t launch_observables(const double* S, int Lx, int Ly, const double* rec_Facc, const double* rec_fill,
+                               const uint8_t* rec_acc, const int32_t* rec_n, int N, double* out, cudaStream_t st) {
+    k_observables<<<1, 1024, 0, st>>>(S, Lx, Ly, rec_Facc, rec_fill, rec_acc, rec_n, N, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ptca

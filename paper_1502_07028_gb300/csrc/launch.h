@@ -1,0 +1,34 @@
+// launch.h -- host-side launchers of the PTCA kernels (called by the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ptca {
+
+struct Model;
+struct StageArgs;
+
+// Dynamic shared memory of one cluster CTA for matrices up to order nA
+// (0 when no kernel instantiation covers nA).  prec: 0 FP64, 1 FP32.
+size_t cluster_smem_bytes(int prec, int nA);
+// Largest order any instantiation covers for the precision.
+int cluster_max_order(int prec);
+// Opt every cluster kernel into the shared memory it may need.
+cudaError_t configure_cluster_kernels(size_t smem_limit);
+
+cudaError_t launch_init_spins(const Model& m, double* S, int N, cudaStream_t st);
+cudaError_t launch_copy_sites(const double* src, double* dst, const int32_t* sites, int count, cudaStream_t st);
+cudaError_t launch_build(int prec, const Model& m, const double* S, const int32_t* sites, int count,
+                         const double* new_spins, void* H, int64_t stride, int64_t* offsets, int32_t* nout,
+                         cudaStream_t st);
+cudaError_t launch_eigvals(int prec, int nA, const void* H, const int64_t* offsets, const int32_t* n, int count,
+                           double* eig, const int64_t* eoff, cudaStream_t st);
+cudaError_t launch_free_energy(const double* eig, const int64_t* eoff, const int32_t* n, int count, double mu,
+                               double T, double* F, cudaStream_t st);
+cudaError_t launch_stage(int prec, const StageArgs& a, cudaStream_t st);
+cudaError_t launch_observables(const double* S, int Lx, int Ly, const double* rec_Facc, const double* rec_fill,
+                               const uint8_t* rec_acc, const int32_t* rec_n, int N, double* out, cudaStream_t st);
+
+}  // namespace ptca

@@ -1,0 +1,344 @@
+"""Thin ctypes binding of libptca.so (C ABI declared in include/ptca.h).
+
+Argument marshalling only: every step of the traveling-cluster hot path runs
+in the library's CUDA kernels.  Torch tensors supply device memory and the
+current CUDA stream; their ``data_ptr()`` is passed as a plain pointer.
+There is no CPU fallback: if the library is missing or no GPU is usable the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+from . import _build
+
+PTCA_OK = 0
+STATUS = {0: "PTCA_OK", 1: "PTCA_ERR_INVALID", 2: "PTCA_ERR_CUDA", 3: "PTCA_ERR_OOM",
+          4: "PTCA_ERR_TIMEOUT", 5: "PTCA_ERR_NUMERIC", 6: "PTCA_ERR_UNSUPPORTED"}
+SCHEDULE_TILED, SCHEDULE_BLOCK = 0, 1
+FP64, MIXED = 0, 1
+PROPOSAL_SPHERE, PROPOSAL_CONE = 0, 1
+
+EXPORTED = [
+    "ptca_init", "ptca_destroy", "ptca_set_T", "ptca_set_mu", "ptca_get_spins", "ptca_set_spins",
+    "ptca_dims", "ptca_build_clusters", "ptca_cluster_eigvals", "ptca_free_energy", "ptca_sweep",
+    "ptca_sweep_record", "ptca_observables", "ptca_schedule", "ptca_last_error", "ptca_version",
+]
+
+
+class PtcaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32), ("periodic", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_double), ("J_H", ctypes.c_double), ("mu", ctypes.c_double), ("T", ctypes.c_double),
+        ("L_c", ctypes.c_int32), ("cluster_periodic", ctypes.c_int32), ("update_offset", ctypes.c_int32),
+        ("schedule", ctypes.c_int32), ("stride", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("proposal", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("cone_deg", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class SweepStats(ctypes.Structure):
+    _fields_ = [("attempts", ctypes.c_int64), ("accepted", ctypes.c_int64), ("eigensolves", ctypes.c_int64),
+                ("resolved", ctypes.c_int64), ("sweeps", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("S_00", ctypes.c_double), ("S_pipi", ctypes.c_double), ("F_site", ctypes.c_double),
+                ("acceptance", ctypes.c_double), ("filling", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libptca.so (it must have been built; see ``__graft_entry__.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        P = ctypes.POINTER
+        sig = {
+            "ptca_init": ([P(Lattice), P(Params), P(vp)], i32),
+            "ptca_destroy": ([vp], i32),
+            "ptca_set_T": ([vp, dbl], i32),
+            "ptca_set_mu": ([vp, dbl], i32),
+            "ptca_get_spins": ([vp, vp, ctypes.c_int, vp], i32),
+            "ptca_set_spins": ([vp, vp, ctypes.c_int, vp], i32),
+            "ptca_dims": ([vp, P(i32), P(i64)], i32),
+            "ptca_build_clusters": ([vp, vp, i32, vp, vp, vp, vp, vp], i32),
+            "ptca_cluster_eigvals": ([vp, vp, vp, vp, i32, vp, vp, vp], i32),
+            "ptca_free_energy": ([vp, vp, vp, vp, i32, dbl, dbl, vp, vp], i32),
+            "ptca_sweep": ([vp, i32, P(SweepStats), vp], i32),
+            "ptca_sweep_record": ([vp, vp, vp, vp, vp, vp, vp], i32),
+            "ptca_observables": ([vp, P(Obs), vp], i32),
+            "ptca_schedule": ([P(Lattice), P(Params), vp, vp, P(i32)], i32),
+            "ptca_last_error": ([], ctypes.c_char_p),
+            "ptca_version": ([], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status != PTCA_OK:
+        raise PtcaError(status, lib().ptca_last_error().decode())
+
+
+def _ptr(t):
+    """Raw pointer of a tensor / numpy array / None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    if hasattr(t, "ctypes"):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(int(t))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+@dataclass
+class Config:
+    """Problem definition, mirrored into ptca_lattice / ptca_params."""
+    Lx: int
+    Ly: int
+    L_c: int
+    periodic: int = 1
+    t: float = 1.0
+    J_H: float = 8.0
+    mu: float = -6.5
+    T: float = 0.05
+    cluster_periodic: int = -1
+    update_offset: int = -1
+    schedule: int = SCHEDULE_TILED
+    stride: int = 0
+    precision: int = FP64
+    proposal: int = PROPOSAL_SPHERE
+    cone_deg: float = 30.0
+    seed: int = 0
+
+    def lattice(self) -> Lattice:
+        return Lattice(self.Lx, self.Ly, self.periodic)
+
+    def params(self) -> Params:
+        return Params(self.t, self.J_H, self.mu, self.T, self.L_c, self.cluster_periodic, self.update_offset,
+                      self.schedule, self.stride, self.precision, self.proposal, 0, self.cone_deg, self.seed)
+
+    @property
+    def N(self) -> int:
+        return self.Lx * self.Ly
+
+
+# ---------------------------------------------------------------------------
+# Functions with the C names (pointer/size marshalling only)
+# ---------------------------------------------------------------------------
+def ptca_version() -> int:
+    return lib().ptca_version()
+
+
+def ptca_schedule(cfg: Config):
+    """Host-only schedule: list of int32 numpy arrays (one per stage)."""
+    import numpy as np
+    N = cfg.N
+    start = np.zeros(N + 1, dtype=np.int32)
+    sites = np.zeros(N, dtype=np.int32)
+    ns = ctypes.c_int32()
+    lat, par = cfg.lattice(), cfg.params()
+    _check(lib().ptca_schedule(ctypes.byref(lat), ctypes.byref(par), _ptr(start), _ptr(sites), ctypes.byref(ns)))
+    return [sites[start[s]:start[s + 1]].copy() for s in range(ns.value)]
+
+
+def ptca_init(cfg: Config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    lat, par = cfg.lattice(), cfg.params()
+    _check(lib().ptca_init(ctypes.byref(lat), ctypes.byref(par), ctypes.byref(h)))
+    return h
+
+
+def ptca_destroy(h) -> None:
+    _check(lib().ptca_destroy(h))
+
+
+def ptca_set_T(h, T: float) -> None:
+    _check(lib().ptca_set_T(h, T))
+
+
+def ptca_set_mu(h, mu: float) -> None:
+    _check(lib().ptca_set_mu(h, mu))
+
+
+def ptca_get_spins(h, dst, stream=None) -> None:
+    on_dev = int(getattr(dst, "is_cuda", False))
+    _check(lib().ptca_get_spins(h, _ptr(dst), on_dev, _stream(stream)))
+
+
+def ptca_set_spins(h, src, stream=None) -> None:
+    on_dev = int(getattr(src, "is_cuda", False))
+    _check(lib().ptca_set_spins(h, _ptr(src), on_dev, _stream(stream)))
+
+
+def ptca_dims(h):
+    nmax, stride = ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().ptca_dims(h, ctypes.byref(nmax), ctypes.byref(stride)))
+    return nmax.value, stride.value
+
+
+def ptca_build_clusters(h, sites, m, new_spins, H_out, offsets_out, n_out, stream=None) -> None:
+    _check(lib().ptca_build_clusters(h, _ptr(sites), m, _ptr(new_spins), _ptr(H_out), _ptr(offsets_out),
+                                     _ptr(n_out), _stream(stream)))
+
+
+def ptca_cluster_eigvals(h, H, offsets, n, m, eig_out, eig_offsets, stream=None) -> None:
+    _check(lib().ptca_cluster_eigvals(h, _ptr(H), _ptr(offsets), _ptr(n), m, _ptr(eig_out), _ptr(eig_offsets),
+                                      _stream(stream)))
+
+
+def ptca_free_energy(h, eig, eig_offsets, n, m, mu, T, F_out, stream=None) -> None:
+    _check(lib().ptca_free_energy(h, _ptr(eig), _ptr(eig_offsets), _ptr(n), m, mu, T, _ptr(F_out),
+                                  _stream(stream)))
+
+
+def ptca_sweep(h, n_sweeps: int, stats: bool = True, stream=None):
+    st = SweepStats() if stats else None
+    _check(lib().ptca_sweep(h, n_sweeps, ctypes.byref(st) if stats else None, _stream(stream)))
+    return st
+
+
+def ptca_sweep_record(h, site=None, F_old=None, F_new=None, lnu=None, accepted=None, stream=None) -> None:
+    _check(lib().ptca_sweep_record(h, _ptr(site), _ptr(F_old), _ptr(F_new), _ptr(lnu), _ptr(accepted),
+                                   _stream(stream)))
+
+
+def ptca_observables(h, stream=None) -> Obs:
+    o = Obs()
+    _check(lib().ptca_observables(h, ctypes.byref(o), _stream(stream)))
+    return o
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper owning a context
+# ---------------------------------------------------------------------------
+class Context:
+    """A PTCA problem on the current CUDA device.
+
+    Uses torch only to allocate device buffers for the batched calls.
+    """
+
+    def __init__(self, cfg: Config):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required (no CPU fallback)")
+        self.cfg = cfg
+        self.h = ptca_init(cfg)
+        self.nmax, self.packed_stride = ptca_dims(self.h)
+
+    def close(self):
+        if self.h:
+            ptca_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def N(self):
+        return self.cfg.N
+
+    def spins(self):
+        import torch
+        out = torch.empty((self.N, 3), dtype=torch.float64, device="cuda")
+        ptca_get_spins(self.h, out)
+        return out
+
+    def set_spins(self, S):
+        import torch
+        S = torch.as_tensor(S, dtype=torch.float64).contiguous()
+        if not S.is_cuda:
+            S = S.cuda()
+        ptca_set_spins(self.h, S)
+
+    def sweep(self, n: int = 1, stats: bool = True):
+        return ptca_sweep(self.h, n, stats)
+
+    def record(self):
+        import torch
+        N = self.N
+        site = torch.empty(N, dtype=torch.int32, device="cuda")
+        Fo = torch.empty(N, dtype=torch.float64, device="cuda")
+        Fn = torch.empty(N, dtype=torch.float64, device="cuda")
+        lnu = torch.empty(N, dtype=torch.float64, device="cuda")
+        acc = torch.empty(N, dtype=torch.uint8, device="cuda")
+        ptca_sweep_record(self.h, site, Fo, Fn, lnu, acc)
+        torch.cuda.synchronize()
+        return site, Fo, Fn, lnu, acc
+
+    def observables(self) -> Obs:
+        return ptca_observables(self.h)
+
+    def build_clusters(self, sites, new_spins=None):
+        """Packed cluster matrices for update sites (device tensors)."""
+        import torch
+        sites = torch.as_tensor(sites, dtype=torch.int32).cuda().contiguous()
+        m = sites.numel()
+        dt = torch.complex128 if self.cfg.precision == FP64 else torch.complex64
+        H = torch.zeros(max(m, 1) * self.packed_stride, dtype=dt, device="cuda")
+        offs = torch.zeros(max(m, 1), dtype=torch.int64, device="cuda")
+        n = torch.zeros(max(m, 1), dtype=torch.int32, device="cuda")
+        ns = None
+        if new_spins is not None:
+            ns = torch.as_tensor(new_spins, dtype=torch.float64).cuda().contiguous()
+        ptca_build_clusters(self.h, sites, m, ns, H, offs, n)
+        return H, offs[:m], n[:m]
+
+    def cluster_eigvals(self, H, offsets, n):
+        import torch
+        m = n.numel()
+        eoff = torch.arange(m, dtype=torch.int64, device="cuda") * self.nmax
+        eig = torch.full((max(m, 1) * self.nmax,), float("nan"), dtype=torch.float64, device="cuda")
+        ptca_cluster_eigvals(self.h, H, offsets, n, m, eig, eoff)
+        return eig[: m * self.nmax].view(m, self.nmax) if m else eig[:0].view(0, self.nmax), eoff
+
+    def free_energy(self, eig_flat, eoff, n, mu=None, T=None):
+        import torch
+        m = n.numel()
+        F = torch.empty(max(m, 1), dtype=torch.float64, device="cuda")
+        ptca_free_energy(self.h, eig_flat, eoff, n, m, self.cfg.mu if mu is None else mu,
+                         self.cfg.T if T is None else T, F)
+        return F[:m]

@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI (no GPU): the library builds and loads,
+exports every entry point include/ptca.h declares, builds the same stage
+schedules as the oracle (Sec. III.a) and rejects invalid problems."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1502_07028_gb300 as P
+from paper_1502_07028_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    _build.build()
+    return P.lib()
+
+
+def _declared():
+    names = []
+    with open(os.path.join(ROOT, "include", "ptca.h")) as f:
+        text = f.read()
+    for m in re.finditer(r"^\s*(?:const\s+char\s*\*|ptca_status|int32_t)\s+(ptca_\w+)\s*\(", text, re.M):
+        names.append(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("ptca_init", "ptca_build_clusters", "ptca_cluster_eigvals", "ptca_free_energy",
+                     "ptca_sweep", "ptca_observables"):
+        assert required in names
+    assert sorted(names) == sorted(P.ptca.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(built):
+    for name in _declared():
+        assert hasattr(built, name), name
+    assert P.ptca_version() == 1
+
+
+def test_symbols_are_c_linkage(built):
+    # extern "C": plain names resolve through dlsym.
+    dl = ctypes.CDLL(_build.LIB)
+    for name in _declared():
+        assert ctypes.cast(getattr(dl, name), ctypes.c_void_p).value
+
+
+@pytest.mark.parametrize("kw", [
+    dict(Lx=8, Ly=8, L_c=4),
+    dict(Lx=10, Ly=10, L_c=8, stride=5),
+    dict(Lx=32, Ly=32, L_c=8, stride=8),
+    dict(Lx=12, Ly=12, L_c=4, schedule=P.SCHEDULE_BLOCK),
+    dict(Lx=100, Ly=100, L_c=8, schedule=P.SCHEDULE_BLOCK),
+    dict(Lx=31, Ly=17, L_c=6, periodic=0, stride=6),
+    dict(Lx=8, Ly=1, L_c=4, schedule=P.SCHEDULE_BLOCK),
+    dict(Lx=9, Ly=7, L_c=4, periodic=0, schedule=P.SCHEDULE_BLOCK),
+])
+def test_schedule_matches_oracle(built, kw):
+    cfg = P.Config(**kw)
+    mine = P.ptca_schedule(cfg)
+    m = oracle.Model(Lx=cfg.Lx, Ly=cfg.Ly, Lc=cfg.L_c, lattice_periodic=cfg.periodic,
+                     schedule=cfg.schedule, stride=cfg.stride)
+    ref = oracle.schedule(m)
+    assert len(mine) == len(ref)
+    for a, b in zip(mine, ref):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("kw,why", [
+    (dict(Lx=8, Ly=8, L_c=4, stride=2), "not exact"),
+    (dict(Lx=10, Ly=10, L_c=4, stride=3), "divide"),
+    (dict(Lx=8, Ly=8, L_c=1), "L_c"),
+    (dict(Lx=8, Ly=8, L_c=9), "L_c"),
+    (dict(Lx=12, Ly=12, L_c=8, schedule=P.SCHEDULE_BLOCK), "not exact"),
+    (dict(Lx=8, Ly=8, L_c=4, T=0.0), "T > 0"),
+    (dict(Lx=66, Ly=66, L_c=11, precision=P.MIXED), "maximum"),
+    (dict(Lx=8, Ly=8, L_c=4, update_offset=4), "update_offset"),
+])
+def test_invalid_problems_are_rejected(built, kw, why):
+    with pytest.raises(P.PtcaError) as e:
+        P.ptca_schedule(P.Config(**kw))
+    assert e.value.status == 1
+    assert why in str(e.value)
+
+
+def test_init_reports_missing_gpu_instead_of_falling_back(built):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(P.PtcaError) as e:
+        P.ptca_init(P.Config(Lx=8, Ly=8, L_c=4))
+    assert e.value.status == 2

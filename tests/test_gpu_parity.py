@@ -1,0 +1,332 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (from the stated accuracy of each precision mode):
+  * PTCA_FP64 -- eigenvalues |d eps| <= 1e-9 (J_H + 4t); free energies
+    |dF| <= 1e-9 max(1, |F|); accept/reject identical wherever
+    |ln u + dF/T| > 1e-6.
+  * PTCA_MIXED (FP32 reduction, FP64 eigenvalue refinement and free energy)
+    -- eigenvalues |d eps| <= 1e-5 (J_H + 4t); free energies
+    |dF| <= 1e-5 max(1, |F|); decisions identical wherever the margin exceeds
+    the band that error allows (1e-2 at T = 0.05).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1502_07028_gb300 as P
+from paper_1502_07028_gb300 import _build
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {P.FP64: 1e-9, P.MIXED: 1e-5}
+BAND = {P.FP64: 1e-6, P.MIXED: 1e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    P.lib()
+
+
+def _oracle_model(cfg: P.Config) -> oracle.Model:
+    return oracle.Model(Lx=cfg.Lx, Ly=cfg.Ly, Lc=cfg.L_c, t=cfg.t, JH=cfg.J_H, mu=cfg.mu, T=cfg.T,
+                        lattice_periodic=cfg.periodic, cluster_periodic=cfg.cluster_periodic,
+                        schedule=cfg.schedule, stride=cfg.stride, proposal=cfg.proposal,
+                        cone_deg=cfg.cone_deg, seed=cfg.seed, ox=cfg.update_offset, oy=cfg.update_offset)
+
+
+def _unpack(packed: np.ndarray, n: int) -> np.ndarray:
+    H = np.zeros((n, n), dtype=np.complex128)
+    k = 0
+    for r in range(n):
+        H[r, : r + 1] = packed[k: k + r + 1]
+        k += r + 1
+    H = np.tril(H) + np.tril(H, -1).conj().T
+    return H
+
+
+def _pack(H: np.ndarray) -> np.ndarray:
+    n = H.shape[0]
+    return np.concatenate([H[r, : r + 1] for r in range(n)]) if n else np.zeros(0, np.complex128)
+
+
+# ---------------------------------------------------------------------------
+# Builder
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [P.FP64, P.MIXED])
+@pytest.mark.parametrize("lat", [(8, 8, 4, 1), (16, 16, 8, 1), (12, 11, 8, 0), (8, 1, 4, 1)])
+def test_build_clusters_matches_oracle(prec, lat):
+    Lx, Ly, Lc, per = lat
+    cfg = P.Config(Lx=Lx, Ly=Ly, L_c=Lc, periodic=per, J_H=8.0, t=1.0, precision=prec,
+                   schedule=P.SCHEDULE_BLOCK if Ly == 1 else P.SCHEDULE_TILED)
+    ctx = P.Context(cfg)
+    S = inputs.random_unit_spins(31, cfg.N)
+    ctx.set_spins(S)
+    sites = np.arange(cfg.N, dtype=np.int32)[:: max(1, cfg.N // 23)]
+    new = inputs.random_unit_spins(32, sites.size)
+    m = _oracle_model(cfg)
+    for use_new in (False, True):
+        H, offs, n = ctx.build_clusters(sites, new if use_new else None)
+        H, offs, n = H.cpu().numpy(), offs.cpu().numpy(), n.cpu().numpy()
+        for i, s in enumerate(sites):
+            ref, _ = oracle.cluster_hamiltonian(m, S, int(s), new[i] if use_new else None)
+            assert n[i] == ref.shape[0]
+            mine = _unpack(H[offs[i]: offs[i] + n[i] * (n[i] + 1) // 2].astype(np.complex128), n[i])
+            tol = 0.0 if prec == P.FP64 else 1e-6 * 8.0
+            assert np.max(np.abs(mine - ref)) <= tol
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# Batched eigenvalues
+# ---------------------------------------------------------------------------
+def _eig_batch(ctx, mats):
+    """Pack host matrices, run ptca_cluster_eigvals, return list of arrays."""
+    dt = np.complex128 if ctx.cfg.precision == P.FP64 else np.complex64
+    packs = [_pack(M).astype(dt) for M in mats]
+    offs = np.cumsum([0] + [p.size for p in packs[:-1]]).astype(np.int64)
+    flat = np.concatenate(packs) if packs else np.zeros(1, dt)
+    H = torch.from_numpy(flat).cuda()
+    n = torch.tensor([M.shape[0] for M in mats], dtype=torch.int32, device="cuda")
+    eig, eoff = ctx.cluster_eigvals(H, torch.from_numpy(offs).cuda(), n)
+    eig = eig.cpu().numpy()
+    return [eig[i, : M.shape[0]] for i, M in enumerate(mats)]
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.MIXED])
+def test_eigvals_cluster_matrices_match_oracle(prec):
+    # n = 128 clusters (8x8 windows) plus a ragged open-lattice batch.
+    for Lx, Ly, Lc, per in ((16, 16, 8, 1), (12, 12, 8, 0), (8, 8, 4, 1)):
+        cfg = P.Config(Lx=Lx, Ly=Ly, L_c=Lc, periodic=per, precision=prec)
+        ctx = P.Context(cfg)
+        S = inputs.random_unit_spins(40 + Lx, cfg.N)
+        ctx.set_spins(S)
+        m = _oracle_model(cfg)
+        sites = inputs.random_sites(41, cfg.N, 12)
+        H, offs, n = ctx.build_clusters(sites)
+        eig, _ = ctx.cluster_eigvals(H, offs, n)
+        eig = eig.cpu().numpy()
+        nn = n.cpu().numpy()
+        for i, s in enumerate(sites):
+            ref = oracle.eigvalsh(oracle.cluster_hamiltonian(m, S, int(s))[0])
+            assert nn[i] == ref.size
+            err = np.max(np.abs(eig[i, : nn[i]] - ref))
+            assert err <= TOL[prec] * (cfg.J_H + 4 * cfg.t), (prec, Lx, Lc, err)
+        ctx.close()
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.MIXED])
+def test_eigvals_random_hermitian_ragged_batch(prec):
+    cfg = P.Config(Lx=16, Ly=16, L_c=8, precision=prec)
+    ctx = P.Context(cfg)
+    sizes = [1, 2, 3, 5, 17, 31, 32, 33, 64, 65, 100, 127, 128]
+    mats = [inputs.random_hermitian(200 + k, k, scale=2.0) for k in sizes]
+    got = _eig_batch(ctx, mats)
+    for M, e in zip(mats, got):
+        ref = oracle.eigvalsh(M)
+        scale = max(1.0, np.max(np.abs(ref)))
+        assert np.max(np.abs(e - ref)) <= TOL[prec] * scale * (10 if prec == P.MIXED else 1), (M.shape, prec)
+    ctx.close()
+
+
+def test_eigvals_degenerate_and_diagonal_fp64():
+    cfg = P.Config(Lx=16, Ly=16, L_c=8, precision=P.FP64)
+    ctx = P.Context(cfg)
+    mats = [np.eye(6) * 2.5, np.diag([3.0, -1.0, 2.0, 2.0, 0.0]), np.zeros((4, 4)),
+            oracle.cluster_hamiltonian(oracle.Model(Lx=8, Ly=8, Lc=4), inputs.ferro_spins(64, (0, 0, 1)), 0)[0]]
+    for M, e in zip(mats, _eig_batch(ctx, mats)):
+        ref = np.sort(np.linalg.eigvalsh(M))
+        assert np.max(np.abs(e - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+    ctx.close()
+
+
+def test_eigvals_rejects_out_of_range_order_with_nan():
+    cfg = P.Config(Lx=8, Ly=8, L_c=4, precision=P.FP64)  # nmax = 32
+    ctx = P.Context(cfg)
+    H = torch.zeros(64 * 65 // 2, dtype=torch.complex128, device="cuda")
+    offs = torch.zeros(1, dtype=torch.int64, device="cuda")
+    n = torch.tensor([33], dtype=torch.int32, device="cuda")
+    eig, _ = ctx.cluster_eigvals(H, offs, n)
+    assert torch.isnan(eig[0]).all()
+    # Empty batch is a no-op.
+    e0, _ = ctx.cluster_eigvals(H, offs[:0], n[:0])
+    assert e0.numel() == 0
+    ctx.close()
+
+
+def test_free_energy_matches_oracle():
+    cfg = P.Config(Lx=8, Ly=8, L_c=4)
+    ctx = P.Context(cfg)
+    rng = inputs.rng(5)
+    lists = [np.sort(rng.normal(scale=5.0, size=k)) for k in (1, 7, 32, 128, 200)]
+    nmax = 200
+    eig = np.full(len(lists) * nmax, np.nan)
+    for i, l in enumerate(lists):
+        eig[i * nmax: i * nmax + l.size] = l
+    eoff = torch.arange(len(lists), dtype=torch.int64, device="cuda") * nmax
+    n = torch.tensor([l.size for l in lists], dtype=torch.int32, device="cuda")
+    for mu, T in ((-6.5, 0.05), (0.3, 1.0), (-2.0, 0.01)):
+        F = ctx.free_energy(torch.from_numpy(eig).cuda(), eoff, n, mu=mu, T=T).cpu().numpy()
+        for i, l in enumerate(lists):
+            ref = oracle.free_energy(l, mu, T)
+            assert abs(F[i] - ref) <= 1e-12 * max(1.0, abs(ref))
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# Sweeps
+# ---------------------------------------------------------------------------
+def _replay(cfg, S0, stages, site, acc, sweep_index):
+    """Stage-start configurations implied by the GPU's decisions."""
+    m = _oracle_model(cfg)
+    S = S0.copy()
+    starts = []
+    pos = {int(s): k for k, s in enumerate(site)}
+    for st in stages:
+        starts.append(S.copy())
+        snap = S.copy()
+        for s in st:
+            s = int(s)
+            if acc[pos[s]]:
+                S[s] = oracle.propose(m, sweep_index, s, snap[s])
+    return starts, S
+
+
+def _check_sweep_against_oracle(cfg, sweeps, sample=None, seed_spins=None):
+    ctx = P.Context(cfg)
+    if seed_spins is not None:
+        ctx.set_spins(inputs.random_unit_spins(seed_spins, cfg.N))
+    m = _oracle_model(cfg)
+    stages = P.ptca_schedule(cfg)
+    flat = np.concatenate(stages)
+    tol, band = TOL[cfg.precision], BAND[cfg.precision]
+    worst = 0.0
+    for sw in range(sweeps):
+        S0 = ctx.spins().cpu().numpy()
+        stats = ctx.sweep(1)
+        assert stats.attempts == cfg.N and stats.eigensolves == 2 * cfg.N
+        site, Fo, Fn, lnu, acc = (x.cpu().numpy() for x in ctx.record())
+        S1 = ctx.spins().cpu().numpy()
+        assert np.array_equal(site, flat)
+        assert stats.accepted == int(acc.sum())
+        starts, S_replay = _replay(cfg, S0, stages, site, acc, sw)
+        assert np.max(np.abs(S1 - S_replay)) < 1e-13
+        stage_of = np.zeros(cfg.N, dtype=np.int64)
+        for k, st in enumerate(stages):
+            stage_of[st] = k
+        idx = np.arange(cfg.N) if sample is None else inputs.rng(sw).choice(cfg.N, size=sample, replace=False)
+        for k in idx:
+            s = int(site[k])
+            Sst = starts[stage_of[s]]
+            Fo_ref = oracle.cluster_free_energy(m, Sst, s)
+            s_new = oracle.propose(m, sw, s, Sst[s])
+            Fn_ref = oracle.cluster_free_energy(m, Sst, s, s_new)
+            lnu_ref = math.log(oracle.uniform2(cfg.seed, sw, s, 2)[0])
+            e1 = abs(Fo[k] - Fo_ref) / max(1.0, abs(Fo_ref))
+            e2 = abs(Fn[k] - Fn_ref) / max(1.0, abs(Fn_ref))
+            worst = max(worst, e1, e2)
+            assert e1 <= tol and e2 <= tol, (sw, s, Fo[k], Fo_ref, Fn[k], Fn_ref)
+            assert abs(lnu[k] - lnu_ref) <= 1e-14 * max(1.0, abs(lnu_ref))
+            margin = abs(lnu_ref + (Fn_ref - Fo_ref) / cfg.T)
+            if margin > band:
+                assert bool(acc[k]) == (lnu_ref < -(Fn_ref - Fo_ref) / cfg.T), (sw, s, margin)
+    ctx.close()
+    return worst
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.MIXED])
+def test_sweep_small_lattice_every_visit(prec):
+    # 8x8 torus, 4x4 clusters (n = 32), mu = -6.5, T = 0.05, sphere proposals.
+    cfg = P.Config(Lx=8, Ly=8, L_c=4, t=1.0, J_H=8.0, mu=-6.5, T=0.05, seed=0, precision=prec)
+    _check_sweep_against_oracle(cfg, sweeps=3)
+
+
+def test_sweep_fp64_equals_sequential_oracle_sweep():
+    # Decisions and spins of whole sweeps equal the oracle's one-visit-at-a-time
+    # sweep in the flattened stage order.
+    cfg = P.Config(Lx=8, Ly=8, L_c=4, t=1.0, J_H=8.0, mu=-6.5, T=0.05, seed=0, precision=P.FP64)
+    ctx = P.Context(cfg)
+    m = _oracle_model(cfg)
+    S = ctx.spins().cpu().numpy()
+    assert np.max(np.abs(S - oracle.init_spins(m))) < 1e-15
+    for sw in range(10):
+        ctx.sweep(1)
+        site, Fo, Fn, lnu, acc = (x.cpu().numpy() for x in ctx.record())
+        S_ref, rec = oracle.sweep(m, S, sw)
+        margin = np.abs(rec.lnu + (rec.F_new - rec.F_old) / cfg.T)
+        assert np.all(margin > 1e-6)
+        assert np.array_equal(acc, rec.accepted)
+        assert np.max(np.abs(Fo - rec.F_old)) <= 1e-9 * np.max(np.abs(rec.F_old))
+        S = ctx.spins().cpu().numpy()
+        assert np.max(np.abs(S - S_ref)) < 1e-13
+    ctx.close()
+
+
+def test_sweep_paper_block_schedule_overlapping_windows():
+    # Corner update site, 4 quadrant blocks (Sec. III.a): windows of one stage
+    # overlap other update sites of the stage, read from the stage start.
+    cfg = P.Config(Lx=8, Ly=8, L_c=4, schedule=P.SCHEDULE_BLOCK, T=0.1, seed=3, precision=P.FP64)
+    _check_sweep_against_oracle(cfg, sweeps=2)
+
+
+def test_sweep_chain_fig3():
+    cfg = P.Config(Lx=8, Ly=1, L_c=4, schedule=P.SCHEDULE_BLOCK, J_H=4.0, mu=-3.0, T=0.2, seed=4)
+    _check_sweep_against_oracle(cfg, sweeps=3)
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.MIXED])
+def test_sweep_open_lattice_ragged_windows(prec):
+    # Open 12x10 lattice, L_c = 6: clipped windows give n from 18 to 72.
+    cfg = P.Config(Lx=12, Ly=10, L_c=6, periodic=0, stride=6, J_H=6.0, mu=-4.5, T=0.1, seed=5, precision=prec)
+    _check_sweep_against_oracle(cfg, sweeps=1)
+
+
+def test_sweep_cone_proposals_stride5_n128():
+    # 10x10 torus, 8x8 clusters (n = 128), centres 5 apart, 30 degree cone.
+    cfg = P.Config(Lx=10, Ly=10, L_c=8, stride=5, proposal=P.PROPOSAL_CONE, cone_deg=30.0, T=0.05,
+                   seed=6, precision=P.FP64)
+    _check_sweep_against_oracle(cfg, sweeps=1, sample=12)
+
+
+@pytest.mark.parametrize("prec,schedule,stride", [(P.MIXED, P.SCHEDULE_BLOCK, 0), (P.MIXED, P.SCHEDULE_TILED, 10),
+                                                  (P.FP64, P.SCHEDULE_BLOCK, 0)])
+def test_full_size_100x100_sampled(prec, schedule, stride):
+    # The benchmark workload: 100x100 torus, 8x8 clusters, cone proposals.
+    cfg = P.Config(Lx=100, Ly=100, L_c=8, schedule=schedule, stride=stride, proposal=P.PROPOSAL_CONE,
+                   cone_deg=30.0, T=0.05, mu=-6.5, seed=0, precision=prec)
+    _check_sweep_against_oracle(cfg, sweeps=1, sample=6)
+
+
+def test_observables_ferro_and_neel():
+    cfg = P.Config(Lx=8, Ly=8, L_c=4)
+    ctx = P.Context(cfg)
+    ctx.set_spins(inputs.ferro_spins(cfg.N, (0.3, 0.4, 0.5)))
+    o = ctx.observables()
+    assert abs(o.S_00 - 1.0) < 1e-13 and abs(o.S_pipi) < 1e-13
+    ctx.set_spins(inputs.neel_spins(8, 8))
+    o = ctx.observables()
+    assert abs(o.S_pipi - 1.0) < 1e-13 and abs(o.S_00) < 1e-13
+    st = ctx.sweep(1)
+    o = ctx.observables()
+    assert abs(o.acceptance - st.accepted / cfg.N) < 1e-15
+    S = ctx.spins().cpu().numpy()
+    assert abs(o.S_pipi - oracle.structure_factor(8, 8, S, math.pi, math.pi)) < 1e-12
+    assert abs(o.S_00 - oracle.structure_factor(8, 8, S, 0.0, 0.0)) < 1e-12
+    assert 0.0 < o.filling < 2.0
+    ctx.close()
+
+
+def test_resume_is_bit_exact():
+    # Counter-based randomness: two contexts given the same spins and sweep
+    # counter produce identical sweeps.
+    cfg = P.Config(Lx=8, Ly=8, L_c=4, precision=P.MIXED, seed=9)
+    a, b = P.Context(cfg), P.Context(cfg)
+    a.sweep(2)
+    b.sweep(2)
+    assert torch.equal(a.spins(), b.spins())
+    a.close(); b.close()
