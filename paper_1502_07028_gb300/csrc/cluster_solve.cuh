@@ -116,11 +116,11 @@ __device__ void build_cluster(const Model& m, const Window& w, const double* __r
 // moduli e2[0..n-2] (the phases of the off-diagonal do not affect the
 // eigenvalues).
 //
-// Work layout: row i of the trailing block belongs to warp i % NW; lane l
-// handles columns j = l + 32 t (t < NT).  Each warp processes its rows in
-// batches of 8; the 8 row sums are reduce-scattered across the warp.  Column
-// (transposed) contributions accumulate per lane and are summed across warps
-// through shared memory.
+// Work layout (indices relative to the active corner j0 = k+1): relative row
+// ri belongs to warp ri % NW; lane l handles relative columns l + 32 t.  Each
+// warp processes its rows in batches of 8; the 8 row sums are
+// reduce-scattered across the warp.  Column (transposed) contributions
+// accumulate per lane and are summed across warps through shared memory.
 // ---------------------------------------------------------------------------
 template <typename T> struct HHScratch {
     cplx_t<T>* Vb;   // 2 x NMAX   Householder vectors of consecutive steps
@@ -156,6 +156,25 @@ __device__ __forceinline__ V reduce_scatter8(const V (&v)[8], int lane) {
     return w1;  // row (lane >> 2) & 7 of the batch
 }
 
+template <typename V>
+__device__ __forceinline__ V reduce_scatter4(const V (&v)[4], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8;
+    V w2[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        V mine = b4 ? v[q + 2] : v[q];
+        V other = b4 ? v[q] : v[q + 2];
+        w2[q] = cadd(mine, cshfl_xor(other, 16));
+    }
+    V mine = b3 ? w2[1] : w2[0];
+    V other = b3 ? w2[0] : w2[1];
+    V w1 = cadd(mine, cshfl_xor(other, 8));
+    w1 = cadd(w1, cshfl_xor(w1, 4));
+    w1 = cadd(w1, cshfl_xor(w1, 2));
+    w1 = cadd(w1, cshfl_xor(w1, 1));
+    return w1;  // row (lane >> 3) & 3 of the batch
+}
+
 template <typename T, int NT, int NW>
 __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc, double* d, double* e2) {
     using V = cplx_t<T>;
@@ -180,128 +199,190 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
         return;
     }
 
-    // Column 0: d_0, ||x||^2 and the first reflector.
-    T tau;
-    {
-        V a = zero;
-        if (tid < n) a = A[tri(tid)];
-        if (tid == 0) d[0] = double(a.x);
-        T s2 = block_sum<T>((tid >= 1 && tid < n) ? cabs2(a) : T(0), sc.redB);
-        const T sigma = sqrt(s2);
-        const V x0 = A[tri(1)];
-        const T ax0 = sqrt(cabs2(x0));
-        if (tid == 0) e2[0] = double(s2);
-        if (tid >= 1 && tid < n) {
-            V v = a;
-            if (tid == 1) {
-                const V ph = ax0 > T(0) ? mk(x0.x / ax0, x0.y / ax0) : mk(T(1), T(0));
-                v = mk(x0.x + ph.x * sigma, x0.y + ph.y * sigma);
-            }
-            Vb[tid] = v;
+    // Column 0 (warp 0): d_0, ||x||^2 and the first reflector.  tau lives in
+    // warp 0's registers; only warp 0 uses it.
+    T tau = T(0);
+    if (warp == 0) {
+        V a[NT];
+        T s2 = T(0);
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            const int i = lane + 32 * q;
+            a[q] = i < n ? A[tri(i)] : zero;
+            if (i >= 1 && i < n) s2 += cabs2(a[q]);
+        }
+        s2 = warp_sum(s2);
+        const T sigma = sqroot(s2);
+        const V x0 = mk(__shfl_sync(FULL_MASK, a[0].x, 1), __shfl_sync(FULL_MASK, a[0].y, 1));
+        const T ax0 = sqroot(cabs2(x0));
+        if (lane == 0) { d[0] = double(a[0].x); e2[0] = double(s2); }
+        const V ph = ax0 > T(0) ? mk(x0.x / ax0, x0.y / ax0) : mk(T(1), T(0));
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            const int i = lane + 32 * q;
+            if (i >= 1 && i < n) Vb[i] = (i == 1) ? mk(x0.x + ph.x * sigma, x0.y + ph.y * sigma) : a[q];
         }
         tau = sigma > T(0) ? T(1) / (sigma * (sigma + ax0)) : T(0);
-        __syncthreads();
     }
+    __syncthreads();
 
     for (int k = 0; k <= n - 3; ++k) {
         const V* V_ = Vb + (k & 1) * NMAX;        // v_k
         const V* U_ = Vb + ((k + 1) & 1) * NMAX;  // v_{k-1} (zero at k = 0)
         const int j0 = k + 1;                     // first active row/column
 
-        // ---- fused pass: A <- A - u w^H - w u^H (step k-1), accumulate A v_k
+        // ---- fused pass: A <- A - u w^H - w u^H (step k-1), accumulate A v_k.
+        // Indices are relative to the active corner j0.  The trailing rows
+        // are cut into batches of RB consecutive rows, dealt to the warps in
+        // snake order (balanced work); lane l handles relative columns
+        // l + 32 t.  Per chunk t the RB elements of a lane are independent and
+        // branch-free (masked loads and stores), so their loads and FMA chains
+        // overlap.  At k = 0, u and w are zero and the update is a no-op.
+        constexpr int RB = sizeof(T) == 4 ? 8 : 4;
+        const int m = n - j0;
+        const int nbatch = (m + RB - 1) / RB;
         V vc[NT], uc[NT], wc[NT], cacc[NT];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int j = 32 * t + lane;
-            vc[t] = V_[j]; uc[t] = U_[j]; wc[t] = Wv[j];
+            const int j = j0 + 32 * t + lane;
+            const bool in = j < n;
+            vc[t] = in ? V_[j] : zero;
+            uc[t] = in ? U_[j] : zero;
+            wc[t] = in ? Wv[j] : zero;
             cacc[t] = zero;
         }
-        const int first = j0 + ((warp - j0) % NW + NW) % NW;
-        for (int rb = first; rb < n; rb += 8 * NW) {
-            V racc[8];
+        for (int round = 0;; ++round) {
+            // Heaviest batches first, snake order over the warps.
+            const int slot = round * NW + ((round & 1) ? (NW - 1 - warp) : warp);
+            if (slot >= nbatch) break;
+            const int b = nbatch - 1 - slot;
+            const int ri0 = b * RB;
+            V ui[RB], wi[RB], vi[RB], racc[RB];
+            int base[RB];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) racc[r] = zero;
+            for (int r = 0; r < RB; ++r) {
+                const int ri = ri0 + r;
+                const bool ok = ri < m;
+                const int i = j0 + ri;
+                ui[r] = ok ? U_[i] : zero;
+                wi[r] = ok ? Wv[i] : zero;
+                vi[r] = ok ? V_[i] : zero;
+                base[r] = ok ? tri(i) + j0 : 0;
+                racc[r] = zero;
+            }
+            const int last = (ri0 + RB - 1 < m ? ri0 + RB - 1 : m - 1);
+            const int nch = (last >> 5) + 1;
+            const bool full_rows = ri0 + RB - 1 < m;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const int i = rb + r * NW;
-                if (i < n) {
-                    const V ui = U_[i], wi = Wv[i], vi = V_[i];
-                    V* row = A + tri(i);
+            for (int t = 0; t < NT; ++t) {
+                if (t < nch) {
+                    const int jr = 32 * t + lane;
+                    if (full_rows && 32 * t + 31 < ri0) {
+                        // Chunk strictly below the diagonal for every row of a
+                        // full batch: no masks.
 #pragma unroll
-                    for (int t = 0; t < NT; ++t) {
-                        if (32 * t + 31 >= j0 && 32 * t <= i) {
-                            const int j = 32 * t + lane;
-                            if (j >= j0 && j <= i) {
-                                V a = row[j];
-                                if (k > 0) {
-                                    a = cfms_conj_b(ui, wc[t], a);
-                                    a = cfms_conj_b(wi, uc[t], a);
-                                    if (j == i) a.y = T(0);
-                                    row[j] = a;
-                                }
-                                racc[r] = cfma(a, vc[t], racc[r]);
-                                if (j < i) cacc[t] = cfma_conj_a(a, vi, cacc[t]);
-                            }
+                        for (int r = 0; r < RB; ++r) {
+                            V a = A[base[r] + jr];
+                            a = cfms_conj_b(ui[r], wc[t], a);
+                            a = cfms_conj_b(wi[r], uc[t], a);
+                            A[base[r] + jr] = a;
+                            racc[r] = cfma(a, vc[t], racc[r]);
+                            cacc[t] = cfma_conj_a(a, vi[r], cacc[t]);
                         }
+                        continue;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        const int ri = ri0 + r;
+                        const bool ok = (ri < m) && (jr <= ri);
+                        V a = A[ok ? base[r] + jr : 0];
+                        a = cfms_conj_b(ui[r], wc[t], a);
+                        a = cfms_conj_b(wi[r], uc[t], a);
+                        if (jr == ri) a.y = T(0);
+                        a = ok ? a : zero;
+                        if (ok) A[base[r] + jr] = a;
+                        racc[r] = cfma(a, vc[t], racc[r]);
+                        const V vrow = (jr < ri) ? vi[r] : zero;
+                        cacc[t] = cfma_conj_a(a, vrow, cacc[t]);
                     }
                 }
             }
-            const V rs = reduce_scatter8(racc, lane);
-            const int ri = rb + ((lane >> 2) & 7) * NW;
-            if ((lane & 3) == 0 && ri < n) pr[ri] = rs;
+            V out;
+            if constexpr (RB == 8) {
+                out = reduce_scatter8(racc, lane);
+                const int ri = ri0 + ((lane >> 2) & 7);
+                if ((lane & 3) == 0 && ri < m) pr[ri] = out;
+            } else {
+                out = reduce_scatter4(racc, lane);
+                const int ri = ri0 + ((lane >> 3) & 3);
+                if ((lane & 7) == 0 && ri < m) pr[ri] = out;
+            }
         }
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int j = 32 * t + lane;
-            if (j >= j0 && j < n) pc[warp * NMAX + j] = cacc[t];
+            const int jr = 32 * t + lane;
+            if (jr < m) pc[warp * NMAX + jr] = cacc[t];
         }
         __syncthreads();
 
-        // ---- p = tau A v, s = v^H p
-        V p = zero, vj = zero;
-        if (tid >= j0 && tid < n) {
-            p = pr[tid];
-            for (int w = 0; w < NW; ++w) p = cadd(p, pc[w * NMAX + tid]);
-            p.x *= tau; p.y *= tau;
-            vj = V_[tid];
-        }
-        const T s = block_sum<T>(vj.x * p.x + vj.y * p.y, sc.redA);
-        const T K = T(0.5) * tau * s;
-
-        // ---- w = p - K v; explicit update of pivot column k+1
-        V wj = mk(p.x - K * vj.x, p.y - K * vj.y);
-        V pk = pr[j0];
-        for (int w = 0; w < NW; ++w) pk = cadd(pk, pc[w * NMAX + j0]);
-        pk.x *= tau; pk.y *= tau;
-        const V vk1 = V_[j0];
-        const V wk1 = mk(pk.x - K * vk1.x, pk.y - K * vk1.y);
-        V a = zero;
-        if (tid >= j0 && tid < n) {
-            Wv[tid] = wj;
-            a = A[tri(tid) + j0];
-            a = cfms_conj_b(vj, wk1, a);
-            a = cfms_conj_b(wj, vk1, a);
-            if (tid == j0) { a.y = T(0); d[j0] = double(a.x); }
-            A[tri(tid) + j0] = a;
-        }
-        const T s2 = block_sum<T>((tid >= j0 + 1 && tid < n) ? cabs2(a) : T(0), sc.redB);
-        if (tid == 0) e2[j0] = double(s2);
-
-        // ---- next reflector from column k+1 (none for the last column)
-        if (k + 1 <= n - 3) {
-            V* Vn = Vb + ((k + 1) & 1) * NMAX;
-            const T sigma = sqrt(s2);
-            const V x0 = A[tri(j0 + 1) + j0];
-            const T ax0 = sqrt(cabs2(x0));
-            if (tid >= j0 + 1 && tid < n) {
-                V v = a;
-                if (tid == j0 + 1) {
-                    const V ph = ax0 > T(0) ? mk(x0.x / ax0, x0.y / ax0) : mk(T(1), T(0));
-                    v = mk(x0.x + ph.x * sigma, x0.y + ph.y * sigma);
+        // ---- warp 0: p = tau A v, s = v^H p, w = p - (tau s/2) v, explicit
+        // update of pivot column k+1, ||x||^2 and the next reflector.
+        if (warp == 0) {
+            V pq[NT], vq[NT], aq[NT];
+            T sp = T(0);
+#pragma unroll
+            for (int q = 0; q < NT; ++q) {
+                const int ri = lane + 32 * q;
+                V p = zero, v = zero;
+                if (ri < m) {
+                    p = pr[ri];
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) p = cadd(p, pc[w * NMAX + ri]);
+                    p.x *= tau; p.y *= tau;
+                    v = V_[j0 + ri];
                 }
-                Vn[tid] = v;
+                pq[q] = p; vq[q] = v;
+                sp += v.x * p.x + v.y * p.y;
             }
-            tau = sigma > T(0) ? T(1) / (sigma * (sigma + ax0)) : T(0);
+            const T K = T(0.5) * tau * warp_sum(sp);
+            // w_{k+1} and v_{k+1} entries of the pivot row (relative index 0).
+            const V w0 = mk(__shfl_sync(FULL_MASK, pq[0].x - K * vq[0].x, 0),
+                            __shfl_sync(FULL_MASK, pq[0].y - K * vq[0].y, 0));
+            const V v0 = mk(__shfl_sync(FULL_MASK, vq[0].x, 0), __shfl_sync(FULL_MASK, vq[0].y, 0));
+            T s2 = T(0);
+#pragma unroll
+            for (int q = 0; q < NT; ++q) {
+                const int ri = lane + 32 * q;
+                V a = zero;
+                if (ri < m) {
+                    const V w = mk(pq[q].x - K * vq[q].x, pq[q].y - K * vq[q].y);
+                    Wv[j0 + ri] = w;
+                    V* ap = A + tri(j0 + ri) + j0;
+                    a = *ap;
+                    a = cfms_conj_b(vq[q], w0, a);
+                    a = cfms_conj_b(w, v0, a);
+                    if (ri == 0) { a.y = T(0); d[j0] = double(a.x); }
+                    *ap = a;
+                    if (ri >= 1) s2 += cabs2(a);
+                }
+                aq[q] = a;
+            }
+            s2 = warp_sum(s2);
+            if (lane == 0) e2[j0] = double(s2);
+            if (k + 1 <= n - 3) {
+                V* Vn = Vb + ((k + 1) & 1) * NMAX;
+                const T sigma = sqroot(s2);
+                const V x0 = mk(__shfl_sync(FULL_MASK, aq[0].x, 1), __shfl_sync(FULL_MASK, aq[0].y, 1));
+                const T ax0 = sqroot(cabs2(x0));
+                const V ph = ax0 > T(0) ? mk(x0.x / ax0, x0.y / ax0) : mk(T(1), T(0));
+#pragma unroll
+                for (int q = 0; q < NT; ++q) {
+                    const int ri = lane + 32 * q;
+                    if (ri >= 1 && ri < m)
+                        Vn[j0 + ri] = (ri == 1) ? mk(x0.x + ph.x * sigma, x0.y + ph.y * sigma) : aq[q];
+                }
+                tau = sigma > T(0) ? T(1) / (sigma * (sigma + ax0)) : T(0);
+            }
         }
         __syncthreads();
     }
@@ -322,12 +403,28 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
 // magnitude below pivmin replaced by -pivmin (Barth, Martin and Wilkinson's
 // bisection with Kahan's safeguard).
 // ---------------------------------------------------------------------------
+
+// FP64 reciprocal by Newton-Raphson: an FP32 reciprocal as seed, then
+// r <- r + r (1 - q r) twice (error squares each time: 2^-22 -> 2^-44 ->
+// below FP64 rounding).  Outside the FP32 range the plain quotient is used.
+__device__ __forceinline__ double rcp64(double q) {
+    const double aq = fabs(q);
+    if (aq > 1e-30 && aq < 1e30) {
+        double r = (double)__fdividef(1.0f, (float)q);
+        double e = __fma_rn(-q, r, 1.0);
+        r = __fma_rn(r, e, r);
+        e = __fma_rn(-q, r, 1.0);
+        return __fma_rn(r, e, r);
+    }
+    return 1.0 / q;
+}
+
 __device__ __forceinline__ int sturm_count_f64(int n, const double* d, const double* e2, double x, double pivmin) {
     double q = d[0] - x;
     if (fabs(q) < pivmin) q = -pivmin;
     int c = q < 0.0;
     for (int i = 1; i < n; ++i) {
-        q = (d[i] - x) - e2[i - 1] / q;
+        q = (d[i] - x) - e2[i - 1] * rcp64(q);
         if (fabs(q) < pivmin) q = -pivmin;
         c += q < 0.0;
     }
@@ -346,60 +443,70 @@ __device__ __forceinline__ int sturm_count_f32(int n, const float* d, const floa
     return c;
 }
 
-// Gershgorin interval of the tridiagonal (computed by every thread from
-// shared memory; the fixed order gives identical results in all threads).
-__device__ __forceinline__ void gershgorin(int n, const double* d, const double* e2, double& lo, double& hi, double& emax2) {
-    lo = 1e300; hi = -1e300; emax2 = 0.0;
-    double eprev = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const double ei = (i < n - 1) ? sqrt(e2[i]) : 0.0;
-        if (i < n - 1) emax2 = fmax(emax2, e2[i]);
-        lo = fmin(lo, d[i] - eprev - ei);
-        hi = fmax(hi, d[i] + eprev + ei);
-        eprev = ei;
-    }
-    const double w = hi - lo, nrm = fmax(fabs(lo), fabs(hi));
-    lo -= 1e-12 * (w + nrm) + 1e-300;
-    hi += 1e-12 * (w + nrm) + 1e-300;
-}
-
-// k-th smallest eigenvalue (0-based) by FP64 bisection on [lo, hi].
-__device__ __forceinline__ double bisect_f64(int n, const double* d, const double* e2, int k, double lo, double hi,
-                                             double pivmin, double atol) {
-    for (int it = 0; it < 80; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (hi - lo <= fmax(atol, 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)))) break;
-        if (sturm_count_f64(n, d, e2, mid, pivmin) <= k) lo = mid; else hi = mid;
-    }
-    return 0.5 * (lo + hi);
-}
-
-// k-th smallest eigenvalue: FP32 bisection to FP32 resolution, then one FP64
-// Newton step on det(T - x) = prod q_i (the logarithmic derivative
-// sum q_i'/q_i comes from the same pivot recurrence), kept only if it stays
-// near the FP32 bracket.
-__device__ __forceinline__ double bisect_f32_newton_f64(int n, const float* df, const float* e2f, const double* d,
-                                                        const double* e2, int k, float lo, float hi, float pivminf,
-                                                        float atolf, double pivmin) {
-    for (int it = 0; it < 48; ++it) {
-        const float mid = 0.5f * (lo + hi);
-        if (hi - lo <= fmaxf(atolf, 2.0f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)))) break;
-        if (sturm_count_f32(n, df, e2f, mid, pivminf) <= k) lo = mid; else hi = mid;
-    }
-    const double x = 0.5 * ((double)lo + (double)hi);
+// One FP64 pass of the pivot recurrence at x: the Sturm count and the
+// logarithmic derivative s = sum_i q_i'/q_i of det(T - x) = prod_i q_i, with
+// q_0' = -1 and q_i' = -1 + e2_{i-1} q_{i-1}' / q_{i-1}^2.
+__device__ __forceinline__ int newton_pass_f64(int n, const double* d, const double* e2, double x, double pivmin,
+                                               double& s) {
     double q = d[0] - x, dq = -1.0;
     if (fabs(q) < pivmin) q = -pivmin;
-    double s = 0.0;
+    int c = q < 0.0;
+    double acc = 0.0;
     for (int i = 1; i < n; ++i) {
-        const double r = 1.0 / q;
-        s = fma(dq, r, s);
+        const double r = rcp64(q);
+        acc = __fma_rn(dq, r, acc);
         const double er = e2[i - 1] * r;
         double qn = (d[i] - x) - er;
-        dq = fma(er * r, dq, -1.0);
+        dq = __fma_rn(er * r, dq, -1.0);
         if (fabs(qn) < pivmin) qn = -pivmin;
         q = qn;
+        c += q < 0.0;
     }
-    s = fma(dq, 1.0 / q, s);
+    s = __fma_rn(dq, rcp64(q), acc);
+    return c;
+}
+
+// k-th smallest eigenvalue (0-based), all FP64: bisection down to a bracket
+// of width ~1e-6 ||T||, then Newton on det(T - x) while the bracket holds
+// exactly this one eigenvalue (bisection otherwise, and whenever a Newton
+// step would leave the bracket or fails to halve it).  Every pass tightens
+// the bracket with its Sturm count.
+__device__ __forceinline__ double eig_f64(int n, const double* d, const double* e2, int k, double lo, double hi,
+                                          double pivmin, double nrm) {
+    const double coarse = 1e-6 * nrm;
+    int clo = 0, chi = n;
+    for (int it = 0; it < 64 && hi - lo > coarse; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        const int c = sturm_count_f64(n, d, e2, mid, pivmin);
+        if (c <= k) { lo = mid; clo = c; } else { hi = mid; chi = c; }
+    }
+    const double tol = 2.0 * DBL_EPSILON * nrm;
+    double x = 0.5 * (lo + hi), width_before = hi - lo;
+    for (int it = 0; it < 96 && hi - lo > tol; ++it) {
+        double s;
+        const int c = newton_pass_f64(n, d, e2, x, pivmin, s);
+        if (c <= k) { lo = x; clo = c; } else { hi = x; chi = c; }
+        const double mid = 0.5 * (lo + hi);
+        double xn = mid;
+        if (chi - clo == 1 && s != 0.0 && isfinite(s)) {
+            const double cand = x - 1.0 / s;
+            if (cand > lo && cand < hi && 2.0 * fabs(cand - x) <= width_before) xn = cand;
+        }
+        const double step = fabs(xn - x);
+        width_before = hi - lo;
+        x = xn;
+        if (chi - clo == 1 && step <= tol) break;
+    }
+    return x;
+}
+
+// One FP64 Newton correction of an eigenvalue located by FP32 multisection
+// in [lo, hi]; kept only if it stays near that bracket.
+__device__ __forceinline__ double newton_polish_f64(int n, const double* d, const double* e2, float lo, float hi,
+                                                    float atolf, double pivmin) {
+    const double x = 0.5 * ((double)lo + (double)hi);
+    double s;
+    newton_pass_f64(n, d, e2, x, pivmin, s);
     const double xn = x - 1.0 / s;
     const double w = fmax((double)(hi - lo), 4.0 * (double)atolf);
     if (isfinite(xn) && xn >= (double)lo - w && xn <= (double)hi + w) return xn;

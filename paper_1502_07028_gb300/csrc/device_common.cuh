@@ -21,24 +21,31 @@ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(
 
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// Precision-explicit fused multiply-add and square root (no implicit
+// promotion of float arguments to double).
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float sqroot(float a) { return sqrtf(a); }
+__device__ __forceinline__ double sqroot(double a) { return sqrt(a); }
+
 // a * b
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) { V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r; }
 // acc + a * b
 template <typename V> __device__ __forceinline__ V cfma(V a, V b, V acc) {
-    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
-    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+    acc.x = fmadd(a.x, b.x, acc.x); acc.x = fmadd(-a.y, b.y, acc.x);
+    acc.y = fmadd(a.x, b.y, acc.y); acc.y = fmadd(a.y, b.x, acc.y);
     return acc;
 }
 // acc + conj(a) * b
 template <typename V> __device__ __forceinline__ V cfma_conj_a(V a, V b, V acc) {
-    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
-    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+    acc.x = fmadd(a.x, b.x, acc.x); acc.x = fmadd(a.y, b.y, acc.x);
+    acc.y = fmadd(a.x, b.y, acc.y); acc.y = fmadd(-a.y, b.x, acc.y);
     return acc;
 }
 // acc - a * conj(b)
 template <typename V> __device__ __forceinline__ V cfms_conj_b(V a, V b, V acc) {
-    acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
-    acc.y = fma(-a.y, b.x, acc.y); acc.y = fma(a.x, b.y, acc.y);
+    acc.x = fmadd(-a.x, b.x, acc.x); acc.x = fmadd(-a.y, b.y, acc.x);
+    acc.y = fmadd(-a.y, b.x, acc.y); acc.y = fmadd(a.x, b.y, acc.y);
     return acc;
 }
 template <typename V> __device__ __forceinline__ auto cabs2(V a) -> decltype(a.x) { return a.x * a.x + a.y * a.y; }

@@ -10,9 +10,12 @@ constexpr int NW = 8;              // warps per CTA of the cluster kernels
 constexpr int CTA = 32 * NW;
 constexpr double kFermiCut = 40.0; // eigenvalues above mu + 40 T change F by < T e^-40 each
 
+// Two CTAs per SM fit in shared memory for FP32 matrices up to n = 128.
+template <typename T, int NT> struct MinBlocks { static constexpr int value = (sizeof(T) == 4 && NT <= 4) ? 2 : 1; };
+
 // Shared-memory layout of one cluster CTA (byte offsets, 16-byte aligned).
 struct SmemLayout {
-    size_t A, Vb, Wv, pr, pc, d, e2, df, e2f, sp, red, total;
+    size_t A, Vb, Wv, pr, pc, d, e2, df, e2f, sp, lam, red, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -31,13 +34,14 @@ __host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs) 
     L.df = o;  o = align16(o + (size_t)nmaxc * sizeof(float));
     L.e2f = o; o = align16(o + (size_t)nmaxc * sizeof(float));
     L.sp = o;  o = align16(o + (size_t)(nmaxc / 2) * 3 * sizeof(double));
+    L.lam = o; o = align16(o + (size_t)nmaxc * 2 * sizeof(float));
     L.red = o; o = align16(o + 4 * (size_t)NW * sizeof(double));
     L.total = o;
     return L;
 }
 
 template <typename T> struct Carve {
-    cplx_t<T>* A; HHScratch<T> hh; double* d; double* e2; float* df; float* e2f; double* sp; double* red;
+    cplx_t<T>* A; HHScratch<T> hh; double* d; double* e2; float* df; float* e2f; double* sp; float* lam; double* red;
 };
 
 template <typename T>
@@ -56,6 +60,7 @@ __device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout&
     c.df = reinterpret_cast<float*>(base + L.df);
     c.e2f = reinterpret_cast<float*>(base + L.e2f);
     c.sp = reinterpret_cast<double*>(base + L.sp);
+    c.lam = reinterpret_cast<float*>(base + L.lam);
     return c;
 }
 
@@ -109,19 +114,45 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
     }
     __syncthreads();
     const int K = s_K;
-    const int k = lane * NW + warp;  // spread consecutive eigenvalues over the warps
+    const double lo = s_lo, hi = s_hi, pivmin = s_pivmin;
+    const double nrm = fmax(fabs(lo), fabs(hi));
+    if constexpr (sizeof(T) == 4) {
+        // FP32 multisection: G threads per eigenvalue evaluate G interior
+        // points per round, narrowing the bracket (G+1)-fold.
+        int G = 1;
+        while (G < 8 && 2 * G * K <= (int)blockDim.x) G *= 2;
+        const int k = tid / G, j = tid % G;
+        const float lof = (float)lo * (lo < 0 ? 1.0000002f : 0.9999998f) - 1e-30f;
+        const float hif = (float)hi * (hi > 0 ? 1.0000002f : 0.9999998f) + 1e-30f;
+        const float atolf = 2.0f * FLT_EPSILON * (float)nrm;
+        const int rounds = (int)ceilf(log2f((hif - lof) / atolf) / log2f((float)(G + 1))) + 1;
+        if ((warp * 32) / G < K) {
+            float a = lof, b = hif;
+            const unsigned gmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+            const int gshift = (lane / G) * G;
+            for (int r = 0; r < rounds; ++r) {
+                const float h = (b - a) / (float)(G + 1);
+                bool flag = false;
+                if (k < K) flag = sturm_count_f32(n, c.df, c.e2f, a + (float)(j + 1) * h, s_pivminf) <= k;
+                const unsigned bal = __ballot_sync(FULL_MASK, flag);
+                const int J = __popc((bal >> gshift) & gmask);
+                const float na = J > 0 ? a + (float)J * h : a;
+                const float nb = J < G ? a + (float)(J + 1) * h : b;
+                a = na; b = nb;
+            }
+            if (k < K && j == 0) { c.lam[2 * k] = a; c.lam[2 * k + 1] = b; }
+        }
+        __syncthreads();
+    }
     double sp = 0.0, fe = 0.0;
+    const int k = tid;  // dense warps for the FP64 work
     if (k < K) {
-        const double lo = s_lo, hi = s_hi, pivmin = s_pivmin;
-        const double nrm = fmax(fabs(lo), fabs(hi));
         double lam;
         if constexpr (sizeof(T) == 8) {
-            lam = bisect_f64(n, c.d, c.e2, k, lo, hi, pivmin, 2.0 * DBL_EPSILON * nrm);
+            lam = eig_f64(n, c.d, c.e2, k, lo, hi, pivmin, nrm);
         } else {
-            const float lof = (float)lo * (lo < 0 ? 1.0000002f : 0.9999998f) - 1e-30f;
-            const float hif = (float)hi * (hi > 0 ? 1.0000002f : 0.9999998f) + 1e-30f;
-            lam = bisect_f32_newton_f64(n, c.df, c.e2f, c.d, c.e2, k, lof, hif, s_pivminf,
-                                        2.0f * FLT_EPSILON * (float)nrm, pivmin);
+            lam = newton_polish_f64(n, c.d, c.e2, c.lam[2 * k], c.lam[2 * k + 1], 2.0f * FLT_EPSILON * (float)nrm,
+                                    pivmin);
         }
         const double x = -(lam - mu) / temp;
         sp = softplus(x);
@@ -162,7 +193,7 @@ __global__ void __launch_bounds__(CTA) k_build(Model m, const double* __restrict
 
 // All eigenvalues of m packed matrices from global memory.
 template <typename T, int NT>
-__global__ void __launch_bounds__(CTA) k_eigvals(const cplx_t<T>* __restrict__ H, const int64_t* __restrict__ offsets,
+__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_eigvals(const cplx_t<T>* __restrict__ H, const int64_t* __restrict__ offsets,
                                                  const int32_t* __restrict__ nin, int count, int nA,
                                                  double* __restrict__ eig, const int64_t* __restrict__ eoff) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -220,7 +251,7 @@ struct StageArgs {
 };
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(CTA) k_stage(StageArgs a) {
+__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_new[3];
     __shared__ int s_last;
