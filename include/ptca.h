@@ -205,6 +205,34 @@ ptca_status ptca_sweep_record(ptca_ctx* ctx, int32_t* site, double* F_old, doubl
 ptca_status ptca_observables(ptca_ctx* ctx, ptca_obs* out, void* stream);
 
 /* ----------------------------------------------------------------------- */
+/* Sweep without device allocation                                           */
+/* ----------------------------------------------------------------------- */
+
+/* Same sweep as ptca_sweep (one sweep, same kernels, same results), for
+ * callers that cannot allocate device memory: hosts whose own pool owns the
+ * device memory or that forbid loaded libraries to allocate, and loops that
+ * cannot afford cudaMalloc/cudaFree (cudaFree synchronises the device).  The
+ * paper has no counterpart; this is a property of the library.
+ *   sites        device int32[N]: the flattened stage list of ptca_schedule
+ *                for the same lattice and params
+ *   stage_start  host int32[n_stages+1]: its stage offsets (checked)
+ *   spins        device double[N*3]: the configuration, updated in place
+ *   sweep_index  counter of the random stream (the sweep number, >= 0)
+ *   F_out        device double[2N] or NULL: F_old of every visit, then F_new
+ *   accepted_out device uint8[N] or NULL: decisions, flattened stage order
+ * No context and no device allocation: working memory is one array of about
+ * 2 MB that the library defines in device global memory and that every GPU
+ * loading the library holds until the process exits.  Limit: N <= 16384
+ * sites (larger lattices return PTCA_ERR_INVALID).  All calls share that
+ * array and its contents persist between calls; calls that overlap on the GPU
+ * (other streams or threads on the same device) race and must be serialised.
+ * The first call on a device looks up the array's address with that device
+ * current; make it before any stream capture.  Stream-ordered, asynchronous. */
+ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptca_params* params, const int32_t* sites,
+                               const int32_t* stage_start, int32_t n_stages, double* spins, int64_t sweep_index,
+                               double* F_out, uint8_t* accepted_out, void* stream);
+
+/* ----------------------------------------------------------------------- */
 /* Host-only helpers (no GPU needed)                                         */
 /* ----------------------------------------------------------------------- */
 

@@ -200,6 +200,9 @@ static void free_ctx(ptca_ctx* c) {
     delete c;
 }
 
+// Failure reporting for the other translation units of the library.
+ptca_status ptca_internal_fail(ptca_status s, const char* msg) { return fail(s, msg); }
+
 extern "C" {
 
 int32_t ptca_version(void) { return PTCA_VERSION_MAJOR * 100 + PTCA_VERSION_MINOR; }

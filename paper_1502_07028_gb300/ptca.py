@@ -26,6 +26,7 @@ EXPORTED = [
     "ptca_init", "ptca_destroy", "ptca_set_T", "ptca_set_mu", "ptca_get_spins", "ptca_set_spins",
     "ptca_dims", "ptca_build_clusters", "ptca_cluster_eigvals", "ptca_free_energy", "ptca_sweep",
     "ptca_sweep_record", "ptca_observables", "ptca_schedule", "ptca_last_error", "ptca_version",
+    "ptca_sweep_noalloc",
 ]
 
 
@@ -97,6 +98,7 @@ def lib():
             "ptca_schedule": ([P(Lattice), P(Params), vp, vp, P(i32)], i32),
             "ptca_last_error": ([], ctypes.c_char_p),
             "ptca_version": ([], i32),
+            "ptca_sweep_noalloc": ([P(Lattice), P(Params), vp, vp, i32, vp, i64, vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -241,6 +243,19 @@ def ptca_sweep(h, n_sweeps: int, stats: bool = True, stream=None):
 def ptca_sweep_record(h, site=None, F_old=None, F_new=None, lnu=None, accepted=None, stream=None) -> None:
     _check(lib().ptca_sweep_record(h, _ptr(site), _ptr(F_old), _ptr(F_new), _ptr(lnu), _ptr(accepted),
                                    _stream(stream)))
+
+
+def ptca_sweep_noalloc(cfg: Config, sites, stage_start, spins, sweep_index: int, F_out=None, accepted_out=None,
+                       stream=None) -> None:
+    """One sweep without a context or device allocation (see include/ptca.h).
+
+    sites: device int32 tensor (flattened schedule); stage_start: host int32
+    numpy array; spins: device float64 tensor (N, 3), updated in place."""
+    import numpy as np
+    ss = np.ascontiguousarray(stage_start, dtype=np.int32)
+    lat, par = cfg.lattice(), cfg.params()
+    _check(lib().ptca_sweep_noalloc(ctypes.byref(lat), ctypes.byref(par), _ptr(sites), _ptr(ss), ss.size - 1,
+                                    _ptr(spins), sweep_index, _ptr(F_out), _ptr(accepted_out), _stream(stream)))
 
 
 def ptca_observables(h, stream=None) -> Obs:
