@@ -60,6 +60,7 @@ typedef enum {
 enum { PTCA_SCHEDULE_TILED = 0, PTCA_SCHEDULE_BLOCK = 1 };
 enum { PTCA_FP64 = 0, PTCA_MIXED = 1 };
 enum { PTCA_PROPOSAL_SPHERE = 0, PTCA_PROPOSAL_CONE = 1 };
+enum { PTCA_PIPELINE_STAGES = 0, PTCA_PIPELINE_PERSISTENT = 1, PTCA_PIPELINE_GRAPH = 2 };
 
 /* Square lattice.  Ly == 1 is a one-dimensional chain (Sec. III.a, Fig. 3). */
 typedef struct {
@@ -193,6 +194,20 @@ ptca_status ptca_free_energy(ptca_ctx* ctx, const double* eig, const int64_t* ei
  * fills *stats_out. */
 ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_out, void* stream);
 
+/* How ptca_sweep launches the stages of a sweep (the paper's MPI gather and
+ * broadcast between blocks, Sec. III.b, become device-wide barriers):
+ *   PTCA_PIPELINE_STAGES      one kernel launch per stage;
+ *   PTCA_PIPELINE_PERSISTENT  one persistent launch for all stages of all
+ *                             requested sweeps: co-resident CTAs take
+ *                             (site, old/new) items of a stage from an atomic
+ *                             queue, largest window first, and meet at a
+ *                             device-wide barrier between stages;
+ *   PTCA_PIPELINE_GRAPH       (default) the persistent launch captured once in
+ *                             a CUDA graph per sweep count and replayed.
+ * Every barrier wait is bounded by barrier_timeout_s (default 30 s): past it
+ * the kernel stops and ptca_sweep (with stats) returns PTCA_ERR_TIMEOUT. */
+ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeout_s);
+
 /* Per-visit record of the last sweep, in flattened stage order (length N):
  * update site, F_old, F_new, ln u and the decision (1 accepted).  Device
  * pointers; any of them may be NULL.  Stream-ordered. */
@@ -242,6 +257,13 @@ ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptca_params* p
  * Same validation as ptca_init. */
 ptca_status ptca_schedule(const ptca_lattice* lattice, const ptca_params* params,
                           int32_t* stage_start, int32_t* sites, int32_t* n_stages);
+
+/* Self-test of the bounded device-wide barrier: `blocks` CTAs wait at a
+ * barrier sized for blocks + 1 participants, so the wait can only end by its
+ * time limit.  Returns PTCA_ERR_TIMEOUT when every wait gave up and reported
+ * it (the expected outcome), PTCA_OK if the barrier completed, PTCA_ERR_CUDA
+ * on a CUDA error.  The GPU stays usable.  Synchronous; allocates 16 bytes. */
+ptca_status ptca_selftest_barrier_timeout(int32_t blocks, double timeout_s, void* stream);
 
 /* Description of the last failure on this thread (never NULL). */
 const char* ptca_last_error(void);

@@ -189,12 +189,33 @@ struct ptca_ctx {
     double* d_obs = nullptr;
     int64_t sweeps = 0;
     int64_t total_accepted = 0;
+    // persistent pipeline
+    int32_t* d_stage_start = nullptr;
+    int32_t* d_perm = nullptr;
+    unsigned int* d_queue = nullptr;
+    unsigned int* d_bar = nullptr;
+    unsigned long long* d_sweep_ctr = nullptr;
+    int pipeline = PTCA_PIPELINE_GRAPH;
+    unsigned long long timeout_ns = 30ull * 1000000000ull;
+    int grid = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_sweeps = -1;
+    cudaStream_t graph_stream = nullptr;
+    bool graph_failed = false;
 };
 
+static void drop_graph(ptca_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_sweeps = -1;
+}
+
 static void free_ctx(ptca_ctx* c) {
+    drop_graph(c);
     void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
-                    c->d_rec_n, c->d_counters, c->d_err, c->d_obs};
+                    c->d_rec_n, c->d_counters, c->d_err, c->d_obs, c->d_stage_start, c->d_perm, c->d_queue,
+                    c->d_bar, c->d_sweep_ctr};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete c;
@@ -280,11 +301,46 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
     if (ce == cudaSuccess) ce = dalloc(&c->d_rec_fill, N);
     if (ce == cudaSuccess) ce = dalloc(&c->d_rec_n, N);
     if (ce == cudaSuccess) ce = dalloc(&c->d_counters, 4);
-    if (ce == cudaSuccess) ce = dalloc(&c->d_err, 1);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_err, 2);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_stage_start, c->nstages + 1);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_perm, N);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_queue, 2);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_bar, 2);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_sweep_ctr, 1);
     if (ce == cudaSuccess) ce = dalloc(&c->d_obs, 8);
     if (ce == cudaSuccess) ce = cudaMemcpy(c->d_sites, si.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemset(c->d_ticket, 0, c->max_stage * sizeof(int32_t));
-    if (ce == cudaSuccess) ce = cudaMemset(c->d_err, 0, sizeof(int32_t));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_err, 0, 2 * sizeof(int32_t));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_queue, 0, 2 * sizeof(unsigned int));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned int));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_sweep_ctr, 0, sizeof(unsigned long long));
+    if (ce == cudaSuccess) {
+        // Work order inside each stage: largest window first (ragged windows
+        // of open lattices), stable, so periodic lattices keep schedule order.
+        std::vector<int32_t> perm(N);
+        for (int stg = 0; stg < c->nstages; ++stg) {
+            const int a0 = st[stg], a1 = st[stg + 1];
+            std::vector<std::pair<int, int>> key;
+            for (int k = a0; k < a1; ++k) {
+                const int b = si[k];
+                int x0, ex, y0, ey;
+                window_axis(p.Lx, p.periodic, p.Lc, p.ox, b % p.Lx, x0, ex);
+                window_axis(p.Ly, p.periodic, p.Lc, p.oy, b / p.Lx, y0, ey);
+                key.push_back({-(ex * ey), k - a0});
+            }
+            std::stable_sort(key.begin(), key.end(),
+                             [](const std::pair<int, int>& u, const std::pair<int, int>& v) { return u.first < v.first; });
+            for (int k = a0; k < a1; ++k) perm[k] = key[k - a0].second;
+        }
+        ce = cudaMemcpy(c->d_perm, perm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->d_stage_start, st.data(), (c->nstages + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+        int sms = 0, per = ptca::persistent_blocks_per_sm(c->prec, c->nA);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        c->grid = sms * per;
+        if (c->grid <= 0) c->pipeline = PTCA_PIPELINE_STAGES;
+    }
     if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_acc, 0, N);
     if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_Facc, 0, N * sizeof(double));
     if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_fill, 0, N * sizeof(double));
@@ -312,6 +368,7 @@ ptca_status ptca_set_T(ptca_ctx* ctx, double T) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
     if (!(T > 0) || !std::isfinite(T)) return fail(PTCA_ERR_INVALID, "T must be finite and > 0");
     ctx->p.T = T;
+    drop_graph(ctx);
     return PTCA_OK;
 }
 
@@ -319,6 +376,7 @@ ptca_status ptca_set_mu(ptca_ctx* ctx, double mu) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
     if (!std::isfinite(mu)) return fail(PTCA_ERR_INVALID, "mu must be finite");
     ctx->p.mu = mu;
+    drop_graph(ctx);
     return PTCA_OK;
 }
 
@@ -382,17 +440,7 @@ ptca_status ptca_free_energy(ptca_ctx* ctx, const double* eig, const int64_t* ei
     return PTCA_OK;
 }
 
-ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_out, void* stream) {
-    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
-    if (n_sweeps < 0) return fail(PTCA_ERR_INVALID, "n_sweeps < 0");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (stats_out) {
-        PTCA_CUDA(cudaEventCreate(&ev0));
-        PTCA_CUDA(cudaEventCreate(&ev1));
-        PTCA_CUDA(cudaEventRecord(ev0, st));
-    }
-    PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
+static StageArgs base_args(ptca_ctx* ctx) {
     StageArgs a;
     std::memset(&a, 0, sizeof a);
     a.m = to_model(ctx->p);
@@ -410,40 +458,121 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
     a.rec_n = ctx->d_rec_n;
     a.counters = ctx->d_counters;
     a.err = ctx->d_err;
+    return a;
+}
+
+// One launch per stage (Sec. III.a stage = one kernel).
+static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
+    StageArgs a = base_args(ctx);
     int64_t g = 0;
     int prev_s = -1;
-    for (int sw = 0; sw < n_sweeps; ++sw) {
+    cudaError_t e = cudaSuccess;
+    for (int sw = 0; sw < n_sweeps && e == cudaSuccess; ++sw) {
         a.sweep = (uint64_t)(ctx->sweeps + sw);
-        for (int s = 0; s < ctx->nstages; ++s, ++g) {
+        for (int s = 0; s < ctx->nstages && e == cudaSuccess; ++s, ++g) {
             a.S_in = ctx->d_S[g & 1];
             a.S_out = ctx->d_S[(g + 1) & 1];
             a.sites = ctx->d_sites + ctx->h_start[s];
             a.count = ctx->h_start[s + 1] - ctx->h_start[s];
             a.rec_base = ctx->h_start[s];
-            if (prev_s >= 0) {
-                a.prev_sites = ctx->d_sites + ctx->h_start[prev_s];
-                a.prev_count = ctx->h_start[prev_s + 1] - ctx->h_start[prev_s];
-            } else {
-                a.prev_sites = nullptr;
-                a.prev_count = 0;
-            }
-            PTCA_CUDA(ptca::launch_stage(ctx->prec, a, st));
+            a.prev_sites = prev_s >= 0 ? ctx->d_sites + ctx->h_start[prev_s] : nullptr;
+            a.prev_count = prev_s >= 0 ? ctx->h_start[prev_s + 1] - ctx->h_start[prev_s] : 0;
+            e = ptca::launch_stage(ctx->prec, a, st);
             prev_s = s;
         }
     }
-    if (g > 0) {
-        // Bring the other buffer up to date so both hold the configuration.
-        const int last = prev_s;
-        PTCA_CUDA(ptca::launch_copy_sites(ctx->d_S[g & 1], ctx->d_S[(g + 1) & 1], ctx->d_sites + ctx->h_start[last],
-                                          ctx->h_start[last + 1] - ctx->h_start[last], st));
+    if (e == cudaSuccess && g > 0)
+        e = ptca::launch_copy_sites(ctx->d_S[g & 1], ctx->d_S[(g + 1) & 1], ctx->d_sites + ctx->h_start[prev_s],
+                                    ctx->h_start[prev_s + 1] - ctx->h_start[prev_s], st);
+    if (e == cudaSuccess) e = ptca::launch_set_u64(ctx->d_sweep_ctr, (unsigned long long)(ctx->sweeps + n_sweeps), st);
+    return e;
+}
+
+// Everything one persistent sweep launch needs, as stream work (capturable).
+static cudaError_t enqueue_persistent(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
+    ptca::PersistArgs p;
+    std::memset(&p, 0, sizeof p);
+    p.st = base_args(ctx);
+    p.st.perm = ctx->d_perm;
+    p.S0 = ctx->d_S[0];
+    p.S1 = ctx->d_S[1];
+    p.sites = ctx->d_sites;
+    p.stage_start = ctx->d_stage_start;
+    p.nstages = ctx->nstages;
+    p.n_sweeps = n_sweeps;
+    p.sweep_ctr = ctx->d_sweep_ctr;
+    p.queue = ctx->d_queue;
+    p.bar = ctx->d_bar;
+    p.timeout_ns = ctx->timeout_ns;
+    cudaError_t e = cudaMemsetAsync(ctx->d_queue, 0, 2 * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = ptca::launch_persistent(ctx->prec, p, ctx->grid, st);
+    return e;
+}
+
+static cudaError_t sweep_graph(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
+    if (ctx->graph && ctx->graph_sweeps == n_sweeps) return cudaGraphLaunch(ctx->graph, st);
+    drop_graph(ctx);
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue_persistent(ctx, n_sweeps, cap);
+        e = cudaStreamEndCapture(cap, &g);
+        if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->graph = nullptr;
+        ctx->graph_failed = true;  // fall back to direct persistent launches
+        return enqueue_persistent(ctx, n_sweeps, st);
+    }
+    ctx->graph_sweeps = n_sweeps;
+    return cudaGraphLaunch(ctx->graph, st);
+}
+
+ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeout_s) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (mode < PTCA_PIPELINE_STAGES || mode > PTCA_PIPELINE_GRAPH) return fail(PTCA_ERR_INVALID, "unknown pipeline");
+    if (mode != PTCA_PIPELINE_STAGES && ctx->grid <= 0)
+        return fail(PTCA_ERR_UNSUPPORTED, "persistent kernel does not fit on this device");
+    if (!(barrier_timeout_s > 0) || barrier_timeout_s > 3600) return fail(PTCA_ERR_INVALID, "timeout out of range");
+    ctx->pipeline = mode;
+    ctx->timeout_ns = (unsigned long long)(barrier_timeout_s * 1e9);
+    drop_graph(ctx);
+    return PTCA_OK;
+}
+
+ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_out, void* stream) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (n_sweeps < 0) return fail(PTCA_ERR_INVALID, "n_sweeps < 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (stats_out) {
+        PTCA_CUDA(cudaEventCreate(&ev0));
+        PTCA_CUDA(cudaEventCreate(&ev1));
+        PTCA_CUDA(cudaEventRecord(ev0, st));
+    }
+    PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
+    if (n_sweeps > 0) {
+        cudaError_t e;
+        if (ctx->pipeline == PTCA_PIPELINE_STAGES) e = sweep_stages(ctx, n_sweeps, st);
+        else if (ctx->pipeline == PTCA_PIPELINE_PERSISTENT || ctx->graph_failed) e = enqueue_persistent(ctx, n_sweeps, st);
+        else e = sweep_graph(ctx, n_sweeps, st);
+        if (e != cudaSuccess) return cuda_fail(e, "ptca_sweep");
     }
     ctx->sweeps += n_sweeps;
     if (stats_out) {
         unsigned long long cnt[4];
-        int32_t err = 0;
+        int32_t err[2] = {0, 0};
         PTCA_CUDA(cudaEventRecord(ev1, st));
         PTCA_CUDA(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, st));
-        PTCA_CUDA(cudaMemcpyAsync(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost, st));
+        PTCA_CUDA(cudaMemcpyAsync(err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost, st));
         PTCA_CUDA(cudaStreamSynchronize(st));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
@@ -452,11 +581,36 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
         stats_out->attempts = (int64_t)n_sweeps * ctx->N;
         stats_out->accepted = (int64_t)cnt[0];
         stats_out->eigensolves = (int64_t)cnt[1];
-        stats_out->resolved = 0;
+        stats_out->resolved = (int64_t)cnt[2];
         stats_out->sweeps = ctx->sweeps;
         stats_out->seconds = ms * 1e-3;
-        if (err) return fail(PTCA_ERR_NUMERIC, "non-finite free-energy difference in a sweep");
+        if (err[1]) {
+            cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(int32_t), st);
+            return fail(PTCA_ERR_TIMEOUT, "a device-wide stage barrier timed out; the sweep is incomplete");
+        }
+        if (err[0]) return fail(PTCA_ERR_NUMERIC, "non-finite free-energy difference in a sweep");
     }
+    return PTCA_OK;
+}
+
+ptca_status ptca_selftest_barrier_timeout(int32_t blocks, double timeout_s, void* stream) {
+    if (blocks < 1 || blocks > 1024 || !(timeout_s > 0) || timeout_s > 10)
+        return fail(PTCA_ERR_INVALID, "blocks in [1,1024], timeout in (0,10] s");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int* bar = nullptr;
+    int32_t* err = nullptr;
+    PTCA_CUDA(cudaMalloc(&bar, 2 * sizeof(unsigned int)));
+    cudaError_t e = cudaMalloc(&err, 2 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), st);
+    if (e == cudaSuccess) e = ptca::launch_barrier_selftest(blocks, bar, err, (unsigned long long)(timeout_s * 1e9), st);
+    int32_t h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, err, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(bar);
+    if (err) cudaFree(err);
+    if (e != cudaSuccess) return cuda_fail(e, "ptca_selftest_barrier_timeout");
+    if (h[1] == 4) return fail(PTCA_ERR_TIMEOUT, "barrier wait timed out as expected");
     return PTCA_OK;
 }
 

@@ -229,6 +229,7 @@ struct StageArgs {
     const double* S_in;
     double* S_out;
     const int32_t* sites;
+    const int32_t* perm;           // work index -> index in the stage's site list (null: identity)
     int32_t count;
     const int32_t* prev_sites;
     int32_t prev_count;
@@ -250,21 +251,15 @@ struct StageArgs {
     int32_t* err;
 };
 
+// One matrix of one update site of a stage: c indexes the stage's site list,
+// var 0/1 selects H_old/H_new.  The second of the pair to finish applies
+// Metropolis.  Called by all threads of the CTA; s_new and s_last are shared.
 template <typename T, int NT>
-__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_new[3];
-    __shared__ int s_last;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.prev_count; k += gridDim.x * blockDim.x) {
-        const int s = a.prev_sites[k];
-        a.S_out[3 * s] = a.S_in[3 * s];
-        a.S_out[3 * s + 1] = a.S_in[3 * s + 1];
-        a.S_out[3 * s + 2] = a.S_in[3 * s + 2];
-    }
-    const int c = blockIdx.x >> 1, var = blockIdx.x & 1;
-    if (c >= a.count) return;
+__device__ __forceinline__ void stage_item(const StageArgs& a, int c, int var, unsigned char* smem, double* s_new,
+                                           int* s_last) {
     const SmemLayout L = smem_layout(a.nA, 32 * NT, sizeof(cplx_t<T>));
     Carve<T> cv = carve<T>(smem, L);
+    c = a.perm ? a.perm[c] : c;
     const int site = a.sites[c];
     const Window w = make_window(a.m, site);
     const int n = 2 * w.ex * w.ey;
@@ -283,10 +278,10 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArg
         a.fillbuf[2 * c + var] = sfe;
         __threadfence();
         const int old = atomicAdd(&a.ticket[c], 1);
-        s_last = (old == 1);
+        *s_last = (old == 1);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!*s_last || threadIdx.x != 0) return;
     __threadfence();
     a.ticket[c] = 0;
     const double Fo = __ldcg(&a.Fbuf[2 * c]), Fn = __ldcg(&a.Fbuf[2 * c + 1]);
@@ -316,5 +311,147 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArg
     if (acc) atomicAdd(&a.counters[0], 1ull);
     atomicAdd(&a.counters[1], 2ull);
 }
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    __shared__ int s_last;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.prev_count; k += gridDim.x * blockDim.x) {
+        const int s = a.prev_sites[k];
+        a.S_out[3 * s] = a.S_in[3 * s];
+        a.S_out[3 * s + 1] = a.S_in[3 * s + 1];
+        a.S_out[3 * s + 2] = a.S_in[3 * s + 2];
+    }
+    const int c = blockIdx.x >> 1, var = blockIdx.x & 1;
+    if (c >= a.count) return;
+    stage_item<T, NT>(a, c, var, smem, s_new, &s_last);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent sweep: one launch runs every stage of n_sweeps sweeps.  Each CTA
+// takes (site, old/new) items of the current stage from an atomic work queue
+// (sites ordered largest window first), then all CTAs meet at a device-wide
+// barrier before the next stage reads the spins the stage wrote.  Every wait
+// at the barrier is bounded: past the time limit the CTA records
+// PTCA_ERR_TIMEOUT in err[1] and returns, so a missing participant cannot
+// hang the GPU.
+// ---------------------------------------------------------------------------
+struct PersistArgs {
+    StageArgs st;                 // model, scratch, records (per-stage fields set in the kernel)
+    double* S0;
+    double* S1;
+    const int32_t* sites;         // flattened schedule, each stage in work order
+    const int32_t* stage_start;   // nstages + 1
+    int32_t nstages;
+    int32_t n_sweeps;
+    unsigned long long* sweep_ctr;// RNG sweep index of the next sweep (advanced by the kernel)
+    unsigned int* queue;          // [2] work-queue counters, alternating by stage
+    unsigned int* bar;            // [0] arrivals, [1] generation
+    unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Device-wide barrier over gridDim.x CTAs (all co-resident).  Returns false
+// (and sets err[1] = PTCA_ERR_TIMEOUT) if the wait exceeds timeout_ns.  The
+// last CTA to arrive also clears `clear_after` (a queue counter nobody uses
+// until two stages later).
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int participants, unsigned long long timeout_ns,
+                                             int32_t* err, unsigned int* clear_after) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = bar + 1;
+        const unsigned int my_gen = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (arrived == participants - 1) {
+            if (clear_after) *clear_after = 0u;
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned long long spins = 0;
+            while (*gen == my_gen) {
+                if (((++spins) & 63u) == 0 && (global_ns() - t0 > timeout_ns || spins > (1ull << 34))) {
+                    atomicExch(err + 1, 4);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(128);
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_sweep_persistent(PersistArgs p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    __shared__ int s_last, s_item;
+    StageArgs a = p.st;
+    const unsigned long long sweep0 = *p.sweep_ctr;
+    const int G = p.nstages * p.n_sweeps;
+    for (int g = 0; g < G; ++g) {
+        const int s = g % p.nstages;
+        const int sp = (g > 0) ? (g - 1) % p.nstages : -1;
+        a.sweep = sweep0 + (unsigned long long)(g / p.nstages);
+        a.S_in = (g & 1) ? p.S1 : p.S0;
+        a.S_out = (g & 1) ? p.S0 : p.S1;
+        a.sites = p.sites + p.stage_start[s];
+        a.perm = p.st.perm ? p.st.perm + p.stage_start[s] : nullptr;
+        a.count = p.stage_start[s + 1] - p.stage_start[s];
+        a.rec_base = p.stage_start[s];
+        if (sp >= 0) {
+            const int32_t* prev = p.sites + p.stage_start[sp];
+            const int pc = p.stage_start[sp + 1] - p.stage_start[sp];
+            for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < pc; k += gridDim.x * blockDim.x) {
+                const int q = prev[k];
+                a.S_out[3 * q] = a.S_in[3 * q];
+                a.S_out[3 * q + 1] = a.S_in[3 * q + 1];
+                a.S_out[3 * q + 2] = a.S_in[3 * q + 2];
+            }
+        }
+        unsigned int* qc = p.queue + (g & 1);
+        for (;;) {
+            if (threadIdx.x == 0) s_item = (int)atomicAdd(qc, 1u);
+            __syncthreads();
+            const int item = s_item;
+            __syncthreads();
+            if (item >= 2 * a.count) break;
+            stage_item<T, NT>(a, item >> 1, item & 1, smem, s_new, &s_last);
+            __syncthreads();
+        }
+        if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, a.err, qc)) return;
+    }
+    if (G > 0) {
+        // Bring the other buffer up to date with the last stage.
+        const int sl = (G - 1) % p.nstages;
+        const double* src = (G & 1) ? p.S1 : p.S0;
+        double* dst = (G & 1) ? p.S0 : p.S1;
+        const int32_t* last = p.sites + p.stage_start[sl];
+        const int lc = p.stage_start[sl + 1] - p.stage_start[sl];
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < lc; k += gridDim.x * blockDim.x) {
+            const int q = last[k];
+            dst[3 * q] = src[3 * q]; dst[3 * q + 1] = src[3 * q + 1]; dst[3 * q + 2] = src[3 * q + 2];
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) *p.sweep_ctr = sweep0 + (unsigned long long)p.n_sweeps;
+    }
+}
+
+// Barrier self-test: `blocks` CTAs wait for `blocks + 1` participants, which
+// never arrive; every CTA must give up after timeout_ns and report it.
+__global__ void k_barrier_selftest(unsigned int* bar, int32_t* err, unsigned long long timeout_ns);
 
 }  // namespace ptca

@@ -22,6 +22,10 @@ cudaError_t launch_eigvals_f64(int, const void*, const int64_t*, const int32_t*,
                                cudaStream_t);
 cudaError_t launch_stage_f32(const StageArgs&, cudaStream_t);
 cudaError_t launch_stage_f64(const StageArgs&, cudaStream_t);
+cudaError_t launch_persistent_f32(const PersistArgs&, int, cudaStream_t);
+cudaError_t launch_persistent_f64(const PersistArgs&, int, cudaStream_t);
+int persistent_blocks_per_sm_f32(int);
+int persistent_blocks_per_sm_f64(int);
 
 size_t cluster_smem_bytes(int prec, int nA) { return prec ? cluster_smem_bytes_f32(nA) : cluster_smem_bytes_f64(nA); }
 int cluster_max_order(int prec) { return prec ? cluster_max_order_f32() : cluster_max_order_f64(); }
@@ -43,6 +47,29 @@ cudaError_t launch_eigvals(int prec, int nA, const void* H, const int64_t* offse
 }
 cudaError_t launch_stage(int prec, const StageArgs& a, cudaStream_t st) {
     return prec ? launch_stage_f32(a, st) : launch_stage_f64(a, st);
+}
+cudaError_t launch_persistent(int prec, const PersistArgs& p, int grid, cudaStream_t st) {
+    return prec ? launch_persistent_f32(p, grid, st) : launch_persistent_f64(p, grid, st);
+}
+int persistent_blocks_per_sm(int prec, int nA) {
+    return prec ? persistent_blocks_per_sm_f32(nA) : persistent_blocks_per_sm_f64(nA);
+}
+
+__global__ void k_barrier_selftest(unsigned int* bar, int32_t* err, unsigned long long timeout_ns) {
+    grid_barrier(bar, gridDim.x + 1, timeout_ns, err, nullptr);
+}
+
+cudaError_t launch_barrier_selftest(int blocks, unsigned int* bar, int32_t* err, unsigned long long timeout_ns,
+                                    cudaStream_t st) {
+    k_barrier_selftest<<<blocks, 32, 0, st>>>(bar, err, timeout_ns);
+    return cudaGetLastError();
+}
+
+__global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) {
+    k_set_u64<<<1, 1, 0, st>>>(p, v);
+    return cudaGetLastError();
 }
 
 // Initial spins: uniform on the sphere from the counter generator.

@@ -9,6 +9,7 @@ namespace ptca {
 
 struct Model;
 struct StageArgs;
+struct PersistArgs;
 
 // Dynamic shared memory of one cluster CTA for matrices up to order nA
 // (0 when no kernel instantiation covers nA).  prec: 0 FP64, 1 FP32.
@@ -28,6 +29,13 @@ cudaError_t launch_eigvals(int prec, int nA, const void* H, const int64_t* offse
 cudaError_t launch_free_energy(const double* eig, const int64_t* eoff, const int32_t* n, int count, double mu,
                                double T, double* F, cudaStream_t st);
 cudaError_t launch_stage(int prec, const StageArgs& a, cudaStream_t st);
+// Persistent sweep kernel: grid CTAs (all co-resident; cooperative launch).
+cudaError_t launch_persistent(int prec, const PersistArgs& p, int grid, cudaStream_t st);
+// CTAs of the persistent kernel that fit on one SM for matrices up to nA.
+int persistent_blocks_per_sm(int prec, int nA);
+cudaError_t launch_barrier_selftest(int blocks, unsigned int* bar, int32_t* err, unsigned long long timeout_ns,
+                                    cudaStream_t st);
+cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 cudaError_t launch_observables(const double* S, int Lx, int Ly, const double* rec_Facc, const double* rec_fill,
                                const uint8_t* rec_acc, const int32_t* rec_n, int N, double* out, cudaStream_t st);
 

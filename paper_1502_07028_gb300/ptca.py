@@ -19,6 +19,7 @@ PTCA_OK = 0
 STATUS = {0: "PTCA_OK", 1: "PTCA_ERR_INVALID", 2: "PTCA_ERR_CUDA", 3: "PTCA_ERR_OOM",
           4: "PTCA_ERR_TIMEOUT", 5: "PTCA_ERR_NUMERIC", 6: "PTCA_ERR_UNSUPPORTED"}
 SCHEDULE_TILED, SCHEDULE_BLOCK = 0, 1
+PIPELINE_STAGES, PIPELINE_PERSISTENT, PIPELINE_GRAPH = 0, 1, 2
 FP64, MIXED = 0, 1
 PROPOSAL_SPHERE, PROPOSAL_CONE = 0, 1
 
@@ -26,7 +27,7 @@ EXPORTED = [
     "ptca_init", "ptca_destroy", "ptca_set_T", "ptca_set_mu", "ptca_get_spins", "ptca_set_spins",
     "ptca_dims", "ptca_build_clusters", "ptca_cluster_eigvals", "ptca_free_energy", "ptca_sweep",
     "ptca_sweep_record", "ptca_observables", "ptca_schedule", "ptca_last_error", "ptca_version",
-    "ptca_sweep_noalloc",
+    "ptca_sweep_noalloc", "ptca_set_pipeline", "ptca_selftest_barrier_timeout",
 ]
 
 
@@ -99,6 +100,8 @@ def lib():
             "ptca_last_error": ([], ctypes.c_char_p),
             "ptca_version": ([], i32),
             "ptca_sweep_noalloc": ([P(Lattice), P(Params), vp, vp, i32, vp, i64, vp, vp, vp], i32),
+            "ptca_set_pipeline": ([vp, i32, dbl], i32),
+            "ptca_selftest_barrier_timeout": ([i32, dbl, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -256,6 +259,16 @@ def ptca_sweep_noalloc(cfg: Config, sites, stage_start, spins, sweep_index: int,
     lat, par = cfg.lattice(), cfg.params()
     _check(lib().ptca_sweep_noalloc(ctypes.byref(lat), ctypes.byref(par), _ptr(sites), _ptr(ss), ss.size - 1,
                                     _ptr(spins), sweep_index, _ptr(F_out), _ptr(accepted_out), _stream(stream)))
+
+
+def ptca_set_pipeline(h, mode: int, barrier_timeout_s: float = 30.0) -> None:
+    _check(lib().ptca_set_pipeline(h, mode, barrier_timeout_s))
+
+
+def ptca_selftest_barrier_timeout(blocks: int, timeout_s: float, stream=None) -> int:
+    """Returns the raw status (PTCA_ERR_TIMEOUT = 4 is the expected outcome)."""
+    st = lib().ptca_selftest_barrier_timeout(blocks, timeout_s, _stream(stream))
+    return st
 
 
 def ptca_observables(h, stream=None) -> Obs:
