@@ -208,6 +208,17 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
  * the kernel stops and ptca_sweep (with stats) returns PTCA_ERR_TIMEOUT. */
 ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeout_s);
 
+/* PTCA_MIXED decision guard.  The FP32 reduction leaves an error of about
+ * 1e-4 in dF at n = 128, so a Metropolis decision whose margin
+ * |ln u + dF/T| is below `margin` is deferred: both cluster matrices of that
+ * update site are solved again in FP64 (reduction and eigenvalues) and the
+ * decision is taken on the FP64 dF, before the next stage starts.  With a
+ * margin above T^-1 times the largest dF error this makes decisions identical
+ * to the FP64 path wherever the FP64 margin exceeds its own error.  Default
+ * 1e-2 in PTCA_MIXED; 0 disables it.  The count of re-solved updates is
+ * ptca_sweep_stats.resolved.  Rejected (PTCA_ERR_INVALID) for PTCA_FP64. */
+ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin);
+
 /* Per-visit record of the last sweep, in flattened stage order (length N):
  * update site, F_old, F_new, ln u and the decision (1 accepted).  Device
  * pointers; any of them may be NULL.  Stream-ordered. */

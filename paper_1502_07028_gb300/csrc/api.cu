@@ -202,6 +202,13 @@ struct ptca_ctx {
     int graph_sweeps = -1;
     cudaStream_t graph_stream = nullptr;
     bool graph_failed = false;
+    // PTCA_MIXED decision guard
+    double margin = 0.0;
+    int32_t* d_flag_list = nullptr;
+    unsigned int* d_flag_count = nullptr;
+    double2* d_gA = nullptr;
+    int64_t gA_stride = 0;
+    int resolve_grid = 0;
 };
 
 static void drop_graph(ptca_ctx* c) {
@@ -215,7 +222,7 @@ static void free_ctx(ptca_ctx* c) {
     void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
                     c->d_rec_n, c->d_counters, c->d_err, c->d_obs, c->d_stage_start, c->d_perm, c->d_queue,
-                    c->d_bar, c->d_sweep_ctr};
+                    c->d_bar, c->d_sweep_ctr, c->d_flag_list, c->d_flag_count, c->d_gA};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete c;
@@ -304,14 +311,17 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
     if (ce == cudaSuccess) ce = dalloc(&c->d_err, 2);
     if (ce == cudaSuccess) ce = dalloc(&c->d_stage_start, c->nstages + 1);
     if (ce == cudaSuccess) ce = dalloc(&c->d_perm, N);
-    if (ce == cudaSuccess) ce = dalloc(&c->d_queue, 2);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_queue, 3);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_flag_list, c->max_stage);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_flag_count, 1);
     if (ce == cudaSuccess) ce = dalloc(&c->d_bar, 2);
     if (ce == cudaSuccess) ce = dalloc(&c->d_sweep_ctr, 1);
     if (ce == cudaSuccess) ce = dalloc(&c->d_obs, 8);
     if (ce == cudaSuccess) ce = cudaMemcpy(c->d_sites, si.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemset(c->d_ticket, 0, c->max_stage * sizeof(int32_t));
     if (ce == cudaSuccess) ce = cudaMemset(c->d_err, 0, 2 * sizeof(int32_t));
-    if (ce == cudaSuccess) ce = cudaMemset(c->d_queue, 0, 2 * sizeof(unsigned int));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_queue, 0, 3 * sizeof(unsigned int));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_flag_count, 0, sizeof(unsigned int));
     if (ce == cudaSuccess) ce = cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned int));
     if (ce == cudaSuccess) ce = cudaMemset(c->d_sweep_ctr, 0, sizeof(unsigned long long));
     if (ce == cudaSuccess) {
@@ -340,6 +350,14 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         c->grid = sms * per;
         if (c->grid <= 0) c->pipeline = PTCA_PIPELINE_STAGES;
+        if (c->prec == 1) {
+            // Global slots for FP64 re-solves: one per CTA of either launch.
+            c->resolve_grid = sms;
+            const int slots = std::max(c->grid, c->resolve_grid);
+            c->gA_stride = (int64_t)c->nA * (c->nA + 1) / 2;
+            ce = dalloc(&c->d_gA, (size_t)slots * (size_t)c->gA_stride);
+            c->margin = 1e-2;
+        }
     }
     if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_acc, 0, N);
     if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_Facc, 0, N * sizeof(double));
@@ -458,6 +476,11 @@ static StageArgs base_args(ptca_ctx* ctx) {
     a.rec_n = ctx->d_rec_n;
     a.counters = ctx->d_counters;
     a.err = ctx->d_err;
+    a.margin = ctx->prec == 1 ? ctx->margin : 0.0;
+    a.flag_list = ctx->d_flag_list;
+    a.flag_count = ctx->d_flag_count;
+    a.gA = ctx->d_gA;
+    a.gA_stride = ctx->gA_stride;
     return a;
 }
 
@@ -478,6 +501,10 @@ static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st
             a.prev_sites = prev_s >= 0 ? ctx->d_sites + ctx->h_start[prev_s] : nullptr;
             a.prev_count = prev_s >= 0 ? ctx->h_start[prev_s + 1] - ctx->h_start[prev_s] : 0;
             e = ptca::launch_stage(ctx->prec, a, st);
+            if (e == cudaSuccess && a.margin > 0.0) {
+                e = ptca::launch_resolve(a, ctx->resolve_grid, st);
+                if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag_count, 0, sizeof(unsigned int), st);
+            }
             prev_s = s;
         }
     }
@@ -504,7 +531,8 @@ static cudaError_t enqueue_persistent(ptca_ctx* ctx, int32_t n_sweeps, cudaStrea
     p.queue = ctx->d_queue;
     p.bar = ctx->d_bar;
     p.timeout_ns = ctx->timeout_ns;
-    cudaError_t e = cudaMemsetAsync(ctx->d_queue, 0, 2 * sizeof(unsigned int), st);
+    cudaError_t e = cudaMemsetAsync(ctx->d_queue, 0, 3 * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag_count, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned int), st);
     if (e == cudaSuccess) e = ptca::launch_persistent(ctx->prec, p, ctx->grid, st);
     return e;
@@ -544,6 +572,15 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
     if (!(barrier_timeout_s > 0) || barrier_timeout_s > 3600) return fail(PTCA_ERR_INVALID, "timeout out of range");
     ctx->pipeline = mode;
     ctx->timeout_ns = (unsigned long long)(barrier_timeout_s * 1e9);
+    drop_graph(ctx);
+    return PTCA_OK;
+}
+
+ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (!(margin >= 0.0) || !std::isfinite(margin)) return fail(PTCA_ERR_INVALID, "margin must be finite and >= 0");
+    if (ctx->prec != 1 && margin > 0.0) return fail(PTCA_ERR_INVALID, "the FP64 re-solve applies to PTCA_MIXED only");
+    ctx->margin = margin;
     drop_graph(ctx);
     return PTCA_OK;
 }

@@ -247,8 +247,17 @@ struct StageArgs {
     double* rec_Facc;
     double* rec_fill;
     int32_t* rec_n;
-    unsigned long long* counters;  // [0] accepted, [1] eigensolves
+    unsigned long long* counters;  // [0] accepted, [1] eigensolves, [2] FP64 re-solves
     int32_t* err;
+    // PTCA_MIXED decision guard: a decision with |ln u + dF/T| < margin is
+    // deferred (its stage index appended to flag_list) and re-solved in FP64
+    // with the matrix in global memory (gA, one slot of gA_stride elements
+    // per CTA).  margin = 0 disables it.
+    double margin;
+    int32_t* flag_list;
+    unsigned int* flag_count;
+    double2* gA;
+    int64_t gA_stride;
 };
 
 // One matrix of one update site of a stage: c indexes the stage's site list,
@@ -295,6 +304,11 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int c, int var, u
     const double lnu = log(u0);
     const double dF = Fn - Fo;
     if (!isfinite(dF)) atomicExch(a.err, 1);
+    if (a.margin > 0.0 && fabs(lnu + dF / a.m.T) < a.margin) {
+        a.flag_list[atomicAdd(a.flag_count, 1u)] = c;
+        atomicAdd(&a.counters[2], 1ull);
+        return;
+    }
     const bool acc = lnu < -dF / a.m.T;
     double* dst = a.S_out + 3 * site;
     if (acc) { dst[0] = sn[0]; dst[1] = sn[1]; dst[2] = sn[2]; }
@@ -328,6 +342,80 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArg
     stage_item<T, NT>(a, c, var, smem, s_new, &s_last);
 }
 
+// FP64 re-solve of one matrix of a deferred update site (stage index c from
+// the flag list): the matrix lives in this CTA's global slot, the reduction
+// and eigenvalues run in FP64, and the second of the pair decides (no
+// margin test).  nmaxc = 32 * NT sizes the FP64 vectors in shared memory.
+template <int NT>
+__device__ __noinline__ void resolve_item(const StageArgs& a, int c, int var, unsigned char* smem, double* s_new,
+                                          int* s_last) {
+    const SmemLayout L = smem_layout(0, 32 * NT, sizeof(double2));
+    Carve<double> cv = carve<double>(smem, L);
+    cv.A = a.gA + (int64_t)blockIdx.x * a.gA_stride;
+    const int site = a.sites[c];
+    const Window w = make_window(a.m, site);
+    const int n = 2 * w.ex * w.ey;
+    if (threadIdx.x == 0 && var == 1)
+        propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, s_new);
+    __syncthreads();
+    build_cluster<double>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    __syncthreads();
+    householder_tridiag<double, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
+    double ssp, sfe;
+    int K;
+    tridiag_eig_F<double>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
+    if (threadIdx.x == 0) {
+        a.Fbuf[2 * c + var] = -a.m.T * ssp;
+        a.fillbuf[2 * c + var] = sfe;
+        __threadfence();
+        *s_last = (atomicAdd(&a.ticket[c], 1) == 1);
+    }
+    __syncthreads();
+    if (!*s_last || threadIdx.x != 0) return;
+    __threadfence();
+    a.ticket[c] = 0;
+    const double Fo = __ldcg(&a.Fbuf[2 * c]), Fn = __ldcg(&a.Fbuf[2 * c + 1]);
+    const double fo = __ldcg(&a.fillbuf[2 * c]), fn = __ldcg(&a.fillbuf[2 * c + 1]);
+    double sn[3];
+    const double* so = a.S_in + 3 * site;
+    if (var == 1) { sn[0] = s_new[0]; sn[1] = s_new[1]; sn[2] = s_new[2]; }
+    else propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, so, sn);
+    double u0, u1;
+    uniform2(a.m.seed, a.sweep, (uint32_t)site, RNG_ACCEPT, u0, u1);
+    const double lnu = log(u0);
+    const double dF = Fn - Fo;
+    if (!isfinite(dF)) atomicExch(a.err, 1);
+    const bool acc = lnu < -dF / a.m.T;
+    double* dst = a.S_out + 3 * site;
+    if (acc) { dst[0] = sn[0]; dst[1] = sn[1]; dst[2] = sn[2]; }
+    else { dst[0] = so[0]; dst[1] = so[1]; dst[2] = so[2]; }
+    const int r = a.rec_base + c;
+    a.rec_site[r] = site;
+    a.rec_Fold[r] = Fo;
+    a.rec_Fnew[r] = Fn;
+    a.rec_lnu[r] = lnu;
+    a.rec_acc[r] = acc ? 1 : 0;
+    a.rec_Facc[r] = acc ? Fn : Fo;
+    a.rec_fill[r] = acc ? fn : fo;
+    a.rec_n[r] = n;
+    if (acc) atomicAdd(&a.counters[0], 1ull);
+    atomicAdd(&a.counters[1], 2ull);
+}
+
+// Re-solve the deferred update sites of one stage (per-stage pipeline).
+template <int NT>
+__global__ void __launch_bounds__(CTA, 1) k_resolve(StageArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    __shared__ int s_last;
+    const int nflag = (int)*(volatile unsigned int*)a.flag_count;
+    for (int item = blockIdx.x; item < 2 * nflag; item += gridDim.x) {
+        const int c = a.flag_list[item >> 1];
+        resolve_item<NT>(a, c, item & 1, smem, s_new, &s_last);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Persistent sweep: one launch runs every stage of n_sweeps sweeps.  Each CTA
 // takes (site, old/new) items of the current stage from an atomic work queue
@@ -346,7 +434,7 @@ struct PersistArgs {
     int32_t nstages;
     int32_t n_sweeps;
     unsigned long long* sweep_ctr;// RNG sweep index of the next sweep (advanced by the kernel)
-    unsigned int* queue;          // [2] work-queue counters, alternating by stage
+    unsigned int* queue;          // [0..1] work-queue counters alternating by stage, [2] re-solve queue
     unsigned int* bar;            // [0] arrivals, [1] generation
     unsigned long long timeout_ns;
 };
@@ -362,7 +450,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // last CTA to arrive also clears `clear_after` (a queue counter nobody uses
 // until two stages later).
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int participants, unsigned long long timeout_ns,
-                                             int32_t* err, unsigned int* clear_after) {
+                                             int32_t* err, unsigned int* clear_after, unsigned int* clear_after2 = nullptr) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -373,6 +461,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int par
         int ok = 1;
         if (arrived == participants - 1) {
             if (clear_after) *clear_after = 0u;
+            if (clear_after2) *clear_after2 = 0u;
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -434,6 +523,22 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_sweep_persiste
             __syncthreads();
         }
         if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, a.err, qc)) return;
+        if constexpr (sizeof(T) == 4) {
+            // Deferred decisions of this stage (PTCA_MIXED margin guard).
+            const int nflag = a.margin > 0.0 ? (int)*(volatile unsigned int*)a.flag_count : 0;
+            if (nflag > 0) {
+                for (;;) {
+                    if (threadIdx.x == 0) s_item = (int)atomicAdd(p.queue + 2, 1u);
+                    __syncthreads();
+                    const int item = s_item;
+                    __syncthreads();
+                    if (item >= 2 * nflag) break;
+                    resolve_item<NT>(a, a.flag_list[item >> 1], item & 1, smem, s_new, &s_last);
+                    __syncthreads();
+                }
+                if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, a.err, p.queue + 2, a.flag_count)) return;
+            }
+        }
     }
     if (G > 0) {
         // Bring the other buffer up to date with the last stage.

@@ -26,6 +26,7 @@ cudaError_t launch_persistent_f32(const PersistArgs&, int, cudaStream_t);
 cudaError_t launch_persistent_f64(const PersistArgs&, int, cudaStream_t);
 int persistent_blocks_per_sm_f32(int);
 int persistent_blocks_per_sm_f64(int);
+cudaError_t launch_resolve_f32(const StageArgs&, int, cudaStream_t);
 
 size_t cluster_smem_bytes(int prec, int nA) { return prec ? cluster_smem_bytes_f32(nA) : cluster_smem_bytes_f64(nA); }
 int cluster_max_order(int prec) { return prec ? cluster_max_order_f32() : cluster_max_order_f64(); }
@@ -51,6 +52,7 @@ cudaError_t launch_stage(int prec, const StageArgs& a, cudaStream_t st) {
 cudaError_t launch_persistent(int prec, const PersistArgs& p, int grid, cudaStream_t st) {
     return prec ? launch_persistent_f32(p, grid, st) : launch_persistent_f64(p, grid, st);
 }
+cudaError_t launch_resolve(const StageArgs& a, int grid, cudaStream_t st) { return launch_resolve_f32(a, grid, st); }
 int persistent_blocks_per_sm(int prec, int nA) {
     return prec ? persistent_blocks_per_sm_f32(nA) : persistent_blocks_per_sm_f64(nA);
 }

@@ -33,6 +33,8 @@ cudaError_t launch_stage(int prec, const StageArgs& a, cudaStream_t st);
 cudaError_t launch_persistent(int prec, const PersistArgs& p, int grid, cudaStream_t st);
 // CTAs of the persistent kernel that fit on one SM for matrices up to nA.
 int persistent_blocks_per_sm(int prec, int nA);
+// FP64 re-solve of the decisions a PTCA_MIXED stage deferred (grid CTAs).
+cudaError_t launch_resolve(const StageArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_barrier_selftest(int blocks, unsigned int* bar, int32_t* err, unsigned long long timeout_ns,
                                     cudaStream_t st);
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);

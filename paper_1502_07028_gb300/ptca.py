@@ -27,7 +27,7 @@ EXPORTED = [
     "ptca_init", "ptca_destroy", "ptca_set_T", "ptca_set_mu", "ptca_get_spins", "ptca_set_spins",
     "ptca_dims", "ptca_build_clusters", "ptca_cluster_eigvals", "ptca_free_energy", "ptca_sweep",
     "ptca_sweep_record", "ptca_observables", "ptca_schedule", "ptca_last_error", "ptca_version",
-    "ptca_sweep_noalloc", "ptca_set_pipeline", "ptca_selftest_barrier_timeout",
+    "ptca_sweep_noalloc", "ptca_set_pipeline", "ptca_selftest_barrier_timeout", "ptca_set_resolve_margin",
 ]
 
 
@@ -101,6 +101,7 @@ def lib():
             "ptca_version": ([], i32),
             "ptca_sweep_noalloc": ([P(Lattice), P(Params), vp, vp, i32, vp, i64, vp, vp, vp], i32),
             "ptca_set_pipeline": ([vp, i32, dbl], i32),
+            "ptca_set_resolve_margin": ([vp, dbl], i32),
             "ptca_selftest_barrier_timeout": ([i32, dbl, vp], i32),
         }
         for name, (args, res) in sig.items():
@@ -263,6 +264,10 @@ def ptca_sweep_noalloc(cfg: Config, sites, stage_start, spins, sweep_index: int,
 
 def ptca_set_pipeline(h, mode: int, barrier_timeout_s: float = 30.0) -> None:
     _check(lib().ptca_set_pipeline(h, mode, barrier_timeout_s))
+
+
+def ptca_set_resolve_margin(h, margin: float) -> None:
+    _check(lib().ptca_set_resolve_margin(h, margin))
 
 
 def ptca_selftest_barrier_timeout(blocks: int, timeout_s: float, stream=None) -> int:

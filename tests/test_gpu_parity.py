@@ -6,8 +6,8 @@ Tolerances (from the stated accuracy of each precision mode):
     |ln u + dF/T| > 1e-6.
   * PTCA_MIXED (FP32 reduction, FP64 eigenvalue refinement and free energy)
     -- eigenvalues |d eps| <= 1e-5 (J_H + 4t); free energies
-    |dF| <= 1e-5 max(1, |F|); decisions identical wherever the margin exceeds
-    the band that error allows (1e-2 at T = 0.05).
+    |dF| <= 1e-5 max(1, |F|); decisions identical wherever |ln u + dF/T| >
+    1e-6, which the FP64 re-solve of decisions within 1e-2 guarantees.
 """
 import math
 
@@ -23,7 +23,7 @@ from tests import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {P.FP64: 1e-9, P.MIXED: 1e-5}
-BAND = {P.FP64: 1e-6, P.MIXED: 1e-2}
+BAND = {P.FP64: 1e-6, P.MIXED: 1e-6}
 
 
 @pytest.fixture(scope="module", autouse=True)
