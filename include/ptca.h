@@ -98,15 +98,18 @@ typedef struct {
     int64_t resolved;   /* PTCA_MIXED: proposals re-solved in FP64 near the threshold  */
     int64_t sweeps;     /* sweeps run so far on this context (RNG sweep counter)       */
     double  seconds;    /* device time of the call, from CUDA events                   */
+    int64_t screened;   /* surrogate on: proposals rejected at stage 1 (no cluster     */
+                        /* diagonalisation)                                           */
 } ptca_sweep_stats;
 
 /* Observables of the current configuration (ptca_observables). */
 typedef struct {
     double S_00;        /* S(q) at q = (0,0), Eq. 2 for one configuration              */
     double S_pipi;      /* S(q) at q = (pi,pi)                                          */
-    double F_site;      /* last sweep: mean over visits of F of the accepted state / N_c */
+    double F_site;      /* last sweep: mean over solved visits of F of the accepted      */
+                        /* state / N_c                                                 */
     double acceptance;  /* last sweep: accepted / attempts                              */
-    double filling;     /* last sweep: mean over visits of sum_k f(eps_k) / N_c, f the  */
+    double filling;     /* last sweep: mean over solved visits of sum_k f(eps_k) / N_c, f the */
                         /* Fermi function, for the accepted state                      */
 } ptca_obs;
 
@@ -229,6 +232,57 @@ ptca_status ptca_sweep_record(ptca_ctx* ctx, int32_t* site, double* F_old, doubl
  * ptca_obs).  S(q) follows Eq. 2 for one configuration.  Synchronises
  * `stream` and writes the host struct *out. */
 ptca_status ptca_observables(ptca_ctx* ctx, ptca_obs* out, void* stream);
+
+/* ----------------------------------------------------------------------- */
+/* Surrogate network and delayed acceptance                                  */
+/* ----------------------------------------------------------------------- */
+/* A multilayer perceptron h: 150 -> 256 -> 256 -> 256 -> 1 (SiLU), reading the
+ * 7x7 patch of the cluster window around the update site (as centred as the
+ * window allows; 147 values, the update site's entry holding a spin s) and a
+ * second spin.  Its estimate of the proposal's free-energy change is
+ *     dF~ = scale * ( h([P(s_old), s_new]) - h([P(s_new), s_old]) ),
+ * antisymmetric in the two states.  Matrix products run on the tensor cores
+ * with bfloat16 operands and FP32 accumulation (library kernels); parameters,
+ * AdamW moments and the rest are FP32.  With the surrogate enabled,
+ * ptca_sweep uses delayed acceptance (Christen and Fox 2005): stage 1 passes
+ * a proposal with probability min(1, exp(-dF~/T)); only passing proposals get
+ * the exact cluster solves, and stage 2 accepts with probability
+ * min(1, exp(-(dF - dF~)/T)).  Detailed balance with respect to the exact
+ * cluster free energy holds for any network; the network only changes how
+ * many exact solves are spent.  Screening runs with the per-stage pipeline.
+ * The paper has no surrogate; its exact TCA step is the judge here.       */
+
+/* Number of FP32 parameters (layout W1[256x160] b1 W2[256x256] b2 W3 b3
+ * W4[8x256] b4[8]; W1 columns 150..159 and W4/b4 rows 1..7 are padding). */
+int32_t ptca_surrogate_param_count(void);
+/* Allocate the network (once) and draw fresh parameters from `seed`. */
+ptca_status ptca_surrogate_init(ptca_ctx* ctx, uint64_t seed, void* stream);
+/* Copy parameters out/in (device or host pointers; synchronous). */
+ptca_status ptca_surrogate_get_params(ptca_ctx* ctx, float* theta, float* scale, void* stream);
+ptca_status ptca_surrogate_set_params(ptca_ctx* ctx, const float* theta, float scale, void* stream);
+/* Run n_sweeps exact sweeps (no screening) and record, per visit in
+ * flattened stage order, the 150 inputs [P(s_old), s_new] (feat, device
+ * float[n_sweeps*N*150]), the patch index of the update site (center,
+ * int32[n_sweeps*N]) and the exact dF (dF, float[n_sweeps*N]). */
+ptca_status ptca_surrogate_collect(ptca_ctx* ctx, int32_t n_sweeps, float* feat, int32_t* center, float* dF,
+                                   void* stream);
+/* `steps` AdamW steps (betas 0.9/0.999, eps 1e-8, decoupled weight decay) on
+ * mini-batches of `batch` samples drawn from n collected samples with the
+ * counter generator (seed), minimising mean((dF~ - dF)^2)/scale^2; scale is
+ * the standard deviation of dF, fixed at the first step.  loss_trace: device
+ * float[steps] or NULL.  Stream-ordered. */
+ptca_status ptca_surrogate_train(ptca_ctx* ctx, const float* feat, const int32_t* center, const float* dF, int64_t n,
+                                 int32_t steps, int32_t batch, float lr, float weight_decay, uint64_t seed,
+                                 float* loss_trace, void* stream);
+/* Loss and its gradient (float[param_count]) over the n samples given, with
+ * no update (gradient checks).  Synchronous. */
+ptca_status ptca_surrogate_grad(ptca_ctx* ctx, const float* feat, const int32_t* center, const float* dF, int32_t n,
+                                float* grad_out, float* loss_out, void* stream);
+/* dF~ for n samples (device float[n]).  Stream-ordered. */
+ptca_status ptca_surrogate_predict(ptca_ctx* ctx, const float* feat, const int32_t* center, int32_t n, float* dF_out,
+                                   void* stream);
+/* Turn delayed-acceptance screening in ptca_sweep on (1) or off (0). */
+ptca_status ptca_surrogate_enable(ptca_ctx* ctx, int32_t on);
 
 /* ----------------------------------------------------------------------- */
 /* Sweep without device allocation                                           */

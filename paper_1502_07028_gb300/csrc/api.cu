@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/ptca.h"
+#include "context.h"
 #include "kernels.cuh"
 #include "launch.h"
 
@@ -33,15 +34,7 @@ ptca_status cuda_fail(cudaError_t e, const char* where) {
         if (_e != cudaSuccess) return cuda_fail(_e, #call);          \
     } while (0)
 
-// Resolved problem (defaults filled in).
-struct Problem {
-    int Lx, Ly, periodic, Lc, ox, oy, cluster_periodic, schedule, stride, precision, proposal;
-    double t, JH, mu, T, cone_deg;
-    uint64_t seed;
-    int N() const { return Lx * Ly; }
-    int nsite_max() const { return Lc * (Ly == 1 ? 1 : Lc); }
-    int nmax() const { return 2 * nsite_max(); }
-};
+
 
 // Window along one axis (same rule as the device code).
 void window_axis(int L, int periodic, int Lc, int o, int c, int& start, int& ext) {
@@ -164,52 +157,6 @@ template <typename T> cudaError_t dalloc(T** p, size_t count) {
 
 }  // namespace
 
-struct ptca_ctx {
-    Problem p;
-    int device = 0;
-    int prec = 0;  // 0 FP64, 1 FP32 reduction
-    int N = 0, nstages = 0, max_stage = 0, nA = 0;
-    size_t smem = 0;
-    std::vector<int32_t> h_start, h_sites;
-    int32_t* d_sites = nullptr;
-    double* d_S[2] = {nullptr, nullptr};
-    double* d_F = nullptr;
-    double* d_fill = nullptr;
-    int32_t* d_ticket = nullptr;
-    int32_t* d_rec_site = nullptr;
-    double* d_rec_Fold = nullptr;
-    double* d_rec_Fnew = nullptr;
-    double* d_rec_lnu = nullptr;
-    uint8_t* d_rec_acc = nullptr;
-    double* d_rec_Facc = nullptr;
-    double* d_rec_fill = nullptr;
-    int32_t* d_rec_n = nullptr;
-    unsigned long long* d_counters = nullptr;
-    int32_t* d_err = nullptr;
-    double* d_obs = nullptr;
-    int64_t sweeps = 0;
-    int64_t total_accepted = 0;
-    // persistent pipeline
-    int32_t* d_stage_start = nullptr;
-    int32_t* d_perm = nullptr;
-    unsigned int* d_queue = nullptr;
-    unsigned int* d_bar = nullptr;
-    unsigned long long* d_sweep_ctr = nullptr;
-    int pipeline = PTCA_PIPELINE_GRAPH;
-    unsigned long long timeout_ns = 30ull * 1000000000ull;
-    int grid = 0;
-    cudaGraphExec_t graph = nullptr;
-    int graph_sweeps = -1;
-    cudaStream_t graph_stream = nullptr;
-    bool graph_failed = false;
-    // PTCA_MIXED decision guard
-    double margin = 0.0;
-    int32_t* d_flag_list = nullptr;
-    unsigned int* d_flag_count = nullptr;
-    double2* d_gA = nullptr;
-    int64_t gA_stride = 0;
-    int resolve_grid = 0;
-};
 
 static void drop_graph(ptca_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -219,6 +166,7 @@ static void drop_graph(ptca_ctx* c) {
 
 static void free_ctx(ptca_ctx* c) {
     drop_graph(c);
+    ptca_free_surrogate(c);
     void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
                     c->d_rec_n, c->d_counters, c->d_err, c->d_obs, c->d_stage_start, c->d_perm, c->d_queue,
@@ -484,14 +432,29 @@ static StageArgs base_args(ptca_ctx* ctx) {
     return a;
 }
 
-// One launch per stage (Sec. III.a stage = one kernel).
-static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
+cudaError_t ptca_screen_stage(ptca_ctx* ctx, ptca::StageArgs& a, cudaStream_t st);
+
+// Training-sample destination of ptca_surrogate_collect (N rows per sweep).
+struct Collect {
+    float* feat;
+    int32_t* center;
+    float* dF;
+};
+
+// One launch per stage (Sec. III.a stage = one kernel); with the surrogate
+// enabled each stage is screened first and only passing sites are solved.
+static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st, const Collect* col = nullptr) {
     StageArgs a = base_args(ctx);
     int64_t g = 0;
     int prev_s = -1;
     cudaError_t e = cudaSuccess;
     for (int sw = 0; sw < n_sweeps && e == cudaSuccess; ++sw) {
         a.sweep = (uint64_t)(ctx->sweeps + sw);
+        if (col) {
+            a.sg_feat = col->feat + (size_t)sw * ctx->N * ptca::SG_IN;
+            a.sg_center = col->center + (size_t)sw * ctx->N;
+            a.sg_dF = col->dF + (size_t)sw * ctx->N;
+        }
         for (int s = 0; s < ctx->nstages && e == cudaSuccess; ++s, ++g) {
             a.S_in = ctx->d_S[g & 1];
             a.S_out = ctx->d_S[(g + 1) & 1];
@@ -500,7 +463,11 @@ static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st
             a.rec_base = ctx->h_start[s];
             a.prev_sites = prev_s >= 0 ? ctx->d_sites + ctx->h_start[prev_s] : nullptr;
             a.prev_count = prev_s >= 0 ? ctx->h_start[prev_s + 1] - ctx->h_start[prev_s] : 0;
-            e = ptca::launch_stage(ctx->prec, a, st);
+            a.perm = nullptr;
+            a.count_dev = nullptr;
+            a.sg_dFt = nullptr;
+            if (ctx->sg.enabled && !col) e = ptca_screen_stage(ctx, a, st);
+            if (e == cudaSuccess) e = ptca::launch_stage(ctx->prec, a, st);
             if (e == cudaSuccess && a.margin > 0.0) {
                 e = ptca::launch_resolve(a, ctx->resolve_grid, st);
                 if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag_count, 0, sizeof(unsigned int), st);
@@ -598,7 +565,7 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
     PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
     if (n_sweeps > 0) {
         cudaError_t e;
-        if (ctx->pipeline == PTCA_PIPELINE_STAGES) e = sweep_stages(ctx, n_sweeps, st);
+        if (ctx->pipeline == PTCA_PIPELINE_STAGES || ctx->sg.enabled) e = sweep_stages(ctx, n_sweeps, st);
         else if (ctx->pipeline == PTCA_PIPELINE_PERSISTENT || ctx->graph_failed) e = enqueue_persistent(ctx, n_sweeps, st);
         else e = sweep_graph(ctx, n_sweeps, st);
         if (e != cudaSuccess) return cuda_fail(e, "ptca_sweep");
@@ -619,6 +586,7 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
         stats_out->accepted = (int64_t)cnt[0];
         stats_out->eigensolves = (int64_t)cnt[1];
         stats_out->resolved = (int64_t)cnt[2];
+        stats_out->screened = (int64_t)cnt[3];
         stats_out->sweeps = ctx->sweeps;
         stats_out->seconds = ms * 1e-3;
         if (err[1]) {
@@ -627,6 +595,18 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
         }
         if (err[0]) return fail(PTCA_ERR_NUMERIC, "non-finite free-energy difference in a sweep");
     }
+    return PTCA_OK;
+}
+
+ptca_status ptca_surrogate_collect(ptca_ctx* ctx, int32_t n_sweeps, float* feat, int32_t* center, float* dF,
+                                   void* stream) {
+    if (!ctx || n_sweeps < 0 || !feat || !center || !dF) return fail(PTCA_ERR_INVALID, "bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
+    Collect col{feat, center, dF};
+    cudaError_t e = sweep_stages(ctx, n_sweeps, st, &col);
+    if (e != cudaSuccess) return cuda_fail(e, "ptca_surrogate_collect");
+    ctx->sweeps += n_sweeps;
     return PTCA_OK;
 }
 

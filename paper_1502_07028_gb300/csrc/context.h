@@ -1,0 +1,97 @@
+// context.h -- the library context behind the opaque ptca_ctx handle.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ptca.h"
+
+// Resolved problem (defaults filled in).
+struct Problem {
+    int Lx, Ly, periodic, Lc, ox, oy, cluster_periodic, schedule, stride, precision, proposal;
+    double t, JH, mu, T, cone_deg;
+    uint64_t seed;
+    int N() const { return Lx * Ly; }
+    int nsite_max() const { return Lc * (Ly == 1 ? 1 : Lc); }
+    int nmax() const { return 2 * nsite_max(); }
+};
+
+namespace ptca {
+
+// Surrogate network state (delayed-acceptance screening).
+struct SurrogateState {
+    bool ready = false;     // parameters initialised
+    bool enabled = false;   // screen proposals in ptca_sweep
+    float scale = 1.f;      // dF scale the network is trained in
+    int adam_step = 0;
+    float* theta = nullptr; // FP32 parameters
+    float* m1 = nullptr;    // AdamW moments
+    float* m2 = nullptr;
+    float* grad = nullptr;
+    // stage screening buffers (rows = 2 * max_stage)
+    float *X = nullptr, *Z1 = nullptr, *A1 = nullptr, *Z2 = nullptr, *A2 = nullptr, *Z3 = nullptr, *A3 = nullptr,
+          *Z4 = nullptr;
+    float* dFt = nullptr;
+    int32_t* work = nullptr;
+    unsigned int* nwork = nullptr;
+    // training buffers (rows = 2 * batch)
+    int batch = 0;
+    float *tX = nullptr, *tZ1 = nullptr, *tA1 = nullptr, *tZ2 = nullptr, *tA2 = nullptr, *tZ3 = nullptr,
+          *tA3 = nullptr, *tZ4 = nullptr, *tdZ4 = nullptr, *tdA = nullptr, *tdZ = nullptr, *tloss = nullptr;
+    int64_t* tidx = nullptr;
+};
+
+}  // namespace ptca
+
+struct ptca_ctx {
+    Problem p;
+    int device = 0;
+    int prec = 0;  // 0 FP64, 1 FP32 reduction
+    int N = 0, nstages = 0, max_stage = 0, nA = 0;
+    size_t smem = 0;
+    std::vector<int32_t> h_start, h_sites;
+    int32_t* d_sites = nullptr;
+    double* d_S[2] = {nullptr, nullptr};
+    double* d_F = nullptr;
+    double* d_fill = nullptr;
+    int32_t* d_ticket = nullptr;
+    int32_t* d_rec_site = nullptr;
+    double* d_rec_Fold = nullptr;
+    double* d_rec_Fnew = nullptr;
+    double* d_rec_lnu = nullptr;
+    uint8_t* d_rec_acc = nullptr;
+    double* d_rec_Facc = nullptr;
+    double* d_rec_fill = nullptr;
+    int32_t* d_rec_n = nullptr;
+    unsigned long long* d_counters = nullptr;
+    int32_t* d_err = nullptr;
+    double* d_obs = nullptr;
+    int64_t sweeps = 0;
+    int64_t total_accepted = 0;
+    // persistent pipeline
+    int32_t* d_stage_start = nullptr;
+    int32_t* d_perm = nullptr;
+    unsigned int* d_queue = nullptr;
+    unsigned int* d_bar = nullptr;
+    unsigned long long* d_sweep_ctr = nullptr;
+    int pipeline = PTCA_PIPELINE_GRAPH;
+    unsigned long long timeout_ns = 30ull * 1000000000ull;
+    int grid = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_sweeps = -1;
+    cudaStream_t graph_stream = nullptr;
+    bool graph_failed = false;
+    // PTCA_MIXED decision guard
+    double margin = 0.0;
+    int32_t* d_flag_list = nullptr;
+    unsigned int* d_flag_count = nullptr;
+    double2* d_gA = nullptr;
+    int64_t gA_stride = 0;
+    int resolve_grid = 0;
+    // surrogate network for delayed-acceptance screening
+    ptca::SurrogateState sg;
+};
+
+void ptca_free_surrogate(ptca_ctx* c);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "cluster_solve.cuh"
+#include "surrogate.cuh"
 
 namespace ptca {
 
@@ -258,7 +259,31 @@ struct StageArgs {
     unsigned int* flag_count;
     double2* gA;
     int64_t gA_stride;
+    // Delayed acceptance: work list (perm) length on the device, and the
+    // stage-1 surrogate dF~ per stage index (stage 2 accepts iff
+    // ln u < -(dF - dF~)/T).  Null when screening is off.
+    const unsigned int* count_dev;
+    const float* sg_dFt;
+    // Training-data collection: per visit (record index) the 150 network
+    // inputs [P(s_old), s_new], the patch index of the update site and dF.
+    float* sg_feat;
+    int32_t* sg_center;
+    float* sg_dF;
 };
+
+// Decision of an update site (thread 0 of the deciding CTA): Metropolis on
+// dF, or delayed-acceptance stage 2 on dF - dF~, and the training sample.
+__device__ __forceinline__ double stage2_dF(const StageArgs& a, int c, double dF) {
+    return a.sg_dFt ? dF - (double)a.sg_dFt[c] : dF;
+}
+
+__device__ __forceinline__ void collect_sample(const StageArgs& a, const Window& w, int r, const double* sn, double dF) {
+    if (!a.sg_feat) return;
+    float* f = a.sg_feat + (int64_t)r * SG_IN;
+    a.sg_center[r] = patch_features(a.m, w, a.S_in, f);
+    f[147] = (float)sn[0]; f[148] = (float)sn[1]; f[149] = (float)sn[2];
+    a.sg_dF[r] = (float)dF;
+}
 
 // One matrix of one update site of a stage: c indexes the stage's site list,
 // var 0/1 selects H_old/H_new.  The second of the pair to finish applies
@@ -304,12 +329,14 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int c, int var, u
     const double lnu = log(u0);
     const double dF = Fn - Fo;
     if (!isfinite(dF)) atomicExch(a.err, 1);
-    if (a.margin > 0.0 && fabs(lnu + dF / a.m.T) < a.margin) {
+    const double dFe = stage2_dF(a, c, dF);
+    if (a.margin > 0.0 && fabs(lnu + dFe / a.m.T) < a.margin) {
         a.flag_list[atomicAdd(a.flag_count, 1u)] = c;
         atomicAdd(&a.counters[2], 1ull);
         return;
     }
-    const bool acc = lnu < -dF / a.m.T;
+    const bool acc = lnu < -dFe / a.m.T;
+    collect_sample(a, w, a.rec_base + c, sn, dF);
     double* dst = a.S_out + 3 * site;
     if (acc) { dst[0] = sn[0]; dst[1] = sn[1]; dst[2] = sn[2]; }
     else { dst[0] = so[0]; dst[1] = so[1]; dst[2] = so[2]; }
@@ -338,7 +365,8 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArg
         a.S_out[3 * s + 2] = a.S_in[3 * s + 2];
     }
     const int c = blockIdx.x >> 1, var = blockIdx.x & 1;
-    if (c >= a.count) return;
+    const int count = a.count_dev ? (int)*a.count_dev : a.count;
+    if (c >= count) return;
     stage_item<T, NT>(a, c, var, smem, s_new, &s_last);
 }
 
@@ -385,7 +413,8 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, int c, int var, un
     const double lnu = log(u0);
     const double dF = Fn - Fo;
     if (!isfinite(dF)) atomicExch(a.err, 1);
-    const bool acc = lnu < -dF / a.m.T;
+    const bool acc = lnu < -stage2_dF(a, c, dF) / a.m.T;
+    collect_sample(a, w, a.rec_base + c, sn, dF);
     double* dst = a.S_out + 3 * site;
     if (acc) { dst[0] = sn[0]; dst[1] = sn[1]; dst[2] = sn[2]; }
     else { dst[0] = so[0]; dst[1] = so[1]; dst[2] = so[2]; }

@@ -134,21 +134,24 @@ __global__ void k_observables(const double* __restrict__ S, int Lx, int Ly, cons
                               const int32_t* __restrict__ rec_n, int N, double* __restrict__ out) {
     __shared__ double red[32];
     double m0[3] = {0, 0, 0}, mp[3] = {0, 0, 0};
-    double fs = 0.0, ac = 0.0, fl = 0.0;
+    double fs = 0.0, ac = 0.0, fl = 0.0, nf = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const int x = i % Lx, y = i / Lx;
         const double sg = ((x + y) & 1) ? -1.0 : 1.0;
         for (int a = 0; a < 3; ++a) { m0[a] += S[3 * i + a]; mp[a] += sg * S[3 * i + a]; }
         if (rec_n[i] > 0) {
-            const double nc = 0.5 * (double)rec_n[i];
-            fs += rec_Facc[i] / nc;
             ac += (double)rec_acc[i];
-            fl += rec_fill[i] / nc;
+            if (isfinite(rec_Facc[i])) {  // proposals rejected by the surrogate screen have no F
+                const double nc = 0.5 * (double)rec_n[i];
+                fs += rec_Facc[i] / nc;
+                fl += rec_fill[i] / nc;
+                nf += 1.0;
+            }
         }
     }
-    double vals[9] = {m0[0], m0[1], m0[2], mp[0], mp[1], mp[2], fs, ac, fl};
-    double tot[9];
-    for (int q = 0; q < 9; ++q) {
+    double vals[10] = {m0[0], m0[1], m0[2], mp[0], mp[1], mp[2], fs, ac, fl, nf};
+    double tot[10];
+    for (int q = 0; q < 10; ++q) {
         tot[q] = block_sum<double>(vals[q], red);
         __syncthreads();
     }
@@ -156,9 +159,10 @@ __global__ void k_observables(const double* __restrict__ S, int Lx, int Ly, cons
         const double N2 = (double)N * (double)N;
         out[0] = (tot[0] * tot[0] + tot[1] * tot[1] + tot[2] * tot[2]) / N2;
         out[1] = (tot[3] * tot[3] + tot[4] * tot[4] + tot[5] * tot[5]) / N2;
-        out[2] = tot[6] / N;
+        const double nfin = tot[9] > 0 ? tot[9] : 1.0;
+        out[2] = tot[6] / nfin;
         out[3] = tot[7] / N;
-        out[4] = tot[8] / N;
+        out[4] = tot[8] / nfin;
     }
 }
 

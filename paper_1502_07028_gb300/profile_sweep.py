@@ -1,0 +1,53 @@
+"""Run PTCA sweeps of a chosen workload, for profilers (ncu) and quick timing.
+
+    python -m paper_1502_07028_gb300.profile_sweep --precision mixed --L 100 --Lc 8 --sweeps 1
+
+Prints one line with the device time of the call and the sweep statistics.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--L", type=int, default=100)
+    ap.add_argument("--Lc", type=int, default=8)
+    ap.add_argument("--open", action="store_true", help="open lattice (clipped windows)")
+    ap.add_argument("--schedule", choices=["block", "tiled"], default="block")
+    ap.add_argument("--stride", type=int, default=0)
+    ap.add_argument("--pipeline", choices=["stages", "persistent", "graph"], default="graph")
+    ap.add_argument("--margin", type=float, default=None, help="mixed-mode FP64 re-solve margin (0 = off)")
+    ap.add_argument("--sweeps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=0)
+    ap.add_argument("--T", type=float, default=0.05)
+    ap.add_argument("--mu", type=float, default=-6.5)
+    ap.add_argument("--JH", type=float, default=8.0)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import paper_1502_07028_gb300 as P
+    from paper_1502_07028_gb300 import _build
+
+    _build.build()
+    cfg = P.Config(Lx=a.L, Ly=a.L, L_c=a.Lc, periodic=0 if a.open else 1, J_H=a.JH, mu=a.mu, T=a.T, seed=a.seed,
+                   schedule=P.SCHEDULE_BLOCK if a.schedule == "block" else P.SCHEDULE_TILED, stride=a.stride,
+                   precision=P.MIXED if a.precision == "mixed" else P.FP64, proposal=P.PROPOSAL_CONE, cone_deg=30.0)
+    ctx = P.Context(cfg)
+    P.ptca_set_pipeline(ctx.h, {"stages": P.PIPELINE_STAGES, "persistent": P.PIPELINE_PERSISTENT,
+                                "graph": P.PIPELINE_GRAPH}[a.pipeline])
+    if a.margin is not None and cfg.precision == P.MIXED:
+        P.ptca_set_resolve_margin(ctx.h, a.margin)
+    if a.warmup:
+        ctx.sweep(a.warmup)
+    st = ctx.sweep(a.sweeps)
+    print(f"{a.precision} L={a.L} Lc={a.Lc} {a.schedule} {a.pipeline}: {st.seconds * 1e3:.3f} ms for {a.sweeps} sweep(s), "
+          f"{cfg.N * a.sweeps / st.seconds:.0f} spin-updates/s, accepted {st.accepted}, resolved {st.resolved}")
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -28,6 +28,9 @@ EXPORTED = [
     "ptca_dims", "ptca_build_clusters", "ptca_cluster_eigvals", "ptca_free_energy", "ptca_sweep",
     "ptca_sweep_record", "ptca_observables", "ptca_schedule", "ptca_last_error", "ptca_version",
     "ptca_sweep_noalloc", "ptca_set_pipeline", "ptca_selftest_barrier_timeout", "ptca_set_resolve_margin",
+    "ptca_surrogate_param_count", "ptca_surrogate_init", "ptca_surrogate_get_params", "ptca_surrogate_set_params",
+    "ptca_surrogate_collect", "ptca_surrogate_train", "ptca_surrogate_grad", "ptca_surrogate_predict",
+    "ptca_surrogate_enable",
 ]
 
 
@@ -53,7 +56,8 @@ class Params(ctypes.Structure):
 
 class SweepStats(ctypes.Structure):
     _fields_ = [("attempts", ctypes.c_int64), ("accepted", ctypes.c_int64), ("eigensolves", ctypes.c_int64),
-                ("resolved", ctypes.c_int64), ("sweeps", ctypes.c_int64), ("seconds", ctypes.c_double)]
+                ("resolved", ctypes.c_int64), ("sweeps", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("screened", ctypes.c_int64)]
 
 
 class Obs(ctypes.Structure):
@@ -102,6 +106,16 @@ def lib():
             "ptca_sweep_noalloc": ([P(Lattice), P(Params), vp, vp, i32, vp, i64, vp, vp, vp], i32),
             "ptca_set_pipeline": ([vp, i32, dbl], i32),
             "ptca_set_resolve_margin": ([vp, dbl], i32),
+            "ptca_surrogate_param_count": ([], i32),
+            "ptca_surrogate_init": ([vp, ctypes.c_uint64, vp], i32),
+            "ptca_surrogate_get_params": ([vp, vp, P(ctypes.c_float), vp], i32),
+            "ptca_surrogate_set_params": ([vp, vp, ctypes.c_float, vp], i32),
+            "ptca_surrogate_collect": ([vp, i32, vp, vp, vp, vp], i32),
+            "ptca_surrogate_train": ([vp, vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_uint64, vp, vp], i32),
+            "ptca_surrogate_grad": ([vp, vp, vp, vp, i32, vp, vp, vp], i32),
+            "ptca_surrogate_predict": ([vp, vp, vp, i32, vp, vp], i32),
+            "ptca_surrogate_enable": ([vp, i32], i32),
             "ptca_selftest_barrier_timeout": ([i32, dbl, vp], i32),
         }
         for name, (args, res) in sig.items():
@@ -268,6 +282,47 @@ def ptca_set_pipeline(h, mode: int, barrier_timeout_s: float = 30.0) -> None:
 
 def ptca_set_resolve_margin(h, margin: float) -> None:
     _check(lib().ptca_set_resolve_margin(h, margin))
+
+
+def ptca_surrogate_param_count() -> int:
+    return lib().ptca_surrogate_param_count()
+
+
+def ptca_surrogate_init(h, seed: int = 0, stream=None) -> None:
+    _check(lib().ptca_surrogate_init(h, seed, _stream(stream)))
+
+
+def ptca_surrogate_get_params(h, theta, stream=None) -> float:
+    sc = ctypes.c_float()
+    _check(lib().ptca_surrogate_get_params(h, _ptr(theta), ctypes.byref(sc), _stream(stream)))
+    return sc.value
+
+
+def ptca_surrogate_set_params(h, theta, scale: float, stream=None) -> None:
+    _check(lib().ptca_surrogate_set_params(h, _ptr(theta), scale, _stream(stream)))
+
+
+def ptca_surrogate_collect(h, n_sweeps: int, feat, center, dF, stream=None) -> None:
+    _check(lib().ptca_surrogate_collect(h, n_sweeps, _ptr(feat), _ptr(center), _ptr(dF), _stream(stream)))
+
+
+def ptca_surrogate_train(h, feat, center, dF, n: int, steps: int, batch: int, lr: float, weight_decay: float,
+                         seed: int, loss_trace=None, stream=None) -> None:
+    _check(lib().ptca_surrogate_train(h, _ptr(feat), _ptr(center), _ptr(dF), n, steps, batch, lr, weight_decay, seed,
+                                      _ptr(loss_trace), _stream(stream)))
+
+
+def ptca_surrogate_grad(h, feat, center, dF, n: int, grad_out, loss_out, stream=None) -> None:
+    _check(lib().ptca_surrogate_grad(h, _ptr(feat), _ptr(center), _ptr(dF), n, _ptr(grad_out), _ptr(loss_out),
+                                     _stream(stream)))
+
+
+def ptca_surrogate_predict(h, feat, center, n: int, dF_out, stream=None) -> None:
+    _check(lib().ptca_surrogate_predict(h, _ptr(feat), _ptr(center), n, _ptr(dF_out), _stream(stream)))
+
+
+def ptca_surrogate_enable(h, on: bool) -> None:
+    _check(lib().ptca_surrogate_enable(h, int(bool(on))))
 
 
 def ptca_selftest_barrier_timeout(blocks: int, timeout_s: float, stream=None) -> int:
