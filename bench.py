@@ -210,6 +210,57 @@ def time_sweeps(ctx, steps, warmup, flush_buf, stream):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def surrogate_mode(P, base, args, flush, stream):
+    """Delayed acceptance with the surrogate network on the same workload: the
+    network is trained on (patch, dF) pairs from exact sweeps of this lattice
+    (collection and training untimed), then screened sweeps are timed."""
+    import torch
+    N = base["Lx"] * base["Ly"]
+    ctx = P.Context(P.Config(**base, precision=P.MIXED))
+    n = args.sg_sweeps * N
+    feat = torch.empty((n, 150), dtype=torch.float32, device="cuda")
+    center = torch.empty(n, dtype=torch.int32, device="cuda")
+    dF = torch.empty(n, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.ptca_surrogate_collect(ctx.h, args.sg_sweeps, feat, center, dF, stream=stream)
+    P.ptca_surrogate_init(ctx.h, 1, stream=stream)
+    loss = torch.empty(args.sg_train_steps, dtype=torch.float32, device="cuda")
+    P.ptca_surrogate_train(ctx.h, feat, center, dF, n, args.sg_train_steps, 512, 1e-3, 1e-4, 7, loss, stream=stream)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del feat, center, dF
+    P.ptca_surrogate_enable(ctx.h, True)
+    steps = max(3, args.steps // 2)
+    ms = time_sweeps(ctx, steps, 2, flush, stream)
+    st = P.ptca_sweep(ctx.h, steps, stats=True, stream=stream)
+    ctx.close()
+    return {"value": N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
+            "exact_eigensolves_per_update": st.eigensolves / st.attempts,
+            "screened_fraction": st.screened / st.attempts, "acceptance": st.accepted / st.attempts,
+            "train_pairs": n, "train_steps": args.sg_train_steps,
+            "train_loss_first_last": [float(loss[:20].mean()), float(loss[-100:].mean())],
+            "collect_and_train_s": t_train,
+            "note": "two-stage delayed acceptance (MLP screen, exact 8x8 cluster solve as judge); mixed guarded"}
+
+
+def uneven_mode(P, args, flush, stream, rank):
+    """316x316 open lattice, 10x10 clusters clipped at the edges (matrix
+    orders 50..200), J_H = 6, mu = -4.5, T = 0.1, sphere proposals, tiled
+    stride 10 (100 stages of 961..1024 clusters), mixed guarded."""
+    cfg = P.Config(Lx=316, Ly=316, L_c=10, periodic=0, t=1.0, J_H=6.0, mu=-4.5, T=0.1, seed=rank,
+                   schedule=P.SCHEDULE_TILED, stride=10, precision=P.MIXED, proposal=P.PROPOSAL_SPHERE)
+    ctx = P.Context(cfg)
+    P.ptca_set_pipeline(ctx.h, P.PIPELINE_GRAPH)
+    steps = 2
+    ms = time_sweeps(ctx, steps, 1, flush, stream)
+    st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
+    ctx.close()
+    return {"value": cfg.N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
+            "resolved_fraction": st.resolved / st.attempts, "acceptance": st.accepted / st.attempts,
+            "workload": "316x316 open, 10x10 clipped clusters (n=50..200), J_H=6, mu=-4.5, T=0.1, tiled s=10"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,6 +270,9 @@ def main():
     ap.add_argument("--schedule", default="block", choices=["block", "tiled10", "tiled5"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sg-sweeps", type=int, default=20, help="exact sweeps collected to train the surrogate")
+    ap.add_argument("--sg-train-steps", type=int, default=3000)
+    ap.add_argument("--no-extra", action="store_true", help="skip the surrogate and uneven-batch measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -272,11 +326,25 @@ def main():
     stats = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
     acc_rate = stats.accepted / stats.attempts
     resolved_frac = stats.resolved / stats.attempts
+    # Error of the FP32 reduction against FP64 on every visit of one sweep
+    # (precision checker; untimed).
+    P.ptca_set_checker(ctx.h, True)
+    P.ptca_sweep(ctx.h, 1, stats=False, stream=stream)
+    rows = P.ptca_checker_read(ctx.h, n_stages, stream=stream)
+    P.ptca_set_checker(ctx.h, False)
+    mixed_error = {"max_abs_eig": float(rows[:, 0].max()), "max_abs_dF": float(rows[:, 1].max()),
+                   "max_eig_over_JH_4t": float(rows[:, 2].max()), "max_dF_over_F": float(rows[:, 3].max()),
+                   "batches": int(n_stages), "note": "FP32-reduction vs FP64 solve of every visit of one sweep"}
     # Same context without the decision guard (pure mixed precision).
     P.ptca_set_resolve_margin(ctx.h, 0.0)
     ung_ms = time_sweeps(ctx, max(3, args.steps // 2), 2, flush, stream)
     unguarded_value = N * len(ung_ms) / (sum(ung_ms) * 1e-3)
     ctx.close()
+
+    extra = {}
+    if not args.no_extra:
+        extra["surrogate_da"] = surrogate_mode(P, base, args, flush, stream)
+        extra["uneven_open"] = uneven_mode(P, args, flush, stream, rank)
 
     # --- plain FP64 GPU path on the same workload
     ctx64 = P.Context(P.Config(**base, precision=P.FP64))
@@ -325,10 +393,12 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak, "traffic": None,
                          "note": "FP32 FMA pipe, Householder flops only; peak = 152 SM x 128 lanes x 2 x max clock"},
+            "mixed_error": mixed_error,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "wall_s_timed": t_wall,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
 
 

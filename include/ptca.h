@@ -222,6 +222,24 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  * ptca_sweep_stats.resolved.  Rejected (PTCA_ERR_INVALID) for PTCA_FP64. */
 ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin);
 
+/* Precision checker (PTCA_MIXED only; PTCA_ERR_UNSUPPORTED otherwise).  While
+ * on, every stage of ptca_sweep first solves both cluster matrices of each of
+ * its visits twice from the stage-start spins -- with the FP32 reduction the
+ * sweep uses and fully in FP64 -- and records per stage (per batch of
+ * concurrent clusters) the largest eigenvalue error max|eps32 - eps64| and
+ * free-energy-difference error max|dF32 - dF64|.  The chain itself is
+ * unchanged; sweeps run the per-stage pipeline while the checker is on. */
+ptca_status ptca_set_checker(ptca_ctx* ctx, int32_t on);
+
+/* Checker results since the last read (or since the checker was first turned
+ * on), then reset.  out: host array of n_rows x 4 doubles, n_rows >= the
+ * number of stages; row s = stage s: [0] max |d eps|, [1] max |d dF|,
+ * [2] max |d eps| / (J_H + 4|t|) (the spectral-norm bound of a cluster
+ * matrix), [3] max |d dF| / max(1, |F_old|, |F_new|).  Maxima over every
+ * sweep since the last read; a NaN anywhere reads as NaN.  Synchronises
+ * `stream`. */
+ptca_status ptca_checker_read(ptca_ctx* ctx, double* out, int32_t n_rows, void* stream);
+
 /* Per-visit record of the last sweep, in flattened stage order (length N):
  * update site, F_old, F_new, ln u and the decision (1 accepted).  Device
  * pointers; any of them may be NULL.  Stream-ordered. */

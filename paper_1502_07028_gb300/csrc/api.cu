@@ -170,7 +170,8 @@ static void free_ctx(ptca_ctx* c) {
     void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
                     c->d_rec_n, c->d_counters, c->d_err, c->d_obs, c->d_stage_start, c->d_perm, c->d_queue,
-                    c->d_bar, c->d_sweep_ctr, c->d_flag_list, c->d_flag_count, c->d_gA};
+                    c->d_bar, c->d_sweep_ctr, c->d_flag_list, c->d_flag_count, c->d_gA,
+                    c->d_chk_eig, c->d_chk_F, c->d_chk_out};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete c;
@@ -441,6 +442,26 @@ struct Collect {
     float* dF;
 };
 
+// Precision checker of one stage: every visit's two matrices solved with the
+// FP32 reduction and in FP64 from the stage-start spins, errors max-reduced
+// into the stage's row of d_chk_out.  Does not change the chain.
+static cudaError_t check_stage(ptca_ctx* ctx, const StageArgs& a, int s, cudaStream_t st) {
+    const int ld = ctx->nA, chunk = ctx->check_chunk;
+    double* e32 = ctx->d_chk_eig;
+    double* e64 = e32 + (size_t)chunk * 2 * ld;
+    double* F32 = ctx->d_chk_F;
+    double* F64 = F32 + 2 * (size_t)chunk;
+    cudaError_t e = cudaSuccess;
+    for (int c0 = 0; c0 < a.count && e == cudaSuccess; c0 += chunk) {
+        const int cnt = std::min(chunk, a.count - c0);
+        e = ptca::launch_check(1, a, c0, cnt, e32, ld, F32, 0, st);
+        if (e == cudaSuccess) e = ptca::launch_check(0, a, c0, cnt, e64, ld, F64, ctx->resolve_grid, st);
+        if (e == cudaSuccess)
+            e = ptca::launch_check_compare(a.m, a.sites + c0, cnt, e32, e64, ld, F32, F64, ctx->d_chk_out + 4 * s, st);
+    }
+    return e;
+}
+
 // One launch per stage (Sec. III.a stage = one kernel); with the surrogate
 // enabled each stage is screened first and only passing sites are solved.
 static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st, const Collect* col = nullptr) {
@@ -466,7 +487,8 @@ static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st
             a.perm = nullptr;
             a.count_dev = nullptr;
             a.sg_dFt = nullptr;
-            if (ctx->sg.enabled && !col) e = ptca_screen_stage(ctx, a, st);
+            if (ctx->checker) e = check_stage(ctx, a, s, st);
+            if (e == cudaSuccess && ctx->sg.enabled && !col) e = ptca_screen_stage(ctx, a, st);
             if (e == cudaSuccess) e = ptca::launch_stage(ctx->prec, a, st);
             if (e == cudaSuccess && a.margin > 0.0) {
                 e = ptca::launch_resolve(a, ctx->resolve_grid, st);
@@ -552,6 +574,50 @@ ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin) {
     return PTCA_OK;
 }
 
+ptca_status ptca_set_checker(ptca_ctx* ctx, int32_t on) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (!on) {
+        ctx->checker = false;
+        return PTCA_OK;
+    }
+    if (ctx->prec != 1) return fail(PTCA_ERR_UNSUPPORTED, "the precision checker compares PTCA_MIXED against FP64");
+    if (!ctx->d_chk_out) {
+        ctx->check_chunk = std::min(ctx->max_stage, 2048);
+        cudaError_t e = dalloc(&ctx->d_chk_eig, (size_t)2 * ctx->check_chunk * 2 * ctx->nA);
+        if (e == cudaSuccess) e = dalloc(&ctx->d_chk_F, (size_t)2 * ctx->check_chunk * 2);
+        if (e == cudaSuccess) e = dalloc(&ctx->d_chk_out, (size_t)4 * ctx->nstages);
+        if (e == cudaSuccess) e = cudaMemset(ctx->d_chk_out, 0, (size_t)4 * ctx->nstages * sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            cudaFree(ctx->d_chk_eig);
+            cudaFree(ctx->d_chk_F);
+            cudaFree(ctx->d_chk_out);
+            ctx->d_chk_eig = nullptr;
+            ctx->d_chk_F = nullptr;
+            ctx->d_chk_out = nullptr;
+            return cuda_fail(e, "ptca_set_checker");
+        }
+    }
+    ctx->checker = true;
+    return PTCA_OK;
+}
+
+ptca_status ptca_checker_read(ptca_ctx* ctx, double* out, int32_t n_rows, void* stream) {
+    if (!ctx || !out) return fail(PTCA_ERR_INVALID, "null argument");
+    if (n_rows < ctx->nstages) return fail(PTCA_ERR_INVALID, "out needs one row per stage");
+    if (!ctx->d_chk_out) {
+        for (int i = 0; i < 4 * ctx->nstages; ++i) out[i] = 0.0;
+        return PTCA_OK;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<unsigned long long> bits((size_t)4 * ctx->nstages);
+    PTCA_CUDA(cudaMemcpyAsync(bits.data(), ctx->d_chk_out, bits.size() * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, st));
+    PTCA_CUDA(cudaMemsetAsync(ctx->d_chk_out, 0, bits.size() * sizeof(unsigned long long), st));
+    PTCA_CUDA(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < bits.size(); ++i) std::memcpy(&out[i], &bits[i], sizeof(double));
+    return PTCA_OK;
+}
+
 ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_out, void* stream) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
     if (n_sweeps < 0) return fail(PTCA_ERR_INVALID, "n_sweeps < 0");
@@ -565,7 +631,7 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
     PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
     if (n_sweeps > 0) {
         cudaError_t e;
-        if (ctx->pipeline == PTCA_PIPELINE_STAGES || ctx->sg.enabled) e = sweep_stages(ctx, n_sweeps, st);
+        if (ctx->pipeline == PTCA_PIPELINE_STAGES || ctx->sg.enabled || ctx->checker) e = sweep_stages(ctx, n_sweeps, st);
         else if (ctx->pipeline == PTCA_PIPELINE_PERSISTENT || ctx->graph_failed) e = enqueue_persistent(ctx, n_sweeps, st);
         else e = sweep_graph(ctx, n_sweeps, st);
         if (e != cudaSuccess) return cuda_fail(e, "ptca_sweep");

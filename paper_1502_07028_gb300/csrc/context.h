@@ -90,6 +90,12 @@ struct ptca_ctx {
     double2* d_gA = nullptr;
     int64_t gA_stride = 0;
     int resolve_grid = 0;
+    // precision checker (PTCA_MIXED): FP32-vs-FP64 spectra of every visit
+    bool checker = false;
+    int check_chunk = 0;
+    double* d_chk_eig = nullptr;              // [2 precisions][check_chunk][2][nA]
+    double* d_chk_F = nullptr;                // [2 precisions][check_chunk][2]
+    unsigned long long* d_chk_out = nullptr;  // [nstages][4], bits of non-negative doubles
     // surrogate network for delayed-acceptance screening
     ptca::SurrogateState sg;
 };

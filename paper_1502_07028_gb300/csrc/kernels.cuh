@@ -218,6 +218,21 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_eigvals(const 
     tridiag_eig_F<T>(n, c, 0.0, 1.0, true, out, s1, s2, K);
 }
 
+struct StageArgs;
+
+// Precision checker: both matrices of visits c0 .. c0+count-1 of a stage
+// (item 2c: H_old of visit c0+c, item 2c+1: H_new with the proposed spin),
+// built from the stage-start spins and solved as a sweep solves them, except
+// that all n eigenvalues are returned: eig[(2c+var)*ld + k] ascending,
+// F[2c+var] = -T sum_k softplus(-(eps_k-mu)/T).  k_check: precision T, matrix
+// in shared memory, one item per CTA.  k_check_ref: FP64 with the matrix in
+// the CTA's global slot (as the FP64 re-solve), items grid-strided.
+template <typename T, int NT>
+__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_check(StageArgs a, int c0, int count, double* eig,
+                                                                          int ld, double* F);
+template <int NT>
+__global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int count, double* eig, int ld, double* F);
+
 // One PTCA stage (Sec. III.a): block 2c holds H_old of update site c, block
 // 2c+1 holds H_new with the proposed spin.  The second block to finish
 // applies Metropolis (Sec. II.c steps e-f) and writes the site's spin for the
@@ -368,6 +383,56 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArg
     const int count = a.count_dev ? (int)*a.count_dev : a.count;
     if (c >= count) return;
     stage_item<T, NT>(a, c, var, smem, s_new, &s_last);
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_check(StageArgs a, int c0, int count, double* eig,
+                                                                          int ld, double* F) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    const int c = blockIdx.x >> 1, var = blockIdx.x & 1;
+    if (c >= count) return;
+    const SmemLayout L = smem_layout(a.nA, 32 * NT, sizeof(cplx_t<T>));
+    Carve<T> cv = carve<T>(smem, L);
+    const int site = a.sites[c0 + c];
+    const Window w = make_window(a.m, site);
+    const int n = 2 * w.ex * w.ey;
+    if (threadIdx.x == 0 && var == 1)
+        propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, s_new);
+    __syncthreads();
+    build_cluster<T>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    __syncthreads();
+    householder_tridiag<T, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
+    double ssp, sfe;
+    int K;
+    tridiag_eig_F<T>(n, cv, a.m.mu, a.m.T, true, eig + (int64_t)(2 * c + var) * ld, ssp, sfe, K);
+    if (threadIdx.x == 0) F[2 * c + var] = -a.m.T * ssp;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int count, double* eig, int ld, double* F) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    const SmemLayout L = smem_layout(0, 32 * NT, sizeof(double2));
+    for (int item = blockIdx.x; item < 2 * count; item += gridDim.x) {
+        Carve<double> cv = carve<double>(smem, L);
+        cv.A = a.gA + (int64_t)blockIdx.x * a.gA_stride;
+        const int c = item >> 1, var = item & 1;
+        const int site = a.sites[c0 + c];
+        const Window w = make_window(a.m, site);
+        const int n = 2 * w.ex * w.ey;
+        if (threadIdx.x == 0 && var == 1)
+            propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, s_new);
+        __syncthreads();
+        build_cluster<double>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+        __syncthreads();
+        householder_tridiag<double, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
+        double ssp, sfe;
+        int K;
+        tridiag_eig_F<double>(n, cv, a.m.mu, a.m.T, true, eig + (int64_t)(2 * c + var) * ld, ssp, sfe, K);
+        if (threadIdx.x == 0) F[2 * c + var] = -a.m.T * ssp;
+        __syncthreads();
+    }
 }
 
 // FP64 re-solve of one matrix of a deferred update site (stage index c from

@@ -27,6 +27,8 @@ cudaError_t launch_persistent_f64(const PersistArgs&, int, cudaStream_t);
 int persistent_blocks_per_sm_f32(int);
 int persistent_blocks_per_sm_f64(int);
 cudaError_t launch_resolve_f32(const StageArgs&, int, cudaStream_t);
+cudaError_t launch_check_f32(const StageArgs&, int, int, double*, int, double*, cudaStream_t);
+cudaError_t launch_check_ref_f32(const StageArgs&, int, int, double*, int, double*, int, cudaStream_t);
 
 size_t cluster_smem_bytes(int prec, int nA) { return prec ? cluster_smem_bytes_f32(nA) : cluster_smem_bytes_f64(nA); }
 int cluster_max_order(int prec) { return prec ? cluster_max_order_f32() : cluster_max_order_f64(); }
@@ -55,6 +57,63 @@ cudaError_t launch_persistent(int prec, const PersistArgs& p, int grid, cudaStre
 cudaError_t launch_resolve(const StageArgs& a, int grid, cudaStream_t st) { return launch_resolve_f32(a, grid, st); }
 int persistent_blocks_per_sm(int prec, int nA) {
     return prec ? persistent_blocks_per_sm_f32(nA) : persistent_blocks_per_sm_f64(nA);
+}
+
+cudaError_t launch_check(int prec, const StageArgs& a, int c0, int count, double* eig, int ld, double* F, int grid,
+                         cudaStream_t st) {
+    return prec ? launch_check_f32(a, c0, count, eig, ld, F, st)
+                : launch_check_ref_f32(a, c0, count, eig, ld, F, grid, st);
+}
+
+// Non-negative doubles order like their bit patterns (NaN above +inf).
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double v) {
+    atomicMax(p, (unsigned long long)__double_as_longlong(fabs(v)));
+}
+
+// Errors of the FP32-reduction spectra (e32, F32) against the FP64 ones (e64,
+// F64) for `count` visits: out[0] max |d eps|, out[1] max |d dF|, out[2] max
+// |d eps| / (J_H + 4|t|) (the spectral-norm bound of every cluster matrix),
+// out[3] max |d dF| / max(1, |F_old|, |F_new|) (as bit patterns of
+// non-negative doubles).
+__global__ void k_check_compare(Model m, const int32_t* __restrict__ sites, int count, const double* __restrict__ e32,
+                                const double* __restrict__ e64, int ld, const double* __restrict__ F32,
+                                const double* __restrict__ F64, unsigned long long* out) {
+    const int c = blockIdx.x;
+    if (c >= count) return;
+    const Window w = make_window(m, sites[c]);
+    const int n = 2 * w.ex * w.ey;
+    double de = 0.0;
+    for (int var = 0; var < 2; ++var) {
+        const double* a = e32 + (int64_t)(2 * c + var) * ld;
+        const double* b = e64 + (int64_t)(2 * c + var) * ld;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const double d = fabs(a[k] - b[k]);
+            de = (d > de || d != d) ? d : de;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double x = __shfl_xor_sync(0xffffffffu, de, o);
+        de = (x > de || x != x) ? x : de;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(out, de);
+        atomic_max_nonneg(out + 2, de / (m.JH + 4.0 * fabs(m.t)));
+    }
+    if (threadIdx.x == 0) {
+        const double d64 = F64[2 * c + 1] - F64[2 * c];
+        const double d32 = F32[2 * c + 1] - F32[2 * c];
+        const double ddF = fabs(d32 - d64);
+        atomic_max_nonneg(out + 1, ddF);
+        atomic_max_nonneg(out + 3, ddF / fmax(1.0, fmax(fabs(F64[2 * c]), fabs(F64[2 * c + 1]))));
+    }
+}
+
+cudaError_t launch_check_compare(const Model& m, const int32_t* sites, int count, const double* e32,
+                                 const double* e64, int ld, const double* F32, const double* F64,
+                                 unsigned long long* out, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_check_compare<<<count, 128, 0, st>>>(m, sites, count, e32, e64, ld, F32, F64, out);
+    return cudaGetLastError();
 }
 
 __global__ void k_barrier_selftest(unsigned int* bar, int32_t* err, unsigned long long timeout_ns) {

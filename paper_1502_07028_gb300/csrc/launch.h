@@ -35,6 +35,14 @@ cudaError_t launch_persistent(int prec, const PersistArgs& p, int grid, cudaStre
 int persistent_blocks_per_sm(int prec, int nA);
 // FP64 re-solve of the decisions a PTCA_MIXED stage deferred (grid CTAs).
 cudaError_t launch_resolve(const StageArgs& a, int grid, cudaStream_t st);
+// Precision checker: spectra of visits c0 .. c0+count-1 of a stage (prec 1:
+// FP32 reduction as PTCA_MIXED sweeps; prec 0: FP64 on the global matrix
+// slots a.gA, grid CTAs), and their FP32-vs-FP64 errors reduced into out[4].
+cudaError_t launch_check(int prec, const StageArgs& a, int c0, int count, double* eig, int ld, double* F, int grid,
+                         cudaStream_t st);
+cudaError_t launch_check_compare(const Model& m, const int32_t* sites, int count, const double* e32,
+                                 const double* e64, int ld, const double* F32, const double* F64,
+                                 unsigned long long* out, cudaStream_t st);
 cudaError_t launch_barrier_selftest(int blocks, unsigned int* bar, int32_t* err, unsigned long long timeout_ns,
                                     cudaStream_t st);
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);

@@ -30,7 +30,7 @@ EXPORTED = [
     "ptca_sweep_noalloc", "ptca_set_pipeline", "ptca_selftest_barrier_timeout", "ptca_set_resolve_margin",
     "ptca_surrogate_param_count", "ptca_surrogate_init", "ptca_surrogate_get_params", "ptca_surrogate_set_params",
     "ptca_surrogate_collect", "ptca_surrogate_train", "ptca_surrogate_grad", "ptca_surrogate_predict",
-    "ptca_surrogate_enable",
+    "ptca_surrogate_enable", "ptca_set_checker", "ptca_checker_read",
 ]
 
 
@@ -106,6 +106,8 @@ def lib():
             "ptca_sweep_noalloc": ([P(Lattice), P(Params), vp, vp, i32, vp, i64, vp, vp, vp], i32),
             "ptca_set_pipeline": ([vp, i32, dbl], i32),
             "ptca_set_resolve_margin": ([vp, dbl], i32),
+            "ptca_set_checker": ([vp, i32], i32),
+            "ptca_checker_read": ([vp, vp, i32, vp], i32),
             "ptca_surrogate_param_count": ([], i32),
             "ptca_surrogate_init": ([vp, ctypes.c_uint64, vp], i32),
             "ptca_surrogate_get_params": ([vp, vp, P(ctypes.c_float), vp], i32),
@@ -282,6 +284,19 @@ def ptca_set_pipeline(h, mode: int, barrier_timeout_s: float = 30.0) -> None:
 
 def ptca_set_resolve_margin(h, margin: float) -> None:
     _check(lib().ptca_set_resolve_margin(h, margin))
+
+
+def ptca_set_checker(h, on: bool) -> None:
+    _check(lib().ptca_set_checker(h, 1 if on else 0))
+
+
+def ptca_checker_read(h, n_stages: int, stream=None):
+    """Per-stage precision-checker maxima since the last read: numpy array
+    (n_stages, 4) = |d eps|, |d dF|, |d eps|/(J_H+4|t|), |d dF|/max(1,|F|)."""
+    import numpy as np
+    out = np.zeros((n_stages, 4), dtype=np.float64)
+    _check(lib().ptca_checker_read(h, _ptr(out), n_stages, _stream(stream)))
+    return out
 
 
 def ptca_surrogate_param_count() -> int:

@@ -65,3 +65,94 @@ def test_guard_off_resolves_nothing_and_fp64_rejects_guard():
     with pytest.raises(P.PtcaError):
         P.ptca_set_resolve_margin(ctx.h, 1e-2)
     ctx.close()
+
+
+def _stage_of(stages, N):
+    out = np.zeros(N, dtype=np.int64)
+    for k, st in enumerate(stages):
+        out[st] = k
+    return out
+
+
+def test_checker_reports_each_stage_error_and_leaves_the_chain_alone():
+    # 32x32 torus, 8x8 clusters, tiled stride 8: 64 stages of 16 visits.
+    base = dict(Lx=32, Ly=32, L_c=8, stride=8, proposal=P.PROPOSAL_CONE, cone_deg=30.0, T=0.05, mu=-6.5, seed=5)
+    cfg = P.Config(**base, precision=P.MIXED)
+    stages = P.ptca_schedule(cfg)
+    ns = len(stages)
+    ctx = P.Context(cfg)
+    S0 = ctx.spins().clone()
+    P.ptca_set_checker(ctx.h, True)
+    ctx.sweep(1)
+    rows = P.ptca_checker_read(ctx.h, ns)
+    assert np.all(P.ptca_checker_read(ctx.h, ns) == 0.0)       # read resets
+    r32 = [x.cpu().numpy() for x in ctx.record()]
+    S_chk = ctx.spins().cpu().numpy()
+    # Eigenvalues of the stage-0 H_old matrices through the batch API, both precisions.
+    sites0 = torch.from_numpy(np.asarray(stages[0], dtype=np.int32))
+    ctx.set_spins(S0)
+    H, off, n = ctx.build_clusters(sites0)
+    e32, _ = ctx.cluster_eigvals(H, off, n)
+    ctx.close()
+    ctx64 = P.Context(P.Config(**base, precision=P.FP64))
+    P.ptca_set_pipeline(ctx64.h, P.PIPELINE_STAGES)
+    H, off, n = ctx64.build_clusters(sites0)
+    e64, _ = ctx64.cluster_eigvals(H, off, n)
+    ctx64.sweep(1)
+    r64 = [x.cpu().numpy() for x in ctx64.record()]
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_checker(ctx64.h, True)
+    ctx64.close()
+
+    assert rows.shape == (ns, 4) and np.all(np.isfinite(rows)) and np.all(rows[:, :2] > 0)
+    scale = cfg.J_H + 4 * cfg.t
+    assert np.all(rows[:, 2] <= 1e-5) and np.all(rows[:, 3] <= 2e-5), rows.max(axis=0)
+    assert np.allclose(rows[:, 2], rows[:, 0] / scale, rtol=1e-12)
+    # Stage 0 H_old eigenvalue errors are part of row 0's maximum.
+    assert float((e32 - e64).abs().max()) <= rows[0, 0] + 1e-11
+    # Per stage, the dF errors between the two sweeps' records (identical
+    # inputs: the guard keeps the decisions equal) are bounded by the row;
+    # over the sweep the largest of them is the largest row value.
+    site, Fo32, Fn32, _, acc32 = r32
+    _, Fo64, Fn64, _, acc64 = r64
+    assert np.array_equal(acc32, acc64)
+    d = np.abs((Fn32 - Fo32) - (Fn64 - Fo64))
+    st_of = _stage_of(stages, cfg.N)[site]
+    for s in range(ns):
+        assert d[st_of == s].max() <= rows[s, 1] + 1e-9
+    assert d.max() == pytest.approx(rows[:, 1].max(), rel=1e-6, abs=1e-9)
+    # The chain with the checker on equals the chain without it.
+    ctx = P.Context(cfg)
+    ctx.sweep(1)
+    assert np.array_equal(ctx.spins().cpu().numpy(), S_chk)
+    ctx.close()
+
+
+def test_checker_on_uneven_open_batches():
+    # 40x40 open lattice, 10x10 clusters clipped at the edges (n = 50 .. 200):
+    # the FP64 side runs on the global-memory path; pin it at a few stage-0
+    # windows against the oracle's Jacobi spectra.
+    import oracle
+    base = dict(Lx=40, Ly=40, L_c=10, periodic=0, stride=10, J_H=6.0, mu=-4.5, T=0.1, seed=6)
+    cfg = P.Config(**base, precision=P.MIXED)
+    stages = P.ptca_schedule(cfg)
+    ctx = P.Context(cfg)
+    S0 = ctx.spins().cpu().numpy()
+    P.ptca_set_checker(ctx.h, True)
+    ctx.sweep(1)
+    rows = P.ptca_checker_read(ctx.h, len(stages))
+    s0 = np.asarray(stages[0], dtype=np.int32)
+    ctx.set_spins(S0)
+    H, off, n = ctx.build_clusters(torch.from_numpy(s0))
+    e32, _ = ctx.cluster_eigvals(H, off, n)
+    ctx.close()
+    assert np.all(np.isfinite(rows)) and np.all(rows[:, 0] > 0)
+    assert np.all(rows[:, 2] <= 1e-5) and np.all(rows[:, 3] <= 2e-5), rows.max(axis=0)
+    m = oracle.Model(Lx=40, Ly=40, Lc=10, lattice_periodic=0, JH=6.0, mu=-4.5, T=0.1, seed=6, stride=10)
+    ncount = n.cpu().numpy()
+    for k in np.argsort(ncount)[[0, len(ncount) // 2, -1]]:
+        ref = oracle.eigvalsh(oracle.cluster_hamiltonian(m, S0, int(s0[k]))[0])
+        err = np.max(np.abs(e32[k, : ncount[k]].cpu().numpy() - ref))
+        # FP32-vs-oracle error of H_old is within the row's FP32-vs-FP64
+        # maximum plus the FP64 path's own 1e-9 parity bound.
+        assert err <= rows[0, 0] + 1e-9 * (6.0 + 4.0), (k, ncount[k], err, rows[0, 0])
