@@ -36,6 +36,11 @@ N_ORDER = 128
 # triangle once with 16 real FMA per complex element (rank-2 update + both
 # halves of the Hermitian matrix-vector product): sum_m 32 m(m+1)/2 ~ (16/3) n^3.
 HH_FLOPS = sum(32 * m * (m + 1) // 2 for m in range(1, N_ORDER))
+# DRAM bytes (read + write) of one launch of the persistent mixed sweep kernel
+# on this workload, from the ncu capture summarised in
+# profiles/k_sweep_persistent_f32_100x100_Lc8_mixed.md.  Set to None whenever
+# that kernel changes until it is captured again.
+PERSISTENT_F32_DRAM_BYTES = 1_381_376 + 8_094_720
 
 
 def peaks():
@@ -391,7 +396,7 @@ def main():
             "eigensolves_per_s": 2 * value,
             "acceptance": acc_rate,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak, "traffic": None,
+                         "frac": achieved_tflops / peak, "traffic": PERSISTENT_F32_DRAM_BYTES,
                          "note": "FP32 FMA pipe, Householder flops only; peak = 152 SM x 128 lanes x 2 x max clock"},
             "mixed_error": mixed_error,
             "cpu_baseline": cpu,
