@@ -144,7 +144,7 @@ __global__ void k_batch_indices(uint64_t seed, uint64_t step, int Bsz, long long
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= Bsz) return;
     double u0, u1;
-    uniform2(seed, step, (uint32_t)b, 16u, u0, u1);
+    uniform2(seed, step, (uint32_t)b, RNG_BATCH, u0, u1);
     long long s = (long long)(u0 * (double)nsamples);
     idx[b] = s < nsamples ? s : nsamples - 1;
 }
@@ -236,7 +236,7 @@ __global__ void k_init_params(float* theta, uint64_t seed) {
     else if (i >= SG_OFF_W4 && i < SG_OFF_W4 + SG_H) sd = sqrtf(1.f / SG_H);
     if (sd > 0.f) {
         double u0, u1;
-        uniform2(seed, 0, (uint32_t)i, 17u, u0, u1);
+        uniform2(seed, 0, (uint32_t)i, RNG_PARAM, u0, u1);
         v = sd * (float)(sqrt(-2.0 * log(u0)) * cos(2.0 * kPi * u1));
     }
     theta[i] = v;
