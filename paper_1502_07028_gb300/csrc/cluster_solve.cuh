@@ -466,22 +466,16 @@ __device__ __forceinline__ int newton_pass_f64(int n, const double* d, const dou
     return c;
 }
 
-// k-th smallest eigenvalue (0-based), all FP64: bisection down to a bracket
-// of width ~1e-6 ||T||, then Newton on det(T - x) while the bracket holds
-// exactly this one eigenvalue (bisection otherwise, and whenever a Newton
-// step would leave the bracket or fails to halve it).  Every pass tightens
-// the bracket with its Sturm count.
-__device__ __forceinline__ double eig_f64(int n, const double* d, const double* e2, int k, double lo, double hi,
-                                          double pivmin, double nrm) {
-    const double coarse = 1e-6 * nrm;
-    int clo = 0, chi = n;
-    for (int it = 0; it < 64 && hi - lo > coarse; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        const int c = sturm_count_f64(n, d, e2, mid, pivmin);
-        if (c <= k) { lo = mid; clo = c; } else { hi = mid; chi = c; }
-    }
+// Safeguarded Newton on det(T - x) for the k-th smallest eigenvalue (0-based)
+// inside [lo, hi], whose Sturm counts are clo <= k < chi, starting at x: a
+// Newton step is taken while the bracket holds exactly this one eigenvalue
+// and the step stays inside it and at least halves the previous width;
+// otherwise the bracket is bisected.  Every pass tightens the bracket with
+// its Sturm count.
+__device__ __forceinline__ double eig_f64_newton(int n, const double* d, const double* e2, int k, double lo, double hi,
+                                                 int clo, int chi, double x, double pivmin, double nrm) {
     const double tol = 2.0 * DBL_EPSILON * nrm;
-    double x = 0.5 * (lo + hi), width_before = hi - lo;
+    double width_before = hi - lo;
     for (int it = 0; it < 96 && hi - lo > tol; ++it) {
         double s;
         const int c = newton_pass_f64(n, d, e2, x, pivmin, s);
@@ -498,6 +492,37 @@ __device__ __forceinline__ double eig_f64(int n, const double* d, const double* 
         if (chi - clo == 1 && step <= tol) break;
     }
     return x;
+}
+
+// k-th smallest eigenvalue, all FP64: bisection from the Gershgorin bracket
+// down to a width of ~1e-6 ||T||, then safeguarded Newton.
+__device__ __forceinline__ double eig_f64(int n, const double* d, const double* e2, int k, double lo, double hi,
+                                          double pivmin, double nrm) {
+    const double coarse = 1e-6 * nrm;
+    int clo = 0, chi = n;
+    for (int it = 0; it < 64 && hi - lo > coarse; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        const int c = sturm_count_f64(n, d, e2, mid, pivmin);
+        if (c <= k) { lo = mid; clo = c; } else { hi = mid; chi = c; }
+    }
+    return eig_f64_newton(n, d, e2, k, lo, hi, clo, chi, 0.5 * (lo + hi), pivmin, nrm);
+}
+
+// k-th smallest eigenvalue in FP64 from the FP32 multisection bracket
+// [blo, bhi] of the FP32-rounded (d, e2).  Rounding the entries to FP32 and
+// the FP32 Sturm counts move an eigenvalue by a few FP32 ulps of ||T||
+// (Weyl's bound on the perturbation), so the bracket is widened by `margin`
+// and confirmed with two FP64 Sturm counts before safeguarded Newton
+// finishes it; if the confirmation fails the full FP64 bisection runs.
+__device__ __forceinline__ double eig_f64_bracketed(int n, const double* d, const double* e2, int k, float blo,
+                                                    float bhi, double margin, double lo, double hi, double pivmin,
+                                                    double nrm) {
+    const double a = fmax((double)blo - margin, lo), b = fmin((double)bhi + margin, hi);
+    const int ca = sturm_count_f64(n, d, e2, a, pivmin);
+    const int cb = sturm_count_f64(n, d, e2, b, pivmin);
+    if (a < b && ca <= k && cb > k)
+        return eig_f64_newton(n, d, e2, k, a, b, ca, cb, 0.5 * ((double)blo + (double)bhi), pivmin, nrm);
+    return eig_f64(n, d, e2, k, lo, hi, pivmin, nrm);
 }
 
 // One FP64 Newton correction of an eigenvalue located by FP32 multisection

@@ -69,8 +69,10 @@ __device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout&
 // eigenvalues with index < K (all when all_eigs, else those below
 // mu + 40 T), one thread per eigenvalue, and returns through eig (if not
 // null, global) and the block sums of softplus(-(eps-mu)/T) and of the Fermi
-// function.  T == float selects FP32 bisection + one FP64 Newton step; T ==
-// double selects FP64 bisection.
+// function.  Both precisions first bracket every eigenvalue by FP32
+// multisection on the FP32-rounded (d, e2); T == float then takes one FP64
+// Newton step, T == double confirms the widened bracket with FP64 Sturm
+// counts and refines it by safeguarded FP64 Newton to full precision.
 template <typename T>
 __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool all_eigs, double* eig,
                               double& sum_sp, double& sum_fermi, int& n_solved) {
@@ -117,7 +119,7 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
     const int K = s_K;
     const double lo = s_lo, hi = s_hi, pivmin = s_pivmin;
     const double nrm = fmax(fabs(lo), fabs(hi));
-    if constexpr (sizeof(T) == 4) {
+    {
         // FP32 multisection: G threads per eigenvalue evaluate G interior
         // points per round, narrowing the bracket (G+1)-fold.
         int G = 1;
@@ -125,8 +127,13 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
         const int k = tid / G, j = tid % G;
         const float lof = (float)lo * (lo < 0 ? 1.0000002f : 0.9999998f) - 1e-30f;
         const float hif = (float)hi * (hi > 0 ? 1.0000002f : 0.9999998f) + 1e-30f;
-        const float atolf = 2.0f * FLT_EPSILON * (float)nrm;
-        const int rounds = (int)ceilf(log2f((hif - lof) / atolf) / log2f((float)(G + 1))) + 1;
+        // Bracket tolerance, floored so that a zero matrix (nrm = 0) still
+        // gives a finite round count; the count is also capped (64 rounds
+        // narrow any float bracket below one ulp even for G = 1).
+        const float atolf = fmaxf(2.0f * FLT_EPSILON * (float)nrm, 1e-30f);
+        const float ratio = (hif - lof) / atolf;
+        int rounds = ratio > 1.0f ? (int)ceilf(log2f(ratio) / log2f((float)(G + 1))) + 1 : 1;
+        rounds = rounds < 64 ? rounds : 64;
         if ((warp * 32) / G < K) {
             float a = lof, b = hif;
             const unsigned gmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
@@ -150,7 +157,8 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
     if (k < K) {
         double lam;
         if constexpr (sizeof(T) == 8) {
-            lam = eig_f64(n, c.d, c.e2, k, lo, hi, pivmin, nrm);
+            lam = eig_f64_bracketed(n, c.d, c.e2, k, c.lam[2 * k], c.lam[2 * k + 1], 8.0 * FLT_EPSILON * nrm, lo, hi,
+                                    pivmin, nrm);
         } else {
             lam = newton_polish_f64(n, c.d, c.e2, c.lam[2 * k], c.lam[2 * k + 1], 2.0f * FLT_EPSILON * (float)nrm,
                                     pivmin);
