@@ -121,6 +121,14 @@ __device__ void build_cluster(const Model& m, const Window& w, const double* __r
 // warp processes its rows in batches of 8; the 8 row sums are
 // reduce-scattered across the warp.  Column (transposed) contributions
 // accumulate per lane and are summed across warps through shared memory.
+//
+// Between passes every vector entry has its own thread (relative index ri =
+// threadIdx.x), so the per-step scalar work -- combining the partial sums of
+// p = tau A v, the reduction v^H p, w, the explicit update of the pivot
+// column, ||x||^2 and the next reflector -- is spread over the whole CTA with
+// three barriers per step.  The first entry of each reflector (x_0 +
+// phase(x_0) ||x||) is kept in registers by every thread; the other entries
+// live in shared memory.
 // ---------------------------------------------------------------------------
 template <typename T> struct HHScratch {
     cplx_t<T>* Vb;   // 2 x NMAX   Householder vectors of consecutive steps
@@ -129,6 +137,7 @@ template <typename T> struct HHScratch {
     cplx_t<T>* pc;   // NW x NMAX  column sums of A v, per warp
     T* redA;         // NW
     T* redB;         // NW
+    cplx_t<T>* sx;   // 3 scalars: x0 of the next reflector, its first entry, (tau, 0)
 };
 
 template <typename V>
@@ -175,10 +184,34 @@ __device__ __forceinline__ V reduce_scatter4(const V (&v)[4], int lane) {
     return w1;  // row (lane >> 3) & 3 of the batch
 }
 
+// Sum over the warps of a per-warp partial (red has NW slots; the caller
+// synchronises between the write and the read).
+template <typename T, int NW>
+__device__ __forceinline__ T sum_partials(const T* red) {
+    T s = red[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) s += red[w];
+    return s;
+}
+
+// Next reflector from the updated pivot column: given ||x||^2 (s2) and x_0,
+// its first entry x_0 + phase(x_0) ||x|| and tau = 1 / (||x|| (||x|| + |x_0|)).
+template <typename T>
+__device__ __forceinline__ void reflector_head(T s2, cplx_t<T> x0, cplx_t<T>& first, T& tau) {
+    const T sigma = sqroot(s2);
+    const T ax0 = sqroot(cabs2(x0));
+    const cplx_t<T> ph = ax0 > T(0) ? mk(x0.x / ax0, x0.y / ax0) : mk(T(1), T(0));
+    first = mk(x0.x + ph.x * sigma, x0.y + ph.y * sigma);
+    tau = sigma > T(0) ? T(1) / (sigma * (sigma + ax0)) : T(0);
+}
+
 template <typename T, int NT, int NW>
 __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc, double* d, double* e2) {
     using V = cplx_t<T>;
     constexpr int NMAX = 32 * NT;
+    // The scalar tail (two square roots, divisions) is recomputed by every
+    // thread in FP32; in FP64 one warp computes it and shares it.
+    constexpr bool kSharedTail = sizeof(T) == 8;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     V* const Vb = sc.Vb;
     V* const Wv = sc.Wv;
@@ -199,36 +232,32 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
         return;
     }
 
-    // Column 0 (warp 0): d_0, ||x||^2 and the first reflector.  tau lives in
-    // warp 0's registers; only warp 0 uses it.
-    T tau = T(0);
-    if (warp == 0) {
-        V a[NT];
-        T s2 = T(0);
-#pragma unroll
-        for (int q = 0; q < NT; ++q) {
-            const int i = lane + 32 * q;
-            a[q] = i < n ? A[tri(i)] : zero;
-            if (i >= 1 && i < n) s2 += cabs2(a[q]);
+    // Column 0: d_0, ||x||^2 and the first reflector v_0 (entries 1 .. n-1;
+    // entry 1 in registers, the rest in Vb[0 .. NMAX)).
+    V vfirst;
+    T tau;
+    {
+        const int ri = tid;
+        T s2p = T(0);
+        if (ri < n) {
+            const V a = A[tri(ri)];
+            if (ri == 0) d[0] = double(a.x);
+            if (ri >= 1) s2p = cabs2(a);
+            if (ri >= 2) Vb[ri] = a;
+            if (ri == 1) sc.sx[0] = a;
         }
-        s2 = warp_sum(s2);
-        const T sigma = sqroot(s2);
-        const V x0 = mk(__shfl_sync(FULL_MASK, a[0].x, 1), __shfl_sync(FULL_MASK, a[0].y, 1));
-        const T ax0 = sqroot(cabs2(x0));
-        if (lane == 0) { d[0] = double(a[0].x); e2[0] = double(s2); }
-        const V ph = ax0 > T(0) ? mk(x0.x / ax0, x0.y / ax0) : mk(T(1), T(0));
-#pragma unroll
-        for (int q = 0; q < NT; ++q) {
-            const int i = lane + 32 * q;
-            if (i >= 1 && i < n) Vb[i] = (i == 1) ? mk(x0.x + ph.x * sigma, x0.y + ph.y * sigma) : a[q];
-        }
-        tau = sigma > T(0) ? T(1) / (sigma * (sigma + ax0)) : T(0);
+        s2p = warp_sum(s2p);
+        if (lane == 0) sc.redB[warp] = s2p;
+        __syncthreads();
+        const T s2 = sum_partials<T, NW>(sc.redB);
+        if (tid == 0) e2[0] = double(s2);
+        reflector_head(s2, sc.sx[0], vfirst, tau);
     }
-    __syncthreads();
 
     for (int k = 0; k <= n - 3; ++k) {
-        const V* V_ = Vb + (k & 1) * NMAX;        // v_k
+        const V* V_ = Vb + (k & 1) * NMAX;        // v_k (entry k+1 is vfirst)
         const V* U_ = Vb + ((k + 1) & 1) * NMAX;  // v_{k-1} (zero at k = 0)
+        V* Vn = Vb + ((k + 1) & 1) * NMAX;        // v_{k+1}, written once U_ is consumed
         const int j0 = k + 1;                     // first active row/column
 
         // ---- fused pass: A <- A - u w^H - w u^H (step k-1), accumulate A v_k.
@@ -251,6 +280,7 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
             wc[t] = in ? Wv[j] : zero;
             cacc[t] = zero;
         }
+        if (lane == 0) vc[0] = vfirst;
         for (int round = 0;; ++round) {
             // Heaviest batches first, snake order over the warps.
             const int slot = round * NW + ((round & 1) ? (NW - 1 - warp) : warp);
@@ -270,6 +300,7 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
                 base[r] = ok ? tri(i) + j0 : 0;
                 racc[r] = zero;
             }
+            if (ri0 == 0) vi[0] = vfirst;
             const int last = (ri0 + RB - 1 < m ? ri0 + RB - 1 : m - 1);
             const int nch = (last >> 5) + 1;
             const bool full_rows = ri0 + RB - 1 < m;
@@ -325,66 +356,70 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
         }
         __syncthreads();
 
-        // ---- warp 0: p = tau A v, s = v^H p, w = p - (tau s/2) v, explicit
-        // update of pivot column k+1, ||x||^2 and the next reflector.
-        if (warp == 0) {
-            V pq[NT], vq[NT], aq[NT];
+        // ---- p = tau A v (thread ri combines the row and per-warp column
+        // partial sums of entry ri) and the partial sums of v^H p.
+        const int ri = tid;
+        const bool mine = ri < m;
+        V v = zero, p = zero;
+        {
             T sp = T(0);
+            if (mine) {
+                p = pr[ri];
 #pragma unroll
-            for (int q = 0; q < NT; ++q) {
-                const int ri = lane + 32 * q;
-                V p = zero, v = zero;
-                if (ri < m) {
-                    p = pr[ri];
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) p = cadd(p, pc[w * NMAX + ri]);
-                    p.x *= tau; p.y *= tau;
-                    v = V_[j0 + ri];
-                }
-                pq[q] = p; vq[q] = v;
-                sp += v.x * p.x + v.y * p.y;
+                for (int w = 0; w < NW; ++w) p = cadd(p, pc[w * NMAX + ri]);
+                p.x *= tau; p.y *= tau;
+                v = ri == 0 ? vfirst : V_[j0 + ri];
+                pr[ri] = p;
+                sp = v.x * p.x + v.y * p.y;
             }
-            const T K = T(0.5) * tau * warp_sum(sp);
-            // w_{k+1} and v_{k+1} entries of the pivot row (relative index 0).
-            const V w0 = mk(__shfl_sync(FULL_MASK, pq[0].x - K * vq[0].x, 0),
-                            __shfl_sync(FULL_MASK, pq[0].y - K * vq[0].y, 0));
-            const V v0 = mk(__shfl_sync(FULL_MASK, vq[0].x, 0), __shfl_sync(FULL_MASK, vq[0].y, 0));
-            T s2 = T(0);
-#pragma unroll
-            for (int q = 0; q < NT; ++q) {
-                const int ri = lane + 32 * q;
-                V a = zero;
-                if (ri < m) {
-                    const V w = mk(pq[q].x - K * vq[q].x, pq[q].y - K * vq[q].y);
-                    Wv[j0 + ri] = w;
-                    V* ap = A + tri(j0 + ri) + j0;
-                    a = *ap;
-                    a = cfms_conj_b(vq[q], w0, a);
-                    a = cfms_conj_b(w, v0, a);
-                    if (ri == 0) { a.y = T(0); d[j0] = double(a.x); }
-                    *ap = a;
-                    if (ri >= 1) s2 += cabs2(a);
-                }
-                aq[q] = a;
-            }
-            s2 = warp_sum(s2);
-            if (lane == 0) e2[j0] = double(s2);
-            if (k + 1 <= n - 3) {
-                V* Vn = Vb + ((k + 1) & 1) * NMAX;
-                const T sigma = sqroot(s2);
-                const V x0 = mk(__shfl_sync(FULL_MASK, aq[0].x, 1), __shfl_sync(FULL_MASK, aq[0].y, 1));
-                const T ax0 = sqroot(cabs2(x0));
-                const V ph = ax0 > T(0) ? mk(x0.x / ax0, x0.y / ax0) : mk(T(1), T(0));
-#pragma unroll
-                for (int q = 0; q < NT; ++q) {
-                    const int ri = lane + 32 * q;
-                    if (ri >= 1 && ri < m)
-                        Vn[j0 + ri] = (ri == 1) ? mk(x0.x + ph.x * sigma, x0.y + ph.y * sigma) : aq[q];
-                }
-                tau = sigma > T(0) ? T(1) / (sigma * (sigma + ax0)) : T(0);
-            }
+            sp = warp_sum(sp);
+            if (lane == 0) sc.redA[warp] = sp;
         }
         __syncthreads();
+
+        // ---- w = p - (tau s / 2) v, the explicit update of pivot column
+        // j0 with (v_k, w_k), d_j0, and the partial sums of ||x||^2 for the
+        // next reflector, whose entries past the first go to Vn.
+        {
+            const T K = T(0.5) * tau * sum_partials<T, NW>(sc.redA);
+            const V p0 = pr[0];
+            const V w0 = mk(p0.x - K * vfirst.x, p0.y - K * vfirst.y);
+            T s2p = T(0);
+            if (mine) {
+                const V w = mk(p.x - K * v.x, p.y - K * v.y);
+                Wv[j0 + ri] = w;
+                V a = A[tri(j0 + ri) + j0];
+                a = cfms_conj_b(v, w0, a);
+                a = cfms_conj_b(w, vfirst, a);
+                if (ri == 0) d[j0] = double(a.x);
+                if (ri >= 1) s2p = cabs2(a);
+                if (ri >= 2) Vn[j0 + ri] = a;
+                if (ri == 1) sc.sx[0] = a;
+            }
+            s2p = warp_sum(s2p);
+            if (lane == 0) sc.redB[warp] = s2p;
+        }
+        __syncthreads();
+
+        // ---- ||x||^2, and the next reflector's first entry and tau.
+        if constexpr (kSharedTail) {
+            if (warp == 0) {
+                const T s2 = sum_partials<T, NW>(sc.redB);
+                if (lane == 0) e2[j0] = double(s2);
+                if (k + 1 <= n - 3) {
+                    V f;
+                    T tn;
+                    reflector_head(s2, sc.sx[0], f, tn);
+                    if (lane == 0) { sc.sx[1] = f; sc.sx[2] = mk(tn, T(0)); }
+                }
+            }
+            __syncthreads();
+            if (k + 1 <= n - 3) { vfirst = sc.sx[1]; tau = sc.sx[2].x; }
+        } else {
+            const T s2 = sum_partials<T, NW>(sc.redB);
+            if (tid == 0) e2[j0] = double(s2);
+            if (k + 1 <= n - 3) reflector_head(s2, sc.sx[0], vfirst, tau);
+        }
     }
 
     // Step n-3's update of the last diagonal entry.
@@ -480,16 +515,17 @@ __device__ __forceinline__ double eig_f64_newton(int n, const double* d, const d
         double s;
         const int c = newton_pass_f64(n, d, e2, x, pivmin, s);
         if (c <= k) { lo = x; clo = c; } else { hi = x; chi = c; }
-        const double mid = 0.5 * (lo + hi);
-        double xn = mid;
+        double xn = 0.5 * (lo + hi);
         if (chi - clo == 1 && s != 0.0 && isfinite(s)) {
             const double cand = x - 1.0 / s;
+            // A step below the tolerance means convergence: once x has
+            // converged it is itself a bracket end, so the candidate can no
+            // longer lie strictly inside and must not trigger a bisection.
+            if (fabs(cand - x) <= tol) return fmin(fmax(cand, lo), hi);
             if (cand > lo && cand < hi && 2.0 * fabs(cand - x) <= width_before) xn = cand;
         }
-        const double step = fabs(xn - x);
         width_before = hi - lo;
         x = xn;
-        if (chi - clo == 1 && step <= tol) break;
     }
     return x;
 }

@@ -36,7 +36,7 @@ __host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs) 
     L.e2f = o; o = align16(o + (size_t)nmaxc * sizeof(float));
     L.sp = o;  o = align16(o + (size_t)(nmaxc / 2) * 3 * sizeof(double));
     L.lam = o; o = align16(o + (size_t)nmaxc * 2 * sizeof(float));
-    L.red = o; o = align16(o + 4 * (size_t)NW * sizeof(double));
+    L.red = o; o = align16(o + 6 * (size_t)NW * sizeof(double));
     L.total = o;
     return L;
 }
@@ -56,6 +56,7 @@ __device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout&
     c.red = reinterpret_cast<double*>(base + L.red);
     c.hh.redA = reinterpret_cast<T*>(base + L.red);
     c.hh.redB = reinterpret_cast<T*>(base + L.red + 2 * NW * sizeof(double));
+    c.hh.sx = reinterpret_cast<cplx_t<T>*>(base + L.red + 4 * NW * sizeof(double));
     c.d = reinterpret_cast<double*>(base + L.d);
     c.e2 = reinterpret_cast<double*>(base + L.e2);
     c.df = reinterpret_cast<float*>(base + L.df);
