@@ -10,6 +10,7 @@
 
 #include <cfloat>
 #include "device_common.cuh"
+#include "dfloat.cuh"
 
 namespace ptca {
 

@@ -444,28 +444,30 @@ __global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int c
     }
 }
 
-// FP64 re-solve of one matrix of a deferred update site (stage index c from
-// the flag list): the matrix lives in this CTA's global slot, the reduction
-// and eigenvalues run in FP64, and the second of the pair decides (no
-// margin test).  nmaxc = 32 * NT sizes the FP64 vectors in shared memory.
+// Re-solve of one matrix of a deferred update site (stage index c from the
+// flag list) at FP64-class precision: the matrix lives in this CTA's global
+// slot and is built and reduced in double-float arithmetic (about 48
+// significant bits on the FP32 pipe), the eigenvalues of the resulting
+// tridiagonal run in FP64, and the second of the pair decides (no margin
+// test).  nmaxc = 32 * NT sizes the vectors in shared memory.
 template <int NT>
 __device__ __noinline__ void resolve_item(const StageArgs& a, int c, int var, unsigned char* smem, double* s_new,
                                           int* s_last) {
-    const SmemLayout L = smem_layout(0, 32 * NT, sizeof(double2));
-    Carve<double> cv = carve<double>(smem, L);
-    cv.A = a.gA + (int64_t)blockIdx.x * a.gA_stride;
+    const SmemLayout L = smem_layout(0, 32 * NT, sizeof(dfl2));
+    Carve<dfl> cv = carve<dfl>(smem, L);
+    cv.A = reinterpret_cast<dfl2*>(a.gA + (int64_t)blockIdx.x * a.gA_stride);
     const int site = a.sites[c];
     const Window w = make_window(a.m, site);
     const int n = 2 * w.ex * w.ey;
     if (threadIdx.x == 0 && var == 1)
         propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, s_new);
     __syncthreads();
-    build_cluster<double>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    build_cluster<dfl>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     __syncthreads();
-    householder_tridiag<double, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
+    householder_tridiag<dfl, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
-    tridiag_eig_F<double>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
+    tridiag_eig_F<dfl>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
     if (threadIdx.x == 0) {
         a.Fbuf[2 * c + var] = -a.m.T * ssp;
         a.fillbuf[2 * c + var] = sfe;
