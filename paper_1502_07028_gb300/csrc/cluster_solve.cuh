@@ -575,6 +575,114 @@ __device__ __forceinline__ double newton_polish_f64(int n, const double* d, cons
     return x;
 }
 
+// ---------------------------------------------------------------------------
+// The same refinements in double-float arithmetic: FP64-class precision on
+// the FP32 pipe.  The tridiagonal is given as float pairs (dh + dl, eh + el),
+// exact copies of the FP64 entries; the pivot guard uses the FP32 pivmin.
+// ---------------------------------------------------------------------------
+
+// 1/q: the float reciprocal r1 and one Newton correction r1 (1 + e),
+// e = 1 - q r1 evaluated with the FMA error of q.hi r1.
+__device__ __forceinline__ dfl rcp_df(dfl q) {
+    const float r1 = __frcp_rn(q.hi);
+    const float p = __fmul_rn(q.hi, r1);
+    float e = __fsub_rn(1.f, p);
+    e = __fsub_rn(e, __fmaf_rn(q.hi, r1, -p));
+    e = __fmaf_rn(-q.lo, r1, e);
+    return fast_two_sum(r1, __fmul_rn(r1, e));
+}
+
+__device__ __forceinline__ dfl pivot_guard(dfl q, float pivmin) {
+    return fabsf(q.hi) < pivmin ? dfl(-pivmin, 0.f) : q;
+}
+
+__device__ __forceinline__ int sturm_count_df(int n, const float* dh, const float* dl, const float* eh,
+                                              const float* el, dfl x, float pivmin) {
+    dfl q = pivot_guard(dfl(dh[0], dl[0]) - x, pivmin);
+    int c = q.hi < 0.f;
+    for (int i = 1; i < n; ++i) {
+        q = pivot_guard((dfl(dh[i], dl[i]) - x) - dfl(eh[i - 1], el[i - 1]) * rcp_df(q), pivmin);
+        c += q.hi < 0.f;
+    }
+    return c;
+}
+
+// Sturm count and logarithmic derivative of det(T - x), as newton_pass_f64.
+__device__ __forceinline__ int newton_pass_df(int n, const float* dh, const float* dl, const float* eh,
+                                              const float* el, dfl x, float pivmin, double& s) {
+    dfl q = pivot_guard(dfl(dh[0], dl[0]) - x, pivmin);
+    dfl dq = dfl(-1.f, 0.f), acc = dfl(0.f, 0.f);
+    int c = q.hi < 0.f;
+    for (int i = 1; i < n; ++i) {
+        const dfl r = rcp_df(q);
+        acc = acc + dq * r;
+        const dfl er = dfl(eh[i - 1], el[i - 1]) * r;
+        const dfl qn = (dfl(dh[i], dl[i]) - x) - er;
+        dq = er * r * dq - dfl(1.f, 0.f);
+        q = pivot_guard(qn, pivmin);
+        c += q.hi < 0.f;
+    }
+    s = double(acc + dq * rcp_df(q));
+    return c;
+}
+
+// Safeguarded Newton as eig_f64_newton, passes in double-float; converged
+// when a step falls below 1e-13 ||T|| (the double-float resolution).
+__device__ __forceinline__ double eig_df_newton(int n, const float* dh, const float* dl, const float* eh,
+                                                const float* el, int k, double lo, double hi, int clo, int chi,
+                                                double x, float pivmin, double nrm) {
+    const double tol = 1e-13 * nrm;
+    double width_before = hi - lo;
+    for (int it = 0; it < 96 && hi - lo > tol; ++it) {
+        double s;
+        const int c = newton_pass_df(n, dh, dl, eh, el, dfl(x), pivmin, s);
+        if (c <= k) { lo = x; clo = c; } else { hi = x; chi = c; }
+        double xn = 0.5 * (lo + hi);
+        if (chi - clo == 1 && s != 0.0 && isfinite(s)) {
+            const double cand = x - 1.0 / s;
+            if (fabs(cand - x) <= tol) return fmin(fmax(cand, lo), hi);
+            if (cand > lo && cand < hi && 2.0 * fabs(cand - x) <= width_before) xn = cand;
+        }
+        width_before = hi - lo;
+        x = xn;
+    }
+    return x;
+}
+
+// k-th eigenvalue from the FP32 multisection bracket, as eig_f64_bracketed:
+// widened, confirmed by two double-float Sturm counts, finished by Newton;
+// the fallback bisects from the Gershgorin bracket.
+__device__ __forceinline__ double eig_df_bracketed(int n, const float* dh, const float* dl, const float* eh,
+                                                   const float* el, int k, float blo, float bhi, double margin,
+                                                   double lo, double hi, float pivmin, double nrm) {
+    double a = fmax((double)blo - margin, lo), b = fmin((double)bhi + margin, hi);
+    int ca = sturm_count_df(n, dh, dl, eh, el, dfl(a), pivmin);
+    int cb = sturm_count_df(n, dh, dl, eh, el, dfl(b), pivmin);
+    if (!(a < b && ca <= k && cb > k)) {
+        a = lo; b = hi; ca = 0; cb = n;
+        for (int it = 0; it < 64 && b - a > 1e-6 * nrm; ++it) {
+            const double mid = 0.5 * (a + b);
+            const int c = sturm_count_df(n, dh, dl, eh, el, dfl(mid), pivmin);
+            if (c <= k) { a = mid; ca = c; } else { b = mid; cb = c; }
+        }
+        return eig_df_newton(n, dh, dl, eh, el, k, a, b, ca, cb, 0.5 * (a + b), pivmin, nrm);
+    }
+    return eig_df_newton(n, dh, dl, eh, el, k, a, b, ca, cb, 0.5 * ((double)blo + (double)bhi), pivmin, nrm);
+}
+
+// One double-float Newton correction of an eigenvalue located by FP32
+// multisection in [lo, hi]; kept only if it stays near that bracket.
+__device__ __forceinline__ double newton_polish_df(int n, const float* dh, const float* dl, const float* eh,
+                                                   const float* el, float lo, float hi, float atolf, float pivmin) {
+    const double x = 0.5 * ((double)lo + (double)hi);
+    double s;
+    newton_pass_df(n, dh, dl, eh, el, dfl(x), pivmin, s);
+    const double xn = x - 1.0 / s;
+    const double w = fmax((double)(hi - lo), 4.0 * (double)atolf);
+    if (isfinite(xn) && xn >= (double)lo - w && xn <= (double)hi + w) return xn;
+    return x;
+}
+
 // softplus(x) = ln(1 + e^x), written as max(x,0) + log1p(e^-|x|).
 __device__ __forceinline__ double softplus(double x) { return fmax(x, 0.0) + log1p(exp(-fabs(x))); }
 

@@ -2,6 +2,8 @@
 // reduction precision T and on NT = ceil(nmax/32)).
 #pragma once
 
+#include <type_traits>
+
 #include "cluster_solve.cuh"
 #include "surrogate.cuh"
 
@@ -16,7 +18,7 @@ template <typename T, int NT> struct MinBlocks { static constexpr int value = (s
 
 // Shared-memory layout of one cluster CTA (byte offsets, 16-byte aligned).
 struct SmemLayout {
-    size_t A, Vb, Wv, pr, pc, d, e2, df, e2f, sp, lam, red, total;
+    size_t A, Vb, Wv, pr, pc, d, e2, df, e2f, dlo, e2lo, sp, lam, red, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -34,6 +36,8 @@ __host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs) 
     L.e2 = o;  o = align16(o + (size_t)nmaxc * sizeof(double));
     L.df = o;  o = align16(o + (size_t)nmaxc * sizeof(float));
     L.e2f = o; o = align16(o + (size_t)nmaxc * sizeof(float));
+    L.dlo = o; o = align16(o + (size_t)nmaxc * sizeof(float));
+    L.e2lo = o; o = align16(o + (size_t)nmaxc * sizeof(float));
     L.sp = o;  o = align16(o + (size_t)(nmaxc / 2) * 3 * sizeof(double));
     L.lam = o; o = align16(o + (size_t)nmaxc * 2 * sizeof(float));
     L.red = o; o = align16(o + 6 * (size_t)NW * sizeof(double));
@@ -42,7 +46,8 @@ __host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs) 
 }
 
 template <typename T> struct Carve {
-    cplx_t<T>* A; HHScratch<T> hh; double* d; double* e2; float* df; float* e2f; double* sp; float* lam; double* red;
+    cplx_t<T>* A; HHScratch<T> hh; double* d; double* e2; float* df; float* e2f; float* dlo; float* e2lo; double* sp;
+    float* lam; double* red;
 };
 
 template <typename T>
@@ -61,6 +66,8 @@ __device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout&
     c.e2 = reinterpret_cast<double*>(base + L.e2);
     c.df = reinterpret_cast<float*>(base + L.df);
     c.e2f = reinterpret_cast<float*>(base + L.e2f);
+    c.dlo = reinterpret_cast<float*>(base + L.dlo);
+    c.e2lo = reinterpret_cast<float*>(base + L.e2lo);
     c.sp = reinterpret_cast<double*>(base + L.sp);
     c.lam = reinterpret_cast<float*>(base + L.lam);
     return c;
@@ -70,10 +77,11 @@ __device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout&
 // eigenvalues with index < K (all when all_eigs, else those below
 // mu + 40 T), one thread per eigenvalue, and returns through eig (if not
 // null, global) and the block sums of softplus(-(eps-mu)/T) and of the Fermi
-// function.  Both precisions first bracket every eigenvalue by FP32
-// multisection on the FP32-rounded (d, e2); T == float then takes one FP64
-// Newton step, T == double confirms the widened bracket with FP64 Sturm
-// counts and refines it by safeguarded FP64 Newton to full precision.
+// function.  Every precision first brackets each eigenvalue by FP32
+// multisection on the FP32-rounded (d, e2).  T == float then takes one
+// double-float Newton step; T == dfl (the re-solve) confirms the widened
+// bracket with double-float Sturm counts and refines it by safeguarded
+// double-float Newton; T == double does the same in FP64.
 template <typename T>
 __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool all_eigs, double* eig,
                               double& sum_sp, double& sum_fermi, int& n_solved) {
@@ -89,8 +97,12 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
         glo = c.d[tid] - el - er;
         ghi = c.d[tid] + el + er;
         ge = tid < n - 1 ? c.e2[tid] : 0.0;
+        // Float pairs (hi + lo) holding (d, e2) exactly, for the FP32
+        // multisection (hi) and the double-float refinement (hi + lo).
         c.df[tid] = (float)c.d[tid];
         c.e2f[tid] = (float)ge;
+        c.dlo[tid] = (float)(c.d[tid] - (double)c.df[tid]);
+        c.e2lo[tid] = (float)(ge - (double)c.e2f[tid]);
     }
     glo = warp_min(glo); ghi = warp_max(ghi); ge = warp_max(ge);
     if (lane == 0) { c.red[warp] = glo; c.red[NW + warp] = ghi; c.red[2 * NW + warp] = ge; }
@@ -157,12 +169,15 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
     const int k = tid;  // dense warps for the FP64 work
     if (k < K) {
         double lam;
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (std::is_same<T, double>::value) {
             lam = eig_f64_bracketed(n, c.d, c.e2, k, c.lam[2 * k], c.lam[2 * k + 1], 8.0 * FLT_EPSILON * nrm, lo, hi,
                                     pivmin, nrm);
+        } else if constexpr (std::is_same<T, dfl>::value) {
+            lam = eig_df_bracketed(n, c.df, c.dlo, c.e2f, c.e2lo, k, c.lam[2 * k], c.lam[2 * k + 1],
+                                   8.0 * FLT_EPSILON * nrm, lo, hi, s_pivminf, nrm);
         } else {
-            lam = newton_polish_f64(n, c.d, c.e2, c.lam[2 * k], c.lam[2 * k + 1], 2.0f * FLT_EPSILON * (float)nrm,
-                                    pivmin);
+            lam = newton_polish_df(n, c.df, c.dlo, c.e2f, c.e2lo, c.lam[2 * k], c.lam[2 * k + 1],
+                                   2.0f * FLT_EPSILON * (float)nrm, s_pivminf);
         }
         const double x = -(lam - mu) / temp;
         sp = softplus(x);
