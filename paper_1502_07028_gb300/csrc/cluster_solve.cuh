@@ -185,6 +185,25 @@ __device__ __forceinline__ V reduce_scatter4(const V (&v)[4], int lane) {
     return w1;  // row (lane >> 3) & 3 of the batch
 }
 
+template <typename V>
+__device__ __forceinline__ V reduce_scatter2(const V (&v)[2], int lane) {
+    const bool b4 = lane & 16;
+    const V mine = b4 ? v[1] : v[0];
+    const V other = b4 ? v[0] : v[1];
+    V w1 = cadd(mine, cshfl_xor(other, 16));
+    w1 = cadd(w1, cshfl_xor(w1, 8));
+    w1 = cadd(w1, cshfl_xor(w1, 4));
+    w1 = cadd(w1, cshfl_xor(w1, 2));
+    w1 = cadd(w1, cshfl_xor(w1, 1));
+    return w1;  // row (lane >> 4) & 1 of the batch
+}
+
+// Rows per batch of the fused pass: the per-row registers of a batch are
+// four complex values, so wider types take fewer rows.
+template <typename T> struct PassRows { static constexpr int value = 4; };
+template <> struct PassRows<float> { static constexpr int value = 8; };
+template <> struct PassRows<dfl> { static constexpr int value = 2; };
+
 // Sum over the warps of a per-warp partial (red has NW slots; the caller
 // synchronises between the write and the read).
 template <typename T, int NW>
@@ -268,7 +287,7 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
         // l + 32 t.  Per chunk t the RB elements of a lane are independent and
         // branch-free (masked loads and stores), so their loads and FMA chains
         // overlap.  At k = 0, u and w are zero and the update is a no-op.
-        constexpr int RB = sizeof(T) == 4 ? 8 : 4;
+        constexpr int RB = PassRows<T>::value;
         const int m = n - j0;
         const int nbatch = (m + RB - 1) / RB;
         V vc[NT], uc[NT], wc[NT], cacc[NT];
@@ -344,10 +363,14 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
                 out = reduce_scatter8(racc, lane);
                 const int ri = ri0 + ((lane >> 2) & 7);
                 if ((lane & 3) == 0 && ri < m) pr[ri] = out;
-            } else {
+            } else if constexpr (RB == 4) {
                 out = reduce_scatter4(racc, lane);
                 const int ri = ri0 + ((lane >> 3) & 3);
                 if ((lane & 7) == 0 && ri < m) pr[ri] = out;
+            } else {
+                out = reduce_scatter2(racc, lane);
+                const int ri = ri0 + ((lane >> 4) & 1);
+                if ((lane & 15) == 0 && ri < m) pr[ri] = out;
             }
         }
 #pragma unroll

@@ -310,16 +310,35 @@ struct StageArgs {
     float* sg_dF;
 };
 
+// The fields of StageArgs that change from stage to stage, passed by value so
+// that the solve can read every invariant field straight from the kernel
+// parameters.
+struct StageVar {
+    const double* S_in;
+    double* S_out;
+    const int32_t* sites;
+    const int32_t* perm;
+    int32_t rec_base;
+    uint64_t sweep;
+};
+
+__device__ __forceinline__ StageVar stage_var(const StageArgs& a) {
+    StageVar v;
+    v.S_in = a.S_in; v.S_out = a.S_out; v.sites = a.sites; v.perm = a.perm; v.rec_base = a.rec_base; v.sweep = a.sweep;
+    return v;
+}
+
 // Decision of an update site (thread 0 of the deciding CTA): Metropolis on
 // dF, or delayed-acceptance stage 2 on dF - dF~, and the training sample.
 __device__ __forceinline__ double stage2_dF(const StageArgs& a, int c, double dF) {
     return a.sg_dFt ? dF - (double)a.sg_dFt[c] : dF;
 }
 
-__device__ __forceinline__ void collect_sample(const StageArgs& a, const Window& w, int r, const double* sn, double dF) {
+__device__ __forceinline__ void collect_sample(const StageArgs& a, const double* S_in, const Window& w, int r,
+                                               const double* sn, double dF) {
     if (!a.sg_feat) return;
     float* f = a.sg_feat + (int64_t)r * SG_IN;
-    a.sg_center[r] = patch_features(a.m, w, a.S_in, f);
+    a.sg_center[r] = patch_features(a.m, w, S_in, f);
     f[147] = (float)sn[0]; f[148] = (float)sn[1]; f[149] = (float)sn[2];
     a.sg_dF[r] = (float)dF;
 }
@@ -328,18 +347,18 @@ __device__ __forceinline__ void collect_sample(const StageArgs& a, const Window&
 // var 0/1 selects H_old/H_new.  The second of the pair to finish applies
 // Metropolis.  Called by all threads of the CTA; s_new and s_last are shared.
 template <typename T, int NT>
-__device__ __forceinline__ void stage_item(const StageArgs& a, int c, int var, unsigned char* smem, double* s_new,
-                                           int* s_last) {
+__device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v, int c, int var, unsigned char* smem,
+                                           double* s_new, int* s_last) {
     const SmemLayout L = smem_layout(a.nA, 32 * NT, sizeof(cplx_t<T>));
     Carve<T> cv = carve<T>(smem, L);
-    c = a.perm ? a.perm[c] : c;
-    const int site = a.sites[c];
+    c = v.perm ? v.perm[c] : c;
+    const int site = v.sites[c];
     const Window w = make_window(a.m, site);
     const int n = 2 * w.ex * w.ey;
     if (threadIdx.x == 0 && var == 1)
-        propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, s_new);
+        propose_spin(a.m.seed, v.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, v.S_in + 3 * site, s_new);
     __syncthreads();
-    build_cluster<T>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    build_cluster<T>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     __syncthreads();
     householder_tridiag<T, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
@@ -360,11 +379,11 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int c, int var, u
     const double Fo = __ldcg(&a.Fbuf[2 * c]), Fn = __ldcg(&a.Fbuf[2 * c + 1]);
     const double fo = __ldcg(&a.fillbuf[2 * c]), fn = __ldcg(&a.fillbuf[2 * c + 1]);
     double sn[3];
-    const double* so = a.S_in + 3 * site;
+    const double* so = v.S_in + 3 * site;
     if (var == 1) { sn[0] = s_new[0]; sn[1] = s_new[1]; sn[2] = s_new[2]; }
-    else propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, so, sn);
+    else propose_spin(a.m.seed, v.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, so, sn);
     double u0, u1;
-    uniform2(a.m.seed, a.sweep, (uint32_t)site, RNG_ACCEPT, u0, u1);
+    uniform2(a.m.seed, v.sweep, (uint32_t)site, RNG_ACCEPT, u0, u1);
     const double lnu = log(u0);
     const double dF = Fn - Fo;
     if (!isfinite(dF)) atomicExch(a.err, 1);
@@ -375,11 +394,11 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, int c, int var, u
         return;
     }
     const bool acc = lnu < -dFe / a.m.T;
-    collect_sample(a, w, a.rec_base + c, sn, dF);
-    double* dst = a.S_out + 3 * site;
+    collect_sample(a, v.S_in, w, v.rec_base + c, sn, dF);
+    double* dst = v.S_out + 3 * site;
     if (acc) { dst[0] = sn[0]; dst[1] = sn[1]; dst[2] = sn[2]; }
     else { dst[0] = so[0]; dst[1] = so[1]; dst[2] = so[2]; }
-    const int r = a.rec_base + c;
+    const int r = v.rec_base + c;
     a.rec_site[r] = site;
     a.rec_Fold[r] = Fo;
     a.rec_Fnew[r] = Fn;
@@ -406,7 +425,7 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArg
     const int c = blockIdx.x >> 1, var = blockIdx.x & 1;
     const int count = a.count_dev ? (int)*a.count_dev : a.count;
     if (c >= count) return;
-    stage_item<T, NT>(a, c, var, smem, s_new, &s_last);
+    stage_item<T, NT>(a, stage_var(a), c, var, smem, s_new, &s_last);
 }
 
 template <typename T, int NT>
@@ -466,18 +485,18 @@ __global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int c
 // tridiagonal run in FP64, and the second of the pair decides (no margin
 // test).  nmaxc = 32 * NT sizes the vectors in shared memory.
 template <int NT>
-__device__ __noinline__ void resolve_item(const StageArgs& a, int c, int var, unsigned char* smem, double* s_new,
-                                          int* s_last) {
+__device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, int c, int var, unsigned char* smem,
+                                          double* s_new, int* s_last) {
     const SmemLayout L = smem_layout(0, 32 * NT, sizeof(dfl2));
     Carve<dfl> cv = carve<dfl>(smem, L);
     cv.A = reinterpret_cast<dfl2*>(a.gA + (int64_t)blockIdx.x * a.gA_stride);
-    const int site = a.sites[c];
+    const int site = v.sites[c];
     const Window w = make_window(a.m, site);
     const int n = 2 * w.ex * w.ey;
     if (threadIdx.x == 0 && var == 1)
-        propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, s_new);
+        propose_spin(a.m.seed, v.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, v.S_in + 3 * site, s_new);
     __syncthreads();
-    build_cluster<dfl>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    build_cluster<dfl>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     __syncthreads();
     householder_tridiag<dfl, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
@@ -496,20 +515,20 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, int c, int var, un
     const double Fo = __ldcg(&a.Fbuf[2 * c]), Fn = __ldcg(&a.Fbuf[2 * c + 1]);
     const double fo = __ldcg(&a.fillbuf[2 * c]), fn = __ldcg(&a.fillbuf[2 * c + 1]);
     double sn[3];
-    const double* so = a.S_in + 3 * site;
+    const double* so = v.S_in + 3 * site;
     if (var == 1) { sn[0] = s_new[0]; sn[1] = s_new[1]; sn[2] = s_new[2]; }
-    else propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, so, sn);
+    else propose_spin(a.m.seed, v.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, so, sn);
     double u0, u1;
-    uniform2(a.m.seed, a.sweep, (uint32_t)site, RNG_ACCEPT, u0, u1);
+    uniform2(a.m.seed, v.sweep, (uint32_t)site, RNG_ACCEPT, u0, u1);
     const double lnu = log(u0);
     const double dF = Fn - Fo;
     if (!isfinite(dF)) atomicExch(a.err, 1);
     const bool acc = lnu < -stage2_dF(a, c, dF) / a.m.T;
-    collect_sample(a, w, a.rec_base + c, sn, dF);
-    double* dst = a.S_out + 3 * site;
+    collect_sample(a, v.S_in, w, v.rec_base + c, sn, dF);
+    double* dst = v.S_out + 3 * site;
     if (acc) { dst[0] = sn[0]; dst[1] = sn[1]; dst[2] = sn[2]; }
     else { dst[0] = so[0]; dst[1] = so[1]; dst[2] = so[2]; }
-    const int r = a.rec_base + c;
+    const int r = v.rec_base + c;
     a.rec_site[r] = site;
     a.rec_Fold[r] = Fo;
     a.rec_Fnew[r] = Fn;
@@ -531,7 +550,7 @@ __global__ void __launch_bounds__(CTA, 1) k_resolve(StageArgs a) {
     const int nflag = (int)*(volatile unsigned int*)a.flag_count;
     for (int item = blockIdx.x; item < 2 * nflag; item += gridDim.x) {
         const int c = a.flag_list[item >> 1];
-        resolve_item<NT>(a, c, item & 1, smem, s_new, &s_last);
+        resolve_item<NT>(a, stage_var(a), c, item & 1, smem, s_new, &s_last);
         __syncthreads();
     }
 }
@@ -605,31 +624,32 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int par
 }
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_sweep_persistent(PersistArgs p) {
+__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_sweep_persistent(const __grid_constant__ PersistArgs p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_new[3];
     __shared__ int s_last, s_item;
-    StageArgs a = p.st;
+    const StageArgs& a = p.st;  // invariant fields, read from the kernel parameters
     const unsigned long long sweep0 = *p.sweep_ctr;
     const int G = p.nstages * p.n_sweeps;
     for (int g = 0; g < G; ++g) {
         const int s = g % p.nstages;
         const int sp = (g > 0) ? (g - 1) % p.nstages : -1;
-        a.sweep = sweep0 + (unsigned long long)(g / p.nstages);
-        a.S_in = (g & 1) ? p.S1 : p.S0;
-        a.S_out = (g & 1) ? p.S0 : p.S1;
-        a.sites = p.sites + p.stage_start[s];
-        a.perm = p.st.perm ? p.st.perm + p.stage_start[s] : nullptr;
-        a.count = p.stage_start[s + 1] - p.stage_start[s];
-        a.rec_base = p.stage_start[s];
+        StageVar v;
+        v.sweep = sweep0 + (unsigned long long)(g / p.nstages);
+        v.S_in = (g & 1) ? p.S1 : p.S0;
+        v.S_out = (g & 1) ? p.S0 : p.S1;
+        v.sites = p.sites + p.stage_start[s];
+        v.perm = a.perm ? a.perm + p.stage_start[s] : nullptr;
+        v.rec_base = p.stage_start[s];
+        const int count = p.stage_start[s + 1] - p.stage_start[s];
         if (sp >= 0) {
             const int32_t* prev = p.sites + p.stage_start[sp];
             const int pc = p.stage_start[sp + 1] - p.stage_start[sp];
             for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < pc; k += gridDim.x * blockDim.x) {
                 const int q = prev[k];
-                a.S_out[3 * q] = a.S_in[3 * q];
-                a.S_out[3 * q + 1] = a.S_in[3 * q + 1];
-                a.S_out[3 * q + 2] = a.S_in[3 * q + 2];
+                v.S_out[3 * q] = v.S_in[3 * q];
+                v.S_out[3 * q + 1] = v.S_in[3 * q + 1];
+                v.S_out[3 * q + 2] = v.S_in[3 * q + 2];
             }
         }
         unsigned int* qc = p.queue + (g & 1);
@@ -638,8 +658,8 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_sweep_persiste
             __syncthreads();
             const int item = s_item;
             __syncthreads();
-            if (item >= 2 * a.count) break;
-            stage_item<T, NT>(a, item >> 1, item & 1, smem, s_new, &s_last);
+            if (item >= 2 * count) break;
+            stage_item<T, NT>(a, v, item >> 1, item & 1, smem, s_new, &s_last);
             __syncthreads();
         }
         if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, a.err, qc)) return;
@@ -653,7 +673,7 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_sweep_persiste
                     const int item = s_item;
                     __syncthreads();
                     if (item >= 2 * nflag) break;
-                    resolve_item<NT>(a, a.flag_list[item >> 1], item & 1, smem, s_new, &s_last);
+                    resolve_item<NT>(a, v, a.flag_list[item >> 1], item & 1, smem, s_new, &s_last);
                     __syncthreads();
                 }
                 if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, a.err, p.queue + 2, a.flag_count)) return;
