@@ -301,7 +301,14 @@ def main():
     # --- mixed precision (headline): FP32 reduction, FP64 eigenvalues and dF,
     # FP64 re-solve of decisions within the margin (decisions equal FP64's)
     ctx = P.Context(P.Config(**base, precision=P.MIXED))
-    P.ptca_set_pipeline(ctx.h, P.PIPELINE_GRAPH)
+    # Autotuner: CTA width x pipeline x persistent CTAs per SM, timed on this
+    # lattice; the chain state is restored and the fastest applied.
+    best, tune_table = P.ptca_autotune(ctx.h, 3)
+    names = {P.PIPELINE_STAGES: "per-stage launches", P.PIPELINE_PERSISTENT: "persistent kernel",
+             P.PIPELINE_GRAPH: "persistent kernel in a CUDA graph"}
+    pipeline_desc = (f"{names[best.pipeline]}, {best.warps_per_cta}-warp CTA per matrix"
+                     + (f", {best.ctas_per_sm} CTAs/SM" if best.pipeline != P.PIPELINE_STAGES else "")
+                     + " (autotuned)")
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -359,7 +366,9 @@ def main():
 
     # --- roofline of the dominant kernel (the persistent sweep kernel: one
     # launch per sweep; its FP32 work is the Householder reduction)
-    launches_per_step = 1
+    # One persistent launch per sweep, or per stage a stage kernel and a
+    # re-solve kernel plus the closing copy and counter kernels.
+    launches_per_step = 1 if best.pipeline != P.PIPELINE_STAGES else 2 * n_stages + 2
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or 2070.0
     matrices_per_step = 2 * N
@@ -387,7 +396,10 @@ def main():
             "e2e": {"value": e2e_value, "unit": "spin-updates/s", "h2d_bytes_per_step": N * 24,
                     "d2h_bytes_per_step": N * 24},
             "gpu_launches": launches_per_step * args.steps,
-            "pipeline": "persistent kernel (all stages, device-wide barrier) in a CUDA graph",
+            "pipeline": pipeline_desc,
+            "autotune": {"best": tune_table["best"],
+                         "candidates": [[c["pipeline"], c["warps_per_cta"], c["ctas_per_sm"], c["ms_per_sweep"]]
+                                        for c in tune_table["candidates"]]},
             "mixed_unguarded": {"value": unguarded_value, "unit": "spin-updates/s",
                                 "note": "same path without the FP64 re-solve of decisions within 1e-2"},
             "resolved_fraction": resolved_frac,

@@ -211,6 +211,38 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
  * the kernel stops and ptca_sweep (with stats) returns PTCA_ERR_TIMEOUT. */
 ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeout_s);
 
+/* Launch configuration of the sweep kernels:
+ *   pipeline       PTCA_PIPELINE_STAGES / _PERSISTENT / _GRAPH (as above);
+ *   warps_per_cta  8: one 8-warp CTA per cluster matrix (every precision
+ *                  and order); 4: one warp group per matrix, twice the
+ *                  resident matrices per SM (PTCA_MIXED, orders up to 128);
+ *   ctas_per_sm    CTAs per SM of the persistent kernel, 0 = as many as fit.
+ * Every configuration computes the same chain (decisions and spins; free
+ * energies to rounding). */
+typedef struct {
+    int32_t pipeline;
+    int32_t warps_per_cta;
+    int32_t ctas_per_sm;
+} ptca_launch_config;
+
+/* Apply a launch configuration.  PTCA_ERR_UNSUPPORTED for a width the
+ * problem cannot use, PTCA_ERR_INVALID for values out of range. */
+ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg);
+ptca_status ptca_get_launch_config(const ptca_ctx* ctx, ptca_launch_config* out);
+
+/* Autotuner: times every launch configuration the problem admits (CTA width
+ * x pipeline x persistent CTAs per SM) on this context's own lattice -- one
+ * warm-up sweep and trial_sweeps (1..100) timed sweeps each, CUDA events on
+ * `stream` -- restoring the spins and the sweep counter before every trial
+ * and at the end, so the chain is left where it was (the per-visit record
+ * of the last sweep is overwritten).  Applies the fastest configuration,
+ * writes it to *best (may be NULL) and, if json is not NULL, a JSON table of
+ * every candidate's ms per sweep (NUL-terminated, at most json_cap bytes;
+ * PTCA_ERR_INVALID if it does not fit).  Synchronises `stream`.  The
+ * precision checker must be off. */
+ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_config* best, char* json, int32_t json_cap,
+                          void* stream);
+
 /* PTCA_MIXED decision guard.  The FP32 reduction leaves an error of about
  * 1e-4 in dF at n = 128, so a Metropolis decision whose margin
  * |ln u + dF/T| is below `margin` is deferred: both cluster matrices of that

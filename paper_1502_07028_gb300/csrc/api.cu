@@ -295,14 +295,19 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
     }
     if (ce == cudaSuccess) ce = cudaMemcpy(c->d_stage_start, st.data(), (c->nstages + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) {
-        int sms = 0, per = ptca::persistent_blocks_per_sm(c->prec, c->nA);
+        int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        c->grid = sms * per;
+        c->sms = sms;
+        c->grid = sms * ptca::persistent_blocks_per_sm(c->prec, 8, c->nA);
         if (c->grid <= 0) c->pipeline = PTCA_PIPELINE_STAGES;
         if (c->prec == 1) {
-            // Global slots for FP64 re-solves: one per CTA of either launch.
+            // Global slots for the re-solves: one per CTA of any launch
+            // configuration (the 4-warp persistent grid is the widest).
             c->resolve_grid = sms;
-            const int slots = std::max(c->grid, c->resolve_grid);
+            int widest = c->grid;
+            if (ptca::sweep_width_supported(c->prec, 4, c->nA))
+                widest = std::max(widest, sms * ptca::persistent_blocks_per_sm(c->prec, 4, c->nA));
+            const int slots = std::max(widest, c->resolve_grid);
             c->gA_stride = (int64_t)c->nA * (c->nA + 1) / 2;
             ce = dalloc(&c->d_gA, (size_t)slots * (size_t)c->gA_stride);
             c->margin = 1e-2;
@@ -489,7 +494,7 @@ static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st
             a.sg_dFt = nullptr;
             if (ctx->checker) e = check_stage(ctx, a, s, st);
             if (e == cudaSuccess && ctx->sg.enabled && !col) e = ptca_screen_stage(ctx, a, st);
-            if (e == cudaSuccess) e = ptca::launch_stage(ctx->prec, a, st);
+            if (e == cudaSuccess) e = ptca::launch_stage(ctx->prec, ctx->nw, a, st);
             if (e == cudaSuccess && a.margin > 0.0) {
                 e = ptca::launch_resolve(a, ctx->resolve_grid, st);
                 if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag_count, 0, sizeof(unsigned int), st);
@@ -523,7 +528,7 @@ static cudaError_t enqueue_persistent(ptca_ctx* ctx, int32_t n_sweeps, cudaStrea
     cudaError_t e = cudaMemsetAsync(ctx->d_queue, 0, 3 * sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag_count, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned int), st);
-    if (e == cudaSuccess) e = ptca::launch_persistent(ctx->prec, p, ctx->grid, st);
+    if (e == cudaSuccess) e = ptca::launch_persistent(ctx->prec, ctx->nw, p, ctx->grid, st);
     return e;
 }
 
@@ -553,6 +558,14 @@ static cudaError_t sweep_graph(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st)
     return cudaGraphLaunch(ctx->graph, st);
 }
 
+// Stream work of n_sweeps sweeps in the context's launch configuration
+// (screening and the checker need the per-stage pipeline).
+static cudaError_t run_sweeps(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
+    if (ctx->pipeline == PTCA_PIPELINE_STAGES || ctx->sg.enabled || ctx->checker) return sweep_stages(ctx, n_sweeps, st);
+    if (ctx->pipeline == PTCA_PIPELINE_PERSISTENT || ctx->graph_failed) return enqueue_persistent(ctx, n_sweeps, st);
+    return sweep_graph(ctx, n_sweeps, st);
+}
+
 ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeout_s) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
     if (mode < PTCA_PIPELINE_STAGES || mode > PTCA_PIPELINE_GRAPH) return fail(PTCA_ERR_INVALID, "unknown pipeline");
@@ -562,6 +575,132 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
     ctx->pipeline = mode;
     ctx->timeout_ns = (unsigned long long)(barrier_timeout_s * 1e9);
     drop_graph(ctx);
+    return PTCA_OK;
+}
+
+ptca_status ptca_get_launch_config(const ptca_ctx* ctx, ptca_launch_config* out) {
+    if (!ctx || !out) return fail(PTCA_ERR_INVALID, "null argument");
+    out->pipeline = ctx->pipeline;
+    out->warps_per_cta = ctx->nw;
+    out->ctas_per_sm = ctx->ctas_per_sm;
+    return PTCA_OK;
+}
+
+ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg) {
+    if (!ctx || !cfg) return fail(PTCA_ERR_INVALID, "null argument");
+    if (cfg->pipeline < PTCA_PIPELINE_STAGES || cfg->pipeline > PTCA_PIPELINE_GRAPH)
+        return fail(PTCA_ERR_INVALID, "unknown pipeline");
+    if (cfg->warps_per_cta != 8 && cfg->warps_per_cta != 4) return fail(PTCA_ERR_INVALID, "warps_per_cta must be 4 or 8");
+    if (!ptca::sweep_width_supported(ctx->prec, cfg->warps_per_cta, ctx->nA))
+        return fail(PTCA_ERR_UNSUPPORTED, "4-warp sweep kernels need PTCA_MIXED and matrix orders up to 128");
+    const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, cfg->warps_per_cta, ctx->nA);
+    if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > maxb)
+        return fail(PTCA_ERR_INVALID, "ctas_per_sm must be in [0, the CTAs that fit on an SM]");
+    if (cfg->pipeline != PTCA_PIPELINE_STAGES && maxb <= 0)
+        return fail(PTCA_ERR_UNSUPPORTED, "persistent kernel does not fit on this device");
+    ctx->pipeline = cfg->pipeline;
+    ctx->nw = cfg->warps_per_cta;
+    ctx->ctas_per_sm = cfg->ctas_per_sm;
+    ctx->grid = maxb > 0 ? ctx->sms * (cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : maxb) : 0;
+    ctx->graph_failed = false;
+    drop_graph(ctx);
+    return PTCA_OK;
+}
+
+static const char* pipeline_name(int p) {
+    return p == PTCA_PIPELINE_STAGES ? "stages" : (p == PTCA_PIPELINE_PERSISTENT ? "persistent" : "graph");
+}
+
+ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_config* best, char* json, int32_t json_cap,
+                          void* stream) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (trial_sweeps < 1 || trial_sweeps > 100) return fail(PTCA_ERR_INVALID, "trial_sweeps in [1, 100]");
+    if (ctx->checker) return fail(PTCA_ERR_INVALID, "turn the precision checker off before autotuning");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Candidates: CTA width x pipeline x persistent CTAs per SM.
+    std::vector<ptca_launch_config> cand;
+    for (int nw : {8, 4}) {
+        if (!ptca::sweep_width_supported(ctx->prec, nw, ctx->nA)) continue;
+        cand.push_back({PTCA_PIPELINE_STAGES, nw, 0});
+        const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, nw, ctx->nA);
+        if (maxb <= 0 || ctx->sg.enabled) continue;
+        for (int pl : {PTCA_PIPELINE_PERSISTENT, PTCA_PIPELINE_GRAPH}) {
+            cand.push_back({pl, nw, maxb});
+            if (maxb > 1) cand.push_back({pl, nw, 1});
+        }
+    }
+    // The chain state every trial starts from (both spin buffers agree
+    // between sweeps) and is restored to afterwards.
+    const size_t nS = 3 * (size_t)ctx->N;
+    double* saved = nullptr;
+    PTCA_CUDA(cudaMalloc(&saved, nS * sizeof(double)));
+    PTCA_CUDA(cudaMemcpyAsync(saved, ctx->d_S[0], nS * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    const int64_t sweeps0 = ctx->sweeps;
+    ptca_launch_config prev;
+    ptca_get_launch_config(ctx, &prev);
+    auto restore = [&]() {
+        cudaError_t e = cudaMemcpyAsync(ctx->d_S[0], saved, nS * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_S[1], saved, nS * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = ptca::launch_set_u64(ctx->d_sweep_ctr, (unsigned long long)sweeps0, st);
+        ctx->sweeps = sweeps0;
+        return e;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<double> ms(cand.size(), -1.0);
+    int ibest = -1;
+    for (size_t i = 0; i < cand.size(); ++i) {
+        if (ptca_set_launch_config(ctx, &cand[i]) != PTCA_OK) continue;
+        cudaError_t e = restore();
+        if (e == cudaSuccess) e = run_sweeps(ctx, 1, st);  // warm-up (and graph capture)
+        if (e == cudaSuccess) e = restore();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = run_sweeps(ctx, trial_sweeps, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        int32_t err[2] = {0, 0};
+        if (e == cudaSuccess) e = cudaMemcpy(err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess || err[1] != 0) {
+            cudaGetLastError();
+            cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(int32_t), st);
+            continue;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[i] = t / trial_sweeps;
+        if (ibest < 0 || ms[i] < ms[ibest]) ibest = (int)i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const ptca_launch_config chosen = ibest >= 0 ? cand[ibest] : prev;
+    ptca_set_launch_config(ctx, &chosen);
+    cudaError_t e = restore();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(saved);
+    if (e != cudaSuccess) return cuda_fail(e, "ptca_autotune");
+    if (ibest < 0) return fail(PTCA_ERR_CUDA, "no launch configuration completed a trial sweep");
+    if (best) *best = chosen;
+    if (json && json_cap > 0) {
+        std::string js = "{\"n_max\": " + std::to_string(ctx->nA) + ", \"precision\": \"" +
+                         (ctx->prec ? "mixed" : "fp64") + "\", \"sites\": " + std::to_string(ctx->N) +
+                         ", \"stages\": " + std::to_string(ctx->nstages) + ", \"trial_sweeps\": " +
+                         std::to_string(trial_sweeps) + ", \"candidates\": [";
+        char buf[256];
+        for (size_t i = 0; i < cand.size(); ++i) {
+            std::snprintf(buf, sizeof buf,
+                          "%s{\"pipeline\": \"%s\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d, \"ms_per_sweep\": %s}",
+                          i ? ", " : "", pipeline_name(cand[i].pipeline), cand[i].warps_per_cta, cand[i].ctas_per_sm,
+                          ms[i] >= 0 ? std::to_string(ms[i]).c_str() : "null");
+            js += buf;
+        }
+        std::snprintf(buf, sizeof buf,
+                      "], \"best\": {\"pipeline\": \"%s\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d}}",
+                      pipeline_name(chosen.pipeline), chosen.warps_per_cta, chosen.ctas_per_sm);
+        js += buf;
+        if ((int)js.size() >= json_cap) return fail(PTCA_ERR_INVALID, "json buffer too small");
+        std::memcpy(json, js.c_str(), js.size() + 1);
+    }
     return PTCA_OK;
 }
 
@@ -631,9 +770,7 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
     PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
     if (n_sweeps > 0) {
         cudaError_t e;
-        if (ctx->pipeline == PTCA_PIPELINE_STAGES || ctx->sg.enabled || ctx->checker) e = sweep_stages(ctx, n_sweeps, st);
-        else if (ctx->pipeline == PTCA_PIPELINE_PERSISTENT || ctx->graph_failed) e = enqueue_persistent(ctx, n_sweeps, st);
-        else e = sweep_graph(ctx, n_sweeps, st);
+        e = run_sweeps(ctx, n_sweeps, st);
         if (e != cudaSuccess) return cuda_fail(e, "ptca_sweep");
     }
     ctx->sweeps += n_sweeps;

@@ -14,7 +14,12 @@ constexpr int CTA = 32 * NW;
 constexpr double kFermiCut = 40.0; // eigenvalues above mu + 40 T change F by < T e^-40 each
 
 // Two CTAs per SM fit in shared memory for FP32 matrices up to n = 128.
-template <typename T, int NT> struct MinBlocks { static constexpr int value = (sizeof(T) == 4 && NT <= 4) ? 2 : 1; };
+// Resident CTAs per SM the launch bounds ask for (caps the registers at
+// 65536 / (value * 32 * NWP)): FP32 matrices up to order 128 run two 8-warp
+// or four 4-warp CTAs per SM.
+template <typename T, int NT, int NWP = NW> struct MinBlocks {
+    static constexpr int value = ((sizeof(T) == 4 && NT <= 4) ? 2 : 1) * (8 / NWP);
+};
 
 // Shared-memory layout of one cluster CTA (byte offsets, 16-byte aligned).
 struct SmemLayout {
@@ -23,15 +28,16 @@ struct SmemLayout {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// nA: largest matrix order stored; nmaxc = 32 * NT; cs = sizeof(complex element)
-__host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs) {
+// nA: largest matrix order stored; nmaxc = 32 * NT; cs = sizeof(complex element);
+// nw: warps per CTA
+__host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs, int nw = NW) {
     SmemLayout L;
     size_t o = 0;
     L.A = o;   o = align16(o + (size_t)nA * (nA + 1) / 2 * cs);
     L.Vb = o;  o = align16(o + 2 * (size_t)nmaxc * cs);
     L.Wv = o;  o = align16(o + (size_t)nmaxc * cs);
     L.pr = o;  o = align16(o + (size_t)nmaxc * cs);
-    L.pc = o;  o = align16(o + (size_t)NW * nmaxc * cs);
+    L.pc = o;  o = align16(o + (size_t)nw * nmaxc * cs);
     L.d = o;   o = align16(o + (size_t)nmaxc * sizeof(double));
     L.e2 = o;  o = align16(o + (size_t)nmaxc * sizeof(double));
     L.df = o;  o = align16(o + (size_t)nmaxc * sizeof(float));
@@ -40,7 +46,7 @@ __host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs) 
     L.e2lo = o; o = align16(o + (size_t)nmaxc * sizeof(float));
     L.sp = o;  o = align16(o + (size_t)(nmaxc / 2) * 3 * sizeof(double));
     L.lam = o; o = align16(o + (size_t)nmaxc * 2 * sizeof(float));
-    L.red = o; o = align16(o + 6 * (size_t)NW * sizeof(double));
+    L.red = o; o = align16(o + 6 * (size_t)nw * sizeof(double));
     L.total = o;
     return L;
 }
@@ -51,7 +57,7 @@ template <typename T> struct Carve {
 };
 
 template <typename T>
-__device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout& L) {
+__device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout& L, int nw = NW) {
     Carve<T> c;
     c.A = reinterpret_cast<cplx_t<T>*>(base + L.A);
     c.hh.Vb = reinterpret_cast<cplx_t<T>*>(base + L.Vb);
@@ -60,8 +66,8 @@ __device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout&
     c.hh.pc = reinterpret_cast<cplx_t<T>*>(base + L.pc);
     c.red = reinterpret_cast<double*>(base + L.red);
     c.hh.redA = reinterpret_cast<T*>(base + L.red);
-    c.hh.redB = reinterpret_cast<T*>(base + L.red + 2 * NW * sizeof(double));
-    c.hh.sx = reinterpret_cast<cplx_t<T>*>(base + L.red + 4 * NW * sizeof(double));
+    c.hh.redB = reinterpret_cast<T*>(base + L.red + 2 * nw * sizeof(double));
+    c.hh.sx = reinterpret_cast<cplx_t<T>*>(base + L.red + 4 * nw * sizeof(double));
     c.d = reinterpret_cast<double*>(base + L.d);
     c.e2 = reinterpret_cast<double*>(base + L.e2);
     c.df = reinterpret_cast<float*>(base + L.df);
@@ -82,7 +88,7 @@ __device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout&
 // double-float Newton step; T == dfl (the re-solve) confirms the widened
 // bracket with double-float Sturm counts and refines it by safeguarded
 // double-float Newton; T == double does the same in FP64.
-template <typename T>
+template <typename T, int NWP = NW>
 __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool all_eigs, double* eig,
                               double& sum_sp, double& sum_fermi, int& n_solved) {
     __shared__ double s_lo, s_hi, s_pivmin;
@@ -105,12 +111,12 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
         c.e2lo[tid] = (float)(ge - (double)c.e2f[tid]);
     }
     glo = warp_min(glo); ghi = warp_max(ghi); ge = warp_max(ge);
-    if (lane == 0) { c.red[warp] = glo; c.red[NW + warp] = ghi; c.red[2 * NW + warp] = ge; }
+    if (lane == 0) { c.red[warp] = glo; c.red[NWP + warp] = ghi; c.red[2 * NWP + warp] = ge; }
     __syncthreads();
     if (tid == 0) {
-        double lo = c.red[0], hi = c.red[NW], emax2 = c.red[2 * NW];
-        for (int w = 1; w < NW; ++w) {
-            lo = fmin(lo, c.red[w]); hi = fmax(hi, c.red[NW + w]); emax2 = fmax(emax2, c.red[2 * NW + w]);
+        double lo = c.red[0], hi = c.red[NWP], emax2 = c.red[2 * NWP];
+        for (int w = 1; w < NWP; ++w) {
+            lo = fmin(lo, c.red[w]); hi = fmax(hi, c.red[NWP + w]); emax2 = fmax(emax2, c.red[2 * NWP + w]);
         }
         const double wdt = hi - lo, nrm = fmax(fabs(lo), fabs(hi));
         lo -= 1e-12 * (wdt + nrm) + 1e-300;
@@ -186,7 +192,7 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
     }
     __syncthreads();
     sum_sp = block_sum<double>(sp, c.red);
-    sum_fermi = block_sum<double>(fe, c.red + NW);
+    sum_fermi = block_sum<double>(fe, c.red + NWP);
     n_solved = K;
 }
 
@@ -346,11 +352,11 @@ __device__ __forceinline__ void collect_sample(const StageArgs& a, const double*
 // One matrix of one update site of a stage: c indexes the stage's site list,
 // var 0/1 selects H_old/H_new.  The second of the pair to finish applies
 // Metropolis.  Called by all threads of the CTA; s_new and s_last are shared.
-template <typename T, int NT>
+template <typename T, int NT, int NWP>
 __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v, int c, int var, unsigned char* smem,
                                            double* s_new, int* s_last) {
-    const SmemLayout L = smem_layout(a.nA, 32 * NT, sizeof(cplx_t<T>));
-    Carve<T> cv = carve<T>(smem, L);
+    const SmemLayout L = smem_layout(a.nA, 32 * NT, sizeof(cplx_t<T>), NWP);
+    Carve<T> cv = carve<T>(smem, L, NWP);
     c = v.perm ? v.perm[c] : c;
     const int site = v.sites[c];
     const Window w = make_window(a.m, site);
@@ -360,10 +366,10 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
     __syncthreads();
     build_cluster<T>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     __syncthreads();
-    householder_tridiag<T, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
+    householder_tridiag<T, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
-    tridiag_eig_F<T>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
+    tridiag_eig_F<T, NWP>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
     if (threadIdx.x == 0) {
         const double F = -a.m.T * ssp;
         a.Fbuf[2 * c + var] = F;
@@ -411,8 +417,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
     atomicAdd(&a.counters[1], 2ull);
 }
 
-template <typename T, int NT>
-__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArgs a) {
+template <typename T, int NT, int NWP = NW>
+__global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value) k_stage(StageArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_new[3];
     __shared__ int s_last;
@@ -425,7 +431,7 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_stage(StageArg
     const int c = blockIdx.x >> 1, var = blockIdx.x & 1;
     const int count = a.count_dev ? (int)*a.count_dev : a.count;
     if (c >= count) return;
-    stage_item<T, NT>(a, stage_var(a), c, var, smem, s_new, &s_last);
+    stage_item<T, NT, NWP>(a, stage_var(a), c, var, smem, s_new, &s_last);
 }
 
 template <typename T, int NT>
@@ -484,11 +490,11 @@ __global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int c
 // significant bits on the FP32 pipe), the eigenvalues of the resulting
 // tridiagonal run in FP64, and the second of the pair decides (no margin
 // test).  nmaxc = 32 * NT sizes the vectors in shared memory.
-template <int NT>
+template <int NT, int NWP = NW>
 __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, int c, int var, unsigned char* smem,
                                           double* s_new, int* s_last) {
-    const SmemLayout L = smem_layout(0, 32 * NT, sizeof(dfl2));
-    Carve<dfl> cv = carve<dfl>(smem, L);
+    const SmemLayout L = smem_layout(0, 32 * NT, sizeof(dfl2), NWP);
+    Carve<dfl> cv = carve<dfl>(smem, L, NWP);
     cv.A = reinterpret_cast<dfl2*>(a.gA + (int64_t)blockIdx.x * a.gA_stride);
     const int site = v.sites[c];
     const Window w = make_window(a.m, site);
@@ -498,10 +504,10 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, 
     __syncthreads();
     build_cluster<dfl>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     __syncthreads();
-    householder_tridiag<dfl, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
+    householder_tridiag<dfl, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
-    tridiag_eig_F<dfl>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
+    tridiag_eig_F<dfl, NWP>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
     if (threadIdx.x == 0) {
         a.Fbuf[2 * c + var] = -a.m.T * ssp;
         a.fillbuf[2 * c + var] = sfe;
@@ -623,8 +629,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int par
     return s_ok != 0;
 }
 
-template <typename T, int NT>
-__global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_sweep_persistent(const __grid_constant__ PersistArgs p) {
+template <typename T, int NT, int NWP = NW>
+__global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value)
+    k_sweep_persistent(const __grid_constant__ PersistArgs p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_new[3];
     __shared__ int s_last, s_item;
@@ -659,7 +666,7 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_sweep_persiste
             const int item = s_item;
             __syncthreads();
             if (item >= 2 * count) break;
-            stage_item<T, NT>(a, v, item >> 1, item & 1, smem, s_new, &s_last);
+            stage_item<T, NT, NWP>(a, v, item >> 1, item & 1, smem, s_new, &s_last);
             __syncthreads();
         }
         if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, a.err, qc)) return;
@@ -673,7 +680,7 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_sweep_persiste
                     const int item = s_item;
                     __syncthreads();
                     if (item >= 2 * nflag) break;
-                    resolve_item<NT>(a, v, a.flag_list[item >> 1], item & 1, smem, s_new, &s_last);
+                    resolve_item<NT, NWP>(a, v, a.flag_list[item >> 1], item & 1, smem, s_new, &s_last);
                     __syncthreads();
                 }
                 if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, a.err, p.queue + 2, a.flag_count)) return;

@@ -28,11 +28,15 @@ cudaError_t launch_eigvals(int prec, int nA, const void* H, const int64_t* offse
                            double* eig, const int64_t* eoff, cudaStream_t st);
 cudaError_t launch_free_energy(const double* eig, const int64_t* eoff, const int32_t* n, int count, double mu,
                                double T, double* F, cudaStream_t st);
-cudaError_t launch_stage(int prec, const StageArgs& a, cudaStream_t st);
+// Sweep kernels come in CTA widths nw = 8 warps (every precision and order)
+// and nw = 4 warps (PTCA_MIXED, orders up to 128).
+bool sweep_width_supported(int prec, int nw, int nA);
+size_t sweep_smem_bytes(int prec, int nw, int nA);
+cudaError_t launch_stage(int prec, int nw, const StageArgs& a, cudaStream_t st);
 // Persistent sweep kernel: grid CTAs (all co-resident; cooperative launch).
-cudaError_t launch_persistent(int prec, const PersistArgs& p, int grid, cudaStream_t st);
+cudaError_t launch_persistent(int prec, int nw, const PersistArgs& p, int grid, cudaStream_t st);
 // CTAs of the persistent kernel that fit on one SM for matrices up to nA.
-int persistent_blocks_per_sm(int prec, int nA);
+int persistent_blocks_per_sm(int prec, int nw, int nA);
 // FP64 re-solve of the decisions a PTCA_MIXED stage deferred (grid CTAs).
 cudaError_t launch_resolve(const StageArgs& a, int grid, cudaStream_t st);
 // Precision checker: spectra of visits c0 .. c0+count-1 of a stage (prec 1:

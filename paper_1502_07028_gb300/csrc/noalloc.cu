@@ -170,7 +170,7 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
         a.rec_base = stage_start[s];
         a.prev_sites = s > 0 ? sites + stage_start[s - 1] : nullptr;
         a.prev_count = s > 0 ? stage_start[s] - stage_start[s - 1] : 0;
-        e = ptca::launch_stage(prec, a, stm);
+        e = ptca::launch_stage(prec, 8, a, stm);
         if (e != cudaSuccess) return ptca_internal_fail(PTCA_ERR_CUDA, cudaGetErrorString(e));
     }
     if (n_stages > 0) {

@@ -30,7 +30,8 @@ EXPORTED = [
     "ptca_sweep_noalloc", "ptca_set_pipeline", "ptca_selftest_barrier_timeout", "ptca_set_resolve_margin",
     "ptca_surrogate_param_count", "ptca_surrogate_init", "ptca_surrogate_get_params", "ptca_surrogate_set_params",
     "ptca_surrogate_collect", "ptca_surrogate_train", "ptca_surrogate_grad", "ptca_surrogate_predict",
-    "ptca_surrogate_enable", "ptca_set_checker", "ptca_checker_read",
+    "ptca_surrogate_enable", "ptca_set_checker", "ptca_checker_read", "ptca_set_launch_config",
+    "ptca_get_launch_config", "ptca_autotune",
 ]
 
 
@@ -38,6 +39,10 @@ class PtcaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("pipeline", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class Lattice(ctypes.Structure):
@@ -107,6 +112,9 @@ def lib():
             "ptca_set_pipeline": ([vp, i32, dbl], i32),
             "ptca_set_resolve_margin": ([vp, dbl], i32),
             "ptca_set_checker": ([vp, i32], i32),
+            "ptca_set_launch_config": ([vp, P(LaunchConfig)], i32),
+            "ptca_get_launch_config": ([vp, P(LaunchConfig)], i32),
+            "ptca_autotune": ([vp, i32, P(LaunchConfig), ctypes.c_char_p, i32, vp], i32),
             "ptca_checker_read": ([vp, vp, i32, vp], i32),
             "ptca_surrogate_param_count": ([], i32),
             "ptca_surrogate_init": ([vp, ctypes.c_uint64, vp], i32),
@@ -284,6 +292,26 @@ def ptca_set_pipeline(h, mode: int, barrier_timeout_s: float = 30.0) -> None:
 
 def ptca_set_resolve_margin(h, margin: float) -> None:
     _check(lib().ptca_set_resolve_margin(h, margin))
+
+
+def ptca_set_launch_config(h, pipeline: int, warps_per_cta: int = 8, ctas_per_sm: int = 0) -> None:
+    _check(lib().ptca_set_launch_config(h, ctypes.byref(LaunchConfig(pipeline, warps_per_cta, ctas_per_sm))))
+
+
+def ptca_get_launch_config(h) -> LaunchConfig:
+    out = LaunchConfig()
+    _check(lib().ptca_get_launch_config(h, ctypes.byref(out)))
+    return out
+
+
+def ptca_autotune(h, trial_sweeps: int = 3, stream=None):
+    """Time every launch configuration, apply the fastest; returns (best, table)
+    with table the parsed JSON of every candidate."""
+    import json
+    best = LaunchConfig()
+    buf = ctypes.create_string_buffer(1 << 14)
+    _check(lib().ptca_autotune(h, trial_sweeps, ctypes.byref(best), buf, len(buf), _stream(stream)))
+    return best, json.loads(buf.value.decode())
 
 
 def ptca_set_checker(h, on: bool) -> None:

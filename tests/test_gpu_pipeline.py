@@ -83,3 +83,69 @@ def test_open_lattice_L10_ragged_windows_up_to_n200(prec):
         sizes.add(2 * ex * ey)
     assert max(sizes) == 200 and min(sizes) <= 72
     _check_sweep_against_oracle(cfg, sweeps=1, sample=5)
+
+
+@pytest.mark.parametrize("lat", [(32, 8), (8, 4)])
+def test_launch_configurations_compute_the_same_chain(lat):
+    # CTA width (8 or 4 warps), pipeline and persistent CTAs per SM change
+    # only how the work is laid out: with the decision guard the decisions,
+    # hence the spins, are identical; free energies agree to rounding.
+    L, Lc = lat
+    cfg = P.Config(Lx=L, Ly=L, L_c=Lc, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, T=0.05, seed=17,
+                   precision=P.MIXED)
+    runs = []
+    for pl, nw, cps in [(P.PIPELINE_GRAPH, 8, 0), (P.PIPELINE_STAGES, 4, 0), (P.PIPELINE_PERSISTENT, 4, 0),
+                        (P.PIPELINE_GRAPH, 4, 1), (P.PIPELINE_PERSISTENT, 8, 1)]:
+        ctx = P.Context(cfg)
+        P.ptca_set_launch_config(ctx.h, pl, nw, cps)
+        got = P.ptca_get_launch_config(ctx.h)
+        assert (got.pipeline, got.warps_per_cta, got.ctas_per_sm) == (pl, nw, cps)
+        ctx.sweep(2)
+        rec = [x.cpu().numpy() for x in ctx.record()]
+        runs.append((ctx.spins().cpu().numpy(), rec))
+        ctx.close()
+    S_ref, (site, Fo, Fn, lnu, acc) = runs[0]
+    for S, (site2, Fo2, Fn2, lnu2, acc2) in runs[1:]:
+        assert np.array_equal(site, site2) and np.array_equal(acc, acc2)
+        assert np.array_equal(S, S_ref)
+        assert np.max(np.abs(Fo2 - Fo) / np.maximum(1.0, np.abs(Fo))) < 1e-5
+
+
+def test_autotune_restores_the_chain_and_applies_the_fastest():
+    cfg = P.Config(Lx=32, Ly=32, L_c=8, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, T=0.05, seed=23,
+                   precision=P.MIXED)
+    ctx = P.Context(cfg)
+    ctx.sweep(1)
+    S0 = ctx.spins().cpu().numpy()
+    best, table = P.ptca_autotune(ctx.h, 2)
+    assert np.array_equal(ctx.spins().cpu().numpy(), S0)
+    got = P.ptca_get_launch_config(ctx.h)
+    assert (got.pipeline, got.warps_per_cta, got.ctas_per_sm) == (best.pipeline, best.warps_per_cta, best.ctas_per_sm)
+    timed = [c for c in table["candidates"] if c["ms_per_sweep"] is not None]
+    assert len(timed) >= 6 and {c["warps_per_cta"] for c in timed} == {4, 8}
+    fastest = min(timed, key=lambda c: c["ms_per_sweep"])
+    names = {P.PIPELINE_STAGES: "stages", P.PIPELINE_PERSISTENT: "persistent", P.PIPELINE_GRAPH: "graph"}
+    assert (names[best.pipeline], best.warps_per_cta, best.ctas_per_sm) == (
+        fastest["pipeline"], fastest["warps_per_cta"], fastest["ctas_per_sm"])
+    # The next sweep continues the chain exactly as without the tuning.
+    ctx.sweep(1)
+    ref = P.Context(cfg)
+    ref.sweep(2)
+    assert np.array_equal(ctx.spins().cpu().numpy(), ref.spins().cpu().numpy())
+    ctx.close()
+    ref.close()
+
+
+def test_launch_configuration_is_validated():
+    ctx = P.Context(P.Config(Lx=16, Ly=16, L_c=8, precision=P.FP64))
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(ctx.h, P.PIPELINE_GRAPH, 4, 0)   # 4-warp kernels are FP32 only
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(ctx.h, P.PIPELINE_GRAPH, 6, 0)
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(ctx.h, P.PIPELINE_GRAPH, 8, 99)
+    ctx.close()
+    ctx = P.Context(P.Config(Lx=40, Ly=40, L_c=10, periodic=0, stride=10, precision=P.MIXED))  # n up to 200
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(ctx.h, P.PIPELINE_STAGES, 4, 0)
+    ctx.close()
