@@ -36,11 +36,10 @@ N_ORDER = 128
 # triangle once with 16 real FMA per complex element (rank-2 update + both
 # halves of the Hermitian matrix-vector product): sum_m 32 m(m+1)/2 ~ (16/3) n^3.
 HH_FLOPS = sum(32 * m * (m + 1) // 2 for m in range(1, N_ORDER))
-# DRAM bytes (read + write) of one launch of the persistent mixed sweep kernel
-# on this workload, from the ncu capture summarised in
-# profiles/k_sweep_persistent_f32_100x100_Lc8_mixed.md.  Set to None whenever
-# that kernel changes until it is captured again.
-PERSISTENT_F32_DRAM_BYTES = None
+# DRAM bytes (read + write) of one launch of each candidate dominant kernel
+# on this workload, from the ncu captures summarised under profiles/.  A
+# value goes back to None whenever its kernel changes, until captured again.
+DRAM_BYTES_PER_LAUNCH = {"k_stage<float,4>": 317_696, "k_sweep_persistent<float,4>": None}
 
 
 def peaks():
@@ -198,13 +197,18 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
-def time_sweeps(ctx, steps, warmup, flush_buf, stream):
-    """Per-step device time (ms) of one sweep each, L2 flushed between steps."""
+def time_sweeps(ctx, steps, warmup, flush_buf, stream, kernel_timing=False):
+    """Per-step device time (ms) of one sweep each, L2 flushed between steps.
+    With kernel_timing the library records the duration of every stage and
+    re-solve kernel launched in the timed steps (read with ptca_kernel_times)."""
     import torch
     import paper_1502_07028_gb300 as P
     for _ in range(warmup):
         P.ptca_sweep(ctx.h, 1, stats=False, stream=stream)
     torch.cuda.synchronize()
+    if kernel_timing:
+        P.ptca_kernel_times(ctx.h, stream=stream)  # clear
+        P.ptca_set_kernel_timing(ctx.h, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for i in range(steps):
         flush_buf.add_(1)  # write 256 MiB: evicts the 129 MB L2 between timed steps
@@ -311,11 +315,16 @@ def main():
                      + " (autotuned)")
     barrier(world)
     torch.cuda.synchronize()
+    per_stage = best.pipeline == P.PIPELINE_STAGES
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
-        step_ms = time_sweeps(ctx, args.steps, args.warmup, flush, stream)
+        # Per-stage pipeline: the library brackets each stage-kernel launch
+        # with CUDA events on the stream, for the kernel's own duration.
+        step_ms = time_sweeps(ctx, args.steps, args.warmup, flush, stream, kernel_timing=per_stage)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
+    kt = P.ptca_kernel_times(ctx.h, stream=stream) if per_stage else None
+    P.ptca_set_kernel_timing(ctx.h, False)
     barrier(world)
     total_ms = max_over_ranks(world, sum(step_ms))
     value = world * N * args.steps / (total_ms * 1e-3)
@@ -364,15 +373,27 @@ def main():
     ctx64.close()
     fp64_value = N * args.fp64_steps / (sum(fp64_ms) * 1e-3)
 
-    # --- roofline of the dominant kernel (the persistent sweep kernel: one
-    # launch per sweep; its FP32 work is the Householder reduction)
-    # One persistent launch per sweep, or per stage a stage kernel and a
-    # re-solve kernel plus the closing copy and counter kernels.
+    # --- roofline of the dominant kernel: the stage kernel (one launch per
+    # stage) when the per-stage pipeline is chosen, else the persistent
+    # kernel (one launch per sweep); its FP32 work is the Householder
+    # reduction.  Launches per step: one persistent launch, or per stage a
+    # stage kernel and a re-solve kernel plus the closing copy and counter
+    # kernels.
     launches_per_step = 1 if best.pipeline != P.PIPELINE_STAGES else 2 * n_stages + 2
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or 2070.0
-    matrices_per_step = 2 * N
-    achieved_tflops = matrices_per_step * HH_FLOPS / (ms_per_step * 1e-3) / 1e12
+    if kt is not None and kt[1] > 0:
+        # k_stage: one launch per stage, 2 matrices per visit of the stage.
+        kernel_name = "k_stage<float,4>"
+        launch_ms = kt[0] / kt[1]
+        matrices_per_launch = 2 * N / n_stages
+        resolve_ms_per_step = kt[2] / args.steps
+    else:
+        kernel_name = "k_sweep_persistent<float,4>"
+        launch_ms = ms_per_step
+        matrices_per_launch = 2 * N
+        resolve_ms_per_step = None
+    achieved_tflops = matrices_per_launch * HH_FLOPS / (launch_ms * 1e-3) / 1e12
     peak = fp32_alu_peak_tflops(clocks["sm_max_mhz"] or 2070.0)
 
     cpu = None
@@ -407,8 +428,10 @@ def main():
             "speedup_vs_fp64_path": value / fp64_value / world,
             "eigensolves_per_s": 2 * value,
             "acceptance": acc_rate,
-            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak, "traffic": PERSISTENT_F32_DRAM_BYTES,
+            "roofline": {"bound": "alu", "kernel": kernel_name, "launch_ms": launch_ms,
+                         "resolve_ms_per_step": resolve_ms_per_step,
+                         "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak, "traffic": DRAM_BYTES_PER_LAUNCH.get(kernel_name),
                          "note": "FP32 FMA pipe, Householder flops only; peak = 152 SM x 128 lanes x 2 x max clock"},
             "mixed_error": mixed_error,
             "cpu_baseline": cpu,

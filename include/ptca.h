@@ -243,6 +243,17 @@ ptca_status ptca_get_launch_config(const ptca_ctx* ctx, ptca_launch_config* out)
 ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_config* best, char* json, int32_t json_cap,
                           void* stream);
 
+/* Per-kernel timing of the per-stage pipeline (off by default).  While on,
+ * every stage-kernel launch and every re-solve launch of ptca_sweep is
+ * bracketed by CUDA events on the sweep's stream.  ptca_kernel_times
+ * synchronises `stream`, writes out[0] = total ms of the stage kernels,
+ * out[1] = their launch count, out[2] = total ms of the re-solve kernels,
+ * out[3] = their launch count (host array of 4 doubles), and clears the
+ * record.  The persistent pipelines time as one launch per call of
+ * ptca_sweep (ptca_sweep_stats.seconds). */
+ptca_status ptca_set_kernel_timing(ptca_ctx* ctx, int32_t on);
+ptca_status ptca_kernel_times(ptca_ctx* ctx, double* out, void* stream);
+
 /* PTCA_MIXED decision guard.  The FP32 reduction leaves an error of about
  * 1e-4 in dF at n = 128, so a Metropolis decision whose margin
  * |ln u + dF/T| is below `margin` is deferred: both cluster matrices of that

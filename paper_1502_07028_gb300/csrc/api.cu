@@ -164,8 +164,35 @@ static void drop_graph(ptca_ctx* c) {
     c->graph_sweeps = -1;
 }
 
+// A launch, bracketed by events on `st` when kernel timing is on.
+template <typename F> static cudaError_t timed_launch(ptca_ctx* ctx, int kind, cudaStream_t st, F launch) {
+    if (!ctx->timing) return launch();
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e != cudaSuccess) {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        return e;
+    }
+    ctx->tev.push_back(ev[0]);
+    ctx->tev.push_back(ev[1]);
+    ctx->tkind.push_back(kind);
+    return cudaSuccess;
+}
+
+static void drop_timing_events(ptca_ctx* c) {
+    for (cudaEvent_t ev : c->tev) cudaEventDestroy(ev);
+    c->tev.clear();
+    c->tkind.clear();
+}
+
 static void free_ctx(ptca_ctx* c) {
     drop_graph(c);
+    drop_timing_events(c);
     ptca_free_surrogate(c);
     void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
@@ -494,9 +521,9 @@ static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st
             a.sg_dFt = nullptr;
             if (ctx->checker) e = check_stage(ctx, a, s, st);
             if (e == cudaSuccess && ctx->sg.enabled && !col) e = ptca_screen_stage(ctx, a, st);
-            if (e == cudaSuccess) e = ptca::launch_stage(ctx->prec, ctx->nw, a, st);
+            if (e == cudaSuccess) e = timed_launch(ctx, 0, st, [&] { return ptca::launch_stage(ctx->prec, ctx->nw, a, st); });
             if (e == cudaSuccess && a.margin > 0.0) {
-                e = ptca::launch_resolve(a, ctx->resolve_grid, st);
+                e = timed_launch(ctx, 1, st, [&] { return ptca::launch_resolve(a, ctx->resolve_grid, st); });
                 if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag_count, 0, sizeof(unsigned int), st);
             }
             prev_s = s;
@@ -575,6 +602,30 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
     ctx->pipeline = mode;
     ctx->timeout_ns = (unsigned long long)(barrier_timeout_s * 1e9);
     drop_graph(ctx);
+    return PTCA_OK;
+}
+
+ptca_status ptca_set_kernel_timing(ptca_ctx* ctx, int32_t on) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    ctx->timing = on != 0;
+    if (!ctx->timing) drop_timing_events(ctx);
+    return PTCA_OK;
+}
+
+ptca_status ptca_kernel_times(ptca_ctx* ctx, double* out, void* stream) {
+    if (!ctx || !out) return fail(PTCA_ERR_INVALID, "null argument");
+    PTCA_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    for (int q = 0; q < 4; ++q) out[q] = 0.0;
+    for (size_t i = 0; i < ctx->tkind.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->tev[2 * i], ctx->tev[2 * i + 1]) != cudaSuccess) {
+            drop_timing_events(ctx);
+            return fail(PTCA_ERR_CUDA, "kernel timing events were not recorded on this stream");
+        }
+        out[2 * ctx->tkind[i]] += ms;
+        out[2 * ctx->tkind[i] + 1] += 1.0;
+    }
+    drop_timing_events(ctx);
     return PTCA_OK;
 }
 

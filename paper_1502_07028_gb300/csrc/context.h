@@ -99,6 +99,11 @@ struct ptca_ctx {
     double* d_chk_eig = nullptr;              // [2 precisions][check_chunk][2][nA]
     double* d_chk_F = nullptr;                // [2 precisions][check_chunk][2]
     unsigned long long* d_chk_out = nullptr;  // [nstages][4], bits of non-negative doubles
+    // optional per-kernel timing of the per-stage pipeline: event pairs
+    // around each stage launch (kind 0) and re-solve launch (kind 1)
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;
+    std::vector<int> tkind;
     // surrogate network for delayed-acceptance screening
     ptca::SurrogateState sg;
 };

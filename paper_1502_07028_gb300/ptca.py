@@ -31,7 +31,7 @@ EXPORTED = [
     "ptca_surrogate_param_count", "ptca_surrogate_init", "ptca_surrogate_get_params", "ptca_surrogate_set_params",
     "ptca_surrogate_collect", "ptca_surrogate_train", "ptca_surrogate_grad", "ptca_surrogate_predict",
     "ptca_surrogate_enable", "ptca_set_checker", "ptca_checker_read", "ptca_set_launch_config",
-    "ptca_get_launch_config", "ptca_autotune",
+    "ptca_get_launch_config", "ptca_autotune", "ptca_set_kernel_timing", "ptca_kernel_times",
 ]
 
 
@@ -115,6 +115,8 @@ def lib():
             "ptca_set_launch_config": ([vp, P(LaunchConfig)], i32),
             "ptca_get_launch_config": ([vp, P(LaunchConfig)], i32),
             "ptca_autotune": ([vp, i32, P(LaunchConfig), ctypes.c_char_p, i32, vp], i32),
+            "ptca_set_kernel_timing": ([vp, i32], i32),
+            "ptca_kernel_times": ([vp, vp, vp], i32),
             "ptca_checker_read": ([vp, vp, i32, vp], i32),
             "ptca_surrogate_param_count": ([], i32),
             "ptca_surrogate_init": ([vp, ctypes.c_uint64, vp], i32),
@@ -312,6 +314,19 @@ def ptca_autotune(h, trial_sweeps: int = 3, stream=None):
     buf = ctypes.create_string_buffer(1 << 14)
     _check(lib().ptca_autotune(h, trial_sweeps, ctypes.byref(best), buf, len(buf), _stream(stream)))
     return best, json.loads(buf.value.decode())
+
+
+def ptca_set_kernel_timing(h, on: bool) -> None:
+    _check(lib().ptca_set_kernel_timing(h, 1 if on else 0))
+
+
+def ptca_kernel_times(h, stream=None):
+    """(stage_ms_total, stage_launches, resolve_ms_total, resolve_launches)
+    since the last call; clears the record."""
+    import numpy as np
+    out = np.zeros(4, dtype=np.float64)
+    _check(lib().ptca_kernel_times(h, _ptr(out), _stream(stream)))
+    return float(out[0]), int(out[1]), float(out[2]), int(out[3])
 
 
 def ptca_set_checker(h, on: bool) -> None:

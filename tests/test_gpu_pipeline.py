@@ -149,3 +149,20 @@ def test_launch_configuration_is_validated():
     with pytest.raises(P.PtcaError):
         P.ptca_set_launch_config(ctx.h, P.PIPELINE_STAGES, 4, 0)
     ctx.close()
+
+
+def test_kernel_timing_counts_the_stage_launches():
+    cfg = P.Config(Lx=32, Ly=32, L_c=8, schedule=P.SCHEDULE_BLOCK, T=0.05, seed=3, precision=P.MIXED)
+    ctx = P.Context(cfg)
+    ns = len(P.ptca_schedule(cfg))
+    P.ptca_set_launch_config(ctx.h, P.PIPELINE_STAGES, 8, 0)
+    P.ptca_set_kernel_timing(ctx.h, True)
+    ctx.sweep(2)
+    st_ms, st_n, rs_ms, rs_n = P.ptca_kernel_times(ctx.h)
+    assert st_n == 2 * ns and rs_n == 2 * ns and st_ms > 0 and rs_ms >= 0
+    assert P.ptca_kernel_times(ctx.h) == (0.0, 0, 0.0, 0)   # read clears
+    P.ptca_set_launch_config(ctx.h, P.PIPELINE_GRAPH, 8, 0)
+    ctx.sweep(1)
+    assert P.ptca_kernel_times(ctx.h)[1] == 0               # one persistent launch: not per-stage
+    P.ptca_set_kernel_timing(ctx.h, False)
+    ctx.close()
