@@ -336,7 +336,9 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
                 widest = std::max(widest, sms * ptca::persistent_blocks_per_sm(c->prec, 4, c->nA));
             const int slots = std::max(widest, c->resolve_grid);
             c->gA_stride = (int64_t)c->nA * (c->nA + 1) / 2;
-            ce = dalloc(&c->d_gA, (size_t)slots * (size_t)c->gA_stride);
+            // + 64 elements: the fused pass may load up to 31 elements past a
+            // slot (masked lanes of the diagonal chunk), also past the last.
+            ce = dalloc(&c->d_gA, (size_t)slots * (size_t)c->gA_stride + 64);
             c->margin = 1e-2;
         }
     }

@@ -204,13 +204,14 @@ template <typename T> struct PassRows { static constexpr int value = 4; };
 template <> struct PassRows<float> { static constexpr int value = 8; };
 template <> struct PassRows<dfl> { static constexpr int value = 2; };
 
-// Sum over the warps of a per-warp partial (red has NW slots; the caller
+// Sum over the first nact warps of a per-warp partial (the caller
 // synchronises between the write and the read).
 template <typename T, int NW>
-__device__ __forceinline__ T sum_partials(const T* red) {
+__device__ __forceinline__ T sum_partials(const T* red, int nact) {
     T s = red[0];
 #pragma unroll
-    for (int w = 1; w < NW; ++w) s += red[w];
+    for (int w = 1; w < NW; ++w)
+        if (w < nact) s += red[w];
     return s;
 }
 
@@ -223,6 +224,18 @@ __device__ __forceinline__ void reflector_head(T s2, cplx_t<T> x0, cplx_t<T>& fi
     const cplx_t<T> ph = ax0 > T(0) ? mk(x0.x / ax0, x0.y / ax0) : mk(T(1), T(0));
     first = mk(x0.x + ph.x * sigma, x0.y + ph.y * sigma);
     tau = sigma > T(0) ? T(1) / (sigma * (sigma + ax0)) : T(0);
+}
+// FP32: reciprocal square roots and a fast reciprocal.  Their few-ulp errors
+// are far below the FP32 reduction's own, and every thread evaluates this.
+template <>
+__device__ __forceinline__ void reflector_head<float>(float s2, float2 x0, float2& first, float& tau) {
+    const float ax2 = x0.x * x0.x + x0.y * x0.y;
+    const float sigma = s2 > 0.f ? s2 * rsqrtf(s2) : 0.f;
+    const float rx = ax2 > 0.f ? rsqrtf(ax2) : 0.f;
+    const float ax0 = ax2 * rx;
+    const float2 ph = ax2 > 0.f ? make_float2(x0.x * rx, x0.y * rx) : make_float2(1.f, 0.f);
+    first = make_float2(x0.x + ph.x * sigma, x0.y + ph.y * sigma);
+    tau = sigma > 0.f ? __fdividef(1.f, sigma * (sigma + ax0)) : 0.f;
 }
 
 template <typename T, int NT, int NW>
@@ -258,18 +271,21 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
     T tau;
     {
         const int ri = tid;
-        T s2p = T(0);
-        if (ri < n) {
-            const V a = A[tri(ri)];
-            if (ri == 0) d[0] = double(a.x);
-            if (ri >= 1) s2p = cabs2(a);
-            if (ri >= 2) Vb[ri] = a;
-            if (ri == 1) sc.sx[0] = a;
+        const int nact = (n + 31) >> 5;  // warps holding entries
+        if (warp < nact) {
+            T s2p = T(0);
+            if (ri < n) {
+                const V a = A[tri(ri)];
+                if (ri == 0) d[0] = double(a.x);
+                if (ri >= 1) s2p = cabs2(a);
+                if (ri >= 2) Vb[ri] = a;
+                if (ri == 1) sc.sx[0] = a;
+            }
+            s2p = warp_sum(s2p);
+            if (lane == 0) sc.redB[warp] = s2p;
         }
-        s2p = warp_sum(s2p);
-        if (lane == 0) sc.redB[warp] = s2p;
         __syncthreads();
-        const T s2 = sum_partials<T, NW>(sc.redB);
+        const T s2 = sum_partials<T, NW>(sc.redB, nact);
         if (tid == 0) e2[0] = double(s2);
         reflector_head(s2, sc.sx[0], vfirst, tau);
     }
@@ -309,21 +325,35 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
             const int ri0 = b * RB;
             V ui[RB], wi[RB], vi[RB], racc[RB];
             int base[RB];
+            const bool full_rows = ri0 + RB - 1 < m;
+            if (full_rows) {
+                int bi = tri(j0 + ri0) + j0;
 #pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const int ri = ri0 + r;
-                const bool ok = ri < m;
-                const int i = j0 + ri;
-                ui[r] = ok ? U_[i] : zero;
-                wi[r] = ok ? Wv[i] : zero;
-                vi[r] = ok ? V_[i] : zero;
-                base[r] = ok ? tri(i) + j0 : 0;
-                racc[r] = zero;
+                for (int r = 0; r < RB; ++r) {
+                    const int i = j0 + ri0 + r;
+                    ui[r] = U_[i];
+                    wi[r] = Wv[i];
+                    vi[r] = V_[i];
+                    base[r] = bi;
+                    bi += i + 1;
+                    racc[r] = zero;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const int ri = ri0 + r;
+                    const bool ok = ri < m;
+                    const int i = j0 + ri;
+                    ui[r] = ok ? U_[i] : zero;
+                    wi[r] = ok ? Wv[i] : zero;
+                    vi[r] = ok ? V_[i] : zero;
+                    base[r] = ok ? tri(i) + j0 : 0;
+                    racc[r] = zero;
+                }
             }
             if (ri0 == 0) vi[0] = vfirst;
             const int last = (ri0 + RB - 1 < m ? ri0 + RB - 1 : m - 1);
             const int nch = (last >> 5) + 1;
-            const bool full_rows = ri0 + RB - 1 < m;
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 if (t < nch) {
@@ -342,16 +372,23 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
                         }
                         continue;
                     }
+                    // Diagonal chunk: lane jr holds element (ri, jr) for
+                    // jr <= ri.  A masked lane still loads base + jr -- at
+                    // most 31 elements past the packed triangle's end, which
+                    // the matrix buffers are padded for -- and its value,
+                    // possibly stale or non-finite, is replaced by zero
+                    // before both sums.  The diagonal's imaginary part is
+                    // mathematically zero under the update and only its real
+                    // part is ever read.
 #pragma unroll
                     for (int r = 0; r < RB; ++r) {
                         const int ri = ri0 + r;
                         const bool ok = (ri < m) && (jr <= ri);
-                        V a = A[ok ? base[r] + jr : 0];
+                        V a = A[base[r] + jr];
                         a = cfms_conj_b(ui[r], wc[t], a);
                         a = cfms_conj_b(wi[r], uc[t], a);
-                        if (jr == ri) a.y = T(0);
-                        a = ok ? a : zero;
                         if (ok) A[base[r] + jr] = a;
+                        a = ok ? a : zero;
                         racc[r] = cfma(a, vc[t], racc[r]);
                         const V vrow = (jr < ri) ? vi[r] : zero;
                         cacc[t] = cfma_conj_a(a, vrow, cacc[t]);
@@ -384,8 +421,9 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
         // partial sums of entry ri) and the partial sums of v^H p.
         const int ri = tid;
         const bool mine = ri < m;
+        const int nact = (m + 31) >> 5;  // warps holding entries
         V v = zero, p = zero;
-        {
+        if (warp < nact) {
             T sp = T(0);
             if (mine) {
                 p = pr[ri];
@@ -404,8 +442,8 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
         // ---- w = p - (tau s / 2) v, the explicit update of pivot column
         // j0 with (v_k, w_k), d_j0, and the partial sums of ||x||^2 for the
         // next reflector, whose entries past the first go to Vn.
-        {
-            const T K = T(0.5) * tau * sum_partials<T, NW>(sc.redA);
+        if (warp < nact) {
+            const T K = T(0.5) * tau * sum_partials<T, NW>(sc.redA, nact);
             const V p0 = pr[0];
             const V w0 = mk(p0.x - K * vfirst.x, p0.y - K * vfirst.y);
             T s2p = T(0);
@@ -428,7 +466,7 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
         // ---- ||x||^2, and the next reflector's first entry and tau.
         if constexpr (kSharedTail) {
             if (warp == 0) {
-                const T s2 = sum_partials<T, NW>(sc.redB);
+                const T s2 = sum_partials<T, NW>(sc.redB, nact);
                 if (lane == 0) e2[j0] = double(s2);
                 if (k + 1 <= n - 3) {
                     V f;
@@ -440,7 +478,7 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
             __syncthreads();
             if (k + 1 <= n - 3) { vfirst = sc.sx[1]; tau = sc.sx[2].x; }
         } else {
-            const T s2 = sum_partials<T, NW>(sc.redB);
+            const T s2 = sum_partials<T, NW>(sc.redB, nact);
             if (tid == 0) e2[j0] = double(s2);
             if (k + 1 <= n - 3) reflector_head(s2, sc.sx[0], vfirst, tau);
         }
