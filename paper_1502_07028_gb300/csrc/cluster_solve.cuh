@@ -668,22 +668,29 @@ __device__ __forceinline__ int sturm_count_df(int n, const float* dh, const floa
     return c;
 }
 
-// Sturm count and logarithmic derivative of det(T - x), as newton_pass_f64.
+// Sturm count and logarithmic derivative s = sum_i q_i'/q_i of det(T - x),
+// as newton_pass_f64.  The pivot chain q_i runs in double-float: near an
+// eigenvalue one pivot is tiny and must be resolved far below FP32.  The
+// derivative chain q_i' = -1 + e2_{i-1} q_{i-1}' / q_{i-1}^2 and the sum s run
+// in FP32 on the leading parts of those accurate pivots: s only sets a
+// Newton correction of size ~1e-6 ||T||, so its FP32 relative error moves
+// the result by ~1e-12 ||T||.
 __device__ __forceinline__ int newton_pass_df(int n, const float* dh, const float* dl, const float* eh,
                                               const float* el, dfl x, float pivmin, double& s) {
     dfl q = pivot_guard(dfl(dh[0], dl[0]) - x, pivmin);
-    dfl dq = dfl(-1.f, 0.f), acc = dfl(0.f, 0.f);
+    float dq = -1.f, acc = 0.f;
     int c = q.hi < 0.f;
     for (int i = 1; i < n; ++i) {
         const dfl r = rcp_df(q);
-        acc = acc + dq * r;
+        const float rh = r.hi;
+        acc = __fmaf_rn(dq, rh, acc);
         const dfl er = dfl(eh[i - 1], el[i - 1]) * r;
         const dfl qn = (dfl(dh[i], dl[i]) - x) - er;
-        dq = er * r * dq - dfl(1.f, 0.f);
+        dq = __fmaf_rn(__fmul_rn(er.hi, rh), dq, -1.f);
         q = pivot_guard(qn, pivmin);
         c += q.hi < 0.f;
     }
-    s = double(acc + dq * rcp_df(q));
+    s = (double)__fmaf_rn(dq, rcp_df(q).hi, acc);
     return c;
 }
 

@@ -146,15 +146,33 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
         const int k = tid / G, j = tid % G;
         const float lof = (float)lo * (lo < 0 ? 1.0000002f : 0.9999998f) - 1e-30f;
         const float hif = (float)hi * (hi > 0 ? 1.0000002f : 0.9999998f) + 1e-30f;
+        // Sampling round: thread t counts the eigenvalues below the point
+        // lof + (t + 1) h0 (P = blockDim points); eigenvalue k then starts
+        // from the gap between the last point counting <= k and the next,
+        // P + 1 times narrower than the Gershgorin interval.  The counts live
+        // in the column-sum scratch, free after the reduction.
+        const int P = (int)blockDim.x;
+        const float h0 = (hif - lof) / (float)(P + 1);
+        int* cnt = reinterpret_cast<int*>(c.hh.pc);
+        cnt[tid] = sturm_count_f32(n, c.df, c.e2f, lof + (float)(tid + 1) * h0, s_pivminf);
+        __syncthreads();
         // Bracket tolerance, floored so that a zero matrix (nrm = 0) still
         // gives a finite round count; the count is also capped (64 rounds
         // narrow any float bracket below one ulp even for G = 1).
         const float atolf = fmaxf(2.0f * FLT_EPSILON * (float)nrm, 1e-30f);
-        const float ratio = (hif - lof) / atolf;
+        const float ratio = 2.f * h0 / atolf;
         int rounds = ratio > 1.0f ? (int)ceilf(log2f(ratio) / log2f((float)(G + 1))) + 1 : 1;
         rounds = rounds < 64 ? rounds : 64;
         if ((warp * 32) / G < K) {
-            float a = lof, b = hif;
+            // Last sample index with count <= k (-1: none), by binary search
+            // over the non-decreasing counts.
+            int lo_i = -1, hi_i = P;
+            while (hi_i - lo_i > 1) {
+                const int mid = (lo_i + hi_i) >> 1;
+                if (cnt[mid] <= k) lo_i = mid; else hi_i = mid;
+            }
+            float a = lo_i < 0 ? lof : lof + (float)(lo_i + 1) * h0;
+            float b = hi_i >= P ? hif : lof + (float)(hi_i + 1) * h0;
             const unsigned gmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
             const int gshift = (lane / G) * G;
             for (int r = 0; r < rounds; ++r) {
