@@ -528,6 +528,20 @@ __device__ __forceinline__ int sturm_count_f64(int n, const double* d, const dou
     return c;
 }
 
+// 2^-e with e the exponent of the largest |value| among a, b, c, d: scaling a
+// sequence by it is exact and keeps its entries near 1 in magnitude.
+__device__ __forceinline__ float pow2_rescale(float a, float b, float c = 0.f, float d = 0.f) {
+    const float m = fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(c), fabsf(d)));
+    int fe = 254 - (int)((__float_as_uint(m) >> 23) & 0xffu);  // biased exponent of 2^-e
+    fe = fe < 1 ? 1 : (fe > 254 ? 254 : fe);
+    return __uint_as_float((unsigned)fe << 23);
+}
+
+// FP32 Sturm count, pivot form (Barth, Martin and Wilkinson's bisection with
+// Kahan's pivot guard).  Run by every thread of the CTA at once in the
+// multisection, it is throughput bound: its reciprocal goes to the separate
+// MUFU pipe, which measured faster here than the division-free three-term
+// recurrence with its extra ALU work.
 __device__ __forceinline__ int sturm_count_f32(int n, const float* d, const float* e2, float x, float pivmin) {
     float q = d[0] - x;
     if (fabsf(q) < pivmin) q = -pivmin;
@@ -639,58 +653,73 @@ __device__ __forceinline__ double newton_polish_f64(int n, const double* d, cons
 // ---------------------------------------------------------------------------
 // The same refinements in double-float arithmetic: FP64-class precision on
 // the FP32 pipe.  The tridiagonal is given as float pairs (dh + dl, eh + el),
-// exact copies of the FP64 entries; the pivot guard uses the FP32 pivmin.
+// exact copies of the FP64 entries.
 // ---------------------------------------------------------------------------
 
-// 1/q: the float reciprocal r1 and one Newton correction r1 (1 + e),
-// e = 1 - q r1 evaluated with the FMA error of q.hi r1.
-__device__ __forceinline__ dfl rcp_df(dfl q) {
-    const float r1 = __frcp_rn(q.hi);
-    const float p = __fmul_rn(q.hi, r1);
-    float e = __fsub_rn(1.f, p);
-    e = __fsub_rn(e, __fmaf_rn(q.hi, r1, -p));
-    e = __fmaf_rn(-q.lo, r1, e);
-    return fast_two_sum(r1, __fmul_rn(r1, e));
-}
-
-__device__ __forceinline__ dfl pivot_guard(dfl q, float pivmin) {
-    return fabsf(q.hi) < pivmin ? dfl(-pivmin, 0.f) : q;
-}
-
+// Double-float Sturm count from the leading principal minors
+//   p_-1 = 1, p_0 = d_0 - x, p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2}:
+// the number of sign changes along p_-1 .. p_{n-1} is the number of
+// eigenvalues below x (p_i / p_{i-1} is the pivot of the LDL^T factors).  No
+// division: each step is one two-product sum with a single renormalisation.
+// Every 8 steps the pair is rescaled by a power of two (exact), keeping it in
+// the float range; a minor that is exactly zero takes a tiny value of the
+// sign opposite to its predecessor (as Kahan's guard counts a zero pivot as
+// negative).
 __device__ __forceinline__ int sturm_count_df(int n, const float* dh, const float* dl, const float* eh,
                                               const float* el, dfl x, float pivmin) {
-    dfl q = pivot_guard(dfl(dh[0], dl[0]) - x, pivmin);
-    int c = q.hi < 0.f;
+    dfl p2 = dfl(1.f, 0.f), p1 = dfl(dh[0], dl[0]) - x;
+    if (p1.hi == 0.f) p1 = dfl(-pivmin, 0.f);
+    int c = (int)(__float_as_uint(p1.hi) >> 31);
     for (int i = 1; i < n; ++i) {
-        q = pivot_guard((dfl(dh[i], dl[i]) - x) - dfl(eh[i - 1], el[i - 1]) * rcp_df(q), pivmin);
-        c += q.hi < 0.f;
+        const dfl dx = dfl(dh[i], dl[i]) - x;
+        dfl p = dot2_acc(dfl(0.f, 0.f), dx, p1, -dfl(eh[i - 1], el[i - 1]), p2);
+        if (p.hi == 0.f) p = dfl(-1e-30f * p1.hi, 0.f);
+        c += (int)((__float_as_uint(p.hi) ^ __float_as_uint(p1.hi)) >> 31);
+        p2 = p1;
+        p1 = p;
+        if ((i & 7) == 0) {
+            const float sc = pow2_rescale(p1.hi, p2.hi);
+            p1 = dfl(p1.hi * sc, p1.lo * sc);
+            p2 = dfl(p2.hi * sc, p2.lo * sc);
+        }
     }
     return c;
 }
 
-// Sturm count and logarithmic derivative s = sum_i q_i'/q_i of det(T - x),
-// as newton_pass_f64.  The pivot chain q_i runs in double-float: near an
-// eigenvalue one pivot is tiny and must be resolved far below FP32.  The
-// derivative chain q_i' = -1 + e2_{i-1} q_{i-1}' / q_{i-1}^2 and the sum s run
-// in FP32 on the leading parts of those accurate pivots: s only sets a
-// Newton correction of size ~1e-6 ||T||, so its FP32 relative error moves
-// the result by ~1e-12 ||T||.
+// Sturm count and logarithmic derivative s = p'/p of det(T - x), as
+// newton_pass_f64.  The minors p_i run in double-float: near an eigenvalue
+// p_{n-1} is small and must be resolved far below FP32.  Their derivatives
+//   p'_i = (d_i - x) p'_{i-1} - p_{i-1} - e2_{i-1} p'_{i-2}
+// run in FP32 on the leading parts: s only sets a Newton correction of size
+// ~1e-6 ||T||, so its FP32 relative error moves the result by ~1e-12 ||T||.
+// Minors and derivatives share the power-of-two rescaling, which leaves s
+// unchanged.
 __device__ __forceinline__ int newton_pass_df(int n, const float* dh, const float* dl, const float* eh,
                                               const float* el, dfl x, float pivmin, double& s) {
-    dfl q = pivot_guard(dfl(dh[0], dl[0]) - x, pivmin);
-    float dq = -1.f, acc = 0.f;
-    int c = q.hi < 0.f;
+    dfl p2 = dfl(1.f, 0.f), p1 = dfl(dh[0], dl[0]) - x;
+    float dp2 = 0.f, dp1 = -1.f;
+    if (p1.hi == 0.f) p1 = dfl(-pivmin, 0.f);
+    int c = (int)(__float_as_uint(p1.hi) >> 31);
     for (int i = 1; i < n; ++i) {
-        const dfl r = rcp_df(q);
-        const float rh = r.hi;
-        acc = __fmaf_rn(dq, rh, acc);
-        const dfl er = dfl(eh[i - 1], el[i - 1]) * r;
-        const dfl qn = (dfl(dh[i], dl[i]) - x) - er;
-        dq = __fmaf_rn(__fmul_rn(er.hi, rh), dq, -1.f);
-        q = pivot_guard(qn, pivmin);
-        c += q.hi < 0.f;
+        const dfl dx = dfl(dh[i], dl[i]) - x;
+        const float e2 = eh[i - 1];
+        dfl p = dot2_acc(dfl(0.f, 0.f), dx, p1, -dfl(e2, el[i - 1]), p2);
+        const float dp = __fmaf_rn(dx.hi, dp1, __fmaf_rn(-e2, dp2, -p1.hi));
+        if (p.hi == 0.f) p = dfl(-1e-30f * p1.hi, 0.f);
+        c += (int)((__float_as_uint(p.hi) ^ __float_as_uint(p1.hi)) >> 31);
+        p2 = p1;
+        p1 = p;
+        dp2 = dp1;
+        dp1 = dp;
+        if ((i & 7) == 0) {
+            const float sc = pow2_rescale(p1.hi, p2.hi, dp1, dp2);
+            p1 = dfl(p1.hi * sc, p1.lo * sc);
+            p2 = dfl(p2.hi * sc, p2.lo * sc);
+            dp1 *= sc;
+            dp2 *= sc;
+        }
     }
-    s = (double)__fmaf_rn(dq, rcp_df(q).hi, acc);
+    s = (double)dp1 / double(p1);
     return c;
 }
 
