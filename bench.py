@@ -165,6 +165,54 @@ def cpu_oracle_rate(cfg_kw, budget_s: float = 12.0, max_visits: int = 64):
     return done / dt, done, dt
 
 
+_POOL_STATE = {}
+
+
+def _pool_init(cfg_kw):
+    """Worker start-up: the oracle problem and its initial spins."""
+    import oracle
+    m = oracle.Model(Lx=cfg_kw["Lx"], Ly=cfg_kw["Ly"], Lc=cfg_kw["L_c"], t=cfg_kw["t"], JH=cfg_kw["J_H"],
+                     mu=cfg_kw["mu"], T=cfg_kw["T"], schedule=cfg_kw["schedule"], stride=cfg_kw.get("stride", 0),
+                     proposal=1, cone_deg=cfg_kw["cone_deg"], seed=cfg_kw["seed"])
+    _POOL_STATE["m"] = m
+    _POOL_STATE["S"] = oracle.init_spins(m)
+
+
+def _pool_visit(s):
+    """One visit of stage 0 by the oracle: 2 cluster eigensolves + Metropolis."""
+    import math as _m
+
+    import oracle
+    m, S = _POOL_STATE["m"], _POOL_STATE["S"]
+    Fo = oracle.cluster_free_energy(m, S, s)
+    sn = oracle.propose(m, 0, s, S[s])
+    Fn = oracle.cluster_free_energy(m, S, s, sn)
+    u = oracle.uniform2(m.seed, 0, s, 2)[0]
+    return _m.log(u) < -(Fn - Fo) / m.T
+
+
+def cpu_oracle_rate_pool(cfg_kw, visits_per_core: int = 6):
+    """The oracle on all host cores: the visits of the first stage are
+    independent clusters, run as tasks of a process pool (spawn start, so
+    no CUDA state is inherited).  Returns (updates/s, visits, seconds, cores)."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    m = oracle.Model(Lx=cfg_kw["Lx"], Ly=cfg_kw["Ly"], Lc=cfg_kw["L_c"], t=cfg_kw["t"], JH=cfg_kw["J_H"],
+                     mu=cfg_kw["mu"], T=cfg_kw["T"], schedule=cfg_kw["schedule"], stride=cfg_kw.get("stride", 0),
+                     proposal=1, cone_deg=cfg_kw["cone_deg"], seed=cfg_kw["seed"])
+    stage = [int(x) for x in oracle.schedule(m)[0][: visits_per_core * cores]]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_pool_init, initargs=(cfg_kw,)) as pool:
+        pool.map(_pool_visit, stage[:cores], chunksize=1)   # start-up and warm-up, untimed
+        t0 = time.perf_counter()
+        pool.map(_pool_visit, stage, chunksize=1)
+        dt = time.perf_counter() - t0
+    return len(stage) / dt, len(stage), dt, cores
+
+
 def run_reference(args, world, rank):
     """The oracle as the reference arm, timed on the host cores."""
     if rank != 0:
@@ -174,9 +222,9 @@ def run_reference(args, world, rank):
     oracle.build()
     per_step = []
     visits = 0
+    cores = 1
     for i in range(args.warmup + args.steps):
-        rate, done, dt = cpu_oracle_rate(cfg_kw, budget_s=max(2.0, 30.0 / max(1, args.steps + args.warmup)),
-                                         max_visits=8)
+        rate, done, dt, cores = cpu_oracle_rate_pool(cfg_kw, visits_per_core=2)
         if i >= args.warmup:
             per_step.append(dt / done)
             visits += done
@@ -188,9 +236,10 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_update * N,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "100x100 torus, 8x8 clusters (n=128), cone 30deg, T=0.05, block schedule",
-                   "sample": "first 8 visits of stage 0 per step"},
-        "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{visits} visits (2 Jacobi eigensolves of 128x128 each) over {args.steps} steps"},
+                   "sample": "2 visits of stage 0 per host core per step"},
+        "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{visits} visits (2 Jacobi eigensolves of 128x128 each) over {args.steps} steps, "
+                                   f"independent clusters of stage 0 on a {cores}-process pool"},
         "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -400,9 +449,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        rate, done, dt = cpu_oracle_rate(dict(base), budget_s=15.0, max_visits=48)
-        cpu = {"value": rate, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{done} visits of the first stage (2 Jacobi eigensolves of 128x128 each), {dt:.1f} s"}
+        rate, done, dt, cores = cpu_oracle_rate_pool(dict(base))
+        rate1, done1, dt1 = cpu_oracle_rate(dict(base), budget_s=10.0, max_visits=32)
+        cpu = {"value": rate, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} visits of the first stage (2 Jacobi eigensolves of 128x128 each), independent "
+                         f"clusters on a {cores}-process pool, {dt:.1f} s",
+               "single_core": {"value": rate1, "sample": f"{done1} visits on one core, {dt1:.1f} s"}}
 
     if rank == 0:
         line = {

@@ -321,6 +321,41 @@ def test_observables_ferro_and_neel():
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", [P.FP64, P.MIXED])
+def test_observables_energy_and_filling_match_oracle(prec):
+    # F_site: mean over the sweep's visits of the accepted state's cluster
+    # free energy / N_c; filling: mean of sum_k f(eps_k) / N_c for that state,
+    # f the Fermi function -- both from the oracle's Jacobi spectra of the
+    # windows at each stage start.
+    cfg = P.Config(Lx=8, Ly=8, L_c=4, T=0.05, mu=-6.5, seed=12, precision=prec)
+    ctx = P.Context(cfg)
+    S0 = ctx.spins().cpu().numpy()
+    ctx.sweep(1)
+    site, Fo, Fn, lnu, acc = (x.cpu().numpy() for x in ctx.record())
+    o = ctx.observables()
+    ctx.close()
+    stages = P.ptca_schedule(cfg)
+    starts, _ = _replay(cfg, S0, stages, site, acc, 0)
+    stage_of = {int(s): k for k, st in enumerate(stages) for s in st}
+    m = _oracle_model(cfg)
+    Nc = 16
+    F_acc, fill = [], []
+    for k, s in enumerate(site):
+        s = int(s)
+        Sst = starts[stage_of[s]]
+        sn = oracle.propose(m, 0, s, Sst[s]) if acc[k] else None
+        eps = oracle.eigvalsh(oracle.cluster_hamiltonian(m, Sst, s, sn)[0])
+        F_acc.append(oracle.free_energy(eps, m.mu, m.T))
+        fill.append(np.sum(1.0 / (1.0 + np.exp((eps - m.mu) / m.T))))
+    tol = 1e-9 if prec == P.FP64 else 1e-5
+    assert abs(o.F_site - np.mean(F_acc) / Nc) <= tol * max(1.0, abs(o.F_site))
+    # f' <= 1/(4T) = 5: mixed-precision eigenvalue errors of ~1e-5 move each
+    # Fermi factor by up to ~5e-5.
+    fill_tol = 1e-8 if prec == P.FP64 else 1e-3
+    assert abs(o.filling - np.mean(fill) / Nc) <= fill_tol
+    assert abs(o.acceptance - np.mean(acc)) < 1e-15
+
+
 def test_resume_is_bit_exact():
     # Counter-based randomness: two contexts given the same spins and sweep
     # counter produce identical sweeps.
