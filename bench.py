@@ -39,7 +39,8 @@ HH_FLOPS = sum(32 * m * (m + 1) // 2 for m in range(1, N_ORDER))
 # DRAM bytes (read + write) of one launch of each candidate dominant kernel
 # on this workload, from the ncu captures summarised under profiles/.  A
 # value goes back to None whenever its kernel changes, until captured again.
-DRAM_BYTES_PER_LAUNCH = {"k_stage<float,4>": 308_224, "k_sweep_persistent<float,4>": None}
+DRAM_BYTES_PER_LAUNCH = {"k_stage<float,4,8>": 308_224, "k_stage<float,4,4>": None,
+                         "k_sweep_persistent<float,4,8>": None, "k_sweep_persistent<float,4,4>": None}
 
 
 def peaks():
@@ -433,12 +434,12 @@ def main():
     sm_mhz = clocks["sm_mhz"] or 2070.0
     if kt is not None and kt[1] > 0:
         # k_stage: one launch per stage, 2 matrices per visit of the stage.
-        kernel_name = "k_stage<float,4>"
+        kernel_name = f"k_stage<float,4,{best.warps_per_cta}>"
         launch_ms = kt[0] / kt[1]
         matrices_per_launch = 2 * N / n_stages
         resolve_ms_per_step = kt[2] / args.steps
     else:
-        kernel_name = "k_sweep_persistent<float,4>"
+        kernel_name = f"k_sweep_persistent<float,4,{best.warps_per_cta}>"
         launch_ms = ms_per_step
         matrices_per_launch = 2 * N
         resolve_ms_per_step = None

@@ -13,47 +13,54 @@ constexpr int NW = 8;              // warps per CTA of the cluster kernels
 constexpr int CTA = 32 * NW;
 constexpr double kFermiCut = 40.0; // eigenvalues above mu + 40 T change F by < T e^-40 each
 
-// Two CTAs per SM fit in shared memory for FP32 matrices up to n = 128.
 // Resident CTAs per SM the launch bounds ask for (caps the registers at
-// 65536 / (value * 32 * NWP)): FP32 matrices up to order 128 run two 8-warp
-// or four 4-warp CTAs per SM.
+// 65536 / (value * 32 * NWP)).  Shared memory holds two 8-warp or three
+// 4-warp FP32 CTAs per SM for matrices up to n = 128, one CTA otherwise.
 template <typename T, int NT, int NWP = NW> struct MinBlocks {
-    static constexpr int value = ((sizeof(T) == 4 && NT <= 4) ? 2 : 1) * (8 / NWP);
+    static constexpr int value = (sizeof(T) == 4 && NT <= 4) ? (NWP == 4 ? 3 : 2) : (NWP == 4 ? 2 : 1);
 };
 
 // Shared-memory layout of one cluster CTA (byte offsets, 16-byte aligned).
+// The per-warp column sums pc are live only during the reduction, so the
+// window spins of the build (sp) and the eigenvalue-phase arrays -- bisection
+// brackets, float copies of (d, e2), their low parts and the sampling counts
+// -- share its region.
 struct SmemLayout {
-    size_t A, Vb, Wv, pr, pc, d, e2, df, e2f, dlo, e2lo, sp, lam, red, total;
+    size_t A, Vb, Wv, pr, pc, d, e2, df, e2f, dlo, e2lo, cnt, sp, lam, red, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline size_t max2(size_t a, size_t b) { return a > b ? a : b; }
 
 // nA: largest matrix order stored; nmaxc = 32 * NT; cs = sizeof(complex element);
 // nw: warps per CTA
 __host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs, int nw = NW) {
     SmemLayout L;
     size_t o = 0;
+    const size_t nm = (size_t)nmaxc;
     L.A = o;   o = align16(o + (size_t)nA * (nA + 1) / 2 * cs);
-    L.Vb = o;  o = align16(o + 2 * (size_t)nmaxc * cs);
-    L.Wv = o;  o = align16(o + (size_t)nmaxc * cs);
-    L.pr = o;  o = align16(o + (size_t)nmaxc * cs);
-    L.pc = o;  o = align16(o + (size_t)nw * nmaxc * cs);
-    L.d = o;   o = align16(o + (size_t)nmaxc * sizeof(double));
-    L.e2 = o;  o = align16(o + (size_t)nmaxc * sizeof(double));
-    L.df = o;  o = align16(o + (size_t)nmaxc * sizeof(float));
-    L.e2f = o; o = align16(o + (size_t)nmaxc * sizeof(float));
-    L.dlo = o; o = align16(o + (size_t)nmaxc * sizeof(float));
-    L.e2lo = o; o = align16(o + (size_t)nmaxc * sizeof(float));
-    L.sp = o;  o = align16(o + (size_t)(nmaxc / 2) * 3 * sizeof(double));
-    L.lam = o; o = align16(o + (size_t)nmaxc * 2 * sizeof(float));
+    L.Vb = o;  o = align16(o + 2 * nm * cs);
+    L.Wv = o;  o = align16(o + nm * cs);
+    L.pr = o;  o = align16(o + nm * cs);
+    L.pc = o;
+    L.sp = o;                       // (nm/2) x 3 doubles = 12 nm bytes
+    L.lam = o;                      // 2 nm floats = 8 nm bytes
+    L.df = o + 8 * nm;              // nm floats each
+    L.e2f = o + 12 * nm;
+    L.dlo = o + 16 * nm;
+    L.e2lo = o + 20 * nm;
+    L.cnt = o + 24 * nm;            // one int per thread (32 nw)
+    o = align16(o + max2((size_t)nw * nm * cs, 24 * nm + 4 * 32 * (size_t)nw));
+    L.d = o;   o = align16(o + nm * sizeof(double));
+    L.e2 = o;  o = align16(o + nm * sizeof(double));
     L.red = o; o = align16(o + 6 * (size_t)nw * sizeof(double));
     L.total = o;
     return L;
 }
 
 template <typename T> struct Carve {
-    cplx_t<T>* A; HHScratch<T> hh; double* d; double* e2; float* df; float* e2f; float* dlo; float* e2lo; double* sp;
-    float* lam; double* red;
+    cplx_t<T>* A; HHScratch<T> hh; double* d; double* e2; float* df; float* e2f; float* dlo; float* e2lo; int* cnt;
+    double* sp; float* lam; double* red;
 };
 
 template <typename T>
@@ -74,6 +81,7 @@ __device__ __forceinline__ Carve<T> carve(unsigned char* base, const SmemLayout&
     c.e2f = reinterpret_cast<float*>(base + L.e2f);
     c.dlo = reinterpret_cast<float*>(base + L.dlo);
     c.e2lo = reinterpret_cast<float*>(base + L.e2lo);
+    c.cnt = reinterpret_cast<int*>(base + L.cnt);
     c.sp = reinterpret_cast<double*>(base + L.sp);
     c.lam = reinterpret_cast<float*>(base + L.lam);
     return c;
@@ -149,11 +157,10 @@ __device__ void tridiag_eig_F(int n, Carve<T>& c, double mu, double temp, bool a
         // Sampling round: thread t counts the eigenvalues below the point
         // lof + (t + 1) h0 (P = blockDim points); eigenvalue k then starts
         // from the gap between the last point counting <= k and the next,
-        // P + 1 times narrower than the Gershgorin interval.  The counts live
-        // in the column-sum scratch, free after the reduction.
+        // P + 1 times narrower than the Gershgorin interval.
         const int P = (int)blockDim.x;
         const float h0 = (hif - lof) / (float)(P + 1);
-        int* cnt = reinterpret_cast<int*>(c.hh.pc);
+        int* cnt = c.cnt;
         cnt[tid] = sturm_count_f32(n, c.df, c.e2f, lof + (float)(tid + 1) * h0, s_pivminf);
         __syncthreads();
         // Bracket tolerance, floored so that a zero matrix (nrm = 0) still
