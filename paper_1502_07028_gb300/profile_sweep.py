@@ -20,6 +20,8 @@ def main(argv=None):
     ap.add_argument("--schedule", choices=["block", "tiled"], default="block")
     ap.add_argument("--stride", type=int, default=0)
     ap.add_argument("--pipeline", choices=["stages", "persistent", "graph"], default="graph")
+    ap.add_argument("--warps", type=int, choices=[4, 8], default=8, help="warps per CTA of the sweep kernels")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: as many as fit)")
     ap.add_argument("--margin", type=float, default=None, help="mixed-mode FP64 re-solve margin (0 = off)")
     ap.add_argument("--sweeps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=0)
@@ -37,14 +39,15 @@ def main(argv=None):
                    schedule=P.SCHEDULE_BLOCK if a.schedule == "block" else P.SCHEDULE_TILED, stride=a.stride,
                    precision=P.MIXED if a.precision == "mixed" else P.FP64, proposal=P.PROPOSAL_CONE, cone_deg=30.0)
     ctx = P.Context(cfg)
-    P.ptca_set_pipeline(ctx.h, {"stages": P.PIPELINE_STAGES, "persistent": P.PIPELINE_PERSISTENT,
-                                "graph": P.PIPELINE_GRAPH}[a.pipeline])
+    P.ptca_set_launch_config(ctx.h, {"stages": P.PIPELINE_STAGES, "persistent": P.PIPELINE_PERSISTENT,
+                                     "graph": P.PIPELINE_GRAPH}[a.pipeline], a.warps, a.ctas_per_sm)
     if a.margin is not None and cfg.precision == P.MIXED:
         P.ptca_set_resolve_margin(ctx.h, a.margin)
     if a.warmup:
         ctx.sweep(a.warmup)
     st = ctx.sweep(a.sweeps)
-    print(f"{a.precision} L={a.L} Lc={a.Lc} {a.schedule} {a.pipeline}: {st.seconds * 1e3:.3f} ms for {a.sweeps} sweep(s), "
+    print(f"{a.precision} L={a.L} Lc={a.Lc} {a.schedule} {a.pipeline} {a.warps} warps: {st.seconds * 1e3:.3f} ms for "
+          f"{a.sweeps} sweep(s), "
           f"{cfg.N * a.sweeps / st.seconds:.0f} spin-updates/s, accepted {st.accepted}, resolved {st.resolved}")
     ctx.close()
 
