@@ -36,10 +36,12 @@ N_ORDER = 128
 # triangle once with 16 real FMA per complex element (rank-2 update + both
 # halves of the Hermitian matrix-vector product): sum_m 32 m(m+1)/2 ~ (16/3) n^3.
 HH_FLOPS = sum(32 * m * (m + 1) // 2 for m in range(1, N_ORDER))
-# DRAM bytes (read + write) of one launch of each candidate dominant kernel
-# on this workload, from the ncu captures summarised under profiles/.  A
-# value goes back to None whenever its kernel changes, until captured again.
-DRAM_BYTES_PER_LAUNCH = {"k_stage<float,4,8>": None, "k_stage<float,4,4>": 322_816,
+# DRAM bytes (read + write) per cluster matrix of each candidate dominant
+# kernel on this workload, from the ncu captures summarised under profiles/
+# (a launch's bytes / the matrices it solved; a launch's traffic is this
+# times its matrices).  A value goes back to None whenever its kernel
+# changes, until captured again.
+DRAM_BYTES_PER_MATRIX = {"k_stage<float,4,8>": None, "k_stage<float,4,4>": None,
                          "k_sweep_persistent<float,4,8>": None, "k_sweep_persistent<float,4,4>": None}
 
 
@@ -359,13 +361,15 @@ def main():
     # lattice; the chain state is restored and the fastest applied.
     best, tune_table = P.ptca_autotune(ctx.h, 3)
     names = {P.PIPELINE_STAGES: "per-stage launches", P.PIPELINE_PERSISTENT: "persistent kernel",
-             P.PIPELINE_GRAPH: "persistent kernel in a CUDA graph"}
+             P.PIPELINE_GRAPH: "persistent kernel in a CUDA graph",
+             P.PIPELINE_OVERLAP: "per-stage launches, each stage's re-solve overlapped with the next stage's "
+                                 "independent visits"}
+    per_stage = best.pipeline in (P.PIPELINE_STAGES, P.PIPELINE_OVERLAP)
     pipeline_desc = (f"{names[best.pipeline]}, {best.warps_per_cta}-warp CTA per matrix"
-                     + (f", {best.ctas_per_sm} CTAs/SM" if best.pipeline != P.PIPELINE_STAGES else "")
+                     + (f", {best.ctas_per_sm} CTAs/SM" if not per_stage else "")
                      + " (autotuned)")
     barrier(world)
     torch.cuda.synchronize()
-    per_stage = best.pipeline == P.PIPELINE_STAGES
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
         # Per-stage pipeline: the library brackets each stage-kernel launch
@@ -423,27 +427,35 @@ def main():
     ctx64.close()
     fp64_value = N * args.fp64_steps / (sum(fp64_ms) * 1e-3)
 
-    # --- roofline of the dominant kernel: the stage kernel (one launch per
-    # stage) when the per-stage pipeline is chosen, else the persistent
-    # kernel (one launch per sweep); its FP32 work is the Householder
-    # reduction.  Launches per step: one persistent launch, or per stage a
-    # stage kernel and a re-solve kernel plus the closing copy and counter
-    # kernels.
-    launches_per_step = 1 if best.pipeline != P.PIPELINE_STAGES else 2 * n_stages + 2
+    # --- roofline of the dominant kernel: the stage kernel when a per-stage
+    # pipeline is chosen, else the persistent kernel (one launch per sweep);
+    # its FP32 work is the Householder reduction.  Launches per step: one
+    # persistent launch; or the stage, dependent-visit and re-solve kernels
+    # the library timed, plus the closing counter kernel (and, one stream,
+    # the closing copy-forward kernel).
+    if kt is not None:
+        launches_per_step = ((kt.stage_launches + kt.dependent_launches + kt.resolve_launches) / args.steps
+                             + (2 if best.pipeline == P.PIPELINE_STAGES else 1))
+    else:
+        launches_per_step = 1
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or 2070.0
-    if kt is not None and kt[1] > 0:
-        # k_stage: one launch per stage, 2 matrices per visit of the stage.
+    if kt is not None and kt.stage_launches > 0:
+        # k_stage launches other than the overlapped pipeline's dependent
+        # visits: 2 matrices per visit, per-launch durations from the
+        # library's CUDA events on the stream each launch runs on.
         kernel_name = f"k_stage<float,4,{best.warps_per_cta}>"
-        launch_ms = kt[0] / kt[1]
-        matrices_per_launch = 2 * N / n_stages
-        resolve_ms_per_step = kt[2] / args.steps
+        launch_ms = kt.stage_ms / kt.stage_launches
+        matrices_per_launch = kt.stage_matrices / kt.stage_launches
+        resolve_ms_per_step = kt.resolve_ms / args.steps
     else:
         kernel_name = f"k_sweep_persistent<float,4,{best.warps_per_cta}>"
         launch_ms = ms_per_step
         matrices_per_launch = 2 * N
         resolve_ms_per_step = None
     achieved_tflops = matrices_per_launch * HH_FLOPS / (launch_ms * 1e-3) / 1e12
+    per_matrix = DRAM_BYTES_PER_MATRIX.get(kernel_name)
+    traffic = None if per_matrix is None else per_matrix * matrices_per_launch
     peak = fp32_alu_peak_tflops(clocks["sm_max_mhz"] or 2070.0)
 
     cpu = None
@@ -469,7 +481,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": "spin-updates/s", "h2d_bytes_per_step": N * 24,
                     "d2h_bytes_per_step": N * 24},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": int(round(launches_per_step * args.steps)),
             "pipeline": pipeline_desc,
             "autotune": {"best": tune_table["best"],
                          "candidates": [[c["pipeline"], c["warps_per_cta"], c["ctas_per_sm"], c["ms_per_sweep"]]
@@ -482,9 +494,9 @@ def main():
             "eigensolves_per_s": 2 * value,
             "acceptance": acc_rate,
             "roofline": {"bound": "alu", "kernel": kernel_name, "launch_ms": launch_ms,
-                         "resolve_ms_per_step": resolve_ms_per_step,
+                         "matrices_per_launch": matrices_per_launch, "resolve_ms_per_step": resolve_ms_per_step,
                          "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak, "traffic": DRAM_BYTES_PER_LAUNCH.get(kernel_name),
+                         "frac": achieved_tflops / peak, "traffic": traffic,
                          "note": "FP32 FMA pipe, Householder flops only; peak = 152 SM x 128 lanes x 2 x max clock"},
             "mixed_error": mixed_error,
             "cpu_baseline": cpu,

@@ -60,7 +60,7 @@ typedef enum {
 enum { PTCA_SCHEDULE_TILED = 0, PTCA_SCHEDULE_BLOCK = 1 };
 enum { PTCA_FP64 = 0, PTCA_MIXED = 1 };
 enum { PTCA_PROPOSAL_SPHERE = 0, PTCA_PROPOSAL_CONE = 1 };
-enum { PTCA_PIPELINE_STAGES = 0, PTCA_PIPELINE_PERSISTENT = 1, PTCA_PIPELINE_GRAPH = 2 };
+enum { PTCA_PIPELINE_STAGES = 0, PTCA_PIPELINE_PERSISTENT = 1, PTCA_PIPELINE_GRAPH = 2, PTCA_PIPELINE_OVERLAP = 3 };
 
 /* Square lattice.  Ly == 1 is a one-dimensional chain (Sec. III.a, Fig. 3). */
 typedef struct {
@@ -206,13 +206,27 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
  *                             queue, largest window first, and meet at a
  *                             device-wide barrier between stages;
  *   PTCA_PIPELINE_GRAPH       (default) the persistent launch captured once in
- *                             a CUDA graph per sweep count and replayed.
- * Every barrier wait is bounded by barrier_timeout_s (default 30 s): past it
- * the kernel stops and ptca_sweep (with stats) returns PTCA_ERR_TIMEOUT. */
+ *                             a CUDA graph per sweep count and replayed;
+ *   PTCA_PIPELINE_OVERLAP     per-stage launches in which the re-solve of
+ *                             the decisions a stage deferred (PTCA_MIXED
+ *                             guard) runs on a high-priority stream of the
+ *                             context, concurrently with the visits of the
+ *                             next stage whose windows hold no site of that
+ *                             stage; the visits whose windows do hold one
+ *                             run after the re-solve, on that stream.  Three
+ *                             rotating spin buffers keep every read on a
+ *                             stable configuration.  Falls back to
+ *                             PTCA_PIPELINE_STAGES when nothing is deferred
+ *                             (PTCA_FP64, margin 0), with the precision
+ *                             checker on and with surrogate screening.
+ * Every pipeline computes the same chain, bit for bit.  Every barrier wait is
+ * bounded by barrier_timeout_s (default 30 s): past it the kernel stops and
+ * ptca_sweep (with stats) returns PTCA_ERR_TIMEOUT. */
 ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeout_s);
 
 /* Launch configuration of the sweep kernels:
- *   pipeline       PTCA_PIPELINE_STAGES / _PERSISTENT / _GRAPH (as above);
+ *   pipeline       PTCA_PIPELINE_STAGES / _PERSISTENT / _GRAPH / _OVERLAP
+ *                  (as above);
  *   warps_per_cta  8: one 8-warp CTA per cluster matrix (every precision
  *                  and order); 4: one warp group per matrix, twice the
  *                  resident matrices per SM (PTCA_MIXED, orders up to 128);
@@ -243,14 +257,21 @@ ptca_status ptca_get_launch_config(const ptca_ctx* ctx, ptca_launch_config* out)
 ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_config* best, char* json, int32_t json_cap,
                           void* stream);
 
-/* Per-kernel timing of the per-stage pipeline (off by default).  While on,
+/* Per-kernel timing of the per-stage pipelines (off by default).  While on,
  * every stage-kernel launch and every re-solve launch of ptca_sweep is
- * bracketed by CUDA events on the sweep's stream.  ptca_kernel_times
- * synchronises `stream`, writes out[0] = total ms of the stage kernels,
- * out[1] = their launch count, out[2] = total ms of the re-solve kernels,
- * out[3] = their launch count (host array of 4 doubles), and clears the
- * record.  The persistent pipelines time as one launch per call of
- * ptca_sweep (ptca_sweep_stats.seconds). */
+ * bracketed by CUDA events on the stream it runs on.  ptca_kernel_times
+ * synchronises `stream` and writes, into a host array of 8 doubles:
+ *   out[0], out[1]  total ms and launch count of the stage kernels (whole
+ *                   stages; in PTCA_PIPELINE_OVERLAP the visits that do not
+ *                   wait for the previous stage's re-solve);
+ *   out[2], out[3]  total ms and launch count of the re-solve kernels;
+ *   out[4], out[5]  total ms and launch count of the stage kernels of
+ *                   PTCA_PIPELINE_OVERLAP that run after a re-solve;
+ *   out[6], out[7]  cluster matrices solved by the launches of out[0] and of
+ *                   out[4] (two per visit);
+ * then clears the record.  Launches of one pipeline may overlap in time, so
+ * the totals can exceed the elapsed time.  The persistent pipelines time as
+ * one launch per call of ptca_sweep (ptca_sweep_stats.seconds). */
 ptca_status ptca_set_kernel_timing(ptca_ctx* ctx, int32_t on);
 ptca_status ptca_kernel_times(ptca_ctx* ctx, double* out, void* stream);
 
@@ -383,6 +404,19 @@ ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptca_params* p
  * Same validation as ptca_init. */
 ptca_status ptca_schedule(const ptca_lattice* lattice, const ptca_params* params,
                           int32_t* stage_start, int32_t* sites, int32_t* n_stages);
+
+/* Dependence of each stage on the one before it (the last stage of a sweep
+ * precedes stage 0 of the next), as PTCA_PIPELINE_OVERLAP uses it.  A visit of
+ * stage s depends on stage s-1 iff its window (Sec. II.b, as ptca_init builds
+ * it) holds a site of stage s-1; the others read only sites that were final
+ * before stage s-1 began.  order: host int32[N]; order[stage_start[s] + k] for
+ * k < stage_start[s+1] - stage_start[s] lists the indices into stage s's site
+ * list: first the n_indep[s] visits that do not depend on stage s-1, then the
+ * rest, each part largest window first and otherwise in schedule order.
+ * n_indep: host int32[n_stages].  stage_start, n_stages as ptca_schedule.
+ * Same validation as ptca_init; no GPU. */
+ptca_status ptca_stage_split(const ptca_lattice* lattice, const ptca_params* params, int32_t* order,
+                             int32_t* n_indep);
 
 /* Self-test of the bounded device-wide barrier: `blocks` CTAs wait at a
  * barrier sized for blocks + 1 participants, so the wait can only end by its

@@ -104,6 +104,64 @@ bool schedule_exact(const Problem& p, const std::vector<int32_t>& start, const s
     return true;
 }
 
+// Work order inside each stage: largest window first (ragged windows of open
+// lattices), stable, so periodic lattices keep schedule order.  perm[k] for k
+// in stage s's range is an index into that stage's site list.
+std::vector<int32_t> window_order(const Problem& p, const std::vector<int32_t>& start,
+                                  const std::vector<int32_t>& sites) {
+    std::vector<int32_t> perm(sites.size());
+    for (size_t stg = 0; stg + 1 < start.size(); ++stg) {
+        const int a0 = start[stg], a1 = start[stg + 1];
+        std::vector<std::pair<int, int>> key;
+        for (int k = a0; k < a1; ++k) {
+            const int b = sites[k];
+            int x0, ex, y0, ey;
+            window_axis(p.Lx, p.periodic, p.Lc, p.ox, b % p.Lx, x0, ex);
+            window_axis(p.Ly, p.periodic, p.Lc, p.oy, b / p.Lx, y0, ey);
+            key.push_back({-(ex * ey), k - a0});
+        }
+        std::stable_sort(key.begin(), key.end(),
+                         [](const std::pair<int, int>& u, const std::pair<int, int>& v) { return u.first < v.first; });
+        for (int k = a0; k < a1; ++k) perm[k] = key[k - a0].second;
+    }
+    return perm;
+}
+
+// Split of every stage's work order (window_order) into the visits whose
+// window holds no site of the previous stage (cyclically: stage 0 follows the
+// last stage), first, and the rest; indep[s] counts the first part.
+void stage_split(const Problem& p, const std::vector<int32_t>& start, const std::vector<int32_t>& sites,
+                 std::vector<int32_t>& order, std::vector<int32_t>& indep) {
+    const int ns = (int)start.size() - 1, N = p.N();
+    const std::vector<int32_t> perm = window_order(p, start, sites);
+    order.assign(sites.size(), 0);
+    indep.assign(ns, 0);
+    std::vector<int32_t> stage_of(N, -1);
+    for (int s = 0; s < ns; ++s)
+        for (int k = start[s]; k < start[s + 1]; ++k) stage_of[sites[k]] = s;
+    for (int s = 0; s < ns; ++s) {
+        const int q = (s + ns - 1) % ns;
+        std::vector<int32_t> a, b;
+        for (int k = start[s]; k < start[s + 1]; ++k) {
+            const int c = perm[k], site = sites[start[s] + c];
+            int x0, ex, y0, ey;
+            window_axis(p.Lx, p.periodic, p.Lc, p.ox, site % p.Lx, x0, ex);
+            window_axis(p.Ly, p.periodic, p.Lc, p.oy, site / p.Lx, y0, ey);
+            bool dep = false;
+            for (int wy = 0; wy < ey && !dep; ++wy)
+                for (int wx = 0; wx < ex && !dep; ++wx) {
+                    int x = x0 + wx, y = y0 + wy;
+                    if (p.periodic) { x %= p.Lx; y %= p.Ly; }
+                    dep = stage_of[y * p.Lx + x] == q;
+                }
+            (dep ? b : a).push_back(c);
+        }
+        indep[s] = (int32_t)a.size();
+        std::copy(a.begin(), a.end(), order.begin() + start[s]);
+        std::copy(b.begin(), b.end(), order.begin() + start[s] + a.size());
+    }
+}
+
 ptca_status resolve(const ptca_lattice* lat, const ptca_params* par, Problem& p) {
     if (!lat || !par) return fail(PTCA_ERR_INVALID, "null lattice or params");
     p.Lx = lat->Lx; p.Ly = lat->Ly; p.periodic = lat->periodic ? 1 : 0;
@@ -164,8 +222,10 @@ static void drop_graph(ptca_ctx* c) {
     c->graph_sweeps = -1;
 }
 
-// A launch, bracketed by events on `st` when kernel timing is on.
-template <typename F> static cudaError_t timed_launch(ptca_ctx* ctx, int kind, cudaStream_t st, F launch) {
+// A launch solving `items` cluster matrices, bracketed by events on `st` when
+// kernel timing is on.
+template <typename F>
+static cudaError_t timed_launch(ptca_ctx* ctx, int kind, int64_t items, cudaStream_t st, F launch) {
     if (!ctx->timing) return launch();
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaError_t e = cudaEventCreate(&ev[0]);
@@ -181,6 +241,7 @@ template <typename F> static cudaError_t timed_launch(ptca_ctx* ctx, int kind, c
     ctx->tev.push_back(ev[0]);
     ctx->tev.push_back(ev[1]);
     ctx->tkind.push_back(kind);
+    ctx->titems.push_back(items);
     return cudaSuccess;
 }
 
@@ -188,13 +249,17 @@ static void drop_timing_events(ptca_ctx* c) {
     for (cudaEvent_t ev : c->tev) cudaEventDestroy(ev);
     c->tev.clear();
     c->tkind.clear();
+    c->titems.clear();
 }
 
 static void free_ctx(ptca_ctx* c) {
     drop_graph(c);
     drop_timing_events(c);
     ptca_free_surrogate(c);
-    void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
+    if (c->side) cudaStreamDestroy(c->side);
+    for (cudaEvent_t ev : {c->ev_indep, c->ev_dep, c->ev_fork, c->ev_join})
+        if (ev) cudaEventDestroy(ev);
+    void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_S[2], c->d_split, c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
                     c->d_rec_n, c->d_counters, c->d_err, c->d_obs, c->d_stage_start, c->d_perm, c->d_queue,
                     c->d_bar, c->d_sweep_ctr, c->d_flag_list, c->d_flag_count, c->d_gA,
@@ -226,6 +291,22 @@ ptca_status ptca_schedule(const ptca_lattice* lattice, const ptca_params* params
     std::memcpy(stage_start, st.data(), st.size() * sizeof(int32_t));
     std::memcpy(sites, si.data(), si.size() * sizeof(int32_t));
     *n_stages = (int32_t)st.size() - 1;
+    return PTCA_OK;
+}
+
+ptca_status ptca_stage_split(const ptca_lattice* lattice, const ptca_params* params, int32_t* order,
+                             int32_t* n_indep) {
+    Problem p;
+    ptca_status s = resolve(lattice, params, p);
+    if (s != PTCA_OK) return s;
+    if (!order || !n_indep) return fail(PTCA_ERR_INVALID, "null output pointer");
+    std::vector<int32_t> st, si, ord, ind;
+    make_schedule(p, st, si);
+    std::string why;
+    if (!schedule_exact(p, st, si, why)) return fail(PTCA_ERR_INVALID, "schedule is not exact: " + why);
+    stage_split(p, st, si, ord, ind);
+    std::memcpy(order, ord.data(), ord.size() * sizeof(int32_t));
+    std::memcpy(n_indep, ind.data(), ind.size() * sizeof(int32_t));
     return PTCA_OK;
 }
 
@@ -272,9 +353,9 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
     if (ce == cudaSuccess) ce = dalloc(&c->d_sites, N);
     if (ce == cudaSuccess) ce = dalloc(&c->d_S[0], 3 * (size_t)N);
     if (ce == cudaSuccess) ce = dalloc(&c->d_S[1], 3 * (size_t)N);
-    if (ce == cudaSuccess) ce = dalloc(&c->d_F, 2 * (size_t)c->max_stage);
-    if (ce == cudaSuccess) ce = dalloc(&c->d_fill, 2 * (size_t)c->max_stage);
-    if (ce == cudaSuccess) ce = dalloc(&c->d_ticket, c->max_stage);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_F, 4 * (size_t)c->max_stage);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_fill, 4 * (size_t)c->max_stage);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_ticket, 2 * (size_t)c->max_stage);
     if (ce == cudaSuccess) ce = dalloc(&c->d_rec_site, N);
     if (ce == cudaSuccess) ce = dalloc(&c->d_rec_Fold, N);
     if (ce == cudaSuccess) ce = dalloc(&c->d_rec_Fnew, N);
@@ -288,36 +369,20 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
     if (ce == cudaSuccess) ce = dalloc(&c->d_stage_start, c->nstages + 1);
     if (ce == cudaSuccess) ce = dalloc(&c->d_perm, N);
     if (ce == cudaSuccess) ce = dalloc(&c->d_queue, 3);
-    if (ce == cudaSuccess) ce = dalloc(&c->d_flag_list, c->max_stage);
-    if (ce == cudaSuccess) ce = dalloc(&c->d_flag_count, 1);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_flag_list, 2 * (size_t)c->max_stage);
+    if (ce == cudaSuccess) ce = dalloc(&c->d_flag_count, 2);
     if (ce == cudaSuccess) ce = dalloc(&c->d_bar, 2);
     if (ce == cudaSuccess) ce = dalloc(&c->d_sweep_ctr, 1);
     if (ce == cudaSuccess) ce = dalloc(&c->d_obs, 8);
     if (ce == cudaSuccess) ce = cudaMemcpy(c->d_sites, si.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = cudaMemset(c->d_ticket, 0, c->max_stage * sizeof(int32_t));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_ticket, 0, 2 * (size_t)c->max_stage * sizeof(int32_t));
     if (ce == cudaSuccess) ce = cudaMemset(c->d_err, 0, 2 * sizeof(int32_t));
     if (ce == cudaSuccess) ce = cudaMemset(c->d_queue, 0, 3 * sizeof(unsigned int));
-    if (ce == cudaSuccess) ce = cudaMemset(c->d_flag_count, 0, sizeof(unsigned int));
+    if (ce == cudaSuccess) ce = cudaMemset(c->d_flag_count, 0, 2 * sizeof(unsigned int));
     if (ce == cudaSuccess) ce = cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned int));
     if (ce == cudaSuccess) ce = cudaMemset(c->d_sweep_ctr, 0, sizeof(unsigned long long));
     if (ce == cudaSuccess) {
-        // Work order inside each stage: largest window first (ragged windows
-        // of open lattices), stable, so periodic lattices keep schedule order.
-        std::vector<int32_t> perm(N);
-        for (int stg = 0; stg < c->nstages; ++stg) {
-            const int a0 = st[stg], a1 = st[stg + 1];
-            std::vector<std::pair<int, int>> key;
-            for (int k = a0; k < a1; ++k) {
-                const int b = si[k];
-                int x0, ex, y0, ey;
-                window_axis(p.Lx, p.periodic, p.Lc, p.ox, b % p.Lx, x0, ex);
-                window_axis(p.Ly, p.periodic, p.Lc, p.oy, b / p.Lx, y0, ey);
-                key.push_back({-(ex * ey), k - a0});
-            }
-            std::stable_sort(key.begin(), key.end(),
-                             [](const std::pair<int, int>& u, const std::pair<int, int>& v) { return u.first < v.first; });
-            for (int k = a0; k < a1; ++k) perm[k] = key[k - a0].second;
-        }
+        const std::vector<int32_t> perm = window_order(p, st, si);
         ce = cudaMemcpy(c->d_perm, perm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     }
     if (ce == cudaSuccess) ce = cudaMemcpy(c->d_stage_start, st.data(), (c->nstages + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -523,9 +588,11 @@ static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st
             a.sg_dFt = nullptr;
             if (ctx->checker) e = check_stage(ctx, a, s, st);
             if (e == cudaSuccess && ctx->sg.enabled && !col) e = ptca_screen_stage(ctx, a, st);
-            if (e == cudaSuccess) e = timed_launch(ctx, 0, st, [&] { return ptca::launch_stage(ctx->prec, ctx->nw, a, st); });
+            if (e == cudaSuccess)
+                e = timed_launch(ctx, 0, 2 * (int64_t)a.count, st,
+                                 [&] { return ptca::launch_stage(ctx->prec, ctx->nw, a, st); });
             if (e == cudaSuccess && a.margin > 0.0) {
-                e = timed_launch(ctx, 1, st, [&] { return ptca::launch_resolve(a, ctx->resolve_grid, st); });
+                e = timed_launch(ctx, 1, 0, st, [&] { return ptca::launch_resolve(a, ctx->resolve_grid, st); });
                 if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag_count, 0, sizeof(unsigned int), st);
             }
             prev_s = s;
@@ -534,6 +601,123 @@ static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st
     if (e == cudaSuccess && g > 0)
         e = ptca::launch_copy_sites(ctx->d_S[g & 1], ctx->d_S[(g + 1) & 1], ctx->d_sites + ctx->h_start[prev_s],
                                     ctx->h_start[prev_s + 1] - ctx->h_start[prev_s], st);
+    if (e == cudaSuccess) e = ptca::launch_set_u64(ctx->d_sweep_ctr, (unsigned long long)(ctx->sweeps + n_sweeps), st);
+    return e;
+}
+
+// Point the per-visit scratch of `a` at half h (stage parity).
+static void use_half(const ptca_ctx* ctx, StageArgs& a, int h) {
+    const size_t ms = (size_t)ctx->max_stage;
+    a.Fbuf = ctx->d_F + h * 2 * ms;
+    a.fillbuf = ctx->d_fill + h * 2 * ms;
+    a.ticket = ctx->d_ticket + h * ms;
+    a.flag_list = ctx->d_flag_list + h * ms;
+    a.flag_count = ctx->d_flag_count + h;
+}
+
+// Resources of the overlapped pipeline, made on first use.
+static cudaError_t ensure_overlap(ptca_ctx* ctx) {
+    if (ctx->side) return cudaSuccess;
+    std::vector<int32_t> order;
+    stage_split(ctx->p, ctx->h_start, ctx->h_sites, order, ctx->h_indep);
+    cudaError_t e = ctx->d_S[2] ? cudaSuccess : dalloc(&ctx->d_S[2], 3 * (size_t)ctx->N);
+    if (e == cudaSuccess && !ctx->d_split) e = dalloc(&ctx->d_split, (size_t)ctx->N);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->d_split, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    for (cudaEvent_t* ev : {&ctx->ev_indep, &ctx->ev_dep, &ctx->ev_fork, &ctx->ev_join})
+        if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    cudaStream_t side = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) ctx->side = side;
+    return e;
+}
+
+// Overlapped per-stage pipeline.  Stage g (counted over the call) reads
+// buffer g mod 3 and writes buffer g+1 mod 3, so the re-solve of stage g-1
+// keeps reading its own start configuration while stage g writes.  On the
+// caller's stream: the visits of stage g whose windows hold no site of stage
+// g-1 (I_g), after the dependent visits of stage g-1.  On the context's
+// high-priority stream: the re-solve of stage g-1 (R_{g-1}, once I_{g-1} has
+// run), then the visits of stage g that depend on stage g-1 (D_g), which also
+// copy the sites of stages g-2 and g-1 forward into buffer g+1 mod 3.  The
+// per-visit scratch alternates halves with g, so R_{g-1} and stage g never
+// share a slot.  Every visit reads the spins it reads in the one-stream
+// pipeline and decides with the same arithmetic: the chain is the same, bit
+// for bit.
+static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
+    cudaError_t e = ensure_overlap(ctx);
+    if (e != cudaSuccess) return e;
+    cudaStream_t hs = ctx->side;
+    const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
+    const int ns = ctx->nstages;
+    const int64_t G = (int64_t)n_sweeps * ns;
+    // buffers 0 and 1 agree between calls; buffer 2 starts from them too
+    e = cudaMemcpyAsync(ctx->d_S[2], ctx->d_S[0], bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ctx->ev_fork, 0);
+    StageArgs prev = base_args(ctx);  // the stage whose re-solve is pending
+    auto resolve_prev = [&]() {
+        cudaError_t r = cudaStreamWaitEvent(hs, ctx->ev_indep, 0);
+        if (r == cudaSuccess)
+            r = timed_launch(ctx, 1, 0, hs, [&] { return ptca::launch_resolve(prev, ctx->resolve_grid, hs); });
+        if (r == cudaSuccess) r = cudaMemsetAsync(prev.flag_count, 0, sizeof(unsigned int), hs);
+        return r;
+    };
+    auto stage_sites = [&](int64_t gg, const int32_t*& sites, int32_t& count) {
+        const int q = (int)(gg % ns);
+        sites = ctx->d_sites + ctx->h_start[q];
+        count = ctx->h_start[q + 1] - ctx->h_start[q];
+    };
+    for (int64_t g = 0; g < G && e == cudaSuccess; ++g) {
+        const int s = (int)(g % ns);
+        StageArgs a = base_args(ctx);
+        use_half(ctx, a, (int)(g & 1));
+        a.sweep = (uint64_t)(ctx->sweeps + g / ns);
+        a.S_in = ctx->d_S[g % 3];
+        a.S_out = ctx->d_S[(g + 1) % 3];
+        a.sites = ctx->d_sites + ctx->h_start[s];
+        a.rec_base = ctx->h_start[s];
+        const int cnt = ctx->h_start[s + 1] - ctx->h_start[s], ni = ctx->h_indep[s];
+        if (g > 0) e = resolve_prev();
+        if (e == cudaSuccess && g > 0) e = cudaStreamWaitEvent(st, ctx->ev_dep, 0);
+        StageArgs ai = a;
+        ai.perm = ctx->d_split + ctx->h_start[s];
+        ai.count = ni;
+        if (e == cudaSuccess && ni > 0)
+            e = timed_launch(ctx, 0, 2 * (int64_t)ni, st,
+                             [&] { return ptca::launch_stage(ctx->prec, ctx->nw, ai, st); });
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_indep, st);
+        StageArgs ad = a;
+        ad.perm = ctx->d_split + ctx->h_start[s] + ni;
+        ad.count = cnt - ni;
+        // sites buffer g+1 mod 3 lacks: those of stages g-2 and g-1 (each
+        // only if it is not stage g itself, whose visits write every site)
+        if (g >= 1 && (g - 1) % ns != s) stage_sites(g - 1, ad.prev_sites, ad.prev_count);
+        if (g >= 2 && (g - 2) % ns != s && (g - 2) % ns != (g - 1) % ns)
+            stage_sites(g - 2, ad.prev2_sites, ad.prev2_count);
+        if (e == cudaSuccess) {
+            if (ad.count > 0) {
+                e = timed_launch(ctx, 2, 2 * (int64_t)ad.count, hs,
+                                 [&] { return ptca::launch_stage(ctx->prec, ctx->nw, ad, hs); });
+            } else {
+                e = ptca::launch_copy_sites(ad.S_in, ad.S_out, ad.prev_sites, ad.prev_count, hs);
+                if (e == cudaSuccess) e = ptca::launch_copy_sites(ad.S_in, ad.S_out, ad.prev2_sites, ad.prev2_count, hs);
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_dep, hs);
+        prev = a;
+    }
+    if (e == cudaSuccess && G > 0) e = resolve_prev();
+    // join the side stream back into the caller's stream, also after a failure
+    cudaError_t ej = cudaEventRecord(ctx->ev_join, hs);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, ctx->ev_join, 0);
+    if (e == cudaSuccess) e = ej;
+    // the configuration after the call is buffer G mod 3; buffers 0 and 1 take it
+    const int f = (int)(G % 3);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        if (b != f) e = cudaMemcpyAsync(ctx->d_S[b], ctx->d_S[f], bytes, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = ptca::launch_set_u64(ctx->d_sweep_ctr, (unsigned long long)(ctx->sweeps + n_sweeps), st);
     return e;
 }
@@ -590,17 +774,26 @@ static cudaError_t sweep_graph(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st)
 // Stream work of n_sweeps sweeps in the context's launch configuration
 // (screening and the checker need the per-stage pipeline).
 static cudaError_t run_sweeps(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
-    if (ctx->pipeline == PTCA_PIPELINE_STAGES || ctx->sg.enabled || ctx->checker) return sweep_stages(ctx, n_sweeps, st);
+    const bool per_stage = ctx->pipeline == PTCA_PIPELINE_STAGES || ctx->pipeline == PTCA_PIPELINE_OVERLAP;
+    if (ctx->pipeline == PTCA_PIPELINE_OVERLAP && ctx->prec == 1 && ctx->margin > 0.0 && !ctx->sg.enabled &&
+        !ctx->checker)
+        return sweep_overlap(ctx, n_sweeps, st);
+    if (per_stage || ctx->sg.enabled || ctx->checker) return sweep_stages(ctx, n_sweeps, st);
     if (ctx->pipeline == PTCA_PIPELINE_PERSISTENT || ctx->graph_failed) return enqueue_persistent(ctx, n_sweeps, st);
     return sweep_graph(ctx, n_sweeps, st);
 }
 
 ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeout_s) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
-    if (mode < PTCA_PIPELINE_STAGES || mode > PTCA_PIPELINE_GRAPH) return fail(PTCA_ERR_INVALID, "unknown pipeline");
-    if (mode != PTCA_PIPELINE_STAGES && ctx->grid <= 0)
+    if (mode < PTCA_PIPELINE_STAGES || mode > PTCA_PIPELINE_OVERLAP) return fail(PTCA_ERR_INVALID, "unknown pipeline");
+    const bool persistent = mode == PTCA_PIPELINE_PERSISTENT || mode == PTCA_PIPELINE_GRAPH;
+    if (persistent && ctx->grid <= 0)
         return fail(PTCA_ERR_UNSUPPORTED, "persistent kernel does not fit on this device");
     if (!(barrier_timeout_s > 0) || barrier_timeout_s > 3600) return fail(PTCA_ERR_INVALID, "timeout out of range");
+    if (mode == PTCA_PIPELINE_OVERLAP) {
+        cudaError_t e = ensure_overlap(ctx);
+        if (e != cudaSuccess) return cuda_fail(e, "ptca_set_pipeline (overlapped pipeline)");
+    }
     ctx->pipeline = mode;
     ctx->timeout_ns = (unsigned long long)(barrier_timeout_s * 1e9);
     drop_graph(ctx);
@@ -617,15 +810,18 @@ ptca_status ptca_set_kernel_timing(ptca_ctx* ctx, int32_t on) {
 ptca_status ptca_kernel_times(ptca_ctx* ctx, double* out, void* stream) {
     if (!ctx || !out) return fail(PTCA_ERR_INVALID, "null argument");
     PTCA_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-    for (int q = 0; q < 4; ++q) out[q] = 0.0;
+    for (int q = 0; q < 8; ++q) out[q] = 0.0;
     for (size_t i = 0; i < ctx->tkind.size(); ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ctx->tev[2 * i], ctx->tev[2 * i + 1]) != cudaSuccess) {
             drop_timing_events(ctx);
             return fail(PTCA_ERR_CUDA, "kernel timing events were not recorded on this stream");
         }
-        out[2 * ctx->tkind[i]] += ms;
-        out[2 * ctx->tkind[i] + 1] += 1.0;
+        const int k = ctx->tkind[i];
+        out[2 * k] += ms;
+        out[2 * k + 1] += 1.0;
+        if (k == 0) out[6] += (double)ctx->titems[i];
+        if (k == 2) out[7] += (double)ctx->titems[i];
     }
     drop_timing_events(ctx);
     return PTCA_OK;
@@ -641,7 +837,7 @@ ptca_status ptca_get_launch_config(const ptca_ctx* ctx, ptca_launch_config* out)
 
 ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg) {
     if (!ctx || !cfg) return fail(PTCA_ERR_INVALID, "null argument");
-    if (cfg->pipeline < PTCA_PIPELINE_STAGES || cfg->pipeline > PTCA_PIPELINE_GRAPH)
+    if (cfg->pipeline < PTCA_PIPELINE_STAGES || cfg->pipeline > PTCA_PIPELINE_OVERLAP)
         return fail(PTCA_ERR_INVALID, "unknown pipeline");
     if (cfg->warps_per_cta != 8 && cfg->warps_per_cta != 4) return fail(PTCA_ERR_INVALID, "warps_per_cta must be 4 or 8");
     if (!ptca::sweep_width_supported(ctx->prec, cfg->warps_per_cta, ctx->nA))
@@ -649,8 +845,12 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, cfg->warps_per_cta, ctx->nA);
     if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > maxb)
         return fail(PTCA_ERR_INVALID, "ctas_per_sm must be in [0, the CTAs that fit on an SM]");
-    if (cfg->pipeline != PTCA_PIPELINE_STAGES && maxb <= 0)
-        return fail(PTCA_ERR_UNSUPPORTED, "persistent kernel does not fit on this device");
+    const bool persistent = cfg->pipeline == PTCA_PIPELINE_PERSISTENT || cfg->pipeline == PTCA_PIPELINE_GRAPH;
+    if (persistent && maxb <= 0) return fail(PTCA_ERR_UNSUPPORTED, "persistent kernel does not fit on this device");
+    if (cfg->pipeline == PTCA_PIPELINE_OVERLAP) {
+        cudaError_t e = ensure_overlap(ctx);
+        if (e != cudaSuccess) return cuda_fail(e, "ptca_set_launch_config (overlapped pipeline)");
+    }
     ctx->pipeline = cfg->pipeline;
     ctx->nw = cfg->warps_per_cta;
     ctx->ctas_per_sm = cfg->ctas_per_sm;
@@ -661,7 +861,12 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
 }
 
 static const char* pipeline_name(int p) {
-    return p == PTCA_PIPELINE_STAGES ? "stages" : (p == PTCA_PIPELINE_PERSISTENT ? "persistent" : "graph");
+    switch (p) {
+        case PTCA_PIPELINE_STAGES: return "stages";
+        case PTCA_PIPELINE_PERSISTENT: return "persistent";
+        case PTCA_PIPELINE_GRAPH: return "graph";
+        default: return "overlap";
+    }
 }
 
 ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_config* best, char* json, int32_t json_cap,
@@ -675,6 +880,7 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
     for (int nw : {8, 4}) {
         if (!ptca::sweep_width_supported(ctx->prec, nw, ctx->nA)) continue;
         cand.push_back({PTCA_PIPELINE_STAGES, nw, 0});
+        if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0});
         const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, nw, ctx->nA);
         if (maxb <= 0 || ctx->sg.enabled) continue;
         for (int pl : {PTCA_PIPELINE_PERSISTENT, PTCA_PIPELINE_GRAPH}) {

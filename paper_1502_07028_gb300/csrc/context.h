@@ -53,10 +53,16 @@ struct ptca_ctx {
     size_t smem = 0;
     std::vector<int32_t> h_start, h_sites;
     int32_t* d_sites = nullptr;
-    double* d_S[2] = {nullptr, nullptr};
-    double* d_F = nullptr;
-    double* d_fill = nullptr;
-    int32_t* d_ticket = nullptr;
+    // Spin buffers: [0] and [1] rotate between stages and hold the same
+    // configuration between calls; [2] joins the rotation in the overlapped
+    // pipeline (allocated when that pipeline is first selected).
+    double* d_S[3] = {nullptr, nullptr, nullptr};
+    // Per-visit scratch of a stage, in two halves (stage parity) so that a
+    // stage's re-solve can run while the next stage is under way; the
+    // other pipelines use half 0.
+    double* d_F = nullptr;     // [2][2 max_stage]
+    double* d_fill = nullptr;  // [2][2 max_stage]
+    int32_t* d_ticket = nullptr;  // [2][max_stage]
     int32_t* d_rec_site = nullptr;
     double* d_rec_Fold = nullptr;
     double* d_rec_Fnew = nullptr;
@@ -88,8 +94,8 @@ struct ptca_ctx {
     bool graph_failed = false;
     // PTCA_MIXED decision guard
     double margin = 0.0;
-    int32_t* d_flag_list = nullptr;
-    unsigned int* d_flag_count = nullptr;
+    int32_t* d_flag_list = nullptr;       // [2][max_stage]
+    unsigned int* d_flag_count = nullptr; // [2]
     double2* d_gA = nullptr;
     int64_t gA_stride = 0;
     int resolve_grid = 0;
@@ -99,11 +105,22 @@ struct ptca_ctx {
     double* d_chk_eig = nullptr;              // [2 precisions][check_chunk][2][nA]
     double* d_chk_F = nullptr;                // [2 precisions][check_chunk][2]
     unsigned long long* d_chk_out = nullptr;  // [nstages][4], bits of non-negative doubles
-    // optional per-kernel timing of the per-stage pipeline: event pairs
-    // around each stage launch (kind 0) and re-solve launch (kind 1)
+    // overlapped pipeline: stage order with the visits independent of the
+    // previous stage first (h_indep[s] of them), a high-priority stream for
+    // the re-solves and the dependent visits, and the events ordering it
+    // against the caller's stream
+    int32_t* d_split = nullptr;
+    std::vector<int32_t> h_indep;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_indep = nullptr, ev_dep = nullptr, ev_fork = nullptr, ev_join = nullptr;
+    // optional per-kernel timing of the per-stage pipelines: event pairs
+    // around each stage launch (kind 0), re-solve launch (kind 1) and
+    // dependent-visit launch of the overlapped pipeline (kind 2), with the
+    // matrices each launch solves
     bool timing = false;
     std::vector<cudaEvent_t> tev;
     std::vector<int> tkind;
+    std::vector<int64_t> titems;
     // surrogate network for delayed-acceptance screening
     ptca::SurrogateState sg;
 };

@@ -292,9 +292,10 @@ __global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int c
 // 2c+1 holds H_new with the proposed spin.  The second block to finish
 // applies Metropolis (Sec. II.c steps e-f) and writes the site's spin for the
 // next stage.  Reads come only from S_in (the configuration at the start of
-// the stage); S_out receives this stage's decisions plus the previous
-// stage's update sites copied forward, so S_out is the full configuration
-// after the stage.
+// the stage); S_out receives this stage's decisions plus the update sites it
+// does not hold yet, copied forward from S_in (the previous stage's with two
+// rotating spin buffers, the two previous stages' with three), so S_out is
+// the full configuration after the stage.
 struct StageArgs {
     Model m;
     const double* S_in;
@@ -304,6 +305,8 @@ struct StageArgs {
     int32_t count;
     const int32_t* prev_sites;
     int32_t prev_count;
+    const int32_t* prev2_sites;    // a second copied-forward range (overlapped pipeline), may be empty
+    int32_t prev2_count;
     int32_t rec_base;
     int32_t nA;
     uint64_t sweep;
@@ -447,8 +450,9 @@ __global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value) k_stag
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_new[3];
     __shared__ int s_last;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.prev_count; k += gridDim.x * blockDim.x) {
-        const int s = a.prev_sites[k];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.prev_count + a.prev2_count;
+         k += gridDim.x * blockDim.x) {
+        const int s = k < a.prev_count ? a.prev_sites[k] : a.prev2_sites[k - a.prev_count];
         a.S_out[3 * s] = a.S_in[3 * s];
         a.S_out[3 * s + 1] = a.S_in[3 * s + 1];
         a.S_out[3 * s + 2] = a.S_in[3 * s + 2];

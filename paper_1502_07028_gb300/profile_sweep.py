@@ -19,7 +19,7 @@ def main(argv=None):
     ap.add_argument("--open", action="store_true", help="open lattice (clipped windows)")
     ap.add_argument("--schedule", choices=["block", "tiled"], default="block")
     ap.add_argument("--stride", type=int, default=0)
-    ap.add_argument("--pipeline", choices=["stages", "persistent", "graph"], default="graph")
+    ap.add_argument("--pipeline", choices=["stages", "persistent", "graph", "overlap"], default="graph")
     ap.add_argument("--warps", type=int, choices=[4, 8], default=8, help="warps per CTA of the sweep kernels")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: as many as fit)")
     ap.add_argument("--margin", type=float, default=None, help="mixed-mode FP64 re-solve margin (0 = off)")
@@ -40,7 +40,7 @@ def main(argv=None):
                    precision=P.MIXED if a.precision == "mixed" else P.FP64, proposal=P.PROPOSAL_CONE, cone_deg=30.0)
     ctx = P.Context(cfg)
     P.ptca_set_launch_config(ctx.h, {"stages": P.PIPELINE_STAGES, "persistent": P.PIPELINE_PERSISTENT,
-                                     "graph": P.PIPELINE_GRAPH}[a.pipeline], a.warps, a.ctas_per_sm)
+                                     "graph": P.PIPELINE_GRAPH, "overlap": P.PIPELINE_OVERLAP}[a.pipeline], a.warps, a.ctas_per_sm)
     if a.margin is not None and cfg.precision == P.MIXED:
         P.ptca_set_resolve_margin(ctx.h, a.margin)
     if a.warmup:

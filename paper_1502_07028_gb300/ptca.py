@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+from collections import namedtuple
 from dataclasses import dataclass
 
 from . import _build
@@ -19,7 +20,7 @@ PTCA_OK = 0
 STATUS = {0: "PTCA_OK", 1: "PTCA_ERR_INVALID", 2: "PTCA_ERR_CUDA", 3: "PTCA_ERR_OOM",
           4: "PTCA_ERR_TIMEOUT", 5: "PTCA_ERR_NUMERIC", 6: "PTCA_ERR_UNSUPPORTED"}
 SCHEDULE_TILED, SCHEDULE_BLOCK = 0, 1
-PIPELINE_STAGES, PIPELINE_PERSISTENT, PIPELINE_GRAPH = 0, 1, 2
+PIPELINE_STAGES, PIPELINE_PERSISTENT, PIPELINE_GRAPH, PIPELINE_OVERLAP = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 PROPOSAL_SPHERE, PROPOSAL_CONE = 0, 1
 
@@ -32,6 +33,7 @@ EXPORTED = [
     "ptca_surrogate_collect", "ptca_surrogate_train", "ptca_surrogate_grad", "ptca_surrogate_predict",
     "ptca_surrogate_enable", "ptca_set_checker", "ptca_checker_read", "ptca_set_launch_config",
     "ptca_get_launch_config", "ptca_autotune", "ptca_set_kernel_timing", "ptca_kernel_times",
+    "ptca_stage_split",
 ]
 
 
@@ -106,6 +108,7 @@ def lib():
             "ptca_sweep_record": ([vp, vp, vp, vp, vp, vp, vp], i32),
             "ptca_observables": ([vp, P(Obs), vp], i32),
             "ptca_schedule": ([P(Lattice), P(Params), vp, vp, P(i32)], i32),
+            "ptca_stage_split": ([P(Lattice), P(Params), vp, vp], i32),
             "ptca_last_error": ([], ctypes.c_char_p),
             "ptca_version": ([], i32),
             "ptca_sweep_noalloc": ([P(Lattice), P(Params), vp, vp, i32, vp, i64, vp, vp, vp], i32),
@@ -214,6 +217,24 @@ def ptca_schedule(cfg: Config):
     return [sites[start[s]:start[s + 1]].copy() for s in range(ns.value)]
 
 
+def ptca_stage_split(cfg: Config):
+    """Host-only dependence split of every stage on the stage before it: list
+    of (order, n_indep) per stage, order = int32 indices into the stage's site
+    list, the n_indep visits whose windows hold no site of the previous stage
+    first."""
+    import numpy as np
+    stages = ptca_schedule(cfg)
+    order = np.zeros(cfg.N, dtype=np.int32)
+    indep = np.zeros(len(stages), dtype=np.int32)
+    lat, par = cfg.lattice(), cfg.params()
+    _check(lib().ptca_stage_split(ctypes.byref(lat), ctypes.byref(par), _ptr(order), _ptr(indep)))
+    out, o = [], 0
+    for s, sites in enumerate(stages):
+        out.append((order[o:o + sites.size].copy(), int(indep[s])))
+        o += sites.size
+    return out
+
+
 def ptca_init(cfg: Config) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
     lat, par = cfg.lattice(), cfg.params()
@@ -320,13 +341,23 @@ def ptca_set_kernel_timing(h, on: bool) -> None:
     _check(lib().ptca_set_kernel_timing(h, 1 if on else 0))
 
 
-def ptca_kernel_times(h, stream=None):
-    """(stage_ms_total, stage_launches, resolve_ms_total, resolve_launches)
-    since the last call; clears the record."""
+# Per-kernel CUDA-event totals since the last read (see ptca_kernel_times).
+KernelTimes = namedtuple("KernelTimes", ["stage_ms", "stage_launches", "resolve_ms", "resolve_launches",
+                                         "dependent_ms", "dependent_launches", "stage_matrices",
+                                         "dependent_matrices"])
+
+
+def ptca_kernel_times(h, stream=None) -> KernelTimes:
+    """(stage_ms, stage_launches, resolve_ms, resolve_launches, dependent_ms,
+    dependent_launches, stage_matrices, dependent_matrices) since the last
+    call; clears the record.  The dependent_* entries are the overlapped
+    pipeline's launches of the visits that wait for the previous stage's
+    re-solve; stage_* are all other stage launches."""
     import numpy as np
-    out = np.zeros(4, dtype=np.float64)
+    out = np.zeros(8, dtype=np.float64)
     _check(lib().ptca_kernel_times(h, _ptr(out), _stream(stream)))
-    return float(out[0]), int(out[1]), float(out[2]), int(out[3])
+    return KernelTimes(float(out[0]), int(out[1]), float(out[2]), int(out[3]), float(out[4]), int(out[5]),
+                       int(out[6]), int(out[7]))
 
 
 def ptca_set_checker(h, on: bool) -> None:

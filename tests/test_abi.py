@@ -96,3 +96,52 @@ def test_init_reports_missing_gpu_instead_of_falling_back(built):
     with pytest.raises(P.PtcaError) as e:
         P.ptca_init(P.Config(Lx=8, Ly=8, L_c=4))
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("kw", [
+    dict(Lx=8, Ly=8, L_c=4),
+    dict(Lx=10, Ly=10, L_c=8, stride=5),
+    dict(Lx=32, Ly=32, L_c=8, stride=8),
+    dict(Lx=12, Ly=12, L_c=4, schedule=P.SCHEDULE_BLOCK),
+    dict(Lx=31, Ly=17, L_c=6, periodic=0, stride=6),
+    dict(Lx=8, Ly=1, L_c=4, schedule=P.SCHEDULE_BLOCK),
+    dict(Lx=9, Ly=7, L_c=4, periodic=0, schedule=P.SCHEDULE_BLOCK),
+])
+def test_stage_split_follows_the_window_rule(built, kw):
+    """The overlapped pipeline's split, against the oracle's window rule
+    (Sec. II.b): a visit of stage s is independent iff no site of stage s-1
+    (cyclically) lies in its window; each part is ordered largest window
+    first, ties in schedule order."""
+    cfg = P.Config(**kw)
+    m = oracle.Model(Lx=cfg.Lx, Ly=cfg.Ly, Lc=cfg.L_c, lattice_periodic=cfg.periodic,
+                     schedule=cfg.schedule, stride=cfg.stride)
+    stages = oracle.schedule(m)
+    split = P.ptca_stage_split(cfg)
+    assert len(split) == len(stages)
+    N = cfg.Lx * cfg.Ly
+    wsize = {}
+    for s, sites in enumerate(stages):
+        prev = stages[(s - 1) % len(stages)]
+        dep = []
+        for c, site in enumerate(sites):
+            dep.append(any(oracle.in_window(m, int(site), int(q)) for q in prev))
+            if int(site) not in wsize:
+                wsize[int(site)] = sum(oracle.in_window(m, int(site), g) for g in range(N))
+        order, n_indep = split[s]
+        assert sorted(order.tolist()) == list(range(sites.size))
+        assert n_indep == dep.count(False)
+        for part in (order[:n_indep], order[n_indep:]):
+            key = [(-wsize[int(sites[c])], int(c)) for c in part]
+            assert key == sorted(key)
+        assert not any(dep[c] for c in order[:n_indep])
+        assert all(dep[c] for c in order[n_indep:])
+
+
+def test_stage_split_of_the_100x100_block_schedule(built):
+    """Block schedule, 100 x 100 torus, L_c = 8, windows [x, x+7] x [y, y+7]:
+    a quadrant's visits that depend on the quadrant before it are the 7
+    columns whose windows wrap or reach into it (7 x 50 = 350), or, for the
+    quadrant diagonal to it, a 7 x 7 corner (49)."""
+    cfg = P.Config(Lx=100, Ly=100, L_c=8, schedule=P.SCHEDULE_BLOCK, precision=P.MIXED)
+    split = P.ptca_stage_split(cfg)
+    assert [n for _, n in split] == [2500 - 49, 2500 - 350, 2500 - 49, 2500 - 350]

@@ -1,7 +1,7 @@
-"""Stage pipeline (persistent launch, device-wide barrier, CUDA graph) and
-ragged window sizes.
+"""Stage pipeline (persistent launch, device-wide barrier, CUDA graph,
+overlapped re-solve) and ragged window sizes.
 
-The three launch modes must give bit-identical sweeps: they run the same
+The four launch modes must give bit-identical sweeps: they run the same
 per-cluster code on the same stage snapshots with the same counter-based
 random numbers.  The bounded barrier must give up and report a timeout
 instead of hanging.  Open lattices with L_c = 10 give windows from 5x5 to
@@ -32,7 +32,7 @@ def _lib():
 def test_pipelines_give_identical_sweeps(prec, lat):
     cfg = P.Config(**lat, T=0.1, mu=-6.5, seed=5, precision=prec, proposal=P.PROPOSAL_CONE)
     runs = {}
-    for mode in (P.PIPELINE_STAGES, P.PIPELINE_PERSISTENT, P.PIPELINE_GRAPH):
+    for mode in (P.PIPELINE_STAGES, P.PIPELINE_PERSISTENT, P.PIPELINE_GRAPH, P.PIPELINE_OVERLAP):
         ctx = P.Context(cfg)
         P.ptca_set_pipeline(ctx.h, mode)
         recs = []
@@ -45,7 +45,7 @@ def test_pipelines_give_identical_sweeps(prec, lat):
         runs[mode] = (ctx.spins().cpu().numpy(), recs)
         ctx.close()
     S0, r0 = runs[P.PIPELINE_STAGES]
-    for mode in (P.PIPELINE_PERSISTENT, P.PIPELINE_GRAPH):
+    for mode in (P.PIPELINE_PERSISTENT, P.PIPELINE_GRAPH, P.PIPELINE_OVERLAP):
         S, r = runs[mode]
         assert np.array_equal(S, S0)
         for a, b in zip(r, r0):
@@ -95,7 +95,8 @@ def test_launch_configurations_compute_the_same_chain(lat):
                    precision=P.MIXED)
     runs = []
     for pl, nw, cps in [(P.PIPELINE_GRAPH, 8, 0), (P.PIPELINE_STAGES, 4, 0), (P.PIPELINE_PERSISTENT, 4, 0),
-                        (P.PIPELINE_GRAPH, 4, 1), (P.PIPELINE_PERSISTENT, 8, 1)]:
+                        (P.PIPELINE_GRAPH, 4, 1), (P.PIPELINE_PERSISTENT, 8, 1), (P.PIPELINE_OVERLAP, 4, 0),
+                        (P.PIPELINE_OVERLAP, 8, 0)]:
         ctx = P.Context(cfg)
         P.ptca_set_launch_config(ctx.h, pl, nw, cps)
         got = P.ptca_get_launch_config(ctx.h)
@@ -124,7 +125,9 @@ def test_autotune_restores_the_chain_and_applies_the_fastest():
     timed = [c for c in table["candidates"] if c["ms_per_sweep"] is not None]
     assert len(timed) >= 6 and {c["warps_per_cta"] for c in timed} == {4, 8}
     fastest = min(timed, key=lambda c: c["ms_per_sweep"])
-    names = {P.PIPELINE_STAGES: "stages", P.PIPELINE_PERSISTENT: "persistent", P.PIPELINE_GRAPH: "graph"}
+    names = {P.PIPELINE_STAGES: "stages", P.PIPELINE_PERSISTENT: "persistent", P.PIPELINE_GRAPH: "graph",
+             P.PIPELINE_OVERLAP: "overlap"}
+    assert {c["pipeline"] for c in timed} == set(names.values())
     assert (names[best.pipeline], best.warps_per_cta, best.ctas_per_sm) == (
         fastest["pipeline"], fastest["warps_per_cta"], fastest["ctas_per_sm"])
     # The next sweep continues the chain exactly as without the tuning.
@@ -158,11 +161,57 @@ def test_kernel_timing_counts_the_stage_launches():
     P.ptca_set_launch_config(ctx.h, P.PIPELINE_STAGES, 8, 0)
     P.ptca_set_kernel_timing(ctx.h, True)
     ctx.sweep(2)
-    st_ms, st_n, rs_ms, rs_n = P.ptca_kernel_times(ctx.h)
+    kt = P.ptca_kernel_times(ctx.h)
+    st_ms, st_n, rs_ms, rs_n = kt[:4]
     assert st_n == 2 * ns and rs_n == 2 * ns and st_ms > 0 and rs_ms >= 0
-    assert P.ptca_kernel_times(ctx.h) == (0.0, 0, 0.0, 0)   # read clears
+    assert kt.stage_matrices == 2 * 2 * cfg.N and kt.dependent_launches == 0
+    assert tuple(P.ptca_kernel_times(ctx.h)) == (0.0, 0, 0.0, 0, 0.0, 0, 0, 0)   # read clears
+    # Overlapped pipeline: the independent and the dependent visits of each
+    # stage are separate launches; together they solve every matrix once.
+    P.ptca_set_launch_config(ctx.h, P.PIPELINE_OVERLAP, 8, 0)
+    ctx.sweep(2)
+    kt = P.ptca_kernel_times(ctx.h)
+    split = P.ptca_stage_split(cfg)
+    assert kt.stage_launches == 2 * sum(1 for _, n in split if n > 0)
+    assert kt.dependent_launches == 2 * sum(1 for o, n in split if o.size > n)
+    assert kt.resolve_launches == 2 * ns
+    assert kt.stage_matrices + kt.dependent_matrices == 2 * 2 * cfg.N
+    assert kt.stage_matrices == 2 * 2 * sum(n for _, n in split)
     P.ptca_set_launch_config(ctx.h, P.PIPELINE_GRAPH, 8, 0)
     ctx.sweep(1)
     assert P.ptca_kernel_times(ctx.h)[1] == 0               # one persistent launch: not per-stage
     P.ptca_set_kernel_timing(ctx.h, False)
     ctx.close()
+
+
+@pytest.mark.parametrize("lat", [
+    dict(Lx=32, Ly=32, L_c=8, schedule=P.SCHEDULE_BLOCK),          # 4 stages
+    dict(Lx=13, Ly=11, L_c=6, periodic=0, stride=6),                # ragged windows, 6 stages
+    dict(Lx=24, Ly=1, L_c=4, schedule=P.SCHEDULE_BLOCK),            # chain: 2 stages
+    dict(Lx=24, Ly=24, L_c=8, stride=8),                            # tiled: 64 stages of 9 sites
+])
+@pytest.mark.parametrize("margin", [1e-2, 50.0])
+def test_overlapped_resolve_gives_the_one_stream_chain_bit_for_bit(lat, margin):
+    """The overlapped pipeline against the one-stream per-stage pipeline:
+    spins and every field of the per-visit record identical (F to the bit).
+    margin 50 defers every decision, so every visit is re-solved while the
+    next stage's independent visits run."""
+    cfg = P.Config(**lat, T=0.1, mu=-6.5, seed=29, precision=P.MIXED, proposal=P.PROPOSAL_CONE)
+    runs = []
+    for mode in (P.PIPELINE_STAGES, P.PIPELINE_OVERLAP):
+        ctx = P.Context(cfg)
+        P.ptca_set_resolve_margin(ctx.h, margin)
+        P.ptca_set_launch_config(ctx.h, mode, 8, 0)
+        recs, stats = [], []
+        for n in (1, 3, 2):
+            st = ctx.sweep(n)
+            stats.append((st.attempts, st.accepted, st.eigensolves))
+            recs.append([x.cpu().numpy() for x in ctx.record()])
+        runs.append((ctx.spins().cpu().numpy(), recs, stats))
+        ctx.close()
+    (S0, r0, t0), (S1, r1, t1) = runs
+    assert t0 == t1
+    assert np.array_equal(S0, S1)
+    for a, b in zip(r0, r1):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
