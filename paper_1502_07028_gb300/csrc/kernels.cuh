@@ -514,17 +514,19 @@ __global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int c
 }
 
 // Re-solve of one matrix of a deferred update site (stage index c from the
-// flag list) at FP64-class precision: the matrix lives in this CTA's global
-// slot and is built and reduced in double-float arithmetic (about 48
-// significant bits on the FP32 pipe), the eigenvalues of the resulting
-// tridiagonal run in FP64, and the second of the pair decides (no margin
-// test).  nmaxc = 32 * NT sizes the vectors in shared memory.
-template <int NT, int NWP = NW>
+// flag list) at FP64-class precision: the matrix is built and reduced in
+// double-float arithmetic (about 48 significant bits on the FP32 pipe), the
+// eigenvalues of the resulting tridiagonal run in FP64, and the second of the
+// pair decides (no margin test).  The matrix lives in shared memory when
+// kSmemA (a.nA up to about 150 fits beside the vectors in one CTA), else in
+// this CTA's global slot; the arithmetic is the same either way.  nmaxc =
+// 32 * NT sizes the vectors in shared memory.
+template <int NT, int NWP = NW, bool kSmemA = false>
 __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, int c, int var, unsigned char* smem,
                                           double* s_new, int* s_last) {
-    const SmemLayout L = smem_layout(0, 32 * NT, sizeof(dfl2), NWP);
+    const SmemLayout L = smem_layout(kSmemA ? a.nA : 0, 32 * NT, sizeof(dfl2), NWP);
     Carve<dfl> cv = carve<dfl>(smem, L, NWP);
-    cv.A = reinterpret_cast<dfl2*>(a.gA + (int64_t)blockIdx.x * a.gA_stride);
+    if constexpr (!kSmemA) cv.A = reinterpret_cast<dfl2*>(a.gA + (int64_t)blockIdx.x * a.gA_stride);
     const int site = v.sites[c];
     const Window w = make_window(a.m, site);
     const int n = 2 * w.ex * w.ey;
@@ -576,13 +578,14 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, 
     atomicAdd(&a.counters[1], 2ull);
 }
 
-// Re-solve the deferred update sites of one stage (per-stage pipeline), one
-// CTA of RESOLVE_NW warps per matrix.  The same width as the persistent
-// kernel's inline re-solve, so both pipelines produce bit-identical results.
-// 16 warps were measured slower: the pass gains less than the scalar phases
-// lose to the wider barriers and to spills at 128 registers.
+// Re-solve the deferred update sites of one stage (per-stage pipelines), one
+// CTA of RESOLVE_NW warps per matrix, the matrix in shared memory when
+// kSmemA.  The same width as the persistent kernel's inline re-solve, so all
+// pipelines produce bit-identical results.  16 warps were measured slower:
+// the pass gains less than the scalar phases lose to the wider barriers and
+// to spills at 128 registers.
 constexpr int RESOLVE_NW = 8;
-template <int NT>
+template <int NT, bool kSmemA>
 __global__ void __launch_bounds__(32 * RESOLVE_NW, 1) k_resolve(StageArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_new[3];
@@ -590,7 +593,7 @@ __global__ void __launch_bounds__(32 * RESOLVE_NW, 1) k_resolve(StageArgs a) {
     const int nflag = (int)*(volatile unsigned int*)a.flag_count;
     for (int item = blockIdx.x; item < 2 * nflag; item += gridDim.x) {
         const int c = a.flag_list[item >> 1];
-        resolve_item<NT, RESOLVE_NW>(a, stage_var(a), c, item & 1, smem, s_new, &s_last);
+        resolve_item<NT, RESOLVE_NW, kSmemA>(a, stage_var(a), c, item & 1, smem, s_new, &s_last);
         __syncthreads();
     }
 }
