@@ -41,7 +41,7 @@ HH_FLOPS = sum(32 * m * (m + 1) // 2 for m in range(1, N_ORDER))
 # (a launch's bytes / the matrices it solved; a launch's traffic is this
 # times its matrices).  A value goes back to None whenever its kernel
 # changes, until captured again.
-DRAM_BYTES_PER_MATRIX = {"k_stage<float,4,8>": None, "k_stage<float,4,4>": None,
+DRAM_BYTES_PER_MATRIX = {"k_stage<float,4,8>": None, "k_stage<float,4,4>": 312_320 / 4902,
                          "k_sweep_persistent<float,4,8>": None, "k_sweep_persistent<float,4,4>": None}
 
 
@@ -497,7 +497,9 @@ def main():
                          "matrices_per_launch": matrices_per_launch, "resolve_ms_per_step": resolve_ms_per_step,
                          "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak, "traffic": traffic,
-                         "note": "FP32 FMA pipe, Householder flops only; peak = 152 SM x 128 lanes x 2 x max clock"},
+                         "note": "FP32 FMA pipe, Householder flops only; peak = 152 SM x 128 lanes x 2 x max clock; "
+                                 "in the overlap pipeline the stage launches share the GPU with the previous "
+                                 "stage's re-solve"},
             "mixed_error": mixed_error,
             "cpu_baseline": cpu,
             "clocks": clocks,
