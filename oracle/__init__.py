@@ -10,7 +10,10 @@ What each function follows (paper sections):
   * ``cluster_hamiltonian`` -- the cluster Hamiltonian H_clus{C[i_s]} built
     around an update site (Sec. II.b-c, Fig. 1), periodic on the cluster
     (Sec. II.b), two spin species per site (Sec. IV, 2N x 2N matrices); the
-    model itself is the double-exchange Hamiltonian (-t hopping, -J_H S.sigma).
+    model is the double-exchange Hamiltonian (-t hopping, -J_H S.sigma) or the
+    Hubbard mean-field Hamiltonian of Eq. 1 with <n_i> = 1 (on-site
+    (U/2)(n_i - m_i.sigma), classical energy (U/4)(m_i^2 - 1) per window site
+    in the cluster free energy), chosen by ``Model.model``.
   * ``eigvalsh`` -- cyclic complex Jacobi diagonalisation (Sec. II.c step b).
   * ``free_energy`` -- grand-canonical one-body free energy of the cluster
     (Sec. II.b: the periodic cluster is a grand-canonical ensemble).
@@ -39,6 +42,8 @@ _lib = None
 
 SCHEDULE_TILED = 0
 SCHEDULE_BLOCK = 1
+MODEL_DOUBLE_EXCHANGE = 0
+MODEL_HUBBARD_MF = 1
 PROPOSAL_SPHERE = 0
 PROPOSAL_CONE = 1
 
@@ -67,6 +72,8 @@ class _Model(ctypes.Structure):
         ("t", ctypes.c_double), ("JH", ctypes.c_double),
         ("mu", ctypes.c_double), ("T", ctypes.c_double),
         ("cone_deg", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("model", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("U", ctypes.c_double), ("m_step", ctypes.c_double),
     ]
 
 
@@ -91,6 +98,9 @@ class Model:
     seed: int = 0
     ox: int = -1
     oy: int = -1
+    model: int = MODEL_DOUBLE_EXCHANGE
+    U: float = 8.0
+    m_step: float = 0.5
 
     def _c(self) -> _Model:
         off = (self.Lc // 2) if self.schedule == SCHEDULE_TILED else 0
@@ -100,7 +110,7 @@ class Model:
         stride = self.stride if self.stride > 0 else self.Lc
         return _Model(self.Lx, self.Ly, self.lattice_periodic, self.Lc, ox, oy, cp,
                       self.schedule, stride, self.proposal, self.t, self.JH,
-                      self.mu, self.T, self.cone_deg, self.seed)
+                      self.mu, self.T, self.cone_deg, self.seed, self.model, 0, self.U, self.m_step)
 
     @property
     def N(self) -> int:

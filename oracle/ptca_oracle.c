@@ -20,10 +20,15 @@
  * the same on x86-64 and aarch64:
  *     gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off -o libptca_oracle.so ptca_oracle.c -lm
  *
- * Model (double-exchange spin-fermion model on a square lattice): hopping -t
- * between nearest neighbours of the same spin and a Hund term -J_H S_i . sigma
- * on every site, with classical unit spins S_i.  The cluster matrix has two
- * rows per cluster site (two spin species, Sec. IV: "2N x 2N").
+ * Models on a square lattice, both with hopping -t between nearest neighbours
+ * of the same spin and two rows per cluster site in the cluster matrix (two
+ * spin species, Sec. IV: "2N x 2N"):
+ *   model 0, double exchange: a Hund term -J_H S_i . sigma on every site, with
+ *     classical unit spins S_i;
+ *   model 1, Hubbard mean field (Eq. 1, <n_i> = 1): an on-site term
+ *     (U/2)(n_i - m_i . sigma_i) with classical vectors m_i of any length, and
+ *     the classical energy (U/4)(m_i^2 - 1) of every site, which the cluster
+ *     free energy includes for the sites of its window.
  */
 #include <complex.h>
 #include <math.h>
@@ -49,6 +54,10 @@ typedef struct {
     double t, JH, mu, T;
     double cone_deg;
     uint64_t seed;
+    int32_t model;             /* 0: double exchange, 1: Hubbard mean field      */
+    int32_t pad0;
+    double U;                  /* model 1: Hubbard U                             */
+    double m_step;             /* model 1: radius of the proposal ball           */
 } oracle_model;
 
 /* ------------------------------------------------------------------------ */
@@ -80,7 +89,7 @@ void oracle_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t
 /* Random-number stream of the method: key = seed, counter = (site, purpose,
  * sweep lo, sweep hi).  Two doubles per call, each built from 53 bits of a
  * 64-bit word as (x/2^11 + 1/2) * 2^-53, which lies strictly inside (0,1). */
-enum { PURPOSE_INIT = 0, PURPOSE_PROPOSE = 1, PURPOSE_ACCEPT = 2 };
+enum { PURPOSE_INIT = 0, PURPOSE_PROPOSE = 1, PURPOSE_ACCEPT = 2, PURPOSE_RADIUS = 4 };
 
 void oracle_uniform2(uint64_t seed, uint64_t sweep, uint32_t site, uint32_t purpose, double u[2])
 {
@@ -125,6 +134,18 @@ void oracle_propose(const oracle_model* m, uint64_t sweep, int site, const doubl
 {
     double u[2];
     oracle_uniform2(m->seed, sweep, (uint32_t)site, PURPOSE_PROPOSE, u);
+    if (m->model == 1) {
+        /* Hubbard mean field: m_new = m_old + d, d uniform in the ball of
+         * radius m_step (direction uniform on the sphere, radius
+         * m_step * v^(1/3)).  The proposal is symmetric in (m_old, m_new), so
+         * Metropolis on dF samples exp(-F/T) d^3m. */
+        double dir[3], v[2];
+        sphere_point(u, dir);
+        oracle_uniform2(m->seed, sweep, (uint32_t)site, PURPOSE_RADIUS, v);
+        double r = m->m_step * cbrt(v[0]);
+        for (int k = 0; k < 3; ++k) s_new[k] = s_old[k] + r * dir[k];
+        return;
+    }
     if (m->proposal == 0) {
         sphere_point(u, s_new);
         return;
@@ -200,12 +221,15 @@ int oracle_cluster_hamiltonian(const oracle_model* m, const double* S, int site,
             int g = window_site(m, x0, y0, wx, wy);
             const double* s = S + 3 * g;
             if (s_new && g == site) s = s_new;
-            /* Hund term -J_H S.sigma on the 2x2 spin block of this site. */
+            /* On-site 2x2 spin block: -J_H S.sigma (model 0), or
+             * (U/2) 1 - (U/2) m.sigma (model 1). */
             int a = 2 * w, b = 2 * w + 1;
-            H[a * n + a] += -m->JH * s[2];
-            H[b * n + b] += m->JH * s[2];
-            H[a * n + b] += -m->JH * (s[0] - I * s[1]);
-            H[b * n + a] += -m->JH * (s[0] + I * s[1]);
+            double J = m->model == 1 ? 0.5 * m->U : m->JH;
+            double e0 = m->model == 1 ? 0.5 * m->U : 0.0;
+            H[a * n + a] += e0 - J * s[2];
+            H[b * n + b] += e0 + J * s[2];
+            H[a * n + b] += -J * (s[0] - I * s[1]);
+            H[b * n + a] += -J * (s[0] + I * s[1]);
             /* Hopping -t to the +x and +y neighbours (each bond once). */
             int nb[2] = {-1, -1};
             if (wx + 1 < ex) nb[0] = wy * ex + (wx + 1);
@@ -302,14 +326,36 @@ double oracle_free_energy(int n, const double* eig, double mu, double T)
     return -T * acc;
 }
 
-/* Cluster free energy at update site `site` (spin replaced when s_new). */
+/* Classical energy of the window of update site `site` (model 1: the sum of
+ * (U/4)(m_i^2 - 1) over its sites, m of the update site replaced by s_new
+ * when given; model 0: zero). */
+static double window_classical(const oracle_model* m, const double* S, int site, const double* s_new)
+{
+    if (m->model != 1) return 0.0;
+    int cx = site % m->Lx, cy = site / m->Lx;
+    int x0, y0, ex, ey;
+    window_axis(m->Lx, m->lattice_periodic, m->Lc, m->ox, cx, &x0, &ex);
+    window_axis(m->Ly, m->lattice_periodic, m->Lc, m->oy, cy, &y0, &ey);
+    double acc = 0.0;
+    for (int wy = 0; wy < ey; ++wy)
+        for (int wx = 0; wx < ex; ++wx) {
+            int g = window_site(m, x0, y0, wx, wy);
+            const double* v = (s_new && g == site) ? s_new : S + 3 * g;
+            acc += 0.25 * m->U * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] - 1.0);
+        }
+    return acc;
+}
+
+/* Cluster free energy at update site `site` (spin replaced when s_new): the
+ * one-body free energy of the cluster matrix plus, for model 1, the classical
+ * energy of the window. */
 static double cluster_F(const oracle_model* m, const double* S, int site, const double* s_new,
                         cplx* Hbuf, double* ebuf, int* n_out)
 {
     int n = oracle_cluster_hamiltonian(m, S, site, s_new, Hbuf, NULL, NULL);
     oracle_eigvalsh_jacobi(n, Hbuf, ebuf);
     if (n_out) *n_out = n;
-    return oracle_free_energy(n, ebuf, m->mu, m->T);
+    return oracle_free_energy(n, ebuf, m->mu, m->T) + window_classical(m, S, site, s_new);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -48,3 +48,12 @@ def random_hermitian(seed: int, n: int, scale: float = 1.0) -> np.ndarray:
 
 def random_sites(seed: int, N: int, m: int) -> np.ndarray:
     return rng(seed).choice(N, size=m, replace=False).astype(np.int32)
+
+
+def random_fields(seed: int, N: int, rmax: float) -> np.ndarray:
+    """N classical vectors with isotropic directions and lengths uniform in
+    [0, rmax] (mean-field magnetisations of any length)."""
+    g = rng(seed)
+    d = g.normal(size=(N, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return d * g.uniform(0.0, rmax, size=(N, 1))
