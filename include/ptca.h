@@ -60,6 +60,7 @@ typedef enum {
 enum { PTCA_SCHEDULE_TILED = 0, PTCA_SCHEDULE_BLOCK = 1 };
 enum { PTCA_FP64 = 0, PTCA_MIXED = 1 };
 enum { PTCA_PROPOSAL_SPHERE = 0, PTCA_PROPOSAL_CONE = 1 };
+enum { PTCA_MODEL_DOUBLE_EXCHANGE = 0, PTCA_MODEL_HUBBARD_MF = 1 };
 enum { PTCA_PIPELINE_STAGES = 0, PTCA_PIPELINE_PERSISTENT = 1, PTCA_PIPELINE_GRAPH = 2, PTCA_PIPELINE_OVERLAP = 3 };
 
 /* Square lattice.  Ly == 1 is a one-dimensional chain (Sec. III.a, Fig. 3). */
@@ -68,9 +69,20 @@ typedef struct {
     int32_t periodic; /* 1: torus; 0: open edges (windows are clipped at the edges) */
 } ptca_lattice;
 
+/* Problem parameters.  Two models share the lattice, the hopping -t and the
+ * two spin species per site:
+ *   PTCA_MODEL_DOUBLE_EXCHANGE  on-site -J_H S_i . sigma, classical unit spins S_i
+ *                               (proposals: sphere or cone);
+ *   PTCA_MODEL_HUBBARD_MF       Eq. 1 with <n_i> = 1: on-site (U/2)(1 - m_i . sigma)
+ *                               with classical vectors m_i of any length, and the
+ *                               classical energy (U/4)(m_i^2 - 1) of every window
+ *                               site in the cluster free energy; proposals
+ *                               m_new = m_old + a step uniform in the ball of
+ *                               radius m_step.  Spins, S(q) and the records then
+ *                               hold the fields m_i. */
 typedef struct {
     double t;                 /* hopping                                              */
-    double J_H;               /* Hund coupling                                        */
+    double J_H;               /* Hund coupling (double exchange)                      */
     double mu;                /* chemical potential                                   */
     double T;                 /* temperature (> 0)                                    */
     int32_t L_c;              /* linear cluster size, 2 <= L_c <= min(Lx, Ly)         */
@@ -85,9 +97,11 @@ typedef struct {
     int32_t precision;        /* PTCA_FP64 or PTCA_MIXED (FP32 reduction to tridiagonal */
                               /* form; FP64 eigenvalues, free energies and dF)        */
     int32_t proposal;         /* PTCA_PROPOSAL_SPHERE or PTCA_PROPOSAL_CONE            */
-    int32_t reserved0;
+    int32_t model;            /* PTCA_MODEL_DOUBLE_EXCHANGE (0) or PTCA_MODEL_HUBBARD_MF */
     double cone_deg;          /* half-angle of the cone proposal, degrees             */
     uint64_t seed;            /* key of the counter-based generator                   */
+    double U;                 /* Hubbard U (PTCA_MODEL_HUBBARD_MF), finite            */
+    double m_step;            /* radius of the field proposal ball (Hubbard), > 0     */
 } ptca_params;
 
 /* Per-call sweep statistics (host struct filled by ptca_sweep when non-NULL). */

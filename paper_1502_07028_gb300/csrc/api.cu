@@ -189,6 +189,13 @@ ptca_status resolve(const ptca_lattice* lat, const ptca_params* par, Problem& p)
     if (p.proposal != PTCA_PROPOSAL_SPHERE && p.proposal != PTCA_PROPOSAL_CONE)
         return fail(PTCA_ERR_INVALID, "unknown proposal");
     p.t = par->t; p.JH = par->J_H; p.mu = par->mu; p.T = par->T; p.cone_deg = par->cone_deg; p.seed = par->seed;
+    p.model = par->model;
+    p.U = par->U;
+    p.m_step = par->m_step;
+    if (p.model != PTCA_MODEL_DOUBLE_EXCHANGE && p.model != PTCA_MODEL_HUBBARD_MF)
+        return fail(PTCA_ERR_INVALID, "unknown model");
+    if (p.model == PTCA_MODEL_HUBBARD_MF && (!std::isfinite(p.U) || !(p.m_step > 0) || !std::isfinite(p.m_step)))
+        return fail(PTCA_ERR_INVALID, "Hubbard mean field needs a finite U and a finite m_step > 0");
     if (!std::isfinite(p.t) || !std::isfinite(p.JH) || !std::isfinite(p.mu) || !std::isfinite(p.T) || !(p.T > 0))
         return fail(PTCA_ERR_INVALID, "t, J_H, mu must be finite and T > 0");
     if (p.proposal == PTCA_PROPOSAL_CONE && !(p.cone_deg > 0 && p.cone_deg <= 180))
@@ -203,8 +210,14 @@ Model to_model(const Problem& p) {
     m.Lx = p.Lx; m.Ly = p.Ly; m.lattice_periodic = p.periodic;
     m.Lc = p.Lc; m.ox = p.ox; m.oy = p.oy; m.cluster_periodic = p.cluster_periodic;
     m.proposal = p.proposal;
-    m.t = p.t; m.JH = p.JH; m.mu = p.mu; m.T = p.T;
+    m.t = p.t; m.mu = p.mu; m.T = p.T;
     m.cone_cos = std::cos(p.cone_deg * ptca::kPi / 180.0);
+    m.model = p.model;
+    if (p.model == PTCA_MODEL_HUBBARD_MF) {
+        m.JH = 0.5 * p.U; m.e0 = 0.5 * p.U; m.ucl = 0.25 * p.U; m.m_step = p.m_step;
+    } else {
+        m.JH = p.JH; m.e0 = 0.0; m.ucl = 0.0; m.m_step = 0.0;
+    }
     m.seed = p.seed;
     return m;
 }
@@ -1062,6 +1075,8 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
 
 ptca_status ptca_surrogate_collect(ptca_ctx* ctx, int32_t n_sweeps, float* feat, int32_t* center, float* dF,
                                    void* stream) {
+    if (ctx && ctx->p.model != PTCA_MODEL_DOUBLE_EXCHANGE)
+        return fail(PTCA_ERR_UNSUPPORTED, "the surrogate screen is built for the double-exchange model");
     if (!ctx || n_sweeps < 0 || !feat || !center || !dF) return fail(PTCA_ERR_INVALID, "bad arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));

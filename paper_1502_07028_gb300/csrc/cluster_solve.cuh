@@ -15,11 +15,17 @@
 namespace ptca {
 
 // Problem description the kernels need (copied by value into each launch).
+// Problem on the device.  model 0 (double exchange): on-site -JH S.sigma with
+// unit spins.  model 1 (Hubbard mean field, Eq. 1 with <n_i> = 1): on-site
+// e0 - JH m.sigma with JH = e0 = U/2, classical energy ucl (|m|^2 - 1) per
+// window site with ucl = U/4, proposals uniform in a ball of radius m_step.
 struct Model {
     int32_t Lx, Ly, lattice_periodic;
     int32_t Lc, ox, oy, cluster_periodic;
     int32_t proposal;
+    int32_t model;
     double t, JH, mu, T, cone_cos;
+    double e0, ucl, m_step;
     uint64_t seed;
 };
 
@@ -55,15 +61,51 @@ __device__ __forceinline__ int window_site(const Model& m, const Window& w, int 
 
 __device__ __forceinline__ int tri(int r) { return (r * (r + 1)) >> 1; }
 
+// Proposed new classical vector at `site` (Sec. II.c step c).  Double
+// exchange: propose_spin (sphere or cone).  Hubbard mean field: the old field
+// plus a step uniform in the ball of radius m_step -- direction from the
+// proposal uniforms (as the sphere proposal), length m_step v^(1/3) with v
+// the first uniform of purpose RNG_RADIUS; symmetric in (old, new).
+__device__ __forceinline__ void propose(const Model& m, uint64_t sweep, uint32_t site, const double so[3],
+                                        double sn[3]) {
+    if (m.model != 1) {
+        propose_spin(m.seed, sweep, site, m.proposal, m.cone_cos, so, sn);
+        return;
+    }
+    double u0, u1, v0, v1, dir[3];
+    uniform2(m.seed, sweep, site, RNG_PROPOSE, u0, u1);
+    unit_from_uniforms(u0, u1, dir);
+    uniform2(m.seed, sweep, site, RNG_RADIUS, v0, v1);
+    const double r = m.m_step * cbrt(v0);
+    sn[0] = so[0] + r * dir[0];
+    sn[1] = so[1] + r * dir[1];
+    sn[2] = so[2] + r * dir[2];
+}
+
+// Classical energy of a window (Hubbard mean field): ucl (|m|^2 - 1) summed
+// over its nsite vectors sp[nsite][3]; zero for the double-exchange model.
+// One thread.
+__device__ __forceinline__ double window_classical(const Model& m, const double* sp, int nsite) {
+    if (m.ucl == 0.0) return 0.0;
+    double acc = 0.0;
+    for (int s = 0; s < nsite; ++s)
+        acc += m.ucl * (sp[3 * s] * sp[3 * s] + sp[3 * s + 1] * sp[3 * s + 1] + sp[3 * s + 2] * sp[3 * s + 2] - 1.0);
+    return acc;
+}
+
 // Gather the window spins into sp[nsite][3] (replacing the update site's spin
 // by s_new when s_new != nullptr) and build the packed cluster matrix:
-//   Hund block   -J_H [[S_z, S_x - i S_y], [S_x + i S_y, -S_z]] per site,
-//   hopping      -t between nearest neighbours, same spin, each bond once;
+//   on-site block  e0 - J [[S_z, S_x - i S_y], [S_x + i S_y, -S_z]] per site
+//                  (J = m.JH; e0 is the caller's diagonal shift),
+//   hopping        -t between nearest neighbours, same spin, each bond once;
 // a periodic cluster wraps inside the window (an axis of extent 2 then has
-// two bonds between its two sites, extent 1 none).  Caller syncs after.
+// two bonds between its two sites, extent 1 none).  Caller syncs after.  The
+// sweep kernels pass e0 = 0 and shift mu by -m.e0 instead: a multiple of the
+// identity moves every eigenvalue by exactly e0, and the reduction keeps its
+// relative precision on the unshifted matrix.
 template <typename T>
 __device__ void build_cluster(const Model& m, const Window& w, const double* __restrict__ S,
-                              const double* s_new, double* sp, cplx_t<T>* A) {
+                              const double* s_new, double* sp, cplx_t<T>* A, double e0 = 0.0) {
     using V = cplx_t<T>;
     const int nsite = w.ex * w.ey, n = 2 * nsite, P = tri(n);
     for (int i = threadIdx.x; i < P; i += blockDim.x) A[i] = mk(T(0), T(0));
@@ -77,13 +119,13 @@ __device__ void build_cluster(const Model& m, const Window& w, const double* __r
         sp[3 * s] = v0; sp[3 * s + 1] = v1; sp[3 * s + 2] = v2;
     }
     __syncthreads();
-    const T t = T(m.t), J = T(m.JH);
+    const T t = T(m.t), J = T(m.JH), d0 = T(e0);
     for (int s = threadIdx.x; s < nsite; s += blockDim.x) {
         const int wx = s % w.ex, wy = s / w.ex;
         const T sx = T(sp[3 * s]), sy = T(sp[3 * s + 1]), sz = T(sp[3 * s + 2]);
         const int a = 2 * s, b = 2 * s + 1;
-        A[tri(a) + a] = mk(-J * sz, T(0));
-        A[tri(b) + b] = mk(J * sz, T(0));
+        A[tri(a) + a] = mk(d0 - J * sz, T(0));
+        A[tri(b) + b] = mk(d0 + J * sz, T(0));
         A[tri(b) + a] = mk(-J * sx, -J * sy);  // element (b, a) = -J_H (S_x + i S_y)
         // +x bond
         int nb = -1, mult = 1;

@@ -10,8 +10,8 @@
 
 // Resolved problem (defaults filled in).
 struct Problem {
-    int Lx, Ly, periodic, Lc, ox, oy, cluster_periodic, schedule, stride, precision, proposal;
-    double t, JH, mu, T, cone_deg;
+    int Lx, Ly, periodic, Lc, ox, oy, cluster_periodic, schedule, stride, precision, proposal, model;
+    double t, JH, mu, T, cone_deg, U, m_step;
     uint64_t seed;
     int N() const { return Lx * Ly; }
     int nsite_max() const { return Lc * (Ly == 1 ? 1 : Lc); }

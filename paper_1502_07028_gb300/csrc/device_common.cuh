@@ -109,7 +109,9 @@ __device__ __forceinline__ U4 philox10(uint32_t k0, uint32_t k1, U4 x) {
     return x;
 }
 
-enum : uint32_t { RNG_INIT = 0, RNG_PROPOSE = 1, RNG_ACCEPT = 2, RNG_SCREEN = 3, RNG_BATCH = 16, RNG_PARAM = 17 };
+enum : uint32_t {
+    RNG_INIT = 0, RNG_PROPOSE = 1, RNG_ACCEPT = 2, RNG_SCREEN = 3, RNG_RADIUS = 4, RNG_BATCH = 16, RNG_PARAM = 17
+};
 
 // Two uniforms in (0,1) for (seed, sweep, site, purpose): each from 53 bits
 // of one 64-bit half of the Philox output, (x + 1/2) 2^-53.

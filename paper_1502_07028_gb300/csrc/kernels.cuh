@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(CTA) k_build(Model m, const double* __restrict
     const int site = sites[c];
     const Window w = make_window(m, site);
     cplx_t<T>* A = H + (int64_t)c * stride;
-    build_cluster<T>(m, w, S, new_spins ? new_spins + 3 * c : nullptr, sp, A);
+    build_cluster<T>(m, w, S, new_spins ? new_spins + 3 * c : nullptr, sp, A, m.e0);
     if (threadIdx.x == 0) { offsets[c] = (int64_t)c * stride; nout[c] = 2 * w.ex * w.ey; }
 }
 
@@ -390,16 +390,19 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
     const Window w = make_window(a.m, site);
     const int n = 2 * w.ex * w.ey;
     if (threadIdx.x == 0 && var == 1)
-        propose_spin(a.m.seed, v.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, v.S_in + 3 * site, s_new);
+        propose(a.m, v.sweep, (uint32_t)site, v.S_in + 3 * site, s_new);
     __syncthreads();
     build_cluster<T>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     __syncthreads();
+    // The window's classical energy (Hubbard mean field), parked in this
+    // matrix's F slot until the eigenvalues are known.
+    if (threadIdx.x == 0 && a.m.ucl != 0.0) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
     householder_tridiag<T, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
-    tridiag_eig_F<T, NWP>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
+    tridiag_eig_F<T, NWP>(n, cv, a.m.mu - a.m.e0, a.m.T, false, nullptr, ssp, sfe, K);
     if (threadIdx.x == 0) {
-        const double F = -a.m.T * ssp;
+        const double F = -a.m.T * ssp + (a.m.ucl != 0.0 ? a.Fbuf[2 * c + var] : 0.0);
         a.Fbuf[2 * c + var] = F;
         a.fillbuf[2 * c + var] = sfe;
         __threadfence();
@@ -415,7 +418,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
     double sn[3];
     const double* so = v.S_in + 3 * site;
     if (var == 1) { sn[0] = s_new[0]; sn[1] = s_new[1]; sn[2] = s_new[2]; }
-    else propose_spin(a.m.seed, v.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, so, sn);
+    else propose(a.m, v.sweep, (uint32_t)site, so, sn);
     double u0, u1;
     uniform2(a.m.seed, v.sweep, (uint32_t)site, RNG_ACCEPT, u0, u1);
     const double lnu = log(u0);
@@ -476,15 +479,16 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_check(StageArg
     const Window w = make_window(a.m, site);
     const int n = 2 * w.ex * w.ey;
     if (threadIdx.x == 0 && var == 1)
-        propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, s_new);
+        propose(a.m, a.sweep, (uint32_t)site, a.S_in + 3 * site, s_new);
     __syncthreads();
     build_cluster<T>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     __syncthreads();
+    const double cls = threadIdx.x == 0 ? window_classical(a.m, cv.sp, n / 2) : 0.0;
     householder_tridiag<T, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
-    tridiag_eig_F<T>(n, cv, a.m.mu, a.m.T, true, eig + (int64_t)(2 * c + var) * ld, ssp, sfe, K);
-    if (threadIdx.x == 0) F[2 * c + var] = -a.m.T * ssp;
+    tridiag_eig_F<T>(n, cv, a.m.mu - a.m.e0, a.m.T, true, eig + (int64_t)(2 * c + var) * ld, ssp, sfe, K);
+    if (threadIdx.x == 0) F[2 * c + var] = -a.m.T * ssp + cls;
 }
 
 template <int NT>
@@ -500,15 +504,16 @@ __global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int c
         const Window w = make_window(a.m, site);
         const int n = 2 * w.ex * w.ey;
         if (threadIdx.x == 0 && var == 1)
-            propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, s_new);
+            propose(a.m, a.sweep, (uint32_t)site, a.S_in + 3 * site, s_new);
         __syncthreads();
         build_cluster<double>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
         __syncthreads();
+        const double cls = threadIdx.x == 0 ? window_classical(a.m, cv.sp, n / 2) : 0.0;
         householder_tridiag<double, NT, NW>(n, cv.A, cv.hh, cv.d, cv.e2);
         double ssp, sfe;
         int K;
-        tridiag_eig_F<double>(n, cv, a.m.mu, a.m.T, true, eig + (int64_t)(2 * c + var) * ld, ssp, sfe, K);
-        if (threadIdx.x == 0) F[2 * c + var] = -a.m.T * ssp;
+        tridiag_eig_F<double>(n, cv, a.m.mu - a.m.e0, a.m.T, true, eig + (int64_t)(2 * c + var) * ld, ssp, sfe, K);
+        if (threadIdx.x == 0) F[2 * c + var] = -a.m.T * ssp + cls;
         __syncthreads();
     }
 }
@@ -531,16 +536,17 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, 
     const Window w = make_window(a.m, site);
     const int n = 2 * w.ex * w.ey;
     if (threadIdx.x == 0 && var == 1)
-        propose_spin(a.m.seed, v.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, v.S_in + 3 * site, s_new);
+        propose(a.m, v.sweep, (uint32_t)site, v.S_in + 3 * site, s_new);
     __syncthreads();
     build_cluster<dfl>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     __syncthreads();
+    if (threadIdx.x == 0 && a.m.ucl != 0.0) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
     householder_tridiag<dfl, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
-    tridiag_eig_F<dfl, NWP>(n, cv, a.m.mu, a.m.T, false, nullptr, ssp, sfe, K);
+    tridiag_eig_F<dfl, NWP>(n, cv, a.m.mu - a.m.e0, a.m.T, false, nullptr, ssp, sfe, K);
     if (threadIdx.x == 0) {
-        a.Fbuf[2 * c + var] = -a.m.T * ssp;
+        a.Fbuf[2 * c + var] = -a.m.T * ssp + (a.m.ucl != 0.0 ? a.Fbuf[2 * c + var] : 0.0);
         a.fillbuf[2 * c + var] = sfe;
         __threadfence();
         *s_last = (atomicAdd(&a.ticket[c], 1) == 1);
@@ -554,7 +560,7 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, 
     double sn[3];
     const double* so = v.S_in + 3 * site;
     if (var == 1) { sn[0] = s_new[0]; sn[1] = s_new[1]; sn[2] = s_new[2]; }
-    else propose_spin(a.m.seed, v.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, so, sn);
+    else propose(a.m, v.sweep, (uint32_t)site, so, sn);
     double u0, u1;
     uniform2(a.m.seed, v.sweep, (uint32_t)site, RNG_ACCEPT, u0, u1);
     const double lnu = log(u0);

@@ -290,7 +290,7 @@ __global__ void k_screen_rows(StageArgs a, float* __restrict__ X) {
     const int site = a.sites[c];
     const Window w = make_window(a.m, site);
     if (threadIdx.x == 0) {
-        propose_spin(a.m.seed, a.sweep, (uint32_t)site, a.m.proposal, a.m.cone_cos, a.S_in + 3 * site, sn);
+        propose(a.m, a.sweep, (uint32_t)site, a.S_in + 3 * site, sn);
         center = patch_features(a.m, w, a.S_in, f);
         f[147] = (float)sn[0]; f[148] = (float)sn[1]; f[149] = (float)sn[2];
     }

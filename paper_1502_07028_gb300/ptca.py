@@ -23,6 +23,7 @@ SCHEDULE_TILED, SCHEDULE_BLOCK = 0, 1
 PIPELINE_STAGES, PIPELINE_PERSISTENT, PIPELINE_GRAPH, PIPELINE_OVERLAP = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 PROPOSAL_SPHERE, PROPOSAL_CONE = 0, 1
+MODEL_DOUBLE_EXCHANGE, MODEL_HUBBARD_MF = 0, 1
 
 EXPORTED = [
     "ptca_init", "ptca_destroy", "ptca_set_T", "ptca_set_mu", "ptca_get_spins", "ptca_set_spins",
@@ -56,8 +57,8 @@ class Params(ctypes.Structure):
         ("t", ctypes.c_double), ("J_H", ctypes.c_double), ("mu", ctypes.c_double), ("T", ctypes.c_double),
         ("L_c", ctypes.c_int32), ("cluster_periodic", ctypes.c_int32), ("update_offset", ctypes.c_int32),
         ("schedule", ctypes.c_int32), ("stride", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("proposal", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("cone_deg", ctypes.c_double),
-        ("seed", ctypes.c_uint64),
+        ("proposal", ctypes.c_int32), ("model", ctypes.c_int32), ("cone_deg", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("U", ctypes.c_double), ("m_step", ctypes.c_double),
     ]
 
 
@@ -185,13 +186,17 @@ class Config:
     proposal: int = PROPOSAL_SPHERE
     cone_deg: float = 30.0
     seed: int = 0
+    model: int = MODEL_DOUBLE_EXCHANGE
+    U: float = 8.0
+    m_step: float = 0.5
 
     def lattice(self) -> Lattice:
         return Lattice(self.Lx, self.Ly, self.periodic)
 
     def params(self) -> Params:
         return Params(self.t, self.J_H, self.mu, self.T, self.L_c, self.cluster_periodic, self.update_offset,
-                      self.schedule, self.stride, self.precision, self.proposal, 0, self.cone_deg, self.seed)
+                      self.schedule, self.stride, self.precision, self.proposal, self.model, self.cone_deg,
+                      self.seed, self.U, self.m_step)
 
     @property
     def N(self) -> int:

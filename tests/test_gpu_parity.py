@@ -37,7 +37,8 @@ def _oracle_model(cfg: P.Config) -> oracle.Model:
     return oracle.Model(Lx=cfg.Lx, Ly=cfg.Ly, Lc=cfg.L_c, t=cfg.t, JH=cfg.J_H, mu=cfg.mu, T=cfg.T,
                         lattice_periodic=cfg.periodic, cluster_periodic=cfg.cluster_periodic,
                         schedule=cfg.schedule, stride=cfg.stride, proposal=cfg.proposal,
-                        cone_deg=cfg.cone_deg, seed=cfg.seed, ox=cfg.update_offset, oy=cfg.update_offset)
+                        cone_deg=cfg.cone_deg, seed=cfg.seed, ox=cfg.update_offset, oy=cfg.update_offset,
+                        model=cfg.model, U=cfg.U, m_step=cfg.m_step)
 
 
 def _unpack(packed: np.ndarray, n: int) -> np.ndarray:
@@ -197,10 +198,12 @@ def _replay(cfg, S0, stages, site, acc, sweep_index):
     return starts, S
 
 
-def _check_sweep_against_oracle(cfg, sweeps, sample=None, seed_spins=None):
+def _check_sweep_against_oracle(cfg, sweeps, sample=None, seed_spins=None, start=None):
     ctx = P.Context(cfg)
     if seed_spins is not None:
         ctx.set_spins(inputs.random_unit_spins(seed_spins, cfg.N))
+    if start is not None:
+        ctx.set_spins(start)
     m = _oracle_model(cfg)
     stages = P.ptca_schedule(cfg)
     flat = np.concatenate(stages)
