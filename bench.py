@@ -322,6 +322,36 @@ def uneven_mode(P, args, flush, stream, rank):
             "workload": "316x316 open, 10x10 clipped clusters (n=50..200), J_H=6, mu=-4.5, T=0.1, tiled s=10"}
 
 
+def hubbard_mode(P, args, flush, stream, rank):
+    """The paper's own benchmark model (Eq. 1, Hubbard mean field, <n> = 1) on
+    its two-dimensional workload shape (Fig. 6(c,d)): 256x256 torus, 4x4
+    traveling clusters (n = 32), U = 8, half filling (mu = U/2), T = 0.1,
+    field steps uniform in a ball of radius 0.5, block schedule.  Mixed
+    precision with the guard (autotuned launch) and the plain FP64 path."""
+    base = dict(Lx=256, Ly=256, L_c=4, periodic=1, t=1.0, U=8.0, mu=4.0, T=0.1, seed=rank, m_step=0.5,
+                model=P.MODEL_HUBBARD_MF, schedule=P.SCHEDULE_BLOCK)
+    N = 256 * 256
+    out = {"workload": "Hubbard mean field (Eq. 1), 256x256 torus, 4x4 clusters (n=32), U=8, mu=U/2, T=0.1, "
+                       "ball steps of radius 0.5, block schedule"}
+    ctx = P.Context(P.Config(**base, precision=P.MIXED))
+    best, _ = P.ptca_autotune(ctx.h, 2)
+    steps = max(3, args.steps // 2)
+    ms = time_sweeps(ctx, steps, 2, flush, stream)
+    st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
+    obs = P.ptca_observables(ctx.h, stream=stream)
+    ctx.close()
+    out.update({"value": N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
+                "resolved_fraction": st.resolved / st.attempts, "acceptance": st.accepted / st.attempts,
+                "S_pipi": obs.S_pipi,
+                "launch": {"pipeline": best.pipeline, "warps_per_cta": best.warps_per_cta,
+                           "ctas_per_sm": best.ctas_per_sm}})
+    ctx = P.Context(P.Config(**base, precision=P.FP64))
+    ms64 = time_sweeps(ctx, 2, 1, flush, stream)
+    ctx.close()
+    out["fp64_path"] = {"value": N * 2 / (sum(ms64) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms64) / 2}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,7 +363,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sg-sweeps", type=int, default=20, help="exact sweeps collected to train the surrogate")
     ap.add_argument("--sg-train-steps", type=int, default=3000)
-    ap.add_argument("--no-extra", action="store_true", help="skip the surrogate and uneven-batch measurements")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the surrogate, uneven-batch and Hubbard-model measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -420,6 +451,7 @@ def main():
     if not args.no_extra:
         extra["surrogate_da"] = surrogate_mode(P, base, args, flush, stream)
         extra["uneven_open"] = uneven_mode(P, args, flush, stream, rank)
+        extra["hubbard_mf"] = hubbard_mode(P, args, flush, stream, rank)
 
     # --- plain FP64 GPU path on the same workload
     ctx64 = P.Context(P.Config(**base, precision=P.FP64))

@@ -29,6 +29,10 @@ def main(argv=None):
     ap.add_argument("--mu", type=float, default=-6.5)
     ap.add_argument("--JH", type=float, default=8.0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--model", choices=["de", "hubbard"], default="de",
+                    help="double exchange, or the Hubbard mean-field model of Eq. 1")
+    ap.add_argument("--U", type=float, default=8.0, help="Hubbard U (model hubbard)")
+    ap.add_argument("--m-step", type=float, default=0.5, help="field proposal radius (model hubbard)")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import paper_1502_07028_gb300 as P
@@ -37,7 +41,9 @@ def main(argv=None):
     _build.build()
     cfg = P.Config(Lx=a.L, Ly=a.L, L_c=a.Lc, periodic=0 if a.open else 1, J_H=a.JH, mu=a.mu, T=a.T, seed=a.seed,
                    schedule=P.SCHEDULE_BLOCK if a.schedule == "block" else P.SCHEDULE_TILED, stride=a.stride,
-                   precision=P.MIXED if a.precision == "mixed" else P.FP64, proposal=P.PROPOSAL_CONE, cone_deg=30.0)
+                   precision=P.MIXED if a.precision == "mixed" else P.FP64, proposal=P.PROPOSAL_CONE, cone_deg=30.0,
+                   model=P.MODEL_HUBBARD_MF if a.model == "hubbard" else P.MODEL_DOUBLE_EXCHANGE, U=a.U,
+                   m_step=a.m_step)
     ctx = P.Context(cfg)
     P.ptca_set_launch_config(ctx.h, {"stages": P.PIPELINE_STAGES, "persistent": P.PIPELINE_PERSISTENT,
                                      "graph": P.PIPELINE_GRAPH, "overlap": P.PIPELINE_OVERLAP}[a.pipeline], a.warps, a.ctas_per_sm)
