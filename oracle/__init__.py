@@ -74,6 +74,7 @@ class _Model(ctypes.Structure):
         ("cone_deg", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("model", ctypes.c_int32), ("pad0", ctypes.c_int32),
         ("U", ctypes.c_double), ("m_step", ctypes.c_double),
+        ("Lz", ctypes.c_int32), ("oz", ctypes.c_int32),
     ]
 
 
@@ -101,24 +102,28 @@ class Model:
     model: int = MODEL_DOUBLE_EXCHANGE
     U: float = 8.0
     m_step: float = 0.5
+    Lz: int = 1
+    oz: int = -1
 
     def _c(self) -> _Model:
         off = (self.Lc // 2) if self.schedule == SCHEDULE_TILED else 0
         ox = off if self.ox < 0 else self.ox
         oy = (off if self.oy < 0 else self.oy) if self.Ly > 1 else 0
+        oz = (off if self.oz < 0 else self.oz) if self.Lz > 1 else 0
         cp = self.lattice_periodic if self.cluster_periodic < 0 else self.cluster_periodic
         stride = self.stride if self.stride > 0 else self.Lc
         return _Model(self.Lx, self.Ly, self.lattice_periodic, self.Lc, ox, oy, cp,
                       self.schedule, stride, self.proposal, self.t, self.JH,
-                      self.mu, self.T, self.cone_deg, self.seed, self.model, 0, self.U, self.m_step)
+                      self.mu, self.T, self.cone_deg, self.seed, self.model, 0, self.U, self.m_step,
+                      self.Lz, oz)
 
     @property
     def N(self) -> int:
-        return self.Lx * self.Ly
+        return self.Lx * self.Ly * self.Lz
 
     @property
     def nmax(self) -> int:
-        return 2 * self.Lc * (1 if self.Ly == 1 else self.Lc)
+        return 2 * self.Lc ** (1 + (self.Ly > 1) + (self.Lz > 1))
 
 
 def lib():
@@ -153,6 +158,8 @@ def lib():
             _lib.oracle_cluster_free_energy.restype = d
             _lib.oracle_structure_factor.argtypes = [ctypes.c_int, ctypes.c_int, P(d), d, d]
             _lib.oracle_structure_factor.restype = d
+            _lib.oracle_structure_factor3.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P(d), d, d, d]
+            _lib.oracle_structure_factor3.restype = d
         return _lib
 
 
@@ -281,6 +288,6 @@ def single_site_chain(m: Model, S, site: int, sweep0: int, steps: int):
     return trace, nacc
 
 
-def structure_factor(Lx: int, Ly: int, S, qx: float, qy: float) -> float:
+def structure_factor(Lx: int, Ly: int, S, qx: float, qy: float, Lz: int = 1, qz: float = 0.0) -> float:
     S = np.ascontiguousarray(S, dtype=np.float64)
-    return lib().oracle_structure_factor(Lx, Ly, _p(S, ctypes.c_double), qx, qy)
+    return lib().oracle_structure_factor3(Lx, Ly, Lz, _p(S, ctypes.c_double), qx, qy, qz)

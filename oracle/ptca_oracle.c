@@ -44,6 +44,7 @@ static const double PI = 3.14159265358979323846;
  * ctypes wrapper in oracle/__init__.py and by nothing else. */
 typedef struct {
     int32_t Lx, Ly;            /* lattice extents; Ly == 1 means a 1-D chain      */
+                               /* (Lz, the third extent, is the last field)       */
     int32_t lattice_periodic;  /* 1: torus, 0: open edges                         */
     int32_t Lc;                /* linear cluster size L_c (N_c = L_c^2 in 2-D)    */
     int32_t ox, oy;            /* position of the update site inside the window  */
@@ -58,7 +59,19 @@ typedef struct {
     int32_t pad0;
     double U;                  /* model 1: Hubbard U                             */
     double m_step;             /* model 1: radius of the proposal ball           */
+    int32_t Lz;                /* third extent; 1 for a square lattice or chain  */
+    int32_t oz;                /* update-site position along z                    */
 } oracle_model;
+
+/* Sites: index (z Ly + y) Lx + x.  Lz > 1 needs Ly > 1 (cubic lattice). */
+static int n_sites(const oracle_model* m) { return m->Lx * m->Ly * m->Lz; }
+static int cluster_dim(const oracle_model* m) { return 1 + (m->Ly > 1) + (m->Lz > 1); }
+static int n_max(const oracle_model* m)
+{
+    int ns = 1;
+    for (int d = 0; d < cluster_dim(m); ++d) ns *= m->Lc;
+    return 2 * ns;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
@@ -118,7 +131,7 @@ static void sphere_point(const double u[2], double s[3])
 /* Initial classical spins: independent, uniform on the sphere. */
 void oracle_init_spins(const oracle_model* m, double* S)
 {
-    int N = m->Lx * m->Ly;
+    int N = n_sites(m);
     for (int i = 0; i < N; ++i) {
         double u[2];
         oracle_uniform2(m->seed, 0, (uint32_t)i, PURPOSE_INIT, u);
@@ -191,34 +204,47 @@ static void window_axis(int L, int periodic, int Lc, int o, int c, int* start, i
     *start = a; *ext = b - a + 1;
 }
 
-/* Lattice site at window coordinates (wx, wy). */
-static int window_site(const oracle_model* m, int x0, int y0, int wx, int wy)
+/* The window of an update site: start and extent along each axis. */
+typedef struct { int x0, y0, z0, ex, ey, ez; } window;
+
+static window window_of(const oracle_model* m, int site)
 {
-    int x = x0 + wx, y = y0 + wy;
-    if (m->lattice_periodic) { x %= m->Lx; y %= m->Ly; }
-    return y * m->Lx + x;
+    window w;
+    int cx = site % m->Lx, cy = (site / m->Lx) % m->Ly, cz = site / (m->Lx * m->Ly);
+    window_axis(m->Lx, m->lattice_periodic, m->Lc, m->ox, cx, &w.x0, &w.ex);
+    window_axis(m->Ly, m->lattice_periodic, m->Lc, m->oy, cy, &w.y0, &w.ey);
+    window_axis(m->Lz, m->lattice_periodic, m->Lc, m->oz, cz, &w.z0, &w.ez);
+    return w;
+}
+
+/* Lattice site at window coordinates (wx, wy, wz). */
+static int window_site(const oracle_model* m, const window* w, int wx, int wy, int wz)
+{
+    int x = w->x0 + wx, y = w->y0 + wy, z = w->z0 + wz;
+    if (m->lattice_periodic) { x %= m->Lx; y %= m->Ly; z %= m->Lz; }
+    return (z * m->Ly + y) * m->Lx + x;
 }
 
 /* Dense cluster Hamiltonian H_clus{C[i_s]} (Sec. II.c step b) for update site
- * `site`.  Basis index 2*(wy*ex + wx) + spin.  Spin of the update site is
- * replaced by s_new when s_new != NULL (step d).  Returns n = 2*ex*ey and
- * writes H (n*n complex, row-major) and the window extents.  The cluster
- * boundary is periodic inside the window when m->cluster_periodic (Sec. II.b:
- * periodic boundary conditions on the cluster); an axis of extent 2 then has
- * two bonds between its two sites, an axis of extent 1 has none. */
+ * `site`.  Basis index 2*((wz*ey + wy)*ex + wx) + spin.  Spin of the update
+ * site is replaced by s_new when s_new != NULL (step d).  Returns
+ * n = 2*ex*ey*ez and writes H (n*n complex, row-major) and the window extents
+ * along x and y.  The cluster boundary is periodic inside the window when
+ * m->cluster_periodic (Sec. II.b: periodic boundary conditions on the
+ * cluster); an axis of extent 2 then has two bonds between its two sites, an
+ * axis of extent 1 has none. */
 int oracle_cluster_hamiltonian(const oracle_model* m, const double* S, int site,
                                const double* s_new, cplx* H, int* ex_out, int* ey_out)
 {
-    int cx = site % m->Lx, cy = site / m->Lx;
-    int x0, y0, ex, ey;
-    window_axis(m->Lx, m->lattice_periodic, m->Lc, m->ox, cx, &x0, &ex);
-    window_axis(m->Ly, m->lattice_periodic, m->Lc, m->oy, cy, &y0, &ey);
-    int nsite = ex * ey, n = 2 * nsite;
+    window win = window_of(m, site);
+    int ex = win.ex, ey = win.ey, ez = win.ez;
+    int nsite = ex * ey * ez, n = 2 * nsite;
     memset(H, 0, sizeof(cplx) * (size_t)n * (size_t)n);
+    for (int wz = 0; wz < ez; ++wz)
     for (int wy = 0; wy < ey; ++wy) {
         for (int wx = 0; wx < ex; ++wx) {
-            int w = wy * ex + wx;
-            int g = window_site(m, x0, y0, wx, wy);
+            int w = (wz * ey + wy) * ex + wx;
+            int g = window_site(m, &win, wx, wy, wz);
             const double* s = S + 3 * g;
             if (s_new && g == site) s = s_new;
             /* On-site 2x2 spin block: -J_H S.sigma (model 0), or
@@ -230,13 +256,15 @@ int oracle_cluster_hamiltonian(const oracle_model* m, const double* S, int site,
             H[b * n + b] += e0 + J * s[2];
             H[a * n + b] += -J * (s[0] - I * s[1]);
             H[b * n + a] += -J * (s[0] + I * s[1]);
-            /* Hopping -t to the +x and +y neighbours (each bond once). */
-            int nb[2] = {-1, -1};
-            if (wx + 1 < ex) nb[0] = wy * ex + (wx + 1);
-            else if (m->cluster_periodic && ex >= 2) nb[0] = wy * ex + 0;
-            if (wy + 1 < ey) nb[1] = (wy + 1) * ex + wx;
-            else if (m->cluster_periodic && ey >= 2) nb[1] = 0 * ex + wx;
-            for (int d = 0; d < 2; ++d) {
+            /* Hopping -t to the +x, +y and +z neighbours (each bond once). */
+            int nb[3] = {-1, -1, -1};
+            if (wx + 1 < ex) nb[0] = (wz * ey + wy) * ex + (wx + 1);
+            else if (m->cluster_periodic && ex >= 2) nb[0] = (wz * ey + wy) * ex + 0;
+            if (wy + 1 < ey) nb[1] = (wz * ey + wy + 1) * ex + wx;
+            else if (m->cluster_periodic && ey >= 2) nb[1] = (wz * ey + 0) * ex + wx;
+            if (wz + 1 < ez) nb[2] = ((wz + 1) * ey + wy) * ex + wx;
+            else if (m->cluster_periodic && ez >= 2) nb[2] = (0 * ey + wy) * ex + wx;
+            for (int d = 0; d < 3; ++d) {
                 if (nb[d] < 0) continue;
                 for (int sp = 0; sp < 2; ++sp) {
                     int i = 2 * w + sp, j = 2 * nb[d] + sp;
@@ -332,14 +360,12 @@ double oracle_free_energy(int n, const double* eig, double mu, double T)
 static double window_classical(const oracle_model* m, const double* S, int site, const double* s_new)
 {
     if (m->model != 1) return 0.0;
-    int cx = site % m->Lx, cy = site / m->Lx;
-    int x0, y0, ex, ey;
-    window_axis(m->Lx, m->lattice_periodic, m->Lc, m->ox, cx, &x0, &ex);
-    window_axis(m->Ly, m->lattice_periodic, m->Lc, m->oy, cy, &y0, &ey);
+    window win = window_of(m, site);
     double acc = 0.0;
-    for (int wy = 0; wy < ey; ++wy)
-        for (int wx = 0; wx < ex; ++wx) {
-            int g = window_site(m, x0, y0, wx, wy);
+    for (int wz = 0; wz < win.ez; ++wz)
+    for (int wy = 0; wy < win.ey; ++wy)
+        for (int wx = 0; wx < win.ex; ++wx) {
+            int g = window_site(m, &win, wx, wy, wz);
             const double* v = (s_new && g == site) ? s_new : S + 3 * g;
             acc += 0.25 * m->U * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] - 1.0);
         }
@@ -361,37 +387,42 @@ static double cluster_F(const oracle_model* m, const double* S, int site, const 
 /* ------------------------------------------------------------------------ */
 /* Schedules (Sec. III.a).  A schedule is an ordered list of stages; each    */
 /* stage lists update sites.  Flattened, every site appears exactly once.    */
-/*   tiled: stage (ax, ay) holds the sites (ax + s p, ay + s q), row-major;   */
-/*          stages in row-major order of (ax, ay).                            */
+/*   tiled: stage (ax, ay, az) holds the sites (ax + s p, ay + s q, az + s r), */
+/*          row-major; stages in row-major order of (ax, ay, az).             */
 /*   block: the lattice is cut in two along each axis (2^d blocks, Sec.     */
-/*          III.a, "four blocks" in two dimensions); a stage is one block,    */
-/*          its sites in row-major order; blocks in row-major order.          */
+/*          III.a, "four blocks" in two dimensions, eight in three); a stage  */
+/*          is one block, its sites in row-major order; blocks row-major.     */
 /* Writes stage_start[nstages+1] and sites[N]; returns nstages.               */
 /* ------------------------------------------------------------------------ */
 int oracle_schedule(const oracle_model* m, int32_t* stage_start, int32_t* sites)
 {
-    int Lx = m->Lx, Ly = m->Ly, ns = 0, pos = 0;
+    int Lx = m->Lx, Ly = m->Ly, Lz = m->Lz, ns = 0, pos = 0;
     stage_start[0] = 0;
     if (m->schedule == 0) {
         int s = m->stride;
-        int sy = (Ly == 1) ? 1 : s;
-        for (int ay = 0; ay < sy && ay < Ly; ++ay)
-            for (int ax = 0; ax < s && ax < Lx; ++ax) {
-                for (int y = ay; y < Ly; y += sy)
-                    for (int x = ax; x < Lx; x += s) sites[pos++] = y * Lx + x;
-                stage_start[++ns] = pos;
-            }
+        int sy = (Ly == 1) ? 1 : s, sz = (Lz == 1) ? 1 : s;
+        for (int az = 0; az < sz && az < Lz; ++az)
+            for (int ay = 0; ay < sy && ay < Ly; ++ay)
+                for (int ax = 0; ax < s && ax < Lx; ++ax) {
+                    for (int z = az; z < Lz; z += sz)
+                        for (int y = ay; y < Ly; y += sy)
+                            for (int x = ax; x < Lx; x += s) sites[pos++] = (z * Ly + y) * Lx + x;
+                    stage_start[++ns] = pos;
+                }
     } else {
-        int hx = (Lx + 1) / 2, hy = (Ly + 1) / 2;
-        int nby = (Ly == 1) ? 1 : 2;
-        for (int by = 0; by < nby; ++by)
-            for (int bx = 0; bx < 2; ++bx) {
-                int xa = bx ? hx : 0, xb = bx ? Lx : hx;
-                int ya = (Ly == 1) ? 0 : (by ? hy : 0), yb = (Ly == 1) ? 1 : (by ? Ly : hy);
-                for (int y = ya; y < yb; ++y)
-                    for (int x = xa; x < xb; ++x) sites[pos++] = y * Lx + x;
-                if (pos > stage_start[ns]) stage_start[++ns] = pos;
-            }
+        int hx = (Lx + 1) / 2, hy = (Ly + 1) / 2, hz = (Lz + 1) / 2;
+        int nby = (Ly == 1) ? 1 : 2, nbz = (Lz == 1) ? 1 : 2;
+        for (int bz = 0; bz < nbz; ++bz)
+            for (int by = 0; by < nby; ++by)
+                for (int bx = 0; bx < 2; ++bx) {
+                    int xa = bx ? hx : 0, xb = bx ? Lx : hx;
+                    int ya = (Ly == 1) ? 0 : (by ? hy : 0), yb = (Ly == 1) ? 1 : (by ? Ly : hy);
+                    int za = (Lz == 1) ? 0 : (bz ? hz : 0), zb = (Lz == 1) ? 1 : (bz ? Lz : hz);
+                    for (int z = za; z < zb; ++z)
+                        for (int y = ya; y < yb; ++y)
+                            for (int x = xa; x < xb; ++x) sites[pos++] = (z * Ly + y) * Lx + x;
+                    if (pos > stage_start[ns]) stage_start[++ns] = pos;
+                }
     }
     return ns;
 }
@@ -399,13 +430,11 @@ int oracle_schedule(const oracle_model* m, int32_t* stage_start, int32_t* sites)
 /* Window membership: is lattice site g inside the window of update site c? */
 int oracle_in_window(const oracle_model* m, int c, int g)
 {
-    int cx = c % m->Lx, cy = c / m->Lx;
-    int x0, y0, ex, ey;
-    window_axis(m->Lx, m->lattice_periodic, m->Lc, m->ox, cx, &x0, &ex);
-    window_axis(m->Ly, m->lattice_periodic, m->Lc, m->oy, cy, &y0, &ey);
-    for (int wy = 0; wy < ey; ++wy)
-        for (int wx = 0; wx < ex; ++wx)
-            if (window_site(m, x0, y0, wx, wy) == g) return 1;
+    window win = window_of(m, c);
+    for (int wz = 0; wz < win.ez; ++wz)
+        for (int wy = 0; wy < win.ey; ++wy)
+            for (int wx = 0; wx < win.ex; ++wx)
+                if (window_site(m, &win, wx, wy, wz) == g) return 1;
     return 0;
 }
 
@@ -424,8 +453,8 @@ int oracle_sweep(const oracle_model* m, double* S, uint64_t sweep,
                  int32_t* rec_site, double* rec_Fold, double* rec_Fnew,
                  double* rec_lnu, uint8_t* rec_acc)
 {
-    int N = m->Lx * m->Ly;
-    int nmax = 2 * m->Lc * ((m->Ly == 1) ? 1 : m->Lc);
+    int N = n_sites(m);
+    int nmax = n_max(m);
     int32_t* stage_start = malloc(sizeof(int32_t) * (size_t)(N + 1));
     int32_t* sites = malloc(sizeof(int32_t) * (size_t)N);
     cplx* H = malloc(sizeof(cplx) * (size_t)nmax * (size_t)nmax);
@@ -471,7 +500,7 @@ int oracle_sweep(const oracle_model* m, double* S, uint64_t sweep,
 int oracle_single_site_chain(const oracle_model* m, double* S, int site, uint64_t sweep0,
                              int steps, double* trace)
 {
-    int nmax = 2 * m->Lc * ((m->Ly == 1) ? 1 : m->Lc);
+    int nmax = n_max(m);
     cplx* H = malloc(sizeof(cplx) * (size_t)nmax * (size_t)nmax);
     double* e = malloc(sizeof(double) * (size_t)nmax);
     if (!H || !e) { free(H); free(e); return -1; }
@@ -497,7 +526,7 @@ int oracle_single_site_chain(const oracle_model* m, double* S, int site, uint64_
 /* Cluster free energy of the current state at one site (for tests). */
 double oracle_cluster_free_energy(const oracle_model* m, const double* S, int site, const double* s_new)
 {
-    int nmax = 2 * m->Lc * ((m->Ly == 1) ? 1 : m->Lc);
+    int nmax = n_max(m);
     cplx* H = malloc(sizeof(cplx) * (size_t)nmax * (size_t)nmax);
     double* e = malloc(sizeof(double) * (size_t)nmax);
     double F = NAN;
@@ -508,18 +537,23 @@ double oracle_cluster_free_energy(const oracle_model* m, const double* S, int si
 
 /* Magnetic structure factor of one configuration (Eq. 2 without the thermal
  * average): S(q) = (1/N^2) sum_{i,j} exp(i q.(r_i - r_j)) S_i . S_j, written
- * as the plain double sum. */
-double oracle_structure_factor(int Lx, int Ly, const double* S, double qx, double qy)
+ * as the plain double sum over an Lx x Ly x Lz lattice. */
+double oracle_structure_factor3(int Lx, int Ly, int Lz, const double* S, double qx, double qy, double qz)
 {
-    int N = Lx * Ly;
+    int N = Lx * Ly * Lz;
     double acc = 0.0;
     for (int i = 0; i < N; ++i) {
-        double xi = i % Lx, yi = i / Lx;
+        double xi = i % Lx, yi = (i / Lx) % Ly, zi = i / (Lx * Ly);
         for (int j = 0; j < N; ++j) {
-            double xj = j % Lx, yj = j / Lx;
+            double xj = j % Lx, yj = (j / Lx) % Ly, zj = j / (Lx * Ly);
             double dot = S[3 * i] * S[3 * j] + S[3 * i + 1] * S[3 * j + 1] + S[3 * i + 2] * S[3 * j + 2];
-            acc += cos(qx * (xi - xj) + qy * (yi - yj)) * dot;
+            acc += cos(qx * (xi - xj) + qy * (yi - yj) + qz * (zi - zj)) * dot;
         }
     }
     return acc / ((double)N * (double)N);
+}
+
+double oracle_structure_factor(int Lx, int Ly, const double* S, double qx, double qy)
+{
+    return oracle_structure_factor3(Lx, Ly, 1, S, qx, qy, 0.0);
 }
