@@ -322,20 +322,25 @@ def uneven_mode(P, args, flush, stream, rank):
             "workload": "316x316 open, 10x10 clipped clusters (n=50..200), J_H=6, mu=-4.5, T=0.1, tiled s=10"}
 
 
-def hubbard_mode(P, args, flush, stream, rank):
+def hubbard_mode(P, args, flush, stream, rank, Lz=1):
     """The paper's own benchmark model (Eq. 1, Hubbard mean field, <n> = 1) on
-    its two-dimensional workload shape (Fig. 6(c,d)): 256x256 torus, 4x4
-    traveling clusters (n = 32), U = 8, half filling (mu = U/2), T = 0.1,
-    field steps uniform in a ball of radius 0.5, block schedule.  Mixed
-    precision with the guard (autotuned launch) and the plain FP64 path."""
-    base = dict(Lx=256, Ly=256, L_c=4, periodic=1, t=1.0, U=8.0, mu=4.0, T=0.1, seed=rank, m_step=0.5,
+    its workload shapes: two dimensions (Fig. 6(c,d)), 256x256 torus with 4x4
+    traveling clusters (n = 32); three dimensions (Fig. 6(a,b)), 40^3 torus
+    with 4^3 clusters (n = 128) and eight blocks.  U = 8, half filling
+    (mu = U/2), field steps uniform in a ball of radius 0.5, block schedule.
+    Mixed precision with the guard (autotuned launch) and the plain FP64
+    path."""
+    L = 256 if Lz == 1 else 40
+    T = 0.1 if Lz == 1 else 0.15
+    base = dict(Lx=L, Ly=L, Lz=Lz, L_c=4, periodic=1, t=1.0, U=8.0, mu=4.0, T=T, seed=rank, m_step=0.5,
                 model=P.MODEL_HUBBARD_MF, schedule=P.SCHEDULE_BLOCK)
-    N = 256 * 256
-    out = {"workload": "Hubbard mean field (Eq. 1), 256x256 torus, 4x4 clusters (n=32), U=8, mu=U/2, T=0.1, "
-                       "ball steps of radius 0.5, block schedule"}
+    N = L * L * Lz
+    shape = f"{L}x{L} torus, 4x4 clusters (n=32)" if Lz == 1 else f"{L}^3 torus, 4^3 clusters (n=128), 8 blocks"
+    out = {"workload": f"Hubbard mean field (Eq. 1), {shape}, U=8, mu=U/2, T={T}, ball steps of radius 0.5, "
+                       "block schedule"}
     ctx = P.Context(P.Config(**base, precision=P.MIXED))
     best, _ = P.ptca_autotune(ctx.h, 2)
-    steps = max(3, args.steps // 2)
+    steps = max(3, args.steps // 2) if Lz == 1 else 3
     ms = time_sweeps(ctx, steps, 2, flush, stream)
     st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
     obs = P.ptca_observables(ctx.h, stream=stream)
@@ -346,9 +351,11 @@ def hubbard_mode(P, args, flush, stream, rank):
                 "launch": {"pipeline": best.pipeline, "warps_per_cta": best.warps_per_cta,
                            "ctas_per_sm": best.ctas_per_sm}})
     ctx = P.Context(P.Config(**base, precision=P.FP64))
-    ms64 = time_sweeps(ctx, 2, 1, flush, stream)
+    n64 = 2 if Lz == 1 else 1
+    ms64 = time_sweeps(ctx, n64, 1, flush, stream)
     ctx.close()
-    out["fp64_path"] = {"value": N * 2 / (sum(ms64) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms64) / 2}
+    out["fp64_path"] = {"value": N * n64 / (sum(ms64) * 1e-3), "unit": "spin-updates/s",
+                        "ms_per_step": sum(ms64) / n64}
     return out
 
 
@@ -452,6 +459,7 @@ def main():
         extra["surrogate_da"] = surrogate_mode(P, base, args, flush, stream)
         extra["uneven_open"] = uneven_mode(P, args, flush, stream, rank)
         extra["hubbard_mf"] = hubbard_mode(P, args, flush, stream, rank)
+        extra["hubbard_mf_3d"] = hubbard_mode(P, args, flush, stream, rank, Lz=40)
 
     # --- plain FP64 GPU path on the same workload
     ctx64 = P.Context(P.Config(**base, precision=P.FP64))

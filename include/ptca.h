@@ -63,10 +63,14 @@ enum { PTCA_PROPOSAL_SPHERE = 0, PTCA_PROPOSAL_CONE = 1 };
 enum { PTCA_MODEL_DOUBLE_EXCHANGE = 0, PTCA_MODEL_HUBBARD_MF = 1 };
 enum { PTCA_PIPELINE_STAGES = 0, PTCA_PIPELINE_PERSISTENT = 1, PTCA_PIPELINE_GRAPH = 2, PTCA_PIPELINE_OVERLAP = 3 };
 
-/* Square lattice.  Ly == 1 is a one-dimensional chain (Sec. III.a, Fig. 3). */
+/* Square lattice, chain or cubic lattice.  Ly == 1 is a one-dimensional chain
+ * (Sec. III.a, Fig. 3); Lz > 1 (with Ly > 1) a cubic lattice of Lx*Ly*Lz
+ * sites, index (z*Ly + y)*Lx + x, with L_c^3 traveling clusters and 2^3 blocks
+ * (Sec. III.a, IV).  Lz of 0 or 1 means a square lattice or chain. */
 typedef struct {
     int32_t Lx, Ly;
     int32_t periodic; /* 1: torus; 0: open edges (windows are clipped at the edges) */
+    int32_t Lz;
 } ptca_lattice;
 
 /* Problem parameters.  Two models share the lattice, the hopping -t and the
@@ -85,7 +89,7 @@ typedef struct {
     double J_H;               /* Hund coupling (double exchange)                      */
     double mu;                /* chemical potential                                   */
     double T;                 /* temperature (> 0)                                    */
-    int32_t L_c;              /* linear cluster size, 2 <= L_c <= min(Lx, Ly)         */
+    int32_t L_c;              /* linear cluster size, 2 <= L_c <= every extent > 1    */
     int32_t cluster_periodic; /* -1: same as the lattice; 1: wrap inside the window   */
                               /* (Sec. II.b); 0: open cluster                         */
     int32_t update_offset;    /* position of the update site inside the window along  */
@@ -118,8 +122,8 @@ typedef struct {
 
 /* Observables of the current configuration (ptca_observables). */
 typedef struct {
-    double S_00;        /* S(q) at q = (0,0), Eq. 2 for one configuration              */
-    double S_pipi;      /* S(q) at q = (pi,pi)                                          */
+    double S_00;        /* S(q) at q = 0, Eq. 2 for one configuration                  */
+    double S_pipi;      /* S(q) at q = (pi,pi), or (pi,pi,pi) on a cubic lattice        */
     double F_site;      /* last sweep: mean over solved visits of F of the accepted      */
                         /* state / N_c                                                 */
     double acceptance;  /* last sweep: accepted / attempts                              */

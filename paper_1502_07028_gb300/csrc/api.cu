@@ -46,31 +46,65 @@ void window_axis(int L, int periodic, int Lc, int o, int c, int& start, int& ext
     start = a; ext = b - a + 1;
 }
 
-// Stage lists.  Tiled: stage (ax, ay) holds (ax + s p, ay + s q), row-major;
-// block: the lattice halved along each axis, 2^d blocks (Sec. III.a), each
-// block one stage, row-major inside.
+// Window of an update site on the host (the device's make_window): start and
+// extent along each axis.  Sites are indexed (z Ly + y) Lx + x.
+struct HostWindow { int x0, y0, z0, ex, ey, ez; };
+
+HostWindow host_window(const Problem& p, int site) {
+    HostWindow w;
+    window_axis(p.Lx, p.periodic, p.Lc, p.ox, site % p.Lx, w.x0, w.ex);
+    window_axis(p.Ly, p.periodic, p.Lc, p.oy, (site / p.Lx) % p.Ly, w.y0, w.ey);
+    window_axis(p.Lz, p.periodic, p.Lc, p.oz, site / (p.Lx * p.Ly), w.z0, w.ez);
+    return w;
+}
+
+// Calls f(g) for every lattice site g of the window of `site`; stops and
+// returns true as soon as f returns true.
+template <typename F> bool any_window_site(const Problem& p, int site, F f) {
+    const HostWindow w = host_window(p, site);
+    for (int wz = 0; wz < w.ez; ++wz)
+        for (int wy = 0; wy < w.ey; ++wy)
+            for (int wx = 0; wx < w.ex; ++wx) {
+                int x = w.x0 + wx, y = w.y0 + wy, z = w.z0 + wz;
+                if (p.periodic) { x %= p.Lx; y %= p.Ly; z %= p.Lz; }
+                if (f((z * p.Ly + y) * p.Lx + x)) return true;
+            }
+    return false;
+}
+
+// Stage lists.  Tiled: stage (ax, ay, az) holds (ax + s p, ay + s q, az + s r),
+// row-major; block: the lattice halved along each axis of extent > 1, 2^d
+// blocks (Sec. III.a: four in two dimensions, eight in three), each block one
+// stage, row-major inside.
 void make_schedule(const Problem& p, std::vector<int32_t>& start, std::vector<int32_t>& sites) {
     start.assign(1, 0);
     sites.clear();
     sites.reserve(p.N());
+    auto idx = [&](int x, int y, int z) { return (int32_t)((z * p.Ly + y) * p.Lx + x); };
     if (p.schedule == PTCA_SCHEDULE_TILED) {
-        const int s = p.stride, sy = p.Ly == 1 ? 1 : s;
-        for (int ay = 0; ay < sy && ay < p.Ly; ++ay)
-            for (int ax = 0; ax < s && ax < p.Lx; ++ax) {
-                for (int y = ay; y < p.Ly; y += sy)
-                    for (int x = ax; x < p.Lx; x += s) sites.push_back(y * p.Lx + x);
-                start.push_back((int32_t)sites.size());
-            }
+        const int s = p.stride, sy = p.Ly == 1 ? 1 : s, sz = p.Lz == 1 ? 1 : s;
+        for (int az = 0; az < sz && az < p.Lz; ++az)
+            for (int ay = 0; ay < sy && ay < p.Ly; ++ay)
+                for (int ax = 0; ax < s && ax < p.Lx; ++ax) {
+                    for (int z = az; z < p.Lz; z += sz)
+                        for (int y = ay; y < p.Ly; y += sy)
+                            for (int x = ax; x < p.Lx; x += s) sites.push_back(idx(x, y, z));
+                    start.push_back((int32_t)sites.size());
+                }
     } else {
-        const int hx = (p.Lx + 1) / 2, hy = (p.Ly + 1) / 2, nby = p.Ly == 1 ? 1 : 2;
-        for (int by = 0; by < nby; ++by)
-            for (int bx = 0; bx < 2; ++bx) {
-                const int xa = bx ? hx : 0, xb = bx ? p.Lx : hx;
-                const int ya = p.Ly == 1 ? 0 : (by ? hy : 0), yb = p.Ly == 1 ? 1 : (by ? p.Ly : hy);
-                for (int y = ya; y < yb; ++y)
-                    for (int x = xa; x < xb; ++x) sites.push_back(y * p.Lx + x);
-                if ((int32_t)sites.size() > start.back()) start.push_back((int32_t)sites.size());
-            }
+        const int hx = (p.Lx + 1) / 2, hy = (p.Ly + 1) / 2, hz = (p.Lz + 1) / 2;
+        const int nby = p.Ly == 1 ? 1 : 2, nbz = p.Lz == 1 ? 1 : 2;
+        for (int bz = 0; bz < nbz; ++bz)
+            for (int by = 0; by < nby; ++by)
+                for (int bx = 0; bx < 2; ++bx) {
+                    const int xa = bx ? hx : 0, xb = bx ? p.Lx : hx;
+                    const int ya = p.Ly == 1 ? 0 : (by ? hy : 0), yb = p.Ly == 1 ? 1 : (by ? p.Ly : hy);
+                    const int za = p.Lz == 1 ? 0 : (bz ? hz : 0), zb = p.Lz == 1 ? 1 : (bz ? p.Lz : hz);
+                    for (int z = za; z < zb; ++z)
+                        for (int y = ya; y < yb; ++y)
+                            for (int x = xa; x < xb; ++x) sites.push_back(idx(x, y, z));
+                    if ((int32_t)sites.size() > start.back()) start.push_back((int32_t)sites.size());
+                }
     }
 }
 
@@ -84,22 +118,18 @@ bool schedule_exact(const Problem& p, const std::vector<int32_t>& start, const s
     for (size_t s = 0; s + 1 < start.size(); ++s)
         for (int k = start[s]; k < start[s + 1]; ++k) { stage_of[sites[k]] = (int)s; pos[sites[k]] = k; }
     for (int k = 0; k < N; ++k) {
-        const int b = sites[k], cx = b % p.Lx, cy = b / p.Lx;
-        int x0, ex, y0, ey;
-        window_axis(p.Lx, p.periodic, p.Lc, p.ox, cx, x0, ex);
-        window_axis(p.Ly, p.periodic, p.Lc, p.oy, cy, y0, ey);
-        for (int wy = 0; wy < ey; ++wy)
-            for (int wx = 0; wx < ex; ++wx) {
-                int x = x0 + wx, y = y0 + wy;
-                if (p.periodic) { x %= p.Lx; y %= p.Ly; }
-                const int g = y * p.Lx + x;
-                if (g != b && stage_of[g] == stage_of[b] && pos[g] < pos[b]) {
-                    char buf[160];
-                    snprintf(buf, sizeof buf, "site %d lies in the window of site %d of the same stage", g, b);
-                    why = buf;
-                    return false;
-                }
-            }
+        const int b = sites[k];
+        int bad = -1;
+        any_window_site(p, b, [&](int g) {
+            if (g != b && stage_of[g] == stage_of[b] && pos[g] < pos[b]) { bad = g; return true; }
+            return false;
+        });
+        if (bad >= 0) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "site %d lies in the window of site %d of the same stage", bad, b);
+            why = buf;
+            return false;
+        }
     }
     return true;
 }
@@ -114,11 +144,8 @@ std::vector<int32_t> window_order(const Problem& p, const std::vector<int32_t>& 
         const int a0 = start[stg], a1 = start[stg + 1];
         std::vector<std::pair<int, int>> key;
         for (int k = a0; k < a1; ++k) {
-            const int b = sites[k];
-            int x0, ex, y0, ey;
-            window_axis(p.Lx, p.periodic, p.Lc, p.ox, b % p.Lx, x0, ex);
-            window_axis(p.Ly, p.periodic, p.Lc, p.oy, b / p.Lx, y0, ey);
-            key.push_back({-(ex * ey), k - a0});
+            const HostWindow w = host_window(p, sites[k]);
+            key.push_back({-(w.ex * w.ey * w.ez), k - a0});
         }
         std::stable_sort(key.begin(), key.end(),
                          [](const std::pair<int, int>& u, const std::pair<int, int>& v) { return u.first < v.first; });
@@ -144,16 +171,7 @@ void stage_split(const Problem& p, const std::vector<int32_t>& start, const std:
         std::vector<int32_t> a, b;
         for (int k = start[s]; k < start[s + 1]; ++k) {
             const int c = perm[k], site = sites[start[s] + c];
-            int x0, ex, y0, ey;
-            window_axis(p.Lx, p.periodic, p.Lc, p.ox, site % p.Lx, x0, ex);
-            window_axis(p.Ly, p.periodic, p.Lc, p.oy, site / p.Lx, y0, ey);
-            bool dep = false;
-            for (int wy = 0; wy < ey && !dep; ++wy)
-                for (int wx = 0; wx < ex && !dep; ++wx) {
-                    int x = x0 + wx, y = y0 + wy;
-                    if (p.periodic) { x %= p.Lx; y %= p.Ly; }
-                    dep = stage_of[y * p.Lx + x] == q;
-                }
+            const bool dep = any_window_site(p, site, [&](int g) { return stage_of[g] == q; });
             (dep ? b : a).push_back(c);
         }
         indep[s] = (int32_t)a.size();
@@ -165,11 +183,13 @@ void stage_split(const Problem& p, const std::vector<int32_t>& start, const std:
 ptca_status resolve(const ptca_lattice* lat, const ptca_params* par, Problem& p) {
     if (!lat || !par) return fail(PTCA_ERR_INVALID, "null lattice or params");
     p.Lx = lat->Lx; p.Ly = lat->Ly; p.periodic = lat->periodic ? 1 : 0;
-    if (p.Lx < 1 || p.Ly < 1 || (int64_t)p.Lx * p.Ly > (1 << 26))
+    p.Lz = lat->Lz == 0 ? 1 : lat->Lz;
+    if (p.Lx < 1 || p.Ly < 1 || p.Lz < 1 || (int64_t)p.Lx * p.Ly * p.Lz > (1 << 26))
         return fail(PTCA_ERR_INVALID, "lattice extents out of range");
+    if (p.Lz > 1 && p.Ly == 1) return fail(PTCA_ERR_INVALID, "a cubic lattice (Lz > 1) needs Ly > 1");
     p.Lc = par->L_c;
-    if (p.Lc < 2 || p.Lc > p.Lx || (p.Ly > 1 && p.Lc > p.Ly))
-        return fail(PTCA_ERR_INVALID, "L_c must satisfy 2 <= L_c <= min(Lx, Ly)");
+    if (p.Lc < 2 || p.Lc > p.Lx || (p.Ly > 1 && p.Lc > p.Ly) || (p.Lz > 1 && p.Lc > p.Lz))
+        return fail(PTCA_ERR_INVALID, "L_c must satisfy 2 <= L_c <= min(Lx, Ly, Lz)");
     p.schedule = par->schedule;
     if (p.schedule != PTCA_SCHEDULE_TILED && p.schedule != PTCA_SCHEDULE_BLOCK)
         return fail(PTCA_ERR_INVALID, "unknown schedule");
@@ -178,10 +198,11 @@ ptca_status resolve(const ptca_lattice* lat, const ptca_params* par, Problem& p)
     if (o >= p.Lc) return fail(PTCA_ERR_INVALID, "update_offset must be < L_c");
     p.ox = o;
     p.oy = p.Ly == 1 ? 0 : o;
+    p.oz = p.Lz == 1 ? 0 : o;
     p.cluster_periodic = par->cluster_periodic < 0 ? p.periodic : (par->cluster_periodic ? 1 : 0);
     p.stride = par->stride > 0 ? par->stride : p.Lc;
     if (p.schedule == PTCA_SCHEDULE_TILED && p.periodic &&
-        (p.Lx % p.stride != 0 || (p.Ly > 1 && p.Ly % p.stride != 0)))
+        (p.Lx % p.stride != 0 || (p.Ly > 1 && p.Ly % p.stride != 0) || (p.Lz > 1 && p.Lz % p.stride != 0)))
         return fail(PTCA_ERR_INVALID, "tiled stride must divide the lattice extents on a torus");
     p.precision = par->precision;
     if (p.precision != PTCA_FP64 && p.precision != PTCA_MIXED) return fail(PTCA_ERR_INVALID, "unknown precision");
@@ -207,8 +228,8 @@ ptca_status resolve(const ptca_lattice* lat, const ptca_params* par, Problem& p)
 
 Model to_model(const Problem& p) {
     Model m;
-    m.Lx = p.Lx; m.Ly = p.Ly; m.lattice_periodic = p.periodic;
-    m.Lc = p.Lc; m.ox = p.ox; m.oy = p.oy; m.cluster_periodic = p.cluster_periodic;
+    m.Lx = p.Lx; m.Ly = p.Ly; m.Lz = p.Lz; m.lattice_periodic = p.periodic;
+    m.Lc = p.Lc; m.ox = p.ox; m.oy = p.oy; m.oz = p.oz; m.cluster_periodic = p.cluster_periodic;
     m.proposal = p.proposal;
     m.t = p.t; m.mu = p.mu; m.T = p.T;
     m.cone_cos = std::cos(p.cone_deg * ptca::kPi / 180.0);
@@ -1075,8 +1096,8 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
 
 ptca_status ptca_surrogate_collect(ptca_ctx* ctx, int32_t n_sweeps, float* feat, int32_t* center, float* dF,
                                    void* stream) {
-    if (ctx && ctx->p.model != PTCA_MODEL_DOUBLE_EXCHANGE)
-        return fail(PTCA_ERR_UNSUPPORTED, "the surrogate screen is built for the double-exchange model");
+    if (ctx && (ctx->p.model != PTCA_MODEL_DOUBLE_EXCHANGE || ctx->p.Lz > 1))
+        return fail(PTCA_ERR_UNSUPPORTED, "the surrogate screen is built for the double-exchange model on square lattices");
     if (!ctx || n_sweeps < 0 || !feat || !center || !dF) return fail(PTCA_ERR_INVALID, "bad arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));

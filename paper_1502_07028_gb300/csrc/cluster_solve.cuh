@@ -20,8 +20,8 @@ namespace ptca {
 // e0 - JH m.sigma with JH = e0 = U/2, classical energy ucl (|m|^2 - 1) per
 // window site with ucl = U/4, proposals uniform in a ball of radius m_step.
 struct Model {
-    int32_t Lx, Ly, lattice_periodic;
-    int32_t Lc, ox, oy, cluster_periodic;
+    int32_t Lx, Ly, Lz, lattice_periodic;   // Lz == 1: square lattice or chain
+    int32_t Lc, ox, oy, oz, cluster_periodic;
     int32_t proposal;
     int32_t model;
     double t, JH, mu, T, cone_cos;
@@ -41,22 +41,33 @@ __device__ __forceinline__ void window_axis(int L, int periodic, int Lc, int o, 
     start = a; ext = b - a + 1;
 }
 
-struct Window { int x0, y0, ex, ey, uwx, uwy; };
+// Window of an update site: start and extent along each axis, and the update
+// site's window coordinates.  Sites are indexed (z Ly + y) Lx + x; window
+// sites (wz ey + wy) ex + wx.
+struct Window { int x0, y0, z0, ex, ey, ez, uwx, uwy, uwz; };
 
 __device__ __forceinline__ Window make_window(const Model& m, int site) {
     Window w;
-    const int cx = site % m.Lx, cy = site / m.Lx;
+    const int cx = site % m.Lx, cy = (site / m.Lx) % m.Ly, cz = site / (m.Lx * m.Ly);
     window_axis(m.Lx, m.lattice_periodic, m.Lc, m.ox, cx, w.x0, w.ex);
     window_axis(m.Ly, m.lattice_periodic, m.Lc, m.oy, cy, w.y0, w.ey);
+    window_axis(m.Lz, m.lattice_periodic, m.Lc, m.oz, cz, w.z0, w.ez);
     w.uwx = cx - w.x0; if (w.uwx < 0) w.uwx += m.Lx;
     w.uwy = cy - w.y0; if (w.uwy < 0) w.uwy += m.Ly;
+    w.uwz = cz - w.z0; if (w.uwz < 0) w.uwz += m.Lz;
     return w;
 }
 
-__device__ __forceinline__ int window_site(const Model& m, const Window& w, int wx, int wy) {
-    int x = w.x0 + wx, y = w.y0 + wy;
-    if (m.lattice_periodic) { if (x >= m.Lx) x -= m.Lx; if (y >= m.Ly) y -= m.Ly; }
-    return y * m.Lx + x;
+__device__ __forceinline__ int window_nsite(const Window& w) { return w.ex * w.ey * w.ez; }
+
+__device__ __forceinline__ int window_site(const Model& m, const Window& w, int wx, int wy, int wz = 0) {
+    int x = w.x0 + wx, y = w.y0 + wy, z = w.z0 + wz;
+    if (m.lattice_periodic) {
+        if (x >= m.Lx) x -= m.Lx;
+        if (y >= m.Ly) y -= m.Ly;
+        if (z >= m.Lz) z -= m.Lz;
+    }
+    return (z * m.Ly + y) * m.Lx + x;
 }
 
 __device__ __forceinline__ int tri(int r) { return (r * (r + 1)) >> 1; }
@@ -97,7 +108,8 @@ __device__ __forceinline__ double window_classical(const Model& m, const double*
 // by s_new when s_new != nullptr) and build the packed cluster matrix:
 //   on-site block  e0 - J [[S_z, S_x - i S_y], [S_x + i S_y, -S_z]] per site
 //                  (J = m.JH; e0 is the caller's diagonal shift),
-//   hopping        -t between nearest neighbours, same spin, each bond once;
+//   hopping        -t between nearest neighbours (x, y and, on a cubic
+//                  lattice, z), same spin, each bond once;
 // a periodic cluster wraps inside the window (an axis of extent 2 then has
 // two bonds between its two sites, extent 1 none).  Caller syncs after.  The
 // sweep kernels pass e0 = 0 and shift mu by -m.e0 instead: a multiple of the
@@ -107,12 +119,12 @@ template <typename T>
 __device__ void build_cluster(const Model& m, const Window& w, const double* __restrict__ S,
                               const double* s_new, double* sp, cplx_t<T>* A, double e0 = 0.0) {
     using V = cplx_t<T>;
-    const int nsite = w.ex * w.ey, n = 2 * nsite, P = tri(n);
+    const int nsite = window_nsite(w), n = 2 * nsite, P = tri(n), exy = w.ex * w.ey;
     for (int i = threadIdx.x; i < P; i += blockDim.x) A[i] = mk(T(0), T(0));
-    const int uw = w.uwy * w.ex + w.uwx;
+    const int uw = (w.uwz * w.ey + w.uwy) * w.ex + w.uwx;
     for (int s = threadIdx.x; s < nsite; s += blockDim.x) {
-        const int wx = s % w.ex, wy = s / w.ex;
-        const int g = window_site(m, w, wx, wy);
+        const int wx = s % w.ex, wy = (s / w.ex) % w.ey, wz = s / exy;
+        const int g = window_site(m, w, wx, wy, wz);
         double v0, v1, v2;
         if (s_new != nullptr && s == uw) { v0 = s_new[0]; v1 = s_new[1]; v2 = s_new[2]; }
         else { v0 = S[3 * g]; v1 = S[3 * g + 1]; v2 = S[3 * g + 2]; }
@@ -121,7 +133,7 @@ __device__ void build_cluster(const Model& m, const Window& w, const double* __r
     __syncthreads();
     const T t = T(m.t), J = T(m.JH), d0 = T(e0);
     for (int s = threadIdx.x; s < nsite; s += blockDim.x) {
-        const int wx = s % w.ex, wy = s / w.ex;
+        const int wx = s % w.ex, wy = (s / w.ex) % w.ey, wz = s / exy;
         const T sx = T(sp[3 * s]), sy = T(sp[3 * s + 1]), sz = T(sp[3 * s + 2]);
         const int a = 2 * s, b = 2 * s + 1;
         A[tri(a) + a] = mk(d0 - J * sz, T(0));
@@ -138,7 +150,15 @@ __device__ void build_cluster(const Model& m, const Window& w, const double* __r
         // +y bond
         nb = -1; mult = 1;
         if (wy + 1 < w.ey) { nb = s + w.ex; if (m.cluster_periodic && w.ey == 2) mult = 2; }
-        else if (m.cluster_periodic && w.ey >= 3) nb = wx;
+        else if (m.cluster_periodic && w.ey >= 3) nb = s - (w.ey - 1) * w.ex;
+        if (nb >= 0) {
+            const int hi = nb > s ? nb : s, lo = nb > s ? s : nb;
+            for (int sg = 0; sg < 2; ++sg) A[tri(2 * hi + sg) + 2 * lo + sg] = mk(-T(mult) * t, T(0));
+        }
+        // +z bond
+        nb = -1; mult = 1;
+        if (wz + 1 < w.ez) { nb = s + exy; if (m.cluster_periodic && w.ez == 2) mult = 2; }
+        else if (m.cluster_periodic && w.ez >= 3) nb = s - (w.ez - 1) * exy;
         if (nb >= 0) {
             const int hi = nb > s ? nb : s, lo = nb > s ? s : nb;
             for (int sg = 0; sg < 2; ++sg) A[tri(2 * hi + sg) + 2 * lo + sg] = mk(-T(mult) * t, T(0));

@@ -10,11 +10,11 @@
 
 // Resolved problem (defaults filled in).
 struct Problem {
-    int Lx, Ly, periodic, Lc, ox, oy, cluster_periodic, schedule, stride, precision, proposal, model;
+    int Lx, Ly, Lz, periodic, Lc, ox, oy, oz, cluster_periodic, schedule, stride, precision, proposal, model;
     double t, JH, mu, T, cone_deg, U, m_step;
     uint64_t seed;
-    int N() const { return Lx * Ly; }
-    int nsite_max() const { return Lc * (Ly == 1 ? 1 : Lc); }
+    int N() const { return Lx * Ly * Lz; }
+    int nsite_max() const { return Lc * (Ly == 1 ? 1 : Lc) * (Lz == 1 ? 1 : Lc); }
     int nmax() const { return 2 * nsite_max(); }
 };
 

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(CTA) k_build(Model m, const double* __restrict
     const Window w = make_window(m, site);
     cplx_t<T>* A = H + (int64_t)c * stride;
     build_cluster<T>(m, w, S, new_spins ? new_spins + 3 * c : nullptr, sp, A, m.e0);
-    if (threadIdx.x == 0) { offsets[c] = (int64_t)c * stride; nout[c] = 2 * w.ex * w.ey; }
+    if (threadIdx.x == 0) { offsets[c] = (int64_t)c * stride; nout[c] = 2 * window_nsite(w); }
 }
 
 // All eigenvalues of m packed matrices from global memory.
@@ -387,12 +387,15 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
     Carve<T> cv = carve<T>(smem, L, NWP);
     c = v.perm ? v.perm[c] : c;
     const int site = v.sites[c];
-    const Window w = make_window(a.m, site);
-    const int n = 2 * w.ex * w.ey;
-    if (threadIdx.x == 0 && var == 1)
-        propose(a.m, v.sweep, (uint32_t)site, v.S_in + 3 * site, s_new);
-    __syncthreads();
-    build_cluster<T>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    int n;
+    {
+        const Window w = make_window(a.m, site);
+        n = 2 * window_nsite(w);
+        if (threadIdx.x == 0 && var == 1)
+            propose(a.m, v.sweep, (uint32_t)site, v.S_in + 3 * site, s_new);
+        __syncthreads();
+        build_cluster<T>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    }
     __syncthreads();
     // The window's classical energy (Hubbard mean field), parked in this
     // matrix's F slot until the eigenvalues are known.
@@ -431,7 +434,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
         return;
     }
     const bool acc = lnu < -dFe / a.m.T;
-    collect_sample(a, v.S_in, w, v.rec_base + c, sn, dF);
+    if (a.sg_feat) collect_sample(a, v.S_in, make_window(a.m, site), v.rec_base + c, sn, dF);
     double* dst = v.S_out + 3 * site;
     if (acc) { dst[0] = sn[0]; dst[1] = sn[1]; dst[2] = sn[2]; }
     else { dst[0] = so[0]; dst[1] = so[1]; dst[2] = so[2]; }
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_check(StageArg
     Carve<T> cv = carve<T>(smem, L);
     const int site = a.sites[c0 + c];
     const Window w = make_window(a.m, site);
-    const int n = 2 * w.ex * w.ey;
+    const int n = 2 * window_nsite(w);
     if (threadIdx.x == 0 && var == 1)
         propose(a.m, a.sweep, (uint32_t)site, a.S_in + 3 * site, s_new);
     __syncthreads();
@@ -502,7 +505,7 @@ __global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int c
         const int c = item >> 1, var = item & 1;
         const int site = a.sites[c0 + c];
         const Window w = make_window(a.m, site);
-        const int n = 2 * w.ex * w.ey;
+        const int n = 2 * window_nsite(w);
         if (threadIdx.x == 0 && var == 1)
             propose(a.m, a.sweep, (uint32_t)site, a.S_in + 3 * site, s_new);
         __syncthreads();
@@ -533,12 +536,15 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, 
     Carve<dfl> cv = carve<dfl>(smem, L, NWP);
     if constexpr (!kSmemA) cv.A = reinterpret_cast<dfl2*>(a.gA + (int64_t)blockIdx.x * a.gA_stride);
     const int site = v.sites[c];
-    const Window w = make_window(a.m, site);
-    const int n = 2 * w.ex * w.ey;
-    if (threadIdx.x == 0 && var == 1)
-        propose(a.m, v.sweep, (uint32_t)site, v.S_in + 3 * site, s_new);
-    __syncthreads();
-    build_cluster<dfl>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    int n;
+    {
+        const Window w = make_window(a.m, site);
+        n = 2 * window_nsite(w);
+        if (threadIdx.x == 0 && var == 1)
+            propose(a.m, v.sweep, (uint32_t)site, v.S_in + 3 * site, s_new);
+        __syncthreads();
+        build_cluster<dfl>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+    }
     __syncthreads();
     if (threadIdx.x == 0 && a.m.ucl != 0.0) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
     householder_tridiag<dfl, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
@@ -567,7 +573,7 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, 
     const double dF = Fn - Fo;
     if (!isfinite(dF)) atomicExch(a.err, 1);
     const bool acc = lnu < -stage2_dF(a, c, dF) / a.m.T;
-    collect_sample(a, v.S_in, w, v.rec_base + c, sn, dF);
+    if (a.sg_feat) collect_sample(a, v.S_in, make_window(a.m, site), v.rec_base + c, sn, dF);
     double* dst = v.S_out + 3 * site;
     if (acc) { dst[0] = sn[0]; dst[1] = sn[1]; dst[2] = sn[2]; }
     else { dst[0] = so[0]; dst[1] = so[1]; dst[2] = so[2]; }

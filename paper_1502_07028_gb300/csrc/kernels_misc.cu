@@ -99,7 +99,7 @@ __global__ void k_check_compare(Model m, const int32_t* __restrict__ sites, int 
     const int c = blockIdx.x;
     if (c >= count) return;
     const Window w = make_window(m, sites[c]);
-    const int n = 2 * w.ex * w.ey;
+    const int n = 2 * window_nsite(w);
     double de = 0.0;
     for (int var = 0; var < 2; ++var) {
         const double* a = e32 + (int64_t)(2 * c + var) * ld;
@@ -213,8 +213,8 @@ __global__ void k_observables(const double* __restrict__ S, int Lx, int Ly, cons
     double m0[3] = {0, 0, 0}, mp[3] = {0, 0, 0};
     double fs = 0.0, ac = 0.0, fl = 0.0, nf = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const int x = i % Lx, y = i / Lx;
-        const double sg = ((x + y) & 1) ? -1.0 : 1.0;
+        const int x = i % Lx, y = (i / Lx) % Ly, z = i / (Lx * Ly);
+        const double sg = ((x + y + z) & 1) ? -1.0 : 1.0;
         for (int a = 0; a < 3; ++a) { m0[a] += S[3 * i + a]; mp[a] += sg * S[3 * i + a]; }
         if (rec_n[i] > 0) {
             ac += (double)rec_acc[i];

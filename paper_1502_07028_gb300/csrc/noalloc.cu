@@ -75,8 +75,8 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
         return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_sweep_noalloc: null argument");
     if (sweep_index < 0) return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_sweep_noalloc: sweep_index < 0");
     // Validate the problem and the schedule on the host (no device memory).
-    const int64_t N64 = (int64_t)lattice->Lx * (int64_t)lattice->Ly;
-    if (lattice->Lx < 1 || lattice->Ly < 1 || N64 > kNoAllocMaxSites)
+    const int64_t N64 = (int64_t)lattice->Lx * (int64_t)lattice->Ly * (int64_t)(lattice->Lz > 1 ? lattice->Lz : 1);
+    if (lattice->Lx < 1 || lattice->Ly < 1 || lattice->Lz < 0 || N64 > kNoAllocMaxSites)
         return ptca_internal_fail(PTCA_ERR_INVALID,
                                   ("ptca_sweep_noalloc: lattice has " + std::to_string(N64) +
                                    " sites; this entry point supports at most " + std::to_string(kNoAllocMaxSites))
@@ -116,8 +116,9 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
     int o = params->update_offset;
     if (o < 0) o = params->schedule == PTCA_SCHEDULE_TILED ? Lc / 2 : 0;
     ptca::Model m;
-    m.Lx = lattice->Lx; m.Ly = lattice->Ly; m.lattice_periodic = lattice->periodic ? 1 : 0;
-    m.Lc = Lc; m.ox = o; m.oy = lattice->Ly == 1 ? 0 : o;
+    const int Lz = lattice->Lz == 0 ? 1 : lattice->Lz;
+    m.Lx = lattice->Lx; m.Ly = lattice->Ly; m.Lz = Lz; m.lattice_periodic = lattice->periodic ? 1 : 0;
+    m.Lc = Lc; m.ox = o; m.oy = lattice->Ly == 1 ? 0 : o; m.oz = Lz == 1 ? 0 : o;
     m.cluster_periodic = params->cluster_periodic < 0 ? m.lattice_periodic : (params->cluster_periodic ? 1 : 0);
     m.proposal = params->proposal;
     m.t = params->t; m.mu = params->mu; m.T = params->T;
@@ -130,7 +131,7 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
     }
     m.seed = params->seed;
     const int prec = params->precision == PTCA_MIXED ? 1 : 0;
-    const int nA = 2 * Lc * (lattice->Ly == 1 ? 1 : Lc);
+    const int nA = 2 * Lc * (lattice->Ly == 1 ? 1 : Lc) * (Lz == 1 ? 1 : Lc);
     const size_t smem = ptca::cluster_smem_bytes(prec, nA);
     if (smem == 0 || smem + 256 > (size_t)optin)
         return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_sweep_noalloc: cluster matrix too large for this precision");

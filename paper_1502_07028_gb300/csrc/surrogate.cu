@@ -328,7 +328,7 @@ __global__ void k_screen_decide(StageArgs a, const float* __restrict__ Z4, float
     a.rec_acc[r] = 0;
     a.rec_Facc[r] = nan;
     a.rec_fill[r] = nan;
-    a.rec_n[r] = 2 * w.ex * w.ey;
+    a.rec_n[r] = 2 * window_nsite(w);
     atomicAdd(&a.counters[3], 1ull);
 }
 

@@ -16,6 +16,7 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--L", type=int, default=100)
     ap.add_argument("--Lc", type=int, default=8)
+    ap.add_argument("--Lz", type=int, default=1, help="third extent (cubic lattice L x L x Lz)")
     ap.add_argument("--open", action="store_true", help="open lattice (clipped windows)")
     ap.add_argument("--schedule", choices=["block", "tiled"], default="block")
     ap.add_argument("--stride", type=int, default=0)
@@ -39,7 +40,7 @@ def main(argv=None):
     from paper_1502_07028_gb300 import _build
 
     _build.build()
-    cfg = P.Config(Lx=a.L, Ly=a.L, L_c=a.Lc, periodic=0 if a.open else 1, J_H=a.JH, mu=a.mu, T=a.T, seed=a.seed,
+    cfg = P.Config(Lx=a.L, Ly=a.L, Lz=a.Lz, L_c=a.Lc, periodic=0 if a.open else 1, J_H=a.JH, mu=a.mu, T=a.T, seed=a.seed,
                    schedule=P.SCHEDULE_BLOCK if a.schedule == "block" else P.SCHEDULE_TILED, stride=a.stride,
                    precision=P.MIXED if a.precision == "mixed" else P.FP64, proposal=P.PROPOSAL_CONE, cone_deg=30.0,
                    model=P.MODEL_HUBBARD_MF if a.model == "hubbard" else P.MODEL_DOUBLE_EXCHANGE, U=a.U,
@@ -52,7 +53,7 @@ def main(argv=None):
     if a.warmup:
         ctx.sweep(a.warmup)
     st = ctx.sweep(a.sweeps)
-    print(f"{a.precision} L={a.L} Lc={a.Lc} {a.schedule} {a.pipeline} {a.warps} warps: {st.seconds * 1e3:.3f} ms for "
+    print(f"{a.precision} {a.model} L={a.L} Lz={a.Lz} Lc={a.Lc} {a.schedule} {a.pipeline} {a.warps} warps: {st.seconds * 1e3:.3f} ms for "
           f"{a.sweeps} sweep(s), "
           f"{cfg.N * a.sweeps / st.seconds:.0f} spin-updates/s, accepted {st.accepted}, resolved {st.resolved}")
     ctx.close()

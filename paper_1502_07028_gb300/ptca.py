@@ -49,7 +49,7 @@ class LaunchConfig(ctypes.Structure):
 
 
 class Lattice(ctypes.Structure):
-    _fields_ = [("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32), ("periodic", ctypes.c_int32)]
+    _fields_ = [("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32), ("periodic", ctypes.c_int32), ("Lz", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -189,9 +189,10 @@ class Config:
     model: int = MODEL_DOUBLE_EXCHANGE
     U: float = 8.0
     m_step: float = 0.5
+    Lz: int = 1
 
     def lattice(self) -> Lattice:
-        return Lattice(self.Lx, self.Ly, self.periodic)
+        return Lattice(self.Lx, self.Ly, self.periodic, self.Lz)
 
     def params(self) -> Params:
         return Params(self.t, self.J_H, self.mu, self.T, self.L_c, self.cluster_periodic, self.update_offset,
@@ -200,7 +201,7 @@ class Config:
 
     @property
     def N(self) -> int:
-        return self.Lx * self.Ly
+        return self.Lx * self.Ly * self.Lz
 
 
 # ---------------------------------------------------------------------------

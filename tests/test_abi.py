@@ -60,11 +60,14 @@ def test_symbols_are_c_linkage(built):
     dict(Lx=31, Ly=17, L_c=6, periodic=0, stride=6),
     dict(Lx=8, Ly=1, L_c=4, schedule=P.SCHEDULE_BLOCK),
     dict(Lx=9, Ly=7, L_c=4, periodic=0, schedule=P.SCHEDULE_BLOCK),
+    dict(Lx=8, Ly=8, Lz=8, L_c=4, schedule=P.SCHEDULE_BLOCK),
+    dict(Lx=6, Ly=6, Lz=6, L_c=3, stride=3),
+    dict(Lx=7, Ly=6, Lz=5, L_c=3, periodic=0, schedule=P.SCHEDULE_BLOCK),
 ])
 def test_schedule_matches_oracle(built, kw):
     cfg = P.Config(**kw)
     mine = P.ptca_schedule(cfg)
-    m = oracle.Model(Lx=cfg.Lx, Ly=cfg.Ly, Lc=cfg.L_c, lattice_periodic=cfg.periodic,
+    m = oracle.Model(Lx=cfg.Lx, Ly=cfg.Ly, Lz=cfg.Lz, Lc=cfg.L_c, lattice_periodic=cfg.periodic,
                      schedule=cfg.schedule, stride=cfg.stride)
     ref = oracle.schedule(m)
     assert len(mine) == len(ref)
@@ -81,6 +84,9 @@ def test_schedule_matches_oracle(built, kw):
     (dict(Lx=8, Ly=8, L_c=4, T=0.0), "T > 0"),
     (dict(Lx=66, Ly=66, L_c=11, precision=P.MIXED), "maximum"),
     (dict(Lx=8, Ly=8, L_c=4, update_offset=4), "update_offset"),
+    (dict(Lx=8, Ly=1, Lz=4, L_c=2), "needs Ly > 1"),
+    (dict(Lx=8, Ly=8, Lz=3, L_c=4), "L_c"),
+    (dict(Lx=8, Ly=8, Lz=6, L_c=4, stride=4), "divide"),
 ])
 def test_invalid_problems_are_rejected(built, kw, why):
     with pytest.raises(P.PtcaError) as e:
@@ -106,6 +112,8 @@ def test_init_reports_missing_gpu_instead_of_falling_back(built):
     dict(Lx=31, Ly=17, L_c=6, periodic=0, stride=6),
     dict(Lx=8, Ly=1, L_c=4, schedule=P.SCHEDULE_BLOCK),
     dict(Lx=9, Ly=7, L_c=4, periodic=0, schedule=P.SCHEDULE_BLOCK),
+    dict(Lx=6, Ly=6, Lz=6, L_c=3, schedule=P.SCHEDULE_BLOCK),
+    dict(Lx=6, Ly=5, Lz=4, L_c=3, periodic=0, schedule=P.SCHEDULE_BLOCK),
 ])
 def test_stage_split_follows_the_window_rule(built, kw):
     """The overlapped pipeline's split, against the oracle's window rule
@@ -113,12 +121,12 @@ def test_stage_split_follows_the_window_rule(built, kw):
     (cyclically) lies in its window; each part is ordered largest window
     first, ties in schedule order."""
     cfg = P.Config(**kw)
-    m = oracle.Model(Lx=cfg.Lx, Ly=cfg.Ly, Lc=cfg.L_c, lattice_periodic=cfg.periodic,
+    m = oracle.Model(Lx=cfg.Lx, Ly=cfg.Ly, Lz=cfg.Lz, Lc=cfg.L_c, lattice_periodic=cfg.periodic,
                      schedule=cfg.schedule, stride=cfg.stride)
     stages = oracle.schedule(m)
     split = P.ptca_stage_split(cfg)
     assert len(split) == len(stages)
-    N = cfg.Lx * cfg.Ly
+    N = cfg.N
     wsize = {}
     for s, sites in enumerate(stages):
         prev = stages[(s - 1) % len(stages)]
