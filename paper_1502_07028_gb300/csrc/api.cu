@@ -221,8 +221,8 @@ ptca_status resolve(const ptca_lattice* lat, const ptca_params* par, Problem& p)
         return fail(PTCA_ERR_INVALID, "t, J_H, mu must be finite and T > 0");
     if (p.proposal == PTCA_PROPOSAL_CONE && !(p.cone_deg > 0 && p.cone_deg <= 180))
         return fail(PTCA_ERR_INVALID, "cone_deg must lie in (0, 180]");
-    if (p.nmax() > ptca::cluster_max_order(p.precision == PTCA_MIXED ? 1 : 0))
-        return fail(PTCA_ERR_INVALID, "cluster matrix order 2*N_c exceeds the supported maximum");
+    if (p.nmax() > ptca::cluster_max_order(p.precision == PTCA_MIXED ? 1 : 0) && p.nmax() > ptca::large_max_order())
+        return fail(PTCA_ERR_INVALID, "cluster matrix order 2*N_c exceeds the supported maximum (512)");
     return PTCA_OK;
 }
 
@@ -293,7 +293,7 @@ static void free_ctx(ptca_ctx* c) {
     if (c->side) cudaStreamDestroy(c->side);
     for (cudaEvent_t ev : {c->ev_indep, c->ev_dep, c->ev_fork, c->ev_join})
         if (ev) cudaEventDestroy(ev);
-    void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_S[2], c->d_split, c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
+    void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_S[2], c->d_split, c->d_gL, c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
                     c->d_rec_n, c->d_counters, c->d_err, c->d_obs, c->d_stage_start, c->d_perm, c->d_queue,
                     c->d_bar, c->d_sweep_ctr, c->d_flag_list, c->d_flag_count, c->d_gA,
@@ -372,13 +372,14 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
     c->nstages = (int)st.size() - 1;
     for (int k = 0; k < c->nstages; ++k) c->max_stage = std::max(c->max_stage, st[k + 1] - st[k]);
     c->nA = p.nmax();
-    c->smem = ptca::cluster_smem_bytes(c->prec, c->nA);
+    c->large = c->nA > ptca::cluster_max_order(c->prec);
+    c->smem = c->large ? ptca::large_smem_bytes(c->prec) : ptca::cluster_smem_bytes(c->prec, c->nA);
     if (c->smem == 0 || c->smem + 256 > (size_t)optin) {
         delete c;
-        return fail(PTCA_ERR_INVALID, "cluster matrix does not fit in shared memory for this precision "
-                                      "(FP64 supports 2*N_c up to about 144)");
+        return fail(PTCA_ERR_INVALID, "cluster kernels do not fit in shared memory on this device");
     }
     cudaError_t ce = ptca::configure_cluster_kernels((size_t)optin);
+    if (ce == cudaSuccess && c->large) ce = ptca::configure_large_kernels((size_t)optin);
     if (ce != cudaSuccess) {
         delete c;
         return cuda_fail(ce, "ptca_init (configuring kernel shared memory)");
@@ -424,9 +425,19 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         c->sms = sms;
-        c->grid = sms * ptca::persistent_blocks_per_sm(c->prec, 8, c->nA);
+        c->grid = c->large ? 0 : sms * ptca::persistent_blocks_per_sm(c->prec, 8, c->nA);
         if (c->grid <= 0) c->pipeline = PTCA_PIPELINE_STAGES;
-        if (c->prec == 1) {
+        if (c->large) {
+            // One global matrix slot per resident CTA of the large-cluster
+            // stage kernel (+ 64 elements of padding, as below).
+            c->large_grid = sms * std::max(1, ptca::large_blocks_per_sm(c->prec));
+            c->gL_stride = (int64_t)c->nA * (c->nA + 1) / 2;
+            const size_t es = c->prec == 1 ? sizeof(float2) : sizeof(double2);
+            void* q = nullptr;
+            ce = cudaMalloc(&q, ((size_t)c->large_grid * (size_t)c->gL_stride + 64) * es);
+            c->d_gL = q;
+        }
+        if (ce == cudaSuccess && c->prec == 1) {
             // Global slots for the re-solves: one per CTA of any launch
             // configuration (the 4-warp persistent grid is the widest).
             c->resolve_grid = sms;
@@ -524,6 +535,7 @@ ptca_status ptca_cluster_eigvals(ptca_ctx* ctx, const void* H, const int64_t* of
     if (m < 0) return fail(PTCA_ERR_INVALID, "m < 0");
     if (m == 0) return PTCA_OK;
     if (!H || !offsets || !n || !eig_out || !eig_offsets) return fail(PTCA_ERR_INVALID, "null buffer");
+    if (ctx->large) return fail(PTCA_ERR_UNSUPPORTED, "batch eigenvalues cover the shared-memory cluster orders only");
     PTCA_CUDA(ptca::launch_eigvals(ctx->prec, ctx->nA, H, offsets, n, m, eig_out, eig_offsets,
                                    static_cast<cudaStream_t>(stream)));
     return PTCA_OK;
@@ -563,10 +575,23 @@ static StageArgs base_args(ptca_ctx* ctx) {
     a.flag_count = ctx->d_flag_count;
     a.gA = ctx->d_gA;
     a.gA_stride = ctx->gA_stride;
+    a.gL = ctx->d_gL;
+    a.gL_stride = ctx->gL_stride;
     return a;
 }
 
 cudaError_t ptca_screen_stage(ptca_ctx* ctx, ptca::StageArgs& a, cudaStream_t st);
+
+// A stage launch and a re-solve launch in the context's configuration
+// (shared-memory kernels, or the large-cluster kernels).
+static cudaError_t launch_stage_ctx(const ptca_ctx* ctx, const StageArgs& a, cudaStream_t st) {
+    if (ctx->large) return ptca::launch_stage_large(ctx->prec, a, ctx->large_grid, st);
+    return ptca::launch_stage(ctx->prec, ctx->nw, a, st);
+}
+static cudaError_t launch_resolve_ctx(const ptca_ctx* ctx, const StageArgs& a, cudaStream_t st) {
+    if (ctx->large) return ptca::launch_resolve_large(a, ctx->resolve_grid, st);
+    return ptca::launch_resolve(a, ctx->resolve_grid, st);
+}
 
 // Training-sample destination of ptca_surrogate_collect (N rows per sweep).
 struct Collect {
@@ -624,9 +649,9 @@ static cudaError_t sweep_stages(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st
             if (e == cudaSuccess && ctx->sg.enabled && !col) e = ptca_screen_stage(ctx, a, st);
             if (e == cudaSuccess)
                 e = timed_launch(ctx, 0, 2 * (int64_t)a.count, st,
-                                 [&] { return ptca::launch_stage(ctx->prec, ctx->nw, a, st); });
+                                 [&] { return launch_stage_ctx(ctx, a, st); });
             if (e == cudaSuccess && a.margin > 0.0) {
-                e = timed_launch(ctx, 1, 0, st, [&] { return ptca::launch_resolve(a, ctx->resolve_grid, st); });
+                e = timed_launch(ctx, 1, 0, st, [&] { return launch_resolve_ctx(ctx, a, st); });
                 if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag_count, 0, sizeof(unsigned int), st);
             }
             prev_s = s;
@@ -695,7 +720,7 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
     auto resolve_prev = [&]() {
         cudaError_t r = cudaStreamWaitEvent(hs, ctx->ev_indep, 0);
         if (r == cudaSuccess)
-            r = timed_launch(ctx, 1, 0, hs, [&] { return ptca::launch_resolve(prev, ctx->resolve_grid, hs); });
+            r = timed_launch(ctx, 1, 0, hs, [&] { return launch_resolve_ctx(ctx, prev, hs); });
         if (r == cudaSuccess) r = cudaMemsetAsync(prev.flag_count, 0, sizeof(unsigned int), hs);
         return r;
     };
@@ -721,7 +746,7 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         ai.count = ni;
         if (e == cudaSuccess && ni > 0)
             e = timed_launch(ctx, 0, 2 * (int64_t)ni, st,
-                             [&] { return ptca::launch_stage(ctx->prec, ctx->nw, ai, st); });
+                             [&] { return launch_stage_ctx(ctx, ai, st); });
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_indep, st);
         StageArgs ad = a;
         ad.perm = ctx->d_split + ctx->h_start[s] + ni;
@@ -734,7 +759,7 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         if (e == cudaSuccess) {
             if (ad.count > 0) {
                 e = timed_launch(ctx, 2, 2 * (int64_t)ad.count, hs,
-                                 [&] { return ptca::launch_stage(ctx->prec, ctx->nw, ad, hs); });
+                                 [&] { return launch_stage_ctx(ctx, ad, hs); });
             } else {
                 e = ptca::launch_copy_sites(ad.S_in, ad.S_out, ad.prev_sites, ad.prev_count, hs);
                 if (e == cudaSuccess) e = ptca::launch_copy_sites(ad.S_in, ad.S_out, ad.prev2_sites, ad.prev2_count, hs);
@@ -874,7 +899,9 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     if (cfg->pipeline < PTCA_PIPELINE_STAGES || cfg->pipeline > PTCA_PIPELINE_OVERLAP)
         return fail(PTCA_ERR_INVALID, "unknown pipeline");
     if (cfg->warps_per_cta != 8 && cfg->warps_per_cta != 4) return fail(PTCA_ERR_INVALID, "warps_per_cta must be 4 or 8");
-    if (!ptca::sweep_width_supported(ctx->prec, cfg->warps_per_cta, ctx->nA))
+    if (ctx->large && cfg->warps_per_cta != 8)
+        return fail(PTCA_ERR_UNSUPPORTED, "large clusters run 16-warp CTAs; pass warps_per_cta = 8 (the default width)");
+    if (!ctx->large && !ptca::sweep_width_supported(ctx->prec, cfg->warps_per_cta, ctx->nA))
         return fail(PTCA_ERR_UNSUPPORTED, "4-warp sweep kernels need PTCA_MIXED and matrix orders up to 128");
     const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, cfg->warps_per_cta, ctx->nA);
     if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > maxb)
@@ -911,8 +938,12 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // Candidates: CTA width x pipeline x persistent CTAs per SM.
     std::vector<ptca_launch_config> cand;
+    if (ctx->large) {
+        cand.push_back({PTCA_PIPELINE_STAGES, 8, 0});
+        if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, 8, 0});
+    }
     for (int nw : {8, 4}) {
-        if (!ptca::sweep_width_supported(ctx->prec, nw, ctx->nA)) continue;
+        if (ctx->large || !ptca::sweep_width_supported(ctx->prec, nw, ctx->nA)) continue;
         cand.push_back({PTCA_PIPELINE_STAGES, nw, 0});
         if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0});
         const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, nw, ctx->nA);
@@ -1013,6 +1044,7 @@ ptca_status ptca_set_checker(ptca_ctx* ctx, int32_t on) {
         return PTCA_OK;
     }
     if (ctx->prec != 1) return fail(PTCA_ERR_UNSUPPORTED, "the precision checker compares PTCA_MIXED against FP64");
+    if (ctx->large) return fail(PTCA_ERR_UNSUPPORTED, "the precision checker covers the shared-memory cluster orders");
     if (!ctx->d_chk_out) {
         ctx->check_chunk = std::min(ctx->max_stage, 2048);
         cudaError_t e = dalloc(&ctx->d_chk_eig, (size_t)2 * ctx->check_chunk * 2 * ctx->nA);
@@ -1096,7 +1128,7 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
 
 ptca_status ptca_surrogate_collect(ptca_ctx* ctx, int32_t n_sweeps, float* feat, int32_t* center, float* dF,
                                    void* stream) {
-    if (ctx && (ctx->p.model != PTCA_MODEL_DOUBLE_EXCHANGE || ctx->p.Lz > 1))
+    if (ctx && (ctx->p.model != PTCA_MODEL_DOUBLE_EXCHANGE || ctx->p.Lz > 1 || ctx->large))
         return fail(PTCA_ERR_UNSUPPORTED, "the surrogate screen is built for the double-exchange model on square lattices");
     if (!ctx || n_sweeps < 0 || !feat || !center || !dF) return fail(PTCA_ERR_INVALID, "bad arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -300,18 +300,19 @@ __device__ __forceinline__ void reflector_head<float>(float s2, float2 x0, float
     tau = sigma > 0.f ? __fdividef(1.f, sigma * (sigma + ax0)) : 0.f;
 }
 
-template <typename T, int NT, int NW>
-__device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc, double* d, double* e2) {
+// Shared phases of the Householder reductions below (one CTA of NW warps per
+// matrix, vectors of NMAX entries in shared memory, A in shared or global
+// memory).  hh_setup zeroes the vectors and forms the first reflector; it
+// returns false when n <= 2 (d and e2 already written).  hh_scalar is the
+// per-step scalar work after a pass (every vector entry has its own thread:
+// blockDim >= n); hh_finish writes the last diagonal entry.
+template <typename T, int NW, int NMAX>
+__device__ __forceinline__ bool hh_setup(int n, cplx_t<T>* A, const HHScratch<T>& sc, double* d, double* e2,
+                                         cplx_t<T>& vfirst, T& tau) {
     using V = cplx_t<T>;
-    constexpr int NMAX = 32 * NT;
-    // The scalar tail (two square roots, divisions) is recomputed by every
-    // thread in FP32; in FP64 one warp computes it and shares it.
-    constexpr bool kSharedTail = sizeof(T) == 8;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     V* const Vb = sc.Vb;
     V* const Wv = sc.Wv;
-    V* const pr = sc.pr;
-    V* const pc = sc.pc;
     const V zero = mk(T(0), T(0));
 
     for (int i = tid; i < 2 * NMAX; i += NW * 32) Vb[i] = zero;
@@ -324,13 +325,11 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
             if (n == 2) { d[1] = double(A[2].x); e2[0] = double(cabs2(A[1])); }
         }
         __syncthreads();
-        return;
+        return false;
     }
 
     // Column 0: d_0, ||x||^2 and the first reflector v_0 (entries 1 .. n-1;
     // entry 1 in registers, the rest in Vb[0 .. NMAX)).
-    V vfirst;
-    T tau;
     {
         const int ri = tid;
         const int nact = (n + 31) >> 5;  // warps holding entries
@@ -352,10 +351,124 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
         reflector_head(s2, sc.sx[0], vfirst, tau);
     }
 
+    return true;
+}
+
+template <typename T, int NW, int NMAX>
+__device__ __forceinline__ void hh_scalar(int k, int n, cplx_t<T>* A, const HHScratch<T>& sc, double* d,
+                                          double* e2, cplx_t<T>& vfirst, T& tau) {
+    using V = cplx_t<T>;
+    // The scalar tail (two square roots, divisions) is recomputed by every
+    // thread in FP32; in FP64 one warp computes it and shares it.
+    constexpr bool kSharedTail = sizeof(T) == 8;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    V* const Vb = sc.Vb;
+    V* const Wv = sc.Wv;
+    V* const pr = sc.pr;
+    V* const pc = sc.pc;
+    const V zero = mk(T(0), T(0));
+    const V* V_ = Vb + (k & 1) * NMAX;        // v_k (entry k+1 is vfirst)
+    V* Vn = Vb + ((k + 1) & 1) * NMAX;        // v_{k+1}
+    const int j0 = k + 1;
+    const int m = n - j0;
+
+    // ---- p = tau A v (thread ri combines the row and per-warp column
+    // partial sums of entry ri) and the partial sums of v^H p.
+    const int ri = tid;
+    const bool mine = ri < m;
+    const int nact = (m + 31) >> 5;  // warps holding entries
+    V v = zero, p = zero;
+    if (warp < nact) {
+        T sp = T(0);
+        if (mine) {
+            p = pr[ri];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) p = cadd(p, pc[w * NMAX + ri]);
+            p.x *= tau; p.y *= tau;
+            v = ri == 0 ? vfirst : V_[j0 + ri];
+            pr[ri] = p;
+            sp = v.x * p.x + v.y * p.y;
+        }
+        sp = warp_sum(sp);
+        if (lane == 0) sc.redA[warp] = sp;
+    }
+    __syncthreads();
+
+    // ---- w = p - (tau s / 2) v, the explicit update of pivot column
+    // j0 with (v_k, w_k), d_j0, and the partial sums of ||x||^2 for the
+    // next reflector, whose entries past the first go to Vn.
+    if (warp < nact) {
+        const T K = T(0.5) * tau * sum_partials<T, NW>(sc.redA, nact);
+        const V p0 = pr[0];
+        const V w0 = mk(p0.x - K * vfirst.x, p0.y - K * vfirst.y);
+        T s2p = T(0);
+        if (mine) {
+            const V w = mk(p.x - K * v.x, p.y - K * v.y);
+            Wv[j0 + ri] = w;
+            V a = A[tri(j0 + ri) + j0];
+            a = cfms_conj_b(v, w0, a);
+            a = cfms_conj_b(w, vfirst, a);
+            if (ri == 0) d[j0] = double(a.x);
+            if (ri >= 1) s2p = cabs2(a);
+            if (ri >= 2) Vn[j0 + ri] = a;
+            if (ri == 1) sc.sx[0] = a;
+        }
+        s2p = warp_sum(s2p);
+        if (lane == 0) sc.redB[warp] = s2p;
+    }
+    __syncthreads();
+
+    // ---- ||x||^2, and the next reflector's first entry and tau.
+    if constexpr (kSharedTail) {
+        if (warp == 0) {
+            const T s2 = sum_partials<T, NW>(sc.redB, nact);
+            if (lane == 0) e2[j0] = double(s2);
+            if (k + 1 <= n - 3) {
+                V f;
+                T tn;
+                reflector_head(s2, sc.sx[0], f, tn);
+                if (lane == 0) { sc.sx[1] = f; sc.sx[2] = mk(tn, T(0)); }
+            }
+        }
+        __syncthreads();
+        if (k + 1 <= n - 3) { vfirst = sc.sx[1]; tau = sc.sx[2].x; }
+    } else {
+        const T s2 = sum_partials<T, NW>(sc.redB, nact);
+        if (tid == 0) e2[j0] = double(s2);
+        if (k + 1 <= n - 3) reflector_head(s2, sc.sx[0], vfirst, tau);
+    }
+}
+
+template <typename T, int NMAX>
+__device__ __forceinline__ void hh_finish(int n, cplx_t<T>* A, const HHScratch<T>& sc, double* d) {
+    using V = cplx_t<T>;
+    // Step n-3's update of the last diagonal entry.
+    if (threadIdx.x == 0) {
+        const V v = sc.Vb[((n - 3) & 1) * NMAX + n - 1];
+        const V w = sc.Wv[n - 1];
+        const T ann = A[tri(n - 1) + n - 1].x - T(2) * (v.x * w.x + v.y * w.y);
+        d[n - 1] = double(ann);
+    }
+    __syncthreads();
+}
+
+template <typename T, int NT, int NW>
+__device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc, double* d, double* e2) {
+    using V = cplx_t<T>;
+    constexpr int NMAX = 32 * NT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    V* const Vb = sc.Vb;
+    V* const Wv = sc.Wv;
+    V* const pr = sc.pr;
+    V* const pc = sc.pc;
+    const V zero = mk(T(0), T(0));
+    V vfirst;
+    T tau;
+    if (!hh_setup<T, NW, NMAX>(n, A, sc, d, e2, vfirst, tau)) return;
+
     for (int k = 0; k <= n - 3; ++k) {
         const V* V_ = Vb + (k & 1) * NMAX;        // v_k (entry k+1 is vfirst)
-        const V* U_ = Vb + ((k + 1) & 1) * NMAX;  // v_{k-1} (zero at k = 0)
-        V* Vn = Vb + ((k + 1) & 1) * NMAX;        // v_{k+1}, written once U_ is consumed
+        const V* U_ = Vb + ((k + 1) & 1) * NMAX;  // v_{k-1} (zero at k = 0); v_{k+1} replaces it later
         const int j0 = k + 1;                     // first active row/column
 
         // ---- fused pass: A <- A - u w^H - w u^H (step k-1), accumulate A v_k.
@@ -479,81 +592,63 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
         }
         __syncthreads();
 
-        // ---- p = tau A v (thread ri combines the row and per-warp column
-        // partial sums of entry ri) and the partial sums of v^H p.
-        const int ri = tid;
-        const bool mine = ri < m;
-        const int nact = (m + 31) >> 5;  // warps holding entries
-        V v = zero, p = zero;
-        if (warp < nact) {
-            T sp = T(0);
-            if (mine) {
-                p = pr[ri];
+        hh_scalar<T, NW, NMAX>(k, n, A, sc, d, e2, vfirst, tau);
+    }
+    hh_finish<T, NMAX>(n, A, sc, d);
+}
+
+// The same reduction for matrices too large for shared memory (n up to
+// 32 NW, the paper's large traveling clusters): A lives in the CTA's global
+// slot (L1/L2 resident), the vectors in shared memory.  The fused pass is the
+// plain form of the one above: warp w takes rows m-1-w, m-1-w-NW, ... (the
+// longest first), lane l the columns l, l+32, ... of the row; each element is
+// updated with the previous step's (u, w), stored, and contributes to its
+// row's sum (reduced across the warp) and, below the diagonal, to its
+// column's sum in the warp's own partial row (lanes own distinct columns, so
+// the order of the additions is fixed).  Between passes the scalar phases are
+// those of householder_tridiag.
+template <typename T, int NW>
+__device__ void householder_tridiag_large(int n, cplx_t<T>* A, const HHScratch<T>& sc, double* d, double* e2) {
+    using V = cplx_t<T>;
+    constexpr int NMAX = 32 * NW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    V* const Vb = sc.Vb;
+    V* const Wv = sc.Wv;
+    V* const pr = sc.pr;
+    V* const pcw = sc.pc + warp * NMAX;
+    const V zero = mk(T(0), T(0));
+    V vfirst;
+    T tau;
+    if (!hh_setup<T, NW, NMAX>(n, A, sc, d, e2, vfirst, tau)) return;
+
+    for (int k = 0; k <= n - 3; ++k) {
+        const V* V_ = Vb + (k & 1) * NMAX;        // v_k (entry k+1 is vfirst)
+        const V* U_ = Vb + ((k + 1) & 1) * NMAX;  // v_{k-1} (zero at k = 0)
+        const int j0 = k + 1, m = n - j0;
+        for (int jr = lane; jr < m; jr += 32) pcw[jr] = zero;
+        for (int r = warp; r < m; r += NW) {
+            const int ri = m - 1 - r, i = j0 + ri;
+            const V ui = U_[i], wi = Wv[i], vi = ri == 0 ? vfirst : V_[i];
+            V* row = A + tri(i) + j0;
+            V racc = zero;
+            for (int jr = lane; jr <= ri; jr += 32) {
+                const int j = j0 + jr;
+                const V vj = jr == 0 ? vfirst : V_[j];
+                V a = row[jr];
+                a = cfms_conj_b(ui, Wv[j], a);
+                a = cfms_conj_b(wi, U_[j], a);
+                row[jr] = a;
+                racc = cfma(a, vj, racc);
+                if (jr < ri) pcw[jr] = cfma_conj_a(a, vi, pcw[jr]);
+            }
 #pragma unroll
-                for (int w = 0; w < NW; ++w) p = cadd(p, pc[w * NMAX + ri]);
-                p.x *= tau; p.y *= tau;
-                v = ri == 0 ? vfirst : V_[j0 + ri];
-                pr[ri] = p;
-                sp = v.x * p.x + v.y * p.y;
-            }
-            sp = warp_sum(sp);
-            if (lane == 0) sc.redA[warp] = sp;
+            for (int o = 16; o > 0; o >>= 1) racc = cadd(racc, cshfl_xor(racc, o));
+            if (lane == 0) pr[ri] = racc;
         }
         __syncthreads();
-
-        // ---- w = p - (tau s / 2) v, the explicit update of pivot column
-        // j0 with (v_k, w_k), d_j0, and the partial sums of ||x||^2 for the
-        // next reflector, whose entries past the first go to Vn.
-        if (warp < nact) {
-            const T K = T(0.5) * tau * sum_partials<T, NW>(sc.redA, nact);
-            const V p0 = pr[0];
-            const V w0 = mk(p0.x - K * vfirst.x, p0.y - K * vfirst.y);
-            T s2p = T(0);
-            if (mine) {
-                const V w = mk(p.x - K * v.x, p.y - K * v.y);
-                Wv[j0 + ri] = w;
-                V a = A[tri(j0 + ri) + j0];
-                a = cfms_conj_b(v, w0, a);
-                a = cfms_conj_b(w, vfirst, a);
-                if (ri == 0) d[j0] = double(a.x);
-                if (ri >= 1) s2p = cabs2(a);
-                if (ri >= 2) Vn[j0 + ri] = a;
-                if (ri == 1) sc.sx[0] = a;
-            }
-            s2p = warp_sum(s2p);
-            if (lane == 0) sc.redB[warp] = s2p;
-        }
-        __syncthreads();
-
-        // ---- ||x||^2, and the next reflector's first entry and tau.
-        if constexpr (kSharedTail) {
-            if (warp == 0) {
-                const T s2 = sum_partials<T, NW>(sc.redB, nact);
-                if (lane == 0) e2[j0] = double(s2);
-                if (k + 1 <= n - 3) {
-                    V f;
-                    T tn;
-                    reflector_head(s2, sc.sx[0], f, tn);
-                    if (lane == 0) { sc.sx[1] = f; sc.sx[2] = mk(tn, T(0)); }
-                }
-            }
-            __syncthreads();
-            if (k + 1 <= n - 3) { vfirst = sc.sx[1]; tau = sc.sx[2].x; }
-        } else {
-            const T s2 = sum_partials<T, NW>(sc.redB, nact);
-            if (tid == 0) e2[j0] = double(s2);
-            if (k + 1 <= n - 3) reflector_head(s2, sc.sx[0], vfirst, tau);
-        }
+        hh_scalar<T, NW, NMAX>(k, n, A, sc, d, e2, vfirst, tau);
     }
-
-    // Step n-3's update of the last diagonal entry.
-    if (tid == 0) {
-        const V v = Vb[((n - 3) & 1) * NMAX + n - 1];
-        const V w = Wv[n - 1];
-        const T ann = A[tri(n - 1) + n - 1].x - T(2) * (v.x * w.x + v.y * w.y);
-        d[n - 1] = double(ann);
-    }
-    __syncthreads();
+    hh_finish<T, NMAX>(n, A, sc, d);
 }
 
 // ---------------------------------------------------------------------------

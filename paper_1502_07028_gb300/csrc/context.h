@@ -99,6 +99,12 @@ struct ptca_ctx {
     double2* d_gA = nullptr;
     int64_t gA_stride = 0;
     int resolve_grid = 0;
+    // large traveling clusters (orders above the shared-memory kernels'):
+    // one global matrix slot per resident 16-warp CTA
+    bool large = false;
+    int large_grid = 0;
+    void* d_gL = nullptr;
+    int64_t gL_stride = 0;
     // precision checker (PTCA_MIXED): FP32-vs-FP64 spectra of every visit
     bool checker = false;
     int check_chunk = 0;

@@ -237,7 +237,7 @@ template <typename T>
 __global__ void __launch_bounds__(CTA) k_build(Model m, const double* __restrict__ S, const int32_t* __restrict__ sites,
                                                int count, const double* __restrict__ new_spins, cplx_t<T>* H,
                                                int64_t stride, int64_t* offsets, int32_t* nout) {
-    __shared__ double sp[3 * 128];
+    __shared__ double sp[3 * 256];  // window spins, up to 16x16 or 6x6x6 sites
     const int c = blockIdx.x;
     if (c >= count) return;
     const int site = sites[c];
@@ -332,6 +332,10 @@ struct StageArgs {
     unsigned int* flag_count;
     double2* gA;
     int64_t gA_stride;
+    // Large clusters (orders above the shared-memory kernels'): one global
+    // packed matrix of gL_stride elements (float2 or double2) per CTA.
+    void* gL;
+    int64_t gL_stride;
     // Delayed acceptance: work list (perm) length on the device, and the
     // stage-1 surrogate dF~ per stage index (stage 2 accepts iff
     // ln u < -(dF - dF~)/T).  Null when screening is off.
@@ -380,11 +384,12 @@ __device__ __forceinline__ void collect_sample(const StageArgs& a, const double*
 // One matrix of one update site of a stage: c indexes the stage's site list,
 // var 0/1 selects H_old/H_new.  The second of the pair to finish applies
 // Metropolis.  Called by all threads of the CTA; s_new and s_last are shared.
-template <typename T, int NT, int NWP>
+template <typename T, int NT, int NWP, bool kLarge = false>
 __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v, int c, int var, unsigned char* smem,
                                            double* s_new, int* s_last) {
-    const SmemLayout L = smem_layout(a.nA, 32 * NT, sizeof(cplx_t<T>), NWP);
+    const SmemLayout L = smem_layout(kLarge ? 0 : a.nA, 32 * NT, sizeof(cplx_t<T>), NWP);
     Carve<T> cv = carve<T>(smem, L, NWP);
+    if constexpr (kLarge) cv.A = static_cast<cplx_t<T>*>(a.gL) + (int64_t)blockIdx.x * a.gL_stride;
     c = v.perm ? v.perm[c] : c;
     const int site = v.sites[c];
     int n;
@@ -400,7 +405,8 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
     // The window's classical energy (Hubbard mean field), parked in this
     // matrix's F slot until the eigenvalues are known.
     if (threadIdx.x == 0 && a.m.ucl != 0.0) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
-    householder_tridiag<T, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
+    if constexpr (kLarge) householder_tridiag_large<T, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
+    else householder_tridiag<T, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
     tridiag_eig_F<T, NWP>(n, cv, a.m.mu - a.m.e0, a.m.T, false, nullptr, ssp, sfe, K);
@@ -529,7 +535,7 @@ __global__ void __launch_bounds__(CTA, 1) k_check_ref(StageArgs a, int c0, int c
 // kSmemA (a.nA up to about 150 fits beside the vectors in one CTA), else in
 // this CTA's global slot; the arithmetic is the same either way.  nmaxc =
 // 32 * NT sizes the vectors in shared memory.
-template <int NT, int NWP = NW, bool kSmemA = false>
+template <int NT, int NWP = NW, bool kSmemA = false, bool kLarge = false>
 __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, int c, int var, unsigned char* smem,
                                           double* s_new, int* s_last) {
     const SmemLayout L = smem_layout(kSmemA ? a.nA : 0, 32 * NT, sizeof(dfl2), NWP);
@@ -547,7 +553,8 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, 
     }
     __syncthreads();
     if (threadIdx.x == 0 && a.m.ucl != 0.0) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
-    householder_tridiag<dfl, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
+    if constexpr (kLarge) householder_tridiag_large<dfl, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
+    else householder_tridiag<dfl, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
     tridiag_eig_F<dfl, NWP>(n, cv, a.m.mu - a.m.e0, a.m.T, false, nullptr, ssp, sfe, K);
@@ -606,6 +613,48 @@ __global__ void __launch_bounds__(32 * RESOLVE_NW, 1) k_resolve(StageArgs a) {
     for (int item = blockIdx.x; item < 2 * nflag; item += gridDim.x) {
         const int c = a.flag_list[item >> 1];
         resolve_item<NT, RESOLVE_NW, kSmemA>(a, stage_var(a), c, item & 1, smem, s_new, &s_last);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Large traveling clusters (the paper's N_c = 12^2 and 16^2, orders up to
+// 32 NW_LARGE = 512): one CTA of NW_LARGE warps per matrix, the matrix in the
+// CTA's global slot (householder_tridiag_large), the vectors and the
+// eigenvalue stage in shared memory.  A grid of resident CTAs strides over
+// the (site, old/new) items, so that each CTA owns one slot.  Same stage
+// semantics, decisions and records as k_stage.
+// ---------------------------------------------------------------------------
+constexpr int NW_LARGE = 16;
+template <typename T>
+__global__ void __launch_bounds__(32 * NW_LARGE, 1) k_stage_large(StageArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    __shared__ int s_last;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.prev_count + a.prev2_count;
+         k += gridDim.x * blockDim.x) {
+        const int s = k < a.prev_count ? a.prev_sites[k] : a.prev2_sites[k - a.prev_count];
+        a.S_out[3 * s] = a.S_in[3 * s];
+        a.S_out[3 * s + 1] = a.S_in[3 * s + 1];
+        a.S_out[3 * s + 2] = a.S_in[3 * s + 2];
+    }
+    for (int item = blockIdx.x; item < 2 * a.count; item += gridDim.x) {
+        stage_item<T, NW_LARGE, NW_LARGE, true>(a, stage_var(a), item >> 1, item & 1, smem, s_new, &s_last);
+        __syncthreads();
+    }
+}
+
+// Double-float re-solve of a stage's deferred large-cluster decisions (matrix
+// in the CTA's global re-solve slot).
+template <int NWL = NW_LARGE>
+__global__ void __launch_bounds__(32 * NWL, 1) k_resolve_large(StageArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    __shared__ int s_last;
+    const int nflag = (int)*(volatile unsigned int*)a.flag_count;
+    for (int item = blockIdx.x; item < 2 * nflag; item += gridDim.x) {
+        const int c = a.flag_list[item >> 1];
+        resolve_item<NWL, NWL, false, true>(a, stage_var(a), c, item & 1, smem, s_new, &s_last);
         __syncthreads();
     }
 }

@@ -50,6 +50,16 @@ cudaError_t launch_check_compare(const Model& m, const int32_t* sites, int count
 cudaError_t launch_barrier_selftest(int blocks, unsigned int* bar, int32_t* err, unsigned long long timeout_ns,
                                     cudaStream_t st);
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
+// Large traveling clusters (orders above cluster_max_order, up to
+// large_max_order): one 16-warp CTA per matrix, the matrix in a global slot
+// per CTA (a.gL, gL_stride elements of float2/double2; the re-solve uses
+// a.gA), grid resident CTAs striding over the items.
+int large_max_order();
+size_t large_smem_bytes(int prec);
+cudaError_t configure_large_kernels(size_t smem_limit);
+int large_blocks_per_sm(int prec);
+cudaError_t launch_stage_large(int prec, const StageArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_resolve_large(const StageArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_observables(const double* S, int Lx, int Ly, const double* rec_Facc, const double* rec_fill,
                                const uint8_t* rec_acc, const int32_t* rec_n, int N, double* out, cudaStream_t st);
 

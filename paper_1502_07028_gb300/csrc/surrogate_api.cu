@@ -127,7 +127,7 @@ int32_t ptca_surrogate_param_count(void) { return ptca::SG_NPARAMS; }
 
 ptca_status ptca_surrogate_init(ptca_ctx* ctx, uint64_t seed, void* stream) {
     if (!ctx) return ptca_internal_fail(PTCA_ERR_INVALID, "null context");
-    if (ctx->p.model != PTCA_MODEL_DOUBLE_EXCHANGE || ctx->p.Lz > 1)
+    if (ctx->p.model != PTCA_MODEL_DOUBLE_EXCHANGE || ctx->p.Lz > 1 || ctx->large)
         return ptca_internal_fail(PTCA_ERR_UNSUPPORTED, "the surrogate screen is built for the double-exchange model on square lattices");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     SurrogateState& g = ctx->sg;

@@ -82,7 +82,8 @@ def test_schedule_matches_oracle(built, kw):
     (dict(Lx=8, Ly=8, L_c=9), "L_c"),
     (dict(Lx=12, Ly=12, L_c=8, schedule=P.SCHEDULE_BLOCK), "not exact"),
     (dict(Lx=8, Ly=8, L_c=4, T=0.0), "T > 0"),
-    (dict(Lx=66, Ly=66, L_c=11, precision=P.MIXED), "maximum"),
+    (dict(Lx=68, Ly=68, L_c=17, precision=P.MIXED), "maximum"),
+    (dict(Lx=56, Ly=56, Lz=7, L_c=7, precision=P.MIXED), "maximum"),
     (dict(Lx=8, Ly=8, L_c=4, update_offset=4), "update_offset"),
     (dict(Lx=8, Ly=1, Lz=4, L_c=2), "needs Ly > 1"),
     (dict(Lx=8, Ly=8, Lz=3, L_c=4), "L_c"),
@@ -153,3 +154,11 @@ def test_stage_split_of_the_100x100_block_schedule(built):
     cfg = P.Config(Lx=100, Ly=100, L_c=8, schedule=P.SCHEDULE_BLOCK, precision=P.MIXED)
     split = P.ptca_stage_split(cfg)
     assert [n for _, n in split] == [2500 - 49, 2500 - 350, 2500 - 49, 2500 - 350]
+
+
+@pytest.mark.parametrize("Lc", [11, 12, 16])
+def test_large_clusters_are_accepted(built, Lc):
+    # Orders above the shared-memory kernels' (2 N_c = 242, 288, 512) go to
+    # the large-cluster path; the schedule is the same rule.
+    stages = P.ptca_schedule(P.Config(Lx=2 * Lc, Ly=2 * Lc, L_c=Lc, schedule=P.SCHEDULE_BLOCK, precision=P.MIXED))
+    assert len(stages) == 4 and sum(st.size for st in stages) == 4 * Lc * Lc
