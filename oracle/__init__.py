@@ -44,6 +44,7 @@ SCHEDULE_TILED = 0
 SCHEDULE_BLOCK = 1
 MODEL_DOUBLE_EXCHANGE = 0
 MODEL_HUBBARD_MF = 1
+MODEL_HOLSTEIN = 2
 PROPOSAL_SPHERE = 0
 PROPOSAL_CONE = 1
 
@@ -75,6 +76,7 @@ class _Model(ctypes.Structure):
         ("model", ctypes.c_int32), ("pad0", ctypes.c_int32),
         ("U", ctypes.c_double), ("m_step", ctypes.c_double),
         ("Lz", ctypes.c_int32), ("oz", ctypes.c_int32),
+        ("lam", ctypes.c_double), ("K", ctypes.c_double),
     ]
 
 
@@ -104,6 +106,8 @@ class Model:
     m_step: float = 0.5
     Lz: int = 1
     oz: int = -1
+    lam: float = 1.0
+    K: float = 1.0
 
     def _c(self) -> _Model:
         off = (self.Lc // 2) if self.schedule == SCHEDULE_TILED else 0
@@ -115,7 +119,7 @@ class Model:
         return _Model(self.Lx, self.Ly, self.lattice_periodic, self.Lc, ox, oy, cp,
                       self.schedule, stride, self.proposal, self.t, self.JH,
                       self.mu, self.T, self.cone_deg, self.seed, self.model, 0, self.U, self.m_step,
-                      self.Lz, oz)
+                      self.Lz, oz, self.lam, self.K)
 
     @property
     def N(self) -> int:

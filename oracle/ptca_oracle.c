@@ -28,7 +28,13 @@
  *   model 1, Hubbard mean field (Eq. 1, <n_i> = 1): an on-site term
  *     (U/2)(n_i - m_i . sigma_i) with classical vectors m_i of any length, and
  *     the classical energy (U/4)(m_i^2 - 1) of every site, which the cluster
- *     free energy includes for the sites of its window.
+ *     free energy includes for the sites of its window;
+ *   model 2, adiabatic Holstein (the model of Sec. VII.b): a classical
+ *     distortion x_i per site (component 0 of the site's vector; the other
+ *     two stay 0), the one-body term lambda x_i n_i, and the classical energy
+ *     K/2 x_i^2 - lambda x_i + mu of every window site (the rest of
+ *     (lambda x_i - mu)(n_i - 1) + K/2 x_i^2; -mu n_i is the chemical
+ *     potential of the free energy).
  */
 #include <complex.h>
 #include <math.h>
@@ -61,6 +67,8 @@ typedef struct {
     double m_step;             /* model 1: radius of the proposal ball           */
     int32_t Lz;                /* third extent; 1 for a square lattice or chain  */
     int32_t oz;                /* update-site position along z                    */
+    double lam;                /* model 2: electron-lattice coupling lambda      */
+    double K;                  /* model 2: elastic constant                      */
 } oracle_model;
 
 /* Sites: index (z Ly + y) Lx + x.  Lz > 1 needs Ly > 1 (cubic lattice). */
@@ -128,14 +136,21 @@ static void sphere_point(const double u[2], double s[3])
     s[2] = z;
 }
 
-/* Initial classical spins: independent, uniform on the sphere. */
+/* Initial classical variables: independent unit vectors uniform on the
+ * sphere (models 0, 1); distortions x_i uniform in [-1, 1] (model 2). */
 void oracle_init_spins(const oracle_model* m, double* S)
 {
     int N = n_sites(m);
     for (int i = 0; i < N; ++i) {
         double u[2];
         oracle_uniform2(m->seed, 0, (uint32_t)i, PURPOSE_INIT, u);
-        sphere_point(u, S + 3 * i);
+        if (m->model == 2) {
+            S[3 * i] = 2.0 * u[0] - 1.0;
+            S[3 * i + 1] = 0.0;
+            S[3 * i + 2] = 0.0;
+        } else {
+            sphere_point(u, S + 3 * i);
+        }
     }
 }
 
@@ -147,6 +162,14 @@ void oracle_propose(const oracle_model* m, uint64_t sweep, int site, const doubl
 {
     double u[2];
     oracle_uniform2(m->seed, sweep, (uint32_t)site, PURPOSE_PROPOSE, u);
+    if (m->model == 2) {
+        /* Holstein: x_new = x_old + m_step (2u - 1), uniform in
+         * [x_old - m_step, x_old + m_step]; symmetric. */
+        s_new[0] = s_old[0] + m->m_step * (2.0 * u[0] - 1.0);
+        s_new[1] = s_old[1];
+        s_new[2] = s_old[2];
+        return;
+    }
     if (m->model == 1) {
         /* Hubbard mean field: m_new = m_old + d, d uniform in the ball of
          * radius m_step (direction uniform on the sphere, radius
@@ -247,11 +270,11 @@ int oracle_cluster_hamiltonian(const oracle_model* m, const double* S, int site,
             int g = window_site(m, &win, wx, wy, wz);
             const double* s = S + 3 * g;
             if (s_new && g == site) s = s_new;
-            /* On-site 2x2 spin block: -J_H S.sigma (model 0), or
-             * (U/2) 1 - (U/2) m.sigma (model 1). */
+            /* On-site 2x2 spin block: -J_H S.sigma (model 0),
+             * (U/2) 1 - (U/2) m.sigma (model 1), or lambda x 1 (model 2). */
             int a = 2 * w, b = 2 * w + 1;
-            double J = m->model == 1 ? 0.5 * m->U : m->JH;
-            double e0 = m->model == 1 ? 0.5 * m->U : 0.0;
+            double J = m->model == 1 ? 0.5 * m->U : (m->model == 2 ? 0.0 : m->JH);
+            double e0 = m->model == 1 ? 0.5 * m->U : (m->model == 2 ? m->lam * s[0] : 0.0);
             H[a * n + a] += e0 - J * s[2];
             H[b * n + b] += e0 + J * s[2];
             H[a * n + b] += -J * (s[0] - I * s[1]);
@@ -354,12 +377,13 @@ double oracle_free_energy(int n, const double* eig, double mu, double T)
     return -T * acc;
 }
 
-/* Classical energy of the window of update site `site` (model 1: the sum of
- * (U/4)(m_i^2 - 1) over its sites, m of the update site replaced by s_new
- * when given; model 0: zero). */
+/* Classical energy of the window of update site `site`: the sum over its
+ * sites of (U/4)(m_i^2 - 1) (model 1) or K/2 x_i^2 - lambda x_i + mu
+ * (model 2), the update site's variable replaced by s_new when given; zero
+ * for model 0. */
 static double window_classical(const oracle_model* m, const double* S, int site, const double* s_new)
 {
-    if (m->model != 1) return 0.0;
+    if (m->model != 1 && m->model != 2) return 0.0;
     window win = window_of(m, site);
     double acc = 0.0;
     for (int wz = 0; wz < win.ez; ++wz)
@@ -367,7 +391,10 @@ static double window_classical(const oracle_model* m, const double* S, int site,
         for (int wx = 0; wx < win.ex; ++wx) {
             int g = window_site(m, &win, wx, wy, wz);
             const double* v = (s_new && g == site) ? s_new : S + 3 * g;
-            acc += 0.25 * m->U * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] - 1.0);
+            if (m->model == 1)
+                acc += 0.25 * m->U * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] - 1.0);
+            else
+                acc += 0.5 * m->K * v[0] * v[0] - m->lam * v[0] + m->mu;
         }
     return acc;
 }
