@@ -41,7 +41,7 @@ HH_FLOPS = sum(32 * m * (m + 1) // 2 for m in range(1, N_ORDER))
 # (a launch's bytes / the matrices it solved; a launch's traffic is this
 # times its matrices).  A value goes back to None whenever its kernel
 # changes, until captured again.
-DRAM_BYTES_PER_MATRIX = {"k_stage<float,4,8>": None, "k_stage<float,4,4>": 312_320 / 4902,
+DRAM_BYTES_PER_MATRIX = {"k_stage<float,4,8>": None, "k_stage<float,4,4>": 330_496 / 4902,
                          "k_sweep_persistent<float,4,8>": None, "k_sweep_persistent<float,4,4>": None}
 
 
@@ -384,6 +384,34 @@ def large_cluster_mode(P, args, flush, stream, rank):
     return out
 
 
+def holstein_mode(P, args, flush, stream, rank):
+    """The adiabatic Holstein chain of Sec. VII.b at scale: 65536 sites,
+    N_c = 8 (n = 16), lambda = 1.5, K = 1, half filling (mu = 0), T = 0.1,
+    central update site (tiled schedule, stride 8), distortion steps of
+    half-width 0.4.  Mixed guarded (autotuned) and the plain FP64 path."""
+    base = dict(Lx=65536, Ly=1, L_c=8, periodic=1, t=1.0, lam=1.5, K=1.0, mu=0.0, T=0.1, seed=rank, m_step=0.4,
+                model=P.MODEL_HOLSTEIN, schedule=P.SCHEDULE_TILED, stride=8, update_offset=4)
+    N = 65536
+    ctx = P.Context(P.Config(**base, precision=P.MIXED))
+    best, _ = P.ptca_autotune(ctx.h, 2)
+    steps = max(3, args.steps // 2)
+    ms = time_sweeps(ctx, steps, 2, flush, stream)
+    st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
+    obs = P.ptca_observables(ctx.h, stream=stream)
+    ctx.close()
+    out = {"workload": "Holstein chain (Sec. VII.b), 65536 sites, N_c=8 (n=16), lambda=1.5, K=1, mu=0, T=0.1, "
+                       "central update site, tiled stride 8",
+           "value": N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
+           "resolved_fraction": st.resolved / st.attempts, "acceptance": st.accepted / st.attempts,
+           "N_pi": obs.S_pipi,
+           "launch": {"pipeline": best.pipeline, "warps_per_cta": best.warps_per_cta, "ctas_per_sm": best.ctas_per_sm}}
+    ctx = P.Context(P.Config(**base, precision=P.FP64))
+    ms64 = time_sweeps(ctx, 2, 1, flush, stream)
+    ctx.close()
+    out["fp64_path"] = {"value": N * 2 / (sum(ms64) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms64) / 2}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,7 +424,7 @@ def main():
     ap.add_argument("--sg-sweeps", type=int, default=20, help="exact sweeps collected to train the surrogate")
     ap.add_argument("--sg-train-steps", type=int, default=3000)
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the surrogate, uneven-batch, Hubbard-model and large-cluster measurements")
+                    help="skip the surrogate, uneven-batch, Hubbard, large-cluster and Holstein measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -486,6 +514,7 @@ def main():
         extra["hubbard_mf"] = hubbard_mode(P, args, flush, stream, rank)
         extra["hubbard_mf_3d"] = hubbard_mode(P, args, flush, stream, rank, Lz=40)
         extra["large_clusters"] = large_cluster_mode(P, args, flush, stream, rank)
+        extra["holstein_chain"] = holstein_mode(P, args, flush, stream, rank)
 
     # --- plain FP64 GPU path on the same workload
     ctx64 = P.Context(P.Config(**base, precision=P.FP64))

@@ -60,7 +60,7 @@ typedef enum {
 enum { PTCA_SCHEDULE_TILED = 0, PTCA_SCHEDULE_BLOCK = 1 };
 enum { PTCA_FP64 = 0, PTCA_MIXED = 1 };
 enum { PTCA_PROPOSAL_SPHERE = 0, PTCA_PROPOSAL_CONE = 1 };
-enum { PTCA_MODEL_DOUBLE_EXCHANGE = 0, PTCA_MODEL_HUBBARD_MF = 1 };
+enum { PTCA_MODEL_DOUBLE_EXCHANGE = 0, PTCA_MODEL_HUBBARD_MF = 1, PTCA_MODEL_HOLSTEIN = 2 };
 enum { PTCA_PIPELINE_STAGES = 0, PTCA_PIPELINE_PERSISTENT = 1, PTCA_PIPELINE_GRAPH = 2, PTCA_PIPELINE_OVERLAP = 3 };
 
 /* Square lattice, chain or cubic lattice.  Ly == 1 is a one-dimensional chain
@@ -83,7 +83,15 @@ typedef struct {
  *                               site in the cluster free energy; proposals
  *                               m_new = m_old + a step uniform in the ball of
  *                               radius m_step.  Spins, S(q) and the records then
- *                               hold the fields m_i. */
+ *                               hold the fields m_i;
+ *   PTCA_MODEL_HOLSTEIN         the adiabatic Holstein model (Sec. VII.b):
+ *                               one classical distortion x_i per site (component
+ *                               0 of the site's vector, the others 0), the
+ *                               one-body term lambda x_i n_i, and the classical
+ *                               energy K/2 x_i^2 - lambda x_i + mu of every window
+ *                               site in the cluster free energy; initial x
+ *                               uniform in [-1, 1], proposals x + m_step (2u - 1).
+ *                               S(q) is then the charge structure factor N(q). */
 typedef struct {
     double t;                 /* hopping                                              */
     double J_H;               /* Hund coupling (double exchange)                      */
@@ -101,11 +109,14 @@ typedef struct {
     int32_t precision;        /* PTCA_FP64 or PTCA_MIXED (FP32 reduction to tridiagonal */
                               /* form; FP64 eigenvalues, free energies and dF)        */
     int32_t proposal;         /* PTCA_PROPOSAL_SPHERE or PTCA_PROPOSAL_CONE            */
-    int32_t model;            /* PTCA_MODEL_DOUBLE_EXCHANGE (0) or PTCA_MODEL_HUBBARD_MF */
+    int32_t model;            /* PTCA_MODEL_DOUBLE_EXCHANGE, _HUBBARD_MF or _HOLSTEIN   */
     double cone_deg;          /* half-angle of the cone proposal, degrees             */
     uint64_t seed;            /* key of the counter-based generator                   */
     double U;                 /* Hubbard U (PTCA_MODEL_HUBBARD_MF), finite            */
-    double m_step;            /* radius of the field proposal ball (Hubbard), > 0     */
+    double m_step;            /* Hubbard: radius of the field proposal ball; Holstein: */
+                              /* half-width of the distortion step; > 0               */
+    double lam;               /* Holstein electron-lattice coupling lambda, finite    */
+    double K;                 /* Holstein elastic constant, finite                    */
 } ptca_params;
 
 /* Per-call sweep statistics (host struct filled by ptca_sweep when non-NULL). */

@@ -213,10 +213,16 @@ ptca_status resolve(const ptca_lattice* lat, const ptca_params* par, Problem& p)
     p.model = par->model;
     p.U = par->U;
     p.m_step = par->m_step;
-    if (p.model != PTCA_MODEL_DOUBLE_EXCHANGE && p.model != PTCA_MODEL_HUBBARD_MF)
+    p.lam = par->lam;
+    p.K = par->K;
+    if (p.model != PTCA_MODEL_DOUBLE_EXCHANGE && p.model != PTCA_MODEL_HUBBARD_MF && p.model != PTCA_MODEL_HOLSTEIN)
         return fail(PTCA_ERR_INVALID, "unknown model");
-    if (p.model == PTCA_MODEL_HUBBARD_MF && (!std::isfinite(p.U) || !(p.m_step > 0) || !std::isfinite(p.m_step)))
-        return fail(PTCA_ERR_INVALID, "Hubbard mean field needs a finite U and a finite m_step > 0");
+    if (p.model != PTCA_MODEL_DOUBLE_EXCHANGE && (!(p.m_step > 0) || !std::isfinite(p.m_step)))
+        return fail(PTCA_ERR_INVALID, "the Hubbard and Holstein models need a finite m_step > 0");
+    if (p.model == PTCA_MODEL_HUBBARD_MF && !std::isfinite(p.U))
+        return fail(PTCA_ERR_INVALID, "Hubbard mean field needs a finite U");
+    if (p.model == PTCA_MODEL_HOLSTEIN && (!std::isfinite(p.lam) || !std::isfinite(p.K)))
+        return fail(PTCA_ERR_INVALID, "Holstein needs finite lambda and K");
     if (!std::isfinite(p.t) || !std::isfinite(p.JH) || !std::isfinite(p.mu) || !std::isfinite(p.T) || !(p.T > 0))
         return fail(PTCA_ERR_INVALID, "t, J_H, mu must be finite and T > 0");
     if (p.proposal == PTCA_PROPOSAL_CONE && !(p.cone_deg > 0 && p.cone_deg <= 180))
@@ -233,12 +239,7 @@ Model to_model(const Problem& p) {
     m.proposal = p.proposal;
     m.t = p.t; m.mu = p.mu; m.T = p.T;
     m.cone_cos = std::cos(p.cone_deg * ptca::kPi / 180.0);
-    m.model = p.model;
-    if (p.model == PTCA_MODEL_HUBBARD_MF) {
-        m.JH = 0.5 * p.U; m.e0 = 0.5 * p.U; m.ucl = 0.25 * p.U; m.m_step = p.m_step;
-    } else {
-        m.JH = p.JH; m.e0 = 0.0; m.ucl = 0.0; m.m_step = 0.0;
-    }
+    ptca::set_model_terms(m, p.model, p.JH, p.U, p.lam, p.K, p.mu, p.m_step);
     m.seed = p.seed;
     return m;
 }

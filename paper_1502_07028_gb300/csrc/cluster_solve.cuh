@@ -15,17 +15,22 @@
 namespace ptca {
 
 // Problem description the kernels need (copied by value into each launch).
-// Problem on the device.  model 0 (double exchange): on-site -JH S.sigma with
-// unit spins.  model 1 (Hubbard mean field, Eq. 1 with <n_i> = 1): on-site
-// e0 - JH m.sigma with JH = e0 = U/2, classical energy ucl (|m|^2 - 1) per
-// window site with ucl = U/4, proposals uniform in a ball of radius m_step.
+// Problem on the device.  The on-site block of site i with classical vector
+// v_i is (e0 + lam v_x) 1 - JH v.sigma, and the cluster free energy adds
+// ca |v|^2 + cb v_x + cc per window site when cls_on:
+//   model 0 (double exchange): JH = J_H, unit spins, no classical term;
+//   model 1 (Hubbard mean field, Eq. 1, <n_i> = 1): JH = e0 = U/2,
+//     ca = U/4, cc = -U/4, proposals uniform in a ball of radius m_step;
+//   model 2 (adiabatic Holstein): lam = lambda, v = (x, 0, 0), ca = K/2,
+//     cb = -lambda, cc = mu, proposals x + m_step (2u - 1).
 struct Model {
     int32_t Lx, Ly, Lz, lattice_periodic;   // Lz == 1: square lattice or chain
     int32_t Lc, ox, oy, oz, cluster_periodic;
     int32_t proposal;
     int32_t model;
+    int32_t cls_on;
     double t, JH, mu, T, cone_cos;
-    double e0, ucl, m_step;
+    double e0, lam, ca, cb, cc, m_step;
     uint64_t seed;
 };
 
@@ -76,9 +81,18 @@ __device__ __forceinline__ int tri(int r) { return (r * (r + 1)) >> 1; }
 // exchange: propose_spin (sphere or cone).  Hubbard mean field: the old field
 // plus a step uniform in the ball of radius m_step -- direction from the
 // proposal uniforms (as the sphere proposal), length m_step v^(1/3) with v
-// the first uniform of purpose RNG_RADIUS; symmetric in (old, new).
+// the first uniform of purpose RNG_RADIUS.  Holstein: x + m_step (2u - 1).
+// All are symmetric in (old, new).
 __device__ __forceinline__ void propose(const Model& m, uint64_t sweep, uint32_t site, const double so[3],
                                         double sn[3]) {
+    if (m.model == 2) {
+        double u0, u1;
+        uniform2(m.seed, sweep, site, RNG_PROPOSE, u0, u1);
+        sn[0] = so[0] + m.m_step * (2.0 * u0 - 1.0);
+        sn[1] = so[1];
+        sn[2] = so[2];
+        return;
+    }
     if (m.model != 1) {
         propose_spin(m.seed, sweep, site, m.proposal, m.cone_cos, so, sn);
         return;
@@ -93,21 +107,23 @@ __device__ __forceinline__ void propose(const Model& m, uint64_t sweep, uint32_t
     sn[2] = so[2] + r * dir[2];
 }
 
-// Classical energy of a window (Hubbard mean field): ucl (|m|^2 - 1) summed
-// over its nsite vectors sp[nsite][3]; zero for the double-exchange model.
-// One thread.
+// Classical energy of a window: ca |v|^2 + cb v_x + cc summed over its nsite
+// vectors sp[nsite][3] (zero unless cls_on).  One thread.
 __device__ __forceinline__ double window_classical(const Model& m, const double* sp, int nsite) {
-    if (m.ucl == 0.0) return 0.0;
+    if (!m.cls_on) return 0.0;
     double acc = 0.0;
-    for (int s = 0; s < nsite; ++s)
-        acc += m.ucl * (sp[3 * s] * sp[3 * s] + sp[3 * s + 1] * sp[3 * s + 1] + sp[3 * s + 2] * sp[3 * s + 2] - 1.0);
+    for (int s = 0; s < nsite; ++s) {
+        const double v0 = sp[3 * s], v1 = sp[3 * s + 1], v2 = sp[3 * s + 2];
+        acc += m.ca * (v0 * v0 + v1 * v1 + v2 * v2) + m.cb * v0 + m.cc;
+    }
     return acc;
 }
 
 // Gather the window spins into sp[nsite][3] (replacing the update site's spin
 // by s_new when s_new != nullptr) and build the packed cluster matrix:
-//   on-site block  e0 - J [[S_z, S_x - i S_y], [S_x + i S_y, -S_z]] per site
-//                  (J = m.JH; e0 is the caller's diagonal shift),
+//   on-site block  (e0 + lam S_x) - J [[S_z, S_x - i S_y], [S_x + i S_y, -S_z]]
+//                  per site (J = m.JH, lam = m.lam; e0 is the caller's
+//                  diagonal shift),
 //   hopping        -t between nearest neighbours (x, y and, on a cubic
 //                  lattice, z), same spin, each bond once;
 // a periodic cluster wraps inside the window (an axis of extent 2 then has
@@ -131,13 +147,14 @@ __device__ void build_cluster(const Model& m, const Window& w, const double* __r
         sp[3 * s] = v0; sp[3 * s + 1] = v1; sp[3 * s + 2] = v2;
     }
     __syncthreads();
-    const T t = T(m.t), J = T(m.JH), d0 = T(e0);
+    const T t = T(m.t), J = T(m.JH), d0 = T(e0), lam = T(m.lam);
     for (int s = threadIdx.x; s < nsite; s += blockDim.x) {
         const int wx = s % w.ex, wy = (s / w.ex) % w.ey, wz = s / exy;
         const T sx = T(sp[3 * s]), sy = T(sp[3 * s + 1]), sz = T(sp[3 * s + 2]);
         const int a = 2 * s, b = 2 * s + 1;
-        A[tri(a) + a] = mk(d0 - J * sz, T(0));
-        A[tri(b) + b] = mk(d0 + J * sz, T(0));
+        const T dg = d0 + lam * sx;
+        A[tri(a) + a] = mk(dg - J * sz, T(0));
+        A[tri(b) + b] = mk(dg + J * sz, T(0));
         A[tri(b) + a] = mk(-J * sx, -J * sy);  // element (b, a) = -J_H (S_x + i S_y)
         // +x bond
         int nb = -1, mult = 1;

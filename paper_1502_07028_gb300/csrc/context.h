@@ -11,7 +11,7 @@
 // Resolved problem (defaults filled in).
 struct Problem {
     int Lx, Ly, Lz, periodic, Lc, ox, oy, oz, cluster_periodic, schedule, stride, precision, proposal, model;
-    double t, JH, mu, T, cone_deg, U, m_step;
+    double t, JH, mu, T, cone_deg, U, m_step, lam, K;
     uint64_t seed;
     int N() const { return Lx * Ly * Lz; }
     int nsite_max() const { return Lc * (Ly == 1 ? 1 : Lc) * (Lz == 1 ? 1 : Lc); }

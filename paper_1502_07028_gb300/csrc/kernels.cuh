@@ -404,14 +404,14 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
     __syncthreads();
     // The window's classical energy (Hubbard mean field), parked in this
     // matrix's F slot until the eigenvalues are known.
-    if (threadIdx.x == 0 && a.m.ucl != 0.0) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
+    if (threadIdx.x == 0 && a.m.cls_on) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
     if constexpr (kLarge) householder_tridiag_large<T, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     else householder_tridiag<T, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
     tridiag_eig_F<T, NWP>(n, cv, a.m.mu - a.m.e0, a.m.T, false, nullptr, ssp, sfe, K);
     if (threadIdx.x == 0) {
-        const double F = -a.m.T * ssp + (a.m.ucl != 0.0 ? a.Fbuf[2 * c + var] : 0.0);
+        const double F = -a.m.T * ssp + (a.m.cls_on ? a.Fbuf[2 * c + var] : 0.0);
         a.Fbuf[2 * c + var] = F;
         a.fillbuf[2 * c + var] = sfe;
         __threadfence();
@@ -552,14 +552,14 @@ __device__ __noinline__ void resolve_item(const StageArgs& a, const StageVar v, 
         build_cluster<dfl>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && a.m.ucl != 0.0) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
+    if (threadIdx.x == 0 && a.m.cls_on) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
     if constexpr (kLarge) householder_tridiag_large<dfl, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     else householder_tridiag<dfl, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     double ssp, sfe;
     int K;
     tridiag_eig_F<dfl, NWP>(n, cv, a.m.mu - a.m.e0, a.m.T, false, nullptr, ssp, sfe, K);
     if (threadIdx.x == 0) {
-        a.Fbuf[2 * c + var] = -a.m.T * ssp + (a.m.ucl != 0.0 ? a.Fbuf[2 * c + var] : 0.0);
+        a.Fbuf[2 * c + var] = -a.m.T * ssp + (a.m.cls_on ? a.Fbuf[2 * c + var] : 0.0);
         a.fillbuf[2 * c + var] = sfe;
         __threadfence();
         *s_last = (atomicAdd(&a.ticket[c], 1) == 1);

@@ -152,13 +152,31 @@ cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStre
 }
 
 // Initial spins: uniform on the sphere from the counter generator.
+// Initial classical variables: unit vectors uniform on the sphere; for the
+// Holstein model distortions x uniform in [-1, 1] in component 0.
 __global__ void k_init_spins(Model m, double* __restrict__ S, int N) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double u0, u1, s[3];
     uniform2(m.seed, 0, (uint32_t)i, RNG_INIT, u0, u1);
-    unit_from_uniforms(u0, u1, s);
+    if (m.model == 2) {
+        s[0] = 2.0 * u0 - 1.0; s[1] = 0.0; s[2] = 0.0;
+    } else {
+        unit_from_uniforms(u0, u1, s);
+    }
     S[3 * i] = s[0]; S[3 * i + 1] = s[1]; S[3 * i + 2] = s[2];
+}
+
+void set_model_terms(Model& m, int model, double J_H, double U, double lam, double K, double mu, double m_step) {
+    m.model = model;
+    m.JH = 0.0; m.e0 = 0.0; m.lam = 0.0; m.ca = 0.0; m.cb = 0.0; m.cc = 0.0; m.m_step = 0.0; m.cls_on = 0;
+    if (model == 1) {
+        m.JH = 0.5 * U; m.e0 = 0.5 * U; m.ca = 0.25 * U; m.cc = -0.25 * U; m.m_step = m_step; m.cls_on = 1;
+    } else if (model == 2) {
+        m.lam = lam; m.ca = 0.5 * K; m.cb = -lam; m.cc = mu; m.m_step = m_step; m.cls_on = 1;
+    } else {
+        m.JH = J_H;
+    }
 }
 
 cudaError_t launch_init_spins(const Model& m, double* S, int N, cudaStream_t st) {

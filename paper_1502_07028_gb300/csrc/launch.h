@@ -20,6 +20,10 @@ int cluster_max_order(int prec);
 cudaError_t configure_cluster_kernels(size_t smem_limit);
 
 cudaError_t launch_init_spins(const Model& m, double* S, int N, cudaStream_t st);
+// The model-dependent fields of m (coupling, on-site terms, classical energy,
+// proposal step) for model 0 (double exchange), 1 (Hubbard mean field) or 2
+// (Holstein).
+void set_model_terms(Model& m, int model, double J_H, double U, double lam, double K, double mu, double m_step);
 cudaError_t launch_copy_sites(const double* src, double* dst, const int32_t* sites, int count, cudaStream_t st);
 cudaError_t launch_build(int prec, const Model& m, const double* S, const int32_t* sites, int count,
                          const double* new_spins, void* H, int64_t stride, int64_t* offsets, int32_t* nout,

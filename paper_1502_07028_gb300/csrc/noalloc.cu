@@ -123,12 +123,8 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
     m.proposal = params->proposal;
     m.t = params->t; m.mu = params->mu; m.T = params->T;
     m.cone_cos = std::cos(params->cone_deg * ptca::kPi / 180.0);
-    m.model = params->model;
-    if (params->model == PTCA_MODEL_HUBBARD_MF) {
-        m.JH = 0.5 * params->U; m.e0 = 0.5 * params->U; m.ucl = 0.25 * params->U; m.m_step = params->m_step;
-    } else {
-        m.JH = params->J_H; m.e0 = 0.0; m.ucl = 0.0; m.m_step = 0.0;
-    }
+    ptca::set_model_terms(m, params->model, params->J_H, params->U, params->lam, params->K, params->mu,
+                          params->m_step);
     m.seed = params->seed;
     const int prec = params->precision == PTCA_MIXED ? 1 : 0;
     const int nA = 2 * Lc * (lattice->Ly == 1 ? 1 : Lc) * (Lz == 1 ? 1 : Lc);

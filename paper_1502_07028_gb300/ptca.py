@@ -23,7 +23,7 @@ SCHEDULE_TILED, SCHEDULE_BLOCK = 0, 1
 PIPELINE_STAGES, PIPELINE_PERSISTENT, PIPELINE_GRAPH, PIPELINE_OVERLAP = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 PROPOSAL_SPHERE, PROPOSAL_CONE = 0, 1
-MODEL_DOUBLE_EXCHANGE, MODEL_HUBBARD_MF = 0, 1
+MODEL_DOUBLE_EXCHANGE, MODEL_HUBBARD_MF, MODEL_HOLSTEIN = 0, 1, 2
 
 EXPORTED = [
     "ptca_init", "ptca_destroy", "ptca_set_T", "ptca_set_mu", "ptca_get_spins", "ptca_set_spins",
@@ -59,6 +59,7 @@ class Params(ctypes.Structure):
         ("schedule", ctypes.c_int32), ("stride", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("proposal", ctypes.c_int32), ("model", ctypes.c_int32), ("cone_deg", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("U", ctypes.c_double), ("m_step", ctypes.c_double),
+        ("lam", ctypes.c_double), ("K", ctypes.c_double),
     ]
 
 
@@ -190,6 +191,8 @@ class Config:
     U: float = 8.0
     m_step: float = 0.5
     Lz: int = 1
+    lam: float = 1.0
+    K: float = 1.0
 
     def lattice(self) -> Lattice:
         return Lattice(self.Lx, self.Ly, self.periodic, self.Lz)
@@ -197,7 +200,7 @@ class Config:
     def params(self) -> Params:
         return Params(self.t, self.J_H, self.mu, self.T, self.L_c, self.cluster_periodic, self.update_offset,
                       self.schedule, self.stride, self.precision, self.proposal, self.model, self.cone_deg,
-                      self.seed, self.U, self.m_step)
+                      self.seed, self.U, self.m_step, self.lam, self.K)
 
     @property
     def N(self) -> int:

@@ -38,7 +38,8 @@ def _oracle_model(cfg: P.Config) -> oracle.Model:
                         lattice_periodic=cfg.periodic, cluster_periodic=cfg.cluster_periodic,
                         schedule=cfg.schedule, stride=cfg.stride, proposal=cfg.proposal,
                         cone_deg=cfg.cone_deg, seed=cfg.seed, ox=cfg.update_offset, oy=cfg.update_offset,
-                        model=cfg.model, U=cfg.U, m_step=cfg.m_step, Lz=cfg.Lz, oz=cfg.update_offset)
+                        model=cfg.model, U=cfg.U, m_step=cfg.m_step, Lz=cfg.Lz, oz=cfg.update_offset,
+                        lam=cfg.lam, K=cfg.K)
 
 
 def _unpack(packed: np.ndarray, n: int) -> np.ndarray:
