@@ -430,12 +430,14 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
         if (c->grid <= 0) c->pipeline = PTCA_PIPELINE_STAGES;
         if (c->large) {
             // One global matrix slot per resident CTA of the large-cluster
-            // stage kernel (+ 64 elements of padding, as below).
+            // stage kernel, twice: the overlapped pipeline runs a stage's
+            // independent and dependent visits as concurrent launches, each
+            // on its own half (+ 64 elements of padding, as below).
             c->large_grid = sms * std::max(1, ptca::large_blocks_per_sm(c->prec));
             c->gL_stride = (int64_t)c->nA * (c->nA + 1) / 2;
             const size_t es = c->prec == 1 ? sizeof(float2) : sizeof(double2);
             void* q = nullptr;
-            ce = cudaMalloc(&q, ((size_t)c->large_grid * (size_t)c->gL_stride + 64) * es);
+            ce = cudaMalloc(&q, (2 * (size_t)c->large_grid * (size_t)c->gL_stride + 64) * es);
             c->d_gL = q;
         }
         if (ce == cudaSuccess && c->prec == 1) {
@@ -752,6 +754,10 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         StageArgs ad = a;
         ad.perm = ctx->d_split + ctx->h_start[s] + ni;
         ad.count = cnt - ni;
+        if (ctx->large) {  // concurrent with ai: the second half of the large-cluster slots
+            const size_t es = ctx->prec == 1 ? sizeof(float2) : sizeof(double2);
+            ad.gL = static_cast<char*>(ctx->d_gL) + (size_t)ctx->large_grid * (size_t)ctx->gL_stride * es;
+        }
         // sites buffer g+1 mod 3 lacks: those of stages g-2 and g-1 (each
         // only if it is not stage g itself, whose visits write every site)
         if (g >= 1 && (g - 1) % ns != s) stage_sites(g - 1, ad.prev_sites, ad.prev_count);

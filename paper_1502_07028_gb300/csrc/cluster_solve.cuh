@@ -648,15 +648,30 @@ __device__ void householder_tridiag_large(int n, cplx_t<T>* A, const HHScratch<T
             const V ui = U_[i], wi = Wv[i], vi = ri == 0 ? vfirst : V_[i];
             V* row = A + tri(i) + j0;
             V racc = zero;
-            for (int jr = lane; jr <= ri; jr += 32) {
-                const int j = j0 + jr;
-                const V vj = jr == 0 ? vfirst : V_[j];
-                V a = row[jr];
-                a = cfms_conj_b(ui, Wv[j], a);
-                a = cfms_conj_b(wi, U_[j], a);
-                row[jr] = a;
-                racc = cfma(a, vj, racc);
-                if (jr < ri) pcw[jr] = cfma_conj_a(a, vi, pcw[jr]);
+            // Four columns per lane at a time: their global loads are issued
+            // together (the additions keep the column order).
+            constexpr int LU = 4;
+            for (int jb = 0; jb <= ri; jb += 32 * LU) {
+                V av[LU];
+#pragma unroll
+                for (int q = 0; q < LU; ++q) {
+                    const int jr = jb + 32 * q + lane;
+                    av[q] = jr <= ri ? row[jr] : zero;
+                }
+#pragma unroll
+                for (int q = 0; q < LU; ++q) {
+                    const int jr = jb + 32 * q + lane;
+                    if (jr <= ri) {
+                        const int j = j0 + jr;
+                        const V vj = jr == 0 ? vfirst : V_[j];
+                        V a = av[q];
+                        a = cfms_conj_b(ui, Wv[j], a);
+                        a = cfms_conj_b(wi, U_[j], a);
+                        row[jr] = a;
+                        racc = cfma(a, vj, racc);
+                        if (jr < ri) pcw[jr] = cfma_conj_a(a, vi, pcw[jr]);
+                    }
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) racc = cadd(racc, cshfl_xor(racc, o));

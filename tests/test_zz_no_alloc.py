@@ -28,6 +28,11 @@ def _lib():
     P.Config(Lx=8, Ly=8, L_c=4, T=0.05, mu=-6.5, seed=0, precision=P.FP64, schedule=P.SCHEDULE_BLOCK),
     P.Config(Lx=10, Ly=10, L_c=8, stride=5, T=0.05, mu=-6.5, seed=3, precision=P.MIXED,
              proposal=P.PROPOSAL_CONE, cone_deg=30.0),
+    P.Config(Lx=8, Ly=8, L_c=4, T=0.1, mu=4.0, U=8.0, m_step=0.5, seed=5, precision=P.FP64,
+             model=P.MODEL_HUBBARD_MF, schedule=P.SCHEDULE_BLOCK),
+    P.Config(Lx=64, Ly=1, L_c=8, T=0.1, mu=0.0, lam=1.5, K=1.0, m_step=0.4, seed=6, precision=P.MIXED,
+             model=P.MODEL_HOLSTEIN, schedule=P.SCHEDULE_TILED, stride=8, update_offset=4),
+    P.Config(Lx=6, Ly=6, Lz=6, L_c=3, stride=3, T=0.1, mu=-6.5, seed=7, precision=P.FP64),
 ])
 def test_noalloc_sweeps_match_context_sweeps(cfg):
     stages = P.ptca_schedule(cfg)
