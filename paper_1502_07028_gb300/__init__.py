@@ -8,7 +8,7 @@ from .ptca import (Config, Context, PtcaError, FP64, MIXED, SCHEDULE_TILED, SCHE
                    ptca_dims, ptca_build_clusters, ptca_cluster_eigvals, ptca_free_energy, ptca_sweep,
                    ptca_sweep_record, ptca_observables, ptca_schedule, ptca_version, ptca_sweep_noalloc, ptca_set_pipeline, ptca_set_resolve_margin, ptca_set_checker, ptca_checker_read, ptca_set_launch_config,
                    ptca_get_launch_config, ptca_autotune, LaunchConfig, ptca_set_kernel_timing, ptca_kernel_times,
-                   KernelTimes, ptca_stage_split, PIPELINE_OVERLAP, MODEL_DOUBLE_EXCHANGE, MODEL_HUBBARD_MF, MODEL_HOLSTEIN,
+                   KernelTimes, ptca_stage_split, ptca_full_spectrum, PIPELINE_OVERLAP, MODEL_DOUBLE_EXCHANGE, MODEL_HUBBARD_MF, MODEL_HOLSTEIN,
                    ptca_surrogate_param_count, ptca_surrogate_init, ptca_surrogate_get_params,
                    ptca_surrogate_set_params, ptca_surrogate_collect, ptca_surrogate_train, ptca_surrogate_grad,
                    ptca_surrogate_predict, ptca_surrogate_enable,

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libptca.so")
-SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "kernels_f32w4.cu", "kernels_large.cu", "api.cu", "kernels_misc.cu", "noalloc.cu", "surrogate.cu",
+SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "kernels_f32w4.cu", "kernels_large.cu", "spectrum.cu", "api.cu", "kernels_misc.cu", "noalloc.cu", "surrogate.cu",
            "surrogate_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
+    subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcusolver"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -307,6 +307,10 @@ static void free_ctx(ptca_ctx* c) {
 // Failure reporting for the other translation units of the library.
 ptca_status ptca_internal_fail(ptca_status s, const char* msg) { return fail(s, msg); }
 
+// The device-side problem description of a context (for the other
+// translation units of the library).
+ptca::Model ptca_context_model(const ptca_ctx* ctx) { return to_model(ctx->p); }
+
 extern "C" {
 
 int32_t ptca_version(void) { return PTCA_VERSION_MAJOR * 100 + PTCA_VERSION_MINOR; }

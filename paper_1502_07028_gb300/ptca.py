@@ -34,7 +34,7 @@ EXPORTED = [
     "ptca_surrogate_collect", "ptca_surrogate_train", "ptca_surrogate_grad", "ptca_surrogate_predict",
     "ptca_surrogate_enable", "ptca_set_checker", "ptca_checker_read", "ptca_set_launch_config",
     "ptca_get_launch_config", "ptca_autotune", "ptca_set_kernel_timing", "ptca_kernel_times",
-    "ptca_stage_split",
+    "ptca_stage_split", "ptca_full_spectrum",
 ]
 
 
@@ -111,6 +111,7 @@ def lib():
             "ptca_observables": ([vp, P(Obs), vp], i32),
             "ptca_schedule": ([P(Lattice), P(Params), vp, vp, P(i32)], i32),
             "ptca_stage_split": ([P(Lattice), P(Params), vp, vp], i32),
+            "ptca_full_spectrum": ([vp, vp, vp], i32),
             "ptca_last_error": ([], ctypes.c_char_p),
             "ptca_version": ([], i32),
             "ptca_sweep_noalloc": ([P(Lattice), P(Params), vp, vp, i32, vp, i64, vp, vp, vp], i32),
@@ -367,6 +368,12 @@ def ptca_kernel_times(h, stream=None) -> KernelTimes:
     _check(lib().ptca_kernel_times(h, _ptr(out), _stream(stream)))
     return KernelTimes(float(out[0]), int(out[1]), float(out[2]), int(out[3]), float(out[4]), int(out[5]),
                        int(out[6]), int(out[7]))
+
+
+def ptca_full_spectrum(h, eig_out, stream=None) -> None:
+    """All 2N eigenvalues of the whole lattice's one-body Hamiltonian (device
+    float64 tensor of 2N entries, filled ascending)."""
+    _check(lib().ptca_full_spectrum(h, _ptr(eig_out), _stream(stream)))
 
 
 def ptca_set_checker(h, on: bool) -> None:
