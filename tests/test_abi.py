@@ -86,6 +86,11 @@ def test_schedule_matches_oracle(built, kw):
     (dict(Lx=56, Ly=56, Lz=7, L_c=7, precision=P.MIXED), "maximum"),
     (dict(Lx=8, Ly=8, L_c=4, update_offset=4), "update_offset"),
     (dict(Lx=8, Ly=1, Lz=4, L_c=2), "needs Ly > 1"),
+    (dict(Lx=8, Ly=8, L_c=4, model=3), "unknown model"),
+    (dict(Lx=8, Ly=8, L_c=4, model=P.MODEL_HUBBARD_MF, m_step=0.0), "m_step"),
+    (dict(Lx=8, Ly=8, L_c=4, model=P.MODEL_HUBBARD_MF, U=float("nan")), "finite U"),
+    (dict(Lx=16, Ly=1, L_c=4, model=P.MODEL_HOLSTEIN, lam=float("inf")), "finite lambda"),
+    (dict(Lx=16, Ly=1, L_c=4, model=P.MODEL_HOLSTEIN, m_step=-1.0), "m_step"),
     (dict(Lx=8, Ly=8, Lz=3, L_c=4), "L_c"),
     (dict(Lx=8, Ly=8, Lz=6, L_c=4, stride=4), "divide"),
 ])
