@@ -571,18 +571,20 @@ __device__ void householder_tridiag(int n, cplx_t<T>* A, const HHScratch<T>& sc,
                     // possibly stale or non-finite, is replaced by zero
                     // before both sums.  The diagonal's imaginary part is
                     // mathematically zero under the update and only its real
-                    // part is ever read.
+                    // part is ever read.  With s = jr - ri0, the lane holds an
+                    // element of row ri0 + r iff s <= r (below the diagonal
+                    // iff s < r), and rows from nr = m - ri0 on do not exist.
+                    const int sl = jr - ri0, nr = m - ri0;
 #pragma unroll
                     for (int r = 0; r < RB; ++r) {
-                        const int ri = ri0 + r;
-                        const bool ok = (ri < m) && (jr <= ri);
+                        const bool ok = (sl <= r) && (r < nr);
                         V a = A[base[r] + jr];
                         a = cfms_conj_b(ui[r], wc[t], a);
                         a = cfms_conj_b(wi[r], uc[t], a);
                         if (ok) A[base[r] + jr] = a;
                         a = ok ? a : zero;
                         racc[r] = cfma(a, vc[t], racc[r]);
-                        const V vrow = (jr < ri) ? vi[r] : zero;
+                        const V vrow = (sl < r) ? vi[r] : zero;
                         cacc[t] = cfma_conj_a(a, vrow, cacc[t]);
                     }
                 }
