@@ -446,11 +446,12 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
         }
         if (ce == cudaSuccess && c->prec == 1) {
             // Global slots for the re-solves: one per CTA of any launch
-            // configuration (the 4-warp persistent grid is the widest).
+            // configuration (the narrowest CTAs give the widest persistent grid).
             c->resolve_grid = sms;
             int widest = c->grid;
-            if (ptca::sweep_width_supported(c->prec, 4, c->nA))
-                widest = std::max(widest, sms * ptca::persistent_blocks_per_sm(c->prec, 4, c->nA));
+            for (int nw : {4, 1})
+                if (ptca::sweep_width_supported(c->prec, nw, c->nA))
+                    widest = std::max(widest, sms * ptca::persistent_blocks_per_sm(c->prec, nw, c->nA));
             const int slots = std::max(widest, c->resolve_grid);
             c->gA_stride = (int64_t)c->nA * (c->nA + 1) / 2;
             // + 64 elements: the fused pass may load up to 31 elements past a
@@ -909,11 +910,13 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     if (!ctx || !cfg) return fail(PTCA_ERR_INVALID, "null argument");
     if (cfg->pipeline < PTCA_PIPELINE_STAGES || cfg->pipeline > PTCA_PIPELINE_OVERLAP)
         return fail(PTCA_ERR_INVALID, "unknown pipeline");
-    if (cfg->warps_per_cta != 8 && cfg->warps_per_cta != 4) return fail(PTCA_ERR_INVALID, "warps_per_cta must be 4 or 8");
+    if (cfg->warps_per_cta != 8 && cfg->warps_per_cta != 4 && cfg->warps_per_cta != 1)
+        return fail(PTCA_ERR_INVALID, "warps_per_cta must be 1, 4 or 8");
     if (ctx->large && cfg->warps_per_cta != 8)
         return fail(PTCA_ERR_UNSUPPORTED, "large clusters run 16-warp CTAs; pass warps_per_cta = 8 (the default width)");
     if (!ctx->large && !ptca::sweep_width_supported(ctx->prec, cfg->warps_per_cta, ctx->nA))
-        return fail(PTCA_ERR_UNSUPPORTED, "4-warp sweep kernels need PTCA_MIXED and matrix orders up to 128");
+        return fail(PTCA_ERR_UNSUPPORTED,
+                    "narrow sweep kernels need PTCA_MIXED and matrix orders up to 128 (4 warps) or 32 (1 warp)");
     const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, cfg->warps_per_cta, ctx->nA);
     if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > maxb)
         return fail(PTCA_ERR_INVALID, "ctas_per_sm must be in [0, the CTAs that fit on an SM]");
@@ -953,7 +956,7 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
         cand.push_back({PTCA_PIPELINE_STAGES, 8, 0});
         if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, 8, 0});
     }
-    for (int nw : {8, 4}) {
+    for (int nw : {8, 4, 1}) {
         if (ctx->large || !ptca::sweep_width_supported(ctx->prec, nw, ctx->nA)) continue;
         cand.push_back({PTCA_PIPELINE_STAGES, nw, 0});
         if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0});

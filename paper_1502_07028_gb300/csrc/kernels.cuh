@@ -15,9 +15,10 @@ constexpr double kFermiCut = 40.0; // eigenvalues above mu + 40 T change F by < 
 
 // Resident CTAs per SM the launch bounds ask for (caps the registers at
 // 65536 / (value * 32 * NWP)).  Shared memory holds two 8-warp or three
-// 4-warp FP32 CTAs per SM for matrices up to n = 128, one CTA otherwise.
+// 4-warp FP32 CTAs per SM for matrices up to n = 128, one CTA otherwise;
+// one-warp CTAs (n <= 32) are capped at 128 registers.
 template <typename T, int NT, int NWP = NW> struct MinBlocks {
-    static constexpr int value = (sizeof(T) == 4 && NT <= 4) ? (NWP == 4 ? 3 : 2) : (NWP == 4 ? 2 : 1);
+    static constexpr int value = NWP == 1 ? 16 : (sizeof(T) == 4 && NT <= 4) ? (NWP == 4 ? 3 : 2) : (NWP == 4 ? 2 : 1);
 };
 
 // Shared-memory layout of one cluster CTA (byte offsets, 16-byte aligned).

@@ -33,6 +33,13 @@ cudaError_t configure_f32w4(size_t);
 cudaError_t launch_stage_f32w4(const StageArgs&, cudaStream_t);
 cudaError_t launch_persistent_f32w4(const PersistArgs&, int, cudaStream_t);
 int persistent_blocks_per_sm_f32w4(int);
+// one-warp FP32 sweep kernels (kernels_f32w1.cu)
+size_t cluster_smem_bytes_f32w1(int nA);
+int cluster_max_order_f32w1();
+cudaError_t configure_f32w1(size_t);
+cudaError_t launch_stage_f32w1(const StageArgs&, cudaStream_t);
+cudaError_t launch_persistent_f32w1(const PersistArgs&, int, cudaStream_t);
+int persistent_blocks_per_sm_f32w1(int);
 cudaError_t launch_resolve_f32(const StageArgs&, int, cudaStream_t);
 cudaError_t launch_check_f32(const StageArgs&, int, int, double*, int, double*, cudaStream_t);
 cudaError_t launch_check_ref_f32(const StageArgs&, int, int, double*, int, double*, int, cudaStream_t);
@@ -42,14 +49,17 @@ int cluster_max_order(int prec) { return prec ? cluster_max_order_f32() : cluste
 cudaError_t configure_cluster_kernels(size_t smem_limit) {
     cudaError_t e = configure_f32(smem_limit);
     if (e == cudaSuccess) e = configure_f32w4(smem_limit);
+    if (e == cudaSuccess) e = configure_f32w1(smem_limit);
     if (e != cudaSuccess) return e;
     return configure_f64(smem_limit);
 }
 bool sweep_width_supported(int prec, int nw, int nA) {
     if (nw == 8) return nA <= cluster_max_order(prec);
+    if (nw == 1) return prec == 1 && nA <= cluster_max_order_f32w1();
     return nw == 4 && prec == 1 && nA <= cluster_max_order_f32w4();
 }
 size_t sweep_smem_bytes(int prec, int nw, int nA) {
+    if (nw == 1) return cluster_smem_bytes_f32w1(nA);
     return nw == 4 ? cluster_smem_bytes_f32w4(nA) : cluster_smem_bytes(prec, nA);
 }
 cudaError_t launch_build(int prec, const Model& m, const double* S, const int32_t* sites, int count,
@@ -65,15 +75,18 @@ cudaError_t launch_eigvals(int prec, int nA, const void* H, const int64_t* offse
 }
 cudaError_t launch_stage(int prec, int nw, const StageArgs& a, cudaStream_t st) {
     if (nw == 4) return prec ? launch_stage_f32w4(a, st) : cudaErrorInvalidValue;
+    if (nw == 1) return prec ? launch_stage_f32w1(a, st) : cudaErrorInvalidValue;
     return prec ? launch_stage_f32(a, st) : launch_stage_f64(a, st);
 }
 cudaError_t launch_persistent(int prec, int nw, const PersistArgs& p, int grid, cudaStream_t st) {
     if (nw == 4) return prec ? launch_persistent_f32w4(p, grid, st) : cudaErrorInvalidValue;
+    if (nw == 1) return prec ? launch_persistent_f32w1(p, grid, st) : cudaErrorInvalidValue;
     return prec ? launch_persistent_f32(p, grid, st) : launch_persistent_f64(p, grid, st);
 }
 cudaError_t launch_resolve(const StageArgs& a, int grid, cudaStream_t st) { return launch_resolve_f32(a, grid, st); }
 int persistent_blocks_per_sm(int prec, int nw, int nA) {
     if (nw == 4) return prec ? persistent_blocks_per_sm_f32w4(nA) : 0;
+    if (nw == 1) return prec ? persistent_blocks_per_sm_f32w1(nA) : 0;
     return prec ? persistent_blocks_per_sm_f32(nA) : persistent_blocks_per_sm_f64(nA);
 }
 

@@ -17,11 +17,13 @@ def main(argv=None):
     ap.add_argument("--L", type=int, default=100)
     ap.add_argument("--Lc", type=int, default=8)
     ap.add_argument("--Lz", type=int, default=1, help="third extent (cubic lattice L x L x Lz)")
+    ap.add_argument("--Ly", type=int, default=0, help="second extent (0: L; 1: a chain of L sites)")
+    ap.add_argument("--offset", type=int, default=-1, help="update-site offset in the window (-1: the default)")
     ap.add_argument("--open", action="store_true", help="open lattice (clipped windows)")
     ap.add_argument("--schedule", choices=["block", "tiled"], default="block")
     ap.add_argument("--stride", type=int, default=0)
     ap.add_argument("--pipeline", choices=["stages", "persistent", "graph", "overlap"], default="graph")
-    ap.add_argument("--warps", type=int, choices=[4, 8], default=8, help="warps per CTA of the sweep kernels")
+    ap.add_argument("--warps", type=int, choices=[1, 4, 8], default=8, help="warps per CTA of the sweep kernels")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: as many as fit)")
     ap.add_argument("--margin", type=float, default=None, help="mixed-mode FP64 re-solve margin (0 = off)")
     ap.add_argument("--sweeps", type=int, default=1)
@@ -30,8 +32,10 @@ def main(argv=None):
     ap.add_argument("--mu", type=float, default=-6.5)
     ap.add_argument("--JH", type=float, default=8.0)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--model", choices=["de", "hubbard"], default="de",
-                    help="double exchange, or the Hubbard mean-field model of Eq. 1")
+    ap.add_argument("--model", choices=["de", "hubbard", "holstein"], default="de",
+                    help="double exchange, the Hubbard mean-field model of Eq. 1, or the Holstein model")
+    ap.add_argument("--lam", type=float, default=1.5, help="Holstein electron-lattice coupling")
+    ap.add_argument("--K", type=float, default=1.0, help="Holstein elastic constant")
     ap.add_argument("--U", type=float, default=8.0, help="Hubbard U (model hubbard)")
     ap.add_argument("--m-step", type=float, default=0.5, help="field proposal radius (model hubbard)")
     a = ap.parse_args(argv)
@@ -40,11 +44,11 @@ def main(argv=None):
     from paper_1502_07028_gb300 import _build
 
     _build.build()
-    cfg = P.Config(Lx=a.L, Ly=a.L, Lz=a.Lz, L_c=a.Lc, periodic=0 if a.open else 1, J_H=a.JH, mu=a.mu, T=a.T, seed=a.seed,
+    cfg = P.Config(Lx=a.L, Ly=a.Ly or a.L, Lz=a.Lz, L_c=a.Lc, update_offset=a.offset, periodic=0 if a.open else 1, J_H=a.JH, mu=a.mu, T=a.T, seed=a.seed,
                    schedule=P.SCHEDULE_BLOCK if a.schedule == "block" else P.SCHEDULE_TILED, stride=a.stride,
                    precision=P.MIXED if a.precision == "mixed" else P.FP64, proposal=P.PROPOSAL_CONE, cone_deg=30.0,
-                   model=P.MODEL_HUBBARD_MF if a.model == "hubbard" else P.MODEL_DOUBLE_EXCHANGE, U=a.U,
-                   m_step=a.m_step)
+                   model={"de": P.MODEL_DOUBLE_EXCHANGE, "hubbard": P.MODEL_HUBBARD_MF,
+                          "holstein": P.MODEL_HOLSTEIN}[a.model], U=a.U, m_step=a.m_step, lam=a.lam, K=a.K)
     ctx = P.Context(cfg)
     P.ptca_set_launch_config(ctx.h, {"stages": P.PIPELINE_STAGES, "persistent": P.PIPELINE_PERSISTENT,
                                      "graph": P.PIPELINE_GRAPH, "overlap": P.PIPELINE_OVERLAP}[a.pipeline], a.warps, a.ctas_per_sm)

@@ -215,3 +215,43 @@ def test_overlapped_resolve_gives_the_one_stream_chain_bit_for_bit(lat, margin):
     for a, b in zip(r0, r1):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("cfgkw", [
+    dict(Lx=16, Ly=16, L_c=4, schedule=P.SCHEDULE_BLOCK, model=P.MODEL_HUBBARD_MF, U=8.0, mu=4.0, T=0.1),   # n = 32
+    dict(Lx=128, Ly=1, L_c=8, stride=8, update_offset=4, model=P.MODEL_HOLSTEIN, lam=1.5, K=1.0, mu=0.0,
+         T=0.1, m_step=0.4),                                                                                 # n = 16
+])
+def test_one_warp_ctas_compute_the_same_chain(cfgkw):
+    # Matrices up to n = 32 also run one warp per matrix; with the guard the
+    # chain (decisions, spins) is that of the wider CTAs in every pipeline.
+    cfg = P.Config(**cfgkw, seed=21, precision=P.MIXED)
+    runs = []
+    for pl, nw in [(P.PIPELINE_STAGES, 8), (P.PIPELINE_STAGES, 1), (P.PIPELINE_OVERLAP, 1),
+                   (P.PIPELINE_PERSISTENT, 1), (P.PIPELINE_GRAPH, 4)]:
+        ctx = P.Context(cfg)
+        P.ptca_set_launch_config(ctx.h, pl, nw, 0)
+        ctx.sweep(2)
+        runs.append((ctx.spins().cpu().numpy(), [x.cpu().numpy() for x in ctx.record()]))
+        ctx.close()
+    S0, (site, Fo, Fn, lnu, acc) = runs[0]
+    for S, (site2, Fo2, Fn2, lnu2, acc2) in runs[1:]:
+        assert np.array_equal(site, site2) and np.array_equal(acc, acc2)
+        assert np.array_equal(S, S0)
+        assert np.max(np.abs(Fo2 - Fo) / np.maximum(1.0, np.abs(Fo))) < 1e-5
+    # The one-warp per-stage and overlapped pipelines re-solve with the same
+    # kernel: bit-identical.  (The persistent kernel re-solves inline at its
+    # own CTA width, so its re-solved free energies agree only to rounding.)
+    for a, b in zip(runs[1][1], runs[2][1]):
+        assert np.array_equal(a, b)
+
+
+def test_one_warp_width_is_limited_to_order_32():
+    ctx = P.Context(P.Config(Lx=16, Ly=16, L_c=8, precision=P.MIXED))   # n = 128
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(ctx.h, P.PIPELINE_STAGES, 1, 0)
+    ctx.close()
+    ctx = P.Context(P.Config(Lx=8, Ly=8, L_c=4, precision=P.FP64))      # FP64
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(ctx.h, P.PIPELINE_STAGES, 1, 0)
+    ctx.close()
