@@ -20,7 +20,7 @@ namespace ptca {
 
 struct __align__(8) dfl {
     float hi, lo;
-    __device__ __forceinline__ dfl() = default;
+    dfl() = default;
     __device__ __forceinline__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
     // Nearest double-float to x (exact for every double within the float range
     // up to the 48-bit significand).
