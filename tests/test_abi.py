@@ -110,6 +110,16 @@ def test_init_reports_missing_gpu_instead_of_falling_back(built):
     assert e.value.status == 2
 
 
+def test_binding_fails_loudly_without_the_library(built, monkeypatch, tmp_path):
+    # No silent substitute: a missing shared library is an error on every call.
+    monkeypatch.setattr(P.ptca, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "libptca.so"))
+    with pytest.raises(RuntimeError, match="is missing"):
+        P.ptca_version()
+    with pytest.raises(RuntimeError, match="is missing"):
+        P.ptca_init(P.Config(Lx=8, Ly=8, L_c=4))
+
+
 @pytest.mark.parametrize("kw", [
     dict(Lx=8, Ly=8, L_c=4),
     dict(Lx=10, Ly=10, L_c=8, stride=5),
