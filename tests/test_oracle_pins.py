@@ -213,6 +213,43 @@ def test_jacobi_matches_lapack(n):
     assert abs(np.sum(e ** 2) - fro2) < 1e-13 * fro2
 
 
+def _cluster_cases():
+    """Physical cluster matrices of order 8 and 16, degenerate spectra included."""
+    cases = []
+    m = oracle.Model(Lx=4, Ly=4, Lc=2, t=1.0, JH=8.0)
+    cases.append(oracle.cluster_hamiltonian(m, inputs.random_unit_spins(21, m.N), 5)[0])
+    cases.append(oracle.cluster_hamiltonian(m, inputs.ferro_spins(m.N, (0.3, -0.4, 0.866)), 5)[0])
+    mh = oracle.Model(Lx=6, Ly=6, Lc=2, t=1.0, U=8.0, mu=4.0, model=oracle.MODEL_HUBBARD_MF, m_step=0.5)
+    cases.append(oracle.cluster_hamiltonian(mh, inputs.random_fields(22, mh.N, 2.0), 7)[0])
+    mq = oracle.Model(Lx=16, Ly=1, Lc=4, t=1.0, lam=1.5, K=1.0, model=oracle.MODEL_HOLSTEIN, m_step=0.4)
+    S = np.zeros((mq.N, 3))
+    S[:, 0] = inputs.rng(23).uniform(-1, 1, size=mq.N)
+    cases.append(oracle.cluster_hamiltonian(mq, S, 6)[0])
+    mc = oracle.Model(Lx=4, Ly=4, Lz=4, Lc=2, t=1.0, JH=6.0)
+    cases.append(oracle.cluster_hamiltonian(mc, inputs.random_unit_spins(24, mc.N), 21)[0])
+    return cases
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_jacobi_spectrum_has_the_power_sums_of_the_cluster_matrix(case):
+    # Newton's identities: the power sums p_k = sum_j eps_j^k = Tr(H^k),
+    # k = 1..n, fix the characteristic polynomial and so the whole spectrum
+    # with multiplicities.  The traces come from plain matrix products, with
+    # no eigensolver involved.
+    H = _cluster_cases()[case]
+    n = H.shape[0]
+    assert n in (8, 16)
+    e = oracle.eigvalsh(H)
+    assert np.all(np.diff(e) >= 0)
+    P = np.eye(n, dtype=np.complex128)
+    for k in range(1, n + 1):
+        P = P @ H
+        tr = np.trace(P)
+        scale = float(np.sum(np.abs(e) ** k))
+        assert abs(tr.imag) <= 1e-12 * scale
+        assert abs(np.sum(e ** k) - tr.real) <= 1e-12 * scale, (k, np.sum(e ** k), tr)
+
+
 def test_jacobi_special_matrices():
     assert np.array_equal(oracle.eigvalsh(np.zeros((5, 5))), np.zeros(5))
     d = np.array([3.0, -1.0, 2.0, 2.0])
