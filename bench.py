@@ -113,6 +113,20 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def clock_verdict(c) -> str | None:
+    """Why a timed region's clock record invalidates its timing, or None.
+    Thermal and hardware slowdowns reject it; a median SM clock below 85 % of
+    the maximum with no reason active is a leftover clock lock and rejects it
+    too.  The power cap alone is kept (it is normal under a dense load)."""
+    bad = [r for r in c.get("reasons", []) if r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")]
+    if bad:
+        return "slowdown: " + ", ".join(bad)
+    sm, mx = c.get("sm_mhz"), c.get("sm_max_mhz")
+    if sm and mx and not c.get("reasons") and sm < 0.85 * mx:
+        return f"SM clock {sm:.0f} of {mx:.0f} MHz with no reason active"
+    return None
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -459,15 +473,26 @@ def main():
     pipeline_desc = (f"{names[best.pipeline]}, {best.warps_per_cta}-warp CTA per matrix"
                      + (f", {best.ctas_per_sm} CTAs/SM" if not per_stage else "")
                      + " (autotuned)")
-    barrier(world)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        t_wall0 = time.perf_counter()
-        # Per-stage pipeline: the library brackets each stage-kernel launch
-        # with CUDA events on the stream, for the kernel's own duration.
-        step_ms = time_sweeps(ctx, args.steps, args.warmup, flush, stream, kernel_timing=per_stage)
+    def timed_region():
+        barrier(world)
         torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall0
+        with ClockSampler(local) as clk:
+            t_wall0 = time.perf_counter()
+            # Per-stage pipeline: the library brackets each stage-kernel launch
+            # with CUDA events on the stream, for the kernel's own duration.
+            ms = time_sweeps(ctx, args.steps, args.warmup, flush, stream, kernel_timing=per_stage)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t_wall0
+        return ms, wall, clk.summary()
+
+    step_ms, t_wall, clocks = timed_region()
+    # A timed region that saw thermal or hardware slowdown, or an SM clock
+    # held well below its maximum with no reason, is measured once more.
+    rejected = clock_verdict(clocks)
+    if max_over_ranks(world, 1.0 if rejected else 0.0) > 0:
+        step_ms, t_wall, clocks = timed_region()
+        clocks["first_attempt_rejected"] = rejected or "on another rank"
+    clocks["verdict"] = clock_verdict(clocks) or "ok"
     kt = P.ptca_kernel_times(ctx.h, stream=stream) if per_stage else None
     P.ptca_set_kernel_timing(ctx.h, False)
     barrier(world)
@@ -533,8 +558,6 @@ def main():
                              + (2 if best.pipeline == P.PIPELINE_STAGES else 1))
     else:
         launches_per_step = 1
-    clocks = clk.summary()
-    sm_mhz = clocks["sm_mhz"] or 2070.0
     if kt is not None and kt.stage_launches > 0:
         # k_stage launches other than the overlapped pipeline's dependent
         # visits: 2 matrices per visit, per-launch durations from the
