@@ -20,9 +20,10 @@
  * the same on x86-64 and aarch64:
  *     gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off -o libptca_oracle.so ptca_oracle.c -lm
  *
- * Models on a square lattice, both with hopping -t between nearest neighbours
- * of the same spin and two rows per cluster site in the cluster matrix (two
- * spin species, Sec. IV: "2N x 2N"):
+ * Models on a chain, a square or a cubic lattice, all with hopping -t between
+ * nearest neighbours of the same spin and two rows per cluster site in the
+ * cluster matrix (two spin species; Sec. IV gives the order as twice the
+ * cluster sites):
  *   model 0, double exchange: a Hund term -J_H S_i . sigma on every site, with
  *     classical unit spins S_i;
  *   model 1, Hubbard mean field (Eq. 1, <n_i> = 1): an on-site term
@@ -154,10 +155,11 @@ void oracle_init_spins(const oracle_model* m, double* S)
     }
 }
 
-/* Proposed new spin at a site (Sec. II.c step c: "the classical DOF is
- * randomly modified").  Sphere: a fresh uniform point.  Cone: a point uniform
- * on the spherical cap of half-angle cone_deg around S_old, i.e. cos(theta)
- * uniform in [cos(cone), 1], rotated from the z axis onto S_old. */
+/* Proposed new spin at a site (Sec. II.c step c: a random change of the
+ * update site's classical variable).  Sphere: a fresh uniform point.  Cone:
+ * a point uniform on the spherical cap of half-angle cone_deg around S_old,
+ * i.e. cos(theta) uniform in [cos(cone), 1], rotated from the z axis onto
+ * S_old.  The Holstein and Hubbard moves are the first two branches. */
 void oracle_propose(const oracle_model* m, uint64_t sweep, int site, const double* s_old, double* s_new)
 {
     double u[2];
@@ -417,7 +419,7 @@ static double cluster_F(const oracle_model* m, const double* S, int site, const 
 /*   tiled: stage (ax, ay, az) holds the sites (ax + s p, ay + s q, az + s r), */
 /*          row-major; stages in row-major order of (ax, ay, az).             */
 /*   block: the lattice is cut in two along each axis (2^d blocks, Sec.     */
-/*          III.a, "four blocks" in two dimensions, eight in three); a stage  */
+/*          III.a: four blocks in two dimensions, eight in three); a stage   */
 /*          is one block, its sites in row-major order; blocks row-major.     */
 /* Writes stage_start[nstages+1] and sites[N]; returns nstages.               */
 /* ------------------------------------------------------------------------ */
