@@ -828,19 +828,6 @@ __device__ __forceinline__ double eig_f64_bracketed(int n, const double* d, cons
     return eig_f64(n, d, e2, k, lo, hi, pivmin, nrm);
 }
 
-// One FP64 Newton correction of an eigenvalue located by FP32 multisection
-// in [lo, hi]; kept only if it stays near that bracket.
-__device__ __forceinline__ double newton_polish_f64(int n, const double* d, const double* e2, float lo, float hi,
-                                                    float atolf, double pivmin) {
-    const double x = 0.5 * ((double)lo + (double)hi);
-    double s;
-    newton_pass_f64(n, d, e2, x, pivmin, s);
-    const double xn = x - 1.0 / s;
-    const double w = fmax((double)(hi - lo), 4.0 * (double)atolf);
-    if (isfinite(xn) && xn >= (double)lo - w && xn <= (double)hi + w) return xn;
-    return x;
-}
-
 // ---------------------------------------------------------------------------
 // The same refinements in double-float arithmetic: FP64-class precision on
 // the FP32 pipe.  The tridiagonal is given as float pairs (dh + dl, eh + el),

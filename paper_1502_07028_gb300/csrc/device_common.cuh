@@ -28,8 +28,6 @@ __device__ __forceinline__ double fmadd(double a, double b, double c) { return _
 __device__ __forceinline__ float sqroot(float a) { return sqrtf(a); }
 __device__ __forceinline__ double sqroot(double a) { return sqrt(a); }
 
-// a * b
-template <typename V> __device__ __forceinline__ V cmul(V a, V b) { V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r; }
 // acc + a * b
 template <typename V> __device__ __forceinline__ V cfma(V a, V b, V acc) {
     acc.x = fmadd(a.x, b.x, acc.x); acc.x = fmadd(-a.y, b.y, acc.x);
@@ -50,7 +48,6 @@ template <typename V> __device__ __forceinline__ V cfms_conj_b(V a, V b, V acc) 
 }
 template <typename V> __device__ __forceinline__ auto cabs2(V a) -> decltype(a.x) { return a.x * a.x + a.y * a.y; }
 
-template <typename T> __device__ __forceinline__ T shfl_xor(T v, int o) { return __shfl_xor_sync(FULL_MASK, v, o); }
 template <typename V> __device__ __forceinline__ V cshfl_xor(V v, int o) {
     v.x = __shfl_xor_sync(FULL_MASK, v.x, o);
     v.y = __shfl_xor_sync(FULL_MASK, v.y, o);
