@@ -37,6 +37,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ptca_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libptca_oracle.so")
+_SAN_PATH = os.path.join(_BUILD, "libptca_oracle_san.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -49,18 +50,24 @@ PROPOSAL_SPHERE = 0
 PROPOSAL_CONE = 1
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle with gcc (no fast-math, no FMA contraction)."""
+def build(force: bool = False, sanitize: bool = False) -> str:
+    """Compile the C oracle with gcc (no fast-math, no FMA contraction).
+    With sanitize, a separate copy instrumented by AddressSanitizer and
+    UndefinedBehaviorSanitizer, every finding fatal; it loads only into a
+    process that has the ASan runtime preloaded."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    path = _SAN_PATH if sanitize else _LIB_PATH
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".{os.getpid()}.tmp"
+    extra = (["-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined", "-fno-sanitize-recover=all"]
+             if sanitize else [])
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-fno-fast-math", *extra, "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class _Model(ctypes.Structure):
@@ -134,7 +141,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = ctypes.CDLL(build())
+            # PTCA_ORACLE_LIB selects another build of the same source (the
+            # sanitizer-instrumented copy).
+            _lib = ctypes.CDLL(os.environ.get("PTCA_ORACLE_LIB") or build())
             P = ctypes.POINTER
             d, i32, u32, u64, u8 = (ctypes.c_double, ctypes.c_int32, ctypes.c_uint32,
                                     ctypes.c_uint64, ctypes.c_uint8)
