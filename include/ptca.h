@@ -3,14 +3,18 @@
  *
  * The library runs the hot path of the parallelised traveling cluster
  * approximation (PTCA, Sec. III of Mukherjee, Patel, Bishop, Dagotto,
- * arXiv:1502.07028) for the double-exchange spin-fermion model on a square
- * lattice: classical unit spins S_i, electrons with nearest-neighbour hopping
- * -t and a Hund coupling -J_H S_i . sigma.  For an update site i_s the
- * traveling cluster is the L_c x L_c window of sites around it (Sec. II.b,
- * Fig. 1); its Hamiltonian is a 2N_c x 2N_c complex Hermitian matrix (two spin
- * species, Sec. IV).  Its eigenvalues eps_k give the cluster free energy
+ * arXiv:1502.07028).  The headline model is the double-exchange spin-fermion
+ * model: classical unit spins S_i, electrons with nearest-neighbour hopping
+ * -t and a Hund coupling -J_H S_i . sigma.  The Hubbard mean-field model
+ * (Eq. 1) and the adiabatic Holstein model (Sec. VII.b) run on the same path
+ * (ptca_params.model), on chains, square and cubic lattices.  For an update
+ * site i_s the traveling cluster is the window of L_c sites per axis around
+ * it (Sec. II.b, Fig. 1); its Hamiltonian is a 2N_c x 2N_c complex Hermitian
+ * matrix (two spin species, Sec. IV).  Its eigenvalues eps_k give the cluster
+ * free energy
  *     F = -T sum_k ln(1 + exp(-(eps_k - mu)/T))
- * (the periodic cluster is a grand-canonical ensemble, Sec. II.b), and
+ * (the periodic cluster is a grand-canonical ensemble, Sec. II.b; the Hubbard
+ * and Holstein models add a classical energy), and
  * Metropolis on dF = F_new - F_old accepts or rejects a proposed spin
  * (Sec. II.c steps a-f).  A sweep is a list of stages; the update sites of a
  * stage are processed at once from the configuration at the start of the
@@ -31,7 +35,8 @@
  *   - Complex matrices are stored as the packed lower triangle, row-major:
  *     element (r, c), c <= r, at index r(r+1)/2 + c, each element an
  *     interleaved (re, im) pair of double (PTCA_FP64) or float (PTCA_MIXED).
- *   - Spins are N x 3 row-major doubles (S_x, S_y, S_z), site i = y*Lx + x.
+ *   - Spins are N x 3 row-major doubles (S_x, S_y, S_z), site
+ *     i = (z*Ly + y)*Lx + x.
  */
 #ifndef PTCA_H
 #define PTCA_H
@@ -73,7 +78,7 @@ typedef struct {
     int32_t Lz;
 } ptca_lattice;
 
-/* Problem parameters.  Two models share the lattice, the hopping -t and the
+/* Problem parameters.  Three models share the lattice, the hopping -t and the
  * two spin species per site:
  *   PTCA_MODEL_DOUBLE_EXCHANGE  on-site -J_H S_i . sigma, classical unit spins S_i
  *                               (proposals: sphere or cone);
@@ -107,7 +112,8 @@ typedef struct {
     int32_t stride;           /* tiled schedule: spacing of the update sites in a     */
                               /* stage along each axis; 0: L_c                        */
     int32_t precision;        /* PTCA_FP64 or PTCA_MIXED (FP32 reduction to tridiagonal */
-                              /* form; FP64 eigenvalues, free energies and dF)        */
+                              /* form, double-float eigenvalue finish, FP64 free      */
+                              /* energies and dF)                                     */
     int32_t proposal;         /* PTCA_PROPOSAL_SPHERE or PTCA_PROPOSAL_CONE            */
     int32_t model;            /* PTCA_MODEL_DOUBLE_EXCHANGE, _HUBBARD_MF or _HOLSTEIN   */
     double cone_deg;          /* half-angle of the cone proposal, degrees             */
@@ -124,7 +130,8 @@ typedef struct {
     int64_t attempts;   /* proposals made (N per sweep)                               */
     int64_t accepted;   /* proposals accepted                                          */
     int64_t eigensolves;/* cluster matrices diagonalised (2 per proposal)              */
-    int64_t resolved;   /* PTCA_MIXED: proposals re-solved in FP64 near the threshold  */
+    int64_t resolved;   /* PTCA_MIXED: proposals re-solved at FP64-class precision     */
+                        /* near the threshold                                          */
     int64_t sweeps;     /* sweeps run so far on this context (RNG sweep counter)       */
     double  seconds;    /* device time of the call, from CUDA events                   */
     int64_t screened;   /* surrogate on: proposals rejected at stage 1 (no cluster     */
@@ -148,11 +155,14 @@ typedef struct {
 
 /* Validate the problem, build the stage schedule (Sec. III.a), allocate the
  * device state and draw the initial spins uniformly on the sphere from
- * `seed` (counter-based Philox4x32-10).  Rejects with PTCA_ERR_INVALID:
+ * `seed` (counter-based Philox4x32-10; Holstein: distortions uniform in
+ * [-1, 1]).  Rejects with PTCA_ERR_INVALID:
  * L_c out of range, a stride that lets a window of one stage contain another
  * update site of the same stage that precedes it, a block schedule with
  * L_c > floor(L/2)+1 on a torus, a tiled stride that does not divide L on a
- * torus, T <= 0, a matrix size above the supported maximum (n = 2 N_c <= 224).
+ * torus, T <= 0, a matrix order n = 2 N_c above 512 (orders above the
+ * shared-memory kernels' -- 224 in PTCA_MIXED, 144 in PTCA_FP64 -- run with
+ * the matrix in global memory).
  * Synchronous.  *out receives the context (owned by the library). */
 ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, ptca_ctx** out);
 
@@ -178,8 +188,8 @@ ptca_status ptca_set_spins(ptca_ctx* ctx, const double* src, int on_device, void
  * the packed-triangle slots that ptca_build_clusters uses (nmax(nmax+1)/2). */
 ptca_status ptca_dims(const ptca_ctx* ctx, int32_t* nmax, int64_t* packed_stride);
 
-/* Step b (and d, with new_spins): build the cluster Hamiltonians H_clus of m
- * update sites from the current spins.
+/* Sec. II.c step b (and d, with new_spins): build the cluster Hamiltonians
+ * H_clus of m update sites from the current spins.
  *   sites      device int32[m], lattice sites (0 <= site < N)
  *   new_spins  device double[m*3] replacing the spin of each update site, or NULL
  *   H_out      device buffer of m * packed_stride complex elements in the
@@ -187,26 +197,31 @@ ptca_status ptca_dims(const ptca_ctx* ctx, int32_t* nmax, int64_t* packed_stride
  *   offsets_out device int64[m]  (= i * packed_stride)
  *   n_out      device int32[m]   matrix order 2 * (window sites)
  * Window, boundary and basis follow the module comment; basis index of window
- * site (wx, wy) and spin s is 2*(wy*ex + wx) + s. */
+ * site (wx, wy, wz) and spin s is 2*((wz*ey + wy)*ex + wx) + s. */
 ptca_status ptca_build_clusters(ptca_ctx* ctx, const int32_t* sites, int32_t m,
                                 const double* new_spins, void* H_out, int64_t* offsets_out,
                                 int32_t* n_out, void* stream);
 
-/* Steps b/d: all eigenvalues, ascending, of m packed Hermitian matrices.
+/* Sec. II.c steps b/d: all eigenvalues, ascending, of m packed Hermitian
+ * matrices (the exact diagonalisation of each cluster).
  *   H        device, packed lower triangles in the context precision
  *   offsets  device int64[m], element offset of matrix i in H
  *   n        device int32[m], order of matrix i (1 <= n <= nmax)
  *   eig_out  device double[], eigenvalues of matrix i at eig_out + eig_offsets[i]
  *   eig_offsets device int64[m]
- * PTCA_FP64: FP64 Householder reduction to tridiagonal form, FP64 bisection.
- * PTCA_MIXED: FP32 reduction, FP32 bisection, one FP64 Newton correction per
- * eigenvalue on the tridiagonal.  Sizes are checked on the device; a matrix
- * with n outside [1, nmax] gets NaN eigenvalues. */
+ * Every eigenvalue is first bracketed by FP32 multisection with Sturm counts.
+ * PTCA_FP64: FP64 Householder reduction to tridiagonal form; the bracket is
+ * confirmed by FP64 Sturm counts and refined by safeguarded FP64 Newton.
+ * PTCA_MIXED: FP32 reduction; one double-float Newton step on the FP64
+ * tridiagonal.  Sizes are checked on the device; a matrix with n outside
+ * [1, nmax] gets NaN eigenvalues.  Shared-memory cluster orders only
+ * (PTCA_ERR_UNSUPPORTED for a large-cluster context). */
 ptca_status ptca_cluster_eigvals(ptca_ctx* ctx, const void* H, const int64_t* offsets,
                                  const int32_t* n, int32_t m, double* eig_out,
                                  const int64_t* eig_offsets, void* stream);
 
-/* Grand-canonical free energy of each eigenvalue list:
+/* Grand-canonical free energy of each eigenvalue list (the cluster free
+ * energy of Sec. II.b, without a model's classical term):
  * F_i = -T sum_k ln(1 + exp(-(eig_k - mu)/T)), FP64, written to F_out[i]
  * (device double[m]).  eig/eig_offsets/n as in ptca_cluster_eigvals. */
 ptca_status ptca_free_energy(ptca_ctx* ctx, const double* eig, const int64_t* eig_offsets,
@@ -257,8 +272,9 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  *   pipeline       PTCA_PIPELINE_STAGES / _PERSISTENT / _GRAPH / _OVERLAP
  *                  (as above);
  *   warps_per_cta  8: one 8-warp CTA per cluster matrix (every precision
- *                  and order); 4: one warp group per matrix, twice the
- *                  resident matrices per SM (PTCA_MIXED, orders up to 128);
+ *                  and order); 4: one warp group per matrix, more resident
+ *                  matrices per SM (PTCA_MIXED, orders up to 128); 1: one
+ *                  warp per matrix (PTCA_MIXED, orders up to 32);
  *   ctas_per_sm    CTAs per SM of the persistent kernel, 0 = as many as fit.
  * Every configuration computes the same chain (decisions and spins; free
  * energies to rounding). */
@@ -307,8 +323,9 @@ ptca_status ptca_kernel_times(ptca_ctx* ctx, double* out, void* stream);
 /* PTCA_MIXED decision guard.  The FP32 reduction leaves an error of about
  * 1e-4 in dF at n = 128, so a Metropolis decision whose margin
  * |ln u + dF/T| is below `margin` is deferred: both cluster matrices of that
- * update site are solved again in FP64 (reduction and eigenvalues) and the
- * decision is taken on the FP64 dF, before the next stage starts.  With a
+ * update site are solved again at FP64-class precision (reduction and
+ * eigenvalues in double-float arithmetic, about 48 significant bits) and the
+ * decision is taken on that dF, before the next stage starts.  With a
  * margin above T^-1 times the largest dF error this makes decisions identical
  * to the FP64 path wherever the FP64 margin exceeds its own error.  Default
  * 1e-2 in PTCA_MIXED; 0 disables it.  The count of re-solved updates is
@@ -353,7 +370,8 @@ ptca_status ptca_observables(ptca_ctx* ctx, ptca_obs* out, void* stream);
  * second spin.  Its estimate of the proposal's free-energy change is
  *     dF~ = scale * ( h([P(s_old), s_new]) - h([P(s_new), s_old]) ),
  * antisymmetric in the two states.  Matrix products run on the tensor cores
- * with bfloat16 operands and FP32 accumulation (library kernels); parameters,
+ * with bfloat16 operands and FP32 accumulation (this library's mma.sync
+ * kernels); parameters,
  * AdamW moments and the rest are FP32.  With the surrogate enabled,
  * ptca_sweep uses delayed acceptance (Christen and Fox 2005): stage 1 passes
  * a proposal with probability min(1, exp(-dF~/T)); only passing proposals get
