@@ -4,6 +4,7 @@ schedules as the oracle (Sec. III.a) and rejects invalid problems."""
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -177,3 +178,28 @@ def test_large_clusters_are_accepted(built, Lc):
     # the large-cluster path; the schedule is the same rule.
     stages = P.ptca_schedule(P.Config(Lx=2 * Lc, Ly=2 * Lc, L_c=Lc, schedule=P.SCHEDULE_BLOCK, precision=P.MIXED))
     assert len(stages) == 4 and sum(st.size for st in stages) == 4 * Lc * Lc
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # gcc compiles include/ptca.h as C and prints each struct's size and field
+    # offsets; the ctypes mirrors must agree field by field.
+    structs = {"ptca_lattice": P.ptca.Lattice, "ptca_params": P.ptca.Params,
+               "ptca_sweep_stats": P.ptca.SweepStats, "ptca_obs": P.ptca.Obs,
+               "ptca_launch_config": P.ptca.LaunchConfig}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ptca.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)

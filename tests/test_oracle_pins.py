@@ -471,3 +471,26 @@ def test_structure_factor_sum_rule():
     tot = sum(oracle.structure_factor(Lx, Ly, S, 2 * math.pi * a / Lx, 2 * math.pi * b / Ly)
               for a in range(Lx) for b in range(Ly))
     assert abs(tot - 1.0) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Marshalling of the oracle's problem struct
+# --------------------------------------------------------------------------
+def test_oracle_model_struct_matches_the_c_layout(tmp_path):
+    # The oracle source is compiled into a probe that prints sizeof and every
+    # offsetof of oracle_model; the ctypes mirror must agree field by field.
+    import ctypes
+    import subprocess
+    fields = [f for f, _ in oracle._Model._fields_ if not f.startswith("pad")]
+    src = tmp_path / "layout.c"
+    body = "\n".join(f'    printf("{f} %zu\\n", offsetof(oracle_model, {f}));' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "ptca_oracle.c"\n'
+                   'int main(void) {\n    printf("size %zu\\n", sizeof(oracle_model));\n' + body + "\n    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    oracle_dir = os.path.join(os.path.dirname(GOLDEN), "..", "oracle")
+    subprocess.run(["gcc", "-std=c11", "-I", oracle_dir, "-o", str(exe), str(src), "-lm"], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {ln.split()[0]: int(ln.split()[1]) for ln in out if ln.strip()}
+    assert got["size"] == ctypes.sizeof(oracle._Model)
+    for f in fields:
+        assert got[f] == getattr(oracle._Model, f).offset, f
