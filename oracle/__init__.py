@@ -26,6 +26,7 @@ What each function follows (paper sections):
 from __future__ import annotations
 
 import ctypes
+import fcntl
 import os
 import subprocess
 import threading
@@ -57,16 +58,23 @@ def build(force: bool = False, sanitize: bool = False) -> str:
     process that has the ASan runtime preloaded."""
     os.makedirs(_BUILD, exist_ok=True)
     path = _SAN_PATH if sanitize else _LIB_PATH
-    if (not force and os.path.exists(path)
-            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+
+    def fresh():
+        return os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC)
+
+    if not force and fresh():
         return path
-    tmp = path + f".{os.getpid()}.tmp"
-    extra = (["-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined", "-fno-sanitize-recover=all"]
-             if sanitize else [])
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", *extra, "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, path)
+    with open(os.path.join(_BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)  # one builder at a time
+        if not force and fresh():
+            return path
+        tmp = path + f".{os.getpid()}.tmp"
+        extra = (["-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined", "-fno-sanitize-recover=all"]
+                 if sanitize else [])
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", *extra, "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, path)
     return path
 
 

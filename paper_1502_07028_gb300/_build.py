@@ -6,6 +6,7 @@ library boundary; the Python binding loads it with ctypes.
 """
 from __future__ import annotations
 
+import fcntl
 import os
 import shutil
 import subprocess
@@ -45,6 +46,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    # One builder at a time (several ranks of one job may start together);
+    # the others wait and then find the library up to date.
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and up_to_date():
+            return LIB
+        return _compile(verbose)
+
+
+def _compile(verbose: bool) -> str:
     cc = nvcc()
     procs = []
     objs = []
