@@ -199,8 +199,10 @@ def _replay(cfg, S0, stages, site, acc, sweep_index):
     return starts, S
 
 
-def _check_sweep_against_oracle(cfg, sweeps, sample=None, seed_spins=None, start=None):
+def _check_sweep_against_oracle(cfg, sweeps, sample=None, seed_spins=None, start=None, launch=None):
     ctx = P.Context(cfg)
+    if launch is not None:
+        P.ptca_set_launch_config(ctx.h, *launch)
     if seed_spins is not None:
         ctx.set_spins(inputs.random_unit_spins(seed_spins, cfg.N))
     if start is not None:
@@ -304,6 +306,16 @@ def test_full_size_100x100_sampled(prec, schedule, stride):
     cfg = P.Config(Lx=100, Ly=100, L_c=8, schedule=schedule, stride=stride, proposal=P.PROPOSAL_CONE,
                    cone_deg=30.0, T=0.05, mu=-6.5, seed=0, precision=prec)
     _check_sweep_against_oracle(cfg, sweeps=1, sample=6)
+
+
+def test_full_size_100x100_sampled_in_the_benchmarked_launch_configuration():
+    # The configuration the autotuner picks for the benchmark workload: the
+    # overlap pipeline (each stage's re-solve beside the next stage's
+    # independent visits) with one 4-warp CTA per cluster matrix.  Two sweeps,
+    # so the second starts while the first's last re-solve has just finished.
+    cfg = P.Config(Lx=100, Ly=100, L_c=8, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, cone_deg=30.0,
+                   T=0.05, mu=-6.5, seed=0, precision=P.MIXED)
+    _check_sweep_against_oracle(cfg, sweeps=2, sample=4, launch=(P.PIPELINE_OVERLAP, 4, 0))
 
 
 def test_observables_ferro_and_neel():
