@@ -11,7 +11,7 @@ import os
 import sys
 
 
-def main(argv=None):
+def parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--L", type=int, default=100)
@@ -38,17 +38,29 @@ def main(argv=None):
     ap.add_argument("--K", type=float, default=1.0, help="Holstein elastic constant")
     ap.add_argument("--U", type=float, default=8.0, help="Hubbard U (model hubbard)")
     ap.add_argument("--m-step", type=float, default=0.5, help="field proposal radius (model hubbard)")
-    a = ap.parse_args(argv)
+    return ap
+
+
+def config(a):
+    """The problem of parsed arguments `a` (30-degree cone proposals)."""
+    import paper_1502_07028_gb300 as P
+    return P.Config(Lx=a.L, Ly=a.Ly or a.L, Lz=a.Lz, L_c=a.Lc, update_offset=a.offset, periodic=0 if a.open else 1,
+                    J_H=a.JH, mu=a.mu, T=a.T, seed=a.seed,
+                    schedule=P.SCHEDULE_BLOCK if a.schedule == "block" else P.SCHEDULE_TILED, stride=a.stride,
+                    precision=P.MIXED if a.precision == "mixed" else P.FP64, proposal=P.PROPOSAL_CONE,
+                    cone_deg=30.0,
+                    model={"de": P.MODEL_DOUBLE_EXCHANGE, "hubbard": P.MODEL_HUBBARD_MF,
+                           "holstein": P.MODEL_HOLSTEIN}[a.model], U=a.U, m_step=a.m_step, lam=a.lam, K=a.K)
+
+
+def main(argv=None):
+    a = parser().parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import paper_1502_07028_gb300 as P
     from paper_1502_07028_gb300 import _build
 
     _build.build()
-    cfg = P.Config(Lx=a.L, Ly=a.Ly or a.L, Lz=a.Lz, L_c=a.Lc, update_offset=a.offset, periodic=0 if a.open else 1, J_H=a.JH, mu=a.mu, T=a.T, seed=a.seed,
-                   schedule=P.SCHEDULE_BLOCK if a.schedule == "block" else P.SCHEDULE_TILED, stride=a.stride,
-                   precision=P.MIXED if a.precision == "mixed" else P.FP64, proposal=P.PROPOSAL_CONE, cone_deg=30.0,
-                   model={"de": P.MODEL_DOUBLE_EXCHANGE, "hubbard": P.MODEL_HUBBARD_MF,
-                          "holstein": P.MODEL_HOLSTEIN}[a.model], U=a.U, m_step=a.m_step, lam=a.lam, K=a.K)
+    cfg = config(a)
     ctx = P.Context(cfg)
     P.ptca_set_launch_config(ctx.h, {"stages": P.PIPELINE_STAGES, "persistent": P.PIPELINE_PERSISTENT,
                                      "graph": P.PIPELINE_GRAPH, "overlap": P.PIPELINE_OVERLAP}[a.pipeline], a.warps, a.ctas_per_sm)

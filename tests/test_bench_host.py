@@ -1,5 +1,6 @@
-"""Host-side pieces of bench.py that need no GPU: the clock sampler's parsing
-of nvidia-smi rows and the rule that rejects a timed region's clocks."""
+"""Host-side pieces of the measurement tools that need no GPU: the clock
+sampler's parsing of nvidia-smi rows, the rule that rejects a timed region's
+clocks, and the profiling commands quoted in the ncu summaries."""
 import os
 import sys
 
@@ -57,3 +58,24 @@ def test_clock_held_low_with_no_reason_is_rejected():
 def test_hardware_slowdown_is_rejected_even_at_full_clock():
     row = "2070, 2070, 900.00, 0x0000000000000008, Active, Not Active, Not Active, Not Active"
     assert "hw_slowdown" in bench.clock_verdict(_summary([row]))
+
+
+def test_profile_commands_in_profiles_parse_to_valid_problems():
+    # Every profiling command that a summary under profiles/ gives must still
+    # be accepted by the CLI and describe a problem the library accepts.
+    import glob
+    import re
+    import shlex
+
+    import paper_1502_07028_gb300 as P
+    from paper_1502_07028_gb300 import profile_sweep
+
+    found = 0
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        text = open(path).read().replace("\\\n", " ")
+        for m in re.finditer(r"python -m paper_1502_07028_gb300\.profile_sweep([^\n`]*)", text):
+            a = profile_sweep.parser().parse_args(shlex.split(m.group(1)))
+            stages = P.ptca_schedule(profile_sweep.config(a))
+            assert sum(len(s) for s in stages) == profile_sweep.config(a).N
+            found += 1
+    assert found >= 3
