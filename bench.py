@@ -426,7 +426,7 @@ def holstein_mode(P, args, flush, stream, rank):
     return out
 
 
-def main():
+def parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -439,7 +439,11 @@ def main():
     ap.add_argument("--sg-train-steps", type=int, default=3000)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the surrogate, uneven-batch, Hubbard, large-cluster and Holstein measurements")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = parser().parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

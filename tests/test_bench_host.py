@@ -78,4 +78,7 @@ def test_profile_commands_in_profiles_parse_to_valid_problems():
             stages = P.ptca_schedule(profile_sweep.config(a))
             assert sum(len(s) for s in stages) == profile_sweep.config(a).N
             found += 1
-    assert found >= 3
+        for m in re.finditer(r"python bench\.py([^\n`]*)", text):
+            bench.parser().parse_args(shlex.split(m.group(1)))
+            found += 1
+    assert found >= 4
