@@ -116,3 +116,36 @@ def test_single_site_chain_samples_the_boltzmann_weight():
     keep = expect > 5
     chi2 = float(np.sum((counts[keep] - expect[keep]) ** 2 / expect[keep]))
     assert chi2 < 45.0, (chi2, counts, expect)
+
+
+def _binned(x, nb=16):
+    b = np.asarray(x)[: len(x) // nb * nb].reshape(nb, -1).mean(axis=1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(nb)
+
+
+def test_corner_and_central_update_sites_give_the_same_order_and_energy():
+    # Sec. VII.b: the 'corner' and the 'central' choice of update site give
+    # the same charge order N(pi) and energy.  Both chains start from the
+    # charge-density wave (from random distortions the domains of either
+    # scheme coarsen slowly) on a 32-site ring with N_c = 8; the means over
+    # 800 sweeps, with errors from 16 bins, must agree within 2 sigma.
+    N, T, sweeps, burn = 32, 0.1, 900, 100
+    stats = []
+    for central in (False, True):
+        if central:
+            m = _hol(Lx=N, Lc=8, T=T, seed=5, schedule=oracle.SCHEDULE_TILED, stride=8, ox=4)
+        else:
+            m = _hol(Lx=N, Lc=8, T=T, seed=5, schedule=oracle.SCHEDULE_BLOCK, ox=0)
+        S = np.zeros((N, 3))
+        S[:, 0] = 1.2 * (-1.0) ** np.arange(N)
+        n_pi, f_site = [], []
+        for sw in range(sweeps):
+            S, rec = oracle.sweep(m, S, sw)
+            if sw >= burn:
+                n_pi.append(oracle.structure_factor(N, 1, S, math.pi, 0.0))
+                f_site.append(np.mean(np.where(rec.accepted == 1, rec.F_new, rec.F_old)) / 8)
+        stats.append((_binned(n_pi), _binned(f_site)))
+    (nc, fc), (nm, fm) = stats
+    assert nc[0] > 1.0 and nm[0] > 1.0           # ordered at T = 0.1
+    assert abs(nc[0] - nm[0]) < 2 * math.hypot(nc[1], nm[1]), (nc, nm)
+    assert abs(fc[0] - fm[0]) < 2 * math.hypot(fc[1], fm[1]), (fc, fm)
