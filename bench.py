@@ -464,7 +464,7 @@ def main():
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     # --- mixed precision (headline): FP32 reduction, FP64 eigenvalues and dF,
-    # FP64 re-solve of decisions within the margin (decisions equal FP64's)
+    # double-float (FP64-class) re-solve of decisions within the margin (decisions equal FP64's)
     ctx = P.Context(P.Config(**base, precision=P.MIXED))
     # Autotuner: CTA width x pipeline x persistent CTAs per SM, timed on this
     # lattice; the chain state is restored and the fastest applied.
@@ -598,7 +598,7 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"100x100 torus, 8x8 clusters (n=128 complex Hermitian), cone 30deg, "
                                    f"T=0.05, mu=-6.5, J_H=8, {args.schedule} schedule ({n_stages} stages), "
-                                   f"mixed precision with FP64 re-solve of near-threshold decisions",
+                                   f"mixed precision with a double-float re-solve of near-threshold decisions",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": "spin-updates/s", "h2d_bytes_per_step": N * 24,
@@ -609,7 +609,7 @@ def main():
                          "candidates": [[c["pipeline"], c["warps_per_cta"], c["ctas_per_sm"], c["ms_per_sweep"]]
                                         for c in tune_table["candidates"]]},
             "mixed_unguarded": {"value": unguarded_value, "unit": "spin-updates/s",
-                                "note": "same path without the FP64 re-solve of decisions within 1e-2"},
+                                "note": "same path without the double-float re-solve of decisions within 1e-2"},
             "resolved_fraction": resolved_frac,
             "fp64_path": {"value": fp64_value, "unit": "spin-updates/s", "ms_per_step": sum(fp64_ms) / len(fp64_ms)},
             "speedup_vs_fp64_path": value / fp64_value / world,

@@ -1045,7 +1045,7 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
 ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
     if (!(margin >= 0.0) || !std::isfinite(margin)) return fail(PTCA_ERR_INVALID, "margin must be finite and >= 0");
-    if (ctx->prec != 1 && margin > 0.0) return fail(PTCA_ERR_INVALID, "the FP64 re-solve applies to PTCA_MIXED only");
+    if (ctx->prec != 1 && margin > 0.0) return fail(PTCA_ERR_INVALID, "the re-solve margin applies to PTCA_MIXED only");
     ctx->margin = margin;
     drop_graph(ctx);
     return PTCA_OK;

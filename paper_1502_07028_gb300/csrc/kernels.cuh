@@ -282,7 +282,7 @@ struct StageArgs;
 // that all n eigenvalues are returned: eig[(2c+var)*ld + k] ascending,
 // F[2c+var] = -T sum_k softplus(-(eps_k-mu)/T).  k_check: precision T, matrix
 // in shared memory, one item per CTA.  k_check_ref: FP64 with the matrix in
-// the CTA's global slot (as the FP64 re-solve), items grid-strided.
+// the CTA's global slot (as the double-float re-solve), items grid-strided.
 template <typename T, int NT>
 __global__ void __launch_bounds__(CTA, MinBlocks<T, NT>::value) k_check(StageArgs a, int c0, int count, double* eig,
                                                                           int ld, double* F);
@@ -322,7 +322,7 @@ struct StageArgs {
     double* rec_Facc;
     double* rec_fill;
     int32_t* rec_n;
-    unsigned long long* counters;  // [0] accepted, [1] eigensolves, [2] FP64 re-solves
+    unsigned long long* counters;  // [0] accepted, [1] eigensolves, [2] re-solves
     int32_t* err;
     // PTCA_MIXED decision guard: a decision with |ln u + dF/T| < margin is
     // deferred (its stage index appended to flag_list) and re-solved in FP64

@@ -41,7 +41,7 @@ cudaError_t launch_stage(int prec, int nw, const StageArgs& a, cudaStream_t st);
 cudaError_t launch_persistent(int prec, int nw, const PersistArgs& p, int grid, cudaStream_t st);
 // CTAs of the persistent kernel that fit on one SM for matrices up to nA.
 int persistent_blocks_per_sm(int prec, int nw, int nA);
-// FP64 re-solve of the decisions a PTCA_MIXED stage deferred (grid CTAs).
+// Double-float (FP64-class) re-solve of the decisions a PTCA_MIXED stage deferred (grid CTAs).
 cudaError_t launch_resolve(const StageArgs& a, int grid, cudaStream_t st);
 // Precision checker: spectra of visits c0 .. c0+count-1 of a stage (prec 1:
 // FP32 reduction as PTCA_MIXED sweeps; prec 0: FP64 on the global matrix

@@ -25,7 +25,7 @@ def parser() -> argparse.ArgumentParser:
     ap.add_argument("--pipeline", choices=["stages", "persistent", "graph", "overlap"], default="graph")
     ap.add_argument("--warps", type=int, choices=[1, 4, 8], default=8, help="warps per CTA of the sweep kernels")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: as many as fit)")
-    ap.add_argument("--margin", type=float, default=None, help="mixed-mode FP64 re-solve margin (0 = off)")
+    ap.add_argument("--margin", type=float, default=None, help="mixed-mode re-solve margin (0 = off)")
     ap.add_argument("--sweeps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=0)
     ap.add_argument("--T", type=float, default=0.05)
