@@ -416,6 +416,34 @@ def test_sequential_sweep_equals_stagewise_snapshot_sweep():
         assert 0 < rec.accepted.sum() < m.N
 
 
+@pytest.mark.parametrize("kw", [
+    dict(Lx=6, Ly=6, Lz=6, Lc=3, schedule=oracle.SCHEDULE_BLOCK, T=0.5),               # cube, 8 blocks
+    dict(Lx=5, Ly=4, Lz=3, Lc=3, lattice_periodic=0, schedule=oracle.SCHEDULE_BLOCK),  # open box
+    dict(Lx=8, Ly=8, Lc=4, model=oracle.MODEL_HUBBARD_MF, U=8.0, mu=4.0, T=0.2, schedule=oracle.SCHEDULE_BLOCK),
+    dict(Lx=32, Ly=1, Lc=8, model=oracle.MODEL_HOLSTEIN, lam=1.5, K=1.0, mu=0.0, T=0.1, m_step=0.4,
+         schedule=oracle.SCHEDULE_TILED, stride=8, ox=4),                               # central site
+])
+def test_stagewise_snapshot_sweep_for_every_model_and_dimension(kw):
+    # The same PTCA claim for cubic lattices and for the Hubbard and Holstein
+    # models, whose cluster free energies carry a classical term.
+    m = oracle.Model(**{"t": 1.0, "seed": 11, **kw})
+    S0 = oracle.init_spins(m)
+    S_seq, rec = oracle.sweep(m, S0, 3)
+    S = S0.copy()
+    for st in oracle.schedule(m):
+        snap = S.copy()
+        for site in st:
+            site = int(site)
+            F_old = oracle.cluster_free_energy(m, snap, site)
+            s_new = oracle.propose(m, 3, site, snap[site])
+            F_new = oracle.cluster_free_energy(m, snap, site, s_new)
+            u = oracle.uniform2(m.seed, 3, site, 2)[0]
+            if math.log(u) < -(F_new - F_old) / m.T:
+                S[site] = s_new
+    assert np.array_equal(S, S_seq)
+    assert 0 < rec.accepted.sum() < m.N
+
+
 # --------------------------------------------------------------------------
 # Metropolis (Sec. II.c steps e-f): stationary distribution of one site
 # --------------------------------------------------------------------------
