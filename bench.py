@@ -230,13 +230,22 @@ def cpu_oracle_rate_pool(cfg_kw, visits_per_core: int = 6):
     return len(stage) / dt, len(stage), dt, cores
 
 
+def workload_name(schedule: str, n_stages: int) -> str:
+    """The headline workload, as both arms name it in config.workload."""
+    return (f"100x100 torus, 8x8 clusters (n=128 complex Hermitian), cone 30deg, T=0.05, mu=-6.5, J_H=8, "
+            f"{schedule} schedule ({n_stages} stages)")
+
+
 def run_reference(args, world, rank):
     """The oracle as the reference arm, timed on the host cores."""
     if rank != 0:
         return
-    cfg_kw = dict(WORKLOAD, schedule=1, stride=0)
+    sched = {"block": (1, 0), "tiled10": (0, 10), "tiled5": (0, 5)}[args.schedule]
+    cfg_kw = dict(WORKLOAD, schedule=sched[0], stride=sched[1])
     import oracle
     oracle.build()
+    n_stages = len(oracle.schedule(oracle.Model(Lx=WORKLOAD["Lx"], Ly=WORKLOAD["Ly"], Lc=WORKLOAD["L_c"],
+                                                schedule=sched[0], stride=sched[1])))
     per_step = []
     visits = 0
     cores = 1
@@ -252,7 +261,10 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_update * N,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "100x100 torus, 8x8 clusters (n=128), cone 30deg, T=0.05, block schedule",
+        "config": {"workload": workload_name(args.schedule, n_stages),
+                   "precision": "FP64 throughout (the oracle's Jacobi eigensolver)",
+                   "l2": "not applicable: the oracle runs on the host cores",
+                   "parallelism": f"{cores} host processes",
                    "sample": "2 visits of stage 0 per host core per step"},
         "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
                          "sample": f"{visits} visits (2 Jacobi eigensolves of 128x128 each) over {args.steps} steps, "
@@ -596,9 +608,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"100x100 torus, 8x8 clusters (n=128 complex Hermitian), cone 30deg, "
-                                   f"T=0.05, mu=-6.5, J_H=8, {args.schedule} schedule ({n_stages} stages), "
-                                   f"mixed precision with a double-float re-solve of near-threshold decisions",
+            "config": {"workload": workload_name(args.schedule, n_stages),
+                       "precision": "mixed: FP32 reduction, double-float eigenvalue finish, FP64 free energies, "
+                                    "double-float re-solve of near-threshold decisions",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": "spin-updates/s", "h2d_bytes_per_step": N * 24,
