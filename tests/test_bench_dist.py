@@ -62,3 +62,8 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    # Same metric, unit, direction and workload as the GPU arm's line.
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["metric"] == bench.METRIC and d["unit"] == "spin-updates/s" and d["higher_is_better"] is True
+    assert d["config"]["workload"] == bench.workload_name("block", 4)
