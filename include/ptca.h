@@ -379,7 +379,7 @@ ptca_status ptca_observables(ptca_ctx* ctx, ptca_obs* out, void* stream);
  * min(1, exp(-(dF - dF~)/T)).  Detailed balance with respect to the exact
  * cluster free energy holds for any network; the network only changes how
  * many exact solves are spent.  Screening runs with the per-stage pipeline.
- * The paper has no surrogate; its exact TCA step is the judge here.       */
+ * The paper has no surrogate; its exact TCA step has the final say here.  */
 
 /* Number of FP32 parameters (layout W1[256x160] b1 W2[256x256] b2 W3 b3
  * W4[8x256] b4[8]; W1 columns 150..159 and W4/b4 rows 1..7 are padding). */
