@@ -151,6 +151,8 @@ def test_host_side_of_the_c_abi_is_clean_under_sanitizers(tmp_path):
                     "-Xcompiler", "-fPIC," + san, "-c", os.path.join(_build.CSRC, "api.cu"), "-o", api_o],
                    check=True, capture_output=True)
     objs = [os.path.join(_build.BUILD, s.replace(".cu", ".o")) for s in _build.SOURCES if s != "api.cu"]
+    if not all(os.path.exists(o) for o in objs):
+        _build.build(force=True)  # the library is current but its objects were removed
     subprocess.run([cc, *_build.ARCH, "-shared", "-Xcompiler", "-fsanitize=address,-fsanitize=undefined",
                     "-o", lib, api_o, *objs, "-lcudart", "-lcusolver"], check=True, capture_output=True)
     env = dict(os.environ, LD_PRELOAD=libasan,
