@@ -65,17 +65,23 @@ def test_init_spins_uniform_on_sphere():
 def test_cone_proposal_stays_in_cap_and_is_uniform_on_it(s_old):
     s_old = np.asarray(s_old, float) / np.linalg.norm(s_old)
     m = oracle.Model(Lx=64, Ly=64, Lc=4, proposal=oracle.PROPOSAL_CONE, cone_deg=30.0, seed=3)
-    cosines = []
+    props = []
     for site in range(3000):
         s = oracle.propose(m, 5, site, s_old)
         assert abs(np.linalg.norm(s) - 1.0) < 1e-14
-        cosines.append(float(s @ s_old))
-    c = np.array(cosines)
+        props.append(s)
+    props = np.array(props)
+    c = props @ s_old
     cmin = math.cos(math.radians(30.0))
     assert c.min() >= cmin - 1e-12
     # cos(theta) uniform on [cos 30deg, 1]: mean (1+cmin)/2, var (1-cmin)^2/12.
     sd = (1 - cmin) / math.sqrt(12 * c.size)
     assert abs(c.mean() - (1 + cmin) / 2) < 5 * sd
+    # Azimuth uniform about s_old: the part perpendicular to s_old averages to
+    # zero, each of its components with variance E[sin^2 theta]/2.
+    perp = props - c[:, None] * s_old
+    sd_perp = math.sqrt(np.mean(np.sum(perp ** 2, axis=1)) / 2 / c.size)
+    assert np.all(np.abs(perp.mean(axis=0)) < 5 * sd_perp)
 
 
 def test_sphere_proposal_ignores_old_spin_and_is_isotropic():
