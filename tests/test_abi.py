@@ -195,8 +195,9 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")
     exe = tmp_path / "layout"
-    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-o", str(exe),
-                    str(src)], check=True)
+    # Strict C99: the header is plain C, usable from any C toolchain.
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-o", str(exe), str(src)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
     got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
     for cname, cls in structs.items():
