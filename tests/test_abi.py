@@ -240,3 +240,14 @@ def test_noalloc_validates_on_the_host_before_touching_the_device(built):
     assert st == 1 and "n_stages" in msg
     assert status(cfg=P.Config(Lx=8, Ly=8, L_c=9))[0] == 1
     assert status(cfg=P.Config(Lx=8, Ly=8, L_c=4, model=P.MODEL_HOLSTEIN, m_step=0.0))[0] == 1
+
+
+def test_smoke_refuses_to_run_without_a_gpu(built):
+    # The smoke check exercises the CUDA path only; without a device it
+    # fails instead of falling back to anything.
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import __graft_entry__
+    with pytest.raises(RuntimeError, match="cuda:0"):
+        __graft_entry__.smoke()
