@@ -172,6 +172,28 @@ def test_stage_split_of_the_100x100_block_schedule(built):
     assert [n for _, n in split] == [2500 - 49, 2500 - 350, 2500 - 49, 2500 - 350]
 
 
+def test_stage_split_of_the_benchmarked_cube_large_cluster_and_chain_workloads(built):
+    """Closed forms of the split for the other benchmarked workloads.  With
+    corner windows [x, x+L_c-1] (block schedule), a visit depends on the
+    previous block iff, along every axis where the two blocks differ, it lies
+    within L_c-1 of its half's end: (L_c-1) of the half's positions on such
+    an axis, all of them on the others."""
+    # 40^3 torus, 4^3 clusters: blocks of 20^3 in the order (bz, by, bx).
+    cube = P.ptca_stage_split(P.Config(Lx=40, Ly=40, Lz=40, L_c=4, schedule=P.SCHEDULE_BLOCK,
+                                       model=P.MODEL_HUBBARD_MF, mu=4.0, precision=P.MIXED))
+    differ = [3, 1, 2, 1, 3, 1, 2, 1]     # axes in which block s and block s-1 differ
+    assert [n for _, n in cube] == [8000 - 3 ** d * 20 ** (3 - d) for d in differ]
+    # 48^2 torus, 12^2 clusters (matrix order 288): blocks of 24^2.
+    large = P.ptca_stage_split(P.Config(Lx=48, Ly=48, L_c=12, schedule=P.SCHEDULE_BLOCK, precision=P.MIXED))
+    assert [n for _, n in large] == [576 - 121, 576 - 11 * 24, 576 - 121, 576 - 11 * 24]
+    # Holstein chain with the central update site (tiled, stride N_c = 8):
+    # every window [c-4, c+3] holds c-1, a site of the previous stage.
+    chain = P.ptca_stage_split(P.Config(Lx=65536, Ly=1, L_c=8, schedule=P.SCHEDULE_TILED, stride=8,
+                                        update_offset=4, model=P.MODEL_HOLSTEIN, lam=1.5, K=1.0, mu=0.0,
+                                        m_step=0.4, precision=P.MIXED))
+    assert len(chain) == 8 and all(n == 0 for _, n in chain)
+
+
 @pytest.mark.parametrize("Lc", [11, 12, 16])
 def test_large_clusters_are_accepted(built, Lc):
     # Orders above the shared-memory kernels' (2 N_c = 242, 288, 512) go to
