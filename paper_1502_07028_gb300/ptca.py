@@ -215,6 +215,11 @@ def ptca_version() -> int:
     return lib().ptca_version()
 
 
+def ptca_last_error() -> str:
+    """Description of the last failure on this thread."""
+    return lib().ptca_last_error().decode()
+
+
 def ptca_schedule(cfg: Config):
     """Host-only schedule: list of int32 numpy arrays (one per stage)."""
     import numpy as np

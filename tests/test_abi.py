@@ -39,6 +39,13 @@ def test_header_declares_the_boundary():
     assert sorted(names) == sorted(P.ptca.EXPORTED)
 
 
+def test_binding_has_a_same_named_function_for_every_entry_point(built):
+    for name in _declared():
+        assert callable(getattr(P, name, None)), name
+    P.lib().ptca_version()
+    assert isinstance(P.ptca_last_error(), str)
+
+
 def test_library_exports_every_declared_symbol(built):
     for name in _declared():
         assert hasattr(built, name), name
