@@ -319,7 +319,7 @@ def surrogate_mode(P, base, args, flush, stream):
     del feat, center, dF
     P.ptca_surrogate_enable(ctx.h, True)
     steps = max(3, args.steps // 2)
-    ms = time_sweeps(ctx, steps, 2, flush, stream)
+    ms = time_sweeps(ctx, steps, 3, flush, stream)
     st = P.ptca_sweep(ctx.h, steps, stats=True, stream=stream)
     ctx.close()
     return {"value": N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
@@ -340,7 +340,7 @@ def uneven_mode(P, args, flush, stream, rank):
     ctx = P.Context(cfg)
     P.ptca_set_pipeline(ctx.h, P.PIPELINE_GRAPH)
     steps = 2
-    ms = time_sweeps(ctx, steps, 1, flush, stream)
+    ms = time_sweeps(ctx, steps, 3, flush, stream)
     st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
     ctx.close()
     return {"value": cfg.N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
@@ -367,7 +367,7 @@ def hubbard_mode(P, args, flush, stream, rank, Lz=1):
     ctx = P.Context(P.Config(**base, precision=P.MIXED))
     best, _ = P.ptca_autotune(ctx.h, 2)
     steps = max(3, args.steps // 2) if Lz == 1 else 3
-    ms = time_sweeps(ctx, steps, 2, flush, stream)
+    ms = time_sweeps(ctx, steps, 3, flush, stream)
     st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
     obs = P.ptca_observables(ctx.h, stream=stream)
     ctx.close()
@@ -378,7 +378,7 @@ def hubbard_mode(P, args, flush, stream, rank, Lz=1):
                            "ctas_per_sm": best.ctas_per_sm}})
     ctx = P.Context(P.Config(**base, precision=P.FP64))
     n64 = 2 if Lz == 1 else 1
-    ms64 = time_sweeps(ctx, n64, 1, flush, stream)
+    ms64 = time_sweeps(ctx, n64, 3, flush, stream)
     ctx.close()
     out["fp64_path"] = {"value": N * n64 / (sum(ms64) * 1e-3), "unit": "spin-updates/s",
                         "ms_per_step": sum(ms64) / n64}
@@ -395,7 +395,7 @@ def large_cluster_mode(P, args, flush, stream, rank):
     N = 48 * 48
     ctx = P.Context(P.Config(**base, precision=P.MIXED))
     best, _ = P.ptca_autotune(ctx.h, 1)
-    ms = time_sweeps(ctx, 3, 1, flush, stream)
+    ms = time_sweeps(ctx, 3, 3, flush, stream)
     st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
     ctx.close()
     out = {"workload": "48x48 torus, 12x12 clusters (n=288 complex Hermitian), J_H=8, mu=-6.5, T=0.05, cone 30deg, "
@@ -404,7 +404,7 @@ def large_cluster_mode(P, args, flush, stream, rank):
            "resolved_fraction": st.resolved / st.attempts, "acceptance": st.accepted / st.attempts,
            "launch": {"pipeline": best.pipeline}}
     ctx = P.Context(P.Config(**base, precision=P.FP64))
-    ms64 = time_sweeps(ctx, 1, 1, flush, stream)
+    ms64 = time_sweeps(ctx, 1, 3, flush, stream)
     ctx.close()
     out["fp64_path"] = {"value": N / (ms64[0] * 1e-3), "unit": "spin-updates/s", "ms_per_step": ms64[0]}
     return out
@@ -421,7 +421,7 @@ def holstein_mode(P, args, flush, stream, rank):
     ctx = P.Context(P.Config(**base, precision=P.MIXED))
     best, _ = P.ptca_autotune(ctx.h, 2)
     steps = max(3, args.steps // 2)
-    ms = time_sweeps(ctx, steps, 2, flush, stream)
+    ms = time_sweeps(ctx, steps, 3, flush, stream)
     st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
     obs = P.ptca_observables(ctx.h, stream=stream)
     ctx.close()
@@ -432,7 +432,7 @@ def holstein_mode(P, args, flush, stream, rank):
            "N_pi": obs.S_pipi,
            "launch": {"pipeline": best.pipeline, "warps_per_cta": best.warps_per_cta, "ctas_per_sm": best.ctas_per_sm}}
     ctx = P.Context(P.Config(**base, precision=P.FP64))
-    ms64 = time_sweeps(ctx, 2, 1, flush, stream)
+    ms64 = time_sweeps(ctx, 2, 3, flush, stream)
     ctx.close()
     out["fp64_path"] = {"value": N * 2 / (sum(ms64) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms64) / 2}
     return out
@@ -544,7 +544,7 @@ def main():
                    "batches": int(n_stages), "note": "FP32-reduction vs FP64 solve of every visit of one sweep"}
     # Same context without the decision guard (pure mixed precision).
     P.ptca_set_resolve_margin(ctx.h, 0.0)
-    ung_ms = time_sweeps(ctx, max(3, args.steps // 2), 2, flush, stream)
+    ung_ms = time_sweeps(ctx, max(3, args.steps // 2), 3, flush, stream)
     unguarded_value = N * len(ung_ms) / (sum(ung_ms) * 1e-3)
     ctx.close()
 
@@ -559,7 +559,7 @@ def main():
 
     # --- plain FP64 GPU path on the same workload
     ctx64 = P.Context(P.Config(**base, precision=P.FP64))
-    fp64_ms = time_sweeps(ctx64, args.fp64_steps, 1, flush, stream)
+    fp64_ms = time_sweeps(ctx64, args.fp64_steps, 3, flush, stream)
     ctx64.close()
     fp64_value = N * args.fp64_steps / (sum(fp64_ms) * 1e-3)
 
