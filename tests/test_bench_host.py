@@ -82,3 +82,18 @@ def test_profile_commands_in_profiles_parse_to_valid_problems():
             bench.parser().parse_args(shlex.split(m.group(1)))
             found += 1
     assert found >= 4
+
+
+def test_every_ncu_command_in_profiles_leaves_the_clocks_alone():
+    # An ncu run locks the GPU clocks unless told not to; every capture
+    # command quoted under profiles/ must carry --clock-control none.
+    import glob
+    import re
+
+    n = 0
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        text = open(path).read().replace("\\\n", " ")
+        for m in re.finditer(r"^\s*ncu (?!-i )[^\n]*", text, re.M):
+            assert "--clock-control none" in m.group(0), (path, m.group(0))
+            n += 1
+    assert n >= 3
