@@ -93,7 +93,7 @@ def test_every_ncu_command_in_profiles_leaves_the_clocks_alone():
     n = 0
     for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         text = open(path).read().replace("\\\n", " ")
-        for m in re.finditer(r"^\s*ncu (?!-i )[^\n]*", text, re.M):
+        for m in re.finditer(r"^\s*ncu (?=-)(?!-i )[^\n]*", text, re.M):
             assert "--clock-control none" in m.group(0), (path, m.group(0))
             n += 1
     assert n >= 3
