@@ -45,6 +45,11 @@ DRAM_BYTES_PER_MATRIX = {"k_stage<float,4,8>": None, "k_stage<float,4,4>": 330_4
                          "k_sweep_persistent<float,4,8>": None, "k_sweep_persistent<float,4,4>": None}
 
 
+# Nominal FP64 rate of a GB300 (TFLOP/s); no measured FP64 peak is on record
+# for this pool.
+FP64_PEAK_TFLOPS = 1.25
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -236,6 +241,11 @@ def workload_name(schedule: str, n_stages: int) -> str:
             f"{schedule} schedule ({n_stages} stages)")
 
 
+# Visits of stage 0 per host core in one step of the reference arm (about 3 s
+# of oracle work per step on 16 Grace cores).
+REF_VISITS_PER_CORE = 32
+
+
 def run_reference(args, world, rank):
     """The oracle as the reference arm, timed on the host cores."""
     if rank != 0:
@@ -246,30 +256,34 @@ def run_reference(args, world, rank):
     oracle.build()
     n_stages = len(oracle.schedule(oracle.Model(Lx=WORKLOAD["Lx"], Ly=WORKLOAD["Ly"], Lc=WORKLOAD["L_c"],
                                                 schedule=sched[0], stride=sched[1])))
-    per_step = []
+    step_s = []
     visits = 0
+    per_step_visits = 0
     cores = 1
     for i in range(args.warmup + args.steps):
-        rate, done, dt, cores = cpu_oracle_rate_pool(cfg_kw, visits_per_core=2)
+        rate, done, dt, cores = cpu_oracle_rate_pool(cfg_kw, visits_per_core=REF_VISITS_PER_CORE)
         if i >= args.warmup:
-            per_step.append(dt / done)
+            step_s.append(dt)
             visits += done
-    sec_per_update = sum(per_step) / len(per_step)
-    value = 1.0 / sec_per_update
+            per_step_visits = done
+    total_s = sum(step_s)
+    value = visits / total_s
     N = WORKLOAD["Lx"] * WORKLOAD["Ly"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_update * N,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args.schedule, n_stages),
                    "precision": "FP64 throughout (the oracle's Jacobi eigensolver)",
                    "l2": "not applicable: the oracle runs on the host cores",
                    "parallelism": f"{cores} host processes",
-                   "sample": "2 visits of stage 0 per host core per step"},
+                   "sample": f"one step = {per_step_visits} visits of stage 0 ({REF_VISITS_PER_CORE} per host core), "
+                             "not a whole sweep"},
         "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
                          "sample": f"{visits} visits (2 Jacobi eigensolves of 128x128 each) over {args.steps} steps, "
                                    f"independent clusters of stage 0 on a {cores}-process pool"},
         "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "full_sweep_s_extrapolated": N / value,
     }
     print(json.dumps(line), flush=True)
 
@@ -346,6 +360,111 @@ def uneven_mode(P, args, flush, stream, rank):
     return {"value": cfg.N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
             "resolved_fraction": st.resolved / st.attempts, "acceptance": st.accepted / st.attempts,
             "workload": "316x316 open, 10x10 clipped clusters (n=50..200), J_H=6, mu=-4.5, T=0.1, tiled s=10"}
+
+
+def schedule_mode(P, base, args, flush, stream, stride):
+    """The headline workload on a tiled schedule of stride s (centres on the
+    stride-s sublattice, 8x8 windows centred on them): s = 10 gives 100 stages
+    of 100 visits, s = 5 gives 25 stages of 400.  Mixed guarded, autotuned."""
+    cfg = dict(base, schedule=P.SCHEDULE_TILED, stride=stride)
+    N = cfg["Lx"] * cfg["Ly"]
+    ctx = P.Context(P.Config(**cfg, precision=P.MIXED))
+    best, _ = P.ptca_autotune(ctx.h, 2)
+    steps = 5
+    ms = time_sweeps(ctx, steps, 3, flush, stream)
+    st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
+    ctx.close()
+    n_stages = len(P.ptca_schedule(P.Config(**cfg, precision=P.MIXED)))
+    return {"workload": f"100x100 torus, 8x8 clusters (n=128), cone 30deg, T=0.05, tiled stride {stride} "
+                        f"({n_stages} stages of {N // n_stages})",
+            "value": N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
+            "resolved_fraction": st.resolved / st.attempts, "acceptance": st.accepted / st.attempts,
+            "launch": {"pipeline": best.pipeline, "warps_per_cta": best.warps_per_cta, "ctas_per_sm": best.ctas_per_sm}}
+
+
+def small_lattice_mode(P, args, flush, stream, rank):
+    """32x32 torus, 8x8 clusters (n = 128), tiled stride 8 (64 stages of 16
+    visits), sphere proposals, T in {0.02, 0.05, 0.1} x seeds {0, 1, 2}.  One
+    stage holds only 32 matrices, so the nine independent chains run
+    concurrently, one context and one stream each (per-stage launches); the
+    value is all chains' updates over the wall time between two device-wide
+    synchronisations.  Mixed guarded."""
+    import torch
+    base = dict(Lx=32, Ly=32, L_c=8, periodic=1, t=1.0, J_H=8.0, mu=-6.5, schedule=P.SCHEDULE_TILED, stride=8,
+                proposal=P.PROPOSAL_SPHERE)
+    N = 32 * 32
+    chains = []
+    for T in (0.02, 0.05, 0.1):
+        for seed in (0, 1, 2):
+            ctx = P.Context(P.Config(**base, T=T, seed=seed + 3 * rank, precision=P.MIXED))
+            P.ptca_set_pipeline(ctx.h, P.PIPELINE_STAGES)
+            chains.append((ctx, torch.cuda.Stream()))
+    sweeps = 5
+    for ctx, s in chains:
+        for _ in range(3):
+            P.ptca_sweep(ctx.h, 1, stats=False, stream=s)
+    torch.cuda.synchronize()
+    flush.add_(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        for ctx, s in chains:
+            P.ptca_sweep(ctx.h, 1, stats=False, stream=s)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    # one chain alone, for comparison
+    ctx0, s0 = chains[4]
+    flush.add_(1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(sweeps):
+        P.ptca_sweep(ctx0.h, 1, stats=False, stream=s0)
+    torch.cuda.synchronize()
+    dt1 = time.perf_counter() - t1
+    acc = {}
+    for (ctx, s), T in zip(chains, [0.02] * 3 + [0.05] * 3 + [0.1] * 3):
+        st = P.ptca_sweep(ctx.h, 1, stats=True, stream=s)
+        acc.setdefault(str(T), []).append(st.accepted / st.attempts)
+        ctx.close()
+    return {"workload": "32x32 torus, 8x8 clusters (n=128), tiled stride 8 (64 stages of 16), sphere proposals, "
+                        "T in {0.02, 0.05, 0.1} x seeds {0, 1, 2}, nine concurrent chains",
+            "value": len(chains) * N * sweeps / dt, "unit": "spin-updates/s", "sweeps_per_chain": sweeps,
+            "wall_s": dt, "single_chain": {"value": N * sweeps / dt1, "unit": "spin-updates/s"},
+            "acceptance_by_T": {k: sum(v) / len(v) for k, v in acc.items()},
+            "timing": "host wall clock between device synchronisations (several streams)"}
+
+
+def ramp_mode(P, args, flush, stream, rank):
+    """The uneven open lattice (316x316, 10x10 clusters clipped at the edges,
+    n = 50..200) through its temperature ramp T_k = 0.1 - 0.01 k, k = 0..9,
+    one sweep per temperature (ptca_set_T between sweeps), timed as a whole.
+    Mixed guarded, persistent kernel in a graph."""
+    cfg = P.Config(Lx=316, Ly=316, L_c=10, periodic=0, t=1.0, J_H=6.0, mu=-4.5, T=0.1, seed=rank,
+                   schedule=P.SCHEDULE_TILED, stride=10, precision=P.MIXED, proposal=P.PROPOSAL_SPHERE)
+    import torch
+    ctx = P.Context(cfg)
+    P.ptca_set_pipeline(ctx.h, P.PIPELINE_GRAPH)
+    for _ in range(2):
+        P.ptca_sweep(ctx.h, 1, stats=False, stream=stream)
+    torch.cuda.synchronize()
+    temps = [0.1 - 0.01 * k for k in range(10)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in temps]
+    acc = []
+    for (a, b), T in zip(ev, temps):
+        P.ptca_set_T(ctx.h, T)
+        flush.add_(1)
+        a.record(stream)
+        P.ptca_sweep(ctx.h, 1, stats=False, stream=stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
+    ctx.close()
+    return {"workload": "316x316 open, 10x10 clipped clusters (n=50..200), J_H=6, mu=-4.5, tiled s=10, "
+                        "T = 0.1 -> 0.01 in 10 linear steps, one sweep per T",
+            "value": cfg.N * len(temps) / (sum(ms) * 1e-3), "unit": "spin-updates/s",
+            "ms_per_sweep_by_T": {f"{T:.2f}": m for T, m in zip(temps, ms)},
+            "acceptance_at_T_0.01": st.accepted / st.attempts}
 
 
 def hubbard_mode(P, args, flush, stream, rank, Lz=1):
@@ -541,7 +660,10 @@ def main():
     P.ptca_set_checker(ctx.h, False)
     mixed_error = {"max_abs_eig": float(rows[:, 0].max()), "max_abs_dF": float(rows[:, 1].max()),
                    "max_eig_over_JH_4t": float(rows[:, 2].max()), "max_dF_over_F": float(rows[:, 3].max()),
-                   "batches": int(n_stages), "note": "FP32-reduction vs FP64 solve of every visit of one sweep"}
+                   "max_dF_over_dF_scale": float(rows[:, 4].max()),
+                   "batches": int(n_stages),
+                   "note": "FP32-reduction vs FP64 solve of every visit of one sweep; dF scale = "
+                           "max(|dF|, sum_k |eps_k - mu| f_k / n) of the old cluster"}
     # Same context without the decision guard (pure mixed precision).
     P.ptca_set_resolve_margin(ctx.h, 0.0)
     ung_ms = time_sweeps(ctx, max(3, args.steps // 2), 3, flush, stream)
@@ -556,6 +678,10 @@ def main():
         extra["hubbard_mf_3d"] = hubbard_mode(P, args, flush, stream, rank, Lz=40)
         extra["large_clusters"] = large_cluster_mode(P, args, flush, stream, rank)
         extra["holstein_chain"] = holstein_mode(P, args, flush, stream, rank)
+        extra["tiled10"] = schedule_mode(P, base, args, flush, stream, 10)
+        extra["tiled5"] = schedule_mode(P, base, args, flush, stream, 5)
+        extra["small_lattice_32"] = small_lattice_mode(P, args, flush, stream, rank)
+        extra["uneven_open_ramp"] = ramp_mode(P, args, flush, stream, rank)
 
     # --- plain FP64 GPU path on the same workload
     ctx64 = P.Context(P.Config(**base, precision=P.FP64))
@@ -596,7 +722,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        rate, done, dt, cores = cpu_oracle_rate_pool(dict(base))
+        rate, done, dt, cores = cpu_oracle_rate_pool(dict(base), visits_per_core=100)
         rate1, done1, dt1 = cpu_oracle_rate(dict(base), budget_s=10.0, max_visits=32)
         cpu = {"value": rate, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
                "sample": f"{done} visits of the first stage (2 Jacobi eigensolves of 128x128 each), independent "
@@ -623,7 +749,13 @@ def main():
             "mixed_unguarded": {"value": unguarded_value, "unit": "spin-updates/s",
                                 "note": "same path without the double-float re-solve of decisions within 1e-2"},
             "resolved_fraction": resolved_frac,
-            "fp64_path": {"value": fp64_value, "unit": "spin-updates/s", "ms_per_step": sum(fp64_ms) / len(fp64_ms)},
+            "fp64_path": {"value": fp64_value, "unit": "spin-updates/s", "ms_per_step": sum(fp64_ms) / len(fp64_ms),
+                          "roofline": {"bound": "alu", "kernel": "k_sweep_persistent<double,4,8>",
+                                       "achieved": fp64_value * 2 * HH_FLOPS / 1e12,
+                                       "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                       "frac": fp64_value * 2 * HH_FLOPS / 1e12 / FP64_PEAK_TFLOPS,
+                                       "note": "FP64 Householder flops per sweep over the sweep time; peak = the "
+                                               "nominal FP64 rate of a GB300"}},
             "speedup_vs_fp64_path": value / fp64_value / world,
             "eigensolves_per_s": 2 * value,
             "acceptance": acc_rate,

@@ -342,10 +342,14 @@ ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin);
 ptca_status ptca_set_checker(ptca_ctx* ctx, int32_t on);
 
 /* Checker results since the last read (or since the checker was first turned
- * on), then reset.  out: host array of n_rows x 4 doubles, n_rows >= the
+ * on), then reset.  out: host array of n_rows x 5 doubles, n_rows >= the
  * number of stages; row s = stage s: [0] max |d eps|, [1] max |d dF|,
  * [2] max |d eps| / (J_H + 4|t|) (the spectral-norm bound of a cluster
- * matrix), [3] max |d dF| / max(1, |F_old|, |F_new|).  Maxima over every
+ * matrix), [3] max |d dF| / max(1, |F_old|, |F_new|), [4] max |d dF| / s,
+ * s = max(|dF|, sum_k |eps_k - mu| f(eps_k) / n) from the FP64 spectrum of
+ * the old cluster (f the Fermi function, n the matrix order): the scale of
+ * a free-energy difference, about 1 on the double-exchange headline where
+ * |F| is about 100.  Maxima over every
  * sweep since the last read; a NaN anywhere reads as NaN.  Synchronises
  * `stream`. */
 ptca_status ptca_checker_read(ptca_ctx* ctx, double* out, int32_t n_rows, void* stream);
@@ -417,29 +421,38 @@ ptca_status ptca_surrogate_enable(ptca_ctx* ctx, int32_t on);
 /* Sweep without device allocation                                           */
 /* ----------------------------------------------------------------------- */
 
-/* Same sweep as ptca_sweep (one sweep, same kernels, same results), for
- * callers that cannot allocate device memory: hosts whose own pool owns the
- * device memory or that forbid loaded libraries to allocate, and loops that
- * cannot afford cudaMalloc/cudaFree (cudaFree synchronises the device).  The
- * paper has no counterpart; this is a property of the library.
- *   sites        device int32[N]: the flattened stage list of ptca_schedule
- *                for the same lattice and params
- *   stage_start  host int32[n_stages+1]: its stage offsets (checked)
+/* One sweep as ptca_sweep runs it in the per-stage pipeline (same stage and
+ * re-solve kernels, same decisions and spins), for callers that cannot
+ * allocate device memory: hosts whose own pool owns the device memory or
+ * that forbid loaded libraries to allocate, and loops that cannot afford
+ * cudaMalloc/cudaFree (cudaFree synchronises the device).  The paper has no
+ * counterpart; this is a property of the library.
  *   spins        device double[N*3]: the configuration, updated in place
  *   sweep_index  counter of the random stream (the sweep number, >= 0)
  *   F_out        device double[2N] or NULL: F_old of every visit, then F_new
- *   accepted_out device uint8[N] or NULL: decisions, flattened stage order
+ *   accepted_out device uint8[N] or NULL: decisions, in the flattened stage
+ *                order of ptca_schedule for the same lattice and params
+ *   status_out   device int32[1] or NULL: receives, stream-ordered after the
+ *                sweep, 0 or the ptca_status of a device-side failure
+ *                (PTCA_ERR_NUMERIC: a free-energy difference was not finite)
+ * The schedule is built and checked on the host, as ptca_init does, and
+ * copied into the library's array.  In PTCA_MIXED the decisions within 1e-2
+ * of the Metropolis threshold are re-solved at FP64-class precision, as
+ * ptca_sweep's default margin does; that re-solve keeps its matrix in shared
+ * memory, so PTCA_MIXED is limited to the orders where that fits (128 on a
+ * GB300; PTCA_ERR_UNSUPPORTED above).
  * No context and no device allocation: working memory is one array of about
- * 2 MB that the library defines in device global memory and that every GPU
+ * 2.2 MB that the library defines in device global memory and that every GPU
  * loading the library holds until the process exits.  Limit: N <= 16384
  * sites (larger lattices return PTCA_ERR_INVALID).  All calls share that
  * array and its contents persist between calls; calls that overlap on the GPU
  * (other streams or threads on the same device) race and must be serialised.
  * The first call on a device looks up the array's address with that device
- * current; make it before any stream capture.  Stream-ordered, asynchronous. */
-ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptca_params* params, const int32_t* sites,
-                               const int32_t* stage_start, int32_t n_stages, double* spins, int64_t sweep_index,
-                               double* F_out, uint8_t* accepted_out, void* stream);
+ * current; make it before any stream capture.  Stream-ordered, asynchronous
+ * (the host-to-device copy of the schedule is staged before it returns). */
+ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptca_params* params, double* spins,
+                               int64_t sweep_index, double* F_out, uint8_t* accepted_out, int32_t* status_out,
+                               void* stream);
 
 /* ----------------------------------------------------------------------- */
 /* Full-system spectrum                                                      */

@@ -623,7 +623,7 @@ static cudaError_t check_stage(ptca_ctx* ctx, const StageArgs& a, int s, cudaStr
         e = ptca::launch_check(1, a, c0, cnt, e32, ld, F32, 0, st);
         if (e == cudaSuccess) e = ptca::launch_check(0, a, c0, cnt, e64, ld, F64, ctx->resolve_grid, st);
         if (e == cudaSuccess)
-            e = ptca::launch_check_compare(a.m, a.sites + c0, cnt, e32, e64, ld, F32, F64, ctx->d_chk_out + 4 * s, st);
+            e = ptca::launch_check_compare(a.m, a.sites + c0, cnt, e32, e64, ld, F32, F64, ctx->d_chk_out + ptca::kCheckCols * s, st);
     }
     return e;
 }
@@ -1063,8 +1063,8 @@ ptca_status ptca_set_checker(ptca_ctx* ctx, int32_t on) {
         ctx->check_chunk = std::min(ctx->max_stage, 2048);
         cudaError_t e = dalloc(&ctx->d_chk_eig, (size_t)2 * ctx->check_chunk * 2 * ctx->nA);
         if (e == cudaSuccess) e = dalloc(&ctx->d_chk_F, (size_t)2 * ctx->check_chunk * 2);
-        if (e == cudaSuccess) e = dalloc(&ctx->d_chk_out, (size_t)4 * ctx->nstages);
-        if (e == cudaSuccess) e = cudaMemset(ctx->d_chk_out, 0, (size_t)4 * ctx->nstages * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = dalloc(&ctx->d_chk_out, (size_t)ptca::kCheckCols * ctx->nstages);
+        if (e == cudaSuccess) e = cudaMemset(ctx->d_chk_out, 0, (size_t)ptca::kCheckCols * ctx->nstages * sizeof(unsigned long long));
         if (e != cudaSuccess) {
             cudaFree(ctx->d_chk_eig);
             cudaFree(ctx->d_chk_F);
@@ -1083,11 +1083,11 @@ ptca_status ptca_checker_read(ptca_ctx* ctx, double* out, int32_t n_rows, void* 
     if (!ctx || !out) return fail(PTCA_ERR_INVALID, "null argument");
     if (n_rows < ctx->nstages) return fail(PTCA_ERR_INVALID, "out needs one row per stage");
     if (!ctx->d_chk_out) {
-        for (int i = 0; i < 4 * ctx->nstages; ++i) out[i] = 0.0;
+        for (int i = 0; i < ptca::kCheckCols * ctx->nstages; ++i) out[i] = 0.0;
         return PTCA_OK;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    std::vector<unsigned long long> bits((size_t)4 * ctx->nstages);
+    std::vector<unsigned long long> bits((size_t)ptca::kCheckCols * ctx->nstages);
     PTCA_CUDA(cudaMemcpyAsync(bits.data(), ctx->d_chk_out, bits.size() * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, st));
     PTCA_CUDA(cudaMemsetAsync(ctx->d_chk_out, 0, bits.size() * sizeof(unsigned long long), st));

@@ -110,7 +110,7 @@ struct ptca_ctx {
     int check_chunk = 0;
     double* d_chk_eig = nullptr;              // [2 precisions][check_chunk][2][nA]
     double* d_chk_F = nullptr;                // [2 precisions][check_chunk][2]
-    unsigned long long* d_chk_out = nullptr;  // [nstages][4], bits of non-negative doubles
+    unsigned long long* d_chk_out = nullptr;  // [nstages][kCheckCols], bits of non-negative doubles
     // overlapped pipeline: stage order with the visits independent of the
     // previous stage first (h_indep[s] of them), a high-priority stream for
     // the re-solves and the dependent visits, and the events ordering it

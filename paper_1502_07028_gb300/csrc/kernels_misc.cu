@@ -41,6 +41,7 @@ cudaError_t launch_stage_f32w1(const StageArgs&, cudaStream_t);
 cudaError_t launch_persistent_f32w1(const PersistArgs&, int, cudaStream_t);
 int persistent_blocks_per_sm_f32w1(int);
 cudaError_t launch_resolve_f32(const StageArgs&, int, cudaStream_t);
+bool resolve_smem_fits_f32(int nA);
 cudaError_t launch_check_f32(const StageArgs&, int, int, double*, int, double*, cudaStream_t);
 cudaError_t launch_check_ref_f32(const StageArgs&, int, int, double*, int, double*, int, cudaStream_t);
 
@@ -84,6 +85,7 @@ cudaError_t launch_persistent(int prec, int nw, const PersistArgs& p, int grid, 
     return prec ? launch_persistent_f32(p, grid, st) : launch_persistent_f64(p, grid, st);
 }
 cudaError_t launch_resolve(const StageArgs& a, int grid, cudaStream_t st) { return launch_resolve_f32(a, grid, st); }
+bool resolve_smem_fits(int nA) { return resolve_smem_fits_f32(nA); }
 int persistent_blocks_per_sm(int prec, int nw, int nA) {
     if (nw == 4) return prec ? persistent_blocks_per_sm_f32w4(nA) : 0;
     if (nw == 1) return prec ? persistent_blocks_per_sm_f32w1(nA) : 0;
@@ -104,38 +106,55 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double 
 // Errors of the FP32-reduction spectra (e32, F32) against the FP64 ones (e64,
 // F64) for `count` visits: out[0] max |d eps|, out[1] max |d dF|, out[2] max
 // |d eps| / (J_H + 4|t|) (the spectral-norm bound of every cluster matrix),
-// out[3] max |d dF| / max(1, |F_old|, |F_new|) (as bit patterns of
-// non-negative doubles).
+// out[3] max |d dF| / max(1, |F_old|, |F_new|), out[4] max |d dF| / s with
+// the free-energy-difference scale s = max(|dF|, sum_k |eps_k - mu| f_k / n)
+// of the FP64 old-cluster spectrum (f the Fermi function): the typical size
+// of one level's contribution to F, the scale on which dF itself lives (as
+// bit patterns of non-negative doubles).
 __global__ void k_check_compare(Model m, const int32_t* __restrict__ sites, int count, const double* __restrict__ e32,
                                 const double* __restrict__ e64, int ld, const double* __restrict__ F32,
                                 const double* __restrict__ F64, unsigned long long* out) {
+    __shared__ double s_part[32];
     const int c = blockIdx.x;
     if (c >= count) return;
     const Window w = make_window(m, sites[c]);
     const int n = 2 * window_nsite(w);
-    double de = 0.0;
+    const double mu = m.mu - m.e0;  // the spectra are of the matrix without its on-site shift e0
+    double de = 0.0, lev = 0.0;
     for (int var = 0; var < 2; ++var) {
         const double* a = e32 + (int64_t)(2 * c + var) * ld;
         const double* b = e64 + (int64_t)(2 * c + var) * ld;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             const double d = fabs(a[k] - b[k]);
             de = (d > de || d != d) ? d : de;
+            if (var == 0) {
+                const double x = (b[k] - mu) / m.T;
+                lev += fabs(b[k] - mu) / (1.0 + exp(x));
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
         const double x = __shfl_xor_sync(0xffffffffu, de, o);
         de = (x > de || x != x) ? x : de;
+        lev += __shfl_xor_sync(0xffffffffu, lev, o);
     }
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         atomic_max_nonneg(out, de);
         atomic_max_nonneg(out + 2, de / (m.JH + 4.0 * fabs(m.t)));
+        s_part[warp] = lev;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double levels = 0.0;
+        for (int q = 0; q < nwarp; ++q) levels += s_part[q];
         const double d64 = F64[2 * c + 1] - F64[2 * c];
         const double d32 = F32[2 * c + 1] - F32[2 * c];
         const double ddF = fabs(d32 - d64);
         atomic_max_nonneg(out + 1, ddF);
         atomic_max_nonneg(out + 3, ddF / fmax(1.0, fmax(fabs(F64[2 * c]), fabs(F64[2 * c + 1]))));
+        const double scale = fmax(fabs(d64), levels / (double)n);
+        atomic_max_nonneg(out + 4, scale > 0.0 ? ddF / scale : ddF);
     }
 }
 
@@ -158,6 +177,16 @@ cudaError_t launch_barrier_selftest(int blocks, unsigned int* bar, int32_t* err,
 }
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+// Status word of a sweep from its device error slots: err[1] (a timed-out
+// barrier) -> 4 (PTCA_ERR_TIMEOUT), else err[0] (a non-finite dF) -> 5
+// (PTCA_ERR_NUMERIC), else 0.
+__global__ void k_status_word(const int32_t* err, int32_t* out) { *out = err[1] ? 4 : (err[0] ? 5 : 0); }
+
+cudaError_t launch_status_word(const int32_t* err, int32_t* out, cudaStream_t st) {
+    k_status_word<<<1, 1, 0, st>>>(err, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) {
     k_set_u64<<<1, 1, 0, st>>>(p, v);

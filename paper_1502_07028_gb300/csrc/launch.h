@@ -43,11 +43,18 @@ cudaError_t launch_persistent(int prec, int nw, const PersistArgs& p, int grid, 
 int persistent_blocks_per_sm(int prec, int nw, int nA);
 // Double-float (FP64-class) re-solve of the decisions a PTCA_MIXED stage deferred (grid CTAs).
 cudaError_t launch_resolve(const StageArgs& a, int grid, cudaStream_t st);
+// Whether launch_resolve keeps matrices up to order nA in shared memory (no
+// global slot a.gA needed).  Valid after configure_cluster_kernels.
+bool resolve_smem_fits(int nA);
+// out[0] = the ptca_status a sweep's device error slots err[0..1] report.
+cudaError_t launch_status_word(const int32_t* err, int32_t* out, cudaStream_t st);
 // Precision checker: spectra of visits c0 .. c0+count-1 of a stage (prec 1:
 // FP32 reduction as PTCA_MIXED sweeps; prec 0: FP64 on the global matrix
 // slots a.gA, grid CTAs), and their FP32-vs-FP64 errors reduced into out[4].
 cudaError_t launch_check(int prec, const StageArgs& a, int c0, int count, double* eig, int ld, double* F, int grid,
                          cudaStream_t st);
+// Columns of a checker row (see k_check_compare).
+constexpr int kCheckCols = 5;
 cudaError_t launch_check_compare(const Model& m, const int32_t* sites, int count, const double* e32,
                                  const double* e64, int ld, const double* F32, const double* F64,
                                  unsigned long long* out, cudaStream_t st);

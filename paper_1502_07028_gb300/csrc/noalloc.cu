@@ -6,21 +6,21 @@
 // forbid the libraries they load from allocating; others run latency-critical
 // loops in which cudaMalloc/cudaFree (cudaFree synchronises the whole device)
 // are not acceptable.  ptca_init allocates the context's buffers, so those
-// callers cannot use ptca_sweep.  This entry point runs the same stage kernel
-// on caller-owned spins and caller-owned outputs, and keeps all of its own
-// working memory in one fixed-size array in device global memory that the
-// library defines at file scope.  It allocates no device memory: no
-// cudaMalloc, cudaFree or allocating library routine (host-side argument
-// checks use ordinary host memory only).
+// callers cannot use ptca_sweep.  This entry point runs the same stage and
+// re-solve kernels on caller-owned spins and caller-owned outputs, and keeps
+// all of its own working memory in one fixed-size array in device global
+// memory that the library defines at file scope.  It allocates no device
+// memory: no cudaMalloc, cudaFree or allocating library routine (host-side
+// argument checks and the schedule use ordinary host memory only).
 //
 // Properties a caller must know:
-//   * The array holds kNoAllocBytes (about 2 MB) on every GPU on which the
+//   * The array holds kNoAllocBytes (about 2.2 MB) on every GPU on which the
 //     library is loaded, until the process exits, whether or not it is used.
 //   * It bounds the problem: at most kNoAllocMaxSites lattice sites.
-//   * All calls share it.  Calls whose work overlaps on the GPU (different
-//     streams, or different host threads on the same device) race on it and
-//     produce garbage; serialise them.  Each call clears what must start at
-//     zero before its first kernel.
+//   * All calls share it and it keeps the last call's contents.  Calls whose
+//     work overlaps on the GPU (different streams, or different host threads
+//     on the same device) race on it and produce garbage; serialise them.
+//     Each call clears what must start at zero before its first kernel.
 //   * The first call on each device resolves the array's device address with
 //     cudaGetSymbolAddress (with that device current) and caches it; make that
 //     first call before any stream capture.
@@ -38,6 +38,7 @@ namespace {
 
 constexpr int kNoAllocMaxSites = 16384;  // e.g. up to a 128 x 128 lattice
 constexpr int kNoAllocMaxDevices = 64;
+constexpr double kNoAllocMargin = 1e-2;  // re-solve band of PTCA_MIXED, as ptca_init's default
 
 // Byte layout of the scratch array (offsets are multiples of 256).
 constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -53,9 +54,12 @@ constexpr size_t kOffRecFacc = al256(kOffRecLnu + sizeof(double) * kNoAllocMaxSi
 constexpr size_t kOffRecFill = al256(kOffRecFacc + sizeof(double) * kNoAllocMaxSites);  // double[N]
 constexpr size_t kOffRecN = al256(kOffRecFill + sizeof(double) * kNoAllocMaxSites);     // int32[N]
 constexpr size_t kOffRecAcc = al256(kOffRecN + sizeof(int32_t) * kNoAllocMaxSites);     // uint8[N]
-constexpr size_t kOffCounters = al256(kOffRecAcc + kNoAllocMaxSites);                  // u64[4]
-constexpr size_t kOffErr = al256(kOffCounters + 4 * sizeof(unsigned long long));        // int32[1]
-constexpr size_t kNoAllocBytes = al256(kOffErr + sizeof(int32_t));
+constexpr size_t kOffSites = al256(kOffRecAcc + kNoAllocMaxSites);                      // int32[N] schedule
+constexpr size_t kOffFlags = al256(kOffSites + sizeof(int32_t) * kNoAllocMaxSites);     // int32[N] deferred visits
+constexpr size_t kOffFlagCount = al256(kOffFlags + sizeof(int32_t) * kNoAllocMaxSites); // u32[1]
+constexpr size_t kOffCounters = al256(kOffFlagCount + sizeof(unsigned int));            // u64[4]
+constexpr size_t kOffErr = al256(kOffCounters + 4 * sizeof(unsigned long long));        // int32[2]
+constexpr size_t kNoAllocBytes = al256(kOffErr + 2 * sizeof(int32_t));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -67,14 +71,13 @@ unsigned char* g_addr[kNoAllocMaxDevices] = {};
 // Defined in api.cu: records the message that ptca_last_error() returns.
 ptca_status ptca_internal_fail(ptca_status s, const char* msg);
 
-extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptca_params* params,
-                                          const int32_t* sites, const int32_t* stage_start, int32_t n_stages,
-                                          double* spins, int64_t sweep_index, double* F_out,
-                                          uint8_t* accepted_out, void* stream) {
-    if (!lattice || !params || !sites || !stage_start || !spins)
+extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptca_params* params, double* spins,
+                                          int64_t sweep_index, double* F_out, uint8_t* accepted_out,
+                                          int32_t* status_out, void* stream) {
+    if (!lattice || !params || !spins)
         return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_sweep_noalloc: null argument");
     if (sweep_index < 0) return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_sweep_noalloc: sweep_index < 0");
-    // Validate the problem and the schedule on the host (no device memory).
+    // Validate the problem and build its schedule on the host (no device memory).
     const int64_t N64 = (int64_t)lattice->Lx * (int64_t)lattice->Ly * (int64_t)(lattice->Lz > 1 ? lattice->Lz : 1);
     if (lattice->Lx < 1 || lattice->Ly < 1 || lattice->Lz < 0 || N64 > kNoAllocMaxSites)
         return ptca_internal_fail(PTCA_ERR_INVALID,
@@ -82,14 +85,10 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
                                    " sites; this entry point supports at most " + std::to_string(kNoAllocMaxSites))
                                       .c_str());
     const int N = (int)N64;
-    std::vector<int32_t> ref_start(N + 1), ref_sites(N);
-    int32_t ref_ns = 0;
-    ptca_status st = ptca_schedule(lattice, params, ref_start.data(), ref_sites.data(), &ref_ns);
+    std::vector<int32_t> stage_start(N + 1), sched(N);
+    int32_t n_stages = 0;
+    ptca_status st = ptca_schedule(lattice, params, stage_start.data(), sched.data(), &n_stages);
     if (st != PTCA_OK) return st;
-    if (n_stages != ref_ns) return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_sweep_noalloc: n_stages does not match the schedule");
-    for (int s = 0; s <= n_stages; ++s)
-        if (stage_start[s] != ref_start[s])
-            return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_sweep_noalloc: stage_start does not match ptca_schedule");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -108,8 +107,9 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
         }
         base = g_addr[dev];
     }
-    int optin = 0;
+    int optin = 0, sms = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
     // Problem description (same resolution rules as ptca_init).
     const int Lc = params->L_c;
@@ -133,16 +133,31 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
         return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_sweep_noalloc: cluster matrix too large for this precision");
     e = ptca::configure_cluster_kernels((size_t)optin);
     if (e != cudaSuccess) return ptca_internal_fail(PTCA_ERR_CUDA, cudaGetErrorString(e));
+    // PTCA_MIXED re-solves the decisions within kNoAllocMargin of the
+    // threshold, as ptca_sweep does; that re-solve must keep its matrix in
+    // shared memory here (the global matrix slots it uses otherwise are
+    // context memory).
+    if (prec == 1 && !ptca::resolve_smem_fits(nA))
+        return ptca_internal_fail(PTCA_ERR_UNSUPPORTED,
+                                  ("ptca_sweep_noalloc: in PTCA_MIXED the re-solve of order-" + std::to_string(nA) +
+                                   " cluster matrices does not fit in shared memory; use ptca_sweep")
+                                      .c_str());
 
     cudaStream_t stm = static_cast<cudaStream_t>(stream);
     double* S_alt = reinterpret_cast<double*>(base + kOffSalt);
+    int32_t* sites = reinterpret_cast<int32_t*>(base + kOffSites);
     int32_t* ticket = reinterpret_cast<int32_t*>(base + kOffTicket);
+    unsigned int* flag_count = reinterpret_cast<unsigned int*>(base + kOffFlagCount);
     unsigned long long* counters = reinterpret_cast<unsigned long long*>(base + kOffCounters);
     int32_t* err = reinterpret_cast<int32_t*>(base + kOffErr);
-    // Clear what must start at zero, and start both spin buffers equal.
-    e = cudaMemsetAsync(ticket, 0, sizeof(int32_t) * N, stm);
+    // The schedule the host built and checked (pageable source: the copy is
+    // staged before the call returns), cleared counters, and both spin
+    // buffers equal.
+    e = cudaMemcpyAsync(sites, sched.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, stm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(int32_t) * N, stm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag_count, 0, sizeof(unsigned int), stm);
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), stm);
-    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), stm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), stm);
     if (e == cudaSuccess) e = cudaMemcpyAsync(S_alt, spins, 3 * sizeof(double) * N, cudaMemcpyDeviceToDevice, stm);
     if (e != cudaSuccess) return ptca_internal_fail(PTCA_ERR_CUDA, cudaGetErrorString(e));
 
@@ -165,6 +180,9 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
     a.rec_n = reinterpret_cast<int32_t*>(base + kOffRecN);
     a.counters = counters;
     a.err = err;
+    a.margin = prec == 1 ? kNoAllocMargin : 0.0;
+    a.flag_list = reinterpret_cast<int32_t*>(base + kOffFlags);
+    a.flag_count = flag_count;
     for (int s = 0; s < n_stages; ++s) {
         a.S_in = buf[s & 1];
         a.S_out = buf[(s + 1) & 1];
@@ -174,6 +192,12 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
         a.prev_sites = s > 0 ? sites + stage_start[s - 1] : nullptr;
         a.prev_count = s > 0 ? stage_start[s] - stage_start[s - 1] : 0;
         e = ptca::launch_stage(prec, 8, a, stm);
+        if (e == cudaSuccess && prec == 1) {
+            // Deferred decisions of this stage: re-solved before the next
+            // stage reads the spins, then the list is emptied.
+            e = ptca::launch_resolve(a, sms, stm);
+            if (e == cudaSuccess) e = cudaMemsetAsync(flag_count, 0, sizeof(unsigned int), stm);
+        }
         if (e != cudaSuccess) return ptca_internal_fail(PTCA_ERR_CUDA, cudaGetErrorString(e));
     }
     if (n_stages > 0) {
@@ -192,6 +216,10 @@ extern "C" ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptc
     }
     if (accepted_out) {
         e = cudaMemcpyAsync(accepted_out, a.rec_acc, N, cudaMemcpyDeviceToDevice, stm);
+        if (e != cudaSuccess) return ptca_internal_fail(PTCA_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (status_out) {
+        e = ptca::launch_status_word(err, status_out, stm);
         if (e != cudaSuccess) return ptca_internal_fail(PTCA_ERR_CUDA, cudaGetErrorString(e));
     }
     return PTCA_OK;

@@ -114,7 +114,7 @@ def lib():
             "ptca_full_spectrum": ([vp, vp, vp], i32),
             "ptca_last_error": ([], ctypes.c_char_p),
             "ptca_version": ([], i32),
-            "ptca_sweep_noalloc": ([P(Lattice), P(Params), vp, vp, i32, vp, i64, vp, vp, vp], i32),
+            "ptca_sweep_noalloc": ([P(Lattice), P(Params), vp, i64, vp, vp, vp, vp], i32),
             "ptca_set_pipeline": ([vp, i32, dbl], i32),
             "ptca_set_resolve_margin": ([vp, dbl], i32),
             "ptca_set_checker": ([vp, i32], i32),
@@ -311,17 +311,33 @@ def ptca_sweep_record(h, site=None, F_old=None, F_new=None, lnu=None, accepted=N
                                    _stream(stream)))
 
 
-def ptca_sweep_noalloc(cfg: Config, sites, stage_start, spins, sweep_index: int, F_out=None, accepted_out=None,
+def ptca_sweep_noalloc(cfg: Config, spins, sweep_index: int, F_out=None, accepted_out=None, status_out=None,
                        stream=None) -> None:
     """One sweep without a context or device allocation (see include/ptca.h).
 
-    sites: device int32 tensor (flattened schedule); stage_start: host int32
-    numpy array; spins: device float64 tensor (N, 3), updated in place."""
-    import numpy as np
-    ss = np.ascontiguousarray(stage_start, dtype=np.int32)
+    spins: CUDA float64 tensor (N, 3), updated in place; F_out: CUDA float64
+    (2N,) or None; accepted_out: CUDA uint8 (N,) or None, in the flattened
+    order of ptca_schedule(cfg); status_out: CUDA int32 (1,) or None."""
+    import torch
+    N = cfg.N
+
+    def need(t, name, dtype, numel):
+        if t is None:
+            return
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor of {numel} elements")
+
+    if spins is None:
+        raise ValueError("spins is required")
+    need(spins, "spins", torch.float64, 3 * N)
+    need(F_out, "F_out", torch.float64, 2 * N)
+    need(accepted_out, "accepted_out", torch.uint8, N)
+    need(status_out, "status_out", torch.int32, 1)
     lat, par = cfg.lattice(), cfg.params()
-    _check(lib().ptca_sweep_noalloc(ctypes.byref(lat), ctypes.byref(par), _ptr(sites), _ptr(ss), ss.size - 1,
-                                    _ptr(spins), sweep_index, _ptr(F_out), _ptr(accepted_out), _stream(stream)))
+    _check(lib().ptca_sweep_noalloc(ctypes.byref(lat), ctypes.byref(par), _ptr(spins), sweep_index, _ptr(F_out),
+                                    _ptr(accepted_out), _ptr(status_out), _stream(stream)))
 
 
 def ptca_set_pipeline(h, mode: int, barrier_timeout_s: float = 30.0) -> None:
@@ -387,9 +403,10 @@ def ptca_set_checker(h, on: bool) -> None:
 
 def ptca_checker_read(h, n_stages: int, stream=None):
     """Per-stage precision-checker maxima since the last read: numpy array
-    (n_stages, 4) = |d eps|, |d dF|, |d eps|/(J_H+4|t|), |d dF|/max(1,|F|)."""
+    (n_stages, 5) = |d eps|, |d dF|, |d eps|/(J_H+4|t|), |d dF|/max(1,|F|),
+    |d dF| / max(|dF|, sum_k |eps_k-mu| f_k / n)."""
     import numpy as np
-    out = np.zeros((n_stages, 4), dtype=np.float64)
+    out = np.zeros((n_stages, 5), dtype=np.float64)
     _check(lib().ptca_checker_read(h, _ptr(out), n_stages, _stream(stream)))
     return out
 

@@ -239,36 +239,40 @@ def test_noalloc_validates_on_the_host_before_touching_the_device(built):
     # Every check of ptca_sweep_noalloc runs on the host before its first CUDA
     # call: without a GPU a valid call stops at the device lookup (status 2),
     # every invalid one earlier (status 1).  The device pointers are dummies
-    # that nothing dereferences on the host.
+    # that nothing dereferences on the host.  The binding's own checks want
+    # CUDA tensors, so the C entry point is called directly.
+    import ctypes
+
     import torch
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
-    cfg = P.Config(Lx=8, Ly=8, L_c=4)
-    ss = np.concatenate([[0], np.cumsum([len(s) for s in P.ptca_schedule(cfg)])]).astype(np.int32)
-    dummy = 0x1000
+    dummy = ctypes.c_void_p(0x1000)
 
-    def status(**kw):
-        args = dict(cfg=cfg, sites=dummy, stage_start=ss, spins=dummy, sweep_index=0, stream=0)
-        args.update(kw)
-        with pytest.raises(P.PtcaError) as e:
-            P.ptca_sweep_noalloc(**args)
-        return e.value.status, str(e.value)
+    def status(cfg=P.Config(Lx=8, Ly=8, L_c=4), spins=dummy, sweep_index=0):
+        lat, par = cfg.lattice(), cfg.params()
+        st = P.lib().ptca_sweep_noalloc(ctypes.byref(lat), ctypes.byref(par), spins, sweep_index, dummy, dummy,
+                                        dummy, None)
+        return st, P.lib().ptca_last_error().decode()
 
     st, msg = status()
     assert st == 2 and "device" in msg
     assert status(sweep_index=-1)[0] == 1
-    assert status(sites=None)[0] == 1
     assert status(spins=None)[0] == 1
     st, msg = status(cfg=P.Config(Lx=200, Ly=200, L_c=4))
     assert st == 1 and "at most 16384" in msg
-    shifted = ss.copy()
-    shifted[1] += 1
-    st, msg = status(stage_start=shifted)
-    assert st == 1 and "stage_start" in msg
-    st, msg = status(stage_start=ss[:-1])
-    assert st == 1 and "n_stages" in msg
     assert status(cfg=P.Config(Lx=8, Ly=8, L_c=9))[0] == 1
     assert status(cfg=P.Config(Lx=8, Ly=8, L_c=4, model=P.MODEL_HOLSTEIN, m_step=0.0))[0] == 1
+
+
+def test_noalloc_binding_checks_its_tensors(built):
+    # The binding refuses anything but contiguous CUDA tensors of the right
+    # dtype and size before it reaches the library.
+    import torch
+    cfg = P.Config(Lx=8, Ly=8, L_c=4)
+    with pytest.raises(ValueError, match="CUDA"):
+        P.ptca_sweep_noalloc(cfg, torch.zeros((cfg.N, 3), dtype=torch.float64), 0)
+    with pytest.raises(ValueError):
+        P.ptca_sweep_noalloc(cfg, None, 0)
 
 
 def test_smoke_refuses_to_run_without_a_gpu(built):
