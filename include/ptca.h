@@ -366,6 +366,40 @@ ptca_status ptca_sweep_record(ptca_ctx* ctx, int32_t* site, double* F_old, doubl
 ptca_status ptca_observables(ptca_ctx* ctx, ptca_obs* out, void* stream);
 
 /* ----------------------------------------------------------------------- */
+/* Partial stages: a lattice split over several GPUs                         */
+/* ----------------------------------------------------------------------- */
+
+/* The paper distributes the independent clusters of a block over processes
+ * and, once the block is done, gathers the accepted updates and broadcasts the
+ * new configuration before the next block (Sec. III.b, Fig. 4).  With the
+ * lattice split into strips, one per GPU, each GPU runs the visits of a stage
+ * that lie in its strip (ptca_stage_run) and then receives, from its
+ * neighbours, the spins of that stage's visits that lie in the windows of its
+ * own visits (ptca_get_sites on the sender, ptca_set_sites on the receiver);
+ * the partition and the exchange live in the Python package (strips.py).
+ *
+ * ptca_stage_run: Sec. II.c steps a-f for the given visits of ONE stage of
+ * this context's schedule, all reading the configuration at the call's start
+ * and writing their decisions together, as a stage of ptca_sweep does, with
+ * the random stream of sweep `sweep_index` (the PTCA_MIXED re-solve guard
+ * included).  sites: HOST int32[count], update sites of a single stage,
+ * without repeats (checked: PTCA_ERR_INVALID otherwise); any subset of the
+ * stage, in any order.  The sweep record (ptca_sweep_record) then holds these
+ * visits, entries 0 .. count-1 in the order given.  The context's sweep
+ * counter is not advanced.  PTCA_ERR_UNSUPPORTED while surrogate screening is
+ * on.  Stream-ordered (the site list is staged before the call returns). */
+ptca_status ptca_stage_run(ptca_ctx* ctx, int64_t sweep_index, const int32_t* sites, int32_t count, void* stream);
+
+/* Spins of `count` sites (HOST int32 list, indices in [0, N), no repeats) out
+ * of / into the context: out/spins hold 3 doubles per listed site, in list
+ * order, on the device if on_device != 0 (stream-ordered) else on the host
+ * (ptca_get_sites then synchronises `stream`). */
+ptca_status ptca_get_sites(ptca_ctx* ctx, const int32_t* sites, int32_t count, double* out, int32_t on_device,
+                           void* stream);
+ptca_status ptca_set_sites(ptca_ctx* ctx, const int32_t* sites, int32_t count, const double* spins, int32_t on_device,
+                           void* stream);
+
+/* ----------------------------------------------------------------------- */
 /* Surrogate network and delayed acceptance                                  */
 /* ----------------------------------------------------------------------- */
 /* A multilayer perceptron h: 150 -> 256 -> 256 -> 256 -> 1 (SiLU), reading the

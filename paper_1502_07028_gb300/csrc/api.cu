@@ -298,7 +298,7 @@ static void free_ctx(ptca_ctx* c) {
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
                     c->d_rec_n, c->d_counters, c->d_err, c->d_obs, c->d_stage_start, c->d_perm, c->d_queue,
                     c->d_bar, c->d_sweep_ctr, c->d_flag_list, c->d_flag_count, c->d_gA,
-                    c->d_chk_eig, c->d_chk_F, c->d_chk_out};
+                    c->d_chk_eig, c->d_chk_F, c->d_chk_out, c->d_sub, c->d_sub_spins};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete c;
@@ -1137,6 +1137,100 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
         }
         if (err[0]) return fail(PTCA_ERR_NUMERIC, "non-finite free-energy difference in a sweep");
     }
+    return PTCA_OK;
+}
+
+// Host-side check of a caller's site list: count sites, each in [0, N), no
+// repeats; with want_stage >= 0 all of stage want_stage (ctx->h_stage_of).
+// Copies the list to ctx->d_sub on `st` (pageable source: staged before
+// cudaMemcpyAsync returns).
+static ptca_status upload_sites(ptca_ctx* ctx, const int32_t* sites, int32_t count, int* stage_out,
+                                cudaStream_t st, const char* who) {
+    if (count < 0 || count > ctx->N) return fail(PTCA_ERR_INVALID, std::string(who) + ": count out of range");
+    if (count > 0 && !sites) return fail(PTCA_ERR_INVALID, std::string(who) + ": null site list");
+    if (ctx->h_stage_of.empty()) {
+        ctx->h_stage_of.assign(ctx->N, -1);
+        for (int q = 0; q < ctx->nstages; ++q)
+            for (int k = ctx->h_start[q]; k < ctx->h_start[q + 1]; ++k) ctx->h_stage_of[ctx->h_sites[k]] = q;
+    }
+    std::vector<char> seen(ctx->N, 0);
+    int stage = -1;
+    for (int k = 0; k < count; ++k) {
+        const int32_t s = sites[k];
+        if (s < 0 || s >= ctx->N) return fail(PTCA_ERR_INVALID, std::string(who) + ": site index out of range");
+        if (seen[s]) return fail(PTCA_ERR_INVALID, std::string(who) + ": repeated site");
+        seen[s] = 1;
+        if (k == 0) stage = ctx->h_stage_of[s];
+        else if (stage_out && ctx->h_stage_of[s] != stage)
+            return fail(PTCA_ERR_INVALID, std::string(who) + ": the sites belong to different stages");
+    }
+    if (stage_out) *stage_out = stage;
+    if (!ctx->d_sub) PTCA_CUDA(dalloc(&ctx->d_sub, (size_t)ctx->N));
+    if (!ctx->d_sub_spins) PTCA_CUDA(dalloc(&ctx->d_sub_spins, 3 * (size_t)ctx->N));
+    if (count > 0)
+        PTCA_CUDA(cudaMemcpyAsync(ctx->d_sub, sites, sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, st));
+    return PTCA_OK;
+}
+
+ptca_status ptca_stage_run(ptca_ctx* ctx, int64_t sweep_index, const int32_t* sites, int32_t count, void* stream) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    if (sweep_index < 0) return fail(PTCA_ERR_INVALID, "ptca_stage_run: sweep_index < 0");
+    if (ctx->sg.enabled) return fail(PTCA_ERR_UNSUPPORTED, "ptca_stage_run: surrogate screening runs in ptca_sweep only");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int stage = -1;
+    ptca_status r = upload_sites(ctx, sites, count, &stage, st, "ptca_stage_run");
+    if (r != PTCA_OK) return r;
+    if (count == 0) return PTCA_OK;
+    // Buffers 0 and 1 hold the same configuration between calls: the visits
+    // read buffer 0 and write their decisions into buffer 1 (the stage-start
+    // snapshot of Sec. III.a), then buffer 0 takes the visited sites back.
+    StageArgs a = base_args(ctx);
+    a.sweep = (uint64_t)sweep_index;
+    a.S_in = ctx->d_S[0];
+    a.S_out = ctx->d_S[1];
+    a.sites = ctx->d_sub;
+    a.count = count;
+    a.rec_base = 0;
+    PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
+    cudaError_t e = launch_stage_ctx(ctx, a, st);
+    if (e == cudaSuccess && a.margin > 0.0) {
+        e = launch_resolve_ctx(ctx, a, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.flag_count, 0, sizeof(unsigned int), st);
+    }
+    if (e == cudaSuccess) e = ptca::launch_copy_sites(ctx->d_S[1], ctx->d_S[0], ctx->d_sub, count, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ptca_stage_run");
+    drop_graph(ctx);
+    return PTCA_OK;
+}
+
+ptca_status ptca_get_sites(ptca_ctx* ctx, const int32_t* sites, int32_t count, double* out, int32_t on_device,
+                           void* stream) {
+    if (!ctx || (count > 0 && !out)) return fail(PTCA_ERR_INVALID, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ptca_status r = upload_sites(ctx, sites, count, nullptr, st, "ptca_get_sites");
+    if (r != PTCA_OK || count == 0) return r;
+    double* dst = on_device ? out : ctx->d_sub_spins;
+    PTCA_CUDA(ptca::launch_gather_sites(ctx->d_S[0], ctx->d_sub, count, dst, st));
+    if (!on_device) {
+        PTCA_CUDA(cudaMemcpyAsync(out, dst, 3 * sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, st));
+        PTCA_CUDA(cudaStreamSynchronize(st));
+    }
+    return PTCA_OK;
+}
+
+ptca_status ptca_set_sites(ptca_ctx* ctx, const int32_t* sites, int32_t count, const double* spins, int32_t on_device,
+                           void* stream) {
+    if (!ctx || (count > 0 && !spins)) return fail(PTCA_ERR_INVALID, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ptca_status r = upload_sites(ctx, sites, count, nullptr, st, "ptca_set_sites");
+    if (r != PTCA_OK || count == 0) return r;
+    const double* src = spins;
+    if (!on_device) {
+        PTCA_CUDA(cudaMemcpyAsync(ctx->d_sub_spins, spins, 3 * sizeof(double) * (size_t)count, cudaMemcpyHostToDevice,
+                                  st));
+        src = ctx->d_sub_spins;
+    }
+    PTCA_CUDA(ptca::launch_scatter_sites(ctx->d_sub, count, src, ctx->d_S[0], ctx->d_S[1], st));
     return PTCA_OK;
 }
 

@@ -127,6 +127,12 @@ struct ptca_ctx {
     std::vector<cudaEvent_t> tev;
     std::vector<int> tkind;
     std::vector<int64_t> titems;
+    // partial stages (ptca_stage_run) and site gathers/scatters
+    // (ptca_get_sites / ptca_set_sites): the stage of every site, and device
+    // copies of the caller's site list and of the spins moved (made on first use)
+    std::vector<int32_t> h_stage_of;
+    int32_t* d_sub = nullptr;         // [N]
+    double* d_sub_spins = nullptr;    // [3 N]
     // surrogate network for delayed-acceptance screening
     ptca::SurrogateState sg;
 };

@@ -241,6 +241,41 @@ cudaError_t launch_copy_sites(const double* src, double* dst, const int32_t* sit
     return cudaGetLastError();
 }
 
+// out[k] = S[sites[k]] (three components), k < count.
+__global__ void k_gather_sites(const double* __restrict__ S, const int32_t* __restrict__ sites, int count,
+                               double* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int s = sites[k];
+    out[3 * k] = S[3 * s]; out[3 * k + 1] = S[3 * s + 1]; out[3 * k + 2] = S[3 * s + 2];
+}
+
+cudaError_t launch_gather_sites(const double* S, const int32_t* sites, int count, double* out, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_gather_sites<<<(count + 255) / 256, 256, 0, st>>>(S, sites, count, out);
+    return cudaGetLastError();
+}
+
+// S0[sites[k]] = S1[sites[k]] = in[k], k < count.
+__global__ void k_scatter_sites(const int32_t* __restrict__ sites, int count, const double* __restrict__ in,
+                                double* __restrict__ S0, double* __restrict__ S1) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int s = sites[k];
+    for (int a = 0; a < 3; ++a) {
+        const double v = in[3 * k + a];
+        S0[3 * s + a] = v;
+        S1[3 * s + a] = v;
+    }
+}
+
+cudaError_t launch_scatter_sites(const int32_t* sites, int count, const double* in, double* S0, double* S1,
+                                 cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_scatter_sites<<<(count + 255) / 256, 256, 0, st>>>(sites, count, in, S0, S1);
+    return cudaGetLastError();
+}
+
 // F_i = -T sum_k softplus(-(eig_k - mu)/T), one warp per list.
 __global__ void k_free_energy(const double* __restrict__ eig, const int64_t* __restrict__ eoff,
                               const int32_t* __restrict__ n, int m, double mu, double temp, double* __restrict__ F) {

@@ -25,6 +25,10 @@ cudaError_t launch_init_spins(const Model& m, double* S, int N, cudaStream_t st)
 // (Holstein).
 void set_model_terms(Model& m, int model, double J_H, double U, double lam, double K, double mu, double m_step);
 cudaError_t launch_copy_sites(const double* src, double* dst, const int32_t* sites, int count, cudaStream_t st);
+// out[k] = S[sites[k]]; and S0[sites[k]] = S1[sites[k]] = in[k] (3 doubles each).
+cudaError_t launch_gather_sites(const double* S, const int32_t* sites, int count, double* out, cudaStream_t st);
+cudaError_t launch_scatter_sites(const int32_t* sites, int count, const double* in, double* S0, double* S1,
+                                 cudaStream_t st);
 cudaError_t launch_build(int prec, const Model& m, const double* S, const int32_t* sites, int count,
                          const double* new_spins, void* H, int64_t stride, int64_t* offsets, int32_t* nout,
                          cudaStream_t st);

@@ -34,7 +34,7 @@ EXPORTED = [
     "ptca_surrogate_collect", "ptca_surrogate_train", "ptca_surrogate_grad", "ptca_surrogate_predict",
     "ptca_surrogate_enable", "ptca_set_checker", "ptca_checker_read", "ptca_set_launch_config",
     "ptca_get_launch_config", "ptca_autotune", "ptca_set_kernel_timing", "ptca_kernel_times",
-    "ptca_stage_split", "ptca_full_spectrum",
+    "ptca_stage_split", "ptca_full_spectrum", "ptca_stage_run", "ptca_get_sites", "ptca_set_sites",
 ]
 
 
@@ -135,6 +135,9 @@ def lib():
             "ptca_surrogate_predict": ([vp, vp, vp, i32, vp, vp], i32),
             "ptca_surrogate_enable": ([vp, i32], i32),
             "ptca_selftest_barrier_timeout": ([i32, dbl, vp], i32),
+            "ptca_stage_run": ([vp, i64, vp, i32, vp], i32),
+            "ptca_get_sites": ([vp, vp, i32, vp, i32, vp], i32),
+            "ptca_set_sites": ([vp, vp, i32, vp, i32, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -338,6 +341,28 @@ def ptca_sweep_noalloc(cfg: Config, spins, sweep_index: int, F_out=None, accepte
     lat, par = cfg.lattice(), cfg.params()
     _check(lib().ptca_sweep_noalloc(ctypes.byref(lat), ctypes.byref(par), _ptr(spins), sweep_index, _ptr(F_out),
                                     _ptr(accepted_out), _ptr(status_out), _stream(stream)))
+
+
+def ptca_stage_run(h, sweep_index: int, sites, stream=None) -> None:
+    """The given visits (host int32 site list, one stage) of sweep `sweep_index`."""
+    import numpy as np
+    s = np.ascontiguousarray(sites, dtype=np.int32)
+    _check(lib().ptca_stage_run(h, sweep_index, _ptr(s), s.size, _stream(stream)))
+
+
+def ptca_get_sites(h, sites, out, stream=None) -> None:
+    """Spins of the listed sites (host int32 list) into `out` (float64, 3 per
+    site; a CUDA tensor stays stream-ordered, a host array synchronises)."""
+    import numpy as np
+    s = np.ascontiguousarray(sites, dtype=np.int32)
+    _check(lib().ptca_get_sites(h, _ptr(s), s.size, _ptr(out), int(getattr(out, 'is_cuda', False)), _stream(stream)))
+
+
+def ptca_set_sites(h, sites, spins, stream=None) -> None:
+    """Write the spins (float64, 3 per listed site) of the listed sites."""
+    import numpy as np
+    s = np.ascontiguousarray(sites, dtype=np.int32)
+    _check(lib().ptca_set_sites(h, _ptr(s), s.size, _ptr(spins), int(getattr(spins, 'is_cuda', False)), _stream(stream)))
 
 
 def ptca_set_pipeline(h, mode: int, barrier_timeout_s: float = 30.0) -> None:
