@@ -496,14 +496,16 @@ ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptca_params* p
  * lattice in the current configuration (the context's model: hopping and
  * on-site terms; the classical energy is not part of it).  The paper
  * diagonalises saved configurations of the whole system with ScaLAPACK
- * (Sec. VI); here the dense 2N x 2N matrix is built on the device by this
- * library and diagonalised by the CUDA toolkit's dense Hermitian eigensolver
- * in FP64 -- the one library eigensolver of the build, off the sweep's path.
+ * (Sec. VI); here the dense 2N x 2N matrix is built on the device, reduced to
+ * real tridiagonal form by this library's Householder reduction spread over
+ * the whole GPU (FP64, one pass over the trailing triangle per reflector),
+ * and its eigenvalues found one thread each (FP32 bisection finished by
+ * double-float Sturm counts and Newton).  No library eigensolver is used.
  *   eig_out  device double[2N]
- * N <= 16384 sites (PTCA_ERR_INVALID otherwise).  Allocates about 16 (2N)^2
- * bytes of device memory for the call (PTCA_ERR_OOM when it does not fit);
- * PTCA_ERR_NUMERIC if the eigensolver does not converge.  Synchronises
- * `stream`. */
+ * N <= 16384 sites (PTCA_ERR_INVALID otherwise).  Allocates about
+ * 8 (2N)^2 bytes of device memory for the call (the packed triangle; plus
+ * 32 (2N)^2 / 64 bytes of partial sums), PTCA_ERR_OOM when it does not fit.
+ * Synchronises `stream`. */
 ptca_status ptca_full_spectrum(ptca_ctx* ctx, double* eig_out, void* stream);
 
 /* ----------------------------------------------------------------------- */

@@ -76,7 +76,7 @@ def _compile(verbose: bool) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcusolver"], check=True)
+    subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

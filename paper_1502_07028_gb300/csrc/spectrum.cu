@@ -1,11 +1,25 @@
-// spectrum.cu -- full-system spectrum of a configuration (Sec. VI): the
-// one-body Hamiltonian of the whole lattice, built densely on the device by
-// this library's kernel, and its eigenvalues from the CUDA toolkit's dense
-// Hermitian eigensolver (FP64), where the paper uses ScaLAPACK on saved
-// configurations.  Off the sweep's hot path.
-#include <cusolverDn.h>
-
+// spectrum.cu -- full-system spectrum of a configuration (Sec. VI): all 2N
+// eigenvalues of the whole lattice's one-body Hamiltonian, where the paper
+// diagonalises saved configurations with ScaLAPACK.  Everything runs in this
+// library's kernels, in FP64, off the sweep's hot path:
+//   1. the dense matrix is built as its packed lower triangle (row-major:
+//      element (i, j <= i) at i(i+1)/2 + j) in global memory;
+//   2. a Householder reduction to real tridiagonal form spread over the whole
+//      GPU: per reflector, one tiled pass applies the previous reflector's
+//      deferred rank-2 update to the trailing block and accumulates the
+//      Hermitian matrix-vector product with the current reflector (row and
+//      column partial sums per 64 x 64 tile, in a fixed order), a reduction
+//      combines the partials, and one CTA forms w, the explicit update of the
+//      next pivot column and the next reflector -- the algorithm of the
+//      cluster kernels (cluster_solve.cuh), with the matrix too large for one
+//      SM;
+//   3. one thread per eigenvalue: FP32 bisection on the FP32-rounded
+//      tridiagonal, then the cluster solver's double-float Sturm counts and
+//      safeguarded Newton on the exact (FP64) tridiagonal.
+#include <cfloat>
+#include <cmath>
 #include <string>
+#include <vector>
 
 #include "../../include/ptca.h"
 #include "context.h"
@@ -14,22 +28,28 @@
 
 namespace ptca {
 
+__host__ __device__ __forceinline__ int64_t tri64(int64_t r) { return r * (r + 1) / 2; }
+
+constexpr int FS_TB = 64;          // tile edge of the reduction pass
+constexpr int FS_PASS_THREADS = 256;
+constexpr int FS_RED_THREADS = 256;
+constexpr int FS_SCALAR_THREADS = 1024;
+constexpr int FS_EIG_THREADS = 128;
+
 // One thread per lattice site: its on-site 2x2 block and its bonds to the
-// +x, +y, +z neighbours (both triangles), hopping added atomically so that an
-// axis of extent 2 on a torus gets both of its bonds (-2t).  H is dense,
-// column-major, n = 2N, zeroed by the caller.
+// +x, +y, +z neighbours, hopping added atomically so that an axis of extent 2
+// on a torus gets both of its bonds (-2t).  H: packed lower triangle of order
+// 2N, zeroed by the caller.
 __global__ void k_full_hamiltonian(Model m, const double* __restrict__ S, int N, double2* __restrict__ H) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int64_t n = 2 * (int64_t)N;
     const int x = i % m.Lx, y = (i / m.Lx) % m.Ly, z = i / (m.Lx * m.Ly);
     const double sx = S[3 * i], sy = S[3 * i + 1], sz = S[3 * i + 2];
     const double dg = m.e0 + m.lam * sx, J = m.JH;
     const int64_t a = 2 * (int64_t)i, b = a + 1;
-    H[a * n + a] = make_double2(dg - J * sz, 0.0);
-    H[b * n + b] = make_double2(dg + J * sz, 0.0);
-    H[a * n + b] = make_double2(-J * sx, -J * sy);  // column a, row b: -J (S_x + i S_y)
-    H[b * n + a] = make_double2(-J * sx, J * sy);   // column b, row a: its conjugate
+    H[tri64(a) + a] = make_double2(dg - J * sz, 0.0);
+    H[tri64(b) + b] = make_double2(dg + J * sz, 0.0);
+    H[tri64(b) + a] = make_double2(-J * sx, -J * sy);  // element (b, a) = -J (S_x + i S_y)
     const int L[3] = {m.Lx, m.Ly, m.Lz};
     const int c[3] = {x, y, z};
     for (int d = 0; d < 3; ++d) {
@@ -43,10 +63,261 @@ __global__ void k_full_hamiltonian(Model m, const double* __restrict__ S, int N,
         const int j = (cc[2] * m.Ly + cc[1]) * m.Lx + cc[0];
         for (int sg = 0; sg < 2; ++sg) {
             const int64_t p = 2 * (int64_t)i + sg, q = 2 * (int64_t)j + sg;
-            atomicAdd(&H[p * n + q].x, -m.t);
-            atomicAdd(&H[q * n + p].x, -m.t);
+            const int64_t hi = p > q ? p : q, lo = p > q ? q : p;
+            atomicAdd(&H[tri64(hi) + lo].x, -m.t);
         }
     }
+}
+
+// Buffers of the reduction.  Reflector k acts on rows/columns k+1 .. n-1;
+// its first entry is stored at index k+1 like the others.
+struct FsArgs {
+    int n;
+    double2* A;
+    const double2* U;   // v_{k-1} (zero at k = 0)
+    const double2* V;   // v_k
+    double2* Vn;        // v_{k+1}, written by the scalar phase of step k
+    const double2* W;   // w_{k-1} (zero at k = 0)
+    double2* Wn;        // w_k, written by the scalar phase of step k
+    double2* pr;        // [T][n] row partial sums of A v_k, by tile column
+    double2* pc;        // [T][n] column partial sums, by tile row
+    double2* p;         // [n]    tau A v_k
+    double* red;        // [blocks of the reduction] partial sums of Re(v^H p)
+    double* tau;        // [2]    tau_k in tau[k & 1]
+    double* d;          // [n]
+    double* e2;         // [n]
+};
+
+// Step k's pass over the trailing block (rows and columns j0 = k+1 .. n-1),
+// one 64 x 64 tile of its lower triangle per CTA: A <- A - u w^H - w u^H
+// with step k-1's (u, w), then the tile's row sums of A v (into pr[tile
+// column][row]) and, below the diagonal, column sums of A^H v (into
+// pc[tile row][column]).  Warp q takes rows q, q+8, ...; lanes take columns
+// lane and lane + 32 of the tile.
+__global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs a, int k) {
+    __shared__ double2 csum[FS_PASS_THREADS / 32][FS_TB];
+    const int n = a.n, j0 = k + 1, m = n - j0;
+    const int64_t b = blockIdx.x;
+    int TR = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while (tri64(TR + 1) <= b) ++TR;
+    while (tri64(TR) > b) --TR;
+    const int TC = (int)(b - tri64(TR));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double2 zero = make_double2(0.0, 0.0);
+    int cr[2];
+    double2 vc[2], uc[2], wc[2], cacc[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        cr[q] = FS_TB * TC + lane + 32 * q;
+        const bool in = cr[q] < m;
+        const int j = j0 + cr[q];
+        vc[q] = in ? a.V[j] : zero;
+        uc[q] = in ? a.U[j] : zero;
+        wc[q] = in ? a.W[j] : zero;
+        cacc[q] = zero;
+    }
+    for (int rr = warp; rr < FS_TB; rr += FS_PASS_THREADS / 32) {
+        const int ri = FS_TB * TR + rr;
+        if (ri >= m) break;
+        const int i = j0 + ri;
+        const double2 ui = a.U[i], wi = a.W[i], vi = a.V[i];
+        double2* row = a.A + tri64(i) + j0;
+        double2 racc = zero;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c = cr[q];
+            if (c <= ri) {
+                double2 x = row[c];
+                x = cfms_conj_b(ui, wc[q], x);
+                x = cfms_conj_b(wi, uc[q], x);
+                if (c == ri) x.y = 0.0;  // the diagonal stays real
+                row[c] = x;
+                racc = cfma(x, vc[q], racc);
+                if (c < ri) cacc[q] = cfma_conj_a(x, vi, cacc[q]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) racc = cadd(racc, cshfl_xor(racc, o));
+        if (lane == 0) a.pr[(int64_t)TC * n + ri] = racc;
+    }
+    csum[warp][lane] = cacc[0];
+    csum[warp][lane + 32] = cacc[1];
+    __syncthreads();
+    if (threadIdx.x < FS_TB) {
+        double2 s = csum[0][threadIdx.x];
+#pragma unroll
+        for (int w = 1; w < FS_PASS_THREADS / 32; ++w) s = cadd(s, csum[w][threadIdx.x]);
+        const int c = FS_TB * TC + threadIdx.x;
+        if (c < m) a.pc[(int64_t)TR * n + c] = s;
+    }
+}
+
+// p = tau (A v): for row ri of band B (its tile row), the row partials of
+// tiles (B, 0 .. B) plus the column partials of tiles (B .. T-1, B) (the
+// diagonal tile's column sums hold the elements below the diagonal), in a
+// fixed order; and each CTA's partial sum of Re(v^H p).
+__global__ void __launch_bounds__(FS_RED_THREADS) k_fs_reduce(FsArgs a, int k) {
+    __shared__ double red[FS_RED_THREADS / 32];
+    const int n = a.n, j0 = k + 1, m = n - j0, T = (m + FS_TB - 1) / FS_TB;
+    const int ri = blockIdx.x * blockDim.x + threadIdx.x;
+    double sp = 0.0;
+    if (ri < m) {
+        const int band = ri / FS_TB;
+        double2 s = make_double2(0.0, 0.0);
+        for (int tc = 0; tc <= band; ++tc) s = cadd(s, a.pr[(int64_t)tc * n + ri]);
+        for (int tr = band; tr < T; ++tr) s = cadd(s, a.pc[(int64_t)tr * n + ri]);
+        const double tau = a.tau[k & 1];
+        s.x *= tau;
+        s.y *= tau;
+        a.p[j0 + ri] = s;
+        const double2 v = a.V[j0 + ri];
+        sp = v.x * s.x + v.y * s.y;
+    }
+    sp = block_sum<double>(sp, red);
+    if (threadIdx.x == 0) a.red[blockIdx.x] = sp;
+}
+
+// Next reflector from the updated pivot column j (entries j+1 .. n-1 in the
+// thread-strided loop of the caller): given ||x||^2 and x_0, its first entry
+// x_0 + phase(x_0) ||x|| and tau = 1 / (||x|| (||x|| + |x_0|)).
+__device__ __forceinline__ void fs_reflector_head(double s2, double2 x0, double2& first, double& tau) {
+    const double sigma = sqrt(s2), ax0 = sqrt(x0.x * x0.x + x0.y * x0.y);
+    const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+    first = make_double2(x0.x + ph.x * sigma, x0.y + ph.y * sigma);
+    tau = sigma > 0.0 ? 1.0 / (sigma * (sigma + ax0)) : 0.0;
+}
+
+// Column 0: d_0, ||x||^2 and the first reflector (one CTA).
+__global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_setup(FsArgs a) {
+    __shared__ double red[FS_SCALAR_THREADS / 32];
+    __shared__ double2 s_x0;
+    const int n = a.n;
+    double s2 = 0.0;
+    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const double2 x = a.A[tri64(i)];
+        s2 += x.x * x.x + x.y * x.y;
+        if (i >= 2) a.Vn[i] = x;
+        if (i == 1) s_x0 = x;
+    }
+    s2 = block_sum<double>(s2, red);
+    if (threadIdx.x == 0) {
+        a.d[0] = a.A[0].x;
+        a.e2[0] = s2;
+        double2 f;
+        double tau;
+        fs_reflector_head(s2, s_x0, f, tau);
+        a.Vn[1] = f;
+        a.tau[0] = tau;
+    }
+}
+
+// Step k's scalar phase (one CTA): w = p - (tau/2)(v^H p) v; the explicit
+// update of pivot column j0 = k+1 with (v_k, w_k); d_j0, e2_j0 and, unless
+// this was the last reflector, the next reflector v_{k+1} and tau_{k+1}.
+__global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_scalar(FsArgs a, int k, int nred) {
+    __shared__ double red[FS_SCALAR_THREADS / 32];
+    __shared__ double s_K;
+    __shared__ double2 s_x0;
+    const int n = a.n, j0 = k + 1;
+    double sp = 0.0;
+    for (int b = threadIdx.x; b < nred; b += blockDim.x) sp += a.red[b];
+    sp = block_sum<double>(sp, red);
+    if (threadIdx.x == 0) s_K = 0.5 * a.tau[k & 1] * sp;
+    __syncthreads();
+    const double K = s_K;
+    const double2 vf = a.V[j0];
+    const double2 p0 = a.p[j0];
+    const double2 w0 = make_double2(p0.x - K * vf.x, p0.y - K * vf.y);
+    double s2 = 0.0;
+    for (int i = j0 + threadIdx.x; i < n; i += blockDim.x) {
+        const double2 v = a.V[i], pi = a.p[i];
+        const double2 w = make_double2(pi.x - K * v.x, pi.y - K * v.y);
+        a.Wn[i] = w;
+        double2 x = a.A[tri64(i) + j0];
+        x = cfms_conj_b(v, w0, x);
+        x = cfms_conj_b(w, vf, x);
+        if (i == j0) a.d[j0] = x.x;
+        if (i >= j0 + 1) s2 += x.x * x.x + x.y * x.y;
+        if (i >= j0 + 2) a.Vn[i] = x;
+        if (i == j0 + 1) s_x0 = x;
+    }
+    s2 = block_sum<double>(s2, red);
+    if (threadIdx.x == 0) {
+        a.e2[j0] = s2;
+        if (k + 1 <= n - 3) {
+            double2 f;
+            double tau;
+            fs_reflector_head(s2, s_x0, f, tau);
+            a.Vn[j0 + 1] = f;
+            a.tau[(k + 1) & 1] = tau;
+        }
+    }
+}
+
+// The last diagonal entry: step n-3's update of A_{n-1,n-1} (V = v_{n-3},
+// W = w_{n-3}).
+__global__ void k_fs_finish(FsArgs a) {
+    const int n = a.n;
+    const double2 v = a.V[n - 1], w = a.W[n - 1];
+    a.d[n - 1] = a.A[tri64(n - 1) + n - 1].x - 2.0 * (v.x * w.x + v.y * w.y);
+}
+
+// Gershgorin bracket and Sturm-count guards of the tridiagonal (d, e2), and
+// its float pairs (hi + lo = the FP64 entries exactly).  One CTA.
+// prm: [0] lo, [1] hi, [2] pivmin (float), [3] nrm.
+__global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_eig_prep(int n, const double* __restrict__ d,
+                                                                  const double* __restrict__ e2, float* df,
+                                                                  float* dlo, float* e2f, float* e2lo, double* prm) {
+    __shared__ double smin[FS_SCALAR_THREADS / 32], smax[FS_SCALAR_THREADS / 32], semax[FS_SCALAR_THREADS / 32];
+    double lo = 1e300, hi = -1e300, em = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double el = i > 0 ? sqrt(e2[i - 1]) : 0.0, er = i < n - 1 ? sqrt(e2[i]) : 0.0;
+        lo = fmin(lo, d[i] - el - er);
+        hi = fmax(hi, d[i] + el + er);
+        const double ee = i < n - 1 ? e2[i] : 0.0;
+        em = fmax(em, ee);
+        df[i] = (float)d[i];
+        dlo[i] = (float)(d[i] - (double)df[i]);
+        e2f[i] = (float)ee;
+        e2lo[i] = (float)(ee - (double)e2f[i]);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    em = warp_max(em);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) { smin[warp] = lo; smax[warp] = hi; semax[warp] = em; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < nw; ++w) { lo = fmin(lo, smin[w]); hi = fmax(hi, smax[w]); em = fmax(em, semax[w]); }
+        const double wdt = hi - lo, nrm = fmax(fabs(lo), fabs(hi));
+        prm[0] = lo - (1e-12 * (wdt + nrm) + 1e-300);
+        prm[1] = hi + (1e-12 * (wdt + nrm) + 1e-300);
+        prm[2] = (double)(FLT_MIN * fmaxf(1.0f, (float)em));
+        prm[3] = fmax(fabs(prm[0]), fabs(prm[1]));
+    }
+}
+
+// Eigenvalue k (ascending), one thread each: FP32 bisection to a few FP32
+// ulps of ||T||, then the widened bracket confirmed by double-float Sturm
+// counts and finished by safeguarded double-float Newton (eig_df_bracketed).
+__global__ void __launch_bounds__(FS_EIG_THREADS) k_fs_eig(int n, const float* __restrict__ df,
+                                                          const float* __restrict__ dlo, const float* __restrict__ e2f,
+                                                          const float* __restrict__ e2lo, const double* __restrict__ prm,
+                                                          double* __restrict__ eig) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double lo = prm[0], hi = prm[1], nrm = prm[3];
+    const float pivminf = (float)prm[2];
+    float a = (float)lo * (lo < 0 ? 1.0000002f : 0.9999998f) - 1e-30f;
+    float b = (float)hi * (hi > 0 ? 1.0000002f : 0.9999998f) + 1e-30f;
+    const float atolf = fmaxf(2.0f * FLT_EPSILON * (float)nrm, 1e-30f);
+    for (int it = 0; it < 96 && b - a > atolf; ++it) {
+        const float mid = 0.5f * (a + b);
+        if (!(mid > a && mid < b)) break;
+        if (sturm_count_f32(n, df, e2f, mid, pivminf) <= k) a = mid;
+        else b = mid;
+    }
+    eig[k] = eig_df_bracketed(n, df, dlo, e2f, e2lo, k, a, b, 8.0 * FLT_EPSILON * nrm, lo, hi, pivminf, nrm);
 }
 
 }  // namespace ptca
@@ -55,66 +326,104 @@ ptca_status ptca_internal_fail(ptca_status s, const char* msg);
 ptca::Model ptca_context_model(const ptca_ctx* ctx);
 
 extern "C" ptca_status ptca_full_spectrum(ptca_ctx* ctx, double* eig_out, void* stream) {
+    using namespace ptca;
     if (!ctx || !eig_out) return ptca_internal_fail(PTCA_ERR_INVALID, "null argument");
     const int N = ctx->N;
     if (N > 16384) return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_full_spectrum covers lattices of up to 16384 sites");
     const int n = 2 * N;
+    const int Tmax = (n - 1 + FS_TB - 1) / FS_TB;
+    const int red_max = (n + FS_RED_THREADS - 1) / FS_RED_THREADS;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cusolverDnHandle_t h = nullptr;
-    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS)
-        return ptca_internal_fail(PTCA_ERR_CUDA, "ptca_full_spectrum: cusolverDnCreate failed");
-    double2* H = nullptr;
-    double2* work = nullptr;
-    int* info = nullptr;
-    ptca_status status = PTCA_OK;
-    std::string why;
-    auto fail_cuda = [&](cudaError_t e, const char* where) {
-        status = e == cudaErrorMemoryAllocation ? PTCA_ERR_OOM : PTCA_ERR_CUDA;
-        why = std::string("ptca_full_spectrum: ") + where + ": " + cudaGetErrorString(e);
+
+    std::vector<void*> owned;
+    auto alloc = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes) != cudaSuccess) return nullptr;
+        owned.push_back(q);
+        return q;
     };
-    cudaError_t e = cusolverDnSetStream(h, st) == CUSOLVER_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
-    if (e == cudaSuccess) e = cudaMalloc(&H, (size_t)n * (size_t)n * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&info, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(H, 0, (size_t)n * (size_t)n * sizeof(double2), st);
-    if (e == cudaSuccess) {
-        const ptca::Model m = ptca_context_model(ctx);
-        ptca::k_full_hamiltonian<<<(N + 255) / 256, 256, 0, st>>>(m, ctx->d_S[0], N, H);
-        e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) fail_cuda(e, "building the matrix");
-    int lwork = 0;
-    if (status == PTCA_OK &&
-        cusolverDnZheevd_bufferSize(h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                    reinterpret_cast<cuDoubleComplex*>(H), n, eig_out, &lwork) !=
-            CUSOLVER_STATUS_SUCCESS) {
-        status = PTCA_ERR_CUDA;
-        why = "ptca_full_spectrum: eigensolver workspace query failed";
-    }
-    if (status == PTCA_OK) {
-        e = cudaMalloc(&work, (size_t)(lwork > 0 ? lwork : 1) * sizeof(double2));
-        if (e != cudaSuccess) fail_cuda(e, "workspace");
-    }
-    if (status == PTCA_OK &&
-        cusolverDnZheevd(h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n, reinterpret_cast<cuDoubleComplex*>(H),
-                         n, eig_out, reinterpret_cast<cuDoubleComplex*>(work), lwork, info) != CUSOLVER_STATUS_SUCCESS) {
-        status = PTCA_ERR_CUDA;
-        why = "ptca_full_spectrum: eigensolver call failed";
-    }
-    int hinfo = 0;
-    if (status == PTCA_OK) {
-        e = cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) fail_cuda(e, "synchronising");
-        else if (hinfo != 0) {
-            status = PTCA_ERR_NUMERIC;
-            why = "ptca_full_spectrum: the eigensolver did not converge (info " + std::to_string(hinfo) + ")";
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (void* q : owned) cudaFree(q);
+    };
+    // + 64 elements of padding past the packed triangle
+    double2* A = static_cast<double2*>(alloc(((size_t)tri64(n) + 64) * sizeof(double2)));
+    double2* vb = static_cast<double2*>(alloc(3 * (size_t)n * sizeof(double2)));
+    double2* wb = static_cast<double2*>(alloc(2 * (size_t)n * sizeof(double2)));
+    double2* p = static_cast<double2*>(alloc((size_t)n * sizeof(double2)));
+    double2* pr = static_cast<double2*>(alloc((size_t)(Tmax > 0 ? Tmax : 1) * n * sizeof(double2)));
+    double2* pc = static_cast<double2*>(alloc((size_t)(Tmax > 0 ? Tmax : 1) * n * sizeof(double2)));
+    double* red = static_cast<double*>(alloc((size_t)red_max * sizeof(double)));
+    double* tau = static_cast<double*>(alloc(2 * sizeof(double)));
+    double* d = static_cast<double*>(alloc((size_t)n * sizeof(double)));
+    double* e2 = static_cast<double*>(alloc((size_t)n * sizeof(double)));
+    float* f32 = static_cast<float*>(alloc(4 * (size_t)n * sizeof(float)));
+    double* prm = static_cast<double*>(alloc(4 * sizeof(double)));
+    for (void* q : {(void*)A, (void*)vb, (void*)wb, (void*)p, (void*)pr, (void*)pc, (void*)red, (void*)tau, (void*)d,
+                    (void*)e2, (void*)f32, (void*)prm})
+        if (!q) {
+            release();
+            return ptca_internal_fail(PTCA_ERR_OOM, "ptca_full_spectrum: not enough device memory for the matrix");
         }
+    auto fail = [&](cudaError_t e, const char* where) {
+        release();
+        cudaGetLastError();
+        return ptca_internal_fail(PTCA_ERR_CUDA, (std::string("ptca_full_spectrum: ") + where + ": " +
+                                                  cudaGetErrorString(e)).c_str());
+    };
+    cudaError_t e = cudaMemsetAsync(A, 0, ((size_t)tri64(n) + 64) * sizeof(double2), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(vb, 0, 3 * (size_t)n * sizeof(double2), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(wb, 0, 2 * (size_t)n * sizeof(double2), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(e2, 0, (size_t)n * sizeof(double), st);
+    if (e != cudaSuccess) return fail(e, "clearing the buffers");
+    const Model m = ptca_context_model(ctx);
+    k_full_hamiltonian<<<(N + 255) / 256, 256, 0, st>>>(m, ctx->d_S[0], N, A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "building the matrix");
+
+    FsArgs a;
+    a.n = n; a.A = A; a.pr = pr; a.pc = pc; a.p = p; a.red = red; a.tau = tau; a.d = d; a.e2 = e2;
+    if (n == 2) {
+        // d_0, d_1 and |e_0|^2 straight from the 2x2 matrix
+        a.U = a.V = vb; a.Vn = vb; a.W = wb; a.Wn = wb;
+        k_fs_setup<<<1, FS_SCALAR_THREADS, 0, st>>>(a);
+        a.V = vb + n; a.W = wb;  // zero vectors: the finish reads A_11 unchanged
+        k_fs_finish<<<1, 1, 0, st>>>(a);
+    } else {
+        // v_k in vb[k mod 3], w_k in wb[k mod 2]; v_{-1} = vb[2] and w_{-1}
+        // = wb[1] start at zero.
+        a.Vn = vb;
+        a.U = vb + 2 * (size_t)n;
+        a.W = wb + n;
+        a.V = vb;
+        a.Wn = wb;
+        k_fs_setup<<<1, FS_SCALAR_THREADS, 0, st>>>(a);
+        for (int k = 0; k <= n - 3 && e == cudaSuccess; ++k) {
+            const int mm = n - k - 1, T = (mm + FS_TB - 1) / FS_TB;
+            a.U = vb + (size_t)((k + 2) % 3) * n;
+            a.V = vb + (size_t)(k % 3) * n;
+            a.Vn = vb + (size_t)((k + 1) % 3) * n;
+            a.W = wb + (size_t)((k + 1) & 1) * n;
+            a.Wn = wb + (size_t)(k & 1) * n;
+            k_fs_pass<<<(unsigned)tri64(T), FS_PASS_THREADS, 0, st>>>(a, k);
+            const int nred = (mm + FS_RED_THREADS - 1) / FS_RED_THREADS;
+            k_fs_reduce<<<nred, FS_RED_THREADS, 0, st>>>(a, k);
+            k_fs_scalar<<<1, FS_SCALAR_THREADS, 0, st>>>(a, k, nred);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return fail(e, "reducing to tridiagonal form");
+        a.V = vb + (size_t)((n - 3) % 3) * n;
+        a.W = wb + (size_t)((n - 3) & 1) * n;
+        k_fs_finish<<<1, 1, 0, st>>>(a);
     }
-    cudaStreamSynchronize(st);
-    cudaFree(H);
-    cudaFree(work);
-    cudaFree(info);
-    cusolverDnDestroy(h);
-    if (status != PTCA_OK) return ptca_internal_fail(status, why.c_str());
+    float* df = f32;
+    float* dlo = f32 + n;
+    float* e2f = f32 + 2 * (size_t)n;
+    float* e2lo = f32 + 3 * (size_t)n;
+    k_fs_eig_prep<<<1, FS_SCALAR_THREADS, 0, st>>>(n, d, e2, df, dlo, e2f, e2lo, prm);
+    k_fs_eig<<<(n + FS_EIG_THREADS - 1) / FS_EIG_THREADS, FS_EIG_THREADS, 0, st>>>(n, df, dlo, e2f, e2lo, prm, eig_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "eigenvalues");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(e, "synchronising");
+    release();
     return PTCA_OK;
 }

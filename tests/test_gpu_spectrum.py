@@ -1,7 +1,8 @@
 """Full-system spectrum (Sec. VI): all 2N eigenvalues of the whole lattice's
 one-body Hamiltonian for the current configuration, against the oracle's
 dense matrix of a window that covers the whole lattice (L_c = L), for each
-model, open and periodic edges, a cube, and a periodic axis of extent 2."""
+model, open and periodic edges, a cube, a periodic axis of extent 2, a
+two-site chain, and an order (2048) where the reduction runs over many tiles."""
 import numpy as np
 import pytest
 import torch
@@ -46,6 +47,9 @@ def _reference(cfg, S):
     dict(cfg=dict(Lx=2, Ly=2, L_c=2), fields="unit"),
     dict(cfg=dict(Lx=6, Ly=6, L_c=3, model=P.MODEL_HUBBARD_MF, U=6.0), fields="free"),
     dict(cfg=dict(Lx=40, Ly=1, L_c=8, model=P.MODEL_HOLSTEIN, lam=1.3), fields="scalar"),
+    dict(cfg=dict(Lx=2, Ly=1, L_c=2), fields="unit"),
+    dict(cfg=dict(Lx=3, Ly=1, L_c=3, periodic=0), fields="unit"),
+    dict(cfg=dict(Lx=10, Ly=7, L_c=3, periodic=0, schedule=P.SCHEDULE_BLOCK), fields="unit"),
 ])
 def test_full_spectrum_matches_the_oracle(case):
     cfg = P.Config(**case["cfg"])
@@ -70,3 +74,19 @@ def test_full_spectrum_rejects_lattices_beyond_its_limit():
         P.ptca_full_spectrum(ctx.h, eig)
     assert e.value.status == 1
     ctx.close()
+
+
+def test_full_spectrum_at_order_2048_matches_lapack():
+    # 32x32 torus (n = 2048): 32 x 32 tiles of the reduction pass in its first
+    # steps; checked against LAPACK's eigvalsh of the oracle's dense matrix.
+    cfg = P.Config(Lx=32, Ly=32, L_c=4)
+    S = inputs.random_unit_spins(7, cfg.N)
+    got = _spectrum(cfg, S)
+    m = oracle.Model(Lx=32, Ly=32, Lc=32, schedule=oracle.SCHEDULE_BLOCK)
+    H, _ = oracle.cluster_hamiltonian(m, S, 0)
+    ref = np.sort(np.linalg.eigvalsh(H))
+    assert np.all(np.diff(got) >= 0)
+    assert np.max(np.abs(got - ref)) <= 1e-10 * 14.0
+    # trace and Frobenius norm of the spectrum against the matrix
+    assert abs(got.sum() - np.trace(H).real) <= 1e-9 * cfg.N
+    assert abs(np.sum(got ** 2) - np.sum(np.abs(H) ** 2)) <= 1e-9 * np.sum(np.abs(H) ** 2)

@@ -154,7 +154,7 @@ def test_host_side_of_the_c_abi_is_clean_under_sanitizers(tmp_path):
     if not all(os.path.exists(o) for o in objs):
         _build.build(force=True)  # the library is current but its objects were removed
     subprocess.run([cc, *_build.ARCH, "-shared", "-Xcompiler", "-fsanitize=address,-fsanitize=undefined",
-                    "-o", lib, api_o, *objs, "-lcudart", "-lcusolver"], check=True, capture_output=True)
+                    "-o", lib, api_o, *objs, "-lcudart"], check=True, capture_output=True)
     env = dict(os.environ, LD_PRELOAD=libasan,
                ASAN_OPTIONS="detect_leaks=0:abort_on_error=1:protect_shadow_gap=0",
                UBSAN_OPTIONS="halt_on_error=1:print_stacktrace=1",
