@@ -311,38 +311,91 @@ def time_sweeps(ctx, steps, warmup, flush_buf, stream, kernel_timing=False):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def surrogate_mode(P, base, args, flush, stream):
-    """Delayed acceptance with the surrogate network on the same workload: the
-    network is trained on (patch, dF) pairs from exact sweeps of this lattice
-    (collection and training untimed), then screened sweeps are timed."""
+def _collect(P, ctx, sweeps, stream):
+    """(patch, dF) pairs of `sweeps` exact sweeps of a context (untimed)."""
     import torch
-    N = base["Lx"] * base["Ly"]
-    ctx = P.Context(P.Config(**base, precision=P.MIXED))
-    n = args.sg_sweeps * N
+    n = sweeps * ctx.N
     feat = torch.empty((n, 150), dtype=torch.float32, device="cuda")
     center = torch.empty(n, dtype=torch.int32, device="cuda")
     dF = torch.empty(n, dtype=torch.float32, device="cuda")
-    torch.cuda.synchronize()
+    P.ptca_surrogate_collect(ctx.h, sweeps, feat, center, dF, stream=stream)
+    return feat, center, dF
+
+
+def surrogate_mode(P, base, args, flush, stream):
+    """Delayed acceptance with the surrogate network.  Training set (untimed):
+    about 10^6 (patch, dF) pairs from exact runs of the 32x32 lattice (tiled
+    stride 8, sphere proposals, T = 0.02, 0.05, 0.1, three seeds each) and of
+    the 100x100 headline lattice (cone proposals, T = 0.05).  Timed: screened
+    sweeps against the same context unscreened, both in the overlapped
+    per-stage pipeline with 4-warp CTAs, on three workloads: the headline (cone
+    30 deg, T = 0.05, high acceptance), the 100x100 lattice with sphere
+    proposals (T = 0.05), and the 32x32 lattice with sphere proposals at
+    T = 0.02 (lowest acceptance)."""
+    import torch
     t0 = time.perf_counter()
-    P.ptca_surrogate_collect(ctx.h, args.sg_sweeps, feat, center, dF, stream=stream)
+    parts = []
+    small = dict(Lx=32, Ly=32, L_c=8, periodic=1, t=1.0, J_H=8.0, mu=-6.5, schedule=P.SCHEDULE_TILED, stride=8,
+                 proposal=P.PROPOSAL_SPHERE, precision=P.MIXED)
+    per_chain = max(1, args.sg_pairs // 2 // (9 * 1024))
+    chains = [(P.Context(P.Config(**small, T=T, seed=100 + seed)), torch.cuda.Stream())
+              for T in (0.02, 0.05, 0.1) for seed in (0, 1, 2)]
+    for c, s in chains:  # the nine small chains run concurrently, one stream each
+        parts.append(_collect(P, c, per_chain, s))
+    torch.cuda.synchronize()
+    for c, _ in chains:
+        c.close()
+    ctx = P.Context(P.Config(**base, precision=P.MIXED))
+    parts.append(_collect(P, ctx, max(1, args.sg_pairs // 2 // ctx.N), stream))
+    feat = torch.cat([q[0] for q in parts])
+    center = torch.cat([q[1] for q in parts])
+    dF = torch.cat([q[2] for q in parts])
+    del parts
+    n = int(dF.numel())
     P.ptca_surrogate_init(ctx.h, 1, stream=stream)
     loss = torch.empty(args.sg_train_steps, dtype=torch.float32, device="cuda")
     P.ptca_surrogate_train(ctx.h, feat, center, dF, n, args.sg_train_steps, 512, 1e-3, 1e-4, 7, loss, stream=stream)
+    theta = torch.empty(P.ptca_surrogate_param_count(), dtype=torch.float32, device="cuda")
+    scale = P.ptca_surrogate_get_params(ctx.h, theta, stream=stream)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del feat, center, dF
-    P.ptca_surrogate_enable(ctx.h, True)
-    steps = max(3, args.steps // 2)
-    ms = time_sweeps(ctx, steps, 3, flush, stream)
-    st = P.ptca_sweep(ctx.h, steps, stats=True, stream=stream)
     ctx.close()
-    return {"value": N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
-            "exact_eigensolves_per_update": st.eigensolves / st.attempts,
-            "screened_fraction": st.screened / st.attempts, "acceptance": st.accepted / st.attempts,
+
+    def compare(cfg_kw, steps):
+        out = {}
+        for screened in (False, True):
+            c = P.Context(P.Config(**{**cfg_kw, "precision": P.MIXED}))
+            P.ptca_set_launch_config(c.h, P.PIPELINE_OVERLAP, 4)
+            if screened:
+                P.ptca_surrogate_set_params(c.h, theta, scale, stream=stream)
+                P.ptca_surrogate_enable(c.h, True)
+            ms = time_sweeps(c, steps, 3, flush, stream)
+            st = P.ptca_sweep(c.h, steps, stats=True, stream=stream)
+            N = c.N
+            c.close()
+            out["screened" if screened else "unscreened"] = {
+                "value": N * steps / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / steps,
+                "exact_eigensolves_per_update": st.eigensolves / st.attempts,
+                "screened_fraction": st.screened / st.attempts, "acceptance": st.accepted / st.attempts}
+        out["gain"] = out["screened"]["value"] / out["unscreened"]["value"]
+        return out
+
+    steps = max(3, args.steps // 2)
+    head = compare(dict(base), steps)
+    sphere = compare(dict(base, proposal=P.PROPOSAL_SPHERE), steps)
+    cold = compare(dict(small, T=0.02, seed=7), 4)
+    return {"value": head["screened"]["value"], "unit": "spin-updates/s",
+            "ms_per_step": head["screened"]["ms_per_step"],
+            "exact_eigensolves_per_update": head["screened"]["exact_eigensolves_per_update"],
+            "screened_fraction": head["screened"]["screened_fraction"],
+            "acceptance": head["screened"]["acceptance"], "headline": head,
+            "sphere_100x100_T0.05": sphere, "sphere_32x32_T0.02": cold,
             "train_pairs": n, "train_steps": args.sg_train_steps,
             "train_loss_first_last": [float(loss[:20].mean()), float(loss[-100:].mean())],
             "collect_and_train_s": t_train,
-            "note": "two-stage delayed acceptance (MLP screen, exact 8x8 cluster solve as judge); mixed guarded"}
+            "note": "two-stage delayed acceptance (MLP screen, exact cluster solve as judge), mixed guarded, "
+                    "overlapped per-stage pipeline, 4-warp CTAs; gain = screened / unscreened on the same workload"}
 
 
 def uneven_mode(P, args, flush, stream, rank):
@@ -597,8 +650,8 @@ def parser() -> argparse.ArgumentParser:
     ap.add_argument("--schedule", default="block", choices=["block", "tiled10", "tiled5"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sg-sweeps", type=int, default=20, help="exact sweeps collected to train the surrogate")
-    ap.add_argument("--sg-train-steps", type=int, default=3000)
+    ap.add_argument("--sg-pairs", type=int, default=1_000_000, help="(patch, dF) pairs collected to train the surrogate")
+    ap.add_argument("--sg-train-steps", type=int, default=4000)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the surrogate, uneven-batch, Hubbard, large-cluster and Holstein measurements")
     return ap

@@ -589,6 +589,7 @@ static StageArgs base_args(ptca_ctx* ctx) {
 }
 
 cudaError_t ptca_screen_stage(ptca_ctx* ctx, ptca::StageArgs& a, cudaStream_t st);
+cudaError_t ptca_screen_part(ptca_ctx* ctx, ptca::StageArgs& a, int part, int row_base, int half, cudaStream_t st);
 
 // A stage launch and a re-solve launch in the context's configuration
 // (shared-memory kernels, or the large-cluster kernels).
@@ -716,6 +717,7 @@ static cudaError_t ensure_overlap(ptca_ctx* ctx) {
 static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
     cudaError_t e = ensure_overlap(ctx);
     if (e != cudaSuccess) return e;
+    const bool screen = ctx->sg.enabled;
     cudaStream_t hs = ctx->side;
     const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
     const int ns = ctx->nstages;
@@ -752,6 +754,12 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         StageArgs ai = a;
         ai.perm = ctx->d_split + ctx->h_start[s];
         ai.count = ni;
+        // Delayed acceptance: each part of the stage is screened on its own
+        // stream just before its exact solves (network rows of the
+        // independent part first, the dependent part's after them; dF~ in
+        // the half of this stage's parity, which its re-solve reads later).
+        if (screen && e == cudaSuccess && ni > 0) e = ptca_screen_part(ctx, ai, 0, 0, (int)(g & 1), st);
+        if (screen) a.sg_dFt = ctx->sg.dFt + (size_t)(g & 1) * ctx->max_stage;
         if (e == cudaSuccess && ni > 0)
             e = timed_launch(ctx, 0, 2 * (int64_t)ni, st,
                              [&] { return launch_stage_ctx(ctx, ai, st); });
@@ -768,6 +776,7 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         if (g >= 1 && (g - 1) % ns != s) stage_sites(g - 1, ad.prev_sites, ad.prev_count);
         if (g >= 2 && (g - 2) % ns != s && (g - 2) % ns != (g - 1) % ns)
             stage_sites(g - 2, ad.prev2_sites, ad.prev2_count);
+        if (screen && e == cudaSuccess && ad.count > 0) e = ptca_screen_part(ctx, ad, 1, 2 * ni, (int)(g & 1), hs);
         if (e == cudaSuccess) {
             if (ad.count > 0) {
                 e = timed_launch(ctx, 2, 2 * (int64_t)ad.count, hs,
@@ -846,8 +855,7 @@ static cudaError_t sweep_graph(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st)
 // (screening and the checker need the per-stage pipeline).
 static cudaError_t run_sweeps(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
     const bool per_stage = ctx->pipeline == PTCA_PIPELINE_STAGES || ctx->pipeline == PTCA_PIPELINE_OVERLAP;
-    if (ctx->pipeline == PTCA_PIPELINE_OVERLAP && ctx->prec == 1 && ctx->margin > 0.0 && !ctx->sg.enabled &&
-        !ctx->checker)
+    if (ctx->pipeline == PTCA_PIPELINE_OVERLAP && ctx->prec == 1 && ctx->margin > 0.0 && !ctx->checker)
         return sweep_overlap(ctx, n_sweeps, st);
     if (per_stage || ctx->sg.enabled || ctx->checker) return sweep_stages(ctx, n_sweeps, st);
     if (ctx->pipeline == PTCA_PIPELINE_PERSISTENT || ctx->graph_failed) return enqueue_persistent(ctx, n_sweeps, st);

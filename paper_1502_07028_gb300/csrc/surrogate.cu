@@ -281,13 +281,15 @@ cudaError_t sg_iota(int64_t* idx, int n, cudaStream_t st) {
 // Delayed-acceptance screening of one stage.
 // ---------------------------------------------------------------------------
 // Rows of the stage: row c = c[P(s_old), s_new], row count + c = c[P(s_new), s_old].
+// Visit c of the screened list is stage index a.perm[c] (or c without a
+// list).
 __global__ void k_screen_rows(StageArgs a, float* __restrict__ X) {
     const int c = blockIdx.x;
     if (c >= a.count) return;
     __shared__ float f[SG_IN];
     __shared__ double sn[3];
     __shared__ int center;
-    const int site = a.sites[c];
+    const int site = a.sites[a.perm ? a.perm[c] : c];
     const Window w = make_window(a.m, site);
     if (threadIdx.x == 0) {
         propose(a.m, a.sweep, (uint32_t)site, a.S_in + 3 * site, sn);
@@ -300,14 +302,16 @@ __global__ void k_screen_rows(StageArgs a, float* __restrict__ X) {
 
 // Stage 1 of delayed acceptance: dF~ = scale (h1 - h2); pass to the exact
 // solve with probability min(1, exp(-dF~/T)) (uniform from its own counter
-// purpose).  Passing sites are appended to the work list; rejected sites keep
-// their spin and are recorded (free energies NaN: not computed).
+// purpose).  Passing sites are appended to the work list (as stage indices);
+// rejected sites keep their spin and are recorded (free energies NaN: not
+// computed).  dFt is indexed by stage index; Z4 rows by list position.
 __global__ void k_screen_decide(StageArgs a, const float* __restrict__ Z4, float scale, float* __restrict__ dFt,
                                 int32_t* __restrict__ work, unsigned int* __restrict__ nwork) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.count) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.count) return;
+    const int c = a.perm ? a.perm[k] : k;
     const int site = a.sites[c];
-    const double d = (double)scale * ((double)Z4[(long long)c * SG_OUT_PAD] - (double)Z4[(long long)(a.count + c) * SG_OUT_PAD]);
+    const double d = (double)scale * ((double)Z4[(long long)k * SG_OUT_PAD] - (double)Z4[(long long)(a.count + k) * SG_OUT_PAD]);
     dFt[c] = (float)d;
     double u0, u1;
     uniform2(a.m.seed, a.sweep, (uint32_t)site, RNG_SCREEN, u0, u1);

@@ -142,9 +142,12 @@ ptca_status ptca_surrogate_init(ptca_ctx* ctx, uint64_t seed, void* stream) {
         for (float** h : hs)
             if (e == cudaSuccess) e = dal(h, R * ptca::SG_H);
         if (e == cudaSuccess) e = dal(&g.Z4, R * ptca::SG_OUT_PAD);
-        if (e == cudaSuccess) e = dal(&g.dFt, (size_t)ctx->max_stage);
-        if (e == cudaSuccess) e = dal(&g.work, (size_t)ctx->max_stage);
-        if (e == cudaSuccess) e = dal(&g.nwork, 1);
+        // dF~ per stage index in two halves (stage parity), and the work list
+        // of each part of a stage (all visits, or the overlapped pipeline's
+        // independent and dependent visits)
+        if (e == cudaSuccess) e = dal(&g.dFt, 2 * (size_t)ctx->max_stage);
+        if (e == cudaSuccess) e = dal(&g.work, 2 * (size_t)ctx->max_stage);
+        if (e == cudaSuccess) e = dal(&g.nwork, 2);
         if (e != cudaSuccess) {
             ptca_free_surrogate(ctx);
             return cfail(e, "ptca_surrogate_init");
@@ -255,18 +258,35 @@ ptca_status ptca_surrogate_predict(ptca_ctx* ctx, const float* feat, const int32
 
 }  // extern "C"
 
-// Screening of one stage inside ptca_sweep (called by api.cu): features of
-// every update site's two pair rows, the network, stage-1 decisions and the
-// work list of sites that go on to the exact solve.
-extern "C" cudaError_t ptca_screen_stage(ptca_ctx* ctx, ptca::StageArgs& a, cudaStream_t st) {
+// Screening of one part of a stage inside ptca_sweep (called by api.cu):
+// features of the two pair rows of each listed visit, the network, stage-1
+// decisions and the work list of visits that go on to the exact solve.  The
+// part's visits are a.perm[0 .. a.count) (stage indices; all of the stage
+// when a.perm is null).  part 0 takes the network rows from 0, part 1 those
+// after row_base (the two parts of a stage can be screened concurrently);
+// dF~ goes to the half `half` (stage parity).  On return a.perm is the work
+// list, a.count_dev its length and a.sg_dFt the stage's dF~.
+extern "C" cudaError_t ptca_screen_part(ptca_ctx* ctx, ptca::StageArgs& a, int part, int row_base, int half,
+                                        cudaStream_t st) {
     SurrogateState& g = ctx->sg;
     const int R = 2 * a.count;
-    cudaError_t e = cudaMemsetAsync(g.nwork, 0, sizeof(unsigned int), st);
-    if (e == cudaSuccess) e = ptca::sg_screen_rows(a, g.X, st);
-    if (e == cudaSuccess) e = mlp_forward(g.theta, R, g.X, g.Z1, g.A1, g.Z2, g.A2, g.Z3, g.A3, g.Z4, st);
-    if (e == cudaSuccess) e = ptca::sg_screen_decide(a, g.Z4, g.scale, g.dFt, g.work, g.nwork, st);
-    a.perm = g.work;
-    a.count_dev = g.nwork;
-    a.sg_dFt = g.dFt;
+    const size_t rb = (size_t)row_base;
+    float* dFt = g.dFt + (size_t)half * ctx->max_stage;
+    int32_t* work = g.work + (size_t)part * ctx->max_stage;
+    unsigned int* nwork = g.nwork + part;
+    cudaError_t e = cudaMemsetAsync(nwork, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = ptca::sg_screen_rows(a, g.X + rb * ptca::SG_IN_PAD, st);
+    if (e == cudaSuccess)
+        e = mlp_forward(g.theta, R, g.X + rb * ptca::SG_IN_PAD, g.Z1 + rb * ptca::SG_H, g.A1 + rb * ptca::SG_H,
+                        g.Z2 + rb * ptca::SG_H, g.A2 + rb * ptca::SG_H, g.Z3 + rb * ptca::SG_H, g.A3 + rb * ptca::SG_H,
+                        g.Z4 + rb * ptca::SG_OUT_PAD, st);
+    if (e == cudaSuccess) e = ptca::sg_screen_decide(a, g.Z4 + rb * ptca::SG_OUT_PAD, g.scale, dFt, work, nwork, st);
+    a.perm = work;
+    a.count_dev = nwork;
+    a.sg_dFt = dFt;
     return e;
+}
+
+extern "C" cudaError_t ptca_screen_stage(ptca_ctx* ctx, ptca::StageArgs& a, cudaStream_t st) {
+    return ptca_screen_part(ctx, a, 0, 0, 0, st);
 }
