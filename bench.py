@@ -560,13 +560,14 @@ def hubbard_mode(P, args, flush, stream, rank, Lz=1):
 def large_cluster_mode(P, args, flush, stream, rank):
     """The paper's large traveling clusters (Sec. VII.a): N_c = 12^2 (n = 288)
     on a 48x48 torus, double exchange as the headline (J_H = 8, mu = -6.5,
-    T = 0.05, cone 30 deg), block schedule.  Mixed guarded (autotuned) and
-    the plain FP64 path; both on the global-memory Householder kernels."""
+    T = 0.05, cone 30 deg), block schedule.  Mixed guarded (autotuned over
+    the 16-warp global-memory kernel and the thread-block-cluster kernel) and
+    the plain FP64 path (global-memory kernel)."""
     base = dict(Lx=48, Ly=48, L_c=12, periodic=1, t=1.0, J_H=8.0, mu=-6.5, T=0.05, seed=rank, cone_deg=30.0,
                 proposal=P.PROPOSAL_CONE, schedule=P.SCHEDULE_BLOCK)
     N = 48 * 48
     ctx = P.Context(P.Config(**base, precision=P.MIXED))
-    best, _ = P.ptca_autotune(ctx.h, 1)
+    best, table = P.ptca_autotune(ctx.h, 1)
     ms = time_sweeps(ctx, 3, 3, flush, stream)
     st = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
     ctx.close()
@@ -574,7 +575,10 @@ def large_cluster_mode(P, args, flush, stream, rank):
                        "block schedule, global-memory Householder (16-warp CTAs)",
            "value": N * 3 / (sum(ms) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms) / 3,
            "resolved_fraction": st.resolved / st.attempts, "acceptance": st.accepted / st.attempts,
-           "launch": {"pipeline": best.pipeline}}
+           "launch": {"pipeline": best.pipeline, "warps_per_cta": best.warps_per_cta,
+                      "kernel": "thread-block cluster, matrix in distributed shared memory" if best.warps_per_cta == 8
+                                else "16-warp CTA, matrix in global memory"},
+           "autotune": [[c["pipeline"], c["warps_per_cta"], c["ms_per_sweep"]] for c in table["candidates"]]}
     ctx = P.Context(P.Config(**base, precision=P.FP64))
     ms64 = time_sweeps(ctx, 1, 3, flush, stream)
     ctx.close()
@@ -608,6 +612,37 @@ def holstein_mode(P, args, flush, stream, rank):
     ctx.close()
     out["fp64_path"] = {"value": N * 2 / (sum(ms64) * 1e-3), "unit": "spin-updates/s", "ms_per_step": sum(ms64) / 2}
     return out
+
+
+def small_config0_mode(P, stream):
+    """The 8x8 torus with 4x4 clusters (n = 32), J_H = 8, mu = -6.5, T = 0.05,
+    sphere proposals, seed 0, 10 sweeps (640 updates, 1280 cluster solves):
+    the whole run on the GPU (plain FP64 path) and by the FP64 oracle on one
+    host core."""
+    import oracle
+    import torch
+    cfg = P.Config(Lx=8, Ly=8, L_c=4, t=1.0, J_H=8.0, mu=-6.5, T=0.05, seed=0, precision=P.FP64)
+    ctx = P.Context(cfg)
+    P.ptca_set_pipeline(ctx.h, P.PIPELINE_STAGES)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    P.ptca_sweep(ctx.h, 10, stats=False, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    gpu_s = a.elapsed_time(b) * 1e-3
+    ctx.close()
+    oracle.build()
+    m = oracle.Model(Lx=8, Ly=8, Lc=4, JH=8.0, mu=-6.5, T=0.05, seed=0)
+    S = oracle.init_spins(m)
+    t0 = time.perf_counter()
+    for sw in range(10):
+        S, _ = oracle.sweep(m, S, sw)
+    cpu_s = time.perf_counter() - t0
+    return {"workload": "8x8 torus, 4x4 clusters (n=32), J_H=8, mu=-6.5, T=0.05, sphere proposals, 10 sweeps",
+            "gpu_fp64": {"value": 640 / gpu_s, "unit": "spin-updates/s", "seconds": gpu_s,
+                         "note": "per-stage launches, 16 stages of 4 visits: latency-bound"},
+            "oracle_one_core": {"value": 640 / cpu_s, "unit": "spin-updates/s", "seconds": cpu_s}}
 
 
 def full_spectrum_mode(P, args, stream, rank):
@@ -767,6 +802,8 @@ def main():
         extra["small_lattice_32"] = small_lattice_mode(P, args, flush, stream, rank)
         extra["uneven_open_ramp"] = ramp_mode(P, args, flush, stream, rank)
         extra["full_spectrum"] = full_spectrum_mode(P, args, stream, rank)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            extra["config0_full"] = small_config0_mode(P, stream)
 
     # --- plain FP64 GPU path on the same workload
     ctx64 = P.Context(P.Config(**base, precision=P.FP64))

@@ -274,7 +274,13 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  *   warps_per_cta  8: one 8-warp CTA per cluster matrix (every precision
  *                  and order); 4: one warp group per matrix, more resident
  *                  matrices per SM (PTCA_MIXED, orders up to 128); 1: one
- *                  warp per matrix (PTCA_MIXED, orders up to 32);
+ *                  warp per matrix (PTCA_MIXED, orders up to 32).  Orders
+ *                  above the shared-memory kernels' (large clusters,
+ *                  Sec. VII.a): 8 runs PTCA_MIXED stages on a thread-block
+ *                  cluster of 2, 4 or 8 CTAs per matrix holding it in
+ *                  distributed shared memory (every precision else: one
+ *                  16-warp CTA, matrix in global memory); 16 runs the
+ *                  16-warp, global-memory kernel;
  *   ctas_per_sm    CTAs per SM of the persistent kernel, 0 = as many as fit.
  * Every configuration computes the same chain (decisions and spins; free
  * energies to rounding). */

@@ -438,6 +438,15 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
             // independent and dependent visits as concurrent launches, each
             // on its own half (+ 64 elements of padding, as below).
             c->large_grid = sms * std::max(1, ptca::large_blocks_per_sm(c->prec));
+            if (c->prec == 1) {
+                c->cl_size = ptca::cluster_stage_size(c->nA, (size_t)optin);
+                c->cl_grid = c->cl_size ? ptca::cluster_stage_grid(c->cl_size, c->nA) : 0;
+                if (c->cl_grid <= 0) c->cl_size = 0;
+            }
+            // Default: the 16-warp kernel with the matrix in global memory,
+            // measured faster than the cluster kernel at orders 288 and 512
+            // (the autotuner times both).
+            c->nw = 16;
             c->gL_stride = (int64_t)c->nA * (c->nA + 1) / 2;
             const size_t es = c->prec == 1 ? sizeof(float2) : sizeof(double2);
             void* q = nullptr;
@@ -594,6 +603,8 @@ cudaError_t ptca_screen_part(ptca_ctx* ctx, ptca::StageArgs& a, int part, int ro
 // A stage launch and a re-solve launch in the context's configuration
 // (shared-memory kernels, or the large-cluster kernels).
 static cudaError_t launch_stage_ctx(const ptca_ctx* ctx, const StageArgs& a, cudaStream_t st) {
+    if (ctx->large && ctx->prec == 1 && ctx->nw == 8 && ctx->cl_size > 0)
+        return ptca::launch_stage_cluster(ctx->cl_size, a, ctx->cl_grid, st);
     if (ctx->large) return ptca::launch_stage_large(ctx->prec, a, ctx->large_grid, st);
     return ptca::launch_stage(ctx->prec, ctx->nw, a, st);
 }
@@ -918,10 +929,14 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     if (!ctx || !cfg) return fail(PTCA_ERR_INVALID, "null argument");
     if (cfg->pipeline < PTCA_PIPELINE_STAGES || cfg->pipeline > PTCA_PIPELINE_OVERLAP)
         return fail(PTCA_ERR_INVALID, "unknown pipeline");
-    if (cfg->warps_per_cta != 8 && cfg->warps_per_cta != 4 && cfg->warps_per_cta != 1)
-        return fail(PTCA_ERR_INVALID, "warps_per_cta must be 1, 4 or 8");
-    if (ctx->large && cfg->warps_per_cta != 8)
-        return fail(PTCA_ERR_UNSUPPORTED, "large clusters run 16-warp CTAs; pass warps_per_cta = 8 (the default width)");
+    if (cfg->warps_per_cta != 8 && cfg->warps_per_cta != 4 && cfg->warps_per_cta != 1 && cfg->warps_per_cta != 16)
+        return fail(PTCA_ERR_INVALID, "warps_per_cta must be 1, 4, 8 or 16");
+    if (ctx->large && cfg->warps_per_cta != 8 && cfg->warps_per_cta != 16)
+        return fail(PTCA_ERR_UNSUPPORTED,
+                    "large clusters run 8-warp CTAs in thread-block clusters (PTCA_MIXED) or 16-warp CTAs with the "
+                    "matrix in global memory: pass warps_per_cta = 8 or 16");
+    if (!ctx->large && cfg->warps_per_cta == 16)
+        return fail(PTCA_ERR_UNSUPPORTED, "16-warp CTAs serve the large-cluster orders only");
     if (!ctx->large && !ptca::sweep_width_supported(ctx->prec, cfg->warps_per_cta, ctx->nA))
         return fail(PTCA_ERR_UNSUPPORTED,
                     "narrow sweep kernels need PTCA_MIXED and matrix orders up to 128 (4 warps) or 32 (1 warp)");
@@ -961,8 +976,11 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
     // Candidates: CTA width x pipeline x persistent CTAs per SM.
     std::vector<ptca_launch_config> cand;
     if (ctx->large) {
-        cand.push_back({PTCA_PIPELINE_STAGES, 8, 0});
-        if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, 8, 0});
+        for (int nw : {16, 8}) {
+            if (nw == 8 && ctx->cl_size == 0) continue;  // 8 would mean the global-slot kernel again
+            cand.push_back({PTCA_PIPELINE_STAGES, nw, 0});
+            if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0});
+        }
     }
     for (int nw : {8, 4, 1}) {
         if (ctx->large || !ptca::sweep_width_supported(ctx->prec, nw, ctx->nA)) continue;

@@ -103,6 +103,11 @@ struct ptca_ctx {
     // one global matrix slot per resident 16-warp CTA
     bool large = false;
     int large_grid = 0;
+    // FP32 large clusters may instead run the cluster kernel (matrix in the
+    // distributed shared memory of cl_size CTAs; 0 when it does not fit),
+    // selected by warps_per_cta = 8 (16: the global-slot kernel)
+    int cl_size = 0;
+    int cl_grid = 0;
     void* d_gL = nullptr;
     int64_t gL_stride = 0;
     // precision checker (PTCA_MIXED): FP32-vs-FP64 spectra of every visit

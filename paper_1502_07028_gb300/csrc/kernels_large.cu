@@ -1,7 +1,9 @@
 // kernels_large.cu -- instantiation and launchers of the large-cluster
 // kernels (orders above the shared-memory kernels' reach, up to 512): the
-// FP32 and FP64 stage kernels and the double-float re-solve, all with the
-// matrix in a global slot per CTA.
+// FP32 and FP64 stage kernels and the double-float re-solve with the matrix
+// in a global slot per CTA, and the FP32 stage kernel with the matrix in the
+// distributed shared memory of a thread-block cluster (cluster_large.cuh).
+#include "cluster_large.cuh"
 #include "kernels.cuh"
 #include "launch.h"
 
@@ -48,6 +50,70 @@ cudaError_t launch_stage_large(int prec, const StageArgs& a, int grid, cudaStrea
     else
         k_stage_large<double><<<grid, 32 * NW_LARGE, large_layout(sizeof(double2)), st>>>(a);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Cluster kernel: the smallest cluster size (2, 4 or 8 CTAs) whose per-CTA
+// share of the matrix fits in shared memory.
+namespace {
+template <int C> cudaError_t cl_allow(size_t smem_limit, int nA) {
+    const size_t need = cl_layout<C>(nA).total;
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, k_stage_cluster<C>);
+    if (e != cudaSuccess) return e;
+    if (need + attr.sharedSizeBytes > smem_limit) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k_stage_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+}
+template <int C> cudaLaunchConfig_t cl_config(int nA, int grid, cudaStream_t st, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(CL_THREADS);
+    cfg.dynamicSmemBytes = cl_layout<C>(nA).total;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+template <int C> int cl_grid(int nA) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cl_config<C>(nA, C, nullptr, attr);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_stage_cluster<C>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return clusters * C;
+}
+}  // namespace
+
+int cluster_stage_size(int nA, size_t smem_limit) {
+    if (nA > 32 * NW_LARGE) return 0;
+    if (cl_allow<2>(smem_limit, nA) == cudaSuccess) return 2;
+    cudaGetLastError();
+    if (cl_allow<4>(smem_limit, nA) == cudaSuccess) return 4;
+    cudaGetLastError();
+    if (cl_allow<8>(smem_limit, nA) == cudaSuccess) return 8;
+    cudaGetLastError();
+    return 0;
+}
+
+int cluster_stage_grid(int C, int nA) {
+    return C == 2 ? cl_grid<2>(nA) : C == 4 ? cl_grid<4>(nA) : C == 8 ? cl_grid<8>(nA) : 0;
+}
+
+cudaError_t launch_stage_cluster(int C, const StageArgs& a, int grid, cudaStream_t st) {
+    if (a.count <= 0 && a.prev_count + a.prev2_count <= 0) return cudaSuccess;
+    cudaLaunchAttribute attr[1];
+    switch (C) {
+        case 2: { cudaLaunchConfig_t cfg = cl_config<2>(a.nA, grid, st, attr); return cudaLaunchKernelEx(&cfg, k_stage_cluster<2>, a); }
+        case 4: { cudaLaunchConfig_t cfg = cl_config<4>(a.nA, grid, st, attr); return cudaLaunchKernelEx(&cfg, k_stage_cluster<4>, a); }
+        case 8: { cudaLaunchConfig_t cfg = cl_config<8>(a.nA, grid, st, attr); return cudaLaunchKernelEx(&cfg, k_stage_cluster<8>, a); }
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_resolve_large(const StageArgs& a, int grid, cudaStream_t st) {

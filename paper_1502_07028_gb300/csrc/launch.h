@@ -75,6 +75,13 @@ cudaError_t configure_large_kernels(size_t smem_limit);
 int large_blocks_per_sm(int prec);
 cudaError_t launch_stage_large(int prec, const StageArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_resolve_large(const StageArgs& a, int grid, cudaStream_t st);
+// FP32 large-cluster stage kernel with the matrix in the distributed shared
+// memory of a thread-block cluster: the cluster size (2, 4 or 8 CTAs, 0 if
+// none fits) for order nA (configures the kernel's shared memory), the grid
+// (CTAs of the clusters that fit at once), and the launch.
+int cluster_stage_size(int nA, size_t smem_limit);
+int cluster_stage_grid(int C, int nA);
+cudaError_t launch_stage_cluster(int C, const StageArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_observables(const double* S, int Lx, int Ly, const double* rec_Facc, const double* rec_fill,
                                const uint8_t* rec_acc, const int32_t* rec_n, int N, double* out, cudaStream_t st);
 

@@ -21,22 +21,27 @@ def _lib():
     P.lib()
 
 
-@pytest.mark.parametrize("prec", [P.FP64, P.MIXED])
+@pytest.mark.parametrize("prec,width", [(P.FP64, 16), (P.MIXED, 16), (P.MIXED, 8)])
 @pytest.mark.parametrize("Lc", [11, 12])
-def test_large_cluster_sweeps_match_oracle(prec, Lc):
+def test_large_cluster_sweeps_match_oracle(prec, width, Lc):
+    # width 16: one CTA per matrix, the matrix in global memory; width 8
+    # (PTCA_MIXED): a thread-block cluster per matrix, the matrix in
+    # distributed shared memory.
     cfg = P.Config(Lx=2 * Lc, Ly=2 * Lc, L_c=Lc, schedule=P.SCHEDULE_BLOCK, J_H=8.0, mu=-6.5, T=0.1, seed=Lc,
                    precision=prec, proposal=P.PROPOSAL_CONE)
-    _check_sweep_against_oracle(cfg, sweeps=1, sample=4)
+    _check_sweep_against_oracle(cfg, sweeps=1, sample=4, launch=(P.PIPELINE_STAGES, width))
 
 
-def test_16x16_clusters_n512_match_oracle():
+@pytest.mark.parametrize("width", [16, 8])
+def test_16x16_clusters_n512_match_oracle(width):
     cfg = P.Config(Lx=32, Ly=32, L_c=16, schedule=P.SCHEDULE_BLOCK, J_H=8.0, mu=-6.5, T=0.1, seed=16,
                    precision=P.MIXED, proposal=P.PROPOSAL_CONE)
-    _check_sweep_against_oracle(cfg, sweeps=1, sample=2)
+    _check_sweep_against_oracle(cfg, sweeps=1, sample=2, launch=(P.PIPELINE_STAGES, width))
 
 
+@pytest.mark.parametrize("width", [16, 8])
 @pytest.mark.parametrize("margin", [None, 1e6])
-def test_large_cluster_pipelines_are_bit_identical(margin):
+def test_large_cluster_pipelines_are_bit_identical(margin, width):
     # Default margin: most decisions come from the FP32 solves of the
     # concurrent independent and dependent launches; 1e6: every decision is
     # re-solved in double-float.
@@ -47,7 +52,7 @@ def test_large_cluster_pipelines_are_bit_identical(margin):
         ctx = P.Context(cfg)
         if margin is not None:
             P.ptca_set_resolve_margin(ctx.h, margin)
-        P.ptca_set_launch_config(ctx.h, pl, 8, 0)
+        P.ptca_set_launch_config(ctx.h, pl, width, 0)
         st = ctx.sweep(2)
         if margin is not None:
             assert st.resolved == 2 * cfg.N
@@ -65,6 +70,10 @@ def test_large_cluster_limits_are_reported():
         with pytest.raises(P.PtcaError) as e:
             P.ptca_set_launch_config(ctx.h, pl, 8, 0)
         assert e.value.status in (1, 6)
+    with pytest.raises(P.PtcaError) as e:
+        P.ptca_set_launch_config(ctx.h, P.PIPELINE_STAGES, 4, 0)
+    assert e.value.status == 6
+    assert P.ptca_get_launch_config(ctx.h).warps_per_cta == 16
     with pytest.raises(P.PtcaError) as e:
         P.ptca_set_checker(ctx.h, True)
     assert e.value.status == 6
