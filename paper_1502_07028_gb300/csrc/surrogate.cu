@@ -1,10 +1,13 @@
 // surrogate.cu -- BF16 tensor-core kernels of the surrogate network (training
 // and inference) and the delayed-acceptance screening of a PTCA stage.
 //
-// All matrix products go through k_gemm_bf16: operands are rounded to bfloat16
-// (round to nearest even) when staged into shared memory and multiplied on
-// the tensor cores with mma.sync m16n8k16, accumulating in FP32.  Everything
-// else (bias, SiLU, loss, AdamW) runs in FP32.
+// Matrix products: operands are rounded to bfloat16 (round to nearest even)
+// when staged into shared memory and multiplied on the tensor cores,
+// accumulating in FP32.  The forward products (activations times the
+// transposed weights) run on tcgen05 with the accumulator in tensor memory
+// (k_gemm_tc); the transposed products of the backward pass use the
+// mma.sync m16n8k16 tile loop (k_gemm_bf16).  Everything else (bias, SiLU,
+// loss, AdamW) runs in FP32.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -95,9 +98,169 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const fl
             }
 }
 
+// ---------------------------------------------------------------------------
+// The forward products of the network on the 5th-generation tensor cores:
+// C[M x N] = A W^T (+ bias) for A row-major (M x K, leading dimension lda)
+// and W row-major (N x K, leading dimension ldw), both FP32 in global memory,
+// N <= 256, K <= 256.  One CTA of 4 warps per 128 rows of A:
+//   * the CTA rounds its rows of A and all of W to bfloat16 (round to nearest
+//     even, as k_gemm_bf16) into shared memory in the K-major, 128-byte
+//     swizzled layout of the tensor cores: 64 K-elements (128 bytes) per row
+//     and K block, 8-row atoms of 1024 bytes, the 16-byte chunk c of row r at
+//     chunk position c ^ (r mod 8);
+//   * one thread issues tcgen05.mma (kind::f16: BF16 x BF16 -> FP32 in
+//     tensor memory; M = 128, N = N rounded up to 16, K = 16 per instruction)
+//     and commits them to an mbarrier;
+//   * each warp reads its 32 accumulator rows (tensor-memory lanes 32w ..
+//     32w + 31) with tcgen05.ld and writes C with the bias.
+// The wait on the mbarrier is bounded: past the limit the CTA writes NaN
+// into its rows of C, sets *err (if given) and still frees its tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_KB = 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading offset
+// (unused with swizzling), 1024 bytes between 8-row groups, descriptor
+// version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5), BF16 A
+// (bits 7-9) and B (bits 10-12), both K-major, N / 8 (bits 17-22), M / 16
+// (bits 24-28).
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__host__ __device__ constexpr int tc_cols(int np) { return np <= 32 ? 32 : np <= 64 ? 64 : np <= 128 ? 128 : 256; }
+
+__host__ __device__ constexpr size_t tc_smem_bytes(int K, int N) {
+    return (size_t)((K + TC_KB - 1) / TC_KB) * (TC_M + (N + 15) / 16 * 16) * 128 + 1024 + 64;
+}
+
+// Rows [r0, r0 + rows) of X (row-major, leading dimension ld; rows >= nrows
+// and columns >= K read as 0) into the swizzled bf16 layout at dst.
+__device__ __forceinline__ void tc_stage(unsigned char* dst, const float* __restrict__ X, int ld, int r0, int rows,
+                                         int nrows, int K, int nkb) {
+    for (int e = threadIdx.x; e < nkb * rows * 8; e += blockDim.x) {
+        const int c = e & 7, r = (e >> 3) % rows, kb = (e >> 3) / rows;
+        const int row = r0 + r, k = kb * TC_KB + 8 * c;
+        float x[8];
+        if (row < nrows && k + 8 <= K && ((ld | k) & 3) == 0) {
+            const float4* q = reinterpret_cast<const float4*>(X + (long long)row * ld + k);
+            const float4 a = q[0], b = q[1];
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        } else {
+#pragma unroll
+            for (int h = 0; h < 8; ++h) x[h] = (row < nrows && k + h < K) ? X[(long long)row * ld + k + h] : 0.f;
+        }
+        uint4 v;
+        v.x = pack_bf16(__float2bfloat16_rn(x[0]), __float2bfloat16_rn(x[1]));
+        v.y = pack_bf16(__float2bfloat16_rn(x[2]), __float2bfloat16_rn(x[3]));
+        v.z = pack_bf16(__float2bfloat16_rn(x[4]), __float2bfloat16_rn(x[5]));
+        v.w = pack_bf16(__float2bfloat16_rn(x[6]), __float2bfloat16_rn(x[7]));
+        *reinterpret_cast<uint4*>(dst + ((size_t)kb * rows + r) * 128 + ((c ^ (r & 7)) << 4)) = v;
+    }
+}
+
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                   const float* __restrict__ W, int ldw,
+                                                   const float* __restrict__ bias, float* __restrict__ C, int ldc,
+                                                   int* err) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
+    const int nkb = (K + TC_KB - 1) / TC_KB, Np = (N + 15) / 16 * 16, ncols = tc_cols(Np);
+    unsigned char* sA = base;
+    unsigned char* sW = base + (size_t)nkb * TC_M * 128;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sW + (size_t)nkb * Np * 128);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M;
+    tc_stage(sA, A, lda, m0, TC_M, M, K, nkb);
+    tc_stage(sW, W, ldw, 0, Np, N, K, nkb);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(ncols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the staged operands and the barrier become visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        const uint32_t idesc = tc_idesc(Np);
+        for (int s = 0; s < 4 * nkb; ++s) {
+            const int kb = s >> 2, kk = s & 3;
+            const uint64_t ad = tc_desc(smem_u32(sA) + (uint32_t)(kb * TC_M * 128 + kk * 32));
+            const uint64_t bd = tc_desc(smem_u32(sW) + (uint32_t)(kb * Np * 128 + kk * 32));
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(s > 0 ? 1 : 0) : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_u32(bar)) : "memory");
+    }
+    // bounded wait for the products (phase 0 of the barrier)
+    uint32_t done = 0;
+    for (long long it = 0; it < (1ll << 24) && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done) : "r"(smem_u32(bar)) : "memory");
+        if (!done && (it & 255) == 255) __nanosleep(64);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int m = m0 + 32 * warp + lane;
+    for (int c0 = 0; c0 < Np; c0 += 16) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m < M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = c0 + j;
+                if (n < N) C[(long long)m * ldc + n] = done ? __uint_as_float(r[j]) + (bias ? bias[n] : 0.f) : nanf("");
+            }
+        }
+    }
+    if (!done && tid == 0 && err) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(ncols) : "memory");
+}
+
+static bool g_tc_ready = false;
+
 cudaError_t sg_gemm(int M, int N, int K, const float* A, long long sam, long long sak, const float* B, long long sbk,
                     long long sbn, const float* bias, float* C, int ldc, cudaStream_t st) {
     if (M <= 0 || N <= 0) return cudaSuccess;
+    if (sak == 1 && sbk == 1 && K >= 1 && K <= 256 && N <= 256 && sam < (1ll << 30) && sbn < (1ll << 30)) {
+        // A row-major, W = B^T row-major: the forward products (tensor cores, tcgen05)
+        if (!g_tc_ready) {
+            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)tc_smem_bytes(256, 256));
+            if (e != cudaSuccess) return e;
+            g_tc_ready = true;
+        }
+        k_gemm_tc<<<(M + TC_M - 1) / TC_M, 128, tc_smem_bytes(K, N), st>>>(M, N, K, A, (int)sam, B, (int)sbn, bias, C,
+                                                                         ldc, nullptr);
+        return cudaGetLastError();
+    }
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
     k_gemm_bf16<<<grid, 128, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, C, ldc);
     return cudaGetLastError();

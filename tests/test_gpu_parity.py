@@ -199,7 +199,12 @@ def _replay(cfg, S0, stages, site, acc, sweep_index):
     return starts, S
 
 
-def _check_sweep_against_oracle(cfg, sweeps, sample=None, seed_spins=None, start=None, launch=None):
+def _check_sweep_against_oracle(cfg, sweeps, sample=None, seed_spins=None, start=None, launch=None, near=0):
+    """Sweeps of cfg against the oracle: every spin by replaying the recorded
+    decisions, and the free energies, ln u and decisions of every visit (or
+    of `sample` random visits plus the `near` visits closest to the
+    Metropolis threshold, which PTCA_MIXED re-solves) against the oracle's
+    own solves of the same windows."""
     ctx = P.Context(cfg)
     if launch is not None:
         P.ptca_set_launch_config(ctx.h, *launch)
@@ -226,6 +231,9 @@ def _check_sweep_against_oracle(cfg, sweeps, sample=None, seed_spins=None, start
         for k, st in enumerate(stages):
             stage_of[st] = k
         idx = np.arange(cfg.N) if sample is None else inputs.rng(sw).choice(cfg.N, size=sample, replace=False)
+        if near:
+            gpu_margin = np.abs(lnu + (Fn - Fo) / cfg.T)
+            idx = np.union1d(idx, np.argsort(gpu_margin)[:near])
         for k in idx:
             s = int(site[k])
             Sst = starts[stage_of[s]]
@@ -305,7 +313,7 @@ def test_full_size_100x100_sampled(prec, schedule, stride):
     # The benchmark workload: 100x100 torus, 8x8 clusters, cone proposals.
     cfg = P.Config(Lx=100, Ly=100, L_c=8, schedule=schedule, stride=stride, proposal=P.PROPOSAL_CONE,
                    cone_deg=30.0, T=0.05, mu=-6.5, seed=0, precision=prec)
-    _check_sweep_against_oracle(cfg, sweeps=1, sample=6)
+    _check_sweep_against_oracle(cfg, sweeps=1, sample=16, near=8)
 
 
 def test_full_size_100x100_sampled_in_the_benchmarked_launch_configuration():
@@ -315,7 +323,7 @@ def test_full_size_100x100_sampled_in_the_benchmarked_launch_configuration():
     # so the second starts while the first's last re-solve has just finished.
     cfg = P.Config(Lx=100, Ly=100, L_c=8, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, cone_deg=30.0,
                    T=0.05, mu=-6.5, seed=0, precision=P.MIXED)
-    _check_sweep_against_oracle(cfg, sweeps=2, sample=4, launch=(P.PIPELINE_OVERLAP, 4, 0))
+    _check_sweep_against_oracle(cfg, sweeps=2, sample=12, launch=(P.PIPELINE_OVERLAP, 4, 0), near=6)
 
 
 def test_observables_ferro_and_neel():

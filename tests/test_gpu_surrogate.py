@@ -49,12 +49,16 @@ def _params(ctx):
     return theta.cpu().numpy().astype(np.float64), scale
 
 
-def test_forward_matches_bf16_reference():
+@pytest.mark.parametrize("n", [96, 700])
+def test_forward_matches_bf16_reference(n):
+    # 2n network rows: one or several 128-row tiles of the tensor-core
+    # forward products, the last one ragged; K = 160 (zero-padded to three
+    # 64-wide blocks) and 256; output widths 256 and 8.
     ctx = P.Context(P.Config(Lx=16, Ly=16, L_c=8))
     P.ptca_surrogate_init(ctx.h, 11)
-    feat, center, _ = _rand_samples(3, 96)
-    out = torch.empty(96, dtype=torch.float32, device="cuda")
-    P.ptca_surrogate_predict(ctx.h, torch.from_numpy(feat).cuda(), torch.from_numpy(center).cuda(), 96, out)
+    feat, center, _ = _rand_samples(3, n)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    P.ptca_surrogate_predict(ctx.h, torch.from_numpy(feat).cuda(), torch.from_numpy(center).cuda(), n, out)
     got = out.cpu().numpy().astype(np.float64)
     theta, scale = _params(ctx)
     ref = SR.surrogate_dF(theta, feat.astype(np.float64), center, scale)
