@@ -102,21 +102,23 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const fl
 // The forward products of the network on the 5th-generation tensor cores:
 // C[M x N] = A W^T (+ bias) for A row-major (M x K, leading dimension lda)
 // and W row-major (N x K, leading dimension ldw), both FP32 in global memory,
-// N <= 256, K <= 256.  One CTA of 4 warps per 128 rows of A:
-//   * the CTA rounds its rows of A and all of W to bfloat16 (round to nearest
+// K <= 256.  CTA (i, j) of 8 warps computes rows 128 i .. 128 i + 127 and
+// columns TC_NT j .. TC_NT j + TC_NT - 1:
+//   * its warps round those rows of A and of W to bfloat16 (round to nearest
 //     even, as k_gemm_bf16) into shared memory in the K-major, 128-byte
 //     swizzled layout of the tensor cores: 64 K-elements (128 bytes) per row
 //     and K block, 8-row atoms of 1024 bytes, the 16-byte chunk c of row r at
 //     chunk position c ^ (r mod 8);
 //   * one thread issues tcgen05.mma (kind::f16: BF16 x BF16 -> FP32 in
-//     tensor memory; M = 128, N = N rounded up to 16, K = 16 per instruction)
-//     and commits them to an mbarrier;
-//   * each warp reads its 32 accumulator rows (tensor-memory lanes 32w ..
-//     32w + 31) with tcgen05.ld and writes C with the bias.
+//     tensor memory; M = 128, N = the tile's width rounded up to 16, K = 16
+//     per instruction) and commits them to an mbarrier;
+//   * warps w and w + 4 read accumulator rows 32 (w mod 4) .. + 31 (the
+//     tensor-memory lanes warp w may access), each half of the columns, with
+//     tcgen05.ld, and write C with the bias.
 // The wait on the mbarrier is bounded: past the limit the CTA writes NaN
-// into its rows of C, sets *err (if given) and still frees its tensor memory.
+// into its block of C, sets *err (if given) and still frees its tensor memory.
 // ---------------------------------------------------------------------------
-constexpr int TC_M = 128, TC_KB = 64;
+constexpr int TC_M = 128, TC_KB = 64, TC_NT = 64, TC_THREADS = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -137,8 +139,11 @@ __host__ __device__ constexpr uint32_t tc_idesc(int n) {
 
 __host__ __device__ constexpr int tc_cols(int np) { return np <= 32 ? 32 : np <= 64 ? 64 : np <= 128 ? 128 : 256; }
 
+// Width of the N tile (the whole of a narrow N), rounded up to 16.
+__host__ __device__ constexpr int tc_ntile(int N) { return N < TC_NT ? (N + 15) / 16 * 16 : TC_NT; }
+
 __host__ __device__ constexpr size_t tc_smem_bytes(int K, int N) {
-    return (size_t)((K + TC_KB - 1) / TC_KB) * (TC_M + (N + 15) / 16 * 16) * 128 + 1024 + 64;
+    return (size_t)((K + TC_KB - 1) / TC_KB) * (TC_M + tc_ntile(N)) * 128 + 1024 + 64;
 }
 
 // Rows [r0, r0 + rows) of X (row-major, leading dimension ld; rows >= nrows
@@ -166,21 +171,21 @@ __device__ __forceinline__ void tc_stage(unsigned char* dst, const float* __rest
     }
 }
 
-__global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const float* __restrict__ A, int lda,
-                                                   const float* __restrict__ W, int ldw,
-                                                   const float* __restrict__ bias, float* __restrict__ C, int ldc,
-                                                   int* err) {
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                       const float* __restrict__ W, int ldw,
+                                                       const float* __restrict__ bias, float* __restrict__ C, int ldc,
+                                                       int* err) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
-    const int nkb = (K + TC_KB - 1) / TC_KB, Np = (N + 15) / 16 * 16, ncols = tc_cols(Np);
+    const int nkb = (K + TC_KB - 1) / TC_KB, Np = tc_ntile(N), ncols = tc_cols(Np);
     unsigned char* sA = base;
     unsigned char* sW = base + (size_t)nkb * TC_M * 128;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sW + (size_t)nkb * Np * 128);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * TC_M;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * Np;
     tc_stage(sA, A, lda, m0, TC_M, M, K, nkb);
-    tc_stage(sW, W, ldw, 0, Np, N, K, nkb);
+    tc_stage(sW, W + (long long)n0 * ldw, ldw, 0, Np, N - n0, K, nkb);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tslot)), "r"(ncols) : "memory");
@@ -219,20 +224,19 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const f
         if (!done && (it & 255) == 255) __nanosleep(64);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int m = m0 + 32 * warp + lane;
-    for (int c0 = 0; c0 < Np; c0 += 16) {
-        uint32_t r[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0));
+    const int quad = warp & 3, half = warp >> 2;
+    const int m = m0 + 32 * quad + lane;
+    const int cw = Np / 2;  // columns per warp of the pair (a multiple of 8)
+    for (int c0 = half * cw; c0 < half * cw + cw; c0 += 8) {
+        uint32_t r[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (m < M) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int n = c0 + j;
+            for (int j = 0; j < 8; ++j) {
+                const int n = n0 + c0 + j;
                 if (n < N) C[(long long)m * ldc + n] = done ? __uint_as_float(r[j]) + (bias ? bias[n] : 0.f) : nanf("");
             }
         }
@@ -257,8 +261,9 @@ cudaError_t sg_gemm(int M, int N, int K, const float* A, long long sam, long lon
             if (e != cudaSuccess) return e;
             g_tc_ready = true;
         }
-        k_gemm_tc<<<(M + TC_M - 1) / TC_M, 128, tc_smem_bytes(K, N), st>>>(M, N, K, A, (int)sam, B, (int)sbn, bias, C,
-                                                                         ldc, nullptr);
+        const dim3 grid((M + TC_M - 1) / TC_M, (N + tc_ntile(N) - 1) / tc_ntile(N));
+        k_gemm_tc<<<grid, TC_THREADS, tc_smem_bytes(K, N), st>>>(M, N, K, A, (int)sam, B, (int)sbn, bias, C, ldc,
+                                                                nullptr);
         return cudaGetLastError();
     }
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);

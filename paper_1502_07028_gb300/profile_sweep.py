@@ -40,6 +40,8 @@ def parser() -> argparse.ArgumentParser:
     ap.add_argument("--U", type=float, default=8.0, help="Hubbard U (model hubbard)")
     ap.add_argument("--m-step", type=float, default=0.5, help="field proposal radius (model hubbard)")
     ap.add_argument("--sphere", action="store_true", help="proposals uniform on the sphere (default: 30-degree cone)")
+    ap.add_argument("--full-spectrum", action="store_true",
+                    help="instead of sweeps, one call of ptca_full_spectrum on the lattice's initial configuration")
     ap.add_argument("--surrogate", type=int, default=0,
                     help="delayed-acceptance screening: train the network on this many exact sweeps first (0: off)")
     return ap
@@ -71,6 +73,17 @@ def main(argv=None):
                                      "graph": P.PIPELINE_GRAPH, "overlap": P.PIPELINE_OVERLAP}[a.pipeline], a.warps, a.ctas_per_sm)
     if a.margin is not None and cfg.precision == P.MIXED:
         P.ptca_set_resolve_margin(ctx.h, a.margin)
+    if a.full_spectrum:
+        import torch
+        eig = torch.empty(2 * cfg.N, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = __import__("time").perf_counter()
+        P.ptca_full_spectrum(ctx.h, eig)
+        dt = __import__("time").perf_counter() - t0
+        print(f"full spectrum of order {2 * cfg.N}: {dt * 1e3:.1f} ms, eigenvalues {float(eig[0]):.6f} .. "
+              f"{float(eig[-1]):.6f}")
+        ctx.close()
+        return
     if a.surrogate > 0:
         import torch
         n = a.surrogate * cfg.N
