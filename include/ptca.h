@@ -238,7 +238,10 @@ ptca_status ptca_free_energy(ptca_ctx* ctx, const double* eig, const int64_t* ei
  * form, computes their eigenvalues and free energies, and accepts iff
  * ln u < -(F_new - F_old)/T; accepted spins become visible to the next stage.
  * Asynchronous when stats_out == NULL; otherwise synchronises `stream` and
- * fills *stats_out. */
+ * fills *stats_out.  In PTCA_PIPELINE_OVERLAP a call without statistics
+ * leaves its last stage's re-solve running on the context's side stream for
+ * the next call to overlap (see ptca_flush); the library's own calls see a
+ * complete configuration. */
 ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_out, void* stream);
 
 /* How ptca_sweep launches the stages of a sweep (the paper's MPI gather and
@@ -363,6 +366,16 @@ ptca_status ptca_checker_read(ptca_ctx* ctx, double* out, int32_t n_rows, void* 
 /* Per-visit record of the last sweep, in flattened stage order (length N):
  * update site, F_old, F_new, ln u and the decision (1 accepted).  Device
  * pointers; any of them may be NULL.  Stream-ordered. */
+/* Completes, stream-ordered on `stream`, what the last ptca_sweep call left
+ * running beside the caller's stream: in PTCA_PIPELINE_OVERLAP a call
+ * without statistics leaves its last stage's re-solve to the next call, which
+ * runs it beside its own first stage (as a multi-sweep call does between its
+ * sweeps).  Every other call that reads or changes the configuration, the
+ * records, the counters or the launch configuration does this itself; a
+ * caller that times sweeps with its own events calls this before the last
+ * event.  No-op when nothing is pending. */
+ptca_status ptca_flush(ptca_ctx* ctx, void* stream);
+
 ptca_status ptca_sweep_record(ptca_ctx* ctx, int32_t* site, double* F_old, double* F_new,
                               double* lnu, uint8_t* accepted, void* stream);
 

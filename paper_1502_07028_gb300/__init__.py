@@ -8,7 +8,7 @@ from .ptca import (
     PIPELINE_PERSISTENT, PIPELINE_STAGES, PROPOSAL_CONE, PROPOSAL_SPHERE, SCHEDULE_BLOCK, SCHEDULE_TILED,
     Config, Context, KernelTimes, LaunchConfig, PtcaError, lib, library_path,
     ptca_autotune, ptca_build_clusters, ptca_checker_read, ptca_cluster_eigvals, ptca_destroy, ptca_dims,
-    ptca_free_energy, ptca_full_spectrum, ptca_get_launch_config, ptca_get_sites, ptca_get_spins, ptca_init,
+    ptca_flush, ptca_free_energy, ptca_full_spectrum, ptca_get_launch_config, ptca_get_sites, ptca_get_spins, ptca_init,
     ptca_kernel_times,
     ptca_last_error, ptca_observables, ptca_schedule, ptca_selftest_barrier_timeout, ptca_set_checker,
     ptca_set_kernel_timing, ptca_set_launch_config, ptca_set_mu, ptca_set_pipeline, ptca_set_resolve_margin,

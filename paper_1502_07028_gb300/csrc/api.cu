@@ -33,6 +33,11 @@ ptca_status cuda_fail(cudaError_t e, const char* where) {
         cudaError_t _e = (call);                                     \
         if (_e != cudaSuccess) return cuda_fail(_e, #call);          \
     } while (0)
+// Complete a re-solve an overlapped sweep left pending before touching the
+// configuration (stream-ordered on st), or before changing how the next sweep
+// runs (synchronously).
+#define PTCA_SETTLE(ctx, st) PTCA_CUDA(ptca_internal_settle((ctx), (st), true))
+#define PTCA_SETTLE_SYNC(ctx) PTCA_CUDA(ptca_internal_settle((ctx), nullptr, false))
 
 
 
@@ -495,6 +500,7 @@ ptca_status ptca_destroy(ptca_ctx* ctx) {
 ptca_status ptca_set_T(ptca_ctx* ctx, double T) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
     if (!(T > 0) || !std::isfinite(T)) return fail(PTCA_ERR_INVALID, "T must be finite and > 0");
+    PTCA_SETTLE_SYNC(ctx);
     ctx->p.T = T;
     drop_graph(ctx);
     return PTCA_OK;
@@ -503,6 +509,7 @@ ptca_status ptca_set_T(ptca_ctx* ctx, double T) {
 ptca_status ptca_set_mu(ptca_ctx* ctx, double mu) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
     if (!std::isfinite(mu)) return fail(PTCA_ERR_INVALID, "mu must be finite");
+    PTCA_SETTLE_SYNC(ctx);
     ctx->p.mu = mu;
     drop_graph(ctx);
     return PTCA_OK;
@@ -511,6 +518,7 @@ ptca_status ptca_set_mu(ptca_ctx* ctx, double mu) {
 ptca_status ptca_get_spins(ptca_ctx* ctx, double* dst, int on_device, void* stream) {
     if (!ctx || !dst) return fail(PTCA_ERR_INVALID, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_SETTLE(ctx, st);
     const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
     PTCA_CUDA(cudaMemcpyAsync(dst, ctx->d_S[0], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     if (!on_device) PTCA_CUDA(cudaStreamSynchronize(st));
@@ -520,6 +528,7 @@ ptca_status ptca_get_spins(ptca_ctx* ctx, double* dst, int on_device, void* stre
 ptca_status ptca_set_spins(ptca_ctx* ctx, const double* src, int on_device, void* stream) {
     if (!ctx || !src) return fail(PTCA_ERR_INVALID, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_SETTLE(ctx, st);
     const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
     PTCA_CUDA(cudaMemcpyAsync(ctx->d_S[0], src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     PTCA_CUDA(cudaMemcpyAsync(ctx->d_S[1], ctx->d_S[0], bytes, cudaMemcpyDeviceToDevice, st));
@@ -541,6 +550,7 @@ ptca_status ptca_build_clusters(ptca_ctx* ctx, const int32_t* sites, int32_t m, 
     if (m == 0) return PTCA_OK;
     if (!sites || !H_out || !offsets_out || !n_out) return fail(PTCA_ERR_INVALID, "null buffer");
     const int64_t stride = (int64_t)ctx->nA * (ctx->nA + 1) / 2;
+    PTCA_SETTLE(ctx, static_cast<cudaStream_t>(stream));
     PTCA_CUDA(ptca::launch_build(ctx->prec, to_model(ctx->p), ctx->d_S[0], sites, m, new_spins, H_out, stride,
                                  offsets_out, n_out, static_cast<cudaStream_t>(stream)));
     return PTCA_OK;
@@ -713,7 +723,24 @@ static cudaError_t ensure_overlap(ptca_ctx* ctx) {
     return e;
 }
 
-// Overlapped per-stage pipeline.  Stage g (counted over the call) reads
+// StageArgs of stage gg of the overlapped pipeline's rotation (counted from
+// the last time the configuration was in buffers 0 and 1): buffer gg mod 3
+// in, gg+1 mod 3 out, the per-visit scratch half gg mod 2, the random stream
+// of sweep `sweep`.
+static StageArgs overlap_args(ptca_ctx* ctx, int64_t gg, uint64_t sweep) {
+    const int s = (int)(gg % ctx->nstages);
+    StageArgs a = base_args(ctx);
+    use_half(ctx, a, (int)(gg & 1));
+    a.sweep = sweep;
+    a.S_in = ctx->d_S[gg % 3];
+    a.S_out = ctx->d_S[(gg + 1) % 3];
+    a.sites = ctx->d_sites + ctx->h_start[s];
+    a.rec_base = ctx->h_start[s];
+    if (ctx->sg.enabled) a.sg_dFt = ctx->sg.dFt + (size_t)(gg & 1) * ctx->max_stage;
+    return a;
+}
+
+// Overlapped per-stage pipeline.  Stage g (counted over the rotation) reads
 // buffer g mod 3 and writes buffer g+1 mod 3, so the re-solve of stage g-1
 // keeps reading its own start configuration while stage g writes.  On the
 // caller's stream: the visits of stage g whose windows hold no site of stage
@@ -725,7 +752,14 @@ static cudaError_t ensure_overlap(ptca_ctx* ctx) {
 // share a slot.  Every visit reads the spins it reads in the one-stream
 // pipeline and decides with the same arithmetic: the chain is the same, bit
 // for bit.
-static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
+//
+// With `defer`, the call ends without the last stage's re-solve: the next
+// call continues the rotation and runs it beside its own first stage's
+// independent visits (stage 0 of a sweep does not depend on the sweep's
+// last stage's sites for those), as a multi-sweep call does between its
+// sweeps.  Until then the configuration is in buffer (rotation) mod 3, not
+// in buffers 0 and 1; every other entry point settles it first.
+static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st, bool defer) {
     cudaError_t e = ensure_overlap(ctx);
     if (e != cudaSuccess) return e;
     const bool screen = ctx->sg.enabled;
@@ -733,11 +767,22 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
     const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
     const int ns = ctx->nstages;
     const int64_t G = (int64_t)n_sweeps * ns;
-    // buffers 0 and 1 agree between calls; buffer 2 starts from them too
-    e = cudaMemcpyAsync(ctx->d_S[2], ctx->d_S[0], bytes, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ctx->ev_fork, 0);
+    const bool cont = ctx->ov_pending;
+    const int64_t g0 = cont ? ctx->ov_g : 0;
+    ctx->ov_pending = false;
     StageArgs prev = base_args(ctx);  // the stage whose re-solve is pending
+    bool have_prev = false;
+    if (cont) {
+        // after the previous call's work on its stream (which may differ)
+        e = cudaStreamWaitEvent(st, ctx->ev_fork, 0);
+        prev = overlap_args(ctx, g0 - 1, (uint64_t)(ctx->sweeps - 1));
+        have_prev = true;
+    } else {
+        // buffers 0 and 1 agree between calls; buffer 2 starts from them too
+        e = cudaMemcpyAsync(ctx->d_S[2], ctx->d_S[0], bytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ctx->ev_fork, 0);
+    }
     auto resolve_prev = [&]() {
         cudaError_t r = cudaStreamWaitEvent(hs, ctx->ev_indep, 0);
         if (r == cudaSuccess)
@@ -751,17 +796,12 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         count = ctx->h_start[q + 1] - ctx->h_start[q];
     };
     for (int64_t g = 0; g < G && e == cudaSuccess; ++g) {
-        const int s = (int)(g % ns);
-        StageArgs a = base_args(ctx);
-        use_half(ctx, a, (int)(g & 1));
-        a.sweep = (uint64_t)(ctx->sweeps + g / ns);
-        a.S_in = ctx->d_S[g % 3];
-        a.S_out = ctx->d_S[(g + 1) % 3];
-        a.sites = ctx->d_sites + ctx->h_start[s];
-        a.rec_base = ctx->h_start[s];
+        const int64_t gg = g0 + g;
+        const int s = (int)(gg % ns);
+        StageArgs a = overlap_args(ctx, gg, (uint64_t)(ctx->sweeps + g / ns));
         const int cnt = ctx->h_start[s + 1] - ctx->h_start[s], ni = ctx->h_indep[s];
-        if (g > 0) e = resolve_prev();
-        if (e == cudaSuccess && g > 0) e = cudaStreamWaitEvent(st, ctx->ev_dep, 0);
+        if (have_prev) e = resolve_prev();
+        if (e == cudaSuccess && have_prev) e = cudaStreamWaitEvent(st, ctx->ev_dep, 0);
         StageArgs ai = a;
         ai.perm = ctx->d_split + ctx->h_start[s];
         ai.count = ni;
@@ -769,8 +809,7 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         // stream just before its exact solves (network rows of the
         // independent part first, the dependent part's after them; dF~ in
         // the half of this stage's parity, which its re-solve reads later).
-        if (screen && e == cudaSuccess && ni > 0) e = ptca_screen_part(ctx, ai, 0, 0, (int)(g & 1), st);
-        if (screen) a.sg_dFt = ctx->sg.dFt + (size_t)(g & 1) * ctx->max_stage;
+        if (screen && e == cudaSuccess && ni > 0) e = ptca_screen_part(ctx, ai, 0, 0, (int)(gg & 1), st);
         if (e == cudaSuccess && ni > 0)
             e = timed_launch(ctx, 0, 2 * (int64_t)ni, st,
                              [&] { return launch_stage_ctx(ctx, ai, st); });
@@ -782,12 +821,12 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
             const size_t es = ctx->prec == 1 ? sizeof(float2) : sizeof(double2);
             ad.gL = static_cast<char*>(ctx->d_gL) + (size_t)ctx->large_grid * (size_t)ctx->gL_stride * es;
         }
-        // sites buffer g+1 mod 3 lacks: those of stages g-2 and g-1 (each
-        // only if it is not stage g itself, whose visits write every site)
-        if (g >= 1 && (g - 1) % ns != s) stage_sites(g - 1, ad.prev_sites, ad.prev_count);
-        if (g >= 2 && (g - 2) % ns != s && (g - 2) % ns != (g - 1) % ns)
-            stage_sites(g - 2, ad.prev2_sites, ad.prev2_count);
-        if (screen && e == cudaSuccess && ad.count > 0) e = ptca_screen_part(ctx, ad, 1, 2 * ni, (int)(g & 1), hs);
+        // sites buffer gg+1 mod 3 lacks: those of stages gg-2 and gg-1 (each
+        // only if it is not stage gg itself, whose visits write every site)
+        if (gg >= 1 && (gg - 1) % ns != s) stage_sites(gg - 1, ad.prev_sites, ad.prev_count);
+        if (gg >= 2 && (gg - 2) % ns != s && (gg - 2) % ns != (gg - 1) % ns)
+            stage_sites(gg - 2, ad.prev2_sites, ad.prev2_count);
+        if (screen && e == cudaSuccess && ad.count > 0) e = ptca_screen_part(ctx, ad, 1, 2 * ni, (int)(gg & 1), hs);
         if (e == cudaSuccess) {
             if (ad.count > 0) {
                 e = timed_launch(ctx, 2, 2 * (int64_t)ad.count, hs,
@@ -799,18 +838,45 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         }
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_dep, hs);
         prev = a;
+        have_prev = true;
     }
-    if (e == cudaSuccess && G > 0) e = resolve_prev();
+    if (e == cudaSuccess && defer && G > 0) {
+        ctx->ov_pending = true;
+        ctx->ov_g = g0 + G;
+        e = cudaEventRecord(ctx->ev_fork, st);  // the next call's stream starts after this one's
+        if (e == cudaSuccess)
+            e = ptca::launch_set_u64(ctx->d_sweep_ctr, (unsigned long long)(ctx->sweeps + n_sweeps), st);
+        return e;
+    }
+    if (e == cudaSuccess && have_prev) e = resolve_prev();
     // join the side stream back into the caller's stream, also after a failure
     cudaError_t ej = cudaEventRecord(ctx->ev_join, hs);
     if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, ctx->ev_join, 0);
     if (e == cudaSuccess) e = ej;
-    // the configuration after the call is buffer G mod 3; buffers 0 and 1 take it
-    const int f = (int)(G % 3);
+    // the configuration after the call is in buffer (g0 + G) mod 3; buffers 0 and 1 take it
+    const int f = (int)((g0 + G) % 3);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
         if (b != f) e = cudaMemcpyAsync(ctx->d_S[b], ctx->d_S[f], bytes, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = ptca::launch_set_u64(ctx->d_sweep_ctr, (unsigned long long)(ctx->sweeps + n_sweeps), st);
     return e;
+}
+
+cudaError_t ptca_internal_settle(ptca_ctx* ctx, cudaStream_t st, bool have_stream) {
+    if (!ctx->ov_pending) return cudaSuccess;
+    ctx->ov_pending = false;
+    cudaStream_t hs = ctx->side;
+    const int64_t g = ctx->ov_g;
+    StageArgs prev = overlap_args(ctx, g - 1, (uint64_t)(ctx->sweeps - 1));
+    cudaError_t e = cudaStreamWaitEvent(hs, ctx->ev_indep, 0);
+    if (e == cudaSuccess) e = timed_launch(ctx, 1, 0, hs, [&] { return launch_resolve_ctx(ctx, prev, hs); });
+    if (e == cudaSuccess) e = cudaMemsetAsync(prev.flag_count, 0, sizeof(unsigned int), hs);
+    const int f = (int)(g % 3);
+    const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        if (b != f) e = cudaMemcpyAsync(ctx->d_S[b], ctx->d_S[f], bytes, cudaMemcpyDeviceToDevice, hs);
+    cudaError_t ej = cudaEventRecord(ctx->ev_join, hs);
+    if (ej == cudaSuccess) ej = have_stream ? cudaStreamWaitEvent(st, ctx->ev_join, 0) : cudaStreamSynchronize(hs);
+    return e == cudaSuccess ? ej : e;
 }
 
 // Everything one persistent sweep launch needs, as stream work (capturable).
@@ -864,10 +930,13 @@ static cudaError_t sweep_graph(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st)
 
 // Stream work of n_sweeps sweeps in the context's launch configuration
 // (screening and the checker need the per-stage pipeline).
-static cudaError_t run_sweeps(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st) {
+static bool overlapped(const ptca_ctx* ctx) {
+    return ctx->pipeline == PTCA_PIPELINE_OVERLAP && ctx->prec == 1 && ctx->margin > 0.0 && !ctx->checker;
+}
+
+static cudaError_t run_sweeps(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st, bool defer = false) {
     const bool per_stage = ctx->pipeline == PTCA_PIPELINE_STAGES || ctx->pipeline == PTCA_PIPELINE_OVERLAP;
-    if (ctx->pipeline == PTCA_PIPELINE_OVERLAP && ctx->prec == 1 && ctx->margin > 0.0 && !ctx->checker)
-        return sweep_overlap(ctx, n_sweeps, st);
+    if (overlapped(ctx)) return sweep_overlap(ctx, n_sweeps, st, defer);
     if (per_stage || ctx->sg.enabled || ctx->checker) return sweep_stages(ctx, n_sweeps, st);
     if (ctx->pipeline == PTCA_PIPELINE_PERSISTENT || ctx->graph_failed) return enqueue_persistent(ctx, n_sweeps, st);
     return sweep_graph(ctx, n_sweeps, st);
@@ -880,6 +949,7 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
     if (persistent && ctx->grid <= 0)
         return fail(PTCA_ERR_UNSUPPORTED, "persistent kernel does not fit on this device");
     if (!(barrier_timeout_s > 0) || barrier_timeout_s > 3600) return fail(PTCA_ERR_INVALID, "timeout out of range");
+    PTCA_SETTLE_SYNC(ctx);
     if (mode == PTCA_PIPELINE_OVERLAP) {
         cudaError_t e = ensure_overlap(ctx);
         if (e != cudaSuccess) return cuda_fail(e, "ptca_set_pipeline (overlapped pipeline)");
@@ -899,6 +969,7 @@ ptca_status ptca_set_kernel_timing(ptca_ctx* ctx, int32_t on) {
 
 ptca_status ptca_kernel_times(ptca_ctx* ctx, double* out, void* stream) {
     if (!ctx || !out) return fail(PTCA_ERR_INVALID, "null argument");
+    PTCA_SETTLE(ctx, static_cast<cudaStream_t>(stream));
     PTCA_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     for (int q = 0; q < 8; ++q) out[q] = 0.0;
     for (size_t i = 0; i < ctx->tkind.size(); ++i) {
@@ -929,6 +1000,7 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     if (!ctx || !cfg) return fail(PTCA_ERR_INVALID, "null argument");
     if (cfg->pipeline < PTCA_PIPELINE_STAGES || cfg->pipeline > PTCA_PIPELINE_OVERLAP)
         return fail(PTCA_ERR_INVALID, "unknown pipeline");
+    PTCA_SETTLE_SYNC(ctx);
     if (cfg->warps_per_cta != 8 && cfg->warps_per_cta != 4 && cfg->warps_per_cta != 1 && cfg->warps_per_cta != 16)
         return fail(PTCA_ERR_INVALID, "warps_per_cta must be 1, 4, 8 or 16");
     if (ctx->large && cfg->warps_per_cta != 8 && cfg->warps_per_cta != 16)
@@ -973,6 +1045,7 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
     if (trial_sweeps < 1 || trial_sweeps > 100) return fail(PTCA_ERR_INVALID, "trial_sweeps in [1, 100]");
     if (ctx->checker) return fail(PTCA_ERR_INVALID, "turn the precision checker off before autotuning");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_SETTLE(ctx, st);
     // Candidates: CTA width x pipeline x persistent CTAs per SM.
     std::vector<ptca_launch_config> cand;
     if (ctx->large) {
@@ -1072,6 +1145,7 @@ ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
     if (!(margin >= 0.0) || !std::isfinite(margin)) return fail(PTCA_ERR_INVALID, "margin must be finite and >= 0");
     if (ctx->prec != 1 && margin > 0.0) return fail(PTCA_ERR_INVALID, "the re-solve margin applies to PTCA_MIXED only");
+    PTCA_SETTLE_SYNC(ctx);
     ctx->margin = margin;
     drop_graph(ctx);
     return PTCA_OK;
@@ -1079,6 +1153,7 @@ ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin) {
 
 ptca_status ptca_set_checker(ptca_ctx* ctx, int32_t on) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    PTCA_SETTLE_SYNC(ctx);
     if (!on) {
         ctx->checker = false;
         return PTCA_OK;
@@ -1132,10 +1207,15 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
         PTCA_CUDA(cudaEventCreate(&ev1));
         PTCA_CUDA(cudaEventRecord(ev0, st));
     }
+    // An overlapped sweep without statistics may continue a re-solve the
+    // previous call left pending, and leave its own last one to the next
+    // call; anything else settles first and completes its sweeps.
+    const bool defer = overlapped(ctx) && !stats_out && n_sweeps > 0;
+    if (!defer) PTCA_CUDA(ptca_internal_settle(ctx, st, true));
     PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
     if (n_sweeps > 0) {
         cudaError_t e;
-        e = run_sweeps(ctx, n_sweeps, st);
+        e = run_sweeps(ctx, n_sweeps, st, defer);
         if (e != cudaSuccess) return cuda_fail(e, "ptca_sweep");
     }
     ctx->sweeps += n_sweeps;
@@ -1203,6 +1283,7 @@ ptca_status ptca_stage_run(ptca_ctx* ctx, int64_t sweep_index, const int32_t* si
     if (sweep_index < 0) return fail(PTCA_ERR_INVALID, "ptca_stage_run: sweep_index < 0");
     if (ctx->sg.enabled) return fail(PTCA_ERR_UNSUPPORTED, "ptca_stage_run: surrogate screening runs in ptca_sweep only");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_SETTLE(ctx, st);
     int stage = -1;
     ptca_status r = upload_sites(ctx, sites, count, &stage, st, "ptca_stage_run");
     if (r != PTCA_OK) return r;
@@ -1233,6 +1314,7 @@ ptca_status ptca_get_sites(ptca_ctx* ctx, const int32_t* sites, int32_t count, d
                            void* stream) {
     if (!ctx || (count > 0 && !out)) return fail(PTCA_ERR_INVALID, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_SETTLE(ctx, st);
     ptca_status r = upload_sites(ctx, sites, count, nullptr, st, "ptca_get_sites");
     if (r != PTCA_OK || count == 0) return r;
     double* dst = on_device ? out : ctx->d_sub_spins;
@@ -1248,6 +1330,7 @@ ptca_status ptca_set_sites(ptca_ctx* ctx, const int32_t* sites, int32_t count, c
                            void* stream) {
     if (!ctx || (count > 0 && !spins)) return fail(PTCA_ERR_INVALID, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_SETTLE(ctx, st);
     ptca_status r = upload_sites(ctx, sites, count, nullptr, st, "ptca_set_sites");
     if (r != PTCA_OK || count == 0) return r;
     const double* src = spins;
@@ -1266,6 +1349,7 @@ ptca_status ptca_surrogate_collect(ptca_ctx* ctx, int32_t n_sweeps, float* feat,
         return fail(PTCA_ERR_UNSUPPORTED, "the surrogate screen is built for the double-exchange model on square lattices");
     if (!ctx || n_sweeps < 0 || !feat || !center || !dF) return fail(PTCA_ERR_INVALID, "bad arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_SETTLE(ctx, st);
     PTCA_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), st));
     Collect col{feat, center, dF};
     cudaError_t e = sweep_stages(ctx, n_sweeps, st, &col);
@@ -1295,10 +1379,17 @@ ptca_status ptca_selftest_barrier_timeout(int32_t blocks, double timeout_s, void
     return PTCA_OK;
 }
 
+ptca_status ptca_flush(ptca_ctx* ctx, void* stream) {
+    if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
+    PTCA_SETTLE(ctx, static_cast<cudaStream_t>(stream));
+    return PTCA_OK;
+}
+
 ptca_status ptca_sweep_record(ptca_ctx* ctx, int32_t* site, double* F_old, double* F_new, double* lnu,
                               uint8_t* accepted, void* stream) {
     if (!ctx) return fail(PTCA_ERR_INVALID, "null context");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_SETTLE(ctx, st);
     const size_t N = ctx->N;
     if (site) PTCA_CUDA(cudaMemcpyAsync(site, ctx->d_rec_site, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     if (F_old) PTCA_CUDA(cudaMemcpyAsync(F_old, ctx->d_rec_Fold, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1311,6 +1402,7 @@ ptca_status ptca_sweep_record(ptca_ctx* ctx, int32_t* site, double* F_old, doubl
 ptca_status ptca_observables(ptca_ctx* ctx, ptca_obs* out, void* stream) {
     if (!ctx || !out) return fail(PTCA_ERR_INVALID, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PTCA_SETTLE(ctx, st);
     PTCA_CUDA(ptca::launch_observables(ctx->d_S[0], ctx->p.Lx, ctx->p.Ly, ctx->d_rec_Facc, ctx->d_rec_fill,
                                        ctx->d_rec_acc, ctx->d_rec_n, ctx->N, ctx->d_obs, st));
     double h[5];

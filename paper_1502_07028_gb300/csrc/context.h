@@ -122,6 +122,12 @@ struct ptca_ctx {
     // against the caller's stream
     int32_t* d_split = nullptr;
     std::vector<int32_t> h_indep;
+    // A ptca_sweep call in the overlapped pipeline may leave its last
+    // stage's re-solve to the next call (ov_pending): the rotation then
+    // continues at global stage ov_g, whose predecessor's re-solve is still
+    // to be enqueued on `side`; ptca_internal_settle completes it.
+    bool ov_pending = false;
+    int64_t ov_g = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_indep = nullptr, ev_dep = nullptr, ev_fork = nullptr, ev_join = nullptr;
     // optional per-kernel timing of the per-stage pipelines: event pairs
@@ -143,3 +149,7 @@ struct ptca_ctx {
 };
 
 void ptca_free_surrogate(ptca_ctx* c);
+// Completes a re-solve that an overlapped sweep left pending (see ov_pending)
+// and puts the configuration back into spin buffers 0 and 1: stream-ordered
+// on `st`, or, when have_stream is false, before returning.
+extern "C" cudaError_t ptca_internal_settle(ptca_ctx* ctx, cudaStream_t st, bool have_stream);

@@ -332,6 +332,8 @@ extern "C" ptca_status ptca_full_spectrum(ptca_ctx* ctx, double* eig_out, void* 
     if (N > 16384) return ptca_internal_fail(PTCA_ERR_INVALID, "ptca_full_spectrum covers lattices of up to 16384 sites");
     const int n = 2 * N;
     const int Tmax = (n - 1 + FS_TB - 1) / FS_TB;
+    cudaError_t es = ptca_internal_settle(ctx, static_cast<cudaStream_t>(stream), true);
+    if (es != cudaSuccess) return ptca_internal_fail(PTCA_ERR_CUDA, cudaGetErrorString(es));
     const int red_max = (n + FS_RED_THREADS - 1) / FS_RED_THREADS;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 

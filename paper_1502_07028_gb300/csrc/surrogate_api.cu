@@ -189,6 +189,7 @@ ptca_status ptca_surrogate_set_params(ptca_ctx* ctx, const float* theta, float s
 ptca_status ptca_surrogate_enable(ptca_ctx* ctx, int32_t on) {
     if (!ctx) return ptca_internal_fail(PTCA_ERR_INVALID, "null context");
     if (on && !ctx->sg.ready) return ptca_internal_fail(PTCA_ERR_INVALID, "surrogate not initialised");
+    SG_CUDA(ptca_internal_settle(ctx, nullptr, false));
     ctx->sg.enabled = on != 0;
     return PTCA_OK;
 }

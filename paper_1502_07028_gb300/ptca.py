@@ -34,7 +34,7 @@ EXPORTED = [
     "ptca_surrogate_collect", "ptca_surrogate_train", "ptca_surrogate_grad", "ptca_surrogate_predict",
     "ptca_surrogate_enable", "ptca_set_checker", "ptca_checker_read", "ptca_set_launch_config",
     "ptca_get_launch_config", "ptca_autotune", "ptca_set_kernel_timing", "ptca_kernel_times",
-    "ptca_stage_split", "ptca_full_spectrum", "ptca_stage_run", "ptca_get_sites", "ptca_set_sites",
+    "ptca_stage_split", "ptca_full_spectrum", "ptca_stage_run", "ptca_get_sites", "ptca_set_sites", "ptca_flush",
 ]
 
 
@@ -136,6 +136,7 @@ def lib():
             "ptca_surrogate_enable": ([vp, i32], i32),
             "ptca_selftest_barrier_timeout": ([i32, dbl, vp], i32),
             "ptca_stage_run": ([vp, i64, vp, i32, vp], i32),
+            "ptca_flush": ([vp, vp], i32),
             "ptca_get_sites": ([vp, vp, i32, vp, i32, vp], i32),
             "ptca_set_sites": ([vp, vp, i32, vp, i32, vp], i32),
         }
@@ -341,6 +342,11 @@ def ptca_sweep_noalloc(cfg: Config, spins, sweep_index: int, F_out=None, accepte
     lat, par = cfg.lattice(), cfg.params()
     _check(lib().ptca_sweep_noalloc(ctypes.byref(lat), ctypes.byref(par), _ptr(spins), sweep_index, _ptr(F_out),
                                     _ptr(accepted_out), _ptr(status_out), _stream(stream)))
+
+
+def ptca_flush(h, stream=None) -> None:
+    """Complete, stream-ordered, a re-solve the last overlapped sweep left running."""
+    _check(lib().ptca_flush(h, _stream(stream)))
 
 
 def ptca_stage_run(h, sweep_index: int, sites, stream=None) -> None:

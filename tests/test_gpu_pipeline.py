@@ -255,3 +255,47 @@ def test_one_warp_width_is_limited_to_order_32():
     with pytest.raises(P.PtcaError):
         P.ptca_set_launch_config(ctx.h, P.PIPELINE_STAGES, 1, 0)
     ctx.close()
+
+
+@pytest.mark.parametrize("margin", [None, 1e6])
+def test_calls_that_leave_the_last_resolve_pending_compute_the_same_chain(margin):
+    # Overlapped pipeline: a call without statistics leaves its last stage's
+    # re-solve for the next call.  Three such calls (the second on another
+    # stream) must give the chain of one three-sweep call, and every entry
+    # point that reads the configuration must see it complete.  margin 1e6:
+    # every decision is re-solved, so the pending work is a whole stage.
+    cfg = P.Config(Lx=32, Ly=32, L_c=8, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, T=0.05, seed=31,
+                   precision=P.MIXED)
+
+    def ctx_():
+        c = P.Context(cfg)
+        P.ptca_set_launch_config(c.h, P.PIPELINE_OVERLAP, 4, 0)
+        if margin is not None:
+            P.ptca_set_resolve_margin(c.h, margin)
+        return c
+
+    a, b = ctx_(), ctx_()
+    other = torch.cuda.Stream()
+    P.ptca_sweep(a.h, 1, stats=False)
+    P.ptca_sweep(a.h, 1, stats=False, stream=other)
+    P.ptca_sweep(a.h, 1, stats=False)
+    rec_a = [x.cpu().numpy() for x in a.record()]
+    S_a = a.spins().cpu().numpy()
+    st_b = b.sweep(3)
+    rec_b = [x.cpu().numpy() for x in b.record()]
+    assert np.array_equal(S_a, b.spins().cpu().numpy())
+    for x, y in zip(rec_a, rec_b):
+        assert np.array_equal(x, y)
+    if margin is not None:
+        assert st_b.resolved == 3 * cfg.N
+    # one more pending call each, then statistics, observables and a flush
+    P.ptca_sweep(a.h, 1, stats=False)
+    P.ptca_sweep(b.h, 1, stats=False)
+    P.ptca_flush(a.h)
+    oa, ob = a.observables(), b.observables()
+    assert (oa.S_pipi, oa.S_00, oa.F_site) == (ob.S_pipi, ob.S_00, ob.F_site)
+    sa, sb = a.sweep(1), b.sweep(1)
+    assert (sa.accepted, sa.resolved, sa.eigensolves) == (sb.accepted, sb.resolved, sb.eigensolves)
+    assert np.array_equal(a.spins().cpu().numpy(), b.spins().cpu().numpy())
+    a.close()
+    b.close()
