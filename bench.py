@@ -730,6 +730,7 @@ def main():
     per_stage = best.pipeline in (P.PIPELINE_STAGES, P.PIPELINE_OVERLAP)
     pipeline_desc = (f"{names[best.pipeline]}, {best.warps_per_cta}-warp CTA per matrix"
                      + (f", {best.ctas_per_sm} CTAs/SM" if not per_stage else "")
+                     + (", register-tiled Householder pass" if best.reduction == P.REDUCTION_TILED else "")
                      + " (autotuned)")
     def timed_region():
         barrier(world)
@@ -830,7 +831,8 @@ def main():
         # k_stage launches other than the overlapped pipeline's dependent
         # visits: 2 matrices per visit, per-launch durations from the
         # library's CUDA events on the stream each launch runs on.
-        kernel_name = f"k_stage<float,4,{best.warps_per_cta}>"
+        kernel_name = (f"k_stage<float,4,{best.warps_per_cta},tiled>" if best.reduction == P.REDUCTION_TILED
+                       else f"k_stage<float,4,{best.warps_per_cta}>")
         launch_ms = kt.stage_ms / kt.stage_launches
         matrices_per_launch = kt.stage_matrices / kt.stage_launches
         resolve_ms_per_step = kt.resolve_ms / args.steps
@@ -870,8 +872,9 @@ def main():
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "pipeline": pipeline_desc,
             "autotune": {"best": tune_table["best"],
-                         "candidates": [[c["pipeline"], c["warps_per_cta"], c["ctas_per_sm"], c["ms_per_sweep"]]
-                                        for c in tune_table["candidates"]]},
+                         "columns": ["pipeline", "warps_per_cta", "ctas_per_sm", "reduction", "ms_per_sweep"],
+                         "candidates": [[c["pipeline"], c["warps_per_cta"], c["ctas_per_sm"], c["reduction"],
+                                         c["ms_per_sweep"]] for c in tune_table["candidates"]]},
             "mixed_unguarded": {"value": unguarded_value, "unit": "spin-updates/s",
                                 "note": "same path without the double-float re-solve of decisions within 1e-2"},
             "resolved_fraction": resolved_frac,

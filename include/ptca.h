@@ -67,6 +67,7 @@ enum { PTCA_FP64 = 0, PTCA_MIXED = 1 };
 enum { PTCA_PROPOSAL_SPHERE = 0, PTCA_PROPOSAL_CONE = 1 };
 enum { PTCA_MODEL_DOUBLE_EXCHANGE = 0, PTCA_MODEL_HUBBARD_MF = 1, PTCA_MODEL_HOLSTEIN = 2 };
 enum { PTCA_PIPELINE_STAGES = 0, PTCA_PIPELINE_PERSISTENT = 1, PTCA_PIPELINE_GRAPH = 2, PTCA_PIPELINE_OVERLAP = 3 };
+enum { PTCA_REDUCTION_ROWS = 0, PTCA_REDUCTION_TILED = 1 };
 
 /* Square lattice, chain or cubic lattice.  Ly == 1 is a one-dimensional chain
  * (Sec. III.a, Fig. 3); Lz > 1 (with Ly > 1) a cubic lattice of Lx*Ly*Lz
@@ -284,13 +285,21 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  *                  distributed shared memory (every precision else: one
  *                  16-warp CTA, matrix in global memory); 16 runs the
  *                  16-warp, global-memory kernel;
- *   ctas_per_sm    CTAs per SM of the persistent kernel, 0 = as many as fit.
+ *   ctas_per_sm    CTAs per SM of the persistent kernel, 0 = as many as fit;
+ *   reduction      organisation of the FP32 Householder pass (Sec. II.c
+ *                  step b): PTCA_REDUCTION_ROWS = lanes on columns of the
+ *                  packed triangle, rows in batches (every width);
+ *                  PTCA_REDUCTION_TILED = register tiles, 4x4
+ *                  complex tiles per lane over pairs of block rows, the
+ *                  matrix stored as tiles (PTCA_MIXED, 4-warp CTAs, orders
+ *                  up to 128, per-stage and overlapped pipelines).
  * Every configuration computes the same chain (decisions and spins; free
  * energies to rounding). */
 typedef struct {
     int32_t pipeline;
     int32_t warps_per_cta;
     int32_t ctas_per_sm;
+    int32_t reduction;
 } ptca_launch_config;
 
 /* Apply a launch configuration.  PTCA_ERR_UNSUPPORTED for a width the
@@ -299,7 +308,7 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
 ptca_status ptca_get_launch_config(const ptca_ctx* ctx, ptca_launch_config* out);
 
 /* Autotuner: times every launch configuration the problem admits (CTA width
- * x pipeline x persistent CTAs per SM) on this context's own lattice -- one
+ * x pipeline x persistent CTAs per SM x reduction) on this context's own lattice -- one
  * warm-up sweep and trial_sweeps (1..100) timed sweeps each, CUDA events on
  * `stream` -- restoring the spins and the sweep counter before every trial
  * and at the end, so the chain is left where it was (the per-visit record

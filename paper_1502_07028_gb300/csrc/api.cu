@@ -616,6 +616,7 @@ static cudaError_t launch_stage_ctx(const ptca_ctx* ctx, const StageArgs& a, cud
     if (ctx->large && ctx->prec == 1 && ctx->nw == 8 && ctx->cl_size > 0)
         return ptca::launch_stage_cluster(ctx->cl_size, a, ctx->cl_grid, st);
     if (ctx->large) return ptca::launch_stage_large(ctx->prec, a, ctx->large_grid, st);
+    if (ctx->reduction == 1) return ptca::launch_stage_tiled(a, st);
     return ptca::launch_stage(ctx->prec, ctx->nw, a, st);
 }
 static cudaError_t launch_resolve_ctx(const ptca_ctx* ctx, const StageArgs& a, cudaStream_t st) {
@@ -993,6 +994,7 @@ ptca_status ptca_get_launch_config(const ptca_ctx* ctx, ptca_launch_config* out)
     out->pipeline = ctx->pipeline;
     out->warps_per_cta = ctx->nw;
     out->ctas_per_sm = ctx->ctas_per_sm;
+    out->reduction = ctx->reduction;
     return PTCA_OK;
 }
 
@@ -1017,6 +1019,12 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
         return fail(PTCA_ERR_INVALID, "ctas_per_sm must be in [0, the CTAs that fit on an SM]");
     const bool persistent = cfg->pipeline == PTCA_PIPELINE_PERSISTENT || cfg->pipeline == PTCA_PIPELINE_GRAPH;
     if (persistent && maxb <= 0) return fail(PTCA_ERR_UNSUPPORTED, "persistent kernel does not fit on this device");
+    if (cfg->reduction != 0 && cfg->reduction != 1) return fail(PTCA_ERR_INVALID, "reduction must be 0 or 1");
+    if (cfg->reduction == 1 &&
+        (ctx->large || cfg->warps_per_cta != 4 || persistent || !ptca::tiled_supported(ctx->prec, ctx->nA)))
+        return fail(PTCA_ERR_UNSUPPORTED,
+                    "the register-tiled reduction runs PTCA_MIXED stage kernels of 4-warp CTAs, orders up to 128, "
+                    "in the per-stage or overlapped pipeline");
     if (cfg->pipeline == PTCA_PIPELINE_OVERLAP) {
         cudaError_t e = ensure_overlap(ctx);
         if (e != cudaSuccess) return cuda_fail(e, "ptca_set_launch_config (overlapped pipeline)");
@@ -1024,6 +1032,7 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     ctx->pipeline = cfg->pipeline;
     ctx->nw = cfg->warps_per_cta;
     ctx->ctas_per_sm = cfg->ctas_per_sm;
+    ctx->reduction = cfg->reduction;
     ctx->grid = maxb > 0 ? ctx->sms * (cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : maxb) : 0;
     ctx->graph_failed = false;
     drop_graph(ctx);
@@ -1051,19 +1060,23 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
     if (ctx->large) {
         for (int nw : {16, 8}) {
             if (nw == 8 && ctx->cl_size == 0) continue;  // 8 would mean the global-slot kernel again
-            cand.push_back({PTCA_PIPELINE_STAGES, nw, 0});
-            if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0});
+            cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 0});
+            if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 0});
         }
     }
     for (int nw : {8, 4, 1}) {
         if (ctx->large || !ptca::sweep_width_supported(ctx->prec, nw, ctx->nA)) continue;
-        cand.push_back({PTCA_PIPELINE_STAGES, nw, 0});
-        if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0});
+        cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 0});
+        if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 0});
+        if (nw == 4 && ptca::tiled_supported(ctx->prec, ctx->nA)) {
+            cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 1});
+            if (ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 1});
+        }
         const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, nw, ctx->nA);
         if (maxb <= 0 || ctx->sg.enabled) continue;
         for (int pl : {PTCA_PIPELINE_PERSISTENT, PTCA_PIPELINE_GRAPH}) {
-            cand.push_back({pl, nw, maxb});
-            if (maxb > 1) cand.push_back({pl, nw, 1});
+            cand.push_back({pl, nw, maxb, 0});
+            if (maxb > 1) cand.push_back({pl, nw, 1, 0});
         }
     }
     // The chain state every trial starts from (both spin buffers agree
@@ -1126,14 +1139,16 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
         char buf[256];
         for (size_t i = 0; i < cand.size(); ++i) {
             std::snprintf(buf, sizeof buf,
-                          "%s{\"pipeline\": \"%s\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d, \"ms_per_sweep\": %s}",
+                          "%s{\"pipeline\": \"%s\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d, \"reduction\": %d, "
+                          "\"ms_per_sweep\": %s}",
                           i ? ", " : "", pipeline_name(cand[i].pipeline), cand[i].warps_per_cta, cand[i].ctas_per_sm,
-                          ms[i] >= 0 ? std::to_string(ms[i]).c_str() : "null");
+                          cand[i].reduction, ms[i] >= 0 ? std::to_string(ms[i]).c_str() : "null");
             js += buf;
         }
         std::snprintf(buf, sizeof buf,
-                      "], \"best\": {\"pipeline\": \"%s\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d}}",
-                      pipeline_name(chosen.pipeline), chosen.warps_per_cta, chosen.ctas_per_sm);
+                      "], \"best\": {\"pipeline\": \"%s\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d, "
+                      "\"reduction\": %d}}",
+                      pipeline_name(chosen.pipeline), chosen.warps_per_cta, chosen.ctas_per_sm, chosen.reduction);
         js += buf;
         if ((int)js.size() >= json_cap) return fail(PTCA_ERR_INVALID, "json buffer too small");
         std::memcpy(json, js.c_str(), js.size() + 1);

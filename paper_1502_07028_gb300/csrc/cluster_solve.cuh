@@ -77,6 +77,29 @@ __device__ __forceinline__ int window_site(const Model& m, const Window& w, int 
 
 __device__ __forceinline__ int tri(int r) { return (r * (r + 1)) >> 1; }
 
+// Storage of a cluster matrix as 4x4 complex tiles over the lower block
+// triangle: tile t = tri(R) + C (C <= R) at elements 16t .. 16t+15; element
+// e = 4r + c of the tile lies in its 16-byte slot e/2, and slot h is stored at
+// position h ^ (t mod 8), so that lanes reading the same slot of consecutive
+// tiles hit distinct shared-memory banks.  Diagonal tiles hold both triangles.
+__device__ __forceinline__ int tl_pos(int t, int e) {
+    return (t << 4) + ((((e >> 1) ^ (t & 7))) << 1) + (e & 1);
+}
+// Storage position of element (r, c), r >= c.
+__device__ __forceinline__ int tl_at(int r, int c) {
+    return tl_pos(tri(r >> 2) + (c >> 2), ((r & 3) << 2) + (c & 3));
+}
+// Complex elements of the tiled storage of an order-n matrix.
+__host__ __device__ __forceinline__ int tl_elems(int n) {
+    const int nb = (n + 3) >> 2;
+    return ((nb * (nb + 1)) >> 1) << 4;
+}
+// Position of element (r, c), r >= c, in the packed lower triangle or the tiled layout.
+template <bool kTiled> __device__ __forceinline__ int mat_at(int r, int c) {
+    if constexpr (kTiled) return tl_at(r, c);
+    else return tri(r) + c;
+}
+
 // Proposed new classical vector at `site` (Sec. II.c step c).  Double
 // exchange: propose_spin (sphere or cone).  Hubbard mean field: the old field
 // plus a step uniform in the ball of radius m_step -- direction from the
@@ -131,11 +154,14 @@ __device__ __forceinline__ double window_classical(const Model& m, const double*
 // sweep kernels pass e0 = 0 and shift mu by -m.e0 instead: a multiple of the
 // identity moves every eigenvalue by exactly e0, and the reduction keeps its
 // relative precision on the unshifted matrix.
-template <typename T>
+//
+// kTiled selects the tiled layout (tl_at): its padding is zeroed and its
+// diagonal tiles receive their upper triangles too.
+template <typename T, bool kTiled = false>
 __device__ void build_cluster(const Model& m, const Window& w, const double* __restrict__ S,
                               const double* s_new, double* sp, cplx_t<T>* A, double e0 = 0.0) {
     using V = cplx_t<T>;
-    const int nsite = window_nsite(w), n = 2 * nsite, P = tri(n), exy = w.ex * w.ey;
+    const int nsite = window_nsite(w), n = 2 * nsite, P = kTiled ? tl_elems(n) : tri(n), exy = w.ex * w.ey;
     for (int i = threadIdx.x; i < P; i += blockDim.x) A[i] = mk(T(0), T(0));
     const int uw = (w.uwz * w.ey + w.uwy) * w.ex + w.uwx;
     for (int s = threadIdx.x; s < nsite; s += blockDim.x) {
@@ -153,16 +179,16 @@ __device__ void build_cluster(const Model& m, const Window& w, const double* __r
         const T sx = T(sp[3 * s]), sy = T(sp[3 * s + 1]), sz = T(sp[3 * s + 2]);
         const int a = 2 * s, b = 2 * s + 1;
         const T dg = d0 + lam * sx;
-        A[tri(a) + a] = mk(dg - J * sz, T(0));
-        A[tri(b) + b] = mk(dg + J * sz, T(0));
-        A[tri(b) + a] = mk(-J * sx, -J * sy);  // element (b, a) = -J_H (S_x + i S_y)
+        A[mat_at<kTiled>(a, a)] = mk(dg - J * sz, T(0));
+        A[mat_at<kTiled>(b, b)] = mk(dg + J * sz, T(0));
+        A[mat_at<kTiled>(b, a)] = mk(-J * sx, -J * sy);  // element (b, a) = -J_H (S_x + i S_y)
         // +x bond
         int nb = -1, mult = 1;
         if (wx + 1 < w.ex) { nb = s + 1; if (m.cluster_periodic && w.ex == 2) mult = 2; }
         else if (m.cluster_periodic && w.ex >= 3) nb = s - (w.ex - 1);
         if (nb >= 0) {
             const int hi = nb > s ? nb : s, lo = nb > s ? s : nb;
-            for (int sg = 0; sg < 2; ++sg) A[tri(2 * hi + sg) + 2 * lo + sg] = mk(-T(mult) * t, T(0));
+            for (int sg = 0; sg < 2; ++sg) A[mat_at<kTiled>(2 * hi + sg, 2 * lo + sg)] = mk(-T(mult) * t, T(0));
         }
         // +y bond
         nb = -1; mult = 1;
@@ -170,7 +196,7 @@ __device__ void build_cluster(const Model& m, const Window& w, const double* __r
         else if (m.cluster_periodic && w.ey >= 3) nb = s - (w.ey - 1) * w.ex;
         if (nb >= 0) {
             const int hi = nb > s ? nb : s, lo = nb > s ? s : nb;
-            for (int sg = 0; sg < 2; ++sg) A[tri(2 * hi + sg) + 2 * lo + sg] = mk(-T(mult) * t, T(0));
+            for (int sg = 0; sg < 2; ++sg) A[mat_at<kTiled>(2 * hi + sg, 2 * lo + sg)] = mk(-T(mult) * t, T(0));
         }
         // +z bond
         nb = -1; mult = 1;
@@ -178,7 +204,18 @@ __device__ void build_cluster(const Model& m, const Window& w, const double* __r
         else if (m.cluster_periodic && w.ez >= 3) nb = s - (w.ez - 1) * exy;
         if (nb >= 0) {
             const int hi = nb > s ? nb : s, lo = nb > s ? s : nb;
-            for (int sg = 0; sg < 2; ++sg) A[tri(2 * hi + sg) + 2 * lo + sg] = mk(-T(mult) * t, T(0));
+            for (int sg = 0; sg < 2; ++sg) A[mat_at<kTiled>(2 * hi + sg, 2 * lo + sg)] = mk(-T(mult) * t, T(0));
+        }
+    }
+    if constexpr (kTiled) {
+        // Upper triangles of the diagonal tiles (6 elements each).
+        __syncthreads();
+        const int nb = (n + 3) >> 2;
+        for (int t = threadIdx.x; t < 6 * nb; t += blockDim.x) {
+            const int R = t / 6, q = t % 6;
+            const int r = q < 1 ? 1 : (q < 3 ? 2 : 3), c = q - (r * (r - 1)) / 2;  // (r, c), r > c
+            const V x = A[tl_at(4 * R + r, 4 * R + c)];
+            A[tl_pos(tri(R) + R, (c << 2) + r)] = mk(x.x, -x.y);
         }
     }
 }

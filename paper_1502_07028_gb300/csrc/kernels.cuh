@@ -5,6 +5,7 @@
 #include <type_traits>
 
 #include "cluster_solve.cuh"
+#include "cluster_tiled.cuh"
 #include "surrogate.cuh"
 
 namespace ptca {
@@ -55,6 +56,35 @@ __host__ __device__ inline SmemLayout smem_layout(int nA, int nmaxc, size_t cs, 
     L.d = o;   o = align16(o + nm * sizeof(double));
     L.e2 = o;  o = align16(o + nm * sizeof(double));
     L.red = o; o = align16(o + 6 * (size_t)nw * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+// Shared-memory layout of the FP32 4-warp CTA with the register-tiled
+// reduction (orders up to 128): the tiled matrix, the two reflectors, w, the
+// per-warp partial vectors of p (their region shared as in smem_layout), d
+// and e2 in FP32, the block-sum slots.  No row-sum vector (pr = pc).  The
+// eigenvalue phase takes (d, e2) as doubles in the matrix region, free by then.
+__host__ __device__ inline SmemLayout smem_layout_tiled() {
+    SmemLayout L;
+    size_t o = 0;
+    const size_t nm = TL_NMAX, cs = sizeof(float2);
+    L.A = o;   o = align16(o + (size_t)tl_elems(TL_NMAX) * cs);
+    L.Vb = o;  o = align16(o + 2 * nm * cs);
+    L.Wv = o;  o = align16(o + nm * cs);
+    L.pc = o;
+    L.pr = o;
+    L.sp = o;
+    L.lam = o;
+    L.df = o + 8 * nm;
+    L.e2f = o + 12 * nm;
+    L.dlo = o + 16 * nm;
+    L.e2lo = o + 20 * nm;
+    L.cnt = o + 24 * nm;
+    o = align16(o + max2((size_t)TL_NW * nm * cs, 24 * nm + 4 * 32 * (size_t)TL_NW));
+    L.d = o;   o = align16(o + nm * sizeof(float));
+    L.e2 = o;  o = align16(o + nm * sizeof(float));
+    L.red = o; o = align16(o + 6 * (size_t)TL_NW * sizeof(double));
     L.total = o;
     return L;
 }
@@ -385,10 +415,15 @@ __device__ __forceinline__ void collect_sample(const StageArgs& a, const double*
 // One matrix of one update site of a stage: c indexes the stage's site list,
 // var 0/1 selects H_old/H_new.  The second of the pair to finish applies
 // Metropolis.  Called by all threads of the CTA; s_new and s_last are shared.
-template <typename T, int NT, int NWP, bool kLarge = false>
+//
+// kTiled (FP32, 4 warps, orders up to 128): the matrix in the tiled layout and
+// the register-tiled reduction (householder_tridiag_tiled).
+template <typename T, int NT, int NWP, bool kLarge = false, bool kTiled = false>
 __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v, int c, int var, unsigned char* smem,
                                            double* s_new, int* s_last) {
-    const SmemLayout L = smem_layout(kLarge ? 0 : a.nA, 32 * NT, sizeof(cplx_t<T>), NWP);
+    static_assert(!kTiled || (std::is_same<T, float>::value && NWP == TL_NW && 32 * NT <= TL_NMAX && !kLarge),
+                  "the tiled reduction is FP32, 4 warps, orders up to 128");
+    const SmemLayout L = kTiled ? smem_layout_tiled() : smem_layout(kLarge ? 0 : a.nA, 32 * NT, sizeof(cplx_t<T>), NWP);
     Carve<T> cv = carve<T>(smem, L, NWP);
     if constexpr (kLarge) cv.A = static_cast<cplx_t<T>*>(a.gL) + (int64_t)blockIdx.x * a.gL_stride;
     c = v.perm ? v.perm[c] : c;
@@ -400,14 +435,32 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
         if (threadIdx.x == 0 && var == 1)
             propose(a.m, v.sweep, (uint32_t)site, v.S_in + 3 * site, s_new);
         __syncthreads();
-        build_cluster<T>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+        build_cluster<T, kTiled>(a.m, w, v.S_in, var ? s_new : nullptr, cv.sp, cv.A);
     }
     __syncthreads();
     // The window's classical energy (Hubbard mean field), parked in this
     // matrix's F slot until the eigenvalues are known.
     if (threadIdx.x == 0 && a.m.cls_on) a.Fbuf[2 * c + var] = window_classical(a.m, cv.sp, n / 2);
-    if constexpr (kLarge) householder_tridiag_large<T, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
-    else householder_tridiag<T, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
+    if constexpr (kTiled) {
+        TlScratch ts;
+        ts.Vb = cv.hh.Vb; ts.Wv = cv.hh.Wv; ts.pc = cv.hh.pc;
+        ts.redA = cv.hh.redA; ts.redB = cv.hh.redB; ts.sx = cv.hh.sx;
+        ts.d = reinterpret_cast<float*>(smem + L.d);
+        ts.e2 = reinterpret_cast<float*>(smem + L.e2);
+        householder_tridiag_tiled(n, cv.A, ts);
+        // (d, e2) as doubles for the eigenvalue phase, in the matrix region
+        cv.d = reinterpret_cast<double*>(smem + L.A);
+        cv.e2 = cv.d + TL_NMAX;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            cv.d[i] = (double)ts.d[i];
+            cv.e2[i] = i < n - 1 ? (double)ts.e2[i] : 0.0;
+        }
+        __syncthreads();
+    } else if constexpr (kLarge) {
+        householder_tridiag_large<T, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
+    } else {
+        householder_tridiag<T, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
+    }
     double ssp, sfe;
     int K;
     tridiag_eig_F<T, NWP>(n, cv, a.m.mu - a.m.e0, a.m.T, false, nullptr, ssp, sfe, K);
@@ -458,7 +511,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
     atomicAdd(&a.counters[1], 2ull);
 }
 
-template <typename T, int NT, int NWP = NW>
+template <typename T, int NT, int NWP = NW, bool kTiled = false>
 __global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value) k_stage(StageArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_new[3];
@@ -473,7 +526,7 @@ __global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value) k_stag
     const int c = blockIdx.x >> 1, var = blockIdx.x & 1;
     const int count = a.count_dev ? (int)*a.count_dev : a.count;
     if (c >= count) return;
-    stage_item<T, NT, NWP>(a, stage_var(a), c, var, smem, s_new, &s_last);
+    stage_item<T, NT, NWP, false, kTiled>(a, stage_var(a), c, var, smem, s_new, &s_last);
 }
 
 template <typename T, int NT>

@@ -41,6 +41,13 @@ cudaError_t launch_free_energy(const double* eig, const int64_t* eoff, const int
 bool sweep_width_supported(int prec, int nw, int nA);
 size_t sweep_smem_bytes(int prec, int nw, int nA);
 cudaError_t launch_stage(int prec, int nw, const StageArgs& a, cudaStream_t st);
+// The FP32 4-warp stage kernel with the register-tiled reduction (orders up
+// to 128): whether it covers (prec, nA), its dynamic shared memory, its
+// configuration (part of configure_cluster_kernels) and launch.
+bool tiled_supported(int prec, int nA);
+size_t tiled_smem_bytes();
+cudaError_t configure_tiled_kernels(size_t smem_limit);
+cudaError_t launch_stage_tiled(const StageArgs& a, cudaStream_t st);
 // Persistent sweep kernel: grid CTAs (all co-resident; cooperative launch).
 cudaError_t launch_persistent(int prec, int nw, const PersistArgs& p, int grid, cudaStream_t st);
 // CTAs of the persistent kernel that fit on one SM for matrices up to nA.

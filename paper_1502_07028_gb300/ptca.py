@@ -21,6 +21,7 @@ STATUS = {0: "PTCA_OK", 1: "PTCA_ERR_INVALID", 2: "PTCA_ERR_CUDA", 3: "PTCA_ERR_
           4: "PTCA_ERR_TIMEOUT", 5: "PTCA_ERR_NUMERIC", 6: "PTCA_ERR_UNSUPPORTED"}
 SCHEDULE_TILED, SCHEDULE_BLOCK = 0, 1
 PIPELINE_STAGES, PIPELINE_PERSISTENT, PIPELINE_GRAPH, PIPELINE_OVERLAP = 0, 1, 2, 3
+REDUCTION_ROWS, REDUCTION_TILED = 0, 1
 FP64, MIXED = 0, 1
 PROPOSAL_SPHERE, PROPOSAL_CONE = 0, 1
 MODEL_DOUBLE_EXCHANGE, MODEL_HUBBARD_MF, MODEL_HOLSTEIN = 0, 1, 2
@@ -45,7 +46,8 @@ class PtcaError(RuntimeError):
 
 
 class LaunchConfig(ctypes.Structure):
-    _fields_ = [("pipeline", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+    _fields_ = [("pipeline", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reduction", ctypes.c_int32)]
 
 
 class Lattice(ctypes.Structure):
@@ -379,8 +381,8 @@ def ptca_set_resolve_margin(h, margin: float) -> None:
     _check(lib().ptca_set_resolve_margin(h, margin))
 
 
-def ptca_set_launch_config(h, pipeline: int, warps_per_cta: int = 8, ctas_per_sm: int = 0) -> None:
-    _check(lib().ptca_set_launch_config(h, ctypes.byref(LaunchConfig(pipeline, warps_per_cta, ctas_per_sm))))
+def ptca_set_launch_config(h, pipeline: int, warps_per_cta: int = 8, ctas_per_sm: int = 0, reduction: int = 0) -> None:
+    _check(lib().ptca_set_launch_config(h, ctypes.byref(LaunchConfig(pipeline, warps_per_cta, ctas_per_sm, reduction))))
 
 
 def ptca_get_launch_config(h) -> LaunchConfig:
