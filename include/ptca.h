@@ -215,8 +215,11 @@ ptca_status ptca_build_clusters(ptca_ctx* ctx, const int32_t* sites, int32_t m,
  * confirmed by FP64 Sturm counts and refined by safeguarded FP64 Newton.
  * PTCA_MIXED: FP32 reduction; one double-float Newton step on the FP64
  * tridiagonal.  Sizes are checked on the device; a matrix with n outside
- * [1, nmax] gets NaN eigenvalues.  Shared-memory cluster orders only
- * (PTCA_ERR_UNSUPPORTED for a large-cluster context). */
+ * [1, nmax] gets NaN eigenvalues.  In a large-cluster context (orders above
+ * the shared-memory kernels', Sec. VII.a) each matrix is copied into one of
+ * the context's global matrix slots and reduced there by a 16-warp CTA; the
+ * call is then ordered after the context's earlier work on `stream` (a
+ * sweep running on another stream must finish first). */
 ptca_status ptca_cluster_eigvals(ptca_ctx* ctx, const void* H, const int64_t* offsets,
                                  const int32_t* n, int32_t m, double* eig_out,
                                  const int64_t* eig_offsets, void* stream);
@@ -253,8 +256,10 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
  *                             (site, old/new) items of a stage from an atomic
  *                             queue, largest window first, and meet at a
  *                             device-wide barrier between stages;
- *   PTCA_PIPELINE_GRAPH       (default) the persistent launch captured once in
- *                             a CUDA graph per sweep count and replayed;
+ *   PTCA_PIPELINE_GRAPH       (default; large clusters default to
+ *                             PTCA_PIPELINE_STAGES) the persistent launch
+ *                             captured once in a CUDA graph per sweep count
+ *                             and replayed;
  *   PTCA_PIPELINE_OVERLAP     per-stage launches in which the re-solve of
  *                             the decisions a stage deferred (PTCA_MIXED
  *                             guard) runs on a high-priority stream of the
@@ -285,7 +290,9 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  *                  distributed shared memory (every precision else: one
  *                  16-warp CTA, matrix in global memory); 16 runs the
  *                  16-warp, global-memory kernel;
- *   ctas_per_sm    CTAs per SM of the persistent kernel, 0 = as many as fit;
+ *   ctas_per_sm    CTAs per SM of the persistent kernel, 0 = as many as fit
+ *                  (large clusters: the persistent pipelines run width 16,
+ *                  the matrix in each CTA's global slot);
  *   reduction      organisation of the FP32 Householder pass (Sec. II.c
  *                  step b): PTCA_REDUCTION_ROWS = lanes on columns of the
  *                  packed triangle, rows in batches (every width);
@@ -356,7 +363,9 @@ ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin);
  * sweep uses and fully in FP64 -- and records per stage (per batch of
  * concurrent clusters) the largest eigenvalue error max|eps32 - eps64| and
  * free-energy-difference error max|dF32 - dF64|.  The chain itself is
- * unchanged; sweeps run the per-stage pipeline while the checker is on. */
+ * unchanged; sweeps run the per-stage pipeline while the checker is on.
+ * Large clusters are checked in the context's global matrix slots (FP32 in
+ * the stage kernel's, FP64 in the re-solve's). */
 ptca_status ptca_set_checker(ptca_ctx* ctx, int32_t on);
 
 /* Checker results since the last read (or since the checker was first turned

@@ -435,8 +435,11 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         c->sms = sms;
-        c->grid = c->large ? 0 : sms * ptca::persistent_blocks_per_sm(c->prec, 8, c->nA);
-        if (c->grid <= 0) c->pipeline = PTCA_PIPELINE_STAGES;
+        c->grid = c->large ? sms * ptca::persistent_blocks_per_sm_large(c->prec)
+                           : sms * ptca::persistent_blocks_per_sm(c->prec, 8, c->nA);
+        // Large clusters start on the per-stage pipeline (the persistent one
+        // is slower there and is chosen explicitly).
+        if (c->grid <= 0 || c->large) c->pipeline = PTCA_PIPELINE_STAGES;
         if (c->large) {
             // One global matrix slot per resident CTA of the large-cluster
             // stage kernel, twice: the overlapped pipeline runs a stage's
@@ -466,7 +469,7 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
             for (int nw : {4, 1})
                 if (ptca::sweep_width_supported(c->prec, nw, c->nA))
                     widest = std::max(widest, sms * ptca::persistent_blocks_per_sm(c->prec, nw, c->nA));
-            const int slots = std::max(widest, c->resolve_grid);
+            const int slots = std::max(std::max(widest, c->resolve_grid), c->large ? c->large_grid : 0);
             c->gA_stride = (int64_t)c->nA * (c->nA + 1) / 2;
             // + 64 elements: the fused pass may load up to 31 elements past a
             // slot (masked lanes of the diagonal chunk), also past the last.
@@ -562,9 +565,15 @@ ptca_status ptca_cluster_eigvals(ptca_ctx* ctx, const void* H, const int64_t* of
     if (m < 0) return fail(PTCA_ERR_INVALID, "m < 0");
     if (m == 0) return PTCA_OK;
     if (!H || !offsets || !n || !eig_out || !eig_offsets) return fail(PTCA_ERR_INVALID, "null buffer");
-    if (ctx->large) return fail(PTCA_ERR_UNSUPPORTED, "batch eigenvalues cover the shared-memory cluster orders only");
-    PTCA_CUDA(ptca::launch_eigvals(ctx->prec, ctx->nA, H, offsets, n, m, eig_out, eig_offsets,
-                                   static_cast<cudaStream_t>(stream)));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (ctx->large) {
+        // the matrices are reduced in the context's large-cluster slots
+        PTCA_SETTLE(ctx, st);
+        PTCA_CUDA(ptca::launch_eigvals_large(ctx->prec, H, offsets, n, m, ctx->nA, eig_out, eig_offsets, ctx->d_gL,
+                                             ctx->gL_stride, ctx->large_grid, st));
+        return PTCA_OK;
+    }
+    PTCA_CUDA(ptca::launch_eigvals(ctx->prec, ctx->nA, H, offsets, n, m, eig_out, eig_offsets, st));
     return PTCA_OK;
 }
 
@@ -643,8 +652,13 @@ static cudaError_t check_stage(ptca_ctx* ctx, const StageArgs& a, int s, cudaStr
     cudaError_t e = cudaSuccess;
     for (int c0 = 0; c0 < a.count && e == cudaSuccess; c0 += chunk) {
         const int cnt = std::min(chunk, a.count - c0);
-        e = ptca::launch_check(1, a, c0, cnt, e32, ld, F32, 0, st);
-        if (e == cudaSuccess) e = ptca::launch_check(0, a, c0, cnt, e64, ld, F64, ctx->resolve_grid, st);
+        if (ctx->large) {
+            e = ptca::launch_check_large(1, a, c0, cnt, e32, ld, F32, ctx->large_grid, st);
+            if (e == cudaSuccess) e = ptca::launch_check_large(0, a, c0, cnt, e64, ld, F64, ctx->resolve_grid, st);
+        } else {
+            e = ptca::launch_check(1, a, c0, cnt, e32, ld, F32, 0, st);
+            if (e == cudaSuccess) e = ptca::launch_check(0, a, c0, cnt, e64, ld, F64, ctx->resolve_grid, st);
+        }
         if (e == cudaSuccess)
             e = ptca::launch_check_compare(a.m, a.sites + c0, cnt, e32, e64, ld, F32, F64, ctx->d_chk_out + ptca::kCheckCols * s, st);
     }
@@ -899,7 +913,9 @@ static cudaError_t enqueue_persistent(ptca_ctx* ctx, int32_t n_sweeps, cudaStrea
     cudaError_t e = cudaMemsetAsync(ctx->d_queue, 0, 3 * sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag_count, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned int), st);
-    if (e == cudaSuccess) e = ptca::launch_persistent(ctx->prec, ctx->nw, p, ctx->grid, st);
+    if (e == cudaSuccess)
+        e = ctx->large ? ptca::launch_persistent_large(ctx->prec, p, ctx->grid, st)
+                       : ptca::launch_persistent(ctx->prec, ctx->nw, p, ctx->grid, st);
     return e;
 }
 
@@ -1014,7 +1030,8 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     if (!ctx->large && !ptca::sweep_width_supported(ctx->prec, cfg->warps_per_cta, ctx->nA))
         return fail(PTCA_ERR_UNSUPPORTED,
                     "narrow sweep kernels need PTCA_MIXED and matrix orders up to 128 (4 warps) or 32 (1 warp)");
-    const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, cfg->warps_per_cta, ctx->nA);
+    const int maxb = ctx->large ? (cfg->warps_per_cta == 16 ? ptca::persistent_blocks_per_sm_large(ctx->prec) : 0)
+                                : ptca::persistent_blocks_per_sm(ctx->prec, cfg->warps_per_cta, ctx->nA);
     if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > maxb)
         return fail(PTCA_ERR_INVALID, "ctas_per_sm must be in [0, the CTAs that fit on an SM]");
     const bool persistent = cfg->pipeline == PTCA_PIPELINE_PERSISTENT || cfg->pipeline == PTCA_PIPELINE_GRAPH;
@@ -1063,6 +1080,9 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
             cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 0});
             if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 0});
         }
+        const int maxb = ptca::persistent_blocks_per_sm_large(ctx->prec);
+        if (maxb > 0 && !ctx->sg.enabled)
+            for (int pl : {PTCA_PIPELINE_PERSISTENT, PTCA_PIPELINE_GRAPH}) cand.push_back({pl, 16, maxb, 0});
     }
     for (int nw : {8, 4, 1}) {
         if (ctx->large || !ptca::sweep_width_supported(ctx->prec, nw, ctx->nA)) continue;
@@ -1174,7 +1194,6 @@ ptca_status ptca_set_checker(ptca_ctx* ctx, int32_t on) {
         return PTCA_OK;
     }
     if (ctx->prec != 1) return fail(PTCA_ERR_UNSUPPORTED, "the precision checker compares PTCA_MIXED against FP64");
-    if (ctx->large) return fail(PTCA_ERR_UNSUPPORTED, "the precision checker covers the shared-memory cluster orders");
     if (!ctx->d_chk_out) {
         ctx->check_chunk = std::min(ctx->max_stage, 2048);
         cudaError_t e = dalloc(&ctx->d_chk_eig, (size_t)2 * ctx->check_chunk * 2 * ctx->nA);

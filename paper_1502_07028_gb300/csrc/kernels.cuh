@@ -781,12 +781,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int par
     return s_ok != 0;
 }
 
-template <typename T, int NT, int NWP = NW>
-__global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value)
-    k_sweep_persistent(const __grid_constant__ PersistArgs p) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_new[3];
-    __shared__ int s_last, s_item;
+// Body of the persistent kernels: shared-memory matrices (k_sweep_persistent)
+// or, with kLarge, each CTA's global slot (k_sweep_persistent_large).
+template <typename T, int NT, int NWP, bool kLarge>
+__device__ __forceinline__ void persistent_body(const PersistArgs& p, unsigned char* smem, double* s_new, int& s_last,
+                                                int& s_item) {
     const StageArgs& a = p.st;  // invariant fields, read from the kernel parameters
     const unsigned long long sweep0 = *p.sweep_ctr;
     const int G = p.nstages * p.n_sweeps;
@@ -818,7 +817,7 @@ __global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value)
             const int item = s_item;
             __syncthreads();
             if (item >= 2 * count) break;
-            stage_item<T, NT, NWP>(a, v, item >> 1, item & 1, smem, s_new, &s_last);
+            stage_item<T, NT, NWP, kLarge>(a, v, item >> 1, item & 1, smem, s_new, &s_last);
             __syncthreads();
         }
         if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, a.err, qc)) return;
@@ -832,7 +831,7 @@ __global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value)
                     const int item = s_item;
                     __syncthreads();
                     if (item >= 2 * nflag) break;
-                    resolve_item<NT, NWP>(a, v, a.flag_list[item >> 1], item & 1, smem, s_new, &s_last);
+                    resolve_item<NT, NWP, false, kLarge>(a, v, a.flag_list[item >> 1], item & 1, smem, s_new, &s_last);
                     __syncthreads();
                 }
                 if (!grid_barrier(p.bar, gridDim.x, p.timeout_ns, a.err, p.queue + 2, a.flag_count)) return;
@@ -851,6 +850,92 @@ __global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value)
             dst[3 * q] = src[3 * q]; dst[3 * q + 1] = src[3 * q + 1]; dst[3 * q + 2] = src[3 * q + 2];
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) *p.sweep_ctr = sweep0 + (unsigned long long)p.n_sweeps;
+    }
+}
+
+template <typename T, int NT, int NWP = NW>
+__global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value)
+    k_sweep_persistent(const __grid_constant__ PersistArgs p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    __shared__ int s_last, s_item;
+    persistent_body<T, NT, NWP, false>(p, smem, s_new, s_last, s_item);
+}
+
+// Large clusters: the persistent pipeline with 16-warp CTAs and the matrix
+// in each CTA's global slot (a.gL; re-solves in a.gA), grid <= the slots.
+template <typename T>
+__global__ void __launch_bounds__(32 * NW_LARGE, 1) k_sweep_persistent_large(const __grid_constant__ PersistArgs p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    __shared__ int s_last, s_item;
+    persistent_body<T, NW_LARGE, NW_LARGE, true>(p, smem, s_new, s_last, s_item);
+}
+
+// Precision checker for large clusters: as k_check (T = float, the sweep's
+// FP32 reduction, slots a.gL) and k_check_ref (T = double, FP64, the re-solve
+// slots a.gA), one 16-warp CTA per item over a grid stride, the matrix in
+// the CTA's global slot and all n eigenvalues returned.
+template <typename T>
+__global__ void __launch_bounds__(32 * NW_LARGE, 1) k_check_large(StageArgs a, int c0, int count, double* eig, int ld,
+                                                                  double* F) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    const SmemLayout L = smem_layout(0, 32 * NW_LARGE, sizeof(cplx_t<T>), NW_LARGE);
+    for (int item = blockIdx.x; item < 2 * count; item += gridDim.x) {
+        Carve<T> cv = carve<T>(smem, L, NW_LARGE);
+        if constexpr (sizeof(T) == 4) cv.A = static_cast<cplx_t<T>*>(a.gL) + (int64_t)blockIdx.x * a.gL_stride;
+        else cv.A = a.gA + (int64_t)blockIdx.x * a.gA_stride;
+        const int c = item >> 1, var = item & 1;
+        const int site = a.sites[c0 + c];
+        const Window w = make_window(a.m, site);
+        const int n = 2 * window_nsite(w);
+        if (threadIdx.x == 0 && var == 1) propose(a.m, a.sweep, (uint32_t)site, a.S_in + 3 * site, s_new);
+        __syncthreads();
+        build_cluster<T>(a.m, w, a.S_in, var ? s_new : nullptr, cv.sp, cv.A);
+        __syncthreads();
+        const double cls = threadIdx.x == 0 ? window_classical(a.m, cv.sp, n / 2) : 0.0;
+        householder_tridiag_large<T, NW_LARGE>(n, cv.A, cv.hh, cv.d, cv.e2);
+        double ssp, sfe;
+        int K;
+        tridiag_eig_F<T, NW_LARGE>(n, cv, a.m.mu - a.m.e0, a.m.T, true, eig + (int64_t)(2 * c + var) * ld, ssp, sfe,
+                                   K);
+        if (threadIdx.x == 0) F[2 * c + var] = -a.m.T * ssp + cls;
+        __syncthreads();
+    }
+}
+
+// All eigenvalues of packed matrices of large orders (up to 32 NW_LARGE), one
+// 16-warp CTA per matrix over a grid stride: the matrix is copied into the
+// CTA's slot (slots + blockIdx.x * stride) and reduced there.
+template <typename T>
+__global__ void __launch_bounds__(32 * NW_LARGE, 1) k_eigvals_large(const cplx_t<T>* __restrict__ H,
+                                                                    const int64_t* __restrict__ offsets,
+                                                                    const int32_t* __restrict__ nin, int count, int nA,
+                                                                    double* __restrict__ eig,
+                                                                    const int64_t* __restrict__ eoff, cplx_t<T>* slots,
+                                                                    int64_t stride) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout L = smem_layout(0, 32 * NW_LARGE, sizeof(cplx_t<T>), NW_LARGE);
+    for (int b = blockIdx.x; b < count; b += gridDim.x) {
+        Carve<T> c = carve<T>(smem, L, NW_LARGE);
+        c.A = slots + (int64_t)blockIdx.x * stride;
+        const int n = nin[b];
+        double* out = eig + eoff[b];
+        if (n < 1 || n > nA || n > 32 * NW_LARGE) {
+            for (int i = threadIdx.x; i < (n > 0 ? n : 0) && i < nA; i += blockDim.x) out[i] = nan("");
+            __syncthreads();
+            continue;
+        }
+        const cplx_t<T>* src = H + offsets[b];
+        const int P = tri(n);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) c.A[i] = src[i];
+        __syncthreads();
+        householder_tridiag_large<T, NW_LARGE>(n, c.A, c.hh, c.d, c.e2);
+        double s1, s2;
+        int K;
+        tridiag_eig_F<T, NW_LARGE>(n, c, 0.0, 1.0, true, out, s1, s2, K);
+        __syncthreads();
     }
 }
 

@@ -28,10 +28,78 @@ int large_max_order() { return 32 * NW_LARGE; }
 size_t large_smem_bytes(int prec) { return large_layout(prec == 1 ? sizeof(float2) : sizeof(double2)); }
 
 cudaError_t configure_large_kernels(size_t smem_limit) {
-    cudaError_t e = allow_smem(k_stage_large<float>, large_layout(sizeof(float2)), smem_limit);
-    if (e == cudaSuccess) e = allow_smem(k_stage_large<double>, large_layout(sizeof(double2)), smem_limit);
+    const size_t f = large_layout(sizeof(float2)), d = large_layout(sizeof(double2));
+    cudaError_t e = allow_smem(k_stage_large<float>, f, smem_limit);
+    if (e == cudaSuccess) e = allow_smem(k_stage_large<double>, d, smem_limit);
     if (e == cudaSuccess) e = allow_smem(k_resolve_large<>, large_layout(sizeof(dfl2)), smem_limit);
+    // the FP32 persistent kernel also runs the double-float re-solve inline
+    const size_t fp = f > large_layout(sizeof(dfl2)) ? f : large_layout(sizeof(dfl2));
+    if (e == cudaSuccess) e = allow_smem(k_sweep_persistent_large<float>, fp, smem_limit);
+    if (e == cudaSuccess) e = allow_smem(k_sweep_persistent_large<double>, d, smem_limit);
+    if (e == cudaSuccess) e = allow_smem(k_check_large<float>, f, smem_limit);
+    if (e == cudaSuccess) e = allow_smem(k_check_large<double>, d, smem_limit);
+    if (e == cudaSuccess) e = allow_smem(k_eigvals_large<float>, f, smem_limit);
+    if (e == cudaSuccess) e = allow_smem(k_eigvals_large<double>, d, smem_limit);
     return e;
+}
+
+namespace {
+size_t persistent_large_smem(int prec) {
+    const size_t f = large_layout(sizeof(float2)), r = large_layout(sizeof(dfl2));
+    return prec == 1 ? (f > r ? f : r) : large_layout(sizeof(double2));
+}
+}  // namespace
+
+// At most large_blocks_per_sm: the persistent grid then fits the stage
+// kernel's slots (a.gL holds two sets of sms x large_blocks_per_sm).
+int persistent_blocks_per_sm_large(int prec) {
+    int b = 0;
+    const size_t smem = persistent_large_smem(prec);
+    cudaError_t e = prec == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_persistent_large<float>,
+                                                                              32 * NW_LARGE, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_persistent_large<double>,
+                                                                              32 * NW_LARGE, smem);
+    if (e != cudaSuccess) return 0;
+    const int s = large_blocks_per_sm(prec);
+    return b < s ? b : s;
+}
+
+cudaError_t launch_persistent_large(int prec, const PersistArgs& p, int grid, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * NW_LARGE);
+    cfg.dynamicSmemBytes = persistent_large_smem(prec);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return prec == 1 ? cudaLaunchKernelEx(&cfg, k_sweep_persistent_large<float>, p)
+                     : cudaLaunchKernelEx(&cfg, k_sweep_persistent_large<double>, p);
+}
+
+cudaError_t launch_check_large(int prec, const StageArgs& a, int c0, int count, double* eig, int ld, double* F,
+                               int grid, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (prec == 1)
+        k_check_large<float><<<grid, 32 * NW_LARGE, large_layout(sizeof(float2)), st>>>(a, c0, count, eig, ld, F);
+    else
+        k_check_large<double><<<grid, 32 * NW_LARGE, large_layout(sizeof(double2)), st>>>(a, c0, count, eig, ld, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eigvals_large(int prec, const void* H, const int64_t* offsets, const int32_t* n, int count, int nA,
+                                 double* eig, const int64_t* eoff, void* slots, int64_t stride, int grid,
+                                 cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (prec == 1)
+        k_eigvals_large<float><<<grid, 32 * NW_LARGE, large_layout(sizeof(float2)), st>>>(
+            static_cast<const float2*>(H), offsets, n, count, nA, eig, eoff, static_cast<float2*>(slots), stride);
+    else
+        k_eigvals_large<double><<<grid, 32 * NW_LARGE, large_layout(sizeof(double2)), st>>>(
+            static_cast<const double2*>(H), offsets, n, count, nA, eig, eoff, static_cast<double2*>(slots), stride);
+    return cudaGetLastError();
 }
 
 int large_blocks_per_sm(int prec) {

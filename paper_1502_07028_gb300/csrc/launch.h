@@ -82,6 +82,20 @@ cudaError_t configure_large_kernels(size_t smem_limit);
 int large_blocks_per_sm(int prec);
 cudaError_t launch_stage_large(int prec, const StageArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_resolve_large(const StageArgs& a, int grid, cudaStream_t st);
+// Persistent pipeline for large clusters (16-warp CTAs, matrix in the CTA's
+// global slot a.gL, FP32 re-solves inline in a.gA): CTAs per SM that fit, and
+// the cooperative launch (grid <= the slots of a.gL and a.gA).
+int persistent_blocks_per_sm_large(int prec);
+cudaError_t launch_persistent_large(int prec, const PersistArgs& p, int grid, cudaStream_t st);
+// Precision checker for large clusters: prec 1 the FP32 reduction in the
+// slots a.gL, prec 0 FP64 in the slots a.gA (grid <= the slots).
+cudaError_t launch_check_large(int prec, const StageArgs& a, int c0, int count, double* eig, int ld, double* F,
+                               int grid, cudaStream_t st);
+// Batch eigenvalues of large orders (<= large_max_order): each CTA copies its
+// matrix into slots + blockIdx.x * stride (grid <= the slots) and reduces it there.
+cudaError_t launch_eigvals_large(int prec, const void* H, const int64_t* offsets, const int32_t* n, int count, int nA,
+                                 double* eig, const int64_t* eoff, void* slots, int64_t stride, int grid,
+                                 cudaStream_t st);
 // FP32 large-cluster stage kernel with the matrix in the distributed shared
 // memory of a thread-block cluster: the cluster size (2, 4 or 8 CTAs, 0 if
 // none fits) for order nA (configures the kernel's shared memory), the grid
