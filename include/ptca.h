@@ -330,7 +330,7 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
 /* Per-kernel timing of the per-stage pipelines (off by default).  While on,
  * every stage-kernel launch and every re-solve launch of ptca_sweep is
  * bracketed by CUDA events on the stream it runs on.  ptca_kernel_times
- * synchronises `stream` and writes, into a host array of 8 doubles:
+ * synchronises `stream` and writes, into a host array of 9 doubles:
  *   out[0], out[1]  total ms and launch count of the stage kernels (whole
  *                   stages; in PTCA_PIPELINE_OVERLAP the visits that do not
  *                   wait for the previous stage's re-solve);
@@ -339,6 +339,10 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
  *                   PTCA_PIPELINE_OVERLAP that run after a re-solve;
  *   out[6], out[7]  cluster matrices solved by the launches of out[0] and of
  *                   out[4] (two per visit);
+ *   out[8]          ms during which at least one launch of out[0] ran (the
+ *                   union of their intervals: in PTCA_PIPELINE_OVERLAP a
+ *                   stage's independent visits start beside the previous
+ *                   stage's, so the launches overlap);
  * then clears the record.  Launches of one pipeline may overlap in time, so
  * the totals can exceed the elapsed time.  The persistent pipelines time as
  * one launch per call of ptca_sweep (ptca_sweep_stats.seconds). */

@@ -297,9 +297,11 @@ static void free_ctx(ptca_ctx* c) {
     drop_timing_events(c);
     ptca_free_surrogate(c);
     if (c->side) cudaStreamDestroy(c->side);
-    for (cudaEvent_t ev : {c->ev_indep, c->ev_dep, c->ev_fork, c->ev_join})
+    if (c->side2) cudaStreamDestroy(c->side2);
+    for (cudaEvent_t ev : {c->ev_indep, c->ev_dep, c->ev_fork, c->ev_join, c->ev_ind[0], c->ev_ind[1], c->ev_res[0],
+                           c->ev_res[1]})
         if (ev) cudaEventDestroy(ev);
-    void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_S[2], c->d_split, c->d_gL, c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
+    void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_S[2], c->d_S[3], c->d_split, c->d_gL, c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
                     c->d_rec_n, c->d_counters, c->d_err, c->d_obs, c->d_stage_start, c->d_perm, c->d_queue,
                     c->d_bar, c->d_sweep_ctr, c->d_flag_list, c->d_flag_count, c->d_gA,
@@ -724,12 +726,16 @@ static cudaError_t ensure_overlap(ptca_ctx* ctx) {
     if (ctx->side) return cudaSuccess;
     std::vector<int32_t> order;
     stage_split(ctx->p, ctx->h_start, ctx->h_sites, order, ctx->h_indep);
-    cudaError_t e = ctx->d_S[2] ? cudaSuccess : dalloc(&ctx->d_S[2], 3 * (size_t)ctx->N);
+    cudaError_t e = cudaSuccess;
+    for (int b = 2; b < 4 && e == cudaSuccess; ++b)
+        if (!ctx->d_S[b]) e = dalloc(&ctx->d_S[b], 3 * (size_t)ctx->N);
     if (e == cudaSuccess && !ctx->d_split) e = dalloc(&ctx->d_split, (size_t)ctx->N);
     if (e == cudaSuccess)
         e = cudaMemcpy(ctx->d_split, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    for (cudaEvent_t* ev : {&ctx->ev_indep, &ctx->ev_dep, &ctx->ev_fork, &ctx->ev_join})
+    for (cudaEvent_t* ev : {&ctx->ev_indep, &ctx->ev_dep, &ctx->ev_fork, &ctx->ev_join, &ctx->ev_ind[0],
+                            &ctx->ev_ind[1], &ctx->ev_res[0], &ctx->ev_res[1]})
         if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->side2) e = cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking);
     int least = 0, greatest = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     cudaStream_t side = nullptr;
@@ -738,47 +744,78 @@ static cudaError_t ensure_overlap(ptca_ctx* ctx) {
     return e;
 }
 
+// Whether the overlapped pipeline runs stage g+1's independent visits beside
+// stage g's (look-ahead).  Not with surrogate screening (one set of network
+// buffers) nor for large clusters (one set of matrix slots for the
+// independent visits).
+static bool lookahead(const ptca_ctx* ctx) { return !ctx->large && !ctx->sg.enabled; }
+
 // StageArgs of stage gg of the overlapped pipeline's rotation (counted from
-// the last time the configuration was in buffers 0 and 1): buffer gg mod 3
-// in, gg+1 mod 3 out, the per-visit scratch half gg mod 2, the random stream
+// the last time the configuration was in buffers 0 and 1): buffer gg mod 4
+// in, gg+1 mod 4 out, the per-visit scratch half gg mod 2, the random stream
 // of sweep `sweep`.
 static StageArgs overlap_args(ptca_ctx* ctx, int64_t gg, uint64_t sweep) {
     const int s = (int)(gg % ctx->nstages);
     StageArgs a = base_args(ctx);
     use_half(ctx, a, (int)(gg & 1));
     a.sweep = sweep;
-    a.S_in = ctx->d_S[gg % 3];
-    a.S_out = ctx->d_S[(gg + 1) % 3];
+    a.S_in = ctx->d_S[gg % 4];
+    a.S_out = ctx->d_S[(gg + 1) % 4];
     a.sites = ctx->d_sites + ctx->h_start[s];
     a.rec_base = ctx->h_start[s];
     if (ctx->sg.enabled) a.sg_dFt = ctx->sg.dFt + (size_t)(gg & 1) * ctx->max_stage;
     return a;
 }
 
+// Sites the dependent-visit launch of stage gg copies forward from buffer gg
+// into buffer gg+1 (mod 4), which last held the configuration after stage
+// gg-4: those of the min(3, ns-1) stages before stage gg, as at most two
+// ranges of the flattened schedule.  (Early in a rotation some of these
+// stages have not run; their sites agree in every buffer, and the copy
+// changes nothing.)
+static void copy_ranges(const ptca_ctx* ctx, int64_t gg, StageArgs& ad) {
+    const int ns = ctx->nstages, s = (int)(gg % ns), k = std::min(3, ns - 1);
+    ad.prev_sites = ad.prev2_sites = nullptr;
+    ad.prev_count = ad.prev2_count = 0;
+    if (k <= 0) return;
+    const int q0 = ((s - k) % ns + ns) % ns, q1 = q0 + k;
+    ad.prev_sites = ctx->d_sites + ctx->h_start[q0];
+    ad.prev_count = ctx->h_start[std::min(q1, ns)] - ctx->h_start[q0];
+    if (q1 > ns) {
+        ad.prev2_sites = ctx->d_sites;
+        ad.prev2_count = ctx->h_start[q1 - ns];
+    }
+}
+
 // Overlapped per-stage pipeline.  Stage g (counted over the rotation) reads
-// buffer g mod 3 and writes buffer g+1 mod 3, so the re-solve of stage g-1
-// keeps reading its own start configuration while stage g writes.  On the
-// caller's stream: the visits of stage g whose windows hold no site of stage
-// g-1 (I_g), after the dependent visits of stage g-1.  On the context's
-// high-priority stream: the re-solve of stage g-1 (R_{g-1}, once I_{g-1} has
-// run), then the visits of stage g that depend on stage g-1 (D_g), which also
-// copy the sites of stages g-2 and g-1 forward into buffer g+1 mod 3.  The
-// per-visit scratch alternates halves with g, so R_{g-1} and stage g never
-// share a slot.  Every visit reads the spins it reads in the one-stream
-// pipeline and decides with the same arithmetic: the chain is the same, bit
-// for bit.
+// buffer g mod 4 and writes buffer g+1 mod 4, so the re-solve of stage g-1
+// keeps reading its own start configuration while stage g writes.  Each
+// stage is cut into the visits whose windows hold no site of stage g-1
+// (I_g) and the rest (D_g).
+//  - I_g reads buffer g-1 mod 4 (the configuration after stage g-2, equal
+//    to that after stage g-1 on its windows) once the re-solve of stage g-2
+//    (R_{g-2}) is done, alternating between the caller's stream and a
+//    second stream: it runs beside the tail of I_{g-1}.  Without look-ahead
+//    (surrogate screening, large clusters) I_g runs on the caller's stream,
+//    reads buffer g mod 4 and waits for D_{g-1}.
+//  - On the context's high-priority stream: R_{g-1} (once I_{g-1} is done),
+//    then D_g, which also copies the sites of the three stages before g
+//    forward into buffer g+1 mod 4.
+// The per-visit scratch alternates halves with g, so R_{g-1} and stage g
+// never share a slot (I_{g+1} shares R_{g-1}'s half and starts after it).
+// Every visit reads the spins it reads in the one-stream pipeline and decides
+// with the same arithmetic: the chain is the same, bit for bit.
 //
 // With `defer`, the call ends without the last stage's re-solve: the next
 // call continues the rotation and runs it beside its own first stage's
-// independent visits (stage 0 of a sweep does not depend on the sweep's
-// last stage's sites for those), as a multi-sweep call does between its
-// sweeps.  Until then the configuration is in buffer (rotation) mod 3, not
-// in buffers 0 and 1; every other entry point settles it first.
+// independent visits, as a multi-sweep call does between its sweeps.  Until
+// then the configuration is in buffer (rotation) mod 4, not in buffers 0 and
+// 1; every other entry point settles it first.
 static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st, bool defer) {
     cudaError_t e = ensure_overlap(ctx);
     if (e != cudaSuccess) return e;
-    const bool screen = ctx->sg.enabled;
-    cudaStream_t hs = ctx->side;
+    const bool screen = ctx->sg.enabled, la = lookahead(ctx);
+    cudaStream_t hs = ctx->side, s2 = ctx->side2;
     const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
     const int ns = ctx->nstages;
     const int64_t G = (int64_t)n_sweeps * ns;
@@ -786,38 +823,45 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
     const int64_t g0 = cont ? ctx->ov_g : 0;
     ctx->ov_pending = false;
     StageArgs prev = base_args(ctx);  // the stage whose re-solve is pending
-    bool have_prev = false;
+    int64_t gprev = -1;
     if (cont) {
         // after the previous call's work on its stream (which may differ)
         e = cudaStreamWaitEvent(st, ctx->ev_fork, 0);
         prev = overlap_args(ctx, g0 - 1, (uint64_t)(ctx->sweeps - 1));
-        have_prev = true;
+        gprev = g0 - 1;
     } else {
-        // buffers 0 and 1 agree between calls; buffer 2 starts from them too
+        // buffers 0 and 1 agree between calls; 2 and 3 start from them too
         e = cudaMemcpyAsync(ctx->d_S[2], ctx->d_S[0], bytes, cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ctx->ev_fork, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_S[3], ctx->d_S[0], bytes, cudaMemcpyDeviceToDevice, st);
     }
+    // the library's streams start after the caller's earlier work
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ctx->ev_fork, 0);
+    if (e == cudaSuccess && la) e = cudaStreamWaitEvent(s2, ctx->ev_fork, 0);
     auto resolve_prev = [&]() {
-        cudaError_t r = cudaStreamWaitEvent(hs, ctx->ev_indep, 0);
+        cudaError_t r = cudaStreamWaitEvent(hs, la ? ctx->ev_ind[gprev & 1] : ctx->ev_indep, 0);
         if (r == cudaSuccess)
             r = timed_launch(ctx, 1, 0, hs, [&] { return launch_resolve_ctx(ctx, prev, hs); });
         if (r == cudaSuccess) r = cudaMemsetAsync(prev.flag_count, 0, sizeof(unsigned int), hs);
+        if (r == cudaSuccess && la) r = cudaEventRecord(ctx->ev_res[gprev & 1], hs);
         return r;
-    };
-    auto stage_sites = [&](int64_t gg, const int32_t*& sites, int32_t& count) {
-        const int q = (int)(gg % ns);
-        sites = ctx->d_sites + ctx->h_start[q];
-        count = ctx->h_start[q + 1] - ctx->h_start[q];
     };
     for (int64_t g = 0; g < G && e == cudaSuccess; ++g) {
         const int64_t gg = g0 + g;
         const int s = (int)(gg % ns);
         StageArgs a = overlap_args(ctx, gg, (uint64_t)(ctx->sweeps + g / ns));
         const int cnt = ctx->h_start[s + 1] - ctx->h_start[s], ni = ctx->h_indep[s];
-        if (have_prev) e = resolve_prev();
-        if (e == cudaSuccess && have_prev) e = cudaStreamWaitEvent(st, ctx->ev_dep, 0);
+        if (gprev >= 0) e = resolve_prev();
+        cudaStream_t is = st;
         StageArgs ai = a;
+        if (la) {
+            // after R_{gg-2}, on the stream of this stage's parity
+            is = (gg & 1) ? s2 : st;
+            if (e == cudaSuccess && gg >= 2) e = cudaStreamWaitEvent(is, ctx->ev_res[gg & 1], 0);
+            ai.S_in = ctx->d_S[(gg + 3) % 4];
+        } else if (e == cudaSuccess && gprev >= 0) {
+            e = cudaStreamWaitEvent(st, ctx->ev_dep, 0);
+        }
         ai.perm = ctx->d_split + ctx->h_start[s];
         ai.count = ni;
         // Delayed acceptance: each part of the stage is screened on its own
@@ -826,9 +870,8 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         // the half of this stage's parity, which its re-solve reads later).
         if (screen && e == cudaSuccess && ni > 0) e = ptca_screen_part(ctx, ai, 0, 0, (int)(gg & 1), st);
         if (e == cudaSuccess && ni > 0)
-            e = timed_launch(ctx, 0, 2 * (int64_t)ni, st,
-                             [&] { return launch_stage_ctx(ctx, ai, st); });
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_indep, st);
+            e = timed_launch(ctx, 0, 2 * (int64_t)ni, is, [&] { return launch_stage_ctx(ctx, ai, is); });
+        if (e == cudaSuccess) e = cudaEventRecord(la ? ctx->ev_ind[gg & 1] : ctx->ev_indep, is);
         StageArgs ad = a;
         ad.perm = ctx->d_split + ctx->h_start[s] + ni;
         ad.count = cnt - ni;
@@ -836,11 +879,7 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
             const size_t es = ctx->prec == 1 ? sizeof(float2) : sizeof(double2);
             ad.gL = static_cast<char*>(ctx->d_gL) + (size_t)ctx->large_grid * (size_t)ctx->gL_stride * es;
         }
-        // sites buffer gg+1 mod 3 lacks: those of stages gg-2 and gg-1 (each
-        // only if it is not stage gg itself, whose visits write every site)
-        if (gg >= 1 && (gg - 1) % ns != s) stage_sites(gg - 1, ad.prev_sites, ad.prev_count);
-        if (gg >= 2 && (gg - 2) % ns != s && (gg - 2) % ns != (gg - 1) % ns)
-            stage_sites(gg - 2, ad.prev2_sites, ad.prev2_count);
+        copy_ranges(ctx, gg, ad);
         if (screen && e == cudaSuccess && ad.count > 0) e = ptca_screen_part(ctx, ad, 1, 2 * ni, (int)(gg & 1), hs);
         if (e == cudaSuccess) {
             if (ad.count > 0) {
@@ -851,9 +890,9 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
                 if (e == cudaSuccess) e = ptca::launch_copy_sites(ad.S_in, ad.S_out, ad.prev2_sites, ad.prev2_count, hs);
             }
         }
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_dep, hs);
+        if (e == cudaSuccess && !la) e = cudaEventRecord(ctx->ev_dep, hs);
         prev = a;
-        have_prev = true;
+        gprev = gg;
     }
     if (e == cudaSuccess && defer && G > 0) {
         ctx->ov_pending = true;
@@ -863,13 +902,16 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
             e = ptca::launch_set_u64(ctx->d_sweep_ctr, (unsigned long long)(ctx->sweeps + n_sweeps), st);
         return e;
     }
-    if (e == cudaSuccess && have_prev) e = resolve_prev();
-    // join the side stream back into the caller's stream, also after a failure
+    if (e == cudaSuccess && gprev >= 0) e = resolve_prev();
+    // join the side stream back into the caller's stream, also after a
+    // failure (every independent-visit launch precedes a re-solve there)
     cudaError_t ej = cudaEventRecord(ctx->ev_join, hs);
     if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, ctx->ev_join, 0);
+    if (ej == cudaSuccess && la) ej = cudaEventRecord(ctx->ev_join, s2);
+    if (ej == cudaSuccess && la) ej = cudaStreamWaitEvent(st, ctx->ev_join, 0);
     if (e == cudaSuccess) e = ej;
-    // the configuration after the call is in buffer (g0 + G) mod 3; buffers 0 and 1 take it
-    const int f = (int)((g0 + G) % 3);
+    // the configuration after the call is in buffer (g0 + G) mod 4; buffers 0 and 1 take it
+    const int f = (int)((g0 + G) % 4);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
         if (b != f) e = cudaMemcpyAsync(ctx->d_S[b], ctx->d_S[f], bytes, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = ptca::launch_set_u64(ctx->d_sweep_ctr, (unsigned long long)(ctx->sweeps + n_sweeps), st);
@@ -881,11 +923,12 @@ cudaError_t ptca_internal_settle(ptca_ctx* ctx, cudaStream_t st, bool have_strea
     ctx->ov_pending = false;
     cudaStream_t hs = ctx->side;
     const int64_t g = ctx->ov_g;
+    const bool la = lookahead(ctx);
     StageArgs prev = overlap_args(ctx, g - 1, (uint64_t)(ctx->sweeps - 1));
-    cudaError_t e = cudaStreamWaitEvent(hs, ctx->ev_indep, 0);
+    cudaError_t e = cudaStreamWaitEvent(hs, la ? ctx->ev_ind[(g - 1) & 1] : ctx->ev_indep, 0);
     if (e == cudaSuccess) e = timed_launch(ctx, 1, 0, hs, [&] { return launch_resolve_ctx(ctx, prev, hs); });
     if (e == cudaSuccess) e = cudaMemsetAsync(prev.flag_count, 0, sizeof(unsigned int), hs);
-    const int f = (int)(g % 3);
+    const int f = (int)(g % 4);
     const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
         if (b != f) e = cudaMemcpyAsync(ctx->d_S[b], ctx->d_S[f], bytes, cudaMemcpyDeviceToDevice, hs);
@@ -988,7 +1031,9 @@ ptca_status ptca_kernel_times(ptca_ctx* ctx, double* out, void* stream) {
     if (!ctx || !out) return fail(PTCA_ERR_INVALID, "null argument");
     PTCA_SETTLE(ctx, static_cast<cudaStream_t>(stream));
     PTCA_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-    for (int q = 0; q < 8; ++q) out[q] = 0.0;
+    for (int q = 0; q < 9; ++q) out[q] = 0.0;
+    std::vector<std::pair<double, double>> span;  // stage launches (kind 0), relative to the first one's start
+    cudaEvent_t ref = nullptr;
     for (size_t i = 0; i < ctx->tkind.size(); ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ctx->tev[2 * i], ctx->tev[2 * i + 1]) != cudaSuccess) {
@@ -1000,7 +1045,26 @@ ptca_status ptca_kernel_times(ptca_ctx* ctx, double* out, void* stream) {
         out[2 * k + 1] += 1.0;
         if (k == 0) out[6] += (double)ctx->titems[i];
         if (k == 2) out[7] += (double)ctx->titems[i];
+        if (k == 0) {
+            float t0 = 0.f;
+            if (!ref) ref = ctx->tev[2 * i];
+            else if (cudaEventElapsedTime(&t0, ref, ctx->tev[2 * i]) != cudaSuccess) t0 = 0.f;
+            span.emplace_back((double)t0, (double)t0 + ms);
+        }
     }
+    // union of the stage launches' intervals (look-ahead launches overlap)
+    std::sort(span.begin(), span.end());
+    double lo = 0.0, hi = -1.0;
+    for (const auto& iv : span) {
+        if (iv.first > hi) {
+            if (hi > lo) out[8] += hi - lo;
+            lo = iv.first;
+            hi = iv.second;
+        } else if (iv.second > hi) {
+            hi = iv.second;
+        }
+    }
+    if (hi > lo) out[8] += hi - lo;
     drop_timing_events(ctx);
     return PTCA_OK;
 }

@@ -56,7 +56,7 @@ struct ptca_ctx {
     // Spin buffers: [0] and [1] rotate between stages and hold the same
     // configuration between calls; [2] joins the rotation in the overlapped
     // pipeline (allocated when that pipeline is first selected).
-    double* d_S[3] = {nullptr, nullptr, nullptr};
+    double* d_S[4] = {nullptr, nullptr, nullptr, nullptr};
     // Per-visit scratch of a stage, in two halves (stage parity) so that a
     // stage's re-solve can run while the next stage is under way; the
     // other pipelines use half 0.
@@ -130,6 +130,11 @@ struct ptca_ctx {
     bool ov_pending = false;
     int64_t ov_g = 0;
     cudaStream_t side = nullptr;
+    // second stream of the independent visits (look-ahead: stage g+1's
+    // independent visits beside stage g's), and per-parity events: the
+    // independent visits of stage g done (ev_ind), its re-solve done (ev_res)
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t ev_ind[2] = {nullptr, nullptr}, ev_res[2] = {nullptr, nullptr};
     cudaEvent_t ev_indep = nullptr, ev_dep = nullptr, ev_fork = nullptr, ev_join = nullptr;
     // optional per-kernel timing of the per-stage pipelines: event pairs
     // around each stage launch (kind 0), re-solve launch (kind 1) and

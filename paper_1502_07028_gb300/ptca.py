@@ -408,7 +408,7 @@ def ptca_set_kernel_timing(h, on: bool) -> None:
 # Per-kernel CUDA-event totals since the last read (see ptca_kernel_times).
 KernelTimes = namedtuple("KernelTimes", ["stage_ms", "stage_launches", "resolve_ms", "resolve_launches",
                                          "dependent_ms", "dependent_launches", "stage_matrices",
-                                         "dependent_matrices"])
+                                         "dependent_matrices", "stage_union_ms"])
 
 
 def ptca_kernel_times(h, stream=None) -> KernelTimes:
@@ -416,12 +416,13 @@ def ptca_kernel_times(h, stream=None) -> KernelTimes:
     dependent_launches, stage_matrices, dependent_matrices) since the last
     call; clears the record.  The dependent_* entries are the overlapped
     pipeline's launches of the visits that wait for the previous stage's
-    re-solve; stage_* are all other stage launches."""
+    re-solve; stage_* are all other stage launches; stage_union_ms is the
+    time at least one stage launch ran (look-ahead launches overlap)."""
     import numpy as np
-    out = np.zeros(8, dtype=np.float64)
+    out = np.zeros(9, dtype=np.float64)
     _check(lib().ptca_kernel_times(h, _ptr(out), _stream(stream)))
     return KernelTimes(float(out[0]), int(out[1]), float(out[2]), int(out[3]), float(out[4]), int(out[5]),
-                       int(out[6]), int(out[7]))
+                       int(out[6]), int(out[7]), float(out[8]))
 
 
 def ptca_full_spectrum(h, eig_out, stream=None) -> None:

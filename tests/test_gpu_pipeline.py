@@ -165,7 +165,9 @@ def test_kernel_timing_counts_the_stage_launches():
     st_ms, st_n, rs_ms, rs_n = kt[:4]
     assert st_n == 2 * ns and rs_n == 2 * ns and st_ms > 0 and rs_ms >= 0
     assert kt.stage_matrices == 2 * 2 * cfg.N and kt.dependent_launches == 0
-    assert tuple(P.ptca_kernel_times(ctx.h)) == (0.0, 0, 0.0, 0, 0.0, 0, 0, 0)   # read clears
+    # one stream: the stage launches do not overlap, their union is their sum
+    assert abs(kt.stage_union_ms - st_ms) <= 1e-3 * st_ms + 0.05
+    assert tuple(P.ptca_kernel_times(ctx.h)) == (0.0, 0, 0.0, 0, 0.0, 0, 0, 0, 0.0)   # read clears
     # Overlapped pipeline: the independent and the dependent visits of each
     # stage are separate launches; together they solve every matrix once.
     P.ptca_set_launch_config(ctx.h, P.PIPELINE_OVERLAP, 8, 0)
@@ -177,6 +179,8 @@ def test_kernel_timing_counts_the_stage_launches():
     assert kt.resolve_launches == 2 * ns
     assert kt.stage_matrices + kt.dependent_matrices == 2 * 2 * cfg.N
     assert kt.stage_matrices == 2 * 2 * sum(n for _, n in split)
+    # look-ahead: a stage's independent visits may start beside the previous stage's
+    assert 0 < kt.stage_union_ms <= kt.stage_ms * (1 + 1e-3) + 0.05
     P.ptca_set_launch_config(ctx.h, P.PIPELINE_GRAPH, 8, 0)
     ctx.sweep(1)
     assert P.ptca_kernel_times(ctx.h)[1] == 0               # one persistent launch: not per-stage
