@@ -289,10 +289,12 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
-def time_sweeps(ctx, steps, warmup, flush_buf, stream, kernel_timing=False):
+def time_sweeps(ctx, steps, warmup, flush_buf, stream, kernel_timing=False, nvtx=None):
     """Per-step device time (ms) of one sweep each, L2 flushed between steps.
     With kernel_timing the library records the duration of every stage and
-    re-solve kernel launched in the timed steps (read with ptca_kernel_times)."""
+    re-solve kernel launched in the timed steps (read with ptca_kernel_times).
+    nvtx names an NVTX range around the timed steps (profilers can restrict
+    a capture to it)."""
     import torch
     import paper_1502_07028_gb300 as P
     for _ in range(warmup):
@@ -302,6 +304,8 @@ def time_sweeps(ctx, steps, warmup, flush_buf, stream, kernel_timing=False):
         P.ptca_kernel_times(ctx.h, stream=stream)  # clear
         P.ptca_set_kernel_timing(ctx.h, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if nvtx:
+        torch.cuda.nvtx.range_push(nvtx)
     for i in range(steps):
         flush_buf.add_(1)  # write 256 MiB: evicts the 129 MB L2 between timed steps
         ev[i][0].record(stream)
@@ -312,6 +316,8 @@ def time_sweeps(ctx, steps, warmup, flush_buf, stream, kernel_timing=False):
             P.ptca_flush(ctx.h, stream=stream)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     return [a.elapsed_time(b) for a, b in ev]
 
 
@@ -739,7 +745,7 @@ def main():
             t_wall0 = time.perf_counter()
             # Per-stage pipeline: the library brackets each stage-kernel launch
             # with CUDA events on the stream, for the kernel's own duration.
-            ms = time_sweeps(ctx, args.steps, args.warmup, flush, stream, kernel_timing=per_stage)
+            ms = time_sweeps(ctx, args.steps, args.warmup, flush, stream, kernel_timing=per_stage, nvtx="headline")
             torch.cuda.synchronize()
             wall = time.perf_counter() - t_wall0
         return ms, wall, clk.summary()
