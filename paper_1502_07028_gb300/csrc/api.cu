@@ -745,10 +745,9 @@ static cudaError_t ensure_overlap(ptca_ctx* ctx) {
 }
 
 // Whether the overlapped pipeline runs stage g+1's independent visits beside
-// stage g's (look-ahead).  Not with surrogate screening (one set of network
-// buffers) nor for large clusters (one set of matrix slots for the
-// independent visits).
-static bool lookahead(const ptca_ctx* ctx) { return !ctx->large && !ctx->sg.enabled; }
+// stage g's (look-ahead).  Not for large clusters (one set of matrix slots
+// for the independent visits).
+static bool lookahead(const ptca_ctx* ctx) { return !ctx->large; }
 
 // StageArgs of stage gg of the overlapped pipeline's rotation (counted from
 // the last time the configuration was in buffers 0 and 1): buffer gg mod 4
@@ -796,8 +795,8 @@ static void copy_ranges(const ptca_ctx* ctx, int64_t gg, StageArgs& ad) {
 //    to that after stage g-1 on its windows) once the re-solve of stage g-2
 //    (R_{g-2}) is done, alternating between the caller's stream and a
 //    second stream: it runs beside the tail of I_{g-1}.  Without look-ahead
-//    (surrogate screening, large clusters) I_g runs on the caller's stream,
-//    reads buffer g mod 4 and waits for D_{g-1}.
+//    (large clusters) I_g runs on the caller's stream, reads buffer g mod 4
+//    and waits for D_{g-1}.
 //  - On the context's high-priority stream: R_{g-1} (once I_{g-1} is done),
 //    then D_g, which also copies the sites of the three stages before g
 //    forward into buffer g+1 mod 4.
@@ -868,7 +867,7 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         // stream just before its exact solves (network rows of the
         // independent part first, the dependent part's after them; dF~ in
         // the half of this stage's parity, which its re-solve reads later).
-        if (screen && e == cudaSuccess && ni > 0) e = ptca_screen_part(ctx, ai, 0, 0, (int)(gg & 1), st);
+        if (screen && e == cudaSuccess && ni > 0) e = ptca_screen_part(ctx, ai, 0, 0, (int)(gg & 1), is);
         if (e == cudaSuccess && ni > 0)
             e = timed_launch(ctx, 0, 2 * (int64_t)ni, is, [&] { return launch_stage_ctx(ctx, ai, is); });
         if (e == cudaSuccess) e = cudaEventRecord(la ? ctx->ev_ind[gg & 1] : ctx->ev_indep, is);

@@ -30,7 +30,7 @@ struct SurrogateState {
     float* m1 = nullptr;    // AdamW moments
     float* m2 = nullptr;
     float* grad = nullptr;
-    // stage screening buffers (rows = 2 * max_stage)
+    // stage screening buffers (two sets by stage parity, 2 * max_stage rows each)
     float *X = nullptr, *Z1 = nullptr, *A1 = nullptr, *Z2 = nullptr, *A2 = nullptr, *Z3 = nullptr, *A3 = nullptr,
           *Z4 = nullptr;
     float* dFt = nullptr;

@@ -132,7 +132,10 @@ ptca_status ptca_surrogate_init(ptca_ctx* ctx, uint64_t seed, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     SurrogateState& g = ctx->sg;
     if (!g.theta) {
-        const size_t P = ptca::SG_NPARAMS, R = 2 * (size_t)ctx->max_stage;
+        // screening rows: two sets (stage parity: the overlapped pipeline
+        // screens a stage's independent visits while the previous stage's
+        // are still being solved), each of 2 * max_stage rows
+        const size_t P = ptca::SG_NPARAMS, R = 4 * (size_t)ctx->max_stage;
         cudaError_t e = dal(&g.theta, P);
         if (e == cudaSuccess) e = dal(&g.m1, P);
         if (e == cudaSuccess) e = dal(&g.m2, P);
@@ -144,10 +147,10 @@ ptca_status ptca_surrogate_init(ptca_ctx* ctx, uint64_t seed, void* stream) {
         if (e == cudaSuccess) e = dal(&g.Z4, R * ptca::SG_OUT_PAD);
         // dF~ per stage index in two halves (stage parity), and the work list
         // of each part of a stage (all visits, or the overlapped pipeline's
-        // independent and dependent visits)
+        // independent and dependent visits), per stage parity
         if (e == cudaSuccess) e = dal(&g.dFt, 2 * (size_t)ctx->max_stage);
-        if (e == cudaSuccess) e = dal(&g.work, 2 * (size_t)ctx->max_stage);
-        if (e == cudaSuccess) e = dal(&g.nwork, 2);
+        if (e == cudaSuccess) e = dal(&g.work, 4 * (size_t)ctx->max_stage);
+        if (e == cudaSuccess) e = dal(&g.nwork, 4);
         if (e != cudaSuccess) {
             ptca_free_surrogate(ctx);
             return cfail(e, "ptca_surrogate_init");
@@ -271,10 +274,10 @@ extern "C" cudaError_t ptca_screen_part(ptca_ctx* ctx, ptca::StageArgs& a, int p
                                         cudaStream_t st) {
     SurrogateState& g = ctx->sg;
     const int R = 2 * a.count;
-    const size_t rb = (size_t)row_base;
+    const size_t rb = (size_t)half * 2 * ctx->max_stage + (size_t)row_base;  // rows of this parity's set
     float* dFt = g.dFt + (size_t)half * ctx->max_stage;
-    int32_t* work = g.work + (size_t)part * ctx->max_stage;
-    unsigned int* nwork = g.nwork + part;
+    int32_t* work = g.work + (size_t)(2 * half + part) * ctx->max_stage;
+    unsigned int* nwork = g.nwork + 2 * half + part;
     cudaError_t e = cudaMemsetAsync(nwork, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = ptca::sg_screen_rows(a, g.X + rb * ptca::SG_IN_PAD, st);
     if (e == cudaSuccess)
