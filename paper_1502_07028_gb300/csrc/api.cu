@@ -298,8 +298,7 @@ static void free_ctx(ptca_ctx* c) {
     ptca_free_surrogate(c);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->side2) cudaStreamDestroy(c->side2);
-    for (cudaEvent_t ev : {c->ev_indep, c->ev_dep, c->ev_fork, c->ev_join, c->ev_ind[0], c->ev_ind[1], c->ev_res[0],
-                           c->ev_res[1]})
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_join, c->ev_ind[0], c->ev_ind[1], c->ev_res[0], c->ev_res[1]})
         if (ev) cudaEventDestroy(ev);
     void* ptrs[] = {c->d_sites, c->d_S[0], c->d_S[1], c->d_S[2], c->d_S[3], c->d_split, c->d_gL, c->d_F, c->d_fill, c->d_ticket, c->d_rec_site,
                     c->d_rec_Fold, c->d_rec_Fnew, c->d_rec_lnu, c->d_rec_acc, c->d_rec_Facc, c->d_rec_fill,
@@ -444,9 +443,10 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
         if (c->grid <= 0 || c->large) c->pipeline = PTCA_PIPELINE_STAGES;
         if (c->large) {
             // One global matrix slot per resident CTA of the large-cluster
-            // stage kernel, twice: the overlapped pipeline runs a stage's
-            // independent and dependent visits as concurrent launches, each
-            // on its own half (+ 64 elements of padding, as below).
+            // stage kernel, three times: the overlapped pipeline runs the
+            // independent visits of two consecutive stages (one set each, by
+            // stage parity) and a stage's dependent visits (the third set) as
+            // concurrent launches (+ 64 elements of padding, as below).
             c->large_grid = sms * std::max(1, ptca::large_blocks_per_sm(c->prec));
             if (c->prec == 1) {
                 c->cl_size = ptca::cluster_stage_size(c->nA, (size_t)optin);
@@ -460,7 +460,7 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
             c->gL_stride = (int64_t)c->nA * (c->nA + 1) / 2;
             const size_t es = c->prec == 1 ? sizeof(float2) : sizeof(double2);
             void* q = nullptr;
-            ce = cudaMalloc(&q, (2 * (size_t)c->large_grid * (size_t)c->gL_stride + 64) * es);
+            ce = cudaMalloc(&q, (3 * (size_t)c->large_grid * (size_t)c->gL_stride + 64) * es);
             c->d_gL = q;
         }
         if (ce == cudaSuccess && c->prec == 1) {
@@ -732,8 +732,8 @@ static cudaError_t ensure_overlap(ptca_ctx* ctx) {
     if (e == cudaSuccess && !ctx->d_split) e = dalloc(&ctx->d_split, (size_t)ctx->N);
     if (e == cudaSuccess)
         e = cudaMemcpy(ctx->d_split, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    for (cudaEvent_t* ev : {&ctx->ev_indep, &ctx->ev_dep, &ctx->ev_fork, &ctx->ev_join, &ctx->ev_ind[0],
-                            &ctx->ev_ind[1], &ctx->ev_res[0], &ctx->ev_res[1]})
+    for (cudaEvent_t* ev : {&ctx->ev_fork, &ctx->ev_join, &ctx->ev_ind[0], &ctx->ev_ind[1], &ctx->ev_res[0],
+                            &ctx->ev_res[1]})
         if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess && !ctx->side2) e = cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking);
     int least = 0, greatest = 0;
@@ -744,10 +744,12 @@ static cudaError_t ensure_overlap(ptca_ctx* ctx) {
     return e;
 }
 
-// Whether the overlapped pipeline runs stage g+1's independent visits beside
-// stage g's (look-ahead).  Not for large clusters (one set of matrix slots
-// for the independent visits).
-static bool lookahead(const ptca_ctx* ctx) { return !ctx->large; }
+// Large clusters: the global matrix slots of set k (0, 1: independent
+// visits by stage parity; 2: dependent visits).
+static void *large_slots(const ptca_ctx* ctx, int k) {
+    const size_t es = ctx->prec == 1 ? sizeof(float2) : sizeof(double2);
+    return static_cast<char*>(ctx->d_gL) + (size_t)k * (size_t)ctx->large_grid * (size_t)ctx->gL_stride * es;
+}
 
 // StageArgs of stage gg of the overlapped pipeline's rotation (counted from
 // the last time the configuration was in buffers 0 and 1): buffer gg mod 4
@@ -794,9 +796,9 @@ static void copy_ranges(const ptca_ctx* ctx, int64_t gg, StageArgs& ad) {
 //  - I_g reads buffer g-1 mod 4 (the configuration after stage g-2, equal
 //    to that after stage g-1 on its windows) once the re-solve of stage g-2
 //    (R_{g-2}) is done, alternating between the caller's stream and a
-//    second stream: it runs beside the tail of I_{g-1}.  Without look-ahead
-//    (large clusters) I_g runs on the caller's stream, reads buffer g mod 4
-//    and waits for D_{g-1}.
+//    second stream: it runs beside the tail of I_{g-1}.  Surrogate screening
+//    keeps a set of network buffers per stage parity, large clusters a set
+//    of matrix slots per stage parity, so two such launches never share one.
 //  - On the context's high-priority stream: R_{g-1} (once I_{g-1} is done),
 //    then D_g, which also copies the sites of the three stages before g
 //    forward into buffer g+1 mod 4.
@@ -813,7 +815,7 @@ static void copy_ranges(const ptca_ctx* ctx, int64_t gg, StageArgs& ad) {
 static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t st, bool defer) {
     cudaError_t e = ensure_overlap(ctx);
     if (e != cudaSuccess) return e;
-    const bool screen = ctx->sg.enabled, la = lookahead(ctx);
+    const bool screen = ctx->sg.enabled;
     cudaStream_t hs = ctx->side, s2 = ctx->side2;
     const size_t bytes = 3 * (size_t)ctx->N * sizeof(double);
     const int ns = ctx->nstages;
@@ -836,13 +838,13 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
     // the library's streams start after the caller's earlier work
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, ctx->ev_fork, 0);
-    if (e == cudaSuccess && la) e = cudaStreamWaitEvent(s2, ctx->ev_fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ctx->ev_fork, 0);
     auto resolve_prev = [&]() {
-        cudaError_t r = cudaStreamWaitEvent(hs, la ? ctx->ev_ind[gprev & 1] : ctx->ev_indep, 0);
+        cudaError_t r = cudaStreamWaitEvent(hs, ctx->ev_ind[gprev & 1], 0);
         if (r == cudaSuccess)
             r = timed_launch(ctx, 1, 0, hs, [&] { return launch_resolve_ctx(ctx, prev, hs); });
         if (r == cudaSuccess) r = cudaMemsetAsync(prev.flag_count, 0, sizeof(unsigned int), hs);
-        if (r == cudaSuccess && la) r = cudaEventRecord(ctx->ev_res[gprev & 1], hs);
+        if (r == cudaSuccess) r = cudaEventRecord(ctx->ev_res[gprev & 1], hs);
         return r;
     };
     for (int64_t g = 0; g < G && e == cudaSuccess; ++g) {
@@ -851,18 +853,14 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         StageArgs a = overlap_args(ctx, gg, (uint64_t)(ctx->sweeps + g / ns));
         const int cnt = ctx->h_start[s + 1] - ctx->h_start[s], ni = ctx->h_indep[s];
         if (gprev >= 0) e = resolve_prev();
-        cudaStream_t is = st;
+        // I_gg: after R_{gg-2}, on the stream of this stage's parity
+        cudaStream_t is = (gg & 1) ? s2 : st;
+        if (e == cudaSuccess && gg >= 2) e = cudaStreamWaitEvent(is, ctx->ev_res[gg & 1], 0);
         StageArgs ai = a;
-        if (la) {
-            // after R_{gg-2}, on the stream of this stage's parity
-            is = (gg & 1) ? s2 : st;
-            if (e == cudaSuccess && gg >= 2) e = cudaStreamWaitEvent(is, ctx->ev_res[gg & 1], 0);
-            ai.S_in = ctx->d_S[(gg + 3) % 4];
-        } else if (e == cudaSuccess && gprev >= 0) {
-            e = cudaStreamWaitEvent(st, ctx->ev_dep, 0);
-        }
+        ai.S_in = ctx->d_S[(gg + 3) % 4];
         ai.perm = ctx->d_split + ctx->h_start[s];
         ai.count = ni;
+        if (ctx->large) ai.gL = large_slots(ctx, (int)(gg & 1));
         // Delayed acceptance: each part of the stage is screened on its own
         // stream just before its exact solves (network rows of the
         // independent part first, the dependent part's after them; dF~ in
@@ -870,14 +868,11 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
         if (screen && e == cudaSuccess && ni > 0) e = ptca_screen_part(ctx, ai, 0, 0, (int)(gg & 1), is);
         if (e == cudaSuccess && ni > 0)
             e = timed_launch(ctx, 0, 2 * (int64_t)ni, is, [&] { return launch_stage_ctx(ctx, ai, is); });
-        if (e == cudaSuccess) e = cudaEventRecord(la ? ctx->ev_ind[gg & 1] : ctx->ev_indep, is);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_ind[gg & 1], is);
         StageArgs ad = a;
         ad.perm = ctx->d_split + ctx->h_start[s] + ni;
         ad.count = cnt - ni;
-        if (ctx->large) {  // concurrent with ai: the second half of the large-cluster slots
-            const size_t es = ctx->prec == 1 ? sizeof(float2) : sizeof(double2);
-            ad.gL = static_cast<char*>(ctx->d_gL) + (size_t)ctx->large_grid * (size_t)ctx->gL_stride * es;
-        }
+        if (ctx->large) ad.gL = large_slots(ctx, 2);  // concurrent with the independent-visit launches
         copy_ranges(ctx, gg, ad);
         if (screen && e == cudaSuccess && ad.count > 0) e = ptca_screen_part(ctx, ad, 1, 2 * ni, (int)(gg & 1), hs);
         if (e == cudaSuccess) {
@@ -889,7 +884,6 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
                 if (e == cudaSuccess) e = ptca::launch_copy_sites(ad.S_in, ad.S_out, ad.prev2_sites, ad.prev2_count, hs);
             }
         }
-        if (e == cudaSuccess && !la) e = cudaEventRecord(ctx->ev_dep, hs);
         prev = a;
         gprev = gg;
     }
@@ -906,8 +900,8 @@ static cudaError_t sweep_overlap(ptca_ctx* ctx, int32_t n_sweeps, cudaStream_t s
     // failure (every independent-visit launch precedes a re-solve there)
     cudaError_t ej = cudaEventRecord(ctx->ev_join, hs);
     if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, ctx->ev_join, 0);
-    if (ej == cudaSuccess && la) ej = cudaEventRecord(ctx->ev_join, s2);
-    if (ej == cudaSuccess && la) ej = cudaStreamWaitEvent(st, ctx->ev_join, 0);
+    if (ej == cudaSuccess) ej = cudaEventRecord(ctx->ev_join, s2);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, ctx->ev_join, 0);
     if (e == cudaSuccess) e = ej;
     // the configuration after the call is in buffer (g0 + G) mod 4; buffers 0 and 1 take it
     const int f = (int)((g0 + G) % 4);
@@ -922,9 +916,8 @@ cudaError_t ptca_internal_settle(ptca_ctx* ctx, cudaStream_t st, bool have_strea
     ctx->ov_pending = false;
     cudaStream_t hs = ctx->side;
     const int64_t g = ctx->ov_g;
-    const bool la = lookahead(ctx);
     StageArgs prev = overlap_args(ctx, g - 1, (uint64_t)(ctx->sweeps - 1));
-    cudaError_t e = cudaStreamWaitEvent(hs, la ? ctx->ev_ind[(g - 1) & 1] : ctx->ev_indep, 0);
+    cudaError_t e = cudaStreamWaitEvent(hs, ctx->ev_ind[(g - 1) & 1], 0);
     if (e == cudaSuccess) e = timed_launch(ctx, 1, 0, hs, [&] { return launch_resolve_ctx(ctx, prev, hs); });
     if (e == cudaSuccess) e = cudaMemsetAsync(prev.flag_count, 0, sizeof(unsigned int), hs);
     const int f = (int)(g % 4);

@@ -135,7 +135,7 @@ struct ptca_ctx {
     // independent visits of stage g done (ev_ind), its re-solve done (ev_res)
     cudaStream_t side2 = nullptr;
     cudaEvent_t ev_ind[2] = {nullptr, nullptr}, ev_res[2] = {nullptr, nullptr};
-    cudaEvent_t ev_indep = nullptr, ev_dep = nullptr, ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // optional per-kernel timing of the per-stage pipelines: event pairs
     // around each stage launch (kind 0), re-solve launch (kind 1) and
     // dependent-visit launch of the overlapped pipeline (kind 2), with the
