@@ -261,19 +261,26 @@ def test_one_warp_width_is_limited_to_order_32():
     ctx.close()
 
 
-@pytest.mark.parametrize("margin", [None, 1e6])
-def test_calls_that_leave_the_last_resolve_pending_compute_the_same_chain(margin):
+@pytest.mark.parametrize("kind,margin", [("n128", None), ("n128", 1e6), ("n288", None)])
+def test_calls_that_leave_the_last_resolve_pending_compute_the_same_chain(kind, margin):
     # Overlapped pipeline: a call without statistics leaves its last stage's
     # re-solve for the next call.  Three such calls (the second on another
     # stream) must give the chain of one three-sweep call, and every entry
     # point that reads the configuration must see it complete.  margin 1e6:
     # every decision is re-solved, so the pending work is a whole stage.
-    cfg = P.Config(Lx=32, Ly=32, L_c=8, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, T=0.05, seed=31,
-                   precision=P.MIXED)
+    # n288: 12x12 clusters, the large-cluster kernel with its matrix-slot sets.
+    if kind == "n128":
+        cfg = P.Config(Lx=32, Ly=32, L_c=8, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, T=0.05, seed=31,
+                       precision=P.MIXED)
+        width = 4
+    else:
+        cfg = P.Config(Lx=24, Ly=24, L_c=12, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, T=0.05, seed=32,
+                       precision=P.MIXED)
+        width = 16
 
     def ctx_():
         c = P.Context(cfg)
-        P.ptca_set_launch_config(c.h, P.PIPELINE_OVERLAP, 4, 0)
+        P.ptca_set_launch_config(c.h, P.PIPELINE_OVERLAP, width, 0)
         if margin is not None:
             P.ptca_set_resolve_margin(c.h, margin)
         return c

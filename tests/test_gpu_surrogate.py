@@ -255,3 +255,18 @@ def test_screened_sweeps_are_one_chain_in_every_per_stage_pipeline(trained, prop
         a, b = runs[(P.PIPELINE_STAGES, w)], runs[(P.PIPELINE_OVERLAP, w)]
         for x, y in zip(a[3:5], b[3:5]):
             assert torch.equal(torch.nan_to_num(x, nan=7.0), torch.nan_to_num(y, nan=7.0)), w
+    # Three one-sweep calls without statistics: each leaves its last re-solve
+    # to the next call, and the next stage's screening and solves run beside
+    # the current stage's (network buffers per stage parity).  Same chain.
+    ctx = P.Context(cfg)
+    P.ptca_surrogate_set_params(ctx.h, trained["theta"], trained["scale"])
+    P.ptca_surrogate_enable(ctx.h, True)
+    P.ptca_set_launch_config(ctx.h, P.PIPELINE_OVERLAP, 4)
+    for _ in range(3):
+        P.ptca_sweep(ctx.h, 1, stats=False)
+    site, Fo, Fn, lnu, acc = ctx.record()
+    ref4 = runs[(P.PIPELINE_STAGES, 4)]
+    assert torch.equal(ctx.spins(), ref4[0]) and torch.equal(site, ref4[1]) and torch.equal(acc, ref4[2])
+    for x, y in zip((Fo, Fn), ref4[3:5]):
+        assert torch.equal(torch.nan_to_num(x, nan=7.0), torch.nan_to_num(y, nan=7.0))
+    ctx.close()
