@@ -732,7 +732,7 @@ def main():
     names = {P.PIPELINE_STAGES: "per-stage launches", P.PIPELINE_PERSISTENT: "persistent kernel",
              P.PIPELINE_GRAPH: "persistent kernel in a CUDA graph",
              P.PIPELINE_OVERLAP: "per-stage launches, each stage's re-solve overlapped with the next stage's "
-                                 "independent visits"}
+                                 "independent visits, which start beside the current stage's tail"}
     per_stage = best.pipeline in (P.PIPELINE_STAGES, P.PIPELINE_OVERLAP)
     pipeline_desc = (f"{names[best.pipeline]}, {best.warps_per_cta}-warp CTA per matrix"
                      + (f", {best.ctas_per_sm} CTAs/SM" if not per_stage else "")
