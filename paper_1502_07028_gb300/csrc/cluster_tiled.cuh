@@ -7,10 +7,11 @@
 // the explicit update of the next pivot column); only the organisation of
 // the fused pass differs.
 //
-// Storage: the lower block triangle of 4x4 complex tiles, tile (R, C), C <= R,
-// at elements 16 (R(R+1)/2 + C) .. +15, element (r, c) of the tile at 4r + c.
-// Diagonal tiles hold both triangles (Hermitian); rows and columns past the
-// order n, up to the next multiple of 4, are zero and stay zero.
+// Storage (tl_at, tl_pos): the lower block triangle of 4x4 complex tiles,
+// tile t = R(R+1)/2 + C (C <= R) at elements 16t .. 16t+15, its 16-byte slots
+// swizzled by t mod 8 so that lanes reading consecutive tiles hit distinct
+// banks.  Diagonal tiles hold both triangles (Hermitian); rows and columns
+// past the order n, up to the next multiple of 4, are zero and stay zero.
 //
 // Fused pass of step k (active corner j0 = k+1 in block K = j0/4, M = NB - K
 // active block rows): the off-diagonal tiles of block rows K+p and K+M-1-p
@@ -22,11 +23,14 @@
 // the previous step's (u, w), stores it once, and forms its row sums (A v) and
 // column sums; the row sums of the pair are reduce-scattered across the warp.
 // One warp also updates the diagonal tiles, one per lane.  Vector entries
-// outside the active range are kept zero in shared memory, so tiles that
-// straddle the corner need no masks.  Per warp, the sums are added into the
-// warp's partial vector in a fixed order (zero, the row sums pair by pair,
-// the column sums, the diagonal tiles' row sums), and the scalar phase adds
-// the warps' vectors in warp order: the result does not depend on timing.
+// outside the active range are kept zero in shared memory (each reflector's
+// first entry stays in registers and is substituted where a lane loads the
+// block holding it), so tiles that straddle the corner need no masks.  Per
+// warp, the sums are added into the warp's partial vector in a fixed order
+// (zero, the row sums pair by pair, the column sums, the diagonal tiles' row
+// sums), and the scalar phase adds the warps' vectors in warp order: the
+// result does not depend on timing.  The pass also sums v^H A v, so a
+// reflector step needs two barriers (after the pass, after the scalar phase).
 #pragma once
 
 #include "cluster_solve.cuh"
