@@ -192,6 +192,7 @@ def test_kernel_timing_counts_the_stage_launches():
     dict(Lx=32, Ly=32, L_c=8, schedule=P.SCHEDULE_BLOCK),          # 4 stages
     dict(Lx=13, Ly=11, L_c=6, periodic=0, stride=6),                # ragged windows, 6 stages
     dict(Lx=24, Ly=1, L_c=4, schedule=P.SCHEDULE_BLOCK),            # chain: 2 stages
+    dict(Lx=12, Ly=1, L_c=3, stride=3),                             # chain: 3 stages (copies wrap)
     dict(Lx=24, Ly=24, L_c=8, stride=8),                            # tiled: 64 stages of 9 sites
 ])
 @pytest.mark.parametrize("margin", [1e-2, 50.0])
@@ -219,6 +220,17 @@ def test_overlapped_resolve_gives_the_one_stream_chain_bit_for_bit(lat, margin):
     for a, b in zip(r0, r1):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+    # The same calls without statistics, back to back: each leaves its last
+    # re-solve to the next, and the rotation runs on across the calls.
+    ctx = P.Context(cfg)
+    P.ptca_set_resolve_margin(ctx.h, margin)
+    P.ptca_set_launch_config(ctx.h, P.PIPELINE_OVERLAP, 8, 0)
+    for n in (1, 3, 2):
+        P.ptca_sweep(ctx.h, n, stats=False)
+    assert np.array_equal(ctx.spins().cpu().numpy(), S0)
+    for x, y in zip([x.cpu().numpy() for x in ctx.record()], r0[-1]):
+        assert np.array_equal(x, y)
+    ctx.close()
 
 
 @pytest.mark.parametrize("cfgkw", [
