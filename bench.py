@@ -737,6 +737,7 @@ def main():
     pipeline_desc = (f"{names[best.pipeline]}, {best.warps_per_cta}-warp CTA per matrix"
                      + (f", {best.ctas_per_sm} CTAs/SM" if not per_stage else "")
                      + (", register-tiled Householder pass" if best.reduction == P.REDUCTION_TILED else "")
+                     + (f", blocked Householder reduction in panels of {best.panel_width}" if best.panel_width > 1 else "")
                      + " (autotuned)")
     def timed_region():
         barrier(world)
@@ -838,6 +839,7 @@ def main():
         # visits: 2 matrices per visit, per-launch durations from the
         # library's CUDA events on the stream each launch runs on.
         kernel_name = (f"k_stage<float,4,{best.warps_per_cta},tiled>" if best.reduction == P.REDUCTION_TILED
+                       else f"k_stage<float,4,{best.warps_per_cta},panel{best.panel_width}>" if best.panel_width > 1
                        else f"k_stage<float,4,{best.warps_per_cta}>")
         launch_ms = kt.stage_ms / kt.stage_launches
         matrices_per_launch = kt.stage_matrices / kt.stage_launches
@@ -884,9 +886,10 @@ def main():
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "pipeline": pipeline_desc,
             "autotune": {"best": tune_table["best"],
-                         "columns": ["pipeline", "warps_per_cta", "ctas_per_sm", "reduction", "ms_per_sweep"],
+                         "columns": ["pipeline", "warps_per_cta", "ctas_per_sm", "reduction", "panel_width",
+                                     "ms_per_sweep"],
                          "candidates": [[c["pipeline"], c["warps_per_cta"], c["ctas_per_sm"], c["reduction"],
-                                         c["ms_per_sweep"]] for c in tune_table["candidates"]]},
+                                         c["panel_width"], c["ms_per_sweep"]] for c in tune_table["candidates"]]},
             "mixed_unguarded": {"value": unguarded_value, "unit": "spin-updates/s",
                                 "note": "same path without the double-float re-solve of decisions within 1e-2"},
             "resolved_fraction": resolved_frac,

@@ -299,7 +299,12 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  *                  PTCA_REDUCTION_TILED = register tiles, 4x4
  *                  complex tiles per lane over pairs of block rows, the
  *                  matrix stored as tiles (PTCA_MIXED, 4-warp CTAs, orders
- *                  up to 128, per-stage and overlapped pipelines).
+ *                  up to 128, per-stage and overlapped pipelines);
+ *   panel_width    0 or 1: the unblocked reduction above; 2, 4 or 8: the
+ *                  blocked form, panels of that many reflectors with one
+ *                  rank-2b update of the trailing block per panel (the
+ *                  LAPACK LATRD scheme; PTCA_MIXED, 8-warp CTAs, orders up to
+ *                  128, per-stage and overlapped pipelines, reduction 0).
  * Every configuration computes the same chain (decisions and spins; free
  * energies to rounding). */
 typedef struct {
@@ -307,6 +312,7 @@ typedef struct {
     int32_t warps_per_cta;
     int32_t ctas_per_sm;
     int32_t reduction;
+    int32_t panel_width;
 } ptca_launch_config;
 
 /* Apply a launch configuration.  PTCA_ERR_UNSUPPORTED for a width the
@@ -315,7 +321,7 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
 ptca_status ptca_get_launch_config(const ptca_ctx* ctx, ptca_launch_config* out);
 
 /* Autotuner: times every launch configuration the problem admits (CTA width
- * x pipeline x persistent CTAs per SM x reduction) on this context's own lattice -- one
+ * x pipeline x persistent CTAs per SM x reduction x panel width) on this context's own lattice -- one
  * warm-up sweep and trial_sweeps (1..100) timed sweeps each, CUDA events on
  * `stream` -- restoring the spins and the sweep counter before every trial
  * and at the end, so the chain is left where it was (the per-visit record

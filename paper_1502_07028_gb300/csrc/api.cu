@@ -628,6 +628,7 @@ static cudaError_t launch_stage_ctx(const ptca_ctx* ctx, const StageArgs& a, cud
         return ptca::launch_stage_cluster(ctx->cl_size, a, ctx->cl_grid, st);
     if (ctx->large) return ptca::launch_stage_large(ctx->prec, a, ctx->large_grid, st);
     if (ctx->reduction == 1) return ptca::launch_stage_tiled(a, st);
+    if (ctx->panel > 1) return ptca::launch_stage_panel(ctx->panel, a, st);
     return ptca::launch_stage(ctx->prec, ctx->nw, a, st);
 }
 static cudaError_t launch_resolve_ctx(const ptca_ctx* ctx, const StageArgs& a, cudaStream_t st) {
@@ -1067,6 +1068,7 @@ ptca_status ptca_get_launch_config(const ptca_ctx* ctx, ptca_launch_config* out)
     out->warps_per_cta = ctx->nw;
     out->ctas_per_sm = ctx->ctas_per_sm;
     out->reduction = ctx->reduction;
+    out->panel_width = ctx->panel;
     return PTCA_OK;
 }
 
@@ -1098,6 +1100,14 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
         return fail(PTCA_ERR_UNSUPPORTED,
                     "the register-tiled reduction runs PTCA_MIXED stage kernels of 4-warp CTAs, orders up to 128, "
                     "in the per-stage or overlapped pipeline");
+    if (cfg->panel_width < 0 || cfg->panel_width > 8 || (cfg->panel_width > 1 && (cfg->panel_width & (cfg->panel_width - 1))))
+        return fail(PTCA_ERR_INVALID, "panel_width must be 0, 1, 2, 4 or 8");
+    if (cfg->panel_width > 1 &&
+        (ctx->large || cfg->warps_per_cta != 8 || persistent || cfg->reduction != 0 ||
+         !ptca::panel_supported(ctx->prec, ctx->nA, cfg->panel_width)))
+        return fail(PTCA_ERR_UNSUPPORTED,
+                    "the panel reduction runs PTCA_MIXED stage kernels of 8-warp CTAs, orders up to 128, in the "
+                    "per-stage or overlapped pipeline");
     if (cfg->pipeline == PTCA_PIPELINE_OVERLAP) {
         cudaError_t e = ensure_overlap(ctx);
         if (e != cudaSuccess) return cuda_fail(e, "ptca_set_launch_config (overlapped pipeline)");
@@ -1106,6 +1116,7 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     ctx->nw = cfg->warps_per_cta;
     ctx->ctas_per_sm = cfg->ctas_per_sm;
     ctx->reduction = cfg->reduction;
+    ctx->panel = cfg->panel_width > 1 ? cfg->panel_width : 0;
     ctx->grid = maxb > 0 ? ctx->sms * (cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : maxb) : 0;
     ctx->graph_failed = false;
     drop_graph(ctx);
@@ -1145,9 +1156,15 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
         cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 0});
         if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 0});
         if (nw == 4 && ptca::tiled_supported(ctx->prec, ctx->nA)) {
-            cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 1});
-            if (ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 1});
+            cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 1, 0});
+            if (ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 1, 0});
         }
+        if (nw == 8)
+            for (int b : {2, 4, 8}) {
+                if (!ptca::panel_supported(ctx->prec, ctx->nA, b)) continue;
+                cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 0, b});
+                if (ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 0, b});
+            }
         const int maxb = ptca::persistent_blocks_per_sm(ctx->prec, nw, ctx->nA);
         if (maxb <= 0 || ctx->sg.enabled) continue;
         for (int pl : {PTCA_PIPELINE_PERSISTENT, PTCA_PIPELINE_GRAPH}) {
@@ -1216,15 +1233,16 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
         for (size_t i = 0; i < cand.size(); ++i) {
             std::snprintf(buf, sizeof buf,
                           "%s{\"pipeline\": \"%s\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d, \"reduction\": %d, "
-                          "\"ms_per_sweep\": %s}",
+                          "\"panel_width\": %d, \"ms_per_sweep\": %s}",
                           i ? ", " : "", pipeline_name(cand[i].pipeline), cand[i].warps_per_cta, cand[i].ctas_per_sm,
-                          cand[i].reduction, ms[i] >= 0 ? std::to_string(ms[i]).c_str() : "null");
+                          cand[i].reduction, cand[i].panel_width, ms[i] >= 0 ? std::to_string(ms[i]).c_str() : "null");
             js += buf;
         }
         std::snprintf(buf, sizeof buf,
                       "], \"best\": {\"pipeline\": \"%s\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d, "
-                      "\"reduction\": %d}}",
-                      pipeline_name(chosen.pipeline), chosen.warps_per_cta, chosen.ctas_per_sm, chosen.reduction);
+                      "\"reduction\": %d, \"panel_width\": %d}}",
+                      pipeline_name(chosen.pipeline), chosen.warps_per_cta, chosen.ctas_per_sm, chosen.reduction,
+                      chosen.panel_width);
         js += buf;
         if ((int)js.size() >= json_cap) return fail(PTCA_ERR_INVALID, "json buffer too small");
         std::memcpy(json, js.c_str(), js.size() + 1);

@@ -85,6 +85,7 @@ struct ptca_ctx {
     int pipeline = PTCA_PIPELINE_GRAPH;
     int nw = 8;              // warps per CTA of the sweep kernels (8, or 4 for PTCA_MIXED, n <= 128)
     int reduction = 0;       // 1: the register-tiled FP32 reduction (4-warp stage kernels)
+    int panel = 0;           // > 1: the blocked FP32 reduction in panels of this width (8-warp stage kernels)
     int ctas_per_sm = 0;     // persistent CTAs per SM (0: as many as fit)
     int sms = 0;
     unsigned long long timeout_ns = 30ull * 1000000000ull;

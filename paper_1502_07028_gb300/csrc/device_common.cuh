@@ -40,6 +40,12 @@ template <typename V> __device__ __forceinline__ V cfma_conj_a(V a, V b, V acc) 
     acc.y = fmadd(a.x, b.y, acc.y); acc.y = fmadd(-a.y, b.x, acc.y);
     return acc;
 }
+// acc - a * b
+template <typename V> __device__ __forceinline__ V cfms(V a, V b, V acc) {
+    acc.x = fmadd(-a.x, b.x, acc.x); acc.x = fmadd(a.y, b.y, acc.x);
+    acc.y = fmadd(-a.x, b.y, acc.y); acc.y = fmadd(-a.y, b.x, acc.y);
+    return acc;
+}
 // acc - a * conj(b)
 template <typename V> __device__ __forceinline__ V cfms_conj_b(V a, V b, V acc) {
     acc.x = fmadd(-a.x, b.x, acc.x); acc.x = fmadd(-a.y, b.y, acc.x);

@@ -5,6 +5,7 @@
 #include <type_traits>
 
 #include "cluster_solve.cuh"
+#include "cluster_panel.cuh"
 #include "cluster_tiled.cuh"
 #include "surrogate.cuh"
 
@@ -417,12 +418,16 @@ __device__ __forceinline__ void collect_sample(const StageArgs& a, const double*
 // Metropolis.  Called by all threads of the CTA; s_new and s_last are shared.
 //
 // kTiled (FP32, 4 warps, orders up to 128): the matrix in the tiled layout and
-// the register-tiled reduction (householder_tridiag_tiled).
-template <typename T, int NT, int NWP, bool kLarge = false, bool kTiled = false>
+// the register-tiled reduction (householder_tridiag_tiled).  kPanel = B > 1
+// (FP32, 8 warps, orders up to 128): the blocked reduction in panels of B
+// reflectors (householder_tridiag_panel), its panel vectors past the layout.
+template <typename T, int NT, int NWP, bool kLarge = false, bool kTiled = false, int kPanel = 0>
 __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v, int c, int var, unsigned char* smem,
                                            double* s_new, int* s_last) {
     static_assert(!kTiled || (std::is_same<T, float>::value && NWP == TL_NW && 32 * NT <= TL_NMAX && !kLarge),
                   "the tiled reduction is FP32, 4 warps, orders up to 128");
+    static_assert(kPanel <= 1 || (std::is_same<T, float>::value && NWP == PN_NW && NT <= 4 && !kLarge && !kTiled),
+                  "the panel reduction is FP32, 8 warps, orders up to 128");
     const SmemLayout L = kTiled ? smem_layout_tiled() : smem_layout(kLarge ? 0 : a.nA, 32 * NT, sizeof(cplx_t<T>), NWP);
     Carve<T> cv = carve<T>(smem, L, NWP);
     if constexpr (kLarge) cv.A = static_cast<cplx_t<T>*>(a.gL) + (int64_t)blockIdx.x * a.gL_stride;
@@ -458,6 +463,11 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
         __syncthreads();
     } else if constexpr (kLarge) {
         householder_tridiag_large<T, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
+    } else if constexpr (kPanel > 1) {
+        float2* PV = reinterpret_cast<float2*>(smem + L.total);
+        float2* PW = PV + kPanel * 32 * NT;
+        float2* dotw = PW + kPanel * 32 * NT;
+        householder_tridiag_panel<NT, kPanel>(n, cv.A, cv.hh, PV, PW, dotw, cv.d, cv.e2);
     } else {
         householder_tridiag<T, NT, NWP>(n, cv.A, cv.hh, cv.d, cv.e2);
     }
@@ -511,7 +521,7 @@ __device__ __forceinline__ void stage_item(const StageArgs& a, const StageVar v,
     atomicAdd(&a.counters[1], 2ull);
 }
 
-template <typename T, int NT, int NWP = NW, bool kTiled = false>
+template <typename T, int NT, int NWP = NW, bool kTiled = false, int kPanel = 0>
 __global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value) k_stage(StageArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_new[3];
@@ -526,7 +536,7 @@ __global__ void __launch_bounds__(32 * NWP, MinBlocks<T, NT, NWP>::value) k_stag
     const int c = blockIdx.x >> 1, var = blockIdx.x & 1;
     const int count = a.count_dev ? (int)*a.count_dev : a.count;
     if (c >= count) return;
-    stage_item<T, NT, NWP, false, kTiled>(a, stage_var(a), c, var, smem, s_new, &s_last);
+    stage_item<T, NT, NWP, false, kTiled, kPanel>(a, stage_var(a), c, var, smem, s_new, &s_last);
 }
 
 template <typename T, int NT>

@@ -48,6 +48,12 @@ bool tiled_supported(int prec, int nA);
 size_t tiled_smem_bytes();
 cudaError_t configure_tiled_kernels(size_t smem_limit);
 cudaError_t launch_stage_tiled(const StageArgs& a, cudaStream_t st);
+// The FP32 8-warp stage kernels with the blocked (panel) reduction, panels of
+// B = 2, 4 or 8 reflectors (orders up to 128).
+bool panel_supported(int prec, int nA, int B);
+size_t panel_smem_bytes(int B);
+cudaError_t configure_panel_kernels(size_t smem_limit);
+cudaError_t launch_stage_panel(int B, const StageArgs& a, cudaStream_t st);
 // Persistent sweep kernel: grid CTAs (all co-resident; cooperative launch).
 cudaError_t launch_persistent(int prec, int nw, const PersistArgs& p, int grid, cudaStream_t st);
 // CTAs of the persistent kernel that fit on one SM for matrices up to nA.

@@ -28,6 +28,8 @@ def parser() -> argparse.ArgumentParser:
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: as many as fit)")
     ap.add_argument("--reduction", choices=["rows", "tiled"], default="rows",
                     help="FP32 Householder pass: lanes on columns (rows) or 4x4 register tiles (tiled; 4 warps)")
+    ap.add_argument("--panel", type=int, choices=[0, 2, 4, 8], default=0,
+                    help="blocked FP32 reduction in panels of this many reflectors (8 warps; 0: unblocked)")
     ap.add_argument("--margin", type=float, default=None, help="mixed-mode re-solve margin (0 = off)")
     ap.add_argument("--sweeps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=0)
@@ -73,7 +75,7 @@ def main(argv=None):
     ctx = P.Context(cfg)
     P.ptca_set_launch_config(ctx.h, {"stages": P.PIPELINE_STAGES, "persistent": P.PIPELINE_PERSISTENT,
                                      "graph": P.PIPELINE_GRAPH, "overlap": P.PIPELINE_OVERLAP}[a.pipeline], a.warps, a.ctas_per_sm,
-                              P.REDUCTION_TILED if a.reduction == "tiled" else P.REDUCTION_ROWS)
+                              P.REDUCTION_TILED if a.reduction == "tiled" else P.REDUCTION_ROWS, a.panel)
     if a.margin is not None and cfg.precision == P.MIXED:
         P.ptca_set_resolve_margin(ctx.h, a.margin)
     if a.full_spectrum:
@@ -104,7 +106,7 @@ def main(argv=None):
     torch.cuda.nvtx.range_push("timed")  # profilers can restrict a capture to the timed sweeps (ncu --nvtx)
     st = ctx.sweep(a.sweeps)
     torch.cuda.nvtx.range_pop()
-    print(f"{a.precision} {a.model} L={a.L} Lz={a.Lz} Lc={a.Lc} {a.schedule} {a.pipeline} {a.warps} warps {a.reduction}: {st.seconds * 1e3:.3f} ms for "
+    print(f"{a.precision} {a.model} L={a.L} Lz={a.Lz} Lc={a.Lc} {a.schedule} {a.pipeline} {a.warps} warps {a.reduction} panel {a.panel}: {st.seconds * 1e3:.3f} ms for "
           f"{a.sweeps} sweep(s), "
           f"{cfg.N * a.sweeps / st.seconds:.0f} spin-updates/s, accepted {st.accepted}, resolved {st.resolved}, "
           f"screened {st.screened}")

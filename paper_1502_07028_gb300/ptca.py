@@ -47,7 +47,7 @@ class PtcaError(RuntimeError):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pipeline", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("reduction", ctypes.c_int32)]
+                ("reduction", ctypes.c_int32), ("panel_width", ctypes.c_int32)]
 
 
 class Lattice(ctypes.Structure):
@@ -381,8 +381,10 @@ def ptca_set_resolve_margin(h, margin: float) -> None:
     _check(lib().ptca_set_resolve_margin(h, margin))
 
 
-def ptca_set_launch_config(h, pipeline: int, warps_per_cta: int = 8, ctas_per_sm: int = 0, reduction: int = 0) -> None:
-    _check(lib().ptca_set_launch_config(h, ctypes.byref(LaunchConfig(pipeline, warps_per_cta, ctas_per_sm, reduction))))
+def ptca_set_launch_config(h, pipeline: int, warps_per_cta: int = 8, ctas_per_sm: int = 0, reduction: int = 0,
+                           panel_width: int = 0) -> None:
+    _check(lib().ptca_set_launch_config(h, ctypes.byref(LaunchConfig(pipeline, warps_per_cta, ctas_per_sm, reduction,
+                                                                     panel_width))))
 
 
 def ptca_get_launch_config(h) -> LaunchConfig:
