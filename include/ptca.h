@@ -545,7 +545,9 @@ ptca_status ptca_sweep_noalloc(const ptca_lattice* lattice, const ptca_params* p
  * diagonalises saved configurations of the whole system with ScaLAPACK
  * (Sec. VI); here the dense 2N x 2N matrix is built on the device, reduced to
  * real tridiagonal form by this library's Householder reduction spread over
- * the whole GPU (FP64, one pass over the trailing triangle per reflector),
+ * the whole GPU (one pass over the trailing triangle per reflector: FP64 for
+ * a PTCA_FP64 context; double-float, about 48 significant bits on the FP32
+ * pipe, for a PTCA_MIXED context, with the per-reflector scalars in FP64),
  * and its eigenvalues found one thread each (FP32 bisection finished by
  * double-float Sturm counts and Newton).  No library eigensolver is used.
  *   eig_out  device double[2N]

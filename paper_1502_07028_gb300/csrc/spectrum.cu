@@ -1,7 +1,9 @@
 // spectrum.cu -- full-system spectrum of a configuration (Sec. VI): all 2N
 // eigenvalues of the whole lattice's one-body Hamiltonian, where the paper
 // diagonalises saved configurations with ScaLAPACK.  Everything runs in this
-// library's kernels, in FP64, off the sweep's hot path:
+// library's kernels, off the sweep's hot path (FP64 throughout for FP64
+// contexts; a PTCA_MIXED context runs step 2's O(n^3) pass in double-float
+// on the FP32 pipe):
 //   1. the dense matrix is built as its packed lower triangle (row-major:
 //      element (i, j <= i) at i(i+1)/2 + j) in global memory;
 //   2. a Householder reduction to real tridiagonal form spread over the whole
@@ -16,6 +18,7 @@
 //   3. one thread per eigenvalue: FP32 bisection on the FP32-rounded
 //      tridiagonal, then the cluster solver's double-float Sturm counts and
 //      safeguarded Newton on the exact (FP64) tridiagonal.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <string>
@@ -69,23 +72,43 @@ __global__ void k_full_hamiltonian(Model m, const double* __restrict__ S, int N,
     }
 }
 
+// The reduction runs in the real arithmetic R: double, or dfl (double-float:
+// about 48 significant bits on the FP32 pipe, which runs 64 times the FP64
+// rate).  A complex entry takes 16 bytes and a real one 8 in either, so the
+// buffers are the same.
+__device__ __forceinline__ double fs_d(double x) { return x; }
+__device__ __forceinline__ double fs_d(dfl x) { return (double)x; }
+template <typename R> __device__ __forceinline__ R fs_r(float x);
+template <> __device__ __forceinline__ double fs_r<double>(float x) { return (double)x; }
+template <> __device__ __forceinline__ dfl fs_r<dfl>(float x) { return dfl(x, 0.f); }
+
+// The built FP64 matrix rewritten in place as double-float pairs.
+__global__ void k_fs_to_dfl(double2* A, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 x = A[i];
+        reinterpret_cast<dfl2*>(A)[i] = mk(dfl(x.x), dfl(x.y));
+    }
+}
+
 // Buffers of the reduction.  Reflector k acts on rows/columns k+1 .. n-1;
 // its first entry is stored at index k+1 like the others.
+template <typename R>
 struct FsArgs {
+    using C = cplx_t<R>;
     int n;
-    double2* A;
-    const double2* U;   // v_{k-1} (zero at k = 0)
-    const double2* V;   // v_k
-    double2* Vn;        // v_{k+1}, written by the scalar phase of step k
-    const double2* W;   // w_{k-1} (zero at k = 0)
-    double2* Wn;        // w_k, written by the scalar phase of step k
-    double2* pr;        // [T][n] row partial sums of A v_k, by tile column
-    double2* pc;        // [T][n] column partial sums, by tile row
-    double2* p;         // [n]    tau A v_k
-    double* red;        // [blocks of the reduction] partial sums of Re(v^H p)
-    double* tau;        // [2]    tau_k in tau[k & 1]
-    double* d;          // [n]
-    double* e2;         // [n]
+    C* A;
+    const C* U;   // v_{k-1} (zero at k = 0)
+    const C* V;   // v_k
+    C* Vn;        // v_{k+1}, written by the scalar phase of step k
+    const C* W;   // w_{k-1} (zero at k = 0)
+    C* Wn;        // w_k, written by the scalar phase of step k
+    C* pr;        // [T][n] row partial sums of A v_k, by tile column
+    C* pc;        // [T][n] column partial sums, by tile row
+    C* p;         // [n]    tau A v_k
+    R* red;       // [blocks of the reduction] partial sums of Re(v^H p)
+    R* tau;       // [2]    tau_k in tau[k & 1]
+    double* d;    // [n]
+    double* e2;   // [n]
 };
 
 // Step k's pass over the trailing block (rows and columns j0 = k+1 .. n-1),
@@ -93,9 +116,15 @@ struct FsArgs {
 // with step k-1's (u, w), then the tile's row sums of A v (into pr[tile
 // column][row]) and, below the diagonal, column sums of A^H v (into
 // pc[tile row][column]).  Warp q takes rows q, q+8, ...; lanes take columns
-// lane and lane + 32 of the tile.
-__global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs a, int k) {
-    __shared__ double2 csum[FS_PASS_THREADS / 32][FS_TB];
+// lane and lane + 32 of the tile.  Each lane's row partials go to shared
+// memory and four threads per row add them up (eight each, then across the
+// four), in a fixed order.
+constexpr int FS_RS_LD = 33;  // row stride of the row partials (16-byte entries)
+template <typename R>
+__global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs<R> a, int k) {
+    using C = cplx_t<R>;
+    __shared__ C rsum[FS_TB][FS_RS_LD];
+    __shared__ C csum[FS_PASS_THREADS / 32][FS_TB];
     const int n = a.n, j0 = k + 1, m = n - j0;
     const int64_t b = blockIdx.x;
     int TR = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
@@ -103,9 +132,10 @@ __global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs a, int k) {
     while (tri64(TR) > b) --TR;
     const int TC = (int)(b - tri64(TR));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double2 zero = make_double2(0.0, 0.0);
+    const R r0 = fs_r<R>(0.f);
+    const C zero = mk(r0, r0);
     int cr[2];
-    double2 vc[2], uc[2], wc[2], cacc[2];
+    C vc[2], uc[2], wc[2], cacc[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         cr[q] = FS_TB * TC + lane + 32 * q;
@@ -120,35 +150,45 @@ __global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs a, int k) {
         const int ri = FS_TB * TR + rr;
         if (ri >= m) break;
         const int i = j0 + ri;
-        const double2 ui = a.U[i], wi = a.W[i], vi = a.V[i];
-        double2* row = a.A + tri64(i) + j0;
-        double2 racc = zero;
+        const C ui = a.U[i], wi = a.W[i], vi = a.V[i];
+        C* row = a.A + tri64(i) + j0;
+        C racc = zero;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int c = cr[q];
             if (c <= ri) {
-                double2 x = row[c];
+                C x = row[c];
                 x = cfms_conj_b(ui, wc[q], x);
                 x = cfms_conj_b(wi, uc[q], x);
-                if (c == ri) x.y = 0.0;  // the diagonal stays real
+                if (c == ri) x.y = r0;  // the diagonal stays real
                 row[c] = x;
                 racc = cfma(x, vc[q], racc);
                 if (c < ri) cacc[q] = cfma_conj_a(x, vi, cacc[q]);
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) racc = cadd(racc, cshfl_xor(racc, o));
-        if (lane == 0) a.pr[(int64_t)TC * n + ri] = racc;
+        rsum[rr][lane] = racc;
     }
     csum[warp][lane] = cacc[0];
     csum[warp][lane + 32] = cacc[1];
     __syncthreads();
-    if (threadIdx.x < FS_TB) {
-        double2 s = csum[0][threadIdx.x];
+    {
+        const int rr = threadIdx.x >> 2, part = threadIdx.x & 3, ri = FS_TB * TR + rr;
+        C sum = zero;
+        if (ri < m) {
+            sum = rsum[rr][part];
 #pragma unroll
-        for (int w = 1; w < FS_PASS_THREADS / 32; ++w) s = cadd(s, csum[w][threadIdx.x]);
+            for (int j = 1; j < 8; ++j) sum = cadd(sum, rsum[rr][part + 4 * j]);
+        }
+        sum = cadd(sum, cshfl_xor(sum, 1));
+        sum = cadd(sum, cshfl_xor(sum, 2));
+        if (part == 0 && ri < m) a.pr[(int64_t)TC * n + ri] = sum;
+    }
+    if (threadIdx.x < FS_TB) {
+        C sum = csum[0][threadIdx.x];
+#pragma unroll
+        for (int w = 1; w < FS_PASS_THREADS / 32; ++w) sum = cadd(sum, csum[w][threadIdx.x]);
         const int c = FS_TB * TC + threadIdx.x;
-        if (c < m) a.pc[(int64_t)TR * n + c] = s;
+        if (c < m) a.pc[(int64_t)TR * n + c] = sum;
     }
 }
 
@@ -156,56 +196,50 @@ __global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs a, int k) {
 // tiles (B, 0 .. B) plus the column partials of tiles (B .. T-1, B) (the
 // diagonal tile's column sums hold the elements below the diagonal), in a
 // fixed order; and each CTA's partial sum of Re(v^H p).
-__global__ void __launch_bounds__(FS_RED_THREADS) k_fs_reduce(FsArgs a, int k) {
-    __shared__ double red[FS_RED_THREADS / 32];
+template <typename R>
+__global__ void __launch_bounds__(FS_RED_THREADS) k_fs_reduce(FsArgs<R> a, int k) {
+    using C = cplx_t<R>;
+    __shared__ R red[FS_RED_THREADS / 32];
     const int n = a.n, j0 = k + 1, m = n - j0, T = (m + FS_TB - 1) / FS_TB;
     const int ri = blockIdx.x * blockDim.x + threadIdx.x;
-    double sp = 0.0;
+    R sp = fs_r<R>(0.f);
     if (ri < m) {
         const int band = ri / FS_TB;
-        double2 s = make_double2(0.0, 0.0);
+        C s = mk(sp, sp);
         for (int tc = 0; tc <= band; ++tc) s = cadd(s, a.pr[(int64_t)tc * n + ri]);
         for (int tr = band; tr < T; ++tr) s = cadd(s, a.pc[(int64_t)tr * n + ri]);
-        const double tau = a.tau[k & 1];
-        s.x *= tau;
-        s.y *= tau;
+        const R tau = a.tau[k & 1];
+        s.x = s.x * tau;
+        s.y = s.y * tau;
         a.p[j0 + ri] = s;
-        const double2 v = a.V[j0 + ri];
+        const C v = a.V[j0 + ri];
         sp = v.x * s.x + v.y * s.y;
     }
-    sp = block_sum<double>(sp, red);
+    sp = block_sum<R>(sp, red);
     if (threadIdx.x == 0) a.red[blockIdx.x] = sp;
 }
 
-// Next reflector from the updated pivot column j (entries j+1 .. n-1 in the
-// thread-strided loop of the caller): given ||x||^2 and x_0, its first entry
-// x_0 + phase(x_0) ||x|| and tau = 1 / (||x|| (||x|| + |x_0|)).
-__device__ __forceinline__ void fs_reflector_head(double s2, double2 x0, double2& first, double& tau) {
-    const double sigma = sqrt(s2), ax0 = sqrt(x0.x * x0.x + x0.y * x0.y);
-    const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-    first = make_double2(x0.x + ph.x * sigma, x0.y + ph.y * sigma);
-    tau = sigma > 0.0 ? 1.0 / (sigma * (sigma + ax0)) : 0.0;
-}
-
 // Column 0: d_0, ||x||^2 and the first reflector (one CTA).
-__global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_setup(FsArgs a) {
-    __shared__ double red[FS_SCALAR_THREADS / 32];
-    __shared__ double2 s_x0;
+template <typename R>
+__global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_setup(FsArgs<R> a) {
+    using C = cplx_t<R>;
+    __shared__ R red[FS_SCALAR_THREADS / 32];
+    __shared__ C s_x0;
     const int n = a.n;
-    double s2 = 0.0;
+    R s2 = fs_r<R>(0.f);
     for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
-        const double2 x = a.A[tri64(i)];
-        s2 += x.x * x.x + x.y * x.y;
+        const C x = a.A[tri64(i)];
+        s2 = s2 + cabs2(x);
         if (i >= 2) a.Vn[i] = x;
         if (i == 1) s_x0 = x;
     }
-    s2 = block_sum<double>(s2, red);
+    s2 = block_sum<R>(s2, red);
     if (threadIdx.x == 0) {
-        a.d[0] = a.A[0].x;
-        a.e2[0] = s2;
-        double2 f;
-        double tau;
-        fs_reflector_head(s2, s_x0, f, tau);
+        a.d[0] = fs_d(a.A[0].x);
+        a.e2[0] = fs_d(s2);
+        C f;
+        R tau;
+        reflector_head<R>(s2, s_x0, f, tau);
         a.Vn[1] = f;
         a.tau[0] = tau;
     }
@@ -214,40 +248,42 @@ __global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_setup(FsArgs a) {
 // Step k's scalar phase (one CTA): w = p - (tau/2)(v^H p) v; the explicit
 // update of pivot column j0 = k+1 with (v_k, w_k); d_j0, e2_j0 and, unless
 // this was the last reflector, the next reflector v_{k+1} and tau_{k+1}.
-__global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_scalar(FsArgs a, int k, int nred) {
-    __shared__ double red[FS_SCALAR_THREADS / 32];
-    __shared__ double s_K;
-    __shared__ double2 s_x0;
+template <typename R>
+__global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_scalar(FsArgs<R> a, int k, int nred) {
+    using C = cplx_t<R>;
+    __shared__ R red[FS_SCALAR_THREADS / 32];
+    __shared__ R s_K;
+    __shared__ C s_x0;
     const int n = a.n, j0 = k + 1;
-    double sp = 0.0;
-    for (int b = threadIdx.x; b < nred; b += blockDim.x) sp += a.red[b];
-    sp = block_sum<double>(sp, red);
-    if (threadIdx.x == 0) s_K = 0.5 * a.tau[k & 1] * sp;
+    R sp = fs_r<R>(0.f);
+    for (int b = threadIdx.x; b < nred; b += blockDim.x) sp = sp + a.red[b];
+    sp = block_sum<R>(sp, red);
+    if (threadIdx.x == 0) s_K = fs_r<R>(0.5f) * a.tau[k & 1] * sp;
     __syncthreads();
-    const double K = s_K;
-    const double2 vf = a.V[j0];
-    const double2 p0 = a.p[j0];
-    const double2 w0 = make_double2(p0.x - K * vf.x, p0.y - K * vf.y);
-    double s2 = 0.0;
+    const R K = s_K;
+    const C vf = a.V[j0];
+    const C p0 = a.p[j0];
+    const C w0 = mk(p0.x - K * vf.x, p0.y - K * vf.y);
+    R s2 = fs_r<R>(0.f);
     for (int i = j0 + threadIdx.x; i < n; i += blockDim.x) {
-        const double2 v = a.V[i], pi = a.p[i];
-        const double2 w = make_double2(pi.x - K * v.x, pi.y - K * v.y);
+        const C v = a.V[i], pi = a.p[i];
+        const C w = mk(pi.x - K * v.x, pi.y - K * v.y);
         a.Wn[i] = w;
-        double2 x = a.A[tri64(i) + j0];
+        C x = a.A[tri64(i) + j0];
         x = cfms_conj_b(v, w0, x);
         x = cfms_conj_b(w, vf, x);
-        if (i == j0) a.d[j0] = x.x;
-        if (i >= j0 + 1) s2 += x.x * x.x + x.y * x.y;
+        if (i == j0) a.d[j0] = fs_d(x.x);
+        if (i >= j0 + 1) s2 = s2 + cabs2(x);
         if (i >= j0 + 2) a.Vn[i] = x;
         if (i == j0 + 1) s_x0 = x;
     }
-    s2 = block_sum<double>(s2, red);
+    s2 = block_sum<R>(s2, red);
     if (threadIdx.x == 0) {
-        a.e2[j0] = s2;
+        a.e2[j0] = fs_d(s2);
         if (k + 1 <= n - 3) {
-            double2 f;
-            double tau;
-            fs_reflector_head(s2, s_x0, f, tau);
+            C f;
+            R tau;
+            reflector_head<R>(s2, s_x0, f, tau);
             a.Vn[j0 + 1] = f;
             a.tau[(k + 1) & 1] = tau;
         }
@@ -256,10 +292,11 @@ __global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_scalar(FsArgs a, int k
 
 // The last diagonal entry: step n-3's update of A_{n-1,n-1} (V = v_{n-3},
 // W = w_{n-3}).
-__global__ void k_fs_finish(FsArgs a) {
+template <typename R>
+__global__ void k_fs_finish(FsArgs<R> a) {
     const int n = a.n;
-    const double2 v = a.V[n - 1], w = a.W[n - 1];
-    a.d[n - 1] = a.A[tri64(n - 1) + n - 1].x - 2.0 * (v.x * w.x + v.y * w.y);
+    const auto v = a.V[n - 1], w = a.W[n - 1];
+    a.d[n - 1] = fs_d(a.A[tri64(n - 1) + n - 1].x - fs_r<R>(2.f) * (v.x * w.x + v.y * w.y));
 }
 
 // Gershgorin bracket and Sturm-count guards of the tridiagonal (d, e2), and
@@ -318,6 +355,61 @@ __global__ void __launch_bounds__(FS_EIG_THREADS) k_fs_eig(int n, const float* _
         else b = mid;
     }
     eig[k] = eig_df_bracketed(n, df, dlo, e2f, e2lo, k, a, b, 8.0 * FLT_EPSILON * nrm, lo, hi, pivminf, nrm);
+}
+
+// Reduction of the packed matrix A (in R's complex form) to the real
+// tridiagonal (d, e2), enqueued on st.  The buffers are those of FsArgs, as
+// raw device memory; v_k sits in vb[k mod 3] and w_k in wb[k mod 2], and
+// v_{-1} = vb[2] and w_{-1} = wb[1] start at zero.
+template <typename R>
+static cudaError_t fs_tridiagonalise(int n, void* A, void* vb_, void* wb_, void* pr, void* pc, void* p, void* red,
+                                     void* tau, double* d, double* e2, cudaStream_t st) {
+    using C = cplx_t<R>;
+    FsArgs<R> a;
+    a.n = n;
+    a.A = static_cast<C*>(A);
+    a.pr = static_cast<C*>(pr);
+    a.pc = static_cast<C*>(pc);
+    a.p = static_cast<C*>(p);
+    a.red = static_cast<R*>(red);
+    a.tau = static_cast<R*>(tau);
+    a.d = d;
+    a.e2 = e2;
+    C* vb = static_cast<C*>(vb_);
+    C* wb = static_cast<C*>(wb_);
+    if (n == 2) {
+        // d_0, d_1 and |e_0|^2 straight from the 2x2 matrix
+        a.U = a.V = vb; a.Vn = vb; a.W = wb; a.Wn = wb;
+        k_fs_setup<R><<<1, FS_SCALAR_THREADS, 0, st>>>(a);
+        a.V = vb + n; a.W = wb;  // zero vectors: the finish reads A_11 unchanged
+        k_fs_finish<R><<<1, 1, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    a.Vn = vb;
+    a.U = vb + 2 * (size_t)n;
+    a.W = wb + n;
+    a.V = vb;
+    a.Wn = wb;
+    k_fs_setup<R><<<1, FS_SCALAR_THREADS, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    for (int k = 0; k <= n - 3 && e == cudaSuccess; ++k) {
+        const int mm = n - k - 1, T = (mm + FS_TB - 1) / FS_TB;
+        a.U = vb + (size_t)((k + 2) % 3) * n;
+        a.V = vb + (size_t)(k % 3) * n;
+        a.Vn = vb + (size_t)((k + 1) % 3) * n;
+        a.W = wb + (size_t)((k + 1) & 1) * n;
+        a.Wn = wb + (size_t)(k & 1) * n;
+        k_fs_pass<R><<<(unsigned)tri64(T), FS_PASS_THREADS, 0, st>>>(a, k);
+        const int nred = (mm + FS_RED_THREADS - 1) / FS_RED_THREADS;
+        k_fs_reduce<R><<<nred, FS_RED_THREADS, 0, st>>>(a, k);
+        k_fs_scalar<R><<<1, FS_SCALAR_THREADS, 0, st>>>(a, k, nred);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    a.V = vb + (size_t)((n - 3) % 3) * n;
+    a.W = wb + (size_t)((n - 3) & 1) * n;
+    k_fs_finish<R><<<1, 1, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace ptca
@@ -382,41 +474,15 @@ extern "C" ptca_status ptca_full_spectrum(ptca_ctx* ctx, double* eig_out, void* 
     k_full_hamiltonian<<<(N + 255) / 256, 256, 0, st>>>(m, ctx->d_S[0], N, A);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "building the matrix");
 
-    FsArgs a;
-    a.n = n; a.A = A; a.pr = pr; a.pc = pc; a.p = p; a.red = red; a.tau = tau; a.d = d; a.e2 = e2;
-    if (n == 2) {
-        // d_0, d_1 and |e_0|^2 straight from the 2x2 matrix
-        a.U = a.V = vb; a.Vn = vb; a.W = wb; a.Wn = wb;
-        k_fs_setup<<<1, FS_SCALAR_THREADS, 0, st>>>(a);
-        a.V = vb + n; a.W = wb;  // zero vectors: the finish reads A_11 unchanged
-        k_fs_finish<<<1, 1, 0, st>>>(a);
+    if (ctx->prec == 1) {
+        // PTCA_MIXED: the reduction in double-float
+        const int64_t cnt = tri64(n) + 64;
+        k_fs_to_dfl<<<(unsigned)std::min<int64_t>((cnt + 255) / 256, 152 * 16), 256, 0, st>>>(A, cnt);
+        e = fs_tridiagonalise<dfl>(n, A, vb, wb, pr, pc, p, red, tau, d, e2, st);
     } else {
-        // v_k in vb[k mod 3], w_k in wb[k mod 2]; v_{-1} = vb[2] and w_{-1}
-        // = wb[1] start at zero.
-        a.Vn = vb;
-        a.U = vb + 2 * (size_t)n;
-        a.W = wb + n;
-        a.V = vb;
-        a.Wn = wb;
-        k_fs_setup<<<1, FS_SCALAR_THREADS, 0, st>>>(a);
-        for (int k = 0; k <= n - 3 && e == cudaSuccess; ++k) {
-            const int mm = n - k - 1, T = (mm + FS_TB - 1) / FS_TB;
-            a.U = vb + (size_t)((k + 2) % 3) * n;
-            a.V = vb + (size_t)(k % 3) * n;
-            a.Vn = vb + (size_t)((k + 1) % 3) * n;
-            a.W = wb + (size_t)((k + 1) & 1) * n;
-            a.Wn = wb + (size_t)(k & 1) * n;
-            k_fs_pass<<<(unsigned)tri64(T), FS_PASS_THREADS, 0, st>>>(a, k);
-            const int nred = (mm + FS_RED_THREADS - 1) / FS_RED_THREADS;
-            k_fs_reduce<<<nred, FS_RED_THREADS, 0, st>>>(a, k);
-            k_fs_scalar<<<1, FS_SCALAR_THREADS, 0, st>>>(a, k, nred);
-            e = cudaGetLastError();
-        }
-        if (e != cudaSuccess) return fail(e, "reducing to tridiagonal form");
-        a.V = vb + (size_t)((n - 3) % 3) * n;
-        a.W = wb + (size_t)((n - 3) & 1) * n;
-        k_fs_finish<<<1, 1, 0, st>>>(a);
+        e = fs_tridiagonalise<double>(n, A, vb, wb, pr, pc, p, red, tau, d, e2, st);
     }
+    if (e != cudaSuccess) return fail(e, "reducing to tridiagonal form");
     float* df = f32;
     float* dlo = f32 + n;
     float* e2f = f32 + 2 * (size_t)n;

@@ -2,7 +2,9 @@
 one-body Hamiltonian for the current configuration, against the oracle's
 dense matrix of a window that covers the whole lattice (L_c = L), for each
 model, open and periodic edges, a cube, a periodic axis of extent 2, a
-two-site chain, and an order (2048) where the reduction runs over many tiles."""
+two-site chain, and an order (2048) where the reduction runs over many tiles.
+FP64 contexts reduce in FP64; PTCA_MIXED contexts run the reduction's pass
+in double-float (about 48 significant bits) and are held to the same bound."""
 import numpy as np
 import pytest
 import torch
@@ -51,8 +53,9 @@ def _reference(cfg, S):
     dict(cfg=dict(Lx=3, Ly=1, L_c=3, periodic=0), fields="unit"),
     dict(cfg=dict(Lx=10, Ly=7, L_c=3, periodic=0, schedule=P.SCHEDULE_BLOCK), fields="unit"),
 ])
-def test_full_spectrum_matches_the_oracle(case):
-    cfg = P.Config(**case["cfg"])
+@pytest.mark.parametrize("precision", [P.FP64, P.MIXED])
+def test_full_spectrum_matches_the_oracle(case, precision):
+    cfg = P.Config(**case["cfg"], precision=precision)
     if case["fields"] == "unit":
         S = inputs.random_unit_spins(100 + cfg.N, cfg.N)
     elif case["fields"] == "free":
@@ -76,10 +79,11 @@ def test_full_spectrum_rejects_lattices_beyond_its_limit():
     ctx.close()
 
 
-def test_full_spectrum_at_order_2048_matches_lapack():
+@pytest.mark.parametrize("precision", [P.FP64, P.MIXED])
+def test_full_spectrum_at_order_2048_matches_lapack(precision):
     # 32x32 torus (n = 2048): 32 x 32 tiles of the reduction pass in its first
     # steps; checked against LAPACK's eigvalsh of the oracle's dense matrix.
-    cfg = P.Config(Lx=32, Ly=32, L_c=4)
+    cfg = P.Config(Lx=32, Ly=32, L_c=4, precision=precision)
     S = inputs.random_unit_spins(7, cfg.N)
     got = _spectrum(cfg, S)
     m = oracle.Model(Lx=32, Ly=32, Lc=32, schedule=oracle.SCHEDULE_BLOCK)
