@@ -35,7 +35,8 @@ __host__ __device__ __forceinline__ int64_t tri64(int64_t r) { return r * (r + 1
 
 constexpr int FS_TB = 64;          // tile edge of the reduction pass
 constexpr int FS_PASS_THREADS = 256;
-constexpr int FS_RED_THREADS = 256;
+constexpr int FS_RED_THREADS = 256;  // 8 warps; each CTA sums the partials of FS_RED_ROWS rows
+constexpr int FS_RED_ROWS = 32;
 constexpr int FS_SCALAR_THREADS = 1024;
 constexpr int FS_EIG_THREADS = 128;
 
@@ -116,18 +117,22 @@ struct FsArgs {
 // with step k-1's (u, w), then the tile's row sums of A v (into pr[tile
 // column][row]) and, below the diagonal, column sums of A^H v (into
 // pc[tile row][column]).  Warp q takes rows q, q+8, ...; lanes take columns
-// lane and lane + 32 of the tile.  Each lane's row partials go to shared
+// lane and lane + 32 of the tile.  The tile's row entries of u, w and v are
+// staged in shared memory, and a warp loads its next row's elements before
+// it updates the current one (the pass is bound by instruction issue once
+// the loads are in flight early).  Each lane's row partials go to shared
 // memory and four threads per row add them up (eight each, then across the
 // four), in a fixed order.
 constexpr int FS_RS_LD = 33;  // row stride of the row partials (16-byte entries)
 template <typename R>
-__global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs<R> a, int k) {
+__global__ void __launch_bounds__(FS_PASS_THREADS, 3) k_fs_pass(FsArgs<R> a, int k) {
     using C = cplx_t<R>;
     __shared__ C rsum[FS_TB][FS_RS_LD];
     __shared__ C csum[FS_PASS_THREADS / 32][FS_TB];
+    __shared__ C svec[3][FS_TB];
     const int n = a.n, j0 = k + 1, m = n - j0;
     const int64_t b = blockIdx.x;
-    int TR = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    int TR = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);  // corrected below
     while (tri64(TR + 1) <= b) ++TR;
     while (tri64(TR) > b) --TR;
     const int TC = (int)(b - tri64(TR));
@@ -146,18 +151,38 @@ __global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs<R> a, int k)
         wc[q] = in ? a.W[j] : zero;
         cacc[q] = zero;
     }
+    // the tile's row entries of u, w and v, staged once
+    for (int t = threadIdx.x; t < 3 * FS_TB; t += FS_PASS_THREADS) {
+        const int r = t % FS_TB, ri = FS_TB * TR + r;
+        const C* src = t < FS_TB ? a.U : (t < 2 * FS_TB ? a.W : a.V);
+        svec[t / FS_TB][r] = ri < m ? src[j0 + ri] : zero;
+    }
+    __syncthreads();
+    // the next row's elements are loaded before the current row is updated
+    C xa[2], xb[2] = {zero, zero};
+    {
+        const int ri = FS_TB * TR + warp;
+        const C* row = a.A + tri64(j0 + ri) + j0;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) xa[q] = (ri < m && cr[q] <= ri) ? row[cr[q]] : zero;
+    }
     for (int rr = warp; rr < FS_TB; rr += FS_PASS_THREADS / 32) {
         const int ri = FS_TB * TR + rr;
         if (ri >= m) break;
-        const int i = j0 + ri;
-        const C ui = a.U[i], wi = a.W[i], vi = a.V[i];
-        C* row = a.A + tri64(i) + j0;
+        const int rn = ri + FS_PASS_THREADS / 32;
+        if (rr + FS_PASS_THREADS / 32 < FS_TB && rn < m) {
+            const C* rown = a.A + tri64(j0 + rn) + j0;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) xb[q] = cr[q] <= rn ? rown[cr[q]] : zero;
+        }
+        const C ui = svec[0][rr], wi = svec[1][rr], vi = svec[2][rr];
+        C* row = a.A + tri64(j0 + ri) + j0;
         C racc = zero;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int c = cr[q];
             if (c <= ri) {
-                C x = row[c];
+                C x = xa[q];
                 x = cfms_conj_b(ui, wc[q], x);
                 x = cfms_conj_b(wi, uc[q], x);
                 if (c == ri) x.y = r0;  // the diagonal stays real
@@ -165,6 +190,7 @@ __global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs<R> a, int k)
                 racc = cfma(x, vc[q], racc);
                 if (c < ri) cacc[q] = cfma_conj_a(x, vi, cacc[q]);
             }
+            xa[q] = xb[q];
         }
         rsum[rr][lane] = racc;
     }
@@ -194,20 +220,31 @@ __global__ void __launch_bounds__(FS_PASS_THREADS) k_fs_pass(FsArgs<R> a, int k)
 
 // p = tau (A v): for row ri of band B (its tile row), the row partials of
 // tiles (B, 0 .. B) plus the column partials of tiles (B .. T-1, B) (the
-// diagonal tile's column sums hold the elements below the diagonal), in a
-// fixed order; and each CTA's partial sum of Re(v^H p).
+// diagonal tile's column sums hold the elements below the diagonal); and
+// each CTA's partial sum of Re(v^H p).  A CTA takes 32 consecutive rows, one
+// per lane; warp q adds the partials q, q+8, ... of that list, and warp 0
+// adds the eight warps' sums, in a fixed order.
 template <typename R>
 __global__ void __launch_bounds__(FS_RED_THREADS) k_fs_reduce(FsArgs<R> a, int k) {
     using C = cplx_t<R>;
-    __shared__ R red[FS_RED_THREADS / 32];
+    __shared__ C part[FS_RED_THREADS / 32][FS_RED_ROWS];
     const int n = a.n, j0 = k + 1, m = n - j0, T = (m + FS_TB - 1) / FS_TB;
-    const int ri = blockIdx.x * blockDim.x + threadIdx.x;
-    R sp = fs_r<R>(0.f);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ri = blockIdx.x * FS_RED_ROWS + lane;
+    const R r0 = fs_r<R>(0.f);
+    C s = mk(r0, r0);
     if (ri < m) {
         const int band = ri / FS_TB;
-        C s = mk(sp, sp);
-        for (int tc = 0; tc <= band; ++tc) s = cadd(s, a.pr[(int64_t)tc * n + ri]);
-        for (int tr = band; tr < T; ++tr) s = cadd(s, a.pc[(int64_t)tr * n + ri]);
+        for (int q = warp; q <= T; q += FS_RED_THREADS / 32)
+            s = cadd(s, q <= band ? a.pr[(int64_t)q * n + ri] : a.pc[(int64_t)(q - 1) * n + ri]);
+    }
+    part[warp][lane] = s;
+    __syncthreads();
+    if (warp != 0) return;
+#pragma unroll
+    for (int w = 1; w < FS_RED_THREADS / 32; ++w) s = cadd(s, part[w][lane]);
+    R sp = r0;
+    if (ri < m) {
         const R tau = a.tau[k & 1];
         s.x = s.x * tau;
         s.y = s.y * tau;
@@ -215,8 +252,8 @@ __global__ void __launch_bounds__(FS_RED_THREADS) k_fs_reduce(FsArgs<R> a, int k
         const C v = a.V[j0 + ri];
         sp = v.x * s.x + v.y * s.y;
     }
-    sp = block_sum<R>(sp, red);
-    if (threadIdx.x == 0) a.red[blockIdx.x] = sp;
+    sp = warp_sum<R>(sp);
+    if (lane == 0) a.red[blockIdx.x] = sp;
 }
 
 // Column 0: d_0, ||x||^2 and the first reflector (one CTA).
@@ -400,7 +437,7 @@ static cudaError_t fs_tridiagonalise(int n, void* A, void* vb_, void* wb_, void*
         a.W = wb + (size_t)((k + 1) & 1) * n;
         a.Wn = wb + (size_t)(k & 1) * n;
         k_fs_pass<R><<<(unsigned)tri64(T), FS_PASS_THREADS, 0, st>>>(a, k);
-        const int nred = (mm + FS_RED_THREADS - 1) / FS_RED_THREADS;
+        const int nred = (mm + FS_RED_ROWS - 1) / FS_RED_ROWS;
         k_fs_reduce<R><<<nred, FS_RED_THREADS, 0, st>>>(a, k);
         k_fs_scalar<R><<<1, FS_SCALAR_THREADS, 0, st>>>(a, k, nred);
         e = cudaGetLastError();
@@ -426,7 +463,7 @@ extern "C" ptca_status ptca_full_spectrum(ptca_ctx* ctx, double* eig_out, void* 
     const int Tmax = (n - 1 + FS_TB - 1) / FS_TB;
     cudaError_t es = ptca_internal_settle(ctx, static_cast<cudaStream_t>(stream), true);
     if (es != cudaSuccess) return ptca_internal_fail(PTCA_ERR_CUDA, cudaGetErrorString(es));
-    const int red_max = (n + FS_RED_THREADS - 1) / FS_RED_THREADS;
+    const int red_max = (n + FS_RED_ROWS - 1) / FS_RED_ROWS;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     std::vector<void*> owned;
