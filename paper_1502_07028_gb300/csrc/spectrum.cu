@@ -256,6 +256,18 @@ __global__ void __launch_bounds__(FS_RED_THREADS) k_fs_reduce(FsArgs<R> a, int k
     if (lane == 0) a.red[blockIdx.x] = sp;
 }
 
+// Sum over the FS_SCALAR_THREADS threads of a scalar-phase CTA; every thread
+// receives the same value (each warp's butterfly, then a butterfly over the
+// 32 warp sums).  `red` holds 32 entries and is not read by another
+// reduction until a later __syncthreads.
+static_assert(FS_SCALAR_THREADS == 32 * 32, "fs_block_sum adds one value per warp in one warp");
+template <typename R> __device__ __forceinline__ R fs_block_sum(R v, R* red) {
+    v = warp_sum<R>(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    return warp_sum<R>(red[threadIdx.x & 31]);
+}
+
 // Column 0: d_0, ||x||^2 and the first reflector (one CTA).
 template <typename R>
 __global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_setup(FsArgs<R> a) {
@@ -270,7 +282,7 @@ __global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_setup(FsArgs<R> a) {
         if (i >= 2) a.Vn[i] = x;
         if (i == 1) s_x0 = x;
     }
-    s2 = block_sum<R>(s2, red);
+    s2 = fs_block_sum<R>(s2, red);
     if (threadIdx.x == 0) {
         a.d[0] = fs_d(a.A[0].x);
         a.e2[0] = fs_d(s2);
@@ -294,7 +306,7 @@ __global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_scalar(FsArgs<R> a, in
     const int n = a.n, j0 = k + 1;
     R sp = fs_r<R>(0.f);
     for (int b = threadIdx.x; b < nred; b += blockDim.x) sp = sp + a.red[b];
-    sp = block_sum<R>(sp, red);
+    sp = fs_block_sum<R>(sp, red);
     if (threadIdx.x == 0) s_K = fs_r<R>(0.5f) * a.tau[k & 1] * sp;
     __syncthreads();
     const R K = s_K;
@@ -314,7 +326,7 @@ __global__ void __launch_bounds__(FS_SCALAR_THREADS) k_fs_scalar(FsArgs<R> a, in
         if (i >= j0 + 2) a.Vn[i] = x;
         if (i == j0 + 1) s_x0 = x;
     }
-    s2 = block_sum<R>(s2, red);
+    s2 = fs_block_sum<R>(s2, red);
     if (threadIdx.x == 0) {
         a.e2[j0] = fs_d(s2);
         if (k + 1 <= n - 3) {
