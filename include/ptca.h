@@ -67,7 +67,7 @@ enum { PTCA_FP64 = 0, PTCA_MIXED = 1 };
 enum { PTCA_PROPOSAL_SPHERE = 0, PTCA_PROPOSAL_CONE = 1 };
 enum { PTCA_MODEL_DOUBLE_EXCHANGE = 0, PTCA_MODEL_HUBBARD_MF = 1, PTCA_MODEL_HOLSTEIN = 2 };
 enum { PTCA_PIPELINE_STAGES = 0, PTCA_PIPELINE_PERSISTENT = 1, PTCA_PIPELINE_GRAPH = 2, PTCA_PIPELINE_OVERLAP = 3 };
-enum { PTCA_REDUCTION_ROWS = 0, PTCA_REDUCTION_TILED = 1 };
+enum { PTCA_REDUCTION_ROWS = 0, PTCA_REDUCTION_TILED = 1, PTCA_REDUCTION_SHARED = 2 };
 
 /* Square lattice, chain or cubic lattice.  Ly == 1 is a one-dimensional chain
  * (Sec. III.a, Fig. 3); Lz > 1 (with Ly > 1) a cubic lattice of Lx*Ly*Lz
@@ -300,6 +300,18 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  *                  complex tiles per lane over pairs of block rows, the
  *                  matrix stored as tiles (PTCA_MIXED, 4-warp CTAs, orders
  *                  up to 128, per-stage and overlapped pipelines);
+ *                  PTCA_REDUCTION_SHARED = one reduction for both matrices
+ *                  of a visit: H_new differs from H_old only in the update
+ *                  site's 2x2 on-site block, so a block Householder
+ *                  reduction in 2-column panels started below that block
+ *                  gives both 2x2 block-tridiagonal forms at once; each is
+ *                  then made tridiagonal by a Givens bulge chase and solved
+ *                  (PTCA_MIXED, 4-warp CTAs, one per update site, orders up
+ *                  to 128, per-stage and overlapped pipelines).  Opt-in:
+ *                  its FP32 free-energy differences carry about three times
+ *                  the row-chunked pass's error, which narrows the re-solve
+ *                  guard's safety factor, so ptca_autotune does not select
+ *                  it;
  *   panel_width    0 or 1: the unblocked reduction above; 2, 4 or 8: the
  *                  blocked form, panels of that many reflectors with one
  *                  rank-2b update of the trailing block per panel (the

@@ -5,7 +5,7 @@ ABI in include/ptca.h); ``ptca`` is its ctypes binding.
 """
 from .ptca import (
     FP64, MIXED, MODEL_DOUBLE_EXCHANGE, MODEL_HOLSTEIN, MODEL_HUBBARD_MF, PIPELINE_GRAPH, PIPELINE_OVERLAP,
-    PIPELINE_PERSISTENT, PIPELINE_STAGES, PROPOSAL_CONE, PROPOSAL_SPHERE, REDUCTION_ROWS, REDUCTION_TILED,
+    PIPELINE_PERSISTENT, PIPELINE_STAGES, PROPOSAL_CONE, PROPOSAL_SPHERE, REDUCTION_ROWS, REDUCTION_SHARED, REDUCTION_TILED,
     SCHEDULE_BLOCK, SCHEDULE_TILED,
     Config, Context, KernelTimes, LaunchConfig, PtcaError, lib, library_path,
     ptca_autotune, ptca_build_clusters, ptca_checker_read, ptca_cluster_eigvals, ptca_destroy, ptca_dims,

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libptca.so")
-SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "kernels_f32w4.cu", "kernels_f32w4t.cu", "kernels_f32p.cu", "kernels_f32w1.cu", "kernels_large.cu", "spectrum.cu", "api.cu", "kernels_misc.cu", "noalloc.cu", "surrogate.cu",
+SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "kernels_f32w4.cu", "kernels_f32w4t.cu", "kernels_f32w4s.cu", "kernels_f32p.cu", "kernels_f32w1.cu", "kernels_large.cu", "spectrum.cu", "api.cu", "kernels_misc.cu", "noalloc.cu", "surrogate.cu",
            "surrogate_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

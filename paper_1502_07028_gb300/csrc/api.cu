@@ -627,6 +627,7 @@ static cudaError_t launch_stage_ctx(const ptca_ctx* ctx, const StageArgs& a, cud
     if (ctx->large && ctx->prec == 1 && ctx->nw == 8 && ctx->cl_size > 0)
         return ptca::launch_stage_cluster(ctx->cl_size, a, ctx->cl_grid, st);
     if (ctx->large) return ptca::launch_stage_large(ctx->prec, a, ctx->large_grid, st);
+    if (ctx->reduction == 2) return ptca::launch_stage_shared(a, st);
     if (ctx->reduction == 1) return ptca::launch_stage_tiled(a, st);
     if (ctx->panel > 1) return ptca::launch_stage_panel(ctx->panel, a, st);
     return ptca::launch_stage(ctx->prec, ctx->nw, a, st);
@@ -1094,7 +1095,12 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
         return fail(PTCA_ERR_INVALID, "ctas_per_sm must be in [0, the CTAs that fit on an SM]");
     const bool persistent = cfg->pipeline == PTCA_PIPELINE_PERSISTENT || cfg->pipeline == PTCA_PIPELINE_GRAPH;
     if (persistent && maxb <= 0) return fail(PTCA_ERR_UNSUPPORTED, "persistent kernel does not fit on this device");
-    if (cfg->reduction != 0 && cfg->reduction != 1) return fail(PTCA_ERR_INVALID, "reduction must be 0 or 1");
+    if (cfg->reduction < 0 || cfg->reduction > 2) return fail(PTCA_ERR_INVALID, "reduction must be 0, 1 or 2");
+    if (cfg->reduction == 2 && (ctx->large || cfg->warps_per_cta != 4 || persistent || cfg->panel_width > 1 ||
+                                !ptca::shared_supported(ctx->prec, ctx->nA)))
+        return fail(PTCA_ERR_UNSUPPORTED,
+                    "the shared reduction runs PTCA_MIXED stage kernels of 4-warp CTAs, orders up to 128, in the "
+                    "per-stage or overlapped pipeline");
     if (cfg->reduction == 1 &&
         (ctx->large || cfg->warps_per_cta != 4 || persistent || !ptca::tiled_supported(ctx->prec, ctx->nA)))
         return fail(PTCA_ERR_UNSUPPORTED,
@@ -1159,6 +1165,9 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
             cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 1, 0});
             if (ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 1, 0});
         }
+        // (The shared reduction, PTCA_REDUCTION_SHARED, is not a candidate:
+        // its FP32 dF error is about three times the row-chunked pass's, and
+        // the re-solve margin is sized for the latter.)
         if (nw == 8)
             for (int b : {2, 4, 8}) {
                 if (!ptca::panel_supported(ctx->prec, ctx->nA, b)) continue;

@@ -52,6 +52,7 @@ cudaError_t configure_cluster_kernels(size_t smem_limit) {
     if (e == cudaSuccess) e = configure_f32w4(smem_limit);
     if (e == cudaSuccess) e = configure_f32w1(smem_limit);
     if (e == cudaSuccess) e = configure_tiled_kernels(smem_limit);
+    if (e == cudaSuccess) e = configure_shared_kernels(smem_limit);
     if (e == cudaSuccess) e = configure_panel_kernels(smem_limit);
     if (e != cudaSuccess) return e;
     return configure_f64(smem_limit);

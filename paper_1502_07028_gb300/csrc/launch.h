@@ -48,6 +48,12 @@ bool tiled_supported(int prec, int nA);
 size_t tiled_smem_bytes();
 cudaError_t configure_tiled_kernels(size_t smem_limit);
 cudaError_t launch_stage_tiled(const StageArgs& a, cudaStream_t st);
+// One reduction for both matrices of a visit (kernels_f32w4s.cu): FP32, 4-warp
+// CTAs, one per update site, orders up to 128.
+bool shared_supported(int prec, int nA);
+size_t shared_smem_bytes();
+cudaError_t configure_shared_kernels(size_t smem_limit);
+cudaError_t launch_stage_shared(const StageArgs& a, cudaStream_t st);
 // The FP32 8-warp stage kernels with the blocked (panel) reduction, panels of
 // B = 2, 4 or 8 reflectors (orders up to 128).
 bool panel_supported(int prec, int nA, int B);

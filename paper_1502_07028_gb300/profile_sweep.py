@@ -26,8 +26,8 @@ def parser() -> argparse.ArgumentParser:
     ap.add_argument("--warps", type=int, choices=[1, 4, 8, 16], default=8,
                     help="warps per CTA of the sweep kernels (large clusters: 8 = cluster kernel, 16 = global memory)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: as many as fit)")
-    ap.add_argument("--reduction", choices=["rows", "tiled"], default="rows",
-                    help="FP32 Householder pass: lanes on columns (rows) or 4x4 register tiles (tiled; 4 warps)")
+    ap.add_argument("--reduction", choices=["rows", "tiled", "shared"], default="rows",
+                    help="FP32 Householder pass: lanes on columns (rows), 4x4 register tiles (tiled; 4 warps) or one block reduction for both matrices of a visit (shared; 4 warps)")
     ap.add_argument("--panel", type=int, choices=[0, 2, 4, 8], default=0,
                     help="blocked FP32 reduction in panels of this many reflectors (8 warps; 0: unblocked)")
     ap.add_argument("--margin", type=float, default=None, help="mixed-mode re-solve margin (0 = off)")
@@ -75,7 +75,7 @@ def main(argv=None):
     ctx = P.Context(cfg)
     P.ptca_set_launch_config(ctx.h, {"stages": P.PIPELINE_STAGES, "persistent": P.PIPELINE_PERSISTENT,
                                      "graph": P.PIPELINE_GRAPH, "overlap": P.PIPELINE_OVERLAP}[a.pipeline], a.warps, a.ctas_per_sm,
-                              P.REDUCTION_TILED if a.reduction == "tiled" else P.REDUCTION_ROWS, a.panel)
+                              {"rows": P.REDUCTION_ROWS, "tiled": P.REDUCTION_TILED, "shared": P.REDUCTION_SHARED}[a.reduction], a.panel)
     if a.margin is not None and cfg.precision == P.MIXED:
         P.ptca_set_resolve_margin(ctx.h, a.margin)
     if a.full_spectrum:

@@ -21,7 +21,7 @@ STATUS = {0: "PTCA_OK", 1: "PTCA_ERR_INVALID", 2: "PTCA_ERR_CUDA", 3: "PTCA_ERR_
           4: "PTCA_ERR_TIMEOUT", 5: "PTCA_ERR_NUMERIC", 6: "PTCA_ERR_UNSUPPORTED"}
 SCHEDULE_TILED, SCHEDULE_BLOCK = 0, 1
 PIPELINE_STAGES, PIPELINE_PERSISTENT, PIPELINE_GRAPH, PIPELINE_OVERLAP = 0, 1, 2, 3
-REDUCTION_ROWS, REDUCTION_TILED = 0, 1
+REDUCTION_ROWS, REDUCTION_TILED, REDUCTION_SHARED = 0, 1, 2
 FP64, MIXED = 0, 1
 PROPOSAL_SPHERE, PROPOSAL_CONE = 0, 1
 MODEL_DOUBLE_EXCHANGE, MODEL_HUBBARD_MF, MODEL_HOLSTEIN = 0, 1, 2

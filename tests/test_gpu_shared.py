@@ -1,0 +1,174 @@
+"""The shared reduction (launch configuration reduction =
+PTCA_REDUCTION_SHARED: one 4-warp CTA per update site, FP32, orders up to
+128).
+
+H_new differs from H_old only in the update site's on-site block, so one
+block Householder reduction in 2-column panels (Sec. II.c step b, blocked)
+serves both matrices; each 2x2 block-tridiagonal form is then made
+tridiagonal by a Givens bulge chase.  Checked against the oracle's solves of
+every visit (free energies, ln u, decisions, spins) on full, clipped and
+odd-sized windows, chains down to two-site windows, the Hubbard and
+Holstein models and a cube; against the row-chunked pass (same chain); and on
+the free-energy-difference scale at the headline size, where its error is
+about three times the row-chunked pass's; the autotuner does not select it."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1502_07028_gb300 as P
+from paper_1502_07028_gb300 import _build
+from tests import inputs
+from tests.test_gpu_parity import _check_sweep_against_oracle
+from tests.test_gpu_precision import MIXED_DF_BOUND, _level_scale
+
+pytestmark = pytest.mark.gpu
+
+SHARED_STAGES = (P.PIPELINE_STAGES, 4, 0, P.REDUCTION_SHARED)
+SHARED_OVERLAP = (P.PIPELINE_OVERLAP, 4, 0, P.REDUCTION_SHARED)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+    assert torch.cuda.is_available()
+    P.lib()
+
+
+@pytest.mark.parametrize("lat", [
+    dict(Lx=8, Ly=8, L_c=4),                                   # n = 32, corner-centred windows (tiled)
+    dict(Lx=8, Ly=8, L_c=4, schedule=P.SCHEDULE_BLOCK),        # update site already first
+    dict(Lx=13, Ly=11, L_c=6, periodic=0, stride=6),           # n = 18 .. 72, clipped windows
+    dict(Lx=24, Ly=1, L_c=2, stride=2),                        # chain, n = 4: one panel
+    dict(Lx=30, Ly=1, L_c=5, stride=5),                        # chain, n = 10
+    dict(Lx=9, Ly=1, L_c=3, periodic=0, stride=3),             # open chain: windows of 2 and 3 sites
+])
+def test_shared_reduction_against_the_oracle_every_visit(lat):
+    cfg = P.Config(**lat, t=1.0, J_H=8.0, mu=-6.5, T=0.05, seed=3, precision=P.MIXED)
+    _check_sweep_against_oracle(cfg, sweeps=2, launch=SHARED_STAGES)
+
+
+def test_shared_reduction_against_the_oracle_n128_overlap():
+    # 24x24 torus, 8x8 clusters (n = 128: 63 panels), the paper's block
+    # schedule, cone proposals: sampled visits plus those nearest the
+    # Metropolis threshold (re-solved), through the overlapped pipeline.
+    cfg = P.Config(Lx=24, Ly=24, L_c=8, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, cone_deg=30.0,
+                   T=0.05, mu=-6.5, seed=9, precision=P.MIXED)
+    _check_sweep_against_oracle(cfg, sweeps=2, sample=12, near=6, launch=SHARED_OVERLAP)
+
+
+def test_shared_reduction_tiled_schedule_n128():
+    # centred windows: the update site is moved to the front of the basis
+    cfg = P.Config(Lx=24, Ly=24, L_c=8, schedule=P.SCHEDULE_TILED, stride=8, T=0.05, mu=-6.5, seed=5,
+                   precision=P.MIXED)
+    _check_sweep_against_oracle(cfg, sweeps=1, sample=16, near=4, launch=SHARED_STAGES)
+
+
+def test_shared_reduction_hubbard_and_holstein():
+    hub = P.Config(Lx=13, Ly=11, L_c=6, periodic=0, stride=6, t=1.0, U=8.0, mu=4.0, T=0.1, seed=3,
+                   model=P.MODEL_HUBBARD_MF, m_step=0.5, precision=P.MIXED)
+    _check_sweep_against_oracle(hub, sweeps=2, start=inputs.random_fields(61, hub.N, 2.0), launch=SHARED_STAGES)
+    hol = P.Config(Lx=32, Ly=1, L_c=8, t=1.0, lam=1.5, K=1.0, mu=0.0, T=0.1, m_step=0.4, seed=2,
+                   model=P.MODEL_HOLSTEIN, precision=P.MIXED)
+    _check_sweep_against_oracle(hol, sweeps=2, launch=SHARED_STAGES)
+
+
+def test_shared_reduction_cube():
+    cfg = P.Config(Lx=8, Ly=8, Lz=8, L_c=4, schedule=P.SCHEDULE_BLOCK, T=0.1, mu=-6.5, seed=8,
+                   precision=P.MIXED)
+    _check_sweep_against_oracle(cfg, sweeps=1, sample=24, near=4, launch=SHARED_STAGES)
+
+
+@pytest.mark.parametrize("lat", [dict(Lx=32, Ly=32, L_c=8, schedule=P.SCHEDULE_BLOCK),
+                                 dict(Lx=23, Ly=21, L_c=7, periodic=0, stride=7)])
+def test_shared_and_row_chunked_reductions_compute_the_same_chain(lat):
+    cfg = P.Config(**lat, proposal=P.PROPOSAL_CONE, T=0.05, mu=-6.5, seed=17, precision=P.MIXED)
+    runs = []
+    for launch in [(P.PIPELINE_STAGES, 4, 0, P.REDUCTION_ROWS), SHARED_STAGES, SHARED_OVERLAP]:
+        ctx = P.Context(cfg)
+        P.ptca_set_launch_config(ctx.h, *launch)
+        got = P.ptca_get_launch_config(ctx.h)
+        assert (got.pipeline, got.warps_per_cta, got.ctas_per_sm, got.reduction) == launch
+        stats = ctx.sweep(2)
+        assert stats.eigensolves == 4 * cfg.N
+        rec = [x.cpu().numpy() for x in ctx.record()]
+        runs.append((ctx.spins().cpu().numpy(), rec))
+        ctx.close()
+    S_ref, (site, Fo, Fn, lnu, acc) = runs[0]
+    for S, (site2, Fo2, Fn2, lnu2, acc2) in runs[1:]:
+        assert np.array_equal(site, site2) and np.array_equal(acc, acc2)
+        assert np.array_equal(lnu, lnu2)
+        assert np.array_equal(S, S_ref)
+        assert np.max(np.abs(Fo2 - Fo) / np.maximum(1.0, np.abs(Fo))) < 1e-5
+        assert np.max(np.abs(Fn2 - Fn) / np.maximum(1.0, np.abs(Fn))) < 1e-5
+    # the two shared pipelines run the same kernel on the same snapshots: bit for bit
+    for x, y in zip(runs[1][1], runs[2][1]):
+        assert np.array_equal(x, y)
+
+
+# dF error bound of the shared reduction on the free-energy-difference scale.
+# Its FP32 dF error is about three times the row-chunked pass's (whole
+# headline stages against FP64: max |d dF| 2.7e-4 .. 3.2e-4 against
+# 0.9e-4 .. 1.1e-4 over four seeds).  Three times the row pass's bound.
+SHARED_DF_BOUND = 3 * MIXED_DF_BOUND
+
+
+def test_shared_dF_error_on_the_free_energy_difference_scale():
+    # Stage 0 of the 100x100 headline, unguarded (margin 0): sampled visits'
+    # dF against the oracle's, on the scale max(|dF|, sum_k |eps_k - mu| f_k / n).
+    base = dict(Lx=100, Ly=100, L_c=8, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, cone_deg=30.0,
+                T=0.05, mu=-6.5, seed=0)
+    m = oracle.Model(Lx=100, Ly=100, Lc=8, JH=8.0, mu=-6.5, T=0.05, schedule=oracle.SCHEDULE_BLOCK,
+                     proposal=oracle.PROPOSAL_CONE, cone_deg=30.0, seed=0)
+    cfg = P.Config(**base, precision=P.MIXED)
+    stage0 = P.ptca_schedule(cfg)[0]
+    ctx = P.Context(cfg)
+    P.ptca_set_launch_config(ctx.h, *SHARED_STAGES)
+    P.ptca_set_resolve_margin(ctx.h, 0.0)
+    ctx.sweep(1)
+    site, Fo, Fn, _, _ = (x.cpu().numpy() for x in ctx.record())
+    ctx.close()
+    S0 = oracle.init_spins(m)
+    worst = 0.0
+    for k in range(0, len(stage0), len(stage0) // 12)[:12]:
+        s = int(stage0[k])
+        assert site[k] == s
+        sn = oracle.propose(m, 0, s, S0[s])
+        e_old = oracle.eigvalsh(oracle.cluster_hamiltonian(m, S0, s)[0])
+        dF = oracle.cluster_free_energy(m, S0, s, sn) - oracle.free_energy(e_old, m.mu, m.T)
+        scale = max(abs(dF), _level_scale(e_old, m.mu, m.T))
+        worst = max(worst, abs((Fn[k] - Fo[k]) - dF) / scale)
+    assert worst <= SHARED_DF_BOUND, worst
+
+
+def test_shared_reduction_configuration_is_validated():
+    mixed = P.Context(P.Config(Lx=16, Ly=16, L_c=8, precision=P.MIXED))
+    for bad in [(P.PIPELINE_STAGES, 8, 0, P.REDUCTION_SHARED),       # 8-warp CTAs
+                (P.PIPELINE_STAGES, 1, 0, P.REDUCTION_SHARED),       # one-warp CTAs
+                (P.PIPELINE_PERSISTENT, 4, 0, P.REDUCTION_SHARED),   # persistent kernel
+                (P.PIPELINE_GRAPH, 4, 0, P.REDUCTION_SHARED)]:
+        with pytest.raises(P.PtcaError):
+            P.ptca_set_launch_config(mixed.h, *bad)
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(mixed.h, P.PIPELINE_STAGES, 4, 0, 3)
+    assert P.ptca_get_launch_config(mixed.h).reduction == P.REDUCTION_ROWS  # unchanged
+    mixed.close()
+    fp64 = P.Context(P.Config(Lx=16, Ly=16, L_c=8, precision=P.FP64))
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(fp64.h, *SHARED_STAGES)
+    fp64.close()
+    big = P.Context(P.Config(Lx=20, Ly=20, L_c=10, precision=P.MIXED))  # n = 200 > 128
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(big.h, *SHARED_STAGES)
+    big.close()
+
+
+def test_autotune_does_not_select_the_shared_reduction():
+    # its larger dF error would narrow the re-solve guard's safety factor
+    cfg = P.Config(Lx=32, Ly=32, L_c=8, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, T=0.05, seed=23,
+                   precision=P.MIXED)
+    ctx = P.Context(cfg)
+    best, table = P.ptca_autotune(ctx.h, 1)
+    assert all(c["reduction"] != P.REDUCTION_SHARED for c in table["candidates"])
+    assert best.reduction != P.REDUCTION_SHARED
+    ctx.close()
