@@ -114,7 +114,7 @@ def test_tiled_reduction_configuration_is_validated():
         with pytest.raises(P.PtcaError):
             P.ptca_set_launch_config(mixed.h, *bad)
     with pytest.raises(P.PtcaError):
-        P.ptca_set_launch_config(mixed.h, P.PIPELINE_STAGES, 4, 0, 2)
+        P.ptca_set_launch_config(mixed.h, P.PIPELINE_STAGES, 4, 0, 3)  # no such reduction
     got = P.ptca_get_launch_config(mixed.h)
     assert got.reduction == P.REDUCTION_ROWS  # unchanged by the rejected calls
     mixed.close()
