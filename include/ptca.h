@@ -308,8 +308,8 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  *                  then made tridiagonal by a Givens bulge chase and solved
  *                  (PTCA_MIXED, 4-warp CTAs, one per update site, orders up
  *                  to 128, per-stage and overlapped pipelines).  Opt-in:
- *                  its FP32 free-energy differences carry about three times
- *                  the row-chunked pass's error, which narrows the re-solve
+ *                  its FP32 free-energy differences carry about twice the
+ *                  row-chunked pass's error, which narrows the re-solve
  *                  guard's safety factor, so ptca_autotune does not select
  *                  it;
  *   panel_width    0 or 1: the unblocked reduction above; 2, 4 or 8: the

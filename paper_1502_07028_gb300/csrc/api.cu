@@ -1166,7 +1166,7 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
             if (ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 1, 0});
         }
         // (The shared reduction, PTCA_REDUCTION_SHARED, is not a candidate:
-        // its FP32 dF error is about three times the row-chunked pass's, and
+        // its FP32 dF error is about twice the row-chunked pass's, and
         // the re-solve margin is sized for the latter.)
         if (nw == 8)
             for (int b : {2, 4, 8}) {

@@ -387,6 +387,27 @@ __device__ void sh_reduce(int n, float2* M, float2* Wv, float2* pc, float* red) 
 // give the result of the sequential chases.  Lane l takes the chases k = l
 // (mod 32).  dd: diagonal, e1[i] = A(i+1, i), e2c[i] = A(i+2, i), bul[i] =
 // A(i+3, i) (zero).  On return dd and e1 hold the tridiagonal.
+// Rotation taking (a, b) to (r, 0): c = |a| / rho, s = a conj(b) / (|a| rho),
+// rho^2 = |a|^2 + |b|^2, in FP32 with correctly rounded square roots and
+// quotients, then scaled to unit length to first order (c^2 + |s|^2 - 1
+// formed with fused multiply-adds).  The rotations' departure from
+// unitarity is not shared by the two matrices' chases and dominates the
+// error of dF; the scaling halves it.
+__device__ __forceinline__ void sh_rot_params(float2 a, float2 b, float aa, float bb, float& c, float2& s) {
+    if (!(aa > 0.f)) {
+        c = 0.f;
+        s = make_float2(1.f, 0.f);
+        return;
+    }
+    const float rho = sqrtf(aa + bb), ra = sqrtf(aa);
+    c = ra / rho;
+    s = sh_scale(sh_mul(a, sh_conj(b)), 1.f / (ra * rho));
+    const float dlt = __fmaf_rn(c, c, __fmaf_rn(s.x, s.x, __fmaf_rn(s.y, s.y, -1.f)));
+    const float f = 1.f - 0.5f * dlt;
+    c *= f;
+    s = sh_scale(s, f);
+}
+
 __device__ void sh_chase(int n, float* dd, float2* e1, float2* e2c, float2* bul) {
     const int lane = threadIdx.x & 31;
     if (n < 3) return;
@@ -409,20 +430,9 @@ __device__ void sh_chase(int n, float* dd, float2* e1, float2* e2c, float2* bul)
             const float2 y3 = r3 ? e2c[p + 1] : zero;
             const float aa = a.x * a.x + a.y * a.y, bb = b.x * b.x + b.y * b.y;
             if (aa + bb > 0.f) {
-                // c = |a| / rho, s = (a / |a|) conj(b) / rho, rho^2 = |a|^2 + |b|^2
-                // (correctly rounded square roots and quotients: the rotations'
-                // departure from unitarity is what the eigenvalues inherit)
                 float c;
                 float2 sv;
-                const float rho = sqrtf(aa + bb);
-                if (aa > 0.f) {
-                    const float ra = sqrtf(aa);
-                    c = ra / rho;
-                    sv = sh_scale(sh_mul(a, sh_conj(b)), 1.f / (ra * rho));
-                } else {
-                    c = 0.f;
-                    sv = make_float2(1.f, 0.f);
-                }
+                sh_rot_params(a, b, aa, bb, c, sv);
                 const float2 sc = sh_conj(sv);
                 const float2 r_ = cadd(sh_scale(a, c), sh_mul(sv, b));
                 if (st == 0) {
