@@ -589,6 +589,18 @@ def large_cluster_mode(P, args, flush, stream, rank):
                       "kernel": "thread-block cluster, matrix in distributed shared memory" if best.warps_per_cta == 8
                                 else "16-warp CTA, matrix in global memory"},
            "autotune": [[c["pipeline"], c["warps_per_cta"], c["ms_per_sweep"]] for c in table["candidates"]]}
+    # the opt-in shared reduction (one block Householder reduction for both
+    # matrices of a visit), overlapped pipeline
+    ctx = P.Context(P.Config(**base, precision=P.MIXED))
+    P.ptca_set_launch_config(ctx.h, P.PIPELINE_OVERLAP, 16, 0, P.REDUCTION_SHARED)
+    ms_sh = time_sweeps(ctx, 3, 3, flush, stream)
+    st_sh = P.ptca_sweep(ctx.h, 1, stats=True, stream=stream)
+    ctx.close()
+    out["shared_reduction"] = {"value": N * 3 / (sum(ms_sh) * 1e-3), "unit": "spin-updates/s",
+                               "ms_per_step": sum(ms_sh) / 3, "resolved_fraction": st_sh.resolved / st_sh.attempts,
+                               "note": "opt-in launch configuration (reduction = PTCA_REDUCTION_SHARED, 16-warp "
+                                       "CTAs, overlapped pipeline): one reduction per visit, its free-energy "
+                                       "differences about 1.3x the default kernel's FP32 error"}
     ctx = P.Context(P.Config(**base, precision=P.FP64))
     ms64 = time_sweeps(ctx, 1, 3, flush, stream)
     ctx.close()
@@ -816,6 +828,13 @@ def main():
     ung_ms = time_sweeps(ctx, max(3, args.steps // 2), 3, flush, stream)
     unguarded_value = N * len(ung_ms) / (sum(ung_ms) * 1e-3)
     ctx.close()
+    # The opt-in shared reduction (one block Householder reduction for both
+    # matrices of a visit), guarded, overlapped pipeline.
+    ctx = P.Context(P.Config(**base, precision=P.MIXED))
+    P.ptca_set_launch_config(ctx.h, P.PIPELINE_OVERLAP, 4, 0, P.REDUCTION_SHARED)
+    sh_ms = time_sweeps(ctx, max(3, args.steps // 2), 3, flush, stream)
+    shared_value = N * len(sh_ms) / (sum(sh_ms) * 1e-3)
+    ctx.close()
 
     extra = {}
     if not args.no_extra:
@@ -908,6 +927,11 @@ def main():
                                          c["panel_width"], c["ms_per_sweep"]] for c in tune_table["candidates"]]},
             "mixed_unguarded": {"value": unguarded_value, "unit": "spin-updates/s",
                                 "note": "same path without the double-float re-solve of decisions within 1e-2"},
+            "shared_reduction": {"value": shared_value, "unit": "spin-updates/s",
+                                 "note": "opt-in launch configuration (reduction = PTCA_REDUCTION_SHARED, 4-warp "
+                                         "CTAs, overlapped pipeline, guarded): one block reduction per visit; its "
+                                         "FP32 free-energy differences carry about twice the row-chunked pass's "
+                                         "error, so the autotuner does not select it"},
             "resolved_fraction": resolved_frac,
             "fp64_path": {"value": fp64_value, "unit": "spin-updates/s", "ms_per_step": sum(fp64_ms) / len(fp64_ms),
                           "roofline": {"bound": "alu", "kernel": "k_sweep_persistent<double,4,8>",

@@ -307,7 +307,9 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  *                  gives both 2x2 block-tridiagonal forms at once; each is
  *                  then made tridiagonal by a Givens bulge chase and solved
  *                  (PTCA_MIXED, 4-warp CTAs, one per update site, orders up
- *                  to 128, per-stage and overlapped pipelines).  Opt-in:
+ *                  to 128; large clusters: 16-warp CTAs striding over the
+ *                  update sites, the matrix in a global slot; per-stage and
+ *                  overlapped pipelines).  Opt-in:
  *                  its FP32 free-energy differences carry about twice the
  *                  row-chunked pass's error, which narrows the re-solve
  *                  guard's safety factor, so ptca_autotune does not select

@@ -624,6 +624,7 @@ cudaError_t ptca_screen_part(ptca_ctx* ctx, ptca::StageArgs& a, int part, int ro
 // A stage launch and a re-solve launch in the context's configuration
 // (shared-memory kernels, or the large-cluster kernels).
 static cudaError_t launch_stage_ctx(const ptca_ctx* ctx, const StageArgs& a, cudaStream_t st) {
+    if (ctx->large && ctx->reduction == 2) return ptca::launch_stage_large_shared(a, ctx->large_grid, st);
     if (ctx->large && ctx->prec == 1 && ctx->nw == 8 && ctx->cl_size > 0)
         return ptca::launch_stage_cluster(ctx->cl_size, a, ctx->cl_grid, st);
     if (ctx->large) return ptca::launch_stage_large(ctx->prec, a, ctx->large_grid, st);
@@ -1096,11 +1097,17 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     const bool persistent = cfg->pipeline == PTCA_PIPELINE_PERSISTENT || cfg->pipeline == PTCA_PIPELINE_GRAPH;
     if (persistent && maxb <= 0) return fail(PTCA_ERR_UNSUPPORTED, "persistent kernel does not fit on this device");
     if (cfg->reduction < 0 || cfg->reduction > 2) return fail(PTCA_ERR_INVALID, "reduction must be 0, 1 or 2");
-    if (cfg->reduction == 2 && (ctx->large || cfg->warps_per_cta != 4 || persistent || cfg->panel_width > 1 ||
-                                !ptca::shared_supported(ctx->prec, ctx->nA)))
-        return fail(PTCA_ERR_UNSUPPORTED,
-                    "the shared reduction runs PTCA_MIXED stage kernels of 4-warp CTAs, orders up to 128, in the "
-                    "per-stage or overlapped pipeline");
+    if (cfg->reduction == 2) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+        const bool ok = ctx->large ? cfg->warps_per_cta == 16 && ptca::large_shared_supported(ctx->prec, ctx->nA,
+                                                                                             (size_t)optin)
+                                   : cfg->warps_per_cta == 4 && ptca::shared_supported(ctx->prec, ctx->nA);
+        if (!ok || persistent || cfg->panel_width > 1)
+            return fail(PTCA_ERR_UNSUPPORTED,
+                        "the shared reduction runs PTCA_MIXED stage kernels of 4-warp CTAs (orders up to 128) or, "
+                        "for large clusters, 16-warp CTAs, in the per-stage or overlapped pipeline");
+    }
     if (cfg->reduction == 1 &&
         (ctx->large || cfg->warps_per_cta != 4 || persistent || !ptca::tiled_supported(ctx->prec, ctx->nA)))
         return fail(PTCA_ERR_UNSUPPORTED,

@@ -408,6 +408,32 @@ __device__ __forceinline__ void sh_rot_params(float2 a, float2 b, float aa, floa
     s = sh_scale(s, f);
 }
 
+// The same rotation with its parameters computed in double-float from the
+// FP32 entries and rounded once (squares, quotients and square roots without
+// FP32 rounding): the rotations are then unitary to FP32 rounding of c and s
+// alone.  Longer to compute; used where the chase is short beside the
+// reduction (large clusters).
+__device__ __forceinline__ void sh_rot_params_df(float2 a, float2 b, float& c, float2& s) {
+    const dfl z(0.f, 0.f);
+    const dfl ax(a.x, 0.f), ay(a.y, 0.f), bx(b.x, 0.f), by(b.y, 0.f);
+    const dfl aa = dot2_acc(z, ax, ax, ay, ay);
+    const dfl bb = dot2_acc(z, bx, bx, by, by);
+    if (!(aa.hi > 0.f)) {
+        c = 0.f;
+        s = make_float2(1.f, 0.f);
+        return;
+    }
+    const dfl rr = aa + bb;
+    const dfl cc = sqroot(aa / rr);
+    const dfl k = dfl(1.f, 0.f) / sqroot(aa * rr);
+    const dfl re = dot2_acc(z, ax, bx, ay, by);   // Re(a conj(b))
+    const dfl im = dot2_acc(z, ay, bx, -ax, by);  // Im(a conj(b))
+    const dfl sr = re * k, si = im * k;
+    c = cc.hi + cc.lo;
+    s = make_float2(sr.hi + sr.lo, si.hi + si.lo);
+}
+
+template <bool kAccurate>
 __device__ void sh_chase(int n, float* dd, float2* e1, float2* e2c, float2* bul) {
     const int lane = threadIdx.x & 31;
     if (n < 3) return;
@@ -415,9 +441,13 @@ __device__ void sh_chase(int n, float* dd, float2* e1, float2* e2c, float2* bul)
     const int rounds = 4 * (n - 3) + 1;
     for (int r = 0; r < rounds; ++r) {
         const int K = r >> 2;
-        const int k = K - ((K - lane) & 31);
-        const int st = r - 4 * k;
-        if (k >= 0 && k <= n - 3 && st <= (n - 3 - k) / 2) {
+        // the chases k = lane (mod 32) active in round r: st = r - 4k grows as
+        // k falls while chase k's last step (n-3-k)/2 grows more slowly, so
+        // the active ones are consecutive from the largest k <= r/4 down
+        for (int k = K - ((K - lane) & 31); k >= 0; k -= 32) {
+            const int st = r - 4 * k;
+            if (k > n - 3) continue;
+            if (st > (n - 3 - k) / 2) break;
             const int p = k + 1 + 2 * st, q = p + 1;
             const bool r2 = p + 2 < n, r3 = p + 3 < n;
             // every operand of the rotation first (independent loads)
@@ -432,7 +462,8 @@ __device__ void sh_chase(int n, float* dd, float2* e1, float2* e2c, float2* bul)
             if (aa + bb > 0.f) {
                 float c;
                 float2 sv;
-                sh_rot_params(a, b, aa, bb, c, sv);
+                if constexpr (kAccurate) sh_rot_params_df(a, b, c, sv);
+                else sh_rot_params(a, b, aa, bb, c, sv);
                 const float2 sc = sh_conj(sv);
                 const float2 r_ = cadd(sh_scale(a, c), sh_mul(sv, b));
                 if (st == 0) {
@@ -463,41 +494,17 @@ __device__ void sh_chase(int n, float* dd, float2* e1, float2* e2c, float2* bul)
     }
 }
 
-// One update site of a stage, both matrices in this CTA (a sweep kernel's
-// stage_item with the shared reduction): build, reduce once, chase and solve
-// each band, decide.
-__device__ __forceinline__ void stage_item_shared(const StageArgs& a, const StageVar v, int c, unsigned char* smem,
-                                                  double* s_new) {
-    const ShLayout L = sh_layout();
-    float2* M = reinterpret_cast<float2*>(smem + L.M);
-    float2* Wv = reinterpret_cast<float2*>(smem + L.W);
-    float2* pc = reinterpret_cast<float2*>(smem + L.pc);
-    float* red = reinterpret_cast<float*>(smem + L.red);
-    c = v.perm ? v.perm[c] : c;
-    const int site = v.sites[c];
-    const Window w = make_window(a.m, site);
-    const int n = 2 * window_nsite(w);
-    const double* so = v.S_in + 3 * site;
-    if (threadIdx.x == 0) propose(a.m, v.sweep, (uint32_t)site, so, s_new);
-    __syncthreads();
-    double* sp = reinterpret_cast<double*>(smem + L.pc);
-    float t11[8];
-    build_cluster_shared(a.m, w, v.S_in, s_new, sp, M, t11);
-    __syncthreads();
-    double cls[2] = {0.0, 0.0};
-    if (threadIdx.x == 0 && a.m.cls_on) {
-        // the window's classical energy with the old and the proposed vector
-        const int uw = (w.uwz * w.ey + w.uwy) * w.ex + w.uwx;
-        cls[0] = window_classical(a.m, sp, n / 2);
-        const double o0 = sp[3 * uw], o1 = sp[3 * uw + 1], o2 = sp[3 * uw + 2];
-        sp[3 * uw] = s_new[0]; sp[3 * uw + 1] = s_new[1]; sp[3 * uw + 2] = s_new[2];
-        cls[1] = window_classical(a.m, sp, n / 2);
-        sp[3 * uw] = o0; sp[3 * uw + 1] = o1; sp[3 * uw + 2] = o2;
-    }
-    sh_reduce(n, M, Wv, pc, red);
-    // the two bands (old, new) in the partial-sum region
-    float2* bnd = reinterpret_cast<float2*>(smem + L.pc);
-    constexpr int BS = 3 * SH_NMAX + SH_NMAX / 2;  // float2 per band: e1, e2c, bul, dd
+// After the reduction: the two bands (the reduction's band with the old and
+// the new leading block, t11 in thread 0's registers) into bandmem, their
+// chases (warp 0: old, warp 1: new), both eigenvalue phases with their
+// scratch in eigmem, and the decision (Metropolis, the guard, the record).
+// nm >= n: the stride of the per-matrix arrays.  Called by all threads.
+template <int NWP, bool kAccurate>
+__device__ void sh_finish(const StageArgs& a, const StageVar v, int c, int site, const Window& w, int n,
+                          const double* so, const double* s_new, const double* cls, const float2* M,
+                          const float* t11, unsigned char* bandmem, unsigned char* eigmem, int nm) {
+    float2* bnd = reinterpret_cast<float2*>(bandmem);
+    const int BS = 3 * nm + nm / 2;  // float2 per band: e1, e2c, bul, dd
     const float2 zero = make_float2(0.f, 0.f);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float2 b1 = (i >= 1 && i + 1 < n) ? M[sh_at(i + 1, i)] : zero;
@@ -505,53 +512,51 @@ __device__ __forceinline__ void stage_item_shared(const StageArgs& a, const Stag
         const float b0 = i >= 2 ? M[sh_at(i, i)].x : 0.f;
         for (int var = 0; var < 2; ++var) {
             float2* e1 = bnd + var * BS;
-            float* dd = reinterpret_cast<float*>(e1 + 3 * SH_NMAX);
+            float* dd = reinterpret_cast<float*>(e1 + 3 * nm);
             if (i >= 1) e1[i] = b1;
-            e1[SH_NMAX + i] = b2;
-            e1[2 * SH_NMAX + i] = zero;
+            e1[nm + i] = b2;
+            e1[2 * nm + i] = zero;
             if (i >= 2) dd[i] = b0;
             if (i == 0) {
                 dd[0] = t11[4 * var];
                 dd[1] = t11[4 * var + 1];
-                e1[0] = n > 1 ? make_float2(t11[4 * var + 2], t11[4 * var + 3]) : zero;
+                e1[0] = make_float2(t11[4 * var + 2], t11[4 * var + 3]);
             }
         }
     }
     __syncthreads();
-    // chase: warp 0 the old band, warp 1 the new one; then (d, e2) as doubles
-    // for the eigenvalue phase, in the matrix region (free by now)
-    double* dv = reinterpret_cast<double*>(smem + L.M);  // [2][2][SH_NMAX]: d, e2 per var
+    // chases, then (d, e2) as doubles for the eigenvalue phase
+    double* dv = reinterpret_cast<double*>(eigmem);  // [2 var][d, e2][nm]
     const int warp = threadIdx.x >> 5;
     if (warp < 2) {
         float2* e1 = bnd + warp * BS;
-        float* dd = reinterpret_cast<float*>(e1 + 3 * SH_NMAX);
-        sh_chase(n, dd, e1, e1 + SH_NMAX, e1 + 2 * SH_NMAX);
-        double* d = dv + 2 * warp * SH_NMAX;
+        float* dd = reinterpret_cast<float*>(e1 + 3 * nm);
+        sh_chase<kAccurate>(n, dd, e1, e1 + nm, e1 + 2 * nm);
+        double* d = dv + 2 * warp * nm;
         for (int i = threadIdx.x & 31; i < n; i += 32) {
             d[i] = (double)dd[i];
-            d[SH_NMAX + i] = i < n - 1 ? (double)(e1[i].x * e1[i].x + e1[i].y * e1[i].y) : 0.0;
+            d[nm + i] = i < n - 1 ? (double)(e1[i].x * e1[i].x + e1[i].y * e1[i].y) : 0.0;
         }
     }
     __syncthreads();
-    // eigenvalue-phase scratch past the (d, e2) pairs
     Carve<float> cv;
     {
-        unsigned char* sc = smem + L.M + 4 * SH_NMAX * sizeof(double);
+        unsigned char* sc = eigmem + 4 * (size_t)nm * sizeof(double);
         cv.df = reinterpret_cast<float*>(sc);
-        cv.e2f = cv.df + SH_NMAX;
-        cv.dlo = cv.e2f + SH_NMAX;
-        cv.e2lo = cv.dlo + SH_NMAX;
-        cv.lam = cv.e2lo + SH_NMAX;                               // 2 SH_NMAX floats
-        cv.cnt = reinterpret_cast<int*>(cv.lam + 2 * SH_NMAX);    // one per thread
-        cv.red = reinterpret_cast<double*>(cv.cnt + 32 * SH_NW);  // 8 SH_NW doubles
+        cv.e2f = cv.df + nm;
+        cv.dlo = cv.e2f + nm;
+        cv.e2lo = cv.dlo + nm;
+        cv.lam = cv.e2lo + nm;                                 // 2 nm floats
+        cv.cnt = reinterpret_cast<int*>(cv.lam + 2 * nm);      // one per thread
+        cv.red = reinterpret_cast<double*>(cv.cnt + 32 * NWP);  // 8 NWP doubles
     }
     double F[2], fill[2];
     for (int var = 0; var < 2; ++var) {
-        cv.d = dv + 2 * var * SH_NMAX;
-        cv.e2 = cv.d + SH_NMAX;
+        cv.d = dv + 2 * var * nm;
+        cv.e2 = cv.d + nm;
         double ssp, sfe;
         int K;
-        tridiag_eig_F<float, SH_NW>(n, cv, a.m.mu - a.m.e0, a.m.T, false, nullptr, ssp, sfe, K);
+        tridiag_eig_F<float, NWP>(n, cv, a.m.mu - a.m.e0, a.m.T, false, nullptr, ssp, sfe, K);
         F[var] = -a.m.T * ssp + cls[var];
         fill[var] = sfe;
         __syncthreads();
@@ -592,6 +597,49 @@ __device__ __forceinline__ void stage_item_shared(const StageArgs& a, const Stag
     atomicAdd(&a.counters[1], 2ull);
 }
 
+// The window's classical energy with the old and the proposed vector
+// (thread 0; zero unless the model has one).
+__device__ __forceinline__ void sh_classical(const Model& m, const Window& w, int n, double* sp, const double* s_new,
+                                             double* cls) {
+    cls[0] = cls[1] = 0.0;
+    if (threadIdx.x != 0 || !m.cls_on) return;
+    const int uw = (w.uwz * w.ey + w.uwy) * w.ex + w.uwx;
+    cls[0] = window_classical(m, sp, n / 2);
+    const double o0 = sp[3 * uw], o1 = sp[3 * uw + 1], o2 = sp[3 * uw + 2];
+    sp[3 * uw] = s_new[0]; sp[3 * uw + 1] = s_new[1]; sp[3 * uw + 2] = s_new[2];
+    cls[1] = window_classical(m, sp, n / 2);
+    sp[3 * uw] = o0; sp[3 * uw + 1] = o1; sp[3 * uw + 2] = o2;
+}
+
+// One update site of a stage, both matrices in this CTA (a sweep kernel's
+// stage_item with the shared reduction): build, reduce once, chase and solve
+// each band, decide.
+__device__ __forceinline__ void stage_item_shared(const StageArgs& a, const StageVar v, int c, unsigned char* smem,
+                                                  double* s_new) {
+    const ShLayout L = sh_layout();
+    float2* M = reinterpret_cast<float2*>(smem + L.M);
+    float2* Wv = reinterpret_cast<float2*>(smem + L.W);
+    float2* pc = reinterpret_cast<float2*>(smem + L.pc);
+    float* red = reinterpret_cast<float*>(smem + L.red);
+    c = v.perm ? v.perm[c] : c;
+    const int site = v.sites[c];
+    const Window w = make_window(a.m, site);
+    const int n = 2 * window_nsite(w);
+    const double* so = v.S_in + 3 * site;
+    if (threadIdx.x == 0) propose(a.m, v.sweep, (uint32_t)site, so, s_new);
+    __syncthreads();
+    double* sp = reinterpret_cast<double*>(smem + L.pc);
+    float t11[8];
+    build_cluster_shared(a.m, w, v.S_in, s_new, sp, M, t11);
+    __syncthreads();
+    double cls[2];
+    sh_classical(a.m, w, n, sp, s_new, cls);
+    sh_reduce(n, M, Wv, pc, red);
+    // the bands in the partial-sum region; (d, e2) and the eigenvalue scratch
+    // in the matrix region, free once the bands are out
+    sh_finish<SH_NW, false>(a, v, c, site, w, n, so, s_new, cls, M, t11, smem + L.pc, smem + L.M, SH_NMAX);
+}
+
 // One stage with the shared reduction: CTA c holds update site c.
 __global__ void __launch_bounds__(32 * SH_NW, 3) k_stage_shared(StageArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -607,6 +655,284 @@ __global__ void __launch_bounds__(32 * SH_NW, 3) k_stage_shared(StageArgs a) {
     const int count = a.count_dev ? (int)*a.count_dev : a.count;
     if (c >= count) return;
     stage_item_shared(a, stage_var(a), c, smem, s_new);
+}
+
+
+// ---------------------------------------------------------------------------
+// The shared reduction for large traveling clusters (orders above the
+// shared-memory kernels', up to 32 NW_LARGE): one NW_LARGE-warp CTA per update
+// site, the matrix in the CTA's global slot (rows 2..n-1 of the packed
+// triangle, as above), the panel's reflectors, w and the partial sums in
+// shared memory.  At these orders the chases' O(n) dependent rounds are small
+// beside the reduction, which is done once per visit instead of twice.
+// ---------------------------------------------------------------------------
+
+constexpr int SHL_NW = NW_LARGE;
+
+// Shared memory of a large shared-reduction CTA for orders up to nA (nm = nA
+// rounded up to 32): w, the reflectors of two consecutive panels, the row
+// sums and per-warp column sums of the two products (two vectors each), the
+// block-sum slots.  The window's vectors (build), the bands and the
+// eigenvalue phase reuse the column-sum region.
+struct ShlLayout { size_t W, Va, Vb, pr, pc, red, total; int nm; };
+__host__ __device__ inline ShlLayout shl_layout(int nA) {
+    ShlLayout L;
+    const int nm = (nA + 31) & ~31;
+    L.nm = nm;
+    const size_t vv = 2 * (size_t)nm * sizeof(float2);
+    size_t o = 0;
+    L.W = o;   o = align16(o + vv);
+    L.Va = o;  o = align16(o + vv);
+    L.Vb = o;  o = align16(o + vv);
+    L.pr = o;  o = align16(o + vv);
+    L.pc = o;  o = align16(o + (size_t)SHL_NW * vv);
+    L.red = o; o = align16(o + 256 * sizeof(float));
+    L.total = o;
+    return L;
+}
+
+// Panel j's fused pass (plain form of sh_pass for a matrix in global memory):
+// warp w takes the trailing rows m-1-w, m-1-w-SHL_NW, ... (longest first),
+// lane l the columns l, l+32, ... of the row, four global loads in flight per
+// lane.  Each element gets panel j-1's rank-4 update (Vp, Wv; skipped at
+// j = 0), is stored, and adds to its row's two sums (reduced across the warp
+// into pr) and, below the diagonal, to its column's two sums in the warp's
+// own partial vectors (lanes own distinct columns: a fixed order).  Vectors
+// hold two components of stride nm, indexed by row; pr and pc by row - r0.
+__device__ __forceinline__ void shl_pass(int n, int j, float2* M, const float2* Wv, const float2* Vc, const float2* Vp,
+                                         float2* pr, float2* pc, int nm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = 2 * j + 2, m = n - r0;
+    const bool upd = j > 0;
+    const float2 zero = make_float2(0.f, 0.f);
+    float2* pw = pc + 2 * warp * (size_t)nm;
+    for (int x = lane; x < m; x += 32) { pw[x] = zero; pw[nm + x] = zero; }
+    __syncwarp();
+    for (int r = warp; r < m; r += SHL_NW) {
+        const int ri = m - 1 - r, i = r0 + ri;
+        const float2 ui1 = upd ? Vp[i] : zero, ui2 = upd ? Vp[nm + i] : zero;
+        const float2 wi1 = upd ? Wv[i] : zero, wi2 = upd ? Wv[nm + i] : zero;
+        const float2 vi1 = Vc[i], vi2 = Vc[nm + i];
+        float2* row = M + sh_at(i, r0);
+        float2 ra1 = zero, ra2 = zero;
+        constexpr int LU = 4;
+        for (int jb = 0; jb <= ri; jb += 32 * LU) {
+            float2 av[LU];
+#pragma unroll
+            for (int q = 0; q < LU; ++q) {
+                const int jr = jb + 32 * q + lane;
+                av[q] = jr <= ri ? row[jr] : zero;
+            }
+#pragma unroll
+            for (int q = 0; q < LU; ++q) {
+                const int jr = jb + 32 * q + lane;
+                if (jr <= ri) {
+                    const int y = r0 + jr;
+                    float2 a = av[q];
+                    if (upd) {
+                        a = cfms_conj_b(ui1, Wv[y], a);
+                        a = cfms_conj_b(wi1, Vp[y], a);
+                        a = cfms_conj_b(ui2, Wv[nm + y], a);
+                        a = cfms_conj_b(wi2, Vp[nm + y], a);
+                        row[jr] = a;
+                    }
+                    ra1 = cfma(a, Vc[y], ra1);
+                    ra2 = cfma(a, Vc[nm + y], ra2);
+                    if (jr < ri) {
+                        pw[jr] = cfma_conj_a(a, vi1, pw[jr]);
+                        pw[nm + jr] = cfma_conj_a(a, vi2, pw[nm + jr]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ra1 = cadd(ra1, cshfl_xor(ra1, o));
+            ra2 = cadd(ra2, cshfl_xor(ra2, o));
+        }
+        if (lane == 0) { pr[ri] = ra1; pr[nm + ri] = ra2; }
+    }
+    __syncthreads();
+}
+
+// The block reduction of the matrix in global memory M (order n <= 32
+// SHL_NW); the algorithm and the thread-per-row vector phases of sh_reduce,
+// with the reflectors kept whole in shared memory (two buffers by panel
+// parity) and only R written back.  red: 256 floats.  Ends with a barrier.
+__device__ void shl_reduce(int n, float2* M, float2* Wv, float2* Va, float2* Vb, float2* pr, float2* pc, float* red,
+                           int nm) {
+    constexpr int NWP = SHL_NW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float2 zero = make_float2(0.f, 0.f), one = make_float2(1.f, 0.f);
+    // block-sum slots: products 10 per warp [0, 160), ||x1||^2 [160, 176),
+    // x1's first entry 176-177, v1^H x2 [178, 210), ||x2||^2 [210, 226),
+    // x2's second entry 226-227
+    for (int j = 0; 2 * j + 2 < n; ++j) {
+        float2* Vc = (j & 1) ? Vb : Va;
+        const float2* Vp = (j & 1) ? Va : Vb;
+        const int r0 = 2 * j + 2, c1 = 2 * j, c2 = 2 * j + 1;
+        const int i = tid;
+        const bool act = i >= r0 && i < n;
+        float2 x1 = act ? M[sh_at(i, c1)] : zero;
+        float2 x2 = act ? M[sh_at(i, c2)] : zero;
+        float s = warp_sum(x1.x * x1.x + x1.y * x1.y);
+        if (lane == 0) red[160 + warp] = s;
+        if (i == r0) { red[176] = x1.x; red[177] = x1.y; }
+        __syncthreads();
+        float s1 = 0.f;
+#pragma unroll
+        for (int w = 0; w < NWP; ++w) s1 += red[160 + w];
+        float2 rv, beta1;
+        float tau1;
+        sh_head(s1, make_float2(red[176], red[177]), rv, tau1, beta1);
+        const float2 v1 = i == r0 ? one : (act ? sh_mul(x1, rv) : zero);
+        float2 g = sh_cmul(v1, x2);
+        g.x = warp_sum(g.x);
+        g.y = warp_sum(g.y);
+        if (lane == 0) { red[178 + 2 * warp] = g.x; red[179 + 2 * warp] = g.y; }
+        __syncthreads();
+        g = zero;
+#pragma unroll
+        for (int w = 0; w < NWP; ++w) { g.x += red[178 + 2 * w]; g.y += red[179 + 2 * w]; }
+        x2 = csub(x2, sh_mul(v1, sh_scale(g, tau1)));
+        const bool act2 = act && i > r0;
+        s = warp_sum(act2 ? x2.x * x2.x + x2.y * x2.y : 0.f);
+        if (lane == 0) red[210 + warp] = s;
+        if (i == r0 + 1) { red[226] = x2.x; red[227] = x2.y; }
+        __syncthreads();
+        float s2 = 0.f;
+#pragma unroll
+        for (int w = 0; w < NWP; ++w) s2 += red[210 + w];
+        float2 beta2;
+        float tau2;
+        sh_head(s2, make_float2(red[226], red[227]), rv, tau2, beta2);
+        const float2 v2 = i == r0 + 1 ? one : (act2 ? sh_mul(x2, rv) : zero);
+        if (act) { Vc[i] = v1; Vc[nm + i] = v2; }
+        if (i == r0) { M[sh_at(i, c1)] = beta1; M[sh_at(i, c2)] = x2; }
+        if (i == r0 + 1) M[sh_at(i, c2)] = beta2;
+        __syncthreads();
+        shl_pass(n, j, M, Wv, Vc, Vp, pr, pc, nm);
+        float2 p1 = zero, p2 = zero;
+        if (act) {
+            p1 = pr[i - r0];
+            p2 = pr[nm + i - r0];
+#pragma unroll
+            for (int w = 0; w < NWP; ++w) {
+                p1 = cadd(p1, pc[2 * w * (size_t)nm + i - r0]);
+                p2 = cadd(p2, pc[(2 * w + 1) * (size_t)nm + i - r0]);
+            }
+        }
+        float q[10];
+        {
+            const float2 a11 = sh_cmul(v1, p1), a12 = sh_cmul(v1, p2), a21 = sh_cmul(v2, p1),
+                         a22 = sh_cmul(v2, p2), d12 = sh_cmul(v1, v2);
+            q[0] = a11.x; q[1] = a11.y; q[2] = a12.x; q[3] = a12.y; q[4] = a21.x;
+            q[5] = a21.y; q[6] = a22.x; q[7] = a22.y; q[8] = d12.x; q[9] = d12.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            q[k] = warp_sum(q[k]);
+            if (lane == 0) red[10 * warp + k] = q[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            float t = red[k];
+#pragma unroll
+            for (int w = 1; w < NWP; ++w) t += red[10 * w + k];
+            q[k] = t;
+        }
+        const float2 P11 = make_float2(q[0], q[1]), P12 = make_float2(q[2], q[3]);
+        const float2 P21 = make_float2(q[4], q[5]), P22 = make_float2(q[6], q[7]);
+        const float2 t12 = sh_scale(make_float2(q[8], q[9]), -tau1 * tau2);
+        const float2 Y11 = sh_scale(P11, tau1), Y21 = sh_scale(P21, tau1);
+        const float2 Y12 = cadd(sh_mul(P11, t12), sh_scale(P12, tau2));
+        const float2 Y22 = cadd(sh_mul(P21, t12), sh_scale(P22, tau2));
+        const float2 Z11 = sh_scale(Y11, tau1), Z12 = sh_scale(Y12, tau1);
+        const float2 Z21 = cadd(sh_cmul(t12, Y11), sh_scale(Y21, tau2));
+        const float2 Z22 = cadd(sh_cmul(t12, Y12), sh_scale(Y22, tau2));
+        const float2 y1 = sh_scale(p1, tau1);
+        const float2 y2 = cadd(sh_mul(t12, p1), sh_scale(p2, tau2));
+        const float2 w1 = csub(y1, sh_scale(cadd(sh_mul(v1, Z11), sh_mul(v2, Z21)), 0.5f));
+        const float2 w2 = csub(y2, sh_scale(cadd(sh_mul(v1, Z12), sh_mul(v2, Z22)), 0.5f));
+        if (act) { Wv[i] = w1; Wv[nm + i] = w2; }
+        __syncthreads();
+        if (act) {
+            const float2 w1a = Wv[r0], w2a = Wv[nm + r0];
+            {
+                float2 a = M[sh_at(i, r0)];
+                a = cfms_conj_b(v1, w1a, a);
+                a = cfms_conj_b(v2, w2a, a);
+                a = csub(a, w1);
+                if (i == r0) a.y = 0.f;
+                M[sh_at(i, r0)] = a;
+            }
+            if (i > r0) {
+                const float2 w1b = Wv[r0 + 1], w2b = Wv[nm + r0 + 1];
+                const float2 v1b = Vc[r0 + 1];
+                float2 a = M[sh_at(i, r0 + 1)];
+                a = cfms_conj_b(v1, w1b, a);
+                a = cfms_conj_b(v2, w2b, a);
+                a = cfms_conj_b(w1, v1b, a);
+                a = csub(a, w2);
+                if (i == r0 + 1) a.y = 0.f;
+                M[sh_at(i, r0 + 1)] = a;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One update site with the large shared reduction (matrix in this CTA's
+// global slot).
+__device__ __forceinline__ void stage_item_large_shared(const StageArgs& a, const StageVar v, int c,
+                                                        unsigned char* smem, double* s_new) {
+    const ShlLayout L = shl_layout(a.nA);
+    const int nm = L.nm;
+    float2* M = static_cast<float2*>(a.gL) + (int64_t)blockIdx.x * a.gL_stride;
+    float2* Wv = reinterpret_cast<float2*>(smem + L.W);
+    float2* Va = reinterpret_cast<float2*>(smem + L.Va);
+    float2* Vb = reinterpret_cast<float2*>(smem + L.Vb);
+    float2* pr = reinterpret_cast<float2*>(smem + L.pr);
+    float2* pc = reinterpret_cast<float2*>(smem + L.pc);
+    float* red = reinterpret_cast<float*>(smem + L.red);
+    c = v.perm ? v.perm[c] : c;
+    const int site = v.sites[c];
+    const Window w = make_window(a.m, site);
+    const int n = 2 * window_nsite(w);
+    const double* so = v.S_in + 3 * site;
+    if (threadIdx.x == 0) propose(a.m, v.sweep, (uint32_t)site, so, s_new);
+    __syncthreads();
+    double* sp = reinterpret_cast<double*>(smem + L.pc);
+    float t11[8];
+    build_cluster_shared(a.m, w, v.S_in, s_new, sp, M, t11);
+    __syncthreads();
+    double cls[2];
+    sh_classical(a.m, w, n, sp, s_new, cls);
+    shl_reduce(n, M, Wv, Va, Vb, pr, pc, red, nm);
+    // bands and the eigenvalue phase in the column-sum region
+    unsigned char* bandmem = smem + L.pc;
+    unsigned char* eigmem = bandmem + align16((size_t)2 * (3 * nm + nm / 2) * sizeof(float2));
+    sh_finish<SHL_NW, true>(a, v, c, site, w, n, so, s_new, cls, M, t11, bandmem, eigmem, nm);
+}
+
+// One stage of large clusters with the shared reduction: the resident CTAs
+// stride over the update sites.
+__global__ void __launch_bounds__(32 * SHL_NW, 1) k_stage_large_shared(StageArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_new[3];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.prev_count + a.prev2_count;
+         k += gridDim.x * blockDim.x) {
+        const int s = k < a.prev_count ? a.prev_sites[k] : a.prev2_sites[k - a.prev_count];
+        a.S_out[3 * s] = a.S_in[3 * s];
+        a.S_out[3 * s + 1] = a.S_in[3 * s + 1];
+        a.S_out[3 * s + 2] = a.S_in[3 * s + 2];
+    }
+    const int count = a.count_dev ? (int)*a.count_dev : a.count;
+    for (int c = blockIdx.x; c < count; c += gridDim.x) {
+        stage_item_large_shared(a, stage_var(a), c, smem, s_new);
+        __syncthreads();
+    }
 }
 
 }  // namespace ptca

@@ -54,6 +54,10 @@ bool shared_supported(int prec, int nA);
 size_t shared_smem_bytes();
 cudaError_t configure_shared_kernels(size_t smem_limit);
 cudaError_t launch_stage_shared(const StageArgs& a, cudaStream_t st);
+// The same for large clusters: NW_LARGE-warp CTAs striding over the update
+// sites, the matrix in the CTA's global slot a.gL (grid <= the slots).
+bool large_shared_supported(int prec, int nA, size_t smem_limit);
+cudaError_t launch_stage_large_shared(const StageArgs& a, int grid, cudaStream_t st);
 // The FP32 8-warp stage kernels with the blocked (panel) reduction, panels of
 // B = 2, 4 or 8 reflectors (orders up to 128).
 bool panel_supported(int prec, int nA, int B);

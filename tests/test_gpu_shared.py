@@ -172,3 +172,45 @@ def test_autotune_does_not_select_the_shared_reduction():
     assert all(c["reduction"] != P.REDUCTION_SHARED for c in table["candidates"])
     assert best.reduction != P.REDUCTION_SHARED
     ctx.close()
+
+
+# Large clusters (orders above the shared-memory kernels'): 16-warp CTAs with
+# the matrix in a global slot.
+LARGE_SHARED_STAGES = (P.PIPELINE_STAGES, 16, 0, P.REDUCTION_SHARED)
+LARGE_SHARED_OVERLAP = (P.PIPELINE_OVERLAP, 16, 0, P.REDUCTION_SHARED)
+
+
+@pytest.mark.parametrize("Lc,sample,near", [(12, 3, 2), (16, 1, 1)])
+def test_large_shared_reduction_against_the_oracle(Lc, sample, near):
+    # n = 288 and 512: sampled visits and the nearest to the threshold
+    cfg = P.Config(Lx=2 * Lc, Ly=2 * Lc, L_c=Lc, schedule=P.SCHEDULE_BLOCK, J_H=8.0, mu=-6.5, T=0.1, seed=Lc,
+                   precision=P.MIXED)
+    _check_sweep_against_oracle(cfg, sweeps=1, sample=sample, near=near, launch=LARGE_SHARED_STAGES)
+
+
+def test_large_shared_reduction_clipped_windows():
+    # open lattice: windows of 9x9 .. 15x15 sites (n = 162 .. 450), ragged
+    cfg = P.Config(Lx=33, Ly=31, L_c=15, periodic=0, stride=15, J_H=8.0, mu=-6.5, T=0.1, seed=4,
+                   precision=P.MIXED)
+    _check_sweep_against_oracle(cfg, sweeps=1, sample=2, launch=LARGE_SHARED_STAGES)
+
+
+def test_large_shared_and_default_large_kernels_compute_the_same_chain():
+    cfg = P.Config(Lx=24, Ly=24, L_c=12, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, T=0.05, seed=5,
+                   precision=P.MIXED)
+    runs = []
+    for launch in [(P.PIPELINE_STAGES, 16, 0, P.REDUCTION_ROWS), LARGE_SHARED_STAGES, LARGE_SHARED_OVERLAP]:
+        ctx = P.Context(cfg)
+        P.ptca_set_launch_config(ctx.h, *launch)
+        ctx.sweep(2)
+        rec = [x.cpu().numpy() for x in ctx.record()]
+        runs.append((ctx.spins().cpu().numpy(), rec))
+        ctx.close()
+    S_ref, (site, Fo, Fn, lnu, acc) = runs[0]
+    for S, (site2, Fo2, Fn2, lnu2, acc2) in runs[1:]:
+        assert np.array_equal(site, site2) and np.array_equal(acc, acc2)
+        assert np.array_equal(S, S_ref)
+        assert np.max(np.abs(Fo2 - Fo) / np.maximum(1.0, np.abs(Fo))) < 1e-5
+        assert np.max(np.abs(Fn2 - Fn) / np.maximum(1.0, np.abs(Fn))) < 1e-5
+    for x, y in zip(runs[1][1], runs[2][1]):
+        assert np.array_equal(x, y)
