@@ -309,11 +309,14 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
  *                  (PTCA_MIXED, 4-warp CTAs, one per update site, orders up
  *                  to 128; large clusters: 16-warp CTAs striding over the
  *                  update sites, the matrix in a global slot; per-stage and
- *                  overlapped pipelines).  Opt-in:
+ *                  overlapped pipelines).  Orders up to 128: opt-in, since
  *                  its FP32 free-energy differences carry about twice the
  *                  row-chunked pass's error, which narrows the re-solve
- *                  guard's safety factor, so ptca_autotune does not select
- *                  it;
+ *                  guard's safety factor (ptca_autotune does not select it).
+ *                  Large clusters: the chases run in double-float, the dF
+ *                  error falls about 400-fold below the per-matrix kernel's,
+ *                  and it is faster; it is the default of PTCA_MIXED large
+ *                  contexts and an autotuner candidate;
  *   panel_width    0 or 1: the unblocked reduction above; 2, 4 or 8: the
  *                  blocked form, panels of that many reflectors with one
  *                  rank-2b update of the trailing block per panel (the

@@ -455,8 +455,11 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
             }
             // Default: the 16-warp kernel with the matrix in global memory,
             // measured faster than the cluster kernel at orders 288 and 512
-            // (the autotuner times both).
+            // (the autotuner times both); in PTCA_MIXED with one reduction
+            // shared by the two matrices of a visit, faster still and with a
+            // far smaller dF error (its chases run in double-float).
             c->nw = 16;
+            if (c->prec == 1 && ptca::large_shared_supported(c->prec, c->nA, (size_t)optin)) c->reduction = 2;
             c->gL_stride = (int64_t)c->nA * (c->nA + 1) / 2;
             const size_t es = c->prec == 1 ? sizeof(float2) : sizeof(double2);
             void* q = nullptr;
@@ -1159,6 +1162,12 @@ ptca_status ptca_autotune(ptca_ctx* ctx, int32_t trial_sweeps, ptca_launch_confi
             if (nw == 8 && ctx->cl_size == 0) continue;  // 8 would mean the global-slot kernel again
             cand.push_back({PTCA_PIPELINE_STAGES, nw, 0, 0});
             if (ctx->prec == 1 && ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, nw, 0, 0});
+        }
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+        if (ptca::large_shared_supported(ctx->prec, ctx->nA, (size_t)optin)) {
+            cand.push_back({PTCA_PIPELINE_STAGES, 16, 0, 2, 0});
+            if (ctx->margin > 0.0) cand.push_back({PTCA_PIPELINE_OVERLAP, 16, 0, 2, 0});
         }
         const int maxb = ptca::persistent_blocks_per_sm_large(ctx->prec);
         if (maxb > 0 && !ctx->sg.enabled)

@@ -408,32 +408,6 @@ __device__ __forceinline__ void sh_rot_params(float2 a, float2 b, float aa, floa
     s = sh_scale(s, f);
 }
 
-// The same rotation with its parameters computed in double-float from the
-// FP32 entries and rounded once (squares, quotients and square roots without
-// FP32 rounding): the rotations are then unitary to FP32 rounding of c and s
-// alone.  Longer to compute; used where the chase is short beside the
-// reduction (large clusters).
-__device__ __forceinline__ void sh_rot_params_df(float2 a, float2 b, float& c, float2& s) {
-    const dfl z(0.f, 0.f);
-    const dfl ax(a.x, 0.f), ay(a.y, 0.f), bx(b.x, 0.f), by(b.y, 0.f);
-    const dfl aa = dot2_acc(z, ax, ax, ay, ay);
-    const dfl bb = dot2_acc(z, bx, bx, by, by);
-    if (!(aa.hi > 0.f)) {
-        c = 0.f;
-        s = make_float2(1.f, 0.f);
-        return;
-    }
-    const dfl rr = aa + bb;
-    const dfl cc = sqroot(aa / rr);
-    const dfl k = dfl(1.f, 0.f) / sqroot(aa * rr);
-    const dfl re = dot2_acc(z, ax, bx, ay, by);   // Re(a conj(b))
-    const dfl im = dot2_acc(z, ay, bx, -ax, by);  // Im(a conj(b))
-    const dfl sr = re * k, si = im * k;
-    c = cc.hi + cc.lo;
-    s = make_float2(sr.hi + sr.lo, si.hi + si.lo);
-}
-
-template <bool kAccurate>
 __device__ void sh_chase(int n, float* dd, float2* e1, float2* e2c, float2* bul) {
     const int lane = threadIdx.x & 31;
     if (n < 3) return;
@@ -462,8 +436,7 @@ __device__ void sh_chase(int n, float* dd, float2* e1, float2* e2c, float2* bul)
             if (aa + bb > 0.f) {
                 float c;
                 float2 sv;
-                if constexpr (kAccurate) sh_rot_params_df(a, b, c, sv);
-                else sh_rot_params(a, b, aa, bb, c, sv);
+                sh_rot_params(a, b, aa, bb, c, sv);
                 const float2 sc = sh_conj(sv);
                 const float2 r_ = cadd(sh_scale(a, c), sh_mul(sv, b));
                 if (st == 0) {
@@ -494,6 +467,81 @@ __device__ void sh_chase(int n, float* dd, float2* e1, float2* e2c, float2* bul)
     }
 }
 
+// sh_chase with the band in double-float (dfl entries, about 48 significant
+// bits) and the rotations computed and applied in double-float: the chases of
+// a visit's two matrices then add rounding far below the FP32 reduction's,
+// which is common to both and cancels in dF.  Same rounds and windows.
+__device__ void sh_chase_df(int n, dfl* dd, dfl2* e1, dfl2* e2c, dfl2* bul) {
+    const int lane = threadIdx.x & 31;
+    if (n < 3) return;
+    const dfl z(0.f, 0.f);
+    const dfl2 zero = mk(z, z);
+    const int rounds = 4 * (n - 3) + 1;
+    for (int r = 0; r < rounds; ++r) {
+        const int K = r >> 2;
+        for (int k = K - ((K - lane) & 31); k >= 0; k -= 32) {
+            const int st = r - 4 * k;
+            if (k > n - 3) continue;
+            if (st > (n - 3 - k) / 2) break;
+            const int p = k + 1 + 2 * st, q = p + 1;
+            const bool r2 = p + 2 < n, r3 = p + 3 < n;
+            const dfl2 a = st == 0 ? e1[p - 1] : e2c[p - 2];
+            const dfl2 b = st == 0 ? e2c[p - 1] : bul[p - 2];
+            const dfl2 x1 = e1[p - 1], y1 = e2c[p - 1];
+            const dfl dp = dd[p], dq = dd[q];
+            const dfl2 ep = e1[p];
+            const dfl2 x2 = r2 ? e2c[p] : zero, y2 = r2 ? e1[p + 1] : zero;
+            const dfl2 y3 = r3 ? e2c[p + 1] : zero;
+            const dfl aa = cabs2(a), bb = cabs2(b);
+            if (!(aa.hi > 0.f) && !(bb.hi > 0.f)) continue;
+            dfl c;
+            dfl2 sv;
+            if (aa.hi > 0.f) {
+                const dfl rr = aa + bb;
+                c = sqroot(aa / rr);
+                const dfl kk = dfl(1.f, 0.f) / sqroot(aa * rr);
+                const dfl2 ab = cfma_conj_a(b, a, zero);  // conj(b) a
+                sv = mk(ab.x * kk, ab.y * kk);
+            } else {
+                c = z;
+                sv = mk(dfl(1.f, 0.f), z);
+            }
+            const dfl2 sc = mk(sv.x, -sv.y);
+            auto lin = [](dfl cc, dfl2 x, dfl2 s, dfl2 y) {  // c x + s y
+                return cfma(s, y, mk(x.x * cc, x.y * cc));
+            };
+            const dfl2 r_ = lin(c, a, sv, b);
+            if (st == 0) {
+                e1[p - 1] = r_;
+                e2c[p - 1] = zero;
+            } else {
+                e2c[p - 2] = r_;
+                bul[p - 2] = zero;
+                e1[p - 1] = lin(c, x1, sv, y1);
+                e2c[p - 1] = csub(mk(y1.x * c, y1.y * c), cfma(sc, x1, zero));
+            }
+            const dfl re = dot2_acc(z, sv.x, ep.x, -sv.y, ep.y);  // Re(s ep)
+            const dfl c2 = c * c, s2 = cabs2(sv);
+            const dfl two_c_re = (c + c) * re;
+            dd[p] = c2 * dp + two_c_re + s2 * dq;
+            dd[q] = s2 * dp - two_c_re + c2 * dq;
+            // c conj(s) (dq - dp) + c^2 ep - conj(s)^2 conj(ep)
+            const dfl cd = c * (dq - dp);
+            const dfl2 sc2 = cfma(sc, sc, zero);
+            e1[p] = csub(mk(sc.x * cd + ep.x * c2, sc.y * cd + ep.y * c2), cfma(sc2, mk(ep.x, -ep.y), zero));
+            if (r2) {
+                e2c[p] = lin(c, x2, sc, y2);
+                e1[p + 1] = csub(mk(y2.x * c, y2.y * c), cfma(sv, x2, zero));
+            }
+            if (r3) {
+                bul[p] = cfma(sc, y3, zero);
+                e2c[p + 1] = mk(y3.x * c, y3.y * c);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // After the reduction: the two bands (the reduction's band with the old and
 // the new leading block, t11 in thread 0's registers) into bandmem, their
 // chases (warp 0: old, warp 1: new), both eigenvalue phases with their
@@ -503,24 +551,36 @@ template <int NWP, bool kAccurate>
 __device__ void sh_finish(const StageArgs& a, const StageVar v, int c, int site, const Window& w, int n,
                           const double* so, const double* s_new, const double* cls, const float2* M,
                           const float* t11, unsigned char* bandmem, unsigned char* eigmem, int nm) {
-    float2* bnd = reinterpret_cast<float2*>(bandmem);
-    const int BS = 3 * nm + nm / 2;  // float2 per band: e1, e2c, bul, dd
+    // band element: float2 (FP32 chase) or dfl2 (double-float chase); per band
+    // e1, e2c, bul (nm each) and the diagonal (nm reals, nm / 2 elements)
+    using BE = typename std::conditional<kAccurate, dfl2, float2>::type;
+    using BR = typename std::conditional<kAccurate, dfl, float>::type;
+    BE* bnd = reinterpret_cast<BE*>(bandmem);
+    const int BS = 3 * nm + nm / 2;
+    auto be = [](float2 x) -> BE {
+        if constexpr (kAccurate) return mk(dfl(x.x, 0.f), dfl(x.y, 0.f));
+        else return x;
+    };
+    auto br = [](float x) -> BR {
+        if constexpr (kAccurate) return dfl(x, 0.f);
+        else return x;
+    };
     const float2 zero = make_float2(0.f, 0.f);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float2 b1 = (i >= 1 && i + 1 < n) ? M[sh_at(i + 1, i)] : zero;
         const float2 b2 = i + 2 < n ? M[sh_at(i + 2, i)] : zero;
         const float b0 = i >= 2 ? M[sh_at(i, i)].x : 0.f;
         for (int var = 0; var < 2; ++var) {
-            float2* e1 = bnd + var * BS;
-            float* dd = reinterpret_cast<float*>(e1 + 3 * nm);
-            if (i >= 1) e1[i] = b1;
-            e1[nm + i] = b2;
-            e1[2 * nm + i] = zero;
-            if (i >= 2) dd[i] = b0;
+            BE* e1 = bnd + var * BS;
+            BR* dd = reinterpret_cast<BR*>(e1 + 3 * nm);
+            if (i >= 1) e1[i] = be(b1);
+            e1[nm + i] = be(b2);
+            e1[2 * nm + i] = be(zero);
+            if (i >= 2) dd[i] = br(b0);
             if (i == 0) {
-                dd[0] = t11[4 * var];
-                dd[1] = t11[4 * var + 1];
-                e1[0] = make_float2(t11[4 * var + 2], t11[4 * var + 3]);
+                dd[0] = br(t11[4 * var]);
+                dd[1] = br(t11[4 * var + 1]);
+                e1[0] = be(make_float2(t11[4 * var + 2], t11[4 * var + 3]));
             }
         }
     }
@@ -529,13 +589,20 @@ __device__ void sh_finish(const StageArgs& a, const StageVar v, int c, int site,
     double* dv = reinterpret_cast<double*>(eigmem);  // [2 var][d, e2][nm]
     const int warp = threadIdx.x >> 5;
     if (warp < 2) {
-        float2* e1 = bnd + warp * BS;
-        float* dd = reinterpret_cast<float*>(e1 + 3 * nm);
-        sh_chase<kAccurate>(n, dd, e1, e1 + nm, e1 + 2 * nm);
+        BE* e1 = bnd + warp * BS;
+        BR* dd = reinterpret_cast<BR*>(e1 + 3 * nm);
+        if constexpr (kAccurate) sh_chase_df(n, dd, e1, e1 + nm, e1 + 2 * nm);
+        else sh_chase(n, dd, e1, e1 + nm, e1 + 2 * nm);
         double* d = dv + 2 * warp * nm;
         for (int i = threadIdx.x & 31; i < n; i += 32) {
-            d[i] = (double)dd[i];
-            d[nm + i] = i < n - 1 ? (double)(e1[i].x * e1[i].x + e1[i].y * e1[i].y) : 0.0;
+            if constexpr (kAccurate) {
+                d[i] = (double)dd[i];
+                const double ex = (double)e1[i].x, ey = (double)e1[i].y;
+                d[nm + i] = i < n - 1 ? ex * ex + ey * ey : 0.0;
+            } else {
+                d[i] = (double)dd[i];
+                d[nm + i] = i < n - 1 ? (double)(e1[i].x * e1[i].x + e1[i].y * e1[i].y) : 0.0;
+            }
         }
     }
     __syncthreads();
@@ -912,7 +979,7 @@ __device__ __forceinline__ void stage_item_large_shared(const StageArgs& a, cons
     shl_reduce(n, M, Wv, Va, Vb, pr, pc, red, nm);
     // bands and the eigenvalue phase in the column-sum region
     unsigned char* bandmem = smem + L.pc;
-    unsigned char* eigmem = bandmem + align16((size_t)2 * (3 * nm + nm / 2) * sizeof(float2));
+    unsigned char* eigmem = bandmem + align16((size_t)2 * (3 * nm + nm / 2) * sizeof(dfl2));
     sh_finish<SHL_NW, true>(a, v, c, site, w, n, so, s_new, cls, M, t11, bandmem, eigmem, nm);
 }
 

@@ -214,3 +214,49 @@ def test_large_shared_and_default_large_kernels_compute_the_same_chain():
         assert np.max(np.abs(Fn2 - Fn) / np.maximum(1.0, np.abs(Fn))) < 1e-5
     for x, y in zip(runs[1][1], runs[2][1]):
         assert np.array_equal(x, y)
+
+
+def test_large_mixed_contexts_default_to_the_shared_reduction():
+    # large clusters in PTCA_MIXED start on the shared reduction (faster than
+    # the per-matrix kernel, and its dF error far smaller: its chases run in
+    # double-float); FP64 contexts keep the per-matrix kernel; the autotuner
+    # times both
+    mixed = P.Context(P.Config(Lx=24, Ly=24, L_c=12, schedule=P.SCHEDULE_BLOCK, precision=P.MIXED))
+    got = P.ptca_get_launch_config(mixed.h)
+    assert (got.pipeline, got.warps_per_cta, got.reduction) == (P.PIPELINE_STAGES, 16, P.REDUCTION_SHARED)
+    best, table = P.ptca_autotune(mixed.h, 1)
+    shared = [c for c in table["candidates"] if c["reduction"] == P.REDUCTION_SHARED]
+    assert {c["pipeline"] for c in shared} == {"stages", "overlap"}
+    assert all(c["ms_per_sweep"] is not None for c in shared)
+    mixed.close()
+    fp64 = P.Context(P.Config(Lx=24, Ly=24, L_c=12, schedule=P.SCHEDULE_BLOCK, precision=P.FP64))
+    assert P.ptca_get_launch_config(fp64.h).reduction == P.REDUCTION_ROWS
+    with pytest.raises(P.PtcaError):
+        P.ptca_set_launch_config(fp64.h, *LARGE_SHARED_STAGES)
+    fp64.close()
+
+
+def test_large_shared_dF_error_is_far_below_the_per_matrix_kernels():
+    # Stage 0 of a 48x48 torus with 12x12 clusters (n = 288), unguarded:
+    # dF against the FP64 path on the same start, every visit of the stage.
+    # The shared reduction's FP32 rounding is common to both matrices and its
+    # chases run in double-float (measured max 4.6e-7 against 2.0e-4 for the
+    # per-matrix kernel).
+    base = dict(Lx=48, Ly=48, L_c=12, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, cone_deg=30.0,
+                T=0.05, mu=-6.5, seed=1)
+    n0 = len(P.ptca_schedule(P.Config(**base, precision=P.FP64))[0])
+    ref = P.Context(P.Config(**base, precision=P.FP64))
+    ref.sweep(1)
+    _, Fo64, Fn64, _, _ = (x.cpu().numpy()[:n0] for x in ref.record())
+    ref.close()
+    err = {}
+    for red in (P.REDUCTION_ROWS, P.REDUCTION_SHARED):
+        ctx = P.Context(P.Config(**base, precision=P.MIXED))
+        P.ptca_set_launch_config(ctx.h, P.PIPELINE_STAGES, 16, 0, red)
+        P.ptca_set_resolve_margin(ctx.h, 0.0)
+        ctx.sweep(1)
+        _, Fo, Fn, _, _ = (x.cpu().numpy()[:n0] for x in ctx.record())
+        ctx.close()
+        err[red] = np.max(np.abs((Fn - Fo) - (Fn64 - Fo64)))
+    assert err[P.REDUCTION_SHARED] < 5e-6
+    assert err[P.REDUCTION_SHARED] < 0.05 * err[P.REDUCTION_ROWS]
