@@ -380,8 +380,12 @@ ptca_status ptca_kernel_times(ptca_ctx* ctx, double* out, void* stream);
  * decision is taken on that dF, before the next stage starts.  With a
  * margin above T^-1 times the largest dF error this makes decisions identical
  * to the FP64 path wherever the FP64 margin exceeds its own error.  Default
- * 1e-2 in PTCA_MIXED; 0 disables it.  The count of re-solved updates is
- * ptca_sweep_stats.resolved.  Rejected (PTCA_ERR_INVALID) for PTCA_FP64. */
+ * in PTCA_MIXED: 1e-2; 1e-4 for large clusters on the shared reduction
+ * (launch configuration reduction = PTCA_REDUCTION_SHARED, their default),
+ * whose dF error is about 5e-7.  The default follows the launch
+ * configuration until the caller sets a margin here; 0 disables it.  The
+ * count of re-solved updates is ptca_sweep_stats.resolved.  Rejected
+ * (PTCA_ERR_INVALID) for PTCA_FP64. */
 ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin);
 
 /* Precision checker (PTCA_MIXED only; PTCA_ERR_UNSUPPORTED otherwise).  While

@@ -355,6 +355,16 @@ ptca_status ptca_stage_split(const ptca_lattice* lattice, const ptca_params* par
     return PTCA_OK;
 }
 
+// Default re-solve margin of a PTCA_MIXED context (unless the caller set
+// one): 5 to 10 times beta times the largest FP32 dF error measured for its
+// reduction.  The per-matrix reductions leave up to about 2e-4 (n = 128 to
+// 288), hence 1e-2; the large-cluster shared reduction, whose chases run in
+// double-float, about 5e-7, hence 1e-4.
+static void default_margin(ptca_ctx* c) {
+    if (c->prec != 1 || c->margin_set) return;
+    c->margin = (c->large && c->reduction == 2) ? 1e-4 : 1e-2;
+}
+
 ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, ptca_ctx** out) {
     if (!out) return fail(PTCA_ERR_INVALID, "null out");
     *out = nullptr;
@@ -479,7 +489,7 @@ ptca_status ptca_init(const ptca_lattice* lattice, const ptca_params* params, pt
             // + 64 elements: the fused pass may load up to 31 elements past a
             // slot (masked lanes of the diagonal chunk), also past the last.
             ce = dalloc(&c->d_gA, (size_t)slots * (size_t)c->gA_stride + 64);
-            c->margin = 1e-2;
+            default_margin(c);
         }
     }
     if (ce == cudaSuccess) ce = cudaMemset(c->d_rec_acc, 0, N);
@@ -1133,6 +1143,7 @@ ptca_status ptca_set_launch_config(ptca_ctx* ctx, const ptca_launch_config* cfg)
     ctx->ctas_per_sm = cfg->ctas_per_sm;
     ctx->reduction = cfg->reduction;
     ctx->panel = cfg->panel_width > 1 ? cfg->panel_width : 0;
+    default_margin(ctx);
     ctx->grid = maxb > 0 ? ctx->sms * (cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : maxb) : 0;
     ctx->graph_failed = false;
     drop_graph(ctx);
@@ -1281,6 +1292,7 @@ ptca_status ptca_set_resolve_margin(ptca_ctx* ctx, double margin) {
     if (ctx->prec != 1 && margin > 0.0) return fail(PTCA_ERR_INVALID, "the re-solve margin applies to PTCA_MIXED only");
     PTCA_SETTLE_SYNC(ctx);
     ctx->margin = margin;
+    ctx->margin_set = true;
     drop_graph(ctx);
     return PTCA_OK;
 }

@@ -96,6 +96,7 @@ struct ptca_ctx {
     bool graph_failed = false;
     // PTCA_MIXED decision guard
     double margin = 0.0;
+    bool margin_set = false;              // chosen by the caller (ptca_set_resolve_margin)
     int32_t* d_flag_list = nullptr;       // [2][max_stage]
     unsigned int* d_flag_count = nullptr; // [2]
     double2* d_gA = nullptr;

@@ -260,3 +260,39 @@ def test_large_shared_dF_error_is_far_below_the_per_matrix_kernels():
         err[red] = np.max(np.abs((Fn - Fo) - (Fn64 - Fo64)))
     assert err[P.REDUCTION_SHARED] < 5e-6
     assert err[P.REDUCTION_SHARED] < 0.05 * err[P.REDUCTION_ROWS]
+
+
+def test_large_shared_default_margin_follows_the_launch_configuration():
+    # n = 288: the shared reduction's default re-solve margin is 1e-4 (its dF
+    # error is about 5e-7); a margin the caller sets is kept across launch
+    # configurations.  Runs compare bit for bit against explicit margins.
+    cfg = P.Config(Lx=24, Ly=24, L_c=12, schedule=P.SCHEDULE_BLOCK, proposal=P.PROPOSAL_CONE, T=0.05, seed=6,
+                   precision=P.MIXED)
+
+    def run(setup):
+        ctx = P.Context(cfg)
+        setup(ctx)
+        st = ctx.sweep(2)
+        rec = [x.cpu().numpy() for x in ctx.record()]
+        ctx.close()
+        return st.resolved, rec
+
+    r_default, rec_default = run(lambda c: None)
+    r_1e4, rec_1e4 = run(lambda c: P.ptca_set_resolve_margin(c.h, 1e-4))
+    assert r_default == r_1e4
+    for x, y in zip(rec_default, rec_1e4):
+        assert np.array_equal(x, y)
+
+    def switch(c):  # through the per-matrix kernel and back: the default follows
+        P.ptca_set_launch_config(c.h, P.PIPELINE_STAGES, 16, 0, P.REDUCTION_ROWS)
+        P.ptca_set_launch_config(c.h, *LARGE_SHARED_STAGES)
+    r_switch, rec_switch = run(switch)
+    assert r_switch == r_default
+    for x, y in zip(rec_default, rec_switch):
+        assert np.array_equal(x, y)
+
+    def user_margin(c):  # set by the caller: kept
+        P.ptca_set_resolve_margin(c.h, 1e-2)
+        P.ptca_set_launch_config(c.h, *LARGE_SHARED_STAGES)
+    r_user, _ = run(user_margin)
+    assert r_user >= r_default
