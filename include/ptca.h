@@ -274,7 +274,11 @@ ptca_status ptca_sweep(ptca_ctx* ctx, int32_t n_sweeps, ptca_sweep_stats* stats_
  *                             checker on and with surrogate screening.
  * Every pipeline computes the same chain, bit for bit.  Every barrier wait is
  * bounded by barrier_timeout_s (default 30 s): past it the kernel stops and
- * ptca_sweep (with stats) returns PTCA_ERR_TIMEOUT. */
+ * ptca_sweep (with stats) returns PTCA_ERR_TIMEOUT.  The persistent kernels
+ * run the row-chunked reduction, one per matrix: selecting
+ * PTCA_PIPELINE_PERSISTENT or PTCA_PIPELINE_GRAPH here resets the launch
+ * configuration's reduction and panel_width to 0 (and a default re-solve
+ * margin to that reduction's, ptca_set_resolve_margin). */
 ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeout_s);
 
 /* Launch configuration of the sweep kernels:

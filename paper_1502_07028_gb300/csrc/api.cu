@@ -1024,6 +1024,13 @@ ptca_status ptca_set_pipeline(ptca_ctx* ctx, int32_t mode, double barrier_timeou
     }
     ctx->pipeline = mode;
     ctx->timeout_ns = (unsigned long long)(barrier_timeout_s * 1e9);
+    if (persistent) {
+        // the persistent kernels run the row-chunked reduction, one per
+        // matrix; the margin must then be that reduction's
+        ctx->reduction = 0;
+        ctx->panel = 0;
+        default_margin(ctx);
+    }
     drop_graph(ctx);
     return PTCA_OK;
 }

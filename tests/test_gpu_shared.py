@@ -302,3 +302,30 @@ def test_large_shared_default_margin_follows_the_launch_configuration():
         P.ptca_set_launch_config(c.h, *LARGE_SHARED_STAGES)
     r_user, _ = run(user_margin)
     assert r_user >= r_default
+
+
+def test_persistent_pipelines_return_large_contexts_to_the_per_matrix_reduction():
+    # The persistent kernels reduce one matrix at a time: selecting one with
+    # ptca_set_pipeline resets the reduction, and the sweep matches the
+    # per-stage per-matrix sweep bit for bit (every decision re-solved, as in
+    # the large-cluster pipeline tests).
+    cfg = P.Config(Lx=24, Ly=24, L_c=12, schedule=P.SCHEDULE_BLOCK, T=0.1, seed=7, precision=P.MIXED,
+                   proposal=P.PROPOSAL_CONE)
+    ref = P.Context(cfg)
+    P.ptca_set_launch_config(ref.h, P.PIPELINE_STAGES, 16, 0, P.REDUCTION_ROWS)
+    P.ptca_set_resolve_margin(ref.h, 1e6)
+    ref.sweep(1)
+    rec_ref = [x.cpu().numpy() for x in ref.record()]
+    S_ref = ref.spins().cpu().numpy()
+    ref.close()
+    ctx = P.Context(cfg)
+    assert P.ptca_get_launch_config(ctx.h).reduction == P.REDUCTION_SHARED
+    P.ptca_set_resolve_margin(ctx.h, 1e6)
+    P.ptca_set_pipeline(ctx.h, P.PIPELINE_PERSISTENT)
+    got = P.ptca_get_launch_config(ctx.h)
+    assert (got.pipeline, got.reduction) == (P.PIPELINE_PERSISTENT, P.REDUCTION_ROWS)
+    ctx.sweep(1)
+    assert np.array_equal(ctx.spins().cpu().numpy(), S_ref)
+    for x, y in zip(rec_ref, (r.cpu().numpy() for r in ctx.record())):
+        assert np.array_equal(x, y)
+    ctx.close()
