@@ -1,9 +1,8 @@
 // spectrum.cu -- full-system spectrum of a configuration (Sec. VI): all 2N
 // eigenvalues of the whole lattice's one-body Hamiltonian, where the paper
 // diagonalises saved configurations with ScaLAPACK.  Everything runs in this
-// library's kernels, off the sweep's hot path (FP64 throughout for FP64
-// contexts; a PTCA_MIXED context runs step 2's O(n^3) pass in double-float
-// on the FP32 pipe):
+// library's kernels, off the sweep's hot path (step 2 in FP64 for FP64
+// contexts and in double-float on the FP32 pipe for PTCA_MIXED contexts):
 //   1. the dense matrix is built as its packed lower triangle (row-major:
 //      element (i, j <= i) at i(i+1)/2 + j) in global memory;
 //   2. a Householder reduction to real tridiagonal form spread over the whole
